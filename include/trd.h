@@ -1,0 +1,256 @@
+/*
+ * trd.h -- C ABI of libtrd: the per-core hot path of auto-weighted robust tensor-ring
+ * decomposition (AWRTRD) and its scalable variant with FGMC and RStS (SAWRTRD), from
+ * He & Atia, "Scalable and Robust Tensor Ring Decomposition for Large-scale Data",
+ * UAI 2023, on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions used by every call
+ *   - Indices are 0-based.  A tensor of order N with mode sizes I[0..N-1] is stored flat
+ *     with i_1 fastest: offset = sum_m i_m * prod_{m'<m} I[m'] (the multi-index
+ *     overline{i_1 ... i_N} of Def. 2).
+ *   - Ranks: R[k] is r_k, the first rank of core k; core k is r_k x I_k x r_{k+1} with
+ *     r_{N+1} = r_1 (Def. 1).
+ *   - Host core layout ("mode-2 unfolding, row-major"): core k is I_k rows of
+ *     K_k = r_k r_{k+1} doubles; element (alpha, i, beta) of Z_k sits at
+ *     i*K_k + beta*r_k + alpha, i.e. row i of Z_{k(2)} with column alpha + beta*r_k.
+ *     Gradients d and scaled gradients h use the same layout; Gram matrices are K_k x K_k
+ *     row-major with that column order on both sides.
+ *   - The observation mask is bit-packed: bit b of 32-bit word w is linear index 32w+b,
+ *     1 = observed (the binary tensor P of Eq. TRWOPT).
+ *   - Device pointers passed in are BORROWED: the caller owns them, they must stay valid
+ *     while the handle uses them, and the library never frees them.  Host pointers are
+ *     only read or written during the call.
+ *   - Every call is ordered on the handle's CUDA stream.  Calls that return values
+ *     through host pointers synchronise that stream before returning.
+ *   - No call aborts or throws.  Each returns a trd_status; trd_last_error() gives a
+ *     one-line message for the last failure on the handle.  After TRD_ECUDA the handle
+ *     should be destroyed.
+ *   - The library has no CPU fallback: without a usable CUDA device trd_create fails.
+ */
+#ifndef TRD_H
+#define TRD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TRD_MAX_ORDER 8   /* tensor order N is 3..TRD_MAX_ORDER */
+#define TRD_MAX_RANK 32   /* every r_k is 1..TRD_MAX_RANK */
+
+typedef enum {
+  TRD_OK = 0,
+  TRD_EINVAL = 1,      /* bad argument, unsupported shape, or calls in the wrong order */
+  TRD_ENOMEM = 2,      /* a device or host allocation failed */
+  TRD_ECUDA = 3,       /* a CUDA runtime call or a kernel launch failed */
+  TRD_ESINGULAR = 4,   /* G + lambda I is not numerically positive definite */
+  TRD_ENONFINITE = 5,  /* non-finite residuals, gradient or step size */
+  TRD_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+  TRD_ENOTIMPL = 7     /* combination not implemented (e.g. precision for this shape) */
+} trd_status;
+
+typedef enum {
+  TRD_FP64 = 0,  /* SIMT FP64 data passes (small problems, debugging) */
+  TRD_FP32 = 1,  /* SIMT FP32 data passes, FP32 accumulation */
+  TRD_BF16 = 2   /* tcgen05 tensor cores: split-BF16 reconstruction, BF16 gradient and
+                    line-search products, FP32 accumulation; residual and weight in FP32 */
+} trd_precision;
+
+typedef enum {
+  TRD_GRAM_GLOBAL = 0,  /* Eq. hI: G of the full cores, by FGMC (the paper's method) */
+  TRD_GRAM_LOCAL = 1,   /* ablation 'local scaled term' (Sec. 5.1): G of the sampled cores */
+  TRD_GRAM_NONE = 2     /* ablation 'gradient descent' (Sec. 5.1): h = d */
+} trd_gram_kind;
+
+typedef struct trd_handle trd_t;
+
+/* Statistics of one reconstruction/residual/weight pass (Eq. updatew on the sketch). */
+typedef struct {
+  double sigma;        /* kernel width used (+inf means W = 1) */
+  double sum_w;        /* sum of w over observed slots */
+  double sum_e2;       /* sum of e^2 over observed slots */
+  double sum_we2;      /* sum of w e^2 over observed slots (2x the weighted objective) */
+  int64_t n_obs;       /* observed slots */
+  int64_t n_nonfinite; /* observed slots whose residual is not finite */
+  int64_t n_slots;     /* slots visited (observed or not) */
+} trd_resid_stats;
+
+/* Parameters of one outer iteration of Algorithm 1. */
+typedef struct {
+  int32_t sketch[TRD_MAX_ORDER]; /* RStS size s_j for every non-updated mode j; 0 = full
+                                    mode (AWRTRD when all are 0).  s_k = I_k always. */
+  double sigma;     /* > 0: fixed kernel width; +inf: W = 1; <= 0: adaptive width */
+  double lambda;    /* Eq. sg regulariser; >= 0 absolute, < 0 means |lambda| tr(G)/K */
+  uint64_t seed;    /* seed of the RStS index draws (SplitMix64, see trd_draw_indices) */
+  int32_t gram;     /* trd_gram_kind */
+  int32_t reserved;
+} trd_params;
+
+/* Result of one outer iteration. */
+typedef struct {
+  double e;                    /* Algorithm 1 stopping quantity ||D^t - D^{t-1}|| / ||D^t|| */
+  double sigma;                /* kernel width used in this iteration */
+  double eta[TRD_MAX_ORDER];   /* step size of every core update */
+  double objective[TRD_MAX_ORDER]; /* 0.5 sum w e^2 on the sketch before each update */
+  int64_t slots;               /* sketch slots visited by the data passes (all cores) */
+  int32_t t;                   /* iteration counter after this step */
+  int32_t reserved;
+} trd_report;
+
+/* ---------------------------------------------------------------- handle */
+
+/* Create a handle for an order-N tensor (3 <= N <= TRD_MAX_ORDER) with mode sizes I[0..N-1]
+ * (each >= 1, product < 2^40) and ring ranks R[0..N-1] (Def. 1, 1 <= r_k <= TRD_MAX_RANK).
+ * `precision` is a trd_precision.  `cuda_stream` is a cudaStream_t (NULL = legacy default
+ * stream) on which every call is ordered; it must outlive the handle.  Allocates the
+ * library's own device state (cores, FGMC factors, work buffers); no data is copied.
+ * Errors: TRD_EINVAL (shape), TRD_ENOMEM, TRD_ECUDA (no usable device). */
+trd_status trd_create(trd_t** handle, int N, const int64_t* I, const int32_t* R,
+                      int precision, void* cuda_stream);
+
+/* Free everything the handle allocated (never the caller's buffers).  NULL is a no-op. */
+void trd_destroy(trd_t* handle);
+
+/* Message for the last failing call on `handle` ("" if none); owned by the handle. */
+const char* trd_last_error(const trd_t* handle);
+
+/* Static name of a status code. */
+const char* trd_status_string(trd_status status);
+
+/* ---------------------------------------------------------------- data and cores */
+
+/* Attach the data tensor X (Eq. TRWOPT) and its observation mask P (Eq. TRWOPT; bit-packed,
+ * ceil(prod I / 32) words, 1 = observed).  Both are DEVICE pointers, borrowed: X is prod(I)
+ * floats in the linear order above, 16-byte aligned.  mask may be NULL, meaning fully
+ * observed.  Resets any sketch.  Errors: TRD_EINVAL (NULL X, misalignment). */
+trd_status trd_set_data(trd_t* handle, const float* X_dev, const uint32_t* mask_dev);
+
+/* Initialise all cores i.i.d. Gaussian (Algorithm 1, 'initialize Z_k'; the law is a
+ * reading, the paper does not state it): entry (alpha, i, beta) of core k is
+ * stddev * Box-Muller normal number base_k + (i r_{k+1} + beta) r_k + alpha of the
+ * SplitMix64 stream of `seed` (u1 from output 2g, u2 from output 2g+1; base_k = entries of
+ * the cores before k).  stddev <= 0 means (r_k r_{k+1})^(-1/4).  Refreshes the FGMC
+ * factors and D^0 and resets the iteration counter. */
+trd_status trd_init_cores(trd_t* handle, uint64_t seed, double stddev);
+
+/* Copy core k (host, I_k * r_k * r_{k+1} doubles, layout above) into / out of the handle.
+ * trd_set_core refreshes the FGMC factor of core k and invalidates cached merges; call
+ * trd_reset_iteration afterwards to recompute D^0 for the stopping rule. */
+trd_status trd_set_core(trd_t* handle, int k, const double* core_host);
+trd_status trd_get_core(trd_t* handle, int k, double* core_host);
+
+/* Recompute D^0 from the current cores and set the iteration counter to t. */
+trd_status trd_reset_iteration(trd_t* handle, int32_t t);
+
+/* ---------------------------------------------------------------- the hot path */
+
+/* RStS (Sec. 3.2.2, Algorithm 1 'obtain subtensor'): for an update of core k, take the
+ * index sets idx[j] (HOST arrays of s[j] int32 each, strictly increasing, in [0, I_j)) for
+ * every j != k; idx[k] and s[k] are ignored (mode k is kept whole).  Gathers the sketch
+ * X_I and P_I into library-owned device memory and selects the sampled core slices.
+ * idx == NULL selects the whole tensor (AWRTRD).  Errors: TRD_EINVAL (unsorted,
+ * duplicated or out-of-range indices, no data). */
+trd_status trd_sample_subtensor(trd_t* handle, int k, const int32_t* const* idx,
+                                const int32_t* s);
+
+/* RStS index draw used by trd_step (host-side, no device work): s distinct indices of
+ * [0, I), uniform without replacement, sorted.  Key = SplitMix64 output (t N + k) N + j of
+ * `seed`; a partial Fisher-Yates shuffle of 0..I-1 then takes pick m = m + (z_m mod (I-m))
+ * with z_m the key's m-th output.  out has room for s ints. */
+trd_status trd_draw_indices(uint64_t seed, int32_t t, int k, int j, int N, int64_t I,
+                            int32_t s, int32_t* out);
+
+/* Steps 'update W' and the first half of 'compute d' for core k on the current sketch:
+ * reconstruct X_hat_I[k] = Z_{k(2)} (Z^{!=k}_{I[2]})^T (Thm. 1), residual e = x - x_hat on
+ * observed slots, HQ weight w = exp(-e^2/(2 sigma^2)) (Eq. updatew, sign reading) and the
+ * weighted contraction of Eq. hatd, all in one pass over the sketch (W is never stored).
+ * sigma > 0 fixed, +inf gives w = 1, <= 0 uses the adaptive width of the current
+ * iteration (computed by trd_adaptive_sigma, or by trd_step).  `out` (host, nullable)
+ * receives the statistics.  Errors: TRD_EINVAL (no data / no sketch for k),
+ * TRD_ENONFINITE (some observed residual not finite; stats still written). */
+trd_status trd_residual_weights(trd_t* handle, int k, double sigma, trd_resid_stats* out);
+
+/* Step 'compute d_I(Z_{k(2)})' (Eq. hatd): finish the weighted gradient of core k from
+ * the last trd_residual_weights pass for k, as an I_k x K_k matrix kept on the device;
+ * d_host (nullable) receives a copy (layout above).  d is the NEGATIVE gradient of
+ * 0.5 ||sqrt(W) o P o (X_I - X_hat_I)||^2 with W held fixed.
+ * Errors: TRD_EINVAL (no residual pass for k). */
+trd_status trd_core_gradient(trd_t* handle, int k, double* d_host);
+
+/* Step 'obtain G' (Eq. FGMC, Prop. 2): G = (Z^{!=k}_[2])^T Z^{!=k}_[2] of the FULL cores
+ * as a chain product of the per-core factors E_m = sum_i Z_m(i) (x) Z_m(i) (r_m^2 x
+ * r_{m+1}^2, FP64) over m = k+1..N, 1..k-1, realigned to K_k x K_k.  Kept on the device;
+ * G_host (nullable) receives a copy. */
+trd_status trd_fgmc_gram(trd_t* handle, int k, double* G_host);
+
+/* Step 'update Z_k' (Eq. hI, Eq. ftrbcn and the exact line search): h = d (G + lambda I)^-1
+ * by FP64 Cholesky; eta = <d,h> / ||sqrt(W) o P o (h B^T)||^2 on the sketch when eta <= 0
+ * (second data pass, W recomputed from the same residuals), else the given eta;
+ * Z_k <- Z_k + eta fold(h) (update-sign reading); refreshes core k's FGMC factor.
+ * lambda >= 0 absolute, < 0 means |lambda| tr(G)/K.  `gram` is a trd_gram_kind.
+ * eta_out (host, nullable) receives the step used.  Needs trd_core_gradient for k; runs
+ * trd_fgmc_gram itself when needed.  Errors: TRD_ESINGULAR, TRD_ENONFINITE. */
+trd_status trd_core_update(trd_t* handle, int k, double lambda, double eta, int gram,
+                           double* eta_out);
+
+/* One outer iteration of Algorithm 1: adaptive width (if params->sigma <= 0), then for
+ * k = 1..N: index draw + RStS gather (if sketched), residual/weights/gradient pass, FGMC
+ * Gram, scaled update with exact line search; then D^t = Z_{N(2)} G^{!=N} Z_{N(2)}^T and
+ * e = ||D^t - D^{t-1}||_F / ||D^t||_F.  report (host, nullable) is filled.  Synchronises. */
+trd_status trd_step(trd_t* handle, const trd_params* params, trd_report* report);
+
+/* ---------------------------------------------------------------- evaluation helpers */
+
+/* Adaptive kernel width (Sec. 5 cites a rule it does not state; reading):
+ * sigma = max(1e-6 rms(x_obs), 2 min(std(e), IQR(e)/1.349), 0.9 sigma_prev) over the
+ * observed residuals e of the full tensor (or of a fixed probe of 2^20 entries when the
+ * tensor has more than 2^20 entries: probe m is linear index SplitMix64(0x5eed, m) mod
+ * numel), population std, type-7 quartiles.  sigma_prev <= 0 or inf disables the
+ * limiter.  Becomes the width used by sigma <= 0 calls.  sigma_out (host) receives it. */
+trd_status trd_adaptive_sigma(trd_t* handle, double sigma_prev, double* sigma_out);
+
+/* Same rule on a caller-given DEVICE array of n residuals (float), for checking the
+ * selection: x_obs_rms is the rms of the observed data used for the floor. */
+trd_status trd_sigma_from_residuals(trd_t* handle, const float* resid_dev, int64_t n,
+                                    double x_obs_rms, double sigma_prev, double* sigma_out);
+
+/* Full TR reconstruction (Def. 1) of the current cores into the caller's DEVICE buffer
+ * out_dev (prod(I) floats, linear order above). */
+trd_status trd_reconstruct(trd_t* handle, float* out_dev);
+
+/* Reconstruction (Def. 1) of arbitrary cores given on the HOST (layout above) into out_dev;
+ * does not touch the handle's cores.  Used to synthesise exact-rank tensors. */
+trd_status trd_reconstruct_from(trd_t* handle, const double* const* cores_host, float* out_dev);
+
+/* ||X_hat - X_ref||_F / ||X_ref||_F over all entries, X_ref a DEVICE tensor (floats). */
+trd_status trd_recovery_error(trd_t* handle, const float* Xref_dev, double* err_out);
+
+/* ---------------------------------------------------------------- sampled correntropy */
+
+/* Forward of the sampled correntropy loss (Eq. corr in Welsch form) for the cores given
+ * as DEVICE arrays cores_dev[k] (layout above): for M multi-indices idx_dev (DEVICE,
+ * M x N int32, row-major, each i_k in [0, I_k)) and values x_dev (DEVICE, M values):
+ * x_hat_m = Tr(prod_k Z_k(i_mk)) (Def. 1), e_m = x_m - x_hat_m,
+ * loss = sum_m sigma^2 (1 - exp(-e_m^2 / (2 sigma^2))) (sigma > 0, finite).
+ * fp64 = 0: cores, x and resid are float arrays and arithmetic is FP32 (FP64 sums);
+ * fp64 = 1: all are double arrays and arithmetic is FP64.  resid_dev (DEVICE, M values,
+ * nullable) receives e_m.  loss_out (host) receives the loss.  Indices are not checked on
+ * the device: out-of-range indices are the caller's error (check with care). */
+trd_status trd_sampled_fwd(trd_t* handle, const void* const* cores_dev, const int32_t* idx_dev,
+                           const void* x_dev, int64_t M, double sigma, int fp64,
+                           void* resid_dev, double* loss_out);
+
+/* Adjoint of trd_sampled_fwd: grad_dev[k] (DEVICE, same layout and type as the cores)
+ * receives g_scale * d loss / d Z_k = g_scale * sum_m -w_m e_m (S_m^{!=k})^T, w_m the HQ
+ * weight exp(-e_m^2/(2 sigma^2)) and S_m^{!=k} the subchain product of Thm. 1 at entry m,
+ * which is recomputed per entry rather than stored.  The arrays are overwritten. */
+trd_status trd_sampled_bwd(trd_t* handle, const void* const* cores_dev, const int32_t* idx_dev,
+                           const void* x_dev, int64_t M, double sigma, int fp64,
+                           double g_scale, void* const* grad_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRD_H */

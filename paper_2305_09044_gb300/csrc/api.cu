@@ -1,0 +1,990 @@
+// C ABI of libtrd: argument checking, device state and the order of the hot-path steps of
+// Algorithm 1 (SAWRTRD; AWRTRD when no sketch is drawn).  Every step's arithmetic runs in
+// the kernels of the other translation units; this file only launches them.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "trd_internal.cuh"
+
+using namespace trd;
+
+namespace trd {
+
+trd_status set_err(trd_handle* h, trd_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+trd_status cuda_check(trd_handle* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return TRD_OK;
+  cudaGetLastError();
+  return set_err(h, TRD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+trd_status ensure(trd_handle* h, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return TRD_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  bytes = (bytes + 255) / 256 * 256;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(h, TRD_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  b.bytes = bytes;
+  return TRD_OK;
+}
+
+// implemented in merge.cu / sampled.cu / pass_tc.cu
+cudaError_t launch_reconstruct_mats(const double* A, const double* C, int64_t P_in, int64_t P_out,
+                                    int Kp, const float* Xref, float* out, double* err_part,
+                                    int parts, cudaStream_t st);
+
+}  // namespace trd
+
+#define TRY(x)                         \
+  do {                                 \
+    trd_status _s = (x);               \
+    if (_s != TRD_OK) return _s;       \
+  } while (0)
+#define CK(x, what) TRY(cuda_check(h, (x), what))
+
+namespace {
+
+// device scalar slots in h->scal
+enum : int { S_SIGMA = 0, S_SIGMA_PREV = 1, S_NUM = 2, S_DEN = 3, S_ETA = 4, S_LAMBDA = 5, S_E = 6 };
+// report_dev layout: [0..7] eta per core, [8..15] objective per core, [16] e, [17] sigma
+enum : int { R_ETA = 0, R_OBJ = 8, R_E = 16, R_SIGMA = 17 };
+
+// extra per-handle buffers that do not need to be visible to other units
+struct Extra {
+  DevBuf meta;          // [N] core pointers, [N] dims (int64), [N] ranks (int)
+  DevBuf stat_sum2;     // pass-2 statistics
+  DevBuf Gloc;          // local Gram (ablation)
+  DevBuf Eloc[kMaxN];   // sampled FGMC factors (ablation)
+  DevBuf recA, recC;    // reconstruction operands
+  DevBuf errp;          // reconstruction error partials
+  DevBuf tmpZ[kMaxN];   // cores given to trd_reconstruct_from
+  DevBuf probe_xsq;
+};
+
+Extra* X_(trd_handle* h);
+
+bool is_fp64(const trd_handle* h) { return h->prec == TRD_FP64; }
+size_t elt(const trd_handle* h) { return is_fp64(h) ? sizeof(double) : sizeof(float); }
+
+// Balanced split of the view's modes into [0, c) and [c, N).
+Split choose_split(const trd_handle* h, const View& v, int k) {
+  Split sp;
+  double best = 1e300;
+  int bestc = 1;
+  for (int c = 1; c < h->N; ++c) {
+    double a = 0, b = 0;
+    for (int m = 0; m < c; ++m) a += log((double)v.dim[m]);
+    for (int m = c; m < h->N; ++m) b += log((double)v.dim[m]);
+    const double cost = fabs(a - b);
+    if (cost < best - 1e-12) { best = cost; bestc = c; }
+  }
+  sp.c = bestc;
+  sp.P_in = 1;
+  sp.P_out = 1;
+  for (int m = 0; m < bestc; ++m) sp.P_in *= v.dim[m];
+  for (int m = bestc; m < h->N; ++m) sp.P_out *= v.dim[m];
+  sp.Kp = h->R[0] * h->R[bestc];
+  sp.rows = k < bestc;
+  sp.P_stat = sp.rows ? sp.P_in : sp.P_out;
+  sp.P_strm = sp.rows ? sp.P_out : sp.P_in;
+  return sp;
+}
+
+// Chain of cores m0..m1-1 over the view's digits; `subst` replaces core k by another array.
+Chain make_chain(const trd_handle* h, const View& v, int m0, int m1, int ksub = -1,
+                 const double* subst = nullptr, const double* const* cores = nullptr) {
+  Chain ch;
+  ch.n = m1 - m0;
+  ch.count = 1;
+  for (int j = 0; j < ch.n; ++j) {
+    const int m = m0 + j;
+    ch.core[j] = (m == ksub && subst) ? subst : (cores ? cores[m] : h->Z[m]);
+    ch.idx[j] = v.idx[m];
+    ch.dim[j] = v.dim[m];
+    ch.rows[j] = h->R[m];
+    ch.cols[j] = h->R[(m + 1) % h->N];
+    ch.count *= v.dim[m];
+  }
+  if (ch.n > 0) {
+    ch.out_rows = ch.rows[0];
+    ch.out_cols = ch.cols[ch.n - 1];
+  }
+  return ch;
+}
+
+View full_view(const trd_handle* h) {
+  View v;
+  v.X = h->X;
+  v.M = h->M;
+  v.N = h->N;
+  v.numel = 1;
+  for (int m = 0; m < h->N; ++m) {
+    v.dim[m] = h->I[m];
+    v.idx[m] = nullptr;
+    v.numel *= h->I[m];
+  }
+  return v;
+}
+
+trd_status check_handle(trd_handle* h) {
+  if (!h) return TRD_EINVAL;
+  return TRD_OK;
+}
+
+trd_status check_k(trd_handle* h, int k) {
+  if (k < 0 || k >= h->N) return set_err(h, TRD_EINVAL, "core index out of range");
+  return TRD_OK;
+}
+
+trd_status sync_and_status(trd_handle* h) {
+  CK(cudaStreamSynchronize(h->stream), "stream synchronize");
+  int st = 0;
+  CK(cudaMemcpy(&st, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+  if (st) {
+    CK(cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream), "status reset");
+    if (st & DEV_SINGULAR) return set_err(h, TRD_ESINGULAR, "G + lambda I is not positive definite");
+    if (st & DEV_NONFINITE) return set_err(h, TRD_ENONFINITE, "non-finite step size");
+    if (st & DEV_TIMEOUT) return set_err(h, TRD_ETIMEOUT, "a device wait gave up");
+    if (st & DEV_BOUNDS) return set_err(h, TRD_EINVAL, "a device index check failed");
+  }
+  return TRD_OK;
+}
+
+// ------------------------------------------------------------------ FGMC
+trd_status refresh_E(trd_handle* h, int k) {
+  CK(launch_fgmc_E(h->Z[k], nullptr, h->I[k], h->R[k], h->R[(k + 1) % h->N], h->E[k], h->stream),
+     "fgmc factor");
+  return TRD_OK;
+}
+
+// G^{!=k} = Phi(E_{k+1} ... E_{k-1}) into `G` from the factors `E` (Prop. 2, E-form).
+trd_status gram_chain(trd_handle* h, int k, double* const* E, double* G) {
+  const int N = h->N;
+  double* cur = nullptr;
+  int rows = 0, cols = 0;
+  double* bufs[2] = {(double*)h->T1.p, (double*)h->T2.p};
+  int which = 0;
+  for (int q = 0; q < N - 1; ++q) {
+    const int m = (k + 1 + q) % N;
+    const int rm = h->R[m], rm1 = h->R[(m + 1) % N];
+    if (q == 0) {
+      cur = E[m];
+      rows = rm * rm;
+      cols = rm1 * rm1;
+      continue;
+    }
+    double* out = bufs[which];
+    which ^= 1;
+    CK(launch_dgemm(cur, E[m], out, rows, rm1 * rm1, cols, false, h->stream), "fgmc chain");
+    cur = out;
+    cols = rm1 * rm1;
+  }
+  CK(launch_phi(cur, h->R[(k + 1) % N], h->R[k], G, h->stream), "fgmc realign");
+  return TRD_OK;
+}
+
+bool gram_valid(const trd_handle* h, int k) {
+  if (h->gram_k != k) return false;
+  for (int m = 0; m < h->N; ++m)
+    if (m != k && h->gram_ver[m] != h->ver[m]) return false;
+  return true;
+}
+
+trd_status ensure_gram(trd_handle* h, int k) {
+  if (gram_valid(h, k)) return TRD_OK;
+  double* E[kMaxN];
+  for (int m = 0; m < h->N; ++m) E[m] = h->E[m];
+  TRY(gram_chain(h, k, E, (double*)h->G.p));
+  h->gram_k = k;
+  for (int m = 0; m < h->N; ++m) h->gram_ver[m] = h->ver[m];
+  return TRD_OK;
+}
+
+// Local Gram of the sampled cores (ablation 'local scaled term'): FGMC on sampled factors.
+trd_status local_gram(trd_handle* h, int k) {
+  Extra* x = X_(h);
+  double* E[kMaxN];
+  for (int m = 0; m < h->N; ++m) {
+    if (m == k) { E[m] = h->E[m]; continue; }
+    const int rm = h->R[m], rm1 = h->R[(m + 1) % h->N];
+    TRY(ensure(h, x->Eloc[m], sizeof(double) * rm * rm * rm1 * rm1));
+    const bool sampled = h->view.idx[m] != nullptr;
+    CK(launch_fgmc_E(h->Z[m], h->view.idx[m], sampled ? h->view.dim[m] : h->I[m], rm, rm1,
+                     (double*)x->Eloc[m].p, h->stream), "local fgmc factor");
+    E[m] = (double*)x->Eloc[m].p;
+  }
+  const int K = h->K[k];
+  TRY(ensure(h, x->Gloc, sizeof(double) * K * K));
+  return gram_chain(h, k, E, (double*)x->Gloc.p);
+}
+
+trd_status compute_D(trd_handle* h, double* D) {
+  const int n = h->N - 1;
+  TRY(ensure_gram(h, n));
+  const int I = (int)h->I[n], K = h->K[n];
+  CK(launch_dgemm(h->Z[n], (const double*)h->G.p, (double*)h->h.p, I, K, K, false, h->stream), "D step 1");
+  CK(launch_dgemm((const double*)h->h.p, h->Z[n], D, I, I, K, true, h->stream), "D step 2");
+  return TRD_OK;
+}
+
+trd_status reset_D0(trd_handle* h) {
+  TRY(compute_D(h, (double*)h->Dprev.p));
+  h->have_D0 = true;
+  return TRD_OK;
+}
+
+// ------------------------------------------------------------------ data passes
+trd_status build_merged(trd_handle* h, int k, bool with_h) {
+  const View& v = h->view;
+  const Split& sp = h->split;
+  const int c = sp.c, Kp = sp.Kp;
+  const bool dbl = is_fp64(h);
+  const size_t e = elt(h);
+  TRY(ensure(h, h->Sst, e * sp.P_stat * Kp));
+  TRY(ensure(h, h->Sstr, e * sp.P_strm * Kp));
+  const Chain inner = make_chain(h, v, 0, c, with_h ? k : -1, with_h ? (const double*)h->h.p : nullptr);
+  const Chain outer = make_chain(h, v, c, h->N, with_h ? k : -1, with_h ? (const double*)h->h.p : nullptr);
+  if (with_h) {
+    TRY(ensure(h, h->Sh, e * sp.P_stat * Kp));
+    if (sp.rows) CK(launch_chain(inner, h->Sh.p, dbl, false, Kp, h->stream), "merge A_h");
+    else CK(launch_chain(outer, h->Sh.p, dbl, true, Kp, h->stream), "merge C_h");
+    return TRD_OK;
+  }
+  void* A = sp.rows ? h->Sst.p : h->Sstr.p;
+  void* C = sp.rows ? h->Sstr.p : h->Sst.p;
+  CK(launch_chain(inner, A, dbl, false, Kp, h->stream), "merge inner block");
+  CK(launch_chain(outer, C, dbl, true, Kp, h->stream), "merge outer block");
+  return TRD_OK;
+}
+
+int choose_splits(const trd_handle* h, const Split& sp) {
+  const int64_t gx = (sp.P_stat + 63) / 64;
+  const int64_t tiles = (sp.P_strm + 63) / 64;
+  int64_t s = (2 * (int64_t)h->num_sms + gx - 1) / gx;
+  s = imax(1, imin(s, tiles));
+  return (int)s;
+}
+
+PassArgs pass_args(trd_handle* h) {
+  PassArgs a{};
+  const Split& sp = h->split;
+  a.X = h->view.X;
+  a.M = h->view.M;
+  a.P_in = sp.P_in;
+  a.P_stat = sp.P_stat;
+  a.P_strm = sp.P_strm;
+  a.Kp = sp.Kp;
+  a.ld = sp.Kp;
+  a.Sst = h->Sst.p;
+  a.Sh = h->Sh.p;
+  a.Sstr = h->Sstr.p;
+  a.sigma = h->scal + S_SIGMA;
+  a.Tpart = h->Tpart.p;
+  a.stat_part = (double*)h->stat_part.p;
+  return a;
+}
+
+trd_status run_pass1(trd_handle* h, int k) {
+  if (h->prec == TRD_BF16) return set_err(h, TRD_ENOTIMPL, "BF16 tensor-core path not built");
+  h->split = choose_split(h, h->view, k);
+  const Split& sp = h->split;
+  if (sp.Kp > 112 && is_fp64(h)) return set_err(h, TRD_ENOTIMPL, "FP64 path supports r_1 r_c <= 112");
+  if (sp.Kp > 256) return set_err(h, TRD_ENOTIMPL, "data passes support r_1 r_c <= 256");
+  TRY(build_merged(h, k, false));
+  int splits = choose_splits(h, sp);
+  const int64_t gx = (sp.P_stat + 63) / 64;
+  TRY(ensure(h, h->Tpart, elt(h) * (size_t)splits * sp.P_stat * sp.Kp));
+  TRY(ensure(h, h->stat_part, sizeof(double) * 8 * (size_t)(gx * splits)));
+  TRY(ensure(h, h->Tsum, sizeof(double) * (size_t)sp.P_stat * sp.Kp));
+  int ctas = 0, used = 0;
+  PassArgs a = pass_args(h);
+  CK(launch_pass_simt(a, is_fp64(h), sp.rows, false, splits, &ctas, &used, h->stream), "data pass 1");
+  h->splits = used;
+  h->ctas = ctas;
+  CK(launch_reduce_T(h->Tpart.p, is_fp64(h), used, sp.P_stat * (int64_t)sp.Kp, (double*)h->Tsum.p,
+                     h->stream), "reduce contraction");
+  CK(launch_reduce_stats((const double*)h->stat_part.p, ctas, (double*)h->stat_sum.p, h->dstatus,
+                         h->stream), "reduce statistics");
+  h->pass1_k = k;
+  h->grad_k = -1;
+  h->slots_last = h->view.numel;
+  return TRD_OK;
+}
+
+trd_status run_gradient(trd_handle* h, int k) {
+  if (h->pass1_k != k) return set_err(h, TRD_EINVAL, "trd_residual_weights must run for this core first");
+  const View& v = h->view;
+  const Split& sp = h->split;
+  const int N = h->N, c = sp.c;
+  const int rk = h->R[k], rk1 = h->R[(k + 1) % N];
+  int pre0, pre1, post0, post1, mr, mc;
+  if (sp.rows) {
+    pre0 = 0; pre1 = k; post0 = k + 1; post1 = c;
+    mr = h->R[c]; mc = h->R[0];
+  } else {
+    pre0 = c; pre1 = k; post0 = k + 1; post1 = N;
+    mr = h->R[0]; mc = h->R[c];
+  }
+  const Chain pre = make_chain(h, v, pre0, pre1);
+  const Chain post = make_chain(h, v, post0, post1);
+  const int64_t n_pre = pre.n > 0 ? pre.count : 1;
+  const int64_t n_post = post.n > 0 ? post.count : 1;
+  if (pre.n > 0) {
+    TRY(ensure(h, h->pre, sizeof(double) * n_pre * mc * rk));
+    CK(launch_chain(pre, h->pre.p, true, false, mc * rk, h->stream), "merge prefix");
+  }
+  if (post.n > 0) {
+    TRY(ensure(h, h->post, sizeof(double) * n_post * rk1 * mr));
+    CK(launch_chain(post, h->post.p, true, false, rk1 * mr, h->stream), "merge suffix");
+  }
+  const int64_t npairs = n_pre * n_post;
+  int64_t nsplit = (2 * (int64_t)h->num_sms + h->I[k] - 1) / h->I[k];
+  nsplit = imax(1, imin(nsplit, imin(npairs, 256)));
+  const int K = h->K[k];
+  TRY(ensure(h, h->d, sizeof(double) * h->I[k] * K));
+  if (nsplit > 1) TRY(ensure(h, h->dpart, sizeof(double) * nsplit * h->I[k] * K));
+  CK(launch_backcontract(h->Tsum.p, sp.Kp, sp.rows, mr, mc, pre.n > 0 ? (const double*)h->pre.p : nullptr,
+                         n_pre, post.n > 0 ? (const double*)h->post.p : nullptr, n_post, h->I[k], rk,
+                         rk1, (double*)h->dpart.p, (int)nsplit, (double*)h->d.p, h->stream),
+     "back-contraction");
+  h->grad_k = k;
+  return TRD_OK;
+}
+
+trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int gram,
+                      double* eta_slot) {
+  if (h->grad_k != k) return set_err(h, TRD_EINVAL, "trd_core_gradient must run for this core first");
+  const int K = h->K[k];
+  const int64_t n = h->I[k] * (int64_t)K;
+  double* d = (double*)h->d.p;
+  double* hh = (double*)h->h.p;
+  if (gram == TRD_GRAM_NONE) {
+    CK(cudaMemcpyAsync(hh, d, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream), "copy d");
+  } else {
+    const double* G;
+    if (gram == TRD_GRAM_LOCAL) {
+      TRY(local_gram(h, k));
+      G = (const double*)X_(h)->Gloc.p;
+    } else {
+      TRY(ensure_gram(h, k));
+      G = (const double*)h->G.p;
+    }
+    CK(launch_cholesky(G, K, lambda, (double*)h->L.p, h->scal, h->dstatus, h->stream), "cholesky");
+    CK(launch_solve_rows((const double*)h->L.p, d, hh, K, h->I[k], h->stream), "triangular solves");
+  }
+  CK(launch_dot(d, hh, n, h->scal + S_NUM, h->stream), "<d,h>");
+  double* den = h->scal + S_DEN;
+  if (eta_fixed <= 0) {
+    TRY(build_merged(h, k, true));
+    int ctas = 0, used = 0;
+    PassArgs a = pass_args(h);
+    CK(launch_pass_simt(a, is_fp64(h), h->split.rows, true, h->splits, &ctas, &used, h->stream),
+       "data pass 2");
+    double* s2 = (double*)X_(h)->stat_sum2.p;
+    CK(launch_reduce_stats((const double*)h->stat_part.p, ctas, s2, h->dstatus, h->stream), "reduce den");
+    den = s2 + 6;
+  }
+  CK(launch_eta(h->scal + S_NUM, den, eta_fixed, h->dstatus, h->scal + S_ETA, eta_slot, h->stream),
+     "step size");
+  CK(launch_axpy_core(h->Z[k], hh, n, h->scal + S_ETA, h->stream), "core update");
+  h->ver[k]++;
+  TRY(refresh_E(h, k));
+  h->grad_k = -1;
+  h->pass1_k = -1;
+  return TRD_OK;
+}
+
+trd_status set_sigma(trd_handle* h, double sigma) {
+  if (sigma > 0) {
+    CK(launch_set_scalar(h->scal + S_SIGMA, sigma, h->stream), "set sigma");
+    h->sigma_set = true;
+    return TRD_OK;
+  }
+  if (!h->sigma_set) return set_err(h, TRD_EINVAL, "adaptive width requested before trd_adaptive_sigma");
+  return TRD_OK;
+}
+
+trd_status run_adaptive(trd_handle* h, double sigma_prev, const double* sigma_prev_dev = nullptr) {
+  if (!h->X) return set_err(h, TRD_EINVAL, "no data attached");
+  Extra* x = X_(h);
+  const int64_t n = h->numel <= kProbeMax ? h->numel : kProbeMax;
+  TRY(ensure(h, h->probe_vals, sizeof(double) * n));
+  TRY(ensure(h, h->probe_keys, sizeof(uint64_t) * n));
+  TRY(ensure(h, x->probe_xsq, sizeof(double) * n));
+  TRY(ensure(h, h->probe_work, sizeof(double) * sigma_work_doubles()));
+  const char* meta = (const char*)x->meta.p;
+  CK(launch_probe_sigma((const double* const*)meta, h->N, (const int64_t*)(meta + 8 * kMaxN),
+                        (const int*)(meta + 16 * kMaxN), h->X, h->M, h->numel, is_fp64(h), sigma_prev,
+                        sigma_prev_dev,
+                        (double*)h->probe_vals.p, (uint64_t*)h->probe_keys.p, (double*)x->probe_xsq.p,
+                        (double*)h->probe_work.p, h->scal + S_SIGMA, h->stream),
+     "adaptive width");
+  h->sigma_set = true;
+  return TRD_OK;
+}
+
+trd_status use_full_view(trd_handle* h) {
+  h->view = full_view(h);
+  h->view_k = -1;
+  h->sketched = false;
+  return TRD_OK;
+}
+
+trd_status sample(trd_handle* h, int k, const int32_t* const* idx, const int32_t* s) {
+  if (!h->X) return set_err(h, TRD_EINVAL, "no data attached");
+  if (!idx) return use_full_view(h);
+  const int N = h->N;
+  View v = full_view(h);
+  size_t off = 0;
+  const size_t need = [&] { size_t t = 0; for (int m = 0; m < N; ++m) t += (size_t)h->I[m]; return t; }();
+  if (h->idx_pinned_cap < need) {
+    if (h->idx_pinned) cudaFreeHost(h->idx_pinned);
+    h->idx_pinned = nullptr;
+    h->idx_pinned_cap = 0;
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    if (cudaMallocHost(&h->idx_pinned, need * sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(h, TRD_ENOMEM, "pinned allocation failed");
+    }
+    h->idx_pinned_cap = need;
+  }
+  // the pinned staging area is reused: wait for any earlier upload from it
+  CK(cudaStreamSynchronize(h->stream), "sync before index upload");
+  bool any = false;
+  for (int m = 0; m < N; ++m) {
+    if (m == k || !idx[m]) continue;
+    const int32_t sm = s[m];
+    if (sm < 1 || sm > h->I[m]) return set_err(h, TRD_EINVAL, "sketch size out of range");
+    for (int q = 0; q < sm; ++q) {
+      const int32_t i = idx[m][q];
+      if (i < 0 || i >= h->I[m] || (q > 0 && i <= idx[m][q - 1]))
+        return set_err(h, TRD_EINVAL, "sketch indices must be strictly increasing and in range");
+    }
+    if (sm == h->I[m]) continue;   // whole mode: identity map
+    if (h->idx_cap[m] < (size_t)h->I[m]) {
+      if (h->idx_dev[m]) cudaFree(h->idx_dev[m]);
+      h->idx_dev[m] = nullptr;
+      if (cudaMalloc(&h->idx_dev[m], sizeof(int32_t) * h->I[m]) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(h, TRD_ENOMEM, "index allocation failed");
+      }
+      h->idx_cap[m] = (size_t)h->I[m];
+    }
+    memcpy(h->idx_pinned + off, idx[m], sizeof(int32_t) * sm);
+    CK(cudaMemcpyAsync(h->idx_dev[m], h->idx_pinned + off, sizeof(int32_t) * sm, cudaMemcpyHostToDevice,
+                       h->stream), "index upload");
+    off += sm;
+    v.dim[m] = sm;
+    v.idx[m] = h->idx_dev[m];
+    any = true;
+  }
+  if (!any) return use_full_view(h);
+  v.numel = 1;
+  for (int m = 0; m < N; ++m) v.numel *= v.dim[m];
+  const int64_t words = ((v.numel + 31) / 32 + 3) / 4 * 4;
+  TRY(ensure(h, h->XI, sizeof(float) * (size_t)v.numel));
+  TRY(ensure(h, h->PI, sizeof(uint32_t) * (size_t)words));
+  CK(launch_gather(h->X, h->M, N, h->I, v, (float*)h->XI.p, (uint32_t*)h->PI.p, h->stream), "RStS gather");
+  v.X = (const float*)h->XI.p;
+  v.M = (const uint32_t*)h->PI.p;
+  h->view = v;
+  h->view_k = k;
+  h->sketched = true;
+  h->pass1_k = -1;
+  h->grad_k = -1;
+  return TRD_OK;
+}
+
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+void draw(uint64_t seed, int32_t t, int k, int j, int N, int64_t I, int32_t s, int32_t* out) {
+  if (s >= I) {
+    for (int64_t i = 0; i < I; ++i) out[i] = (int32_t)i;
+    return;
+  }
+  const uint64_t key = mix64(seed + ((uint64_t)(((int64_t)t * N + k) * N + j) + 1) * kGamma);
+  std::vector<int32_t> perm((size_t)I);
+  for (int64_t i = 0; i < I; ++i) perm[(size_t)i] = (int32_t)i;
+  for (int32_t m = 0; m < s; ++m) {
+    const uint64_t z = mix64(key + (uint64_t)(m + 1) * kGamma);
+    const int64_t pick = m + (int64_t)(z % (uint64_t)(I - m));
+    std::swap(perm[(size_t)m], perm[(size_t)pick]);
+  }
+  std::sort(perm.begin(), perm.begin() + s);
+  for (int32_t m = 0; m < s; ++m) out[m] = perm[(size_t)m];
+}
+
+trd_status alloc_state(trd_handle* h) {
+  const int N = h->N;
+  int maxK = 1;
+  int64_t maxIK = 1;
+  for (int k = 0; k < N; ++k) {
+    const int rk = h->R[k], rk1 = h->R[(k + 1) % N];
+    h->K[k] = rk * rk1;
+    maxK = std::max(maxK, h->K[k]);
+    maxIK = std::max(maxIK, h->I[k] * (int64_t)h->K[k]);
+    if (cudaMalloc(&h->Z[k], sizeof(double) * h->I[k] * h->K[k]) != cudaSuccess ||
+        cudaMalloc(&h->E[k], sizeof(double) * (size_t)rk * rk * rk1 * rk1) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(h, TRD_ENOMEM, "core allocation failed");
+    }
+    cudaMemsetAsync(h->Z[k], 0, sizeof(double) * h->I[k] * h->K[k], h->stream);
+  }
+  // chain buffers hold p^2 x q^2 intermediates: bound by maxR^4
+  size_t chain = 1;
+  for (int k = 0; k < N; ++k)
+    for (int m = 0; m < N; ++m)
+      chain = std::max(chain, (size_t)h->R[k] * h->R[k] * h->R[m] * h->R[m]);
+  const int64_t IN = h->I[N - 1];
+  TRY(ensure(h, h->G, sizeof(double) * maxK * maxK));
+  TRY(ensure(h, h->L, sizeof(double) * maxK * maxK));
+  TRY(ensure(h, h->T1, sizeof(double) * chain));
+  TRY(ensure(h, h->T2, sizeof(double) * chain));
+  TRY(ensure(h, h->d, sizeof(double) * maxIK));
+  TRY(ensure(h, h->h, sizeof(double) * std::max<int64_t>(maxIK, IN * h->K[N - 1])));
+  TRY(ensure(h, h->D, sizeof(double) * IN * IN));
+  TRY(ensure(h, h->Dprev, sizeof(double) * IN * IN));
+  TRY(ensure(h, h->stat_sum, sizeof(double) * 8));
+  TRY(ensure(h, X_(h)->stat_sum2, sizeof(double) * 8));
+  if (cudaMalloc(&h->scal, sizeof(double) * 64) != cudaSuccess ||
+      cudaMalloc(&h->dstatus, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->report_dev, sizeof(double) * 64) != cudaSuccess ||
+      cudaMallocHost(&h->host_pinned, sizeof(double) * 256) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(h, TRD_ENOMEM, "state allocation failed");
+  }
+  cudaMemsetAsync(h->scal, 0, sizeof(double) * 64, h->stream);
+  cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->stream);
+  cudaMemsetAsync(h->report_dev, 0, sizeof(double) * 64, h->stream);
+  // meta: core pointers, dims, ranks for kernels that walk all cores
+  Extra* x = X_(h);
+  TRY(ensure(h, x->meta, 32 * kMaxN));
+  char hostmeta[32 * kMaxN];
+  memset(hostmeta, 0, sizeof(hostmeta));
+  for (int m = 0; m < N; ++m) {
+    memcpy(hostmeta + 8 * m, &h->Z[m], 8);
+    memcpy(hostmeta + 8 * kMaxN + 8 * m, &h->I[m], 8);
+    memcpy(hostmeta + 16 * kMaxN + 4 * m, &h->R[m], 4);
+  }
+  CK(cudaMemcpy(x->meta.p, hostmeta, sizeof(hostmeta), cudaMemcpyHostToDevice), "meta upload");
+  return TRD_OK;
+}
+
+void free_buf(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+}  // namespace
+
+// Extra state lives right after the handle in one host allocation.
+struct trd_handle_full {
+  trd_handle h;
+  Extra x;
+};
+namespace {
+Extra* X_(trd_handle* h) { return &reinterpret_cast<trd_handle_full*>(h)->x; }
+}  // namespace
+
+// =================================================================== ABI
+
+extern "C" {
+
+const char* trd_status_string(trd_status s) {
+  switch (s) {
+    case TRD_OK: return "TRD_OK";
+    case TRD_EINVAL: return "TRD_EINVAL";
+    case TRD_ENOMEM: return "TRD_ENOMEM";
+    case TRD_ECUDA: return "TRD_ECUDA";
+    case TRD_ESINGULAR: return "TRD_ESINGULAR";
+    case TRD_ENONFINITE: return "TRD_ENONFINITE";
+    case TRD_ETIMEOUT: return "TRD_ETIMEOUT";
+    case TRD_ENOTIMPL: return "TRD_ENOTIMPL";
+  }
+  return "TRD_UNKNOWN";
+}
+
+const char* trd_last_error(const trd_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+trd_status trd_create(trd_t** out, int N, const int64_t* I, const int32_t* R, int precision,
+                      void* cuda_stream) {
+  if (!out) return TRD_EINVAL;
+  *out = nullptr;
+  if (N < 3 || N > kMaxN || !I || !R) return TRD_EINVAL;
+  if (precision != TRD_FP64 && precision != TRD_FP32 && precision != TRD_BF16) return TRD_EINVAL;
+  double logtot = 0;
+  for (int m = 0; m < N; ++m) {
+    if (I[m] < 1 || I[m] > (int64_t(1) << 31) - 1) return TRD_EINVAL;
+    if (R[m] < 1 || R[m] > kMaxR) return TRD_EINVAL;
+    logtot += log2((double)I[m]);
+  }
+  if (logtot >= 40.0) return TRD_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return TRD_ECUDA;
+  }
+  trd_handle_full* hf = new (std::nothrow) trd_handle_full();
+  if (!hf) return TRD_ENOMEM;
+  trd_handle* h = &hf->h;
+  h->N = N;
+  for (int m = 0; m < N; ++m) { h->I[m] = I[m]; h->R[m] = R[m]; }
+  h->prec = precision;
+  h->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&h->device);
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (h->num_sms < 1) h->num_sms = 1;
+  trd_status s = alloc_state(h);
+  if (s != TRD_OK) {
+    trd_destroy(h);
+    return s;
+  }
+  *out = h;
+  return TRD_OK;
+}
+
+void trd_destroy(trd_t* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (int k = 0; k < kMaxN; ++k) {
+    if (h->Z[k]) cudaFree(h->Z[k]);
+    if (h->E[k]) cudaFree(h->E[k]);
+    if (h->idx_dev[k]) cudaFree(h->idx_dev[k]);
+  }
+  DevBuf* bufs[] = {&h->XI, &h->PI, &h->Sst, &h->Sstr, &h->Sh, &h->Sst_bf, &h->Sstr_bf, &h->Sh_bf,
+                    &h->SstrT_bf, &h->SstT_bf, &h->Tpart, &h->Tsum, &h->stat_part, &h->stat_sum,
+                    &h->pre, &h->post, &h->dpart, &h->d, &h->h, &h->G, &h->L, &h->T1, &h->T2,
+                    &h->D, &h->Dprev, &h->probe_keys, &h->probe_vals, &h->probe_work};
+  for (DevBuf* b : bufs) free_buf(*b);
+  Extra* x = X_(h);
+  DevBuf* xb[] = {&x->meta, &x->stat_sum2, &x->Gloc, &x->recA, &x->recC, &x->errp, &x->probe_xsq};
+  for (DevBuf* b : xb) free_buf(*b);
+  for (int k = 0; k < kMaxN; ++k) { free_buf(x->Eloc[k]); free_buf(x->tmpZ[k]); }
+  if (h->scal) cudaFree(h->scal);
+  if (h->dstatus) cudaFree(h->dstatus);
+  if (h->report_dev) cudaFree(h->report_dev);
+  if (h->host_pinned) cudaFreeHost(h->host_pinned);
+  if (h->idx_pinned) cudaFreeHost(h->idx_pinned);
+  cudaGetLastError();
+  delete reinterpret_cast<trd_handle_full*>(h);
+}
+
+trd_status trd_set_data(trd_t* h, const float* X, const uint32_t* mask) {
+  TRY(check_handle(h));
+  if (!X) return set_err(h, TRD_EINVAL, "X must not be NULL");
+  if (((uintptr_t)X & 15) || ((uintptr_t)mask & 15))
+    return set_err(h, TRD_EINVAL, "X and mask must be 16-byte aligned");
+  h->X = X;
+  h->M = mask;
+  h->numel = 1;
+  for (int m = 0; m < h->N; ++m) h->numel *= h->I[m];
+  use_full_view(h);
+  h->pass1_k = h->grad_k = -1;
+  return TRD_OK;
+}
+
+trd_status trd_init_cores(trd_t* h, uint64_t seed, double stddev) {
+  TRY(check_handle(h));
+  const int N = h->N;
+  uint64_t base = 0;
+  for (int k = 0; k < N; ++k) {
+    const int rk = h->R[k], rk1 = h->R[(k + 1) % N];
+    const double sd = stddev > 0 ? stddev : pow((double)rk * rk1, -0.25);
+    const int64_t n = h->I[k] * (int64_t)rk * rk1;
+    std::vector<double> v((size_t)n);
+    for (int64_t f = 0; f < n; ++f) {
+      const uint64_t g = base + (uint64_t)f;
+      const uint64_t z1 = mix64(seed + (2 * g + 1) * kGamma);
+      const uint64_t z2 = mix64(seed + (2 * g + 2) * kGamma);
+      const double u1 = ((double)(z1 >> 11) + 1.0) * 0x1.0p-53;
+      const double u2 = (double)(z2 >> 11) * 0x1.0p-53;
+      v[(size_t)f] = sd * (sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2));
+    }
+    CK(cudaMemcpyAsync(h->Z[k], v.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream), "core upload");
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    h->ver[k]++;
+    TRY(refresh_E(h, k));
+    base += (uint64_t)n;
+  }
+  h->t = 0;
+  h->pass1_k = h->grad_k = -1;
+  TRY(reset_D0(h));
+  return sync_and_status(h);
+}
+
+trd_status trd_set_core(trd_t* h, int k, const double* core) {
+  TRY(check_handle(h));
+  TRY(check_k(h, k));
+  if (!core) return set_err(h, TRD_EINVAL, "NULL core");
+  CK(cudaMemcpyAsync(h->Z[k], core, sizeof(double) * h->I[k] * h->K[k], cudaMemcpyHostToDevice, h->stream),
+     "core upload");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  h->ver[k]++;
+  h->pass1_k = h->grad_k = -1;
+  TRY(refresh_E(h, k));
+  return sync_and_status(h);
+}
+
+trd_status trd_get_core(trd_t* h, int k, double* core) {
+  TRY(check_handle(h));
+  TRY(check_k(h, k));
+  if (!core) return set_err(h, TRD_EINVAL, "NULL core");
+  CK(cudaMemcpyAsync(core, h->Z[k], sizeof(double) * h->I[k] * h->K[k], cudaMemcpyDeviceToHost, h->stream),
+     "core download");
+  return sync_and_status(h);
+}
+
+trd_status trd_reset_iteration(trd_t* h, int32_t t) {
+  TRY(check_handle(h));
+  h->t = t;
+  TRY(reset_D0(h));
+  return sync_and_status(h);
+}
+
+trd_status trd_draw_indices(uint64_t seed, int32_t t, int k, int j, int N, int64_t I, int32_t s,
+                            int32_t* out) {
+  if (!out || N < 1 || I < 1 || s < 1 || s > I || k < 0 || j < 0) return TRD_EINVAL;
+  draw(seed, t, k, j, N, I, s, out);
+  return TRD_OK;
+}
+
+trd_status trd_sample_subtensor(trd_t* h, int k, const int32_t* const* idx, const int32_t* s) {
+  TRY(check_handle(h));
+  TRY(check_k(h, k));
+  if (idx && !s) return set_err(h, TRD_EINVAL, "sizes missing");
+  return sample(h, k, idx, s);
+}
+
+trd_status trd_residual_weights(trd_t* h, int k, double sigma, trd_resid_stats* out) {
+  TRY(check_handle(h));
+  TRY(check_k(h, k));
+  if (!h->X) return set_err(h, TRD_EINVAL, "no data attached");
+  if (h->sketched && h->view_k != k) return set_err(h, TRD_EINVAL, "the current sketch was drawn for another core");
+  TRY(set_sigma(h, sigma));
+  TRY(run_pass1(h, k));
+  if (!out) return TRD_OK;
+  double* hp = h->host_pinned;
+  CK(cudaMemcpyAsync(hp, h->stat_sum.p, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream), "stats");
+  CK(cudaMemcpyAsync(hp + 8, h->scal + S_SIGMA, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "sigma");
+  TRY(sync_and_status(h));
+  out->sum_w = hp[0];
+  out->sum_e2 = hp[1];
+  out->sum_we2 = hp[2];
+  out->n_obs = (int64_t)hp[3];
+  out->n_nonfinite = (int64_t)hp[4];
+  out->n_slots = (int64_t)hp[5];
+  out->sigma = hp[8];
+  if (out->n_nonfinite > 0) return set_err(h, TRD_ENONFINITE, "non-finite residuals");
+  return TRD_OK;
+}
+
+trd_status trd_core_gradient(trd_t* h, int k, double* d_host) {
+  TRY(check_handle(h));
+  TRY(check_k(h, k));
+  TRY(run_gradient(h, k));
+  if (!d_host) return TRD_OK;
+  CK(cudaMemcpyAsync(d_host, h->d.p, sizeof(double) * h->I[k] * h->K[k], cudaMemcpyDeviceToHost, h->stream),
+     "gradient download");
+  return sync_and_status(h);
+}
+
+trd_status trd_fgmc_gram(trd_t* h, int k, double* G_host) {
+  TRY(check_handle(h));
+  TRY(check_k(h, k));
+  TRY(ensure_gram(h, k));
+  if (!G_host) return TRD_OK;
+  CK(cudaMemcpyAsync(G_host, h->G.p, sizeof(double) * h->K[k] * h->K[k], cudaMemcpyDeviceToHost, h->stream),
+     "gram download");
+  return sync_and_status(h);
+}
+
+trd_status trd_core_update(trd_t* h, int k, double lambda, double eta, int gram, double* eta_out) {
+  TRY(check_handle(h));
+  TRY(check_k(h, k));
+  if (gram < TRD_GRAM_GLOBAL || gram > TRD_GRAM_NONE) return set_err(h, TRD_EINVAL, "bad gram kind");
+  TRY(run_update(h, k, lambda, eta, gram, nullptr));
+  if (!eta_out) return TRD_OK;
+  CK(cudaMemcpyAsync(h->host_pinned, h->scal + S_ETA, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+     "eta");
+  TRY(sync_and_status(h));
+  *eta_out = h->host_pinned[0];
+  return TRD_OK;
+}
+
+trd_status trd_adaptive_sigma(trd_t* h, double sigma_prev, double* sigma_out) {
+  TRY(check_handle(h));
+  TRY(run_adaptive(h, sigma_prev));
+  if (!sigma_out) return TRD_OK;
+  CK(cudaMemcpyAsync(h->host_pinned, h->scal + S_SIGMA, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+     "sigma");
+  TRY(sync_and_status(h));
+  *sigma_out = h->host_pinned[0];
+  return TRD_OK;
+}
+
+trd_status trd_sigma_from_residuals(trd_t* h, const float* r, int64_t n, double rms, double sigma_prev,
+                                    double* sigma_out) {
+  TRY(check_handle(h));
+  if (!r || n < 1 || rms < 0 || !sigma_out) return set_err(h, TRD_EINVAL, "bad arguments");
+  Extra* x = X_(h);
+  TRY(ensure(h, h->probe_vals, sizeof(double) * n));
+  TRY(ensure(h, h->probe_keys, sizeof(uint64_t) * n));
+  TRY(ensure(h, x->probe_xsq, sizeof(double) * n));
+  TRY(ensure(h, h->probe_work, sizeof(double) * sigma_work_doubles()));
+  CK(launch_sigma_from_floats(r, n, rms, sigma_prev, (double*)h->probe_vals.p, (uint64_t*)h->probe_keys.p,
+                              (double*)x->probe_xsq.p, (double*)h->probe_work.p, h->scal + S_SIGMA + 8,
+                              h->stream), "sigma from residuals");
+  CK(cudaMemcpyAsync(h->host_pinned, h->scal + S_SIGMA + 8, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+     "sigma");
+  TRY(sync_and_status(h));
+  *sigma_out = h->host_pinned[0];
+  return TRD_OK;
+}
+
+trd_status trd_step(trd_t* h, const trd_params* p, trd_report* rep) {
+  TRY(check_handle(h));
+  if (!p) return set_err(h, TRD_EINVAL, "NULL params");
+  if (!h->X) return set_err(h, TRD_EINVAL, "no data attached");
+  if (p->gram < TRD_GRAM_GLOBAL || p->gram > TRD_GRAM_NONE) return set_err(h, TRD_EINVAL, "bad gram kind");
+  const int N = h->N;
+  if (!h->have_D0) TRY(reset_D0(h));
+  if (p->sigma > 0) {
+    TRY(set_sigma(h, p->sigma));
+  } else {
+    // width of this iteration from the residuals of the current cores, limited by the
+    // width of the previous iteration (kept on the device, no host round trip)
+    if (h->sigma_set && h->t > 0) {
+      CK(cudaMemcpyAsync(h->scal + S_SIGMA_PREV, h->scal + S_SIGMA, sizeof(double),
+                         cudaMemcpyDeviceToDevice, h->stream), "sigma prev");
+      TRY(run_adaptive(h, -1.0, h->scal + S_SIGMA_PREV));
+    } else {
+      TRY(run_adaptive(h, -1.0));
+    }
+  }
+  int64_t slots = 0;
+  std::vector<int32_t> idxbuf;
+  for (int k = 0; k < N; ++k) {
+    bool sketch = false;
+    for (int m = 0; m < N; ++m)
+      if (m != k && p->sketch[m] > 0 && p->sketch[m] < h->I[m]) sketch = true;
+    if (sketch) {
+      std::vector<std::vector<int32_t>> sets(N);
+      const int32_t* ptrs[kMaxN] = {};
+      int32_t sizes[kMaxN] = {};
+      for (int m = 0; m < N; ++m) {
+        if (m == k) continue;
+        const int32_t s = (p->sketch[m] > 0 && p->sketch[m] < h->I[m]) ? p->sketch[m] : (int32_t)h->I[m];
+        sets[m].resize((size_t)s);
+        draw(p->seed, h->t, k, m, N, h->I[m], s, sets[m].data());
+        ptrs[m] = sets[m].data();
+        sizes[m] = s;
+      }
+      TRY(sample(h, k, ptrs, sizes));
+    } else if (h->sketched) {
+      use_full_view(h);
+    }
+    TRY(run_pass1(h, k));
+    CK(cudaMemcpyAsync(h->report_dev + R_OBJ + k, (double*)h->stat_sum.p + 2, sizeof(double),
+                       cudaMemcpyDeviceToDevice, h->stream), "objective");
+    TRY(run_gradient(h, k));
+    TRY(run_update(h, k, p->lambda, -1.0, p->gram, h->report_dev + R_ETA + k));
+    slots += h->slots_last;
+  }
+  TRY(compute_D(h, (double*)h->D.p));
+  CK(launch_stop_error((const double*)h->D.p, (double*)h->Dprev.p, h->I[N - 1] * h->I[N - 1],
+                       h->report_dev + R_E, h->stream), "stopping quantity");
+  CK(cudaMemcpyAsync(h->report_dev + R_SIGMA, h->scal + S_SIGMA, sizeof(double), cudaMemcpyDeviceToDevice,
+                     h->stream), "sigma");
+  CK(cudaMemcpyAsync(h->host_pinned, h->report_dev, sizeof(double) * 32, cudaMemcpyDeviceToHost, h->stream),
+     "report");
+  trd_status st = sync_and_status(h);
+  h->t += 1;
+  if (rep) {
+    memset(rep, 0, sizeof(*rep));
+    for (int k = 0; k < N; ++k) {
+      rep->eta[k] = h->host_pinned[R_ETA + k];
+      rep->objective[k] = 0.5 * h->host_pinned[R_OBJ + k];
+    }
+    rep->e = h->host_pinned[R_E];
+    rep->sigma = h->host_pinned[R_SIGMA];
+    rep->slots = slots;
+    rep->t = h->t;
+  }
+  return st;
+}
+
+// ------------------------------------------------------------------ reconstruction helpers
+static trd_status reconstruct_impl(trd_t* h, const double* const* cores, float* out, const float* ref,
+                                   double* err_out) {
+  const View v = full_view(h);
+  const Split sp = choose_split(h, v, 0);
+  Extra* x = X_(h);
+  TRY(ensure(h, x->recA, sizeof(double) * sp.P_in * sp.Kp));
+  TRY(ensure(h, x->recC, sizeof(double) * sp.P_out * sp.Kp));
+  const Chain inner = make_chain(h, v, 0, sp.c, -1, nullptr, cores);
+  const Chain outer = make_chain(h, v, sp.c, h->N, -1, nullptr, cores);
+  CK(launch_chain(inner, x->recA.p, true, false, sp.Kp, h->stream), "merge inner");
+  CK(launch_chain(outer, x->recC.p, true, true, sp.Kp, h->stream), "merge outer");
+  const int parts = 4 * h->num_sms;
+  TRY(ensure(h, x->errp, sizeof(double) * 2 * parts));
+  CK(launch_reconstruct_mats((const double*)x->recA.p, (const double*)x->recC.p, sp.P_in, sp.P_out, sp.Kp,
+                             ref, out, ref ? (double*)x->errp.p : nullptr, parts, h->stream),
+     "reconstruct");
+  if (!ref) return sync_and_status(h);
+  std::vector<double> hp(2 * (size_t)parts);
+  CK(cudaMemcpyAsync(hp.data(), x->errp.p, sizeof(double) * 2 * parts, cudaMemcpyDeviceToHost, h->stream),
+     "error partials");
+  TRY(sync_and_status(h));
+  double se = 0, sr = 0;
+  for (int i = 0; i < parts; ++i) { se += hp[2 * i]; sr += hp[2 * i + 1]; }
+  *err_out = sr > 0 ? sqrt(se / sr) : sqrt(se);
+  return TRD_OK;
+}
+
+trd_status trd_reconstruct(trd_t* h, float* out) {
+  TRY(check_handle(h));
+  if (!out) return set_err(h, TRD_EINVAL, "NULL output");
+  return reconstruct_impl(h, nullptr, out, nullptr, nullptr);
+}
+
+trd_status trd_reconstruct_from(trd_t* h, const double* const* cores_host, float* out) {
+  TRY(check_handle(h));
+  if (!out || !cores_host) return set_err(h, TRD_EINVAL, "NULL argument");
+  Extra* x = X_(h);
+  const double* ptrs[kMaxN] = {};
+  for (int k = 0; k < h->N; ++k) {
+    if (!cores_host[k]) return set_err(h, TRD_EINVAL, "NULL core");
+    const size_t bytes = sizeof(double) * h->I[k] * h->K[k];
+    TRY(ensure(h, x->tmpZ[k], bytes));
+    CK(cudaMemcpyAsync(x->tmpZ[k].p, cores_host[k], bytes, cudaMemcpyHostToDevice, h->stream), "core upload");
+    ptrs[k] = (const double*)x->tmpZ[k].p;
+  }
+  return reconstruct_impl(h, ptrs, out, nullptr, nullptr);
+}
+
+trd_status trd_recovery_error(trd_t* h, const float* ref, double* err) {
+  TRY(check_handle(h));
+  if (!ref || !err) return set_err(h, TRD_EINVAL, "NULL argument");
+  return reconstruct_impl(h, nullptr, nullptr, ref, err);
+}
+
+}  // extern "C"

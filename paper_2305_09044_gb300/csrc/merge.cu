@@ -1,0 +1,382 @@
+// Subchain merges (Def. 2 / Thm. 1), the back-contraction of the weighted contraction into
+// the gradient of one core (Eq. sd / Eq. hatd), RStS gather (Sec. 3.2.2), fixed-order
+// reductions and full reconstruction (Def. 1).
+#include "trd_internal.cuh"
+
+namespace trd {
+
+// ------------------------------------------------------------------ chain products
+// One warp per multi-index p: M = Z_{m0}(i_0) Z_{m1}(i_1) ... (Def. 2 core merging), built
+// in shared memory (FP64), then written row-major (transposed = false) or column-major
+// (transposed = true) into row p of `out` (stride ld).
+template <typename Tout>
+__global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_t ld, int cap) {
+  extern __shared__ double smem[];
+  const int warps = blockDim.x >> 5;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* Mb = smem + (size_t)w * 3 * cap;
+  double* Mn = Mb + cap;
+  double* Zs = Mn + cap;
+  for (int64_t p = (int64_t)blockIdx.x * warps + w; p < ch.count; p += (int64_t)gridDim.x * warps) {
+    int64_t rem = p;
+    int64_t sl[kMaxN];
+    for (int j = 0; j < ch.n; ++j) {
+      const int64_t i = rem % ch.dim[j];
+      rem /= ch.dim[j];
+      sl[j] = ch.idx[j] ? (int64_t)ch.idx[j][i] : i;
+    }
+    int R0 = ch.rows[0], C = ch.cols[0];
+    {
+      const double* z = ch.core[0] + sl[0] * (int64_t)(R0 * C);
+      for (int e = lane; e < R0 * C; e += 32) {
+        const int a = e % R0, b = e / R0;     // source is column-major within the slice
+        Mb[a * C + b] = z[e];
+      }
+    }
+    __syncwarp();
+    for (int j = 1; j < ch.n; ++j) {
+      const int Rj = ch.rows[j], Cj = ch.cols[j];
+      const double* z = ch.core[j] + sl[j] * (int64_t)(Rj * Cj);
+      for (int e = lane; e < Rj * Cj; e += 32) {
+        const int c = e % Rj, b = e / Rj;
+        Zs[c * Cj + b] = z[e];
+      }
+      __syncwarp();
+      for (int e = lane; e < R0 * Cj; e += 32) {
+        const int a = e / Cj, b = e % Cj;
+        double acc = 0.0;
+        for (int c = 0; c < C; ++c) acc = fma(Mb[a * C + c], Zs[c * Cj + b], acc);
+        Mn[e] = acc;
+      }
+      __syncwarp();
+      double* t = Mb; Mb = Mn; Mn = t;
+      C = Cj;
+      __syncwarp();
+    }
+    Tout* o = out + p * ld;
+    for (int e = lane; e < R0 * C; e += 32) {
+      const int a = e / C, b = e % C;
+      if (transposed) o[b * R0 + a] = (Tout)Mb[e];
+      else o[e] = (Tout)Mb[e];
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool transposed,
+                         int64_t ld, cudaStream_t st) {
+  if (ch.n <= 0 || ch.count <= 0) return cudaSuccess;
+  int cap = 1;
+  for (int j = 0; j < ch.n; ++j) {
+    cap = max(cap, ch.rows[0] * ch.cols[j]);
+    cap = max(cap, ch.rows[j] * ch.cols[j]);
+  }
+  const int warps = 4;
+  const size_t smem = (size_t)warps * 3 * cap * sizeof(double);
+  int64_t blocks = (ch.count + warps - 1) / warps;
+  if (blocks > 65535LL * 8) blocks = 65535LL * 8;
+  if (out_double) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_chain<double><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (double*)out, transposed, ld, cap);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_chain<float><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (float*)out, transposed, ld, cap);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ back-contraction
+// d(i_k)[alpha, beta] = sum over the other digits of the stationary block of
+//   [Post * M(s) * Pre][beta, alpha]
+// where M(s) is the r x r matrix held in row s of the reduced weighted contraction
+// (ROWS case: Ct[delta, gamma] = T[s][gamma r_c + delta]; COLS case: At[gamma, delta] =
+// T[s][gamma r_c + delta]) and s = pre + n_pre (i_k + I_k post).  Pre / Post are the
+// products of the cores between the block boundary and core k (identity when empty).
+__global__ void k_backcontract(const double* __restrict__ T, int Kp, int rows_case, int mr, int mc,
+                               const double* __restrict__ pre, int64_t n_pre,
+                               const double* __restrict__ post, int64_t n_post, int64_t Ik,
+                               int rk, int rk1, int64_t pairs_per_split,
+                               double* __restrict__ out) {
+  __shared__ double sM[kMaxR * kMaxR];
+  __shared__ double sPre[kMaxR * kMaxR];
+  __shared__ double sPost[kMaxR * kMaxR];
+  __shared__ double sV[kMaxR * kMaxR];
+  const int64_t ik = blockIdx.x;
+  const int K = rk * rk1;
+  const int64_t npairs = n_pre * n_post;
+  const int64_t q0 = (int64_t)blockIdx.y * pairs_per_split;
+  const int64_t q1 = min(npairs, q0 + pairs_per_split);
+  double acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+  for (int64_t q = q0; q < q1; ++q) {
+    const int64_t ip = q % n_pre, iq = q / n_pre;
+    const int64_t s = ip + n_pre * (ik + Ik * iq);
+    const double* Ts = T + s * (int64_t)Kp;
+    __syncthreads();
+    for (int e = threadIdx.x; e < mr * mc; e += blockDim.x) {
+      const int i = e / mc, j = e % mc;
+      sM[e] = rows_case ? Ts[j * mr + i] : Ts[i * mc + j];
+    }
+    if (pre)
+      for (int e = threadIdx.x; e < mc * rk; e += blockDim.x) sPre[e] = pre[ip * (int64_t)(mc * rk) + e];
+    if (post)
+      for (int e = threadIdx.x; e < rk1 * mr; e += blockDim.x) sPost[e] = post[iq * (int64_t)(rk1 * mr) + e];
+    __syncthreads();
+    // V = M * Pre  (mr x rk)
+    for (int e = threadIdx.x; e < mr * rk; e += blockDim.x) {
+      const int i = e / rk, a = e % rk;
+      double v;
+      if (pre) {
+        v = 0.0;
+        for (int j = 0; j < mc; ++j) v = fma(sM[i * mc + j], sPre[j * rk + a], v);
+      } else {
+        v = sM[i * mc + a];
+      }
+      sV[e] = v;
+    }
+    __syncthreads();
+    // U = Post * V  (rk1 x rk); thread owns entries e = beta*rk + alpha
+    int u = 0;
+    for (int e = threadIdx.x; e < K; e += blockDim.x, ++u) {
+      const int b = e / rk, a = e % rk;
+      double v;
+      if (post) {
+        v = 0.0;
+        for (int i = 0; i < mr; ++i) v = fma(sPost[b * mr + i], sV[i * rk + a], v);
+      } else {
+        v = sV[b * rk + a];
+      }
+      acc[u] += v;
+    }
+  }
+  int u = 0;
+  double* o = out + ((int64_t)blockIdx.y * Ik + ik) * K;
+  for (int e = threadIdx.x; e < K; e += blockDim.x, ++u) o[e] = acc[u];
+}
+
+__global__ void k_sum_splits(const double* __restrict__ part, int nsplit, int64_t n,
+                             double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < nsplit; ++j) s += part[(int64_t)j * n + i];
+    out[i] = s;
+  }
+}
+
+cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int mr, int mc,
+                                const double* pre, int64_t n_pre, const double* post,
+                                int64_t n_post, int64_t Ik, int rk, int rk1, double* dpart,
+                                int nsplit, double* d, cudaStream_t st) {
+  const int64_t npairs = n_pre * n_post;
+  const int64_t per = (npairs + nsplit - 1) / nsplit;
+  const int threads = 128;
+  dim3 grid((unsigned)Ik, (unsigned)nsplit);
+  double* target = nsplit == 1 ? d : dpart;
+  k_backcontract<<<grid, threads, 0, st>>>((const double*)Tsum_d, Kp, rows_case ? 1 : 0, mr, mc,
+                                           pre, n_pre, post, n_post, Ik, rk, rk1, per, target);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || nsplit == 1) return e;
+  const int64_t n = Ik * rk * rk1;
+  k_sum_splits<<<(unsigned)imin((n + 255) / 256, 4096), 256, 0, st>>>(dpart, nsplit, n, d);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ fixed-order reductions
+template <typename T>
+__global__ void k_reduce_T(const T* __restrict__ part, int splits, int64_t n, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < splits; ++j) s += (double)part[(int64_t)j * n + i];
+    out[i] = s;
+  }
+}
+
+cudaError_t launch_reduce_T(const void* Tpart, bool is_double, int splits, int64_t n,
+                            double* Tsum, cudaStream_t st) {
+  const unsigned blocks = (unsigned)imin((n + 255) / 256, 8192);
+  if (is_double) k_reduce_T<double><<<blocks, 256, 0, st>>>((const double*)Tpart, splits, n, Tsum);
+  else k_reduce_T<float><<<blocks, 256, 0, st>>>((const float*)Tpart, splits, n, Tsum);
+  return cudaGetLastError();
+}
+
+// stat_part[c][8] -> stat_sum[8], fixed order (one block of 256 threads, strided partial
+// sums then a fixed tree).
+__global__ void k_reduce_stats(const double* __restrict__ part, int ctas, double* __restrict__ out) {
+  __shared__ double sh[256];
+  for (int f = 0; f < 8; ++f) {
+    double s = 0.0;
+    for (int c = threadIdx.x; c < ctas; c += blockDim.x) s += part[(int64_t)c * 8 + f];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[f] = sh[0];
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_reduce_stats(const double* stat_part, int ctas, double* stat_sum,
+                                int* /*dstatus*/, cudaStream_t st) {
+  k_reduce_stats<<<1, 256, 0, st>>>(stat_part, ctas, stat_sum);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ reconstruction
+// out(a, b) = sum_kappa A[a][kappa] C[b][kappa] = Tr(A(a) C(b)) (Def. 1 via Thm. 1's split);
+// optional comparison with a reference tensor accumulates sum (xhat - ref)^2 and sum ref^2.
+__global__ void k_reconstruct(const double* __restrict__ A, const double* __restrict__ C,
+                              int64_t P_in, int64_t P_out, int Kp, const float* __restrict__ ref,
+                              float* __restrict__ out, double* __restrict__ err_part) {
+  __shared__ double sh[2][256];
+  double se = 0.0, sr = 0.0;
+  const int64_t n = P_in * P_out;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = l % P_in, b = l / P_in;
+    const double* Ar = A + a * Kp;
+    const double* Cr = C + b * Kp;
+    double v = 0.0;
+    for (int k = 0; k < Kp; ++k) v = fma(Ar[k], Cr[k], v);
+    if (out) out[l] = (float)v;
+    if (ref) {
+      const double r = (double)ref[l];
+      se += (v - r) * (v - r);
+      sr += r * r;
+    }
+  }
+  if (!err_part) return;
+  sh[0][threadIdx.x] = se;
+  sh[1][threadIdx.x] = sr;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    err_part[2 * blockIdx.x] = sh[0][0];
+    err_part[2 * blockIdx.x + 1] = sh[1][0];
+  }
+}
+
+cudaError_t launch_reconstruct_mats(const double* A, const double* C, int64_t P_in, int64_t P_out,
+                                    int Kp, const float* Xref, float* out, double* err_part,
+                                    int parts, cudaStream_t st) {
+  k_reconstruct<<<parts, 256, 0, st>>>(A, C, P_in, P_out, Kp, Xref, out, err_part);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ RStS gather
+// One warp per 32 consecutive sketch entries: each lane maps its sketch multi-index through
+// the index sets to the full tensor, copies the value, and the warp packs the mask bits.
+struct GatherArgs {
+  const float* X;
+  const uint32_t* M;
+  int N;
+  int64_t sdim[kMaxN];
+  int64_t fstride[kMaxN];
+  const int32_t* idx[kMaxN];
+  int64_t numel;
+  float* XI;
+  uint32_t* PI;
+  int64_t words;
+};
+
+__global__ void k_gather(GatherArgs g) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t wd = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); wd < g.words;
+       wd += (int64_t)gridDim.x * wpb) {
+    const int64_t l = wd * 32 + lane;
+    bool obs = false;
+    if (l < g.numel) {
+      int64_t rem = l, full = 0;
+      for (int m = 0; m < g.N; ++m) {
+        const int64_t i = rem % g.sdim[m];
+        rem /= g.sdim[m];
+        const int64_t fi = g.idx[m] ? (int64_t)g.idx[m][i] : i;
+        full += fi * g.fstride[m];
+      }
+      g.XI[l] = g.X[full];
+      obs = g.M ? ((g.M[full >> 5] >> (full & 31)) & 1u) : true;
+    }
+    const unsigned bits = __ballot_sync(0xffffffffu, obs);
+    if (lane == 0) g.PI[wd] = bits;
+  }
+}
+
+cudaError_t launch_gather(const float* X, const uint32_t* M, int N, const int64_t* full_dim,
+                          const View& v, float* XI, uint32_t* PI, cudaStream_t st) {
+  GatherArgs g;
+  g.X = X; g.M = M; g.N = N; g.numel = v.numel; g.XI = XI; g.PI = PI;
+  int64_t stride = 1;
+  for (int m = 0; m < N; ++m) {
+    g.sdim[m] = v.dim[m];
+    g.fstride[m] = stride;
+    stride *= full_dim[m];
+    g.idx[m] = v.idx[m];
+  }
+  g.words = (v.numel + 31) / 32;
+  const int64_t words_padded = (g.words + 3) / 4 * 4;
+  // zero the padding words
+  if (words_padded > g.words) {
+    cudaError_t e = cudaMemsetAsync(PI + g.words, 0, (words_padded - g.words) * 4, st);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned blocks = (unsigned)imin((g.words + 7) / 8, 152 * 32);
+  k_gather<<<blocks, 256, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ small helpers
+__global__ void k_set_scalar(double* p, double v) { *p = v; }
+
+cudaError_t launch_set_scalar(double* p, double v, cudaStream_t st) {
+  k_set_scalar<<<1, 1, 0, st>>>(p, v);
+  return cudaGetLastError();
+}
+
+// Split a float/double matrix into BF16 hi + lo parts (x ~ hi + lo), optionally with a
+// transposed copy of hi ([Kp][rows], stride ldT); columns >= Kp of the destination rows
+// are zero-filled up to ld_dst.
+template <typename T>
+__global__ void k_to_bf16_split(const T* __restrict__ src, int64_t rows, int Kp, int64_t ld_src,
+                                __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                __nv_bfloat16* __restrict__ hiT, int64_t ldT, int64_t ld_dst) {
+  const int64_t n = rows * ld_dst;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / ld_dst;
+    const int c = (int)(e % ld_dst);
+    const float v = c < Kp ? (float)src[r * ld_src + c] : 0.0f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    hi[e] = h;
+    if (lo) lo[e] = l;
+    if (hiT && c < Kp) hiT[(int64_t)c * ldT + r] = h;
+  }
+}
+
+cudaError_t launch_to_bf16_split(const void* src, bool src_double, int64_t rows, int Kp,
+                                 int64_t ld_src, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                 __nv_bfloat16* hiT, int64_t ldT, int64_t ld_dst,
+                                 cudaStream_t st) {
+  const int64_t n = rows * ld_dst;
+  const unsigned blocks = (unsigned)imin((n + 255) / 256, 8192);
+  if (src_double)
+    k_to_bf16_split<double><<<blocks, 256, 0, st>>>((const double*)src, rows, Kp, ld_src, hi, lo, hiT, ldT, ld_dst);
+  else
+    k_to_bf16_split<float><<<blocks, 256, 0, st>>>((const float*)src, rows, Kp, ld_src, hi, lo, hiT, ldT, ld_dst);
+  return cudaGetLastError();
+}
+
+}  // namespace trd

@@ -1,0 +1,223 @@
+// Internal declarations shared by the libtrd translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/trd.h"
+
+namespace trd {
+
+constexpr int kMaxN = TRD_MAX_ORDER;
+constexpr int kMaxR = TRD_MAX_RANK;
+constexpr int64_t kProbeMax = int64_t(1) << 20;   // adaptive-width probe size
+constexpr uint64_t kProbeSeed = 0x5eedull;
+
+__host__ __device__ inline int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ inline int64_t imax(int64_t a, int64_t b) { return a > b ? a : b; }
+
+// ------------------------------------------------------------------ device-side status
+enum DevStatus : int {
+  DEV_OK = 0,
+  DEV_SINGULAR = 1,   // Cholesky pivot <= 0
+  DEV_NONFINITE = 2,  // non-finite step or residual
+  DEV_TIMEOUT = 4,    // a bounded wait gave up
+  DEV_BOUNDS = 8      // an index check failed (access skipped)
+};
+
+// ------------------------------------------------------------------ a subchain of cores
+// Chain product Z_{m_0}(i_0) Z_{m_1}(i_1) ... over a multi-index p = overline{i_0 i_1 ..}
+// (first digit fastest).  Core slices use the mode-2 row-major layout: slice i of a core
+// with ranks (rows, cols) is element (a, b) at i*rows*cols + b*rows + a.
+struct Chain {
+  int n = 0;                         // number of cores (0 = identity)
+  const double* core[kMaxN] = {};
+  const int32_t* idx[kMaxN] = {};    // digit -> core slice (nullptr = identity)
+  int64_t dim[kMaxN] = {};           // extent of each digit
+  int rows[kMaxN] = {}, cols[kMaxN] = {};
+  int64_t count = 1;                 // product of dims
+  int out_rows = 0, out_cols = 0;    // product shape
+};
+
+// A tensor (full data or RStS sketch) seen by the data passes.
+struct View {
+  const float* X = nullptr;          // values, linear order (first mode fastest)
+  const uint32_t* M = nullptr;       // packed mask (nullptr = all observed)
+  int N = 0;
+  int64_t dim[kMaxN] = {};           // sizes of the view (s_j)
+  const int32_t* idx[kMaxN] = {};    // device map view index -> full index (nullptr = identity)
+  int64_t numel = 0;
+};
+
+// Split of the modes into an inner block 0..c-1 and an outer block c..N-1.
+struct Split {
+  int c = 1;
+  int64_t P_in = 1, P_out = 1;       // products of the view dims of each block
+  int Kp = 1;                        // r_0 * r_c
+  bool rows = true;                  // updated core in the inner block (stationary = inner)
+  int64_t P_stat = 1, P_strm = 1;
+};
+
+// Arguments of the fused data-pass kernels (all precisions).
+struct PassArgs {
+  const float* X;
+  const uint32_t* M;
+  int64_t P_in;                      // X(a, b) at a + P_in * b
+  int64_t P_stat, P_strm;
+  int Kp, ld;                        // row length and stride (elements) of the merged matrices
+  const void* Sst;                   // stationary merged matrix [P_stat][ld]
+  const void* Sh;                    // stationary merged with h (pass 2)
+  const void* Sstr;                  // streaming merged matrix [P_strm][ld]
+  const double* sigma;               // device scalar: kernel width (inf -> w = 1)
+  void* Tpart;                       // pass 1: partial contractions [splits][P_stat][Kp]
+  double* stat_part;                 // per-CTA statistics [ctas][8]
+  int64_t tiles_per_split;           // streaming tiles per CTA column split
+};
+
+// ------------------------------------------------------------------ work buffers
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace trd
+
+// The opaque handle.
+struct trd_handle {
+  int N = 0;
+  int64_t I[trd::kMaxN] = {};
+  int R[trd::kMaxN] = {};
+  int K[trd::kMaxN] = {};
+  int prec = TRD_FP32;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+
+  // data
+  const float* X = nullptr;
+  const uint32_t* M = nullptr;
+  int64_t numel = 0;
+
+  // cores (FP64 master, mode-2 row-major) and FGMC factors E_k (r_k^2 x r_{k+1}^2)
+  double* Z[trd::kMaxN] = {};
+  double* E[trd::kMaxN] = {};
+  uint64_t ver[trd::kMaxN] = {};     // core versions
+
+  // current view and sketch storage
+  trd::View view;
+  int view_k = -1;                   // core the current sketch was drawn for (-1: full)
+  bool sketched = false;
+  int32_t* idx_dev[trd::kMaxN] = {};
+  size_t idx_cap[trd::kMaxN] = {};
+  trd::DevBuf XI, PI;
+
+  // per-update state
+  int pass1_k = -1;                  // core of the last residual pass (-1 none)
+  int grad_k = -1;                   // core of the current d
+  int gram_k = -1;                   // core of the current G
+  uint64_t gram_ver[trd::kMaxN] = {};
+  trd::Split split;
+  int splits = 1, ctas = 1;
+  int64_t slots_last = 0;
+
+  // device scalars: [0] sigma in use, [1] sigma_prev, [2] num <d,h>, [3] den, [4] eta,
+  // [5] lambda used, [6] e (stop), [7] status word (as double), [8..] spare
+  double* scal = nullptr;
+  int* dstatus = nullptr;            // device status word (DevStatus bits)
+  double* report_dev = nullptr;      // per-iteration report staging [64]
+  double* host_pinned = nullptr;     // pinned staging for read-backs [256]
+  int32_t* idx_pinned = nullptr;     // pinned staging for index uploads
+  size_t idx_pinned_cap = 0;
+
+  // work buffers
+  trd::DevBuf Sst, Sstr, Sh;         // merged matrices (compute type)
+  trd::DevBuf Sst_bf, Sstr_bf, Sh_bf, SstrT_bf, SstT_bf; // BF16 operands (hi|lo)
+  trd::DevBuf Tpart, Tsum, stat_part, stat_sum;
+  trd::DevBuf pre, post, dpart;      // back-contraction
+  trd::DevBuf d, h, G, L, T1, T2, D, Dprev;
+  trd::DevBuf probe_keys, probe_vals, probe_work;
+  bool merged_valid_st = false, merged_valid_str = false;
+  uint64_t merged_ver[trd::kMaxN] = {};
+  int merged_k = -1;
+  int32_t t = 0;
+  bool have_D0 = false;
+  bool sigma_set = false;
+};
+
+namespace trd {
+
+// ------------------------------------------------------------------ host helpers (api)
+trd_status set_err(trd_handle* h, trd_status s, const std::string& msg);
+trd_status cuda_check(trd_handle* h, cudaError_t e, const char* what);
+trd_status ensure(trd_handle* h, DevBuf& b, size_t bytes);
+
+// ------------------------------------------------------------------ launchers
+// merge.cu
+cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool transposed,
+                         int64_t ld, cudaStream_t st);
+cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int mr, int mc,
+                                const double* pre, int64_t n_pre, const double* post,
+                                int64_t n_post, int64_t Ik, int rk, int rk1, double* dpart,
+                                int nsplit, double* d, cudaStream_t st);
+cudaError_t launch_reduce_T(const void* Tpart, bool is_double, int splits, int64_t n,
+                            double* Tsum, cudaStream_t st);
+cudaError_t launch_reduce_stats(const double* stat_part, int ctas, double* stat_sum,
+                                int* dstatus, cudaStream_t st);
+cudaError_t launch_reconstruct_mats(const double* A, const double* C, int64_t P_in, int64_t P_out,
+                                    int Kp, const float* Xref, float* out, double* err_part,
+                                    int parts, cudaStream_t st);
+cudaError_t launch_gather(const float* X, const uint32_t* M, int N, const int64_t* full_dim,
+                          const View& v, float* XI, uint32_t* PI, cudaStream_t st);
+cudaError_t launch_set_scalar(double* p, double v, cudaStream_t st);
+cudaError_t launch_to_bf16_split(const void* src, bool src_double, int64_t rows, int Kp,
+                                 int64_t ld_src, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                 __nv_bfloat16* hiT, int64_t ldT, int64_t ld_dst,
+                                 cudaStream_t st);
+
+// pass_simt.cu
+cudaError_t launch_pass_simt(const PassArgs& a, bool is_double, bool rows_case, bool pass2,
+                             int splits, int* ctas_out, int* splits_out, cudaStream_t st);
+
+// fgmc_solve.cu
+cudaError_t launch_fgmc_E(const double* Z, const int32_t* idx, int64_t n, int rk, int rk1,
+                          double* E, cudaStream_t st);
+cudaError_t launch_dgemm(const double* A, const double* B, double* C, int M, int N, int K,
+                         bool transB, cudaStream_t st);
+cudaError_t launch_phi(const double* T, int p, int q, double* G, cudaStream_t st);
+cudaError_t launch_cholesky(const double* G, int K, double lambda, double* L, double* scal,
+                            int* dstatus, cudaStream_t st);
+cudaError_t launch_solve_rows(const double* L, const double* d, double* h, int K, int64_t rows,
+                              cudaStream_t st);
+cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* out,
+                       cudaStream_t st);
+cudaError_t launch_eta(const double* num, const double* den, double fixed_eta, int* dstatus,
+                       double* eta, double* eta_slot, cudaStream_t st);
+cudaError_t launch_axpy_core(double* Z, const double* h, int64_t n, const double* eta,
+                             cudaStream_t st);
+cudaError_t launch_stop_error(const double* D, double* Dprev, int64_t n, double* e_out,
+                              cudaStream_t st);
+
+// sigma.cu
+size_t sigma_work_doubles();
+cudaError_t launch_probe_sigma(const double* const* Zdev_ptrs, int N, const int64_t* dim_dev,
+                               const int* R_dev, const float* X, const uint32_t* M, int64_t numel,
+                               bool fp64, double sigma_prev, const double* sigma_prev_dev,
+                               double* vals, uint64_t* keys, double* xsq, double* work,
+                               double* sigma_out, cudaStream_t st);
+cudaError_t launch_sigma_from_floats(const float* r, int64_t n, double x_obs_rms, double sigma_prev,
+                                     double* vals, uint64_t* keys, double* xsq, double* work,
+                                     double* sigma_out, cudaStream_t st);
+
+// sampled.cu
+cudaError_t launch_sampled(const void* const* cores, int N, const int* R, const int64_t* I,
+                           const int32_t* idx, const void* x, int64_t M, double sigma,
+                           bool fp64, void* resid, double* loss_part, int parts,
+                           void* const* grads, double g_scale, bool backward,
+                           cudaStream_t st);
+
+}  // namespace trd
