@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput of the AWRTRD hot path on one GB300 (or N independent replicas).
+
+A step is one outer iteration of Algorithm 1 (every core updated once: residuals, HQ
+weights, weighted gradient, FGMC Gram, Cholesky-scaled step with exact line search) on the
+100^4 workload: TR ranks 8, 50 % missing, 20 % of observed entries replaced by outliers
+U[-10 std, 10 std], additive N(0, 1e-3) noise, full-tensor gradient (no sketch).  Inputs are
+synthetic (seeded), the tensor (400 MB) is larger than L2, so no flush is needed between
+steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32|fp64]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "AWRTRD iters/s & sampled entries/s to rel-err≤1e-3: BF16-TC vs FP32 on one GB300"
+UNIT = "sampled entries/s"
+WORKLOAD = "cfg100"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# CPU-oracle sample: the sub-tensor i_4 < 10 of the 100^4 workload (10^7 slots)
+ORACLE_SLICES = 10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=None, choices=[None, "bf16", "fp32", "fp64"])
+    ap.add_argument("--no-converge", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--converge-iters", type=int, default=60)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload_config(w, precision):
+    return {
+        "workload": f"{w.name}: {'x'.join(map(str, w.dims))} TR ranks {w.ranks[0]}, "
+                    f"{int(w.missing * 100)}% missing, {int(w.outlier_frac * 100)}% outliers "
+                    f"U[-10 std,10 std] + N(0,{w.noise_var:g}) noise, full-tensor AWRTRD step "
+                    f"(all {len(w.dims)} cores)",
+        "dims": list(w.dims), "ranks": list(w.ranks), "precision": precision,
+        "sigma": "adaptive (per iteration, 2^20-entry probe)",
+        "l2": "inputs larger than L2 (400 MB tensor + 12.5 MB mask per pass), no flush",
+        "seeds": {"data": w.data_seed, "init": w.init_seed},
+    }
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ----------------------------------------------------------------------------- problem
+def build_problem(w, torch, prec):
+    """Seeded synthetic tensor on the device: X_true = R(Z_true) by the library's
+    reconstruction kernel, then noise and outliers from the workload generator."""
+    from paper_2305_09044_gb300 import TRD, synth
+    truth = synth.gaussian_cores(w.dims, w.ranks, w.data_seed)
+    t = TRD(w.dims, w.ranks, prec)
+    Xt = t.reconstruct_from(truth)
+    torch.cuda.synchronize()
+    xt_host = Xt.cpu().numpy().astype(np.float64).reshape(w.dims, order="F")
+    c = synth.draw_corruption(w)
+    X = synth.assemble(xt_host, c).astype(np.float32).reshape(-1, order="F")
+    words = synth.pack_mask(c.mask)
+    del xt_host
+    Xh = torch.from_numpy(X).pin_memory()
+    Mh = torch.from_numpy(words.view(np.int32)).pin_memory()
+    Xd = Xh.cuda()
+    Md = Mh.cuda()
+    t.set_data(Xd, Md)
+    return t, Xt, (Xh, Mh), (Xd, Md), c
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2305_09044_gb300 import synth
+    from paper_2305_09044_gb300.binding import kernel_launches
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    prec = args.precision or "fp32"
+    w = synth.WORKLOADS[WORKLOAD]
+    if world > 1:   # independent replicas: a different data seed per rank
+        import dataclasses
+        w = dataclasses.replace(w, data_seed=w.data_seed + 100 * rank, init_seed=w.init_seed + 100 * rank)
+    t, Xt, host, dev, corr = build_problem(w, torch, prec)
+    t.init_cores(w.init_seed)
+    slots_per_step = len(w.dims) * int(np.prod(w.dims))
+    stream = t.stream
+
+    for _ in range(max(args.warmup, 3)):
+        t.step(sigma=-1.0)
+    t.set_profiling(True)
+    t.get_profile(reset=True)
+    _barrier(world)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        t.step(sigma=-1.0)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = kernel_launches() - l0
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = t.get_profile(reset=True)
+    t.set_profiling(False)
+    ms = _max_over_ranks(ms, world)
+    ms_step = ms / args.steps
+    value = world * slots_per_step * args.steps / (ms / 1e3)
+
+    # e2e through the public API with host buffers: H2D of X and mask from pinned memory,
+    # one trd_step, the report read back (inside trd_step)
+    Xh, Mh = host
+    Xd, Md = dev
+    h2d = Xh.numel() * 4 + Mh.numel() * 4
+    d2h = 32 * 8
+    torch.cuda.synchronize()
+    _barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Xd.copy_(Xh, non_blocking=True)
+        Md.copy_(Mh, non_blocking=True)
+        t.step(sigma=-1.0)
+    torch.cuda.synchronize()
+    e2e_s = _max_over_ranks((time.perf_counter() - t0) * 1e3, world) / 1e3
+    e2e = {"value": world * slots_per_step * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "ms_per_step": e2e_s * 1e3 / args.steps}
+
+    # roofline of the dominant kernel (the fused data passes), from the in-region events
+    pk, src = peaks()
+    Kp = w.ranks[0] * w.ranks[len(w.dims) // 2]
+    n_slots = int(np.prod(w.dims))
+    launches_pass = prof["pass1_n"] + prof["pass2_n"]
+    pass_ms = (prof["pass1_ms"] + prof["pass2_ms"]) / max(launches_pass, 1)
+    if prec == "bf16":
+        algo = n_slots * (4 + 1 / 8)                    # x (FP32) + mask bit per slot
+        achieved = algo / (pass_ms / 1e3) / 1e9
+        roof = {"kernel": "fused data pass (tcgen05)", "bound": "hbm", "achieved": achieved,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                "traffic": None, "peak_source": src}
+    else:
+        algo = n_slots * 4 * Kp                         # 2 Kp recon + 2 Kp contraction per slot
+        sm = pk.get("sm_max_mhz", 2070.0)
+        if prec == "fp32":
+            peak = 152 * 128 * 2 * sm * 1e6 / 1e12
+            psrc = f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm:.0f} MHz"
+        else:
+            peak, psrc = 1.25, "nominal GB300 FP64 rate"
+        achieved = algo / (pass_ms / 1e3) / 1e12
+        roof = {"kernel": "k_pass_simt (fused data pass, CUDA cores)", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": psrc}
+    roof["ms_per_launch"] = pass_ms
+    roof["launches"] = launches_pass
+    roof["algorithmic_per_launch"] = algo
+    roof["hbm_bytes_per_launch"] = n_slots * (4 + 1 / 8)
+    roof["hbm_gbs_achieved"] = roof["hbm_bytes_per_launch"] / (pass_ms / 1e3) / 1e9
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[prec],
+           "data": "synthetic", "config": workload_config(w, prec), "iters_per_s": 1e3 / ms_step,
+           "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": ck}
+
+    if rank == 0 and not args.no_converge:
+        out["time_to_rel_err_1e-3"] = converge(t, Xt, w, args.converge_iters, torch)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, corr, budget_s=15.0)
+    t.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def converge(t, Xt, w, iters, torch):
+    """Iterations and device time from a fresh initialisation until the recovery error
+    ||R(Z) - X_true|| / ||X_true|| <= 1e-3 (error evaluated outside the timed steps)."""
+    t.init_cores(w.init_seed)
+    stream = t.stream
+    total = 0.0
+    err = t.recovery_error(Xt)
+    for it in range(iters):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        t.step(sigma=-1.0)
+        b.record(stream)
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b)
+        err = t.recovery_error(Xt)
+        if err <= 1e-3:
+            return {"reached": True, "iters": it + 1, "seconds": total / 1e3, "rel_err": err}
+    return {"reached": False, "iters": iters, "seconds": total / 1e3, "rel_err": err}
+
+
+# ----------------------------------------------------------------------------- oracle
+def oracle_sample(w, corr):
+    """The CPU oracle's bounded sample: the sub-tensor i_4 < 10 of the workload."""
+    from oracle import trd_oracle as O
+    from paper_2305_09044_gb300 import synth
+    dims = list(w.dims)
+    sub = dims[:-1] + [ORACLE_SLICES]
+    truth = synth.gaussian_cores(w.dims, w.ranks, w.data_seed)
+    truth_sub = [Z if k < len(dims) - 1 else Z[:, :ORACLE_SLICES, :] for k, Z in enumerate(truth)]
+    Xt = O.reconstruct_unfold(truth_sub)
+    if corr is None:
+        corr = synth.draw_corruption(w)
+    sl = (slice(None),) * (len(dims) - 1) + (slice(0, ORACLE_SLICES),)
+    c = synth.Corruption(corr.mask[sl], corr.outlier[sl], corr.outlier_u[sl],
+                         None if corr.noise is None else corr.noise[sl])
+    X = synth.assemble(Xt, c).astype(np.float32).astype(np.float64)
+    P = c.mask.astype(np.float64)
+    cores = O.init_cores(w.dims, w.ranks, seed=w.init_seed)
+    cores = [Z if k < len(dims) - 1 else Z[:, :ORACLE_SLICES, :] for k, Z in enumerate(cores)]
+    obs = P > 0
+    sigma = O.adaptive_sigma((X - O.reconstruct_unfold(cores))[obs], float(np.sqrt(np.mean(X[obs] ** 2))))
+    return X, P, cores, sigma, sub
+
+
+def cpu_baseline(w, corr, budget_s=15.0):
+    from oracle import trd_oracle as O
+    X, P, cores, sigma, sub = oracle_sample(w, corr)
+    slots = int(np.prod(sub))
+    done, spent, k = 0, 0.0, 0
+    while spent < budget_s or done == 0:
+        t0 = time.perf_counter()
+        cores = O.core_update(X, P, cores, k % len(sub), sigma).cores
+        spent += time.perf_counter() - t0
+        done += 1
+        k += 1
+        if done >= 8:
+            break
+    return {"value": done * slots / spent, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} FP64 oracle core updates on the {'x'.join(map(str, sub))} sub-tensor "
+                      f"(i_4 < {ORACLE_SLICES}) of the workload, {slots} slots each; numpy BLAS "
+                      f"threads for the products, element-wise steps single-threaded",
+            "seconds": spent}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2305_09044_gb300 import synth
+    from oracle import trd_oracle as O
+    w = synth.WORKLOADS[WORKLOAD]
+    X, P, cores, sigma, sub = oracle_sample(w, None)
+    slots = int(np.prod(sub))
+    N = len(sub)
+    for i in range(max(args.warmup, 3)):
+        cores = O.core_update(X, P, cores, i % N, sigma).cores
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        cores = O.core_update(X, P, cores, i % N, sigma).cores
+    dt = time.perf_counter() - t0
+    value = args.steps * slots / dt
+    cfg = workload_config(w, "fp64 (CPU oracle)")
+    cfg["sample"] = f"each step is one oracle core update on the {'x'.join(map(str, sub))} sub-tensor"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": dt * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": cfg["sample"]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- dist helpers
+_pg = None
+
+
+def _init_dist(world):
+    global _pg
+    if world > 1 and _pg is None:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo")
+        _pg = dist
+
+
+def _barrier(world):
+    if world > 1:
+        _pg.barrier()
+
+
+def _max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    _pg.all_reduce(t, op=_pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    _init_dist(world)
+    run_ours(args, rank, world, local)
+    if world > 1:
+        _pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -227,6 +227,21 @@ trd_status trd_reconstruct_from(trd_t* handle, const double* const* cores_host, 
 /* ||X_hat - X_ref||_F / ||X_ref||_F over all entries, X_ref a DEVICE tensor (floats). */
 trd_status trd_recovery_error(trd_t* handle, const float* Xref_dev, double* err_out);
 
+/* ---------------------------------------------------------------- tracing */
+
+/* When `on` is nonzero the handle records CUDA events on its stream around every launch of
+ * the fused data-pass kernels (pass 1: reconstruction, residual, weight and weighted
+ * contraction; pass 2: the line-search pass).  Off by default. */
+trd_status trd_set_profiling(trd_t* handle, int on);
+
+/* Synchronise the handle's stream and write out[0] = total milliseconds of the pass-1
+ * launches recorded since the last reset, out[1] = their number, out[2] and out[3] the same
+ * for pass 2 (host array of 4 doubles).  reset != 0 clears the totals afterwards. */
+trd_status trd_get_profile(trd_t* handle, int reset, double* out);
+
+/* Number of kernels the library has launched in this process (all handles). */
+int64_t trd_kernel_launches(void);
+
 /* ---------------------------------------------------------------- sampled correntropy */
 
 /* Forward of the sampled correntropy loss (Eq. corr in Welsch form) for the cores given

@@ -34,7 +34,8 @@ EXPORTS = [
     "trd_sample_subtensor", "trd_draw_indices", "trd_residual_weights", "trd_core_gradient",
     "trd_fgmc_gram", "trd_core_update", "trd_step", "trd_adaptive_sigma",
     "trd_sigma_from_residuals", "trd_reconstruct", "trd_reconstruct_from",
-    "trd_recovery_error", "trd_sampled_fwd", "trd_sampled_bwd",
+    "trd_recovery_error", "trd_sampled_fwd", "trd_sampled_bwd", "trd_set_profiling",
+    "trd_get_profile", "trd_kernel_launches",
 ]
 
 
@@ -99,12 +100,16 @@ def load(path: str = LIB_PATH):
         "trd_recovery_error": [vp, vp, P(dbl)],
         "trd_sampled_fwd": [vp, P(vp), vp, vp, i64, dbl, C.c_int, vp, P(dbl)],
         "trd_sampled_bwd": [vp, P(vp), vp, vp, i64, dbl, C.c_int, dbl, P(vp)],
+        "trd_set_profiling": [vp, C.c_int],
+        "trd_get_profile": [vp, C.c_int, P(dbl)],
+        "trd_kernel_launches": [],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = C.c_int
     lib.trd_destroy.restype = None
+    lib.trd_kernel_launches.restype = C.c_int64
     lib.trd_last_error.restype = C.c_char_p
     lib.trd_status_string.restype = C.c_char_p
     _lib = lib
@@ -129,6 +134,10 @@ def core_to_abi(Z: np.ndarray) -> np.ndarray:
 
 def core_from_abi(A: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(A.transpose(2, 0, 1))
+
+
+def kernel_launches() -> int:
+    return int(load().trd_kernel_launches())
 
 
 def draw_indices(seed: int, t: int, k: int, j: int, N: int, I: int, s: int) -> np.ndarray:
@@ -299,6 +308,14 @@ class TRD:
         self._check(self.lib.trd_reconstruct_from(self.h, ptrs, C.c_void_p(_dptr(out))),
                     "trd_reconstruct_from")
         return out
+
+    def set_profiling(self, on: bool = True):
+        self._check(self.lib.trd_set_profiling(self.h, 1 if on else 0), "trd_set_profiling")
+
+    def get_profile(self, reset: bool = False) -> dict:
+        out = (C.c_double * 4)()
+        self._check(self.lib.trd_get_profile(self.h, 1 if reset else 0, out), "trd_get_profile")
+        return {"pass1_ms": out[0], "pass1_n": int(out[1]), "pass2_ms": out[2], "pass2_n": int(out[3])}
 
     def recovery_error(self, Xref) -> float:
         out = C.c_double()

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -41,6 +42,10 @@ trd_status ensure(trd_handle* h, DevBuf& b, size_t bytes) {
   return TRD_OK;
 }
 
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
 // implemented in merge.cu / sampled.cu / pass_tc.cu
 cudaError_t launch_reconstruct_mats(const double* A, const double* C, int64_t P_in, int64_t P_out,
                                     int Kp, const float* Xref, float* out, double* err_part,
@@ -72,11 +77,71 @@ struct Extra {
   DevBuf errp;          // reconstruction error partials
   DevBuf tmpZ[kMaxN];   // cores given to trd_reconstruct_from
   DevBuf probe_xsq;
+  // BF16 tensor-core operands and the padded mask rows of the current view
+  DevBuf bShi, bSlo, bSh, bThi, bTlo, bTT, Mrows;
+  const float* mrows_X = nullptr;
+  const uint32_t* mrows_M = nullptr;
+  int64_t mrows_Pin = -1, mrows_Pout = -1;
+  int64_t ldT = 0, W = 0;
+  int tcG = 0;
+  // tracing: event pairs around data-pass launches (kind 0 = pass 1, 1 = pass 2)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Pending { cudaEvent_t a, b; int kind; };
+  std::vector<Pending> pending;
+  double prof_ms[2] = {0, 0};
+  int64_t prof_n[2] = {0, 0};
+  cudaEvent_t ev_open = nullptr;
 };
 
 Extra* X_(trd_handle* h);
 
 bool is_fp64(const trd_handle* h) { return h->prec == TRD_FP64; }
+
+cudaEvent_t pool_event(Extra* x) {
+  if (!x->ev_pool.empty()) {
+    cudaEvent_t e = x->ev_pool.back();
+    x->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return e;
+}
+
+void prof_begin(trd_handle* h) {
+  Extra* x = X_(h);
+  if (!x->prof) return;
+  x->ev_open = pool_event(x);
+  if (x->ev_open) cudaEventRecord(x->ev_open, h->stream);
+}
+
+void prof_end(trd_handle* h, int kind) {
+  Extra* x = X_(h);
+  if (!x->prof || !x->ev_open) return;
+  cudaEvent_t b = pool_event(x);
+  if (!b) return;
+  cudaEventRecord(b, h->stream);
+  x->pending.push_back({x->ev_open, b, kind});
+  x->ev_open = nullptr;
+}
+
+// After a stream synchronisation: fold finished event pairs into the totals.
+void prof_harvest(trd_handle* h) {
+  Extra* x = X_(h);
+  for (auto& p : x->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      x->prof_ms[p.kind] += ms;
+      x->prof_n[p.kind] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    x->ev_pool.push_back(p.a);
+    x->ev_pool.push_back(p.b);
+  }
+  x->pending.clear();
+}
 size_t elt(const trd_handle* h) { return is_fp64(h) ? sizeof(double) : sizeof(float); }
 
 // Balanced split of the view's modes into [0, c) and [c, N).
@@ -297,27 +362,106 @@ PassArgs pass_args(trd_handle* h) {
   return a;
 }
 
+trd_status run_pass1_tc(trd_handle* h, int k) {
+  const Split& sp = h->split;
+  Extra* x = X_(h);
+  const int KP = tc_kpad();
+  if (sp.Kp > KP) return set_err(h, TRD_ENOTIMPL, "BF16 path supports r_1 r_c <= 64");
+  if (sp.P_in % 4) return set_err(h, TRD_ENOTIMPL, "BF16 path needs the inner block size to be a multiple of 4");
+  TRY(build_merged(h, k, false));
+  const View& v = h->view;
+  // padded mask rows of the view (cached while the view and split are unchanged)
+  const int64_t W = ((sp.P_in + 31) / 32 + 3) / 4 * 4;
+  if (x->mrows_X != v.X || x->mrows_M != v.M || x->mrows_Pin != sp.P_in || x->mrows_Pout != sp.P_out) {
+    TRY(ensure(h, x->Mrows, sizeof(uint32_t) * (size_t)(sp.P_out * W)));
+    CK(launch_mask_rows(v.M, sp.P_in, sp.P_out, W, (uint32_t*)x->Mrows.p, h->stream), "mask rows");
+    x->mrows_X = v.X;
+    x->mrows_M = v.M;
+    x->mrows_Pin = sp.P_in;
+    x->mrows_Pout = sp.P_out;
+  }
+  x->W = W;
+  const int64_t ldT = (sp.P_strm + 63) / 64 * 64;
+  x->ldT = ldT;
+  const size_t b2 = sizeof(__nv_bfloat16);
+  TRY(ensure(h, x->bShi, b2 * sp.P_stat * KP));
+  TRY(ensure(h, x->bSlo, b2 * sp.P_stat * KP));
+  TRY(ensure(h, x->bThi, b2 * sp.P_strm * KP));
+  TRY(ensure(h, x->bTlo, b2 * sp.P_strm * KP));
+  TRY(ensure(h, x->bTT, b2 * KP * ldT));
+  CK(launch_tc_prep((const float*)h->Sst.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bShi.p,
+                    (__nv_bfloat16*)x->bSlo.p, nullptr, 0, h->stream), "bf16 stationary operands");
+  CK(launch_tc_prep((const float*)h->Sstr.p, sp.P_strm, sp.Kp, (__nv_bfloat16*)x->bThi.p,
+                    (__nv_bfloat16*)x->bTlo.p, (__nv_bfloat16*)x->bTT.p, ldT, h->stream), "bf16 streaming operands");
+  const int64_t RB = (sp.P_stat + tc_bm() - 1) / tc_bm();
+  const int64_t NT = (sp.P_strm + tc_bn() - 1) / tc_bn();
+  const int G = (int)imin(h->num_sms, RB * NT);
+  x->tcG = G;
+  TRY(ensure(h, h->Tpart, sizeof(float) * (size_t)(G + RB) * tc_bm() * sp.Kp));
+  TRY(ensure(h, h->stat_part, sizeof(double) * 8 * (size_t)G));
+  TRY(ensure(h, h->Tsum, sizeof(double) * (size_t)sp.P_stat * sp.Kp));
+  prof_begin(h);
+  CK(launch_pass_tc(sp.rows, false, (const __nv_bfloat16*)x->bShi.p, (const __nv_bfloat16*)x->bSlo.p, nullptr,
+                    (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p, (const __nv_bfloat16*)x->bTT.p,
+                    ldT, v.X, sp.P_in, sp.P_out, (const uint32_t*)x->Mrows.p, W, sp.P_stat, sp.P_strm, sp.Kp,
+                    h->scal + S_SIGMA, (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, G, h->stream),
+     "tensor-core data pass 1");
+  prof_end(h, 0);
+  CK(launch_reduce_slots((const float*)h->Tpart.p, RB, NT, G, sp.P_stat, sp.Kp, (double*)h->Tsum.p, h->stream),
+     "reduce contraction");
+  CK(launch_reduce_stats((const double*)h->stat_part.p, G, (double*)h->stat_sum.p, h->dstatus, h->stream),
+     "reduce statistics");
+  h->ctas = G;
+  return TRD_OK;
+}
+
+trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
+  const Split& sp = h->split;
+  Extra* x = X_(h);
+  TRY(build_merged(h, k, true));
+  TRY(ensure(h, x->bSh, sizeof(__nv_bfloat16) * sp.P_stat * tc_kpad()));
+  CK(launch_tc_prep((const float*)h->Sh.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bSh.p, nullptr, nullptr, 0,
+                    h->stream), "bf16 step operands");
+  prof_begin(h);
+  CK(launch_pass_tc(sp.rows, true, (const __nv_bfloat16*)x->bShi.p, (const __nv_bfloat16*)x->bSlo.p,
+                    (const __nv_bfloat16*)x->bSh.p, (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p,
+                    (const __nv_bfloat16*)x->bTT.p, x->ldT, h->view.X, sp.P_in, sp.P_out,
+                    (const uint32_t*)x->Mrows.p, x->W, sp.P_stat, sp.P_strm, sp.Kp, h->scal + S_SIGMA,
+                    (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, x->tcG, h->stream),
+     "tensor-core data pass 2");
+  prof_end(h, 1);
+  double* s2 = (double*)x->stat_sum2.p;
+  CK(launch_reduce_stats((const double*)h->stat_part.p, x->tcG, s2, h->dstatus, h->stream), "reduce den");
+  *den = s2 + 6;
+  return TRD_OK;
+}
+
 trd_status run_pass1(trd_handle* h, int k) {
-  if (h->prec == TRD_BF16) return set_err(h, TRD_ENOTIMPL, "BF16 tensor-core path not built");
   h->split = choose_split(h, h->view, k);
   const Split& sp = h->split;
-  if (sp.Kp > 112 && is_fp64(h)) return set_err(h, TRD_ENOTIMPL, "FP64 path supports r_1 r_c <= 112");
-  if (sp.Kp > 256) return set_err(h, TRD_ENOTIMPL, "data passes support r_1 r_c <= 256");
-  TRY(build_merged(h, k, false));
-  int splits = choose_splits(h, sp);
-  const int64_t gx = (sp.P_stat + 63) / 64;
-  TRY(ensure(h, h->Tpart, elt(h) * (size_t)splits * sp.P_stat * sp.Kp));
-  TRY(ensure(h, h->stat_part, sizeof(double) * 8 * (size_t)(gx * splits)));
-  TRY(ensure(h, h->Tsum, sizeof(double) * (size_t)sp.P_stat * sp.Kp));
-  int ctas = 0, used = 0;
-  PassArgs a = pass_args(h);
-  CK(launch_pass_simt(a, is_fp64(h), sp.rows, false, splits, &ctas, &used, h->stream), "data pass 1");
-  h->splits = used;
-  h->ctas = ctas;
-  CK(launch_reduce_T(h->Tpart.p, is_fp64(h), used, sp.P_stat * (int64_t)sp.Kp, (double*)h->Tsum.p,
-                     h->stream), "reduce contraction");
-  CK(launch_reduce_stats((const double*)h->stat_part.p, ctas, (double*)h->stat_sum.p, h->dstatus,
-                         h->stream), "reduce statistics");
+  if (h->prec == TRD_BF16) {
+    TRY(run_pass1_tc(h, k));
+  } else {
+    if (sp.Kp > 112 && is_fp64(h)) return set_err(h, TRD_ENOTIMPL, "FP64 path supports r_1 r_c <= 112");
+    if (sp.Kp > 256) return set_err(h, TRD_ENOTIMPL, "data passes support r_1 r_c <= 256");
+    TRY(build_merged(h, k, false));
+    int splits = choose_splits(h, sp);
+    const int64_t gx = (sp.P_stat + 63) / 64;
+    TRY(ensure(h, h->Tpart, elt(h) * (size_t)splits * sp.P_stat * sp.Kp));
+    TRY(ensure(h, h->stat_part, sizeof(double) * 8 * (size_t)(gx * splits)));
+    TRY(ensure(h, h->Tsum, sizeof(double) * (size_t)sp.P_stat * sp.Kp));
+    int ctas = 0, used = 0;
+    PassArgs a = pass_args(h);
+    prof_begin(h);
+    CK(launch_pass_simt(a, is_fp64(h), sp.rows, false, splits, &ctas, &used, h->stream), "data pass 1");
+    prof_end(h, 0);
+    h->splits = used;
+    h->ctas = ctas;
+    CK(launch_reduce_T(h->Tpart.p, is_fp64(h), used, sp.P_stat * (int64_t)sp.Kp, (double*)h->Tsum.p,
+                       h->stream), "reduce contraction");
+    CK(launch_reduce_stats((const double*)h->stat_part.p, ctas, (double*)h->stat_sum.p, h->dstatus,
+                           h->stream), "reduce statistics");
+  }
   h->pass1_k = k;
   h->grad_k = -1;
   h->slots_last = h->view.numel;
@@ -387,12 +531,16 @@ trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int
   }
   CK(launch_dot(d, hh, n, h->scal + S_NUM, h->stream), "<d,h>");
   double* den = h->scal + S_DEN;
-  if (eta_fixed <= 0) {
+  if (eta_fixed <= 0 && h->prec == TRD_BF16) {
+    TRY(run_pass2_tc(h, k, &den));
+  } else if (eta_fixed <= 0) {
     TRY(build_merged(h, k, true));
     int ctas = 0, used = 0;
     PassArgs a = pass_args(h);
+    prof_begin(h);
     CK(launch_pass_simt(a, is_fp64(h), h->split.rows, true, h->splits, &ctas, &used, h->stream),
        "data pass 2");
+    prof_end(h, 1);
     double* s2 = (double*)X_(h)->stat_sum2.p;
     CK(launch_reduce_stats((const double*)h->stat_part.p, ctas, s2, h->dstatus, h->stream), "reduce den");
     den = s2 + 6;
@@ -679,6 +827,9 @@ void trd_destroy(trd_t* h) {
   DevBuf* xb[] = {&x->meta, &x->stat_sum2, &x->Gloc, &x->recA, &x->recC, &x->errp, &x->probe_xsq};
   for (DevBuf* b : xb) free_buf(*b);
   for (int k = 0; k < kMaxN; ++k) { free_buf(x->Eloc[k]); free_buf(x->tmpZ[k]); }
+  for (auto& p : x->pending) { x->ev_pool.push_back(p.a); x->ev_pool.push_back(p.b); }
+  if (x->ev_open) x->ev_pool.push_back(x->ev_open);
+  for (cudaEvent_t e : x->ev_pool) cudaEventDestroy(e);
   if (h->scal) cudaFree(h->scal);
   if (h->dstatus) cudaFree(h->dstatus);
   if (h->report_dev) cudaFree(h->report_dev);
@@ -917,6 +1068,7 @@ trd_status trd_step(trd_t* h, const trd_params* p, trd_report* rep) {
   CK(cudaMemcpyAsync(h->host_pinned, h->report_dev, sizeof(double) * 32, cudaMemcpyDeviceToHost, h->stream),
      "report");
   trd_status st = sync_and_status(h);
+  prof_harvest(h);
   h->t += 1;
   if (rep) {
     memset(rep, 0, sizeof(*rep));
@@ -986,5 +1138,30 @@ trd_status trd_recovery_error(trd_t* h, const float* ref, double* err) {
   if (!ref || !err) return set_err(h, TRD_EINVAL, "NULL argument");
   return reconstruct_impl(h, nullptr, nullptr, ref, err);
 }
+
+trd_status trd_set_profiling(trd_t* h, int on) {
+  TRY(check_handle(h));
+  X_(h)->prof = on != 0;
+  return TRD_OK;
+}
+
+trd_status trd_get_profile(trd_t* h, int reset, double* out) {
+  TRY(check_handle(h));
+  if (!out) return set_err(h, TRD_EINVAL, "NULL output");
+  CK(cudaStreamSynchronize(h->stream), "stream synchronize");
+  prof_harvest(h);
+  Extra* x = X_(h);
+  out[0] = x->prof_ms[0];
+  out[1] = (double)x->prof_n[0];
+  out[2] = x->prof_ms[1];
+  out[3] = (double)x->prof_n[1];
+  if (reset) {
+    x->prof_ms[0] = x->prof_ms[1] = 0;
+    x->prof_n[0] = x->prof_n[1] = 0;
+  }
+  return TRD_OK;
+}
+
+int64_t trd_kernel_launches(void) { return launches_total(); }
 
 }  // extern "C"

@@ -31,6 +31,7 @@ cudaError_t launch_fgmc_E(const double* Z, const int32_t* idx, int64_t n, int rk
   const int64_t tot = (int64_t)rk * rk * rk1 * rk1;
   const unsigned blocks = (unsigned)imin((tot + 127) / 128, 4096);
   k_fgmc_E<<<blocks, 128, 0, st>>>(Z, idx, n, rk, rk1, E);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -60,6 +61,7 @@ cudaError_t launch_dgemm(const double* A, const double* B, double* C, int M, int
                          bool transB, cudaStream_t st) {
   dim3 grid((N + 15) / 16, (M + 15) / 16), block(16, 16);
   k_dgemm<<<grid, block, 0, st>>>(A, B, C, M, N, K, transB ? 1 : 0);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -78,6 +80,7 @@ __global__ void k_phi(const double* __restrict__ T, int p, int q, double* __rest
 cudaError_t launch_phi(const double* T, int p, int q, double* G, cudaStream_t st) {
   const int K = p * q;
   k_phi<<<(K * K + 255) / 256, 256, 0, st>>>(T, p, q, G);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -144,6 +147,7 @@ cudaError_t launch_cholesky(const double* G, int K, double lambda, double* L, do
   const bool sm = bytes <= 200 * 1024;
   if (sm) cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   k_cholesky<<<1, 1024, sm ? bytes : 0, st>>>(G, K, lambda, L, scal, dstatus, sm ? 1 : 0);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -184,6 +188,7 @@ cudaError_t launch_solve_rows(const double* L, const double* d, double* h, int K
     cudaFuncSetAttribute(k_solve_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const unsigned blocks = (unsigned)imin((rows + warps - 1) / warps, 4096);
   k_solve_rows<<<blocks, warps * 32, smem, st>>>(L, d, h, K, rows);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -204,6 +209,7 @@ __global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b
 
 cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* out, cudaStream_t st) {
   k_dot<<<1, 256, 0, st>>>(a, b, n, out);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -231,6 +237,7 @@ __global__ void k_eta(const double* num, const double* den, double fixed_eta, in
 cudaError_t launch_eta(const double* num, const double* den, double fixed_eta, int* dstatus,
                        double* eta, double* eta_slot, cudaStream_t st) {
   k_eta<<<1, 1, 0, st>>>(num, den, fixed_eta, dstatus, eta, eta_slot);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -247,6 +254,7 @@ __global__ void k_axpy_core(double* __restrict__ Z, const double* __restrict__ h
 cudaError_t launch_axpy_core(double* Z, const double* h, int64_t n, const double* eta,
                              cudaStream_t st) {
   k_axpy_core<<<(unsigned)imin((n + 255) / 256, 4096), 256, 0, st>>>(Z, h, n, eta);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -278,6 +286,7 @@ __global__ void k_stop_error(const double* __restrict__ D, double* __restrict__ 
 cudaError_t launch_stop_error(const double* D, double* Dprev, int64_t n, double* e_out,
                               cudaStream_t st) {
   k_stop_error<<<1, 256, 0, st>>>(D, Dprev, n, e_out);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -79,10 +79,12 @@ cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool trans
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_chain<double><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (double*)out, transposed, ld, cap);
+    note_launch();
   } else {
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_chain<float><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (float*)out, transposed, ld, cap);
+    note_launch();
   }
   return cudaGetLastError();
 }
@@ -178,10 +180,12 @@ cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int 
   double* target = nsplit == 1 ? d : dpart;
   k_backcontract<<<grid, threads, 0, st>>>((const double*)Tsum_d, Kp, rows_case ? 1 : 0, mr, mc,
                                            pre, n_pre, post, n_post, Ik, rk, rk1, per, target);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || nsplit == 1) return e;
   const int64_t n = Ik * rk * rk1;
   k_sum_splits<<<(unsigned)imin((n + 255) / 256, 4096), 256, 0, st>>>(dpart, nsplit, n, d);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -201,6 +205,7 @@ cudaError_t launch_reduce_T(const void* Tpart, bool is_double, int splits, int64
   const unsigned blocks = (unsigned)imin((n + 255) / 256, 8192);
   if (is_double) k_reduce_T<double><<<blocks, 256, 0, st>>>((const double*)Tpart, splits, n, Tsum);
   else k_reduce_T<float><<<blocks, 256, 0, st>>>((const float*)Tpart, splits, n, Tsum);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -225,6 +230,7 @@ __global__ void k_reduce_stats(const double* __restrict__ part, int ctas, double
 cudaError_t launch_reduce_stats(const double* stat_part, int ctas, double* stat_sum,
                                 int* /*dstatus*/, cudaStream_t st) {
   k_reduce_stats<<<1, 256, 0, st>>>(stat_part, ctas, stat_sum);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -272,6 +278,7 @@ cudaError_t launch_reconstruct_mats(const double* A, const double* C, int64_t P_
                                     int Kp, const float* Xref, float* out, double* err_part,
                                     int parts, cudaStream_t st) {
   k_reconstruct<<<parts, 256, 0, st>>>(A, C, P_in, P_out, Kp, Xref, out, err_part);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -334,6 +341,7 @@ cudaError_t launch_gather(const float* X, const uint32_t* M, int N, const int64_
   }
   const unsigned blocks = (unsigned)imin((g.words + 7) / 8, 152 * 32);
   k_gather<<<blocks, 256, 0, st>>>(g);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -342,6 +350,7 @@ __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
 cudaError_t launch_set_scalar(double* p, double v, cudaStream_t st) {
   k_set_scalar<<<1, 1, 0, st>>>(p, v);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -376,6 +385,7 @@ cudaError_t launch_to_bf16_split(const void* src, bool src_double, int64_t rows,
     k_to_bf16_split<double><<<blocks, 256, 0, st>>>((const double*)src, rows, Kp, ld_src, hi, lo, hiT, ldT, ld_dst);
   else
     k_to_bf16_split<float><<<blocks, 256, 0, st>>>((const float*)src, rows, Kp, ld_src, hi, lo, hiT, ldT, ld_dst);
+  note_launch();
   return cudaGetLastError();
 }
 

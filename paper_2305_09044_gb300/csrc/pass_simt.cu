@@ -185,6 +185,7 @@ cudaError_t launch_kj(const PassArgs& a, bool rows, bool pass2, dim3 grid, cudaS
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<grid, NT, smem, st>>>(a);
+    note_launch();
     return cudaGetLastError();
   };
   if (rows) return pass2 ? go(k_pass_simt<T, KJ, true, true>) : go(k_pass_simt<T, KJ, true, false>);

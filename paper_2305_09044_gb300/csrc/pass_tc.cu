@@ -1,0 +1,710 @@
+// Fused data passes on the 5th-generation tensor cores (BF16 path), sm_103a.
+//
+// Same contraction as the CUDA-core passes (X_hat = S_st S_str^T, row kappa = gamma r_c +
+// delta of the merged subchains), mapped onto tcgen05:
+//   GEMM 1  D1[m][n]   = sum_k S_st[m][k] S_str[n][k]      (split BF16: hi*hi + hi*lo + lo*hi,
+//                                                           FP32 accumulation in TMEM)
+//   epilogue (FP32)    e = x - x_hat, w = exp(-e^2 / 2 sigma^2), y = w e on observed slots
+//   GEMM 2  T[m][k]   += sum_n Y[m][n] S_str[n][k]          (BF16 Y and S_str, FP32 in TMEM)
+// Pass 2 replaces GEMM 2 by D2 = S_h S_str^T (BF16) and reduces den = sum w D2^2.
+//
+// Work split: the stationary index (128 rows per block, the UMMA M) times the streaming
+// tiles (64 columns) form units; CTA c of G (one per SM) takes the contiguous unit range
+// [cU/G, (c+1)U/G), which may span several stationary blocks ("segments").  Each segment's
+// partial contraction goes to slot c + rb of a partial buffer; a fixed-order reduction adds
+// the slots, so results are deterministic.
+//
+// Warp roles (192 threads): warp 0 TMA producer, warp 1 TMEM allocator + single-thread MMA
+// issuer, warps 2..5 epilogue (TMEM lane quarter = warp % 4).  Tiles move by TMA
+// (cp.async.bulk.tensor) into 1024-byte aligned SWIZZLE_128B operand buffers; every mbarrier
+// wait is bounded: a wait that runs out sets an error word, all roles drain and the kernel
+// returns after freeing its TMEM.
+#include <cuda.h>
+
+#include "trd_internal.cuh"
+
+namespace trd {
+
+namespace tc {
+
+constexpr int BM = 128;        // UMMA M: stationary rows per block
+constexpr int BN = 64;         // streaming columns per tile
+constexpr int KPAD = 64;       // padded contraction length (one 128-byte swizzle atom)
+constexpr int STAGES = 3;
+constexpr int NTHREADS = 192;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;
+
+// shared-memory carve-up (bytes, every buffer 1024-aligned)
+constexpr int S_TILE = BM * KPAD * 2;          // 16 KB: one stationary operand
+constexpr int X_TILE = BN * BM * 4;            // 32 KB: one data tile
+constexpr int T_TILE = BN * KPAD * 2;          // 8 KB: one streaming operand
+constexpr int TT_TILE = KPAD * BN * 2;         // 8 KB: streaming operand, transposed
+constexpr int M_TILE = 1024;                   // mask words of one tile (ROWS: 64 x 4 words)
+constexpr int Y_TILE = BM * BN * 2;            // 16 KB: weighted residuals (A of GEMM 2)
+
+struct Layout {
+  int s_hi, s_lo, s_h, stage0, stage_bytes, x_off, thi_off, tlo_off, tt_off, m_off, y, bars, total;
+};
+
+__host__ __device__ constexpr Layout layout(bool pass2) {
+  Layout L{};
+  int o = 0;
+  L.s_hi = o; o += S_TILE;
+  L.s_lo = o; o += S_TILE;
+  L.s_h = o; if (pass2) o += S_TILE;
+  L.stage0 = o;
+  L.x_off = 0;
+  L.thi_off = X_TILE;
+  L.tlo_off = X_TILE + T_TILE;
+  L.tt_off = X_TILE + 2 * T_TILE;
+  L.m_off = X_TILE + 2 * T_TILE + (pass2 ? 0 : TT_TILE);
+  L.stage_bytes = L.m_off + M_TILE;
+  o += STAGES * L.stage_bytes;
+  L.y = o; if (!pass2) o += Y_TILE;
+  L.bars = o; o += 1024;
+  L.total = o;
+  return L;
+}
+
+struct Params {
+  int64_t P_in, P_stat, P_strm;
+  int Kp;                    // valid contraction columns (<= KPAD)
+  int64_t RB, NT, U;         // stationary blocks, streaming tiles, units
+  int G;                     // CTAs
+  const uint32_t* Mrows;     // COLS case: padded mask rows [P_out][W] (direct loads)
+  int64_t W;                 // words per padded mask row
+  const double* sigma;
+  float* Tpart;              // [G + RB][BM][Kp]
+  double* stat_part;         // [G][8]
+  int* err;                  // device status word
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false (and the abort flag set) when the limit is reached or another role
+// has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+    if (mbar_try(b, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          su32(dst)),
+      "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// UMMA shared-memory descriptor: K-major, SWIZZLE_128B (8-row groups 1024 B apart).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  return d;
+}
+// Instruction descriptor, kind::f16: D FP32, A/B BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// ------------------------------------------------------------------ the kernel
+template <bool ROWS, bool PASS2>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_pass_tc(const __grid_constant__ CUtensorMap mS_hi, const __grid_constant__ CUtensorMap mS_lo,
+              const __grid_constant__ CUtensorMap mS_h, const __grid_constant__ CUtensorMap mT_hi,
+              const __grid_constant__ CUtensorMap mT_lo, const __grid_constant__ CUtensorMap mTT,
+              const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mM,
+              const Params p) {
+  constexpr Layout L = layout(PASS2);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // align the dynamic window to 1024 bytes (the launcher over-allocates by 1 KB)
+  unsigned char* sm = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);
+  uint64_t* full = bars;                  // [STAGES]
+  uint64_t* empty = bars + STAGES;        // [STAGES]
+  uint64_t* d_full = bars + 2 * STAGES;   // [2]
+  uint64_t* d_empty = d_full + 2;         // [2]
+  uint64_t* y_full = d_empty + 2;
+  uint64_t* y_empty = y_full + 1;
+  uint64_t* s_full = y_empty + 1;
+  uint64_t* s_empty = s_full + 1;
+  uint64_t* acc_full = s_empty + 1;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* mma_done = acc_empty + 1;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(mma_done + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 2);
+  double* red = reinterpret_cast<double*>(mma_done + 4);   // [4 warps][8] statistics
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = blockIdx.x;
+  const int64_t u_begin = c * p.U / p.G, u_end = (c + 1) * p.U / p.G;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1 + 128);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&d_full[b], 1);
+      mbar_init(&d_empty[b], 128);
+    }
+    mbar_init(y_full, 128);
+    mbar_init(y_empty, 1);
+    mbar_init(s_full, 1);
+    mbar_init(s_empty, 1);
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 128);
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  constexpr uint32_t TMEM_COLS = 256;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // TMEM columns: D1[b] at b*BN, D2[b] (pass 2) at 2*BN + b*BN, T accumulator at 2*BN
+  const uint32_t col_d1[2] = {0u, (uint32_t)BN};
+  const uint32_t col_d2[2] = {2u * BN, 3u * BN};
+  const uint32_t col_acc = 2u * BN;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      int64_t it = 0;
+      int g = 0;
+      bool ok = true;
+      int last_phase[STAGES];
+      for (int s = 0; s < STAGES; ++s) last_phase[s] = -1;
+      int s_phase = -1;
+      for (int64_t u = u_begin; u < u_end && ok; ++g) {
+        const int64_t rb = u / p.NT;
+        const int64_t seg_end = imin(u_end, (rb + 1) * p.NT);
+        if (g > 0) ok = mbar_wait(s_empty, (uint32_t)((g - 1) & 1), abort_flag);
+        if (!ok) break;
+        mbar_expect_tx(s_full, (PASS2 ? 3 : 2) * S_TILE);
+        s_phase = g & 1;
+        tma_2d(sm + L.s_hi, &mS_hi, s_full, 0, (int)(rb * BM));
+        tma_2d(sm + L.s_lo, &mS_lo, s_full, 0, (int)(rb * BM));
+        if (PASS2) tma_2d(sm + L.s_h, &mS_h, s_full, 0, (int)(rb * BM));
+        for (; u < seg_end; ++u, ++it) {
+          const int s = (int)(it % STAGES);
+          if (!mbar_wait(&empty[s], (uint32_t)(((it / STAGES) & 1) ^ 1), abort_flag)) { ok = false; break; }
+          const int t0 = (int)((u % p.NT) * BN);
+          unsigned char* st = sm + L.stage0 + s * L.stage_bytes;
+          uint32_t bytes = X_TILE + 2 * T_TILE + (PASS2 ? 0 : TT_TILE) + (ROWS ? BN * 16 : 0);
+          mbar_expect_tx(&full[s], bytes);
+          last_phase[s] = (int)((it / STAGES) & 1);
+          tma_2d(st + L.thi_off, &mT_hi, &full[s], 0, t0);
+          tma_2d(st + L.tlo_off, &mT_lo, &full[s], 0, t0);
+          if (!PASS2) tma_2d(st + L.tt_off, &mTT, &full[s], t0, 0);
+          if (ROWS) {
+            tma_2d(st + L.x_off, &mX, &full[s], (int)(rb * BM), t0);
+            tma_2d(st + L.m_off, &mM, &full[s], (int)(rb * BM / 32), t0);
+          } else {
+            tma_2d(st + L.x_off, &mX, &full[s], t0, (int)(rb * BM));
+            tma_2d(st + L.x_off + X_TILE / 2, &mX, &full[s], t0 + 32, (int)(rb * BM));
+          }
+        }
+      }
+      if (!ok) {
+        // drain: wait (bounded) for the last copies issued into every buffer
+        for (int s = 0; s < STAGES; ++s)
+          if (last_phase[s] >= 0)
+            for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+              if (mbar_try(&full[s], (uint32_t)last_phase[s])) break;
+        if (s_phase >= 0)
+          for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+            if (mbar_try(s_full, (uint32_t)s_phase)) break;
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t ID1 = idesc_bf16(BM, BN);
+      constexpr uint32_t ID2 = idesc_bf16(BM, KPAD);
+      const uint32_t a_hi = su32(sm + L.s_hi), a_lo = su32(sm + L.s_lo), a_h = su32(sm + L.s_h);
+      const uint32_t ybuf = su32(sm + L.y);
+      int64_t it = 0;
+      int g = 0;
+      bool ok = true;
+      for (int64_t u = u_begin; u < u_end && ok; ++g) {
+        const int64_t rb = u / p.NT;
+        const int64_t seg_end = imin(u_end, (rb + 1) * p.NT);
+        if (!mbar_wait(s_full, (uint32_t)(g & 1), abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        int64_t prev = -1;        // tile whose GEMM 2 is pending
+        bool first2 = true;
+        for (; u < seg_end; ++u, ++it) {
+          const int s = (int)(it % STAGES), b = (int)(it & 1);
+          if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&d_empty[b], (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t st = su32(sm + L.stage0 + s * L.stage_bytes);
+          const uint32_t b_hi = st + L.thi_off, b_lo = st + L.tlo_off;
+          for (int kk = 0; kk < KPAD / 16; ++kk) {
+            const uint32_t ko = kk * 32;
+            tc_mma(tmem + col_d1[b], sdesc(a_hi + ko), sdesc(b_hi + ko), ID1, kk > 0);
+            tc_mma(tmem + col_d1[b], sdesc(a_hi + ko), sdesc(b_lo + ko), ID1, 1);
+            tc_mma(tmem + col_d1[b], sdesc(a_lo + ko), sdesc(b_hi + ko), ID1, 1);
+            if (PASS2) tc_mma(tmem + col_d2[b], sdesc(a_h + ko), sdesc(b_hi + ko), ID1, kk > 0);
+          }
+          tc_commit(&d_full[b]);
+          if (PASS2) {
+            tc_commit(&empty[s]);
+            continue;
+          }
+          if (prev >= 0) {
+            // GEMM 2 of the previous tile: T += Y * S_str (B = transposed streaming tile)
+            if (first2) {
+              if (g > 0 && !mbar_wait(acc_empty, (uint32_t)((g - 1) & 1), abort_flag)) { ok = false; break; }
+            }
+            if (!mbar_wait(y_full, (uint32_t)(prev & 1), abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const int sp = (int)(prev % STAGES);
+            const uint32_t tt = su32(sm + L.stage0 + sp * L.stage_bytes + L.tt_off);
+            for (int kk = 0; kk < BN / 16; ++kk)
+              tc_mma(tmem + col_acc, sdesc(ybuf + kk * 32), sdesc(tt + kk * 32), ID2, (first2 && kk == 0) ? 0u : 1u);
+            first2 = false;
+            tc_commit(y_empty);
+            tc_commit(&empty[sp]);
+          }
+          prev = it;
+        }
+        if (!ok) break;
+        if (!PASS2 && prev >= 0) {
+          if (first2 && g > 0 && !mbar_wait(acc_empty, (uint32_t)((g - 1) & 1), abort_flag)) { ok = false; break; }
+          if (!mbar_wait(y_full, (uint32_t)(prev & 1), abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const int sp = (int)(prev % STAGES);
+          const uint32_t tt = su32(sm + L.stage0 + sp * L.stage_bytes + L.tt_off);
+          for (int kk = 0; kk < BN / 16; ++kk)
+            tc_mma(tmem + col_acc, sdesc(ybuf + kk * 32), sdesc(tt + kk * 32), ID2, (first2 && kk == 0) ? 0u : 1u);
+          tc_commit(y_empty);
+          tc_commit(&empty[sp]);
+          tc_commit(acc_full);
+        }
+        tc_commit(s_empty);
+      }
+      // every issued MMA has finished before TMEM can be released
+      tc_commit(mma_done);
+      for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try(mma_done, 0)) break;
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue (128 threads)
+    const int q = warp & 3;                 // TMEM lane quarter of this warp
+    const int row = q * 32 + lane;          // stationary row within the block
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const double sg = *p.sigma;
+    // exp(-e^2 / (2 sigma^2)) = exp2(-e^2 * k), k = log2(e) / (2 sigma^2); sigma = inf -> k = 0
+    const float kexp = isinf(sg) ? 0.0f : (float)(1.4426950408889634 / (2.0 * sg * sg));
+    float sw = 0.f, se2 = 0.f, swe2 = 0.f, sden = 0.f;
+    uint32_t nobs = 0, nnf = 0, nslot = 0;
+    int64_t it = 0;
+    int g = 0;
+    bool ok = true;
+    for (int64_t u = u_begin; u < u_end && ok; ++g) {
+      const int64_t rb = u / p.NT;
+      const int64_t seg_end = imin(u_end, (rb + 1) * p.NT);
+      const int64_t srow = rb * BM + row;
+      const bool row_ok = srow < p.P_stat;
+      for (; u < seg_end; ++u, ++it) {
+        const int s = (int)(it % STAGES), b = (int)(it & 1);
+        const int64_t t0 = (u % p.NT) * BN;
+        if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), abort_flag)) { ok = false; break; }
+        if (!mbar_wait(&d_full[b], (uint32_t)((it >> 1) & 1), abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const unsigned char* st = sm + L.stage0 + s * L.stage_bytes;
+        const float* sx = reinterpret_cast<const float*>(st + L.x_off);
+        const uint32_t* smk = reinterpret_cast<const uint32_t*>(st + L.m_off);
+        uint2 mrow = make_uint2(0u, 0u);
+        if (!ROWS && row_ok) {
+          const uint32_t* mp = p.Mrows + srow * p.W + (t0 >> 5);
+          mrow = *reinterpret_cast<const uint2*>(mp);
+        }
+        uint32_t ypk[BN / 2];
+#pragma unroll
+        for (int h = 0; h < BN / 32; ++h) {
+          float xh[32], dh[32];
+          tmem_ld32(tmem + lane_base + col_d1[b] + h * 32, xh);
+          if (PASS2) tmem_ld32(tmem + lane_base + col_d2[b] + h * 32, dh);
+          float xv[32];
+          if (ROWS) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) xv[j] = sx[(h * 32 + j) * BM + row];
+          } else {
+            // two SWIZZLE_128B boxes of 32 columns; 16-byte chunk c of row r sits at chunk c ^ (r & 7)
+            const unsigned char* box = st + L.x_off + h * (X_TILE / 2) + row * 128;
+#pragma unroll
+            for (int c4 = 0; c4 < 8; ++c4) {
+              const float4 v = *reinterpret_cast<const float4*>(box + ((c4 ^ (row & 7)) << 4));
+              xv[4 * c4 + 0] = v.x; xv[4 * c4 + 1] = v.y; xv[4 * c4 + 2] = v.z; xv[4 * c4 + 3] = v.w;
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = h * 32 + j;
+            bool obs;
+            if (ROWS) obs = (smk[col * 4 + q] >> lane) & 1u;
+            else obs = ((h == 0 ? mrow.x : mrow.y) >> j) & 1u;
+            const bool valid = row_ok && (t0 + col < p.P_strm);
+            float y = 0.f;
+            if (valid) {
+              nslot += 1;
+              if (obs) {
+                nobs += 1;
+                const float e = xv[j] - xh[j];
+                if (isfinite(e)) {
+                  const float w = exp2f(-e * e * kexp);
+                  if (PASS2) {
+                    sden += w * dh[j] * dh[j];
+                  } else {
+                    y = w * e;
+                    sw += w;
+                    se2 += e * e;
+                    swe2 += y * e;
+                  }
+                } else {
+                  nnf += 1;
+                }
+              }
+            }
+            if (!PASS2) xv[j] = y;
+          }
+          if (!PASS2) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) ypk[(h * 32 + j) >> 1] = pack_bf16(xv[j], xv[j + 1]);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&d_empty[b]);
+        mbar_arrive(&empty[s]);
+        if (!PASS2) {
+          if (!mbar_wait(y_empty, (uint32_t)((it & 1) ^ 1), abort_flag)) { ok = false; break; }
+          unsigned char* yrow = sm + L.y + row * 128;
+#pragma unroll
+          for (int c8 = 0; c8 < 8; ++c8) {
+            const uint4 v = make_uint4(ypk[4 * c8], ypk[4 * c8 + 1], ypk[4 * c8 + 2], ypk[4 * c8 + 3]);
+            *reinterpret_cast<uint4*>(yrow + ((c8 ^ (row & 7)) << 4)) = v;
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(y_full);
+        }
+      }
+      if (!ok) break;
+      if (!PASS2) {
+        // drain the segment's contraction: row `row` of T (Kp valid columns) -> partial slot c + rb
+        if (!mbar_wait(acc_full, (uint32_t)(g & 1), abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        float* dst = p.Tpart + ((c + rb) * BM + row) * (int64_t)p.Kp;
+#pragma unroll
+        for (int h = 0; h < KPAD / 32; ++h) {
+          float v[32];
+          tmem_ld32(tmem + lane_base + col_acc + h * 32, v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (h * 32 + j < p.Kp) dst[h * 32 + j] = row_ok ? v[j] : 0.f;
+        }
+        tc_fence_before();
+        mbar_arrive(acc_empty);
+      }
+    }
+    // statistics: warp shuffle, then one row per CTA (fixed order)
+    const double fv[7] = {(double)sw, (double)se2, (double)swe2, (double)nobs, (double)nnf, (double)nslot,
+                          (double)sden};
+#pragma unroll
+    for (int f = 0; f < 7; ++f) {
+      double x = fv[f];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) red[q * 8 + f] = x;
+    }
+  }
+  // ------------------------------------------------------------------ teardown
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int f = 0; f < 7; ++f) {
+      double x = 0.0;
+      for (int w = 0; w < 4; ++w) x += red[w * 8 + f];
+      p.stat_part[c * 8 + f] = x;
+    }
+    p.stat_part[c * 8 + 7] = 0.0;
+    if (*abort_flag) atomicOr(p.err, (int)DEV_TIMEOUT);
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ operand preparation
+// BF16 hi/lo split of a merged matrix [rows][Kp] (float) into [rows][KPAD] (zero padded),
+// plus, for the streaming side, the transposed hi part [KPAD][ldT] (zero padded).
+__global__ void k_split_rows(const float* __restrict__ src, int64_t rows, int Kp, __nv_bfloat16* __restrict__ hi,
+                             __nv_bfloat16* __restrict__ lo) {
+  const int64_t n = rows * KPAD;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / KPAD;
+    const int k = (int)(e % KPAD);
+    const float v = k < Kp ? src[r * Kp + k] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[e] = h;
+    if (lo) lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+__global__ void k_transpose_hi(const float* __restrict__ src, int64_t rows, int Kp, int64_t ldT,
+                               __nv_bfloat16* __restrict__ dst) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int k0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i;
+    const int k = k0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < rows && k < Kp) ? src[r * Kp + k] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int k = k0 + i;
+    const int64_t r = r0 + threadIdx.x;
+    if (k < KPAD && r < ldT) dst[(int64_t)k * ldT + r] = __float2bfloat16_rn(tile[threadIdx.x][i]);
+  }
+}
+
+// Padded mask rows: Mrows[b][w] = bits [P_in b + 32 w, P_in b + 32 w + 32) of the packed mask
+// (bits at or beyond P_in are zero).
+__global__ void k_mask_rows(const uint32_t* __restrict__ M, int64_t P_in, int64_t P_out, int64_t W,
+                            uint32_t* __restrict__ out) {
+  const int64_t n = P_out * W;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / W, w = e % W;
+    const int64_t a0 = 32 * w;
+    uint32_t v = 0;
+    if (a0 < P_in) {
+      if (!M) {
+        const int64_t nb = imin(32, P_in - a0);
+        v = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
+      } else {
+        const int64_t bit = P_in * b + a0;
+        const int64_t wd = bit >> 5;
+        const int sh = (int)(bit & 31);
+        const int64_t nwords = (P_in * P_out + 31) / 32;
+        const uint64_t lo = M[wd];
+        const uint64_t hi = (sh && wd + 1 < nwords) ? (uint64_t)M[wd + 1] : 0ull;
+        v = (uint32_t)(((hi << 32) | lo) >> sh);
+        const int64_t nb = imin(32, P_in - a0);
+        if (nb < 32) v &= (1u << nb) - 1u;
+      }
+    }
+    out[e] = v;
+  }
+}
+
+__global__ void k_reduce_slots(const float* __restrict__ part, int64_t RB, int64_t NT, int G, int64_t P_stat,
+                               int Kp, double* __restrict__ out) {
+  const int64_t U = RB * NT;
+  const int64_t n = P_stat * Kp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t srow = e / Kp;
+    const int k = (int)(e % Kp);
+    const int64_t rb = srow / BM, r = srow % BM;
+    const int64_t ulo = rb * NT, uhi = (rb + 1) * NT;
+    // CTAs whose unit range [cU/G, (c+1)U/G) meets [ulo, uhi)
+    int64_t c0 = (ulo * G) / U;
+    while (c0 > 0 && (c0 * U) / G > ulo) --c0;
+    while (((c0 + 1) * U) / G <= ulo) ++c0;
+    double s = 0.0;
+    for (int64_t cc = c0; cc < G && (cc * U) / G < uhi; ++cc) s += (double)part[((cc + rb) * BM + r) * Kp + k];
+    out[e] = s;
+  }
+}
+
+}  // namespace tc
+
+// ------------------------------------------------------------------ host side
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, CUtensorMapDataType dt, int esize, const void* base, uint64_t inner, uint64_t outer,
+              uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle sw) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {row_bytes};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t es[2] = {1, 1};
+  (void)esize;
+  return fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+int tc_kpad() { return tc::KPAD; }
+int tc_bm() { return tc::BM; }
+int tc_bn() { return tc::BN; }
+
+cudaError_t launch_tc_prep(const float* src, int64_t rows, int Kp, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                           __nv_bfloat16* hiT, int64_t ldT, cudaStream_t st) {
+  const int64_t n = rows * tc::KPAD;
+  tc::k_split_rows<<<(unsigned)imin((n + 255) / 256, 8192), 256, 0, st>>>(src, rows, Kp, hi, lo);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !hiT) return e;
+  dim3 grid((unsigned)((ldT + 31) / 32), (unsigned)((tc::KPAD + 31) / 32)), block(32, 8);
+  tc::k_transpose_hi<<<grid, block, 0, st>>>(src, rows, Kp, ldT, hiT);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask_rows(const uint32_t* M, int64_t P_in, int64_t P_out, int64_t W, uint32_t* out,
+                             cudaStream_t st) {
+  const int64_t n = P_out * W;
+  tc::k_mask_rows<<<(unsigned)imin((n + 255) / 256, 8192), 256, 0, st>>>(M, P_in, P_out, W, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_slots(const float* part, int64_t RB, int64_t NT, int G, int64_t P_stat, int Kp,
+                                double* out, cudaStream_t st) {
+  const int64_t n = P_stat * Kp;
+  tc::k_reduce_slots<<<(unsigned)imin((n + 255) / 256, 8192), 256, 0, st>>>(part, RB, NT, G, P_stat, Kp, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Launch one fused pass.  S operands: [P_stat][KPAD] bf16 (hi, lo, h); streaming: [P_strm][KPAD]
+// (hi, lo) and [KPAD][ldT] (hi transposed); X: [P_out][P_in] floats; Mrows: [P_out][W] words.
+cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi, const __nv_bfloat16* S_lo,
+                           const __nv_bfloat16* S_h, const __nv_bfloat16* T_hi, const __nv_bfloat16* T_lo,
+                           const __nv_bfloat16* TT, int64_t ldT, const float* X, int64_t P_in, int64_t P_out,
+                           const uint32_t* Mrows, int64_t W, int64_t P_stat, int64_t P_strm, int Kp,
+                           const double* sigma, float* Tpart, double* stat_part, int* err, int G,
+                           cudaStream_t st) {
+  using namespace tc;
+  if (Kp > KPAD || (P_in % 4) != 0 || (W % 4) != 0 || (ldT % 64) != 0) return cudaErrorInvalidValue;
+  CUtensorMap mS_hi, mS_lo, mS_h, mT_hi, mT_lo, mTT, mX, mM;
+  const CUtensorMapDataType BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUtensorMapSwizzle SW = CU_TENSOR_MAP_SWIZZLE_128B;
+  bool ok = make_map(&mS_hi, BF, 2, S_hi, KPAD, P_stat, KPAD * 2, 64, BM, SW) &&
+            make_map(&mS_lo, BF, 2, S_lo, KPAD, P_stat, KPAD * 2, 64, BM, SW) &&
+            make_map(&mS_h, BF, 2, pass2 ? S_h : S_hi, KPAD, P_stat, KPAD * 2, 64, BM, SW) &&
+            make_map(&mT_hi, BF, 2, T_hi, KPAD, P_strm, KPAD * 2, 64, BN, SW) &&
+            make_map(&mT_lo, BF, 2, T_lo, KPAD, P_strm, KPAD * 2, 64, BN, SW) &&
+            make_map(&mTT, BF, 2, TT, ldT, KPAD, ldT * 2, 64, KPAD, SW);
+  if (rows_case) {
+    ok = ok && make_map(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, P_in, P_out, P_in * 4, BM, BN,
+                        CU_TENSOR_MAP_SWIZZLE_NONE) &&
+         make_map(&mM, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, Mrows, W, P_out, W * 4, 4, BN, CU_TENSOR_MAP_SWIZZLE_NONE);
+  } else {
+    ok = ok && make_map(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, P_in, P_out, P_in * 4, 32, BM, SW);
+    mM = mX;
+  }
+  if (!ok) return cudaErrorInvalidValue;
+  Params p;
+  p.P_in = P_in;
+  p.P_stat = P_stat;
+  p.P_strm = P_strm;
+  p.Kp = Kp;
+  p.RB = (P_stat + BM - 1) / BM;
+  p.NT = (P_strm + BN - 1) / BN;
+  p.U = p.RB * p.NT;
+  p.G = (int)imin(G, p.U);
+  p.Mrows = Mrows;
+  p.W = W;
+  p.sigma = sigma;
+  p.Tpart = Tpart;
+  p.stat_part = stat_part;
+  p.err = err;
+  const Layout L = layout(pass2);
+  const size_t smem = (size_t)L.total + 1024;
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<p.G, NTHREADS, smem, st>>>(mS_hi, mS_lo, mS_h, mT_hi, mT_lo, mTT, mX, mM, p);
+    note_launch();
+    return cudaGetLastError();
+  };
+  if (rows_case) return pass2 ? go(k_pass_tc<true, true>) : go(k_pass_tc<true, false>);
+  return pass2 ? go(k_pass_tc<false, true>) : go(k_pass_tc<false, false>);
+}
+
+}  // namespace trd

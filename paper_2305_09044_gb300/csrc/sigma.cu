@@ -235,16 +235,24 @@ cudaError_t finish_sigma(const double* vals, const uint64_t* keys, const double*
   const int nb = 256;
   double* parts = work + 64 + 1024;
   k_probe_sums<<<nb, 256, 0, st>>>(vals, keys, xsq, n, nullptr, parts);
+  note_launch();
   k_finish_sums<<<1, 1, 0, st>>>(parts, nb, work, 0);
+  note_launch();
   k_probe_sums<<<nb, 256, 0, st>>>(vals, keys, xsq, n, work + 1, parts);
+  note_launch();
   k_finish_sums<<<1, 1, 0, st>>>(parts, nb, work, 1);
+  note_launch();
   k_select_init<<<1, 1, 0, st>>>(work);
+  note_launch();
   for (int pass = 0; pass < 8; ++pass) {
     const int shift = 56 - 8 * pass;
     k_select_hist<<<(unsigned)imin((n + 255) / 256, 512), 256, 0, st>>>(keys, n, work, shift);
+    note_launch();
     k_select_pick<<<1, 256, 0, st>>>(work, shift);
+    note_launch();
   }
   k_sigma_final<<<1, 1, 0, st>>>(work, rms_override, sigma_prev, sigma_prev_dev, sigma_out);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -264,6 +272,7 @@ cudaError_t launch_probe_sigma(const double* const* Zdev_ptrs, int N, const int6
     k_probe_resid<double><<<blocks, 128, 0, st>>>(Zdev_ptrs, N, dim_dev, R_dev, X, M, numel, full, n, vals, keys, xsq);
   else
     k_probe_resid<float><<<blocks, 128, 0, st>>>(Zdev_ptrs, N, dim_dev, R_dev, X, M, numel, full, n, vals, keys, xsq);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return finish_sigma(vals, keys, xsq, n, -1.0, sigma_prev, sigma_prev_dev, work, sigma_out, st);
@@ -273,6 +282,7 @@ cudaError_t launch_sigma_from_floats(const float* r, int64_t n, double x_obs_rms
                                      double* vals, uint64_t* keys, double* xsq, double* work,
                                      double* sigma_out, cudaStream_t st) {
   k_float_keys<<<(unsigned)imin((n + 255) / 256, 4096), 256, 0, st>>>(r, n, vals, keys, xsq);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return finish_sigma(vals, keys, xsq, n, x_obs_rms, sigma_prev, nullptr, work, sigma_out, st);

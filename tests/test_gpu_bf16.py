@@ -1,0 +1,130 @@
+"""Parity of the tensor-core (tcgen05, BF16) data passes with the FP64 oracle (needs a GB300).
+
+Tolerance: 5e-3 relative (Frobenius) per step for d, eta and the core change.  Shapes keep
+r_1 r_c <= 64 and an inner block size that is a multiple of 4 (the path's limits) while
+leaving every tile ragged (no size is a multiple of the 128 x 64 tile).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import trd_oracle as O
+
+from .helpers import flat, problem, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL = 5e-3
+
+SHAPES = [
+    ((48, 40, 36, 32), (8, 8, 8, 8)),       # K' = 64, 1920 x 1152
+    ((52, 44, 30, 28), (4, 3, 4, 2)),       # small ranks, 2288 x 840
+    ((64, 40, 36), (8, 8, 8)),              # order 3: 64 x 1440 (one ragged stationary block)
+    ((20, 16, 12, 10, 9), (2, 3, 2, 2, 3)), # order 5: 320 x 1080
+]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_09044_gb300 import build
+    build.build()
+    return torch
+
+
+def _make(torch, dims, ranks, missing=0.3, outliers=0.1, seed=5):
+    from paper_2305_09044_gb300 import TRD
+    X, P, words, truth, Xt = problem(dims, ranks, missing, outliers, seed)
+    t = TRD(dims, ranks, "bf16")
+    Xd = torch.from_numpy(flat(X)).cuda()
+    Md = torch.from_numpy(words.view(np.int32)).cuda()
+    t.set_data(Xd, Md)
+    return t, X, P, Xt, (Xd, Md)
+
+
+@pytest.mark.parametrize("dims,ranks", SHAPES)
+def test_bf16_core_step_parity(torch_cuda, dims, ranks):
+    t, X, P, Xt, keep = _make(torch_cuda, dims, ranks)
+    cores = O.init_cores(dims, ranks, seed=11)
+    sigma = 1.3
+    for k in range(len(dims)):
+        t.set_cores(cores)
+        st = O.core_update(X, P, cores, k, sigma, lam=-1e-10)
+        s = t.residual_weights(k, sigma)
+        assert s["n_obs"] == st.n_obs and s["n_slots"] == X.size
+        assert abs(s["sum_w"] - st.sum_w) <= TOL * st.sum_w
+        d = t.core_gradient(k)
+        assert rel(d, st.d) <= TOL, (k, rel(d, st.d))
+        eta = t.core_update(k, -1e-10)
+        assert abs(eta - st.eta) <= TOL * abs(st.eta), (k, eta, st.eta)
+        assert rel(t.get_core(k) - cores[k], st.cores[k] - cores[k]) <= TOL
+        cores = st.cores
+
+
+def test_bf16_sigma_inf_and_fully_observed(torch_cuda):
+    """w = 1 (sigma = inf), no mask: the pass reduces to the TRALS-like masked LS step."""
+    from paper_2305_09044_gb300 import TRD
+    dims, ranks = (48, 40, 36, 32), (4, 4, 4, 4)
+    X, P, words, truth, Xt = problem(dims, ranks, 0.0, 0.0, 3)
+    t = TRD(dims, ranks, "bf16")
+    Xd = torch_cuda.from_numpy(flat(X)).cuda()
+    t.set_data(Xd, None)
+    cores = O.init_cores(dims, ranks, seed=4)
+    for k in range(4):
+        t.set_cores(cores)
+        st = O.core_update(X, np.ones_like(X), cores, k, math.inf, lam=0.0)
+        s = t.residual_weights(k, math.inf)
+        assert s["n_obs"] == X.size and abs(s["sum_w"] - X.size) < 1e-6 * X.size
+        assert rel(t.core_gradient(k), st.d) <= TOL
+        eta = t.core_update(k, 0.0)
+        assert abs(eta - 1.0) <= TOL
+        cores = st.cores
+
+
+def test_bf16_full_size_workload(torch_cuda):
+    """The 100^4 rank-8 workload at full size in the benchmark's launch configuration:
+    one update of core 1 (stationary inner block) and core 4 (stationary outer block) from
+    identical state, against the oracle on the full tensor."""
+    from paper_2305_09044_gb300 import TRD, synth
+    w = synth.WORKLOADS["cfg100"]
+    truth = synth.gaussian_cores(w.dims, w.ranks, w.data_seed)
+    Xt = O.reconstruct_unfold(truth)
+    c = synth.draw_corruption(w)
+    X = synth.assemble(Xt, c).astype(np.float32)
+    P = c.mask.astype(np.float64)
+    t = TRD(w.dims, w.ranks, "bf16")
+    Xd = torch_cuda.from_numpy(flat(X)).cuda()
+    Md = torch_cuda.from_numpy(synth.pack_mask(c.mask).view(np.int32)).cuda()
+    t.set_data(Xd, Md)
+    X = X.astype(np.float64)
+    del Xt
+    cores = O.init_cores(w.dims, w.ranks, seed=w.init_seed)
+    sigma = 2.0
+    for k in (0, 3):
+        t.set_cores(cores)
+        st = O.core_update(X, P, cores, k, sigma, lam=-1e-10)
+        t.residual_weights(k, sigma)
+        d = t.core_gradient(k)
+        assert rel(d, st.d) <= TOL, (k, rel(d, st.d))
+        eta = t.core_update(k, -1e-10)
+        assert abs(eta - st.eta) <= TOL * abs(st.eta)
+        assert rel(t.get_core(k) - cores[k], st.cores[k] - cores[k]) <= TOL
+
+
+def test_bf16_recovery_matches_oracle(torch_cuda):
+    """Exact TR tensor with 30 % missing entries, no outliers, sigma = inf: after 40
+    iterations the BF16 path's recovery error is within 1e-4 of the oracle's."""
+    dims, ranks = (48, 40, 36, 32), (3, 3, 3, 3)
+    t, X, P, Xt, keep = _make(torch_cuda, dims, ranks, missing=0.3, outliers=0.0, seed=31)
+    cores = O.init_cores(dims, ranks, seed=7)
+    t.set_cores(cores)
+    for it in range(40):
+        for k in range(4):
+            cores = O.core_update(X, P, cores, k, math.inf, lam=-1e-10).cores
+        t.step(sigma=math.inf)
+    err_o = O.relative_error(cores, Xt)
+    err_g = t.recovery_error(torch_cuda.from_numpy(flat(Xt)).cuda())
+    assert abs(err_o - err_g) <= 1e-4, (err_o, err_g)
