@@ -78,11 +78,16 @@ struct Extra {
   DevBuf tmpZ[kMaxN];   // cores given to trd_reconstruct_from
   DevBuf probe_xsq;
   // BF16 tensor-core operands and the padded mask rows of the current view
-  DevBuf bShi, bSlo, bSh, bThi, bTlo, bTT, Mrows;
-  const float* mrows_X = nullptr;
-  const uint32_t* mrows_M = nullptr;
-  int64_t mrows_Pin = -1, mrows_Pout = -1;
+  DevBuf bShi, bSlo, bSh, bThi, bTlo, bTT;
+  // observation bits re-laid per stationary index: [0] inner index along the outer one
+  // (rows case), [1] outer index along the inner one (cols case); cached per view and split
+  DevBuf Mst[2];
+  const float* mst_X[2] = {nullptr, nullptr};
+  const uint32_t* mst_M[2] = {nullptr, nullptr};
+  int64_t mst_Pin[2] = {-1, -1}, mst_Pout[2] = {-1, -1};
+  int64_t mst_W[2] = {0, 0};
   int64_t ldT = 0, W = 0;
+  int mst_o = 0;
   int tcG = 0;
   // tracing: event pairs around data-pass launches (kind 0 = pass 1, 1 = pass 2)
   bool prof = false;
@@ -370,17 +375,23 @@ trd_status run_pass1_tc(trd_handle* h, int k) {
   if (sp.P_in % 4) return set_err(h, TRD_ENOTIMPL, "BF16 path needs the inner block size to be a multiple of 4");
   TRY(build_merged(h, k, false));
   const View& v = h->view;
-  // padded mask rows of the view (cached while the view and split are unchanged)
-  const int64_t W = ((sp.P_in + 31) / 32 + 3) / 4 * 4;
-  if (x->mrows_X != v.X || x->mrows_M != v.M || x->mrows_Pin != sp.P_in || x->mrows_Pout != sp.P_out) {
-    TRY(ensure(h, x->Mrows, sizeof(uint32_t) * (size_t)(sp.P_out * W)));
-    CK(launch_mask_rows(v.M, sp.P_in, sp.P_out, W, (uint32_t*)x->Mrows.p, h->stream), "mask rows");
-    x->mrows_X = v.X;
-    x->mrows_M = v.M;
-    x->mrows_Pin = sp.P_in;
-    x->mrows_Pout = sp.P_out;
+  // observation bits of every stationary index along the streaming index (cached)
+  const int o = sp.rows ? 0 : 1;
+  const int64_t nstat = sp.rows ? sp.P_in : sp.P_out, nstrm = sp.rows ? sp.P_out : sp.P_in;
+  const int64_t W = ((nstrm + 31) / 32 + 3) / 4 * 4;
+  if (x->mst_X[o] != v.X || x->mst_M[o] != v.M || x->mst_Pin[o] != sp.P_in || x->mst_Pout[o] != sp.P_out) {
+    TRY(ensure(h, x->Mst[o], sizeof(uint32_t) * (size_t)(nstat * W)));
+    if (sp.rows)
+      CK(launch_mask_transpose(v.M, sp.P_in, sp.P_out, W, (uint32_t*)x->Mst[o].p, h->stream), "mask layout");
+    else
+      CK(launch_mask_rows(v.M, sp.P_in, sp.P_out, W, (uint32_t*)x->Mst[o].p, h->stream), "mask layout");
+    x->mst_X[o] = v.X;
+    x->mst_M[o] = v.M;
+    x->mst_Pin[o] = sp.P_in;
+    x->mst_Pout[o] = sp.P_out;
   }
   x->W = W;
+  x->mst_o = o;
   const int64_t ldT = (sp.P_strm + 63) / 64 * 64;
   x->ldT = ldT;
   const size_t b2 = sizeof(__nv_bfloat16);
@@ -403,7 +414,7 @@ trd_status run_pass1_tc(trd_handle* h, int k) {
   prof_begin(h);
   CK(launch_pass_tc(sp.rows, false, (const __nv_bfloat16*)x->bShi.p, (const __nv_bfloat16*)x->bSlo.p, nullptr,
                     (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p, (const __nv_bfloat16*)x->bTT.p,
-                    ldT, v.X, sp.P_in, sp.P_out, (const uint32_t*)x->Mrows.p, W, sp.P_stat, sp.P_strm, sp.Kp,
+                    ldT, v.X, sp.P_in, sp.P_out, (const uint32_t*)x->Mst[o].p, W, sp.P_stat, sp.P_strm, sp.Kp,
                     h->scal + S_SIGMA, (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, G, h->stream),
      "tensor-core data pass 1");
   prof_end(h, 0);
@@ -426,7 +437,7 @@ trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
   CK(launch_pass_tc(sp.rows, true, (const __nv_bfloat16*)x->bShi.p, (const __nv_bfloat16*)x->bSlo.p,
                     (const __nv_bfloat16*)x->bSh.p, (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p,
                     (const __nv_bfloat16*)x->bTT.p, x->ldT, h->view.X, sp.P_in, sp.P_out,
-                    (const uint32_t*)x->Mrows.p, x->W, sp.P_stat, sp.P_strm, sp.Kp, h->scal + S_SIGMA,
+                    (const uint32_t*)x->Mst[x->mst_o].p, x->W, sp.P_stat, sp.P_strm, sp.Kp, h->scal + S_SIGMA,
                     (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, x->tcG, h->stream),
      "tensor-core data pass 2");
   prof_end(h, 1);
@@ -824,7 +835,8 @@ void trd_destroy(trd_t* h) {
                     &h->D, &h->Dprev, &h->probe_keys, &h->probe_vals, &h->probe_work};
   for (DevBuf* b : bufs) free_buf(*b);
   Extra* x = X_(h);
-  DevBuf* xb[] = {&x->meta, &x->stat_sum2, &x->Gloc, &x->recA, &x->recC, &x->errp, &x->probe_xsq};
+  DevBuf* xb[] = {&x->meta, &x->stat_sum2, &x->Gloc, &x->recA, &x->recC, &x->errp, &x->probe_xsq,
+                  &x->bShi, &x->bSlo, &x->bSh, &x->bThi, &x->bTlo, &x->bTT, &x->Mst[0], &x->Mst[1]};
   for (DevBuf* b : xb) free_buf(*b);
   for (int k = 0; k < kMaxN; ++k) { free_buf(x->Eloc[k]); free_buf(x->tmpZ[k]); }
   for (auto& p : x->pending) { x->ev_pool.push_back(p.a); x->ev_pool.push_back(p.b); }

@@ -31,7 +31,9 @@ constexpr int BM = 128;        // UMMA M: stationary rows per block
 constexpr int BN = 64;         // streaming columns per tile
 constexpr int KPAD = 64;       // padded contraction length (one 128-byte swizzle atom)
 constexpr int STAGES = 3;
-constexpr int NTHREADS = 192;
+constexpr int NEPI = 8;                    // epilogue warps: 4 TMEM lane quarters x 2 column halves
+constexpr int NTHREADS = 64 + 32 * NEPI;   // producer warp, MMA warp, epilogue warps
+constexpr int EPI_THREADS = 32 * NEPI;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
 // shared-memory carve-up (bytes, every buffer 1024-aligned)
@@ -39,7 +41,6 @@ constexpr int S_TILE = BM * KPAD * 2;          // 16 KB: one stationary operand
 constexpr int X_TILE = BN * BM * 4;            // 32 KB: one data tile
 constexpr int T_TILE = BN * KPAD * 2;          // 8 KB: one streaming operand
 constexpr int TT_TILE = KPAD * BN * 2;         // 8 KB: streaming operand, transposed
-constexpr int M_TILE = 1024;                   // mask words of one tile (ROWS: 64 x 4 words)
 constexpr int Y_TILE = BM * BN * 2;            // 16 KB: weighted residuals (A of GEMM 2)
 
 struct Layout {
@@ -57,8 +58,8 @@ __host__ __device__ constexpr Layout layout(bool pass2) {
   L.thi_off = X_TILE;
   L.tlo_off = X_TILE + T_TILE;
   L.tt_off = X_TILE + 2 * T_TILE;
-  L.m_off = X_TILE + 2 * T_TILE + (pass2 ? 0 : TT_TILE);
-  L.stage_bytes = L.m_off + M_TILE;
+  L.m_off = 0;
+  L.stage_bytes = X_TILE + 2 * T_TILE + (pass2 ? 0 : TT_TILE);
   o += STAGES * L.stage_bytes;
   L.y = o; if (!pass2) o += Y_TILE;
   L.bars = o; o += 1024;
@@ -71,8 +72,8 @@ struct Params {
   int Kp;                    // valid contraction columns (<= KPAD)
   int64_t RB, NT, U;         // stationary blocks, streaming tiles, units
   int G;                     // CTAs
-  const uint32_t* Mrows;     // COLS case: padded mask rows [P_out][W] (direct loads)
-  int64_t W;                 // words per padded mask row
+  const uint32_t* Mst;       // mask bits of each stationary index along the streaming index
+  int64_t W;                 // words per mask row (multiple of 4)
   const double* sigma;
   float* Tpart;              // [G + RB][BM][Kp]
   double* stat_part;         // [G][8]
@@ -159,6 +160,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// 2^x on the special-function unit (ex2.approx, flush-to-zero); the weight needs only
+// about 1e-6 relative accuracy in this path.
+__device__ __forceinline__ float fast_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&v);
@@ -190,7 +199,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* mma_done = acc_empty + 1;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(mma_done + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 2);
-  double* red = reinterpret_cast<double*>(mma_done + 4);   // [4 warps][8] statistics
+  double* red = reinterpret_cast<double*>(mma_done + 4);   // [NEPI warps][8] statistics
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t c = blockIdx.x;
@@ -199,18 +208,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1 + 128);
+      mbar_init(&empty[s], 1 + EPI_THREADS);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&d_full[b], 1);
-      mbar_init(&d_empty[b], 128);
+      mbar_init(&d_empty[b], EPI_THREADS);
     }
-    mbar_init(y_full, 128);
+    mbar_init(y_full, EPI_THREADS);
     mbar_init(y_empty, 1);
     mbar_init(s_full, 1);
     mbar_init(s_empty, 1);
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 128);
+    mbar_init(acc_empty, EPI_THREADS);
     mbar_init(mma_done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -226,9 +235,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  // TMEM columns: D1[b] at b*BN, D2[b] (pass 2) at 2*BN + b*BN, T accumulator at 2*BN
-  const uint32_t col_d1[2] = {0u, (uint32_t)BN};
-  const uint32_t col_d2[2] = {2u * BN, 3u * BN};
+  // TMEM columns: D1[b] at b*BN, D2[b] (pass 2) at (2 + b)*BN, T accumulator at 2*BN
   const uint32_t col_acc = 2u * BN;
 
   if (warp == 0) {
@@ -255,7 +262,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (!mbar_wait(&empty[s], (uint32_t)(((it / STAGES) & 1) ^ 1), abort_flag)) { ok = false; break; }
           const int t0 = (int)((u % p.NT) * BN);
           unsigned char* st = sm + L.stage0 + s * L.stage_bytes;
-          uint32_t bytes = X_TILE + 2 * T_TILE + (PASS2 ? 0 : TT_TILE) + (ROWS ? BN * 16 : 0);
+          const uint32_t bytes = X_TILE + 2 * T_TILE + (PASS2 ? 0 : TT_TILE);
           mbar_expect_tx(&full[s], bytes);
           last_phase[s] = (int)((it / STAGES) & 1);
           tma_2d(st + L.thi_off, &mT_hi, &full[s], 0, t0);
@@ -263,7 +270,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (!PASS2) tma_2d(st + L.tt_off, &mTT, &full[s], t0, 0);
           if (ROWS) {
             tma_2d(st + L.x_off, &mX, &full[s], (int)(rb * BM), t0);
-            tma_2d(st + L.m_off, &mM, &full[s], (int)(rb * BM / 32), t0);
           } else {
             tma_2d(st + L.x_off, &mX, &full[s], t0, (int)(rb * BM));
             tma_2d(st + L.x_off + X_TILE / 2, &mX, &full[s], t0 + 32, (int)(rb * BM));
@@ -307,10 +313,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const uint32_t b_hi = st + L.thi_off, b_lo = st + L.tlo_off;
           for (int kk = 0; kk < KPAD / 16; ++kk) {
             const uint32_t ko = kk * 32;
-            tc_mma(tmem + col_d1[b], sdesc(a_hi + ko), sdesc(b_hi + ko), ID1, kk > 0);
-            tc_mma(tmem + col_d1[b], sdesc(a_hi + ko), sdesc(b_lo + ko), ID1, 1);
-            tc_mma(tmem + col_d1[b], sdesc(a_lo + ko), sdesc(b_hi + ko), ID1, 1);
-            if (PASS2) tc_mma(tmem + col_d2[b], sdesc(a_h + ko), sdesc(b_hi + ko), ID1, kk > 0);
+            tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_hi + ko), sdesc(b_hi + ko), ID1, kk > 0);
+            tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_hi + ko), sdesc(b_lo + ko), ID1, 1);
+            tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_lo + ko), sdesc(b_hi + ko), ID1, 1);
+            if (PASS2) tc_mma(tmem + (uint32_t)((2 + b) * BN), sdesc(a_h + ko), sdesc(b_hi + ko), ID1, kk > 0);
           }
           tc_commit(&d_full[b]);
           if (PASS2) {
@@ -355,13 +361,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (mbar_try(mma_done, 0)) break;
     }
   } else {
-    // ---------------------------------------------------------------- epilogue (128 threads)
-    const int q = warp & 3;                 // TMEM lane quarter of this warp
+    // ---------------------------------------------------------------- epilogue (8 warps)
+    // warp w (2..9) reads TMEM lane quarter q = w % 4 and column half grp of every tile
+    const int q = warp & 3;
+    const int grp = (warp - 2) >> 2;
     const int row = q * 32 + lane;          // stationary row within the block
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const double sg = *p.sigma;
     // exp(-e^2 / (2 sigma^2)) = exp2(-e^2 * k), k = log2(e) / (2 sigma^2); sigma = inf -> k = 0
-    const float kexp = isinf(sg) ? 0.0f : (float)(1.4426950408889634 / (2.0 * sg * sg));
+    const float nk = isinf(sg) ? 0.0f : (float)(-1.4426950408889634 / (2.0 * sg * sg));
     float sw = 0.f, se2 = 0.f, swe2 = 0.f, sden = 0.f;
     uint32_t nobs = 0, nnf = 0, nslot = 0;
     int64_t it = 0;
@@ -372,84 +380,70 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t seg_end = imin(u_end, (rb + 1) * p.NT);
       const int64_t srow = rb * BM + row;
       const bool row_ok = srow < p.P_stat;
+      const uint32_t* mrow = p.Mst + (row_ok ? srow : 0) * p.W;
       for (; u < seg_end; ++u, ++it) {
         const int s = (int)(it % STAGES), b = (int)(it & 1);
         const int64_t t0 = (u % p.NT) * BN;
+        // this thread's 32 observation bits (issued before the waits to hide the latency)
+        const uint32_t mword = row_ok ? __ldg(mrow + (t0 >> 5) + grp) : 0u;
+        const int64_t nc = p.P_strm - t0 - 32 * grp;    // valid columns in this half
+        const uint32_t vmask = (!row_ok || nc <= 0) ? 0u : (nc >= 32 ? 0xffffffffu : ((1u << nc) - 1u));
         if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), abort_flag)) { ok = false; break; }
         if (!mbar_wait(&d_full[b], (uint32_t)((it >> 1) & 1), abort_flag)) { ok = false; break; }
         tc_fence_after();
         const unsigned char* st = sm + L.stage0 + s * L.stage_bytes;
-        const float* sx = reinterpret_cast<const float*>(st + L.x_off);
-        const uint32_t* smk = reinterpret_cast<const uint32_t*>(st + L.m_off);
-        uint2 mrow = make_uint2(0u, 0u);
-        if (!ROWS && row_ok) {
-          const uint32_t* mp = p.Mrows + srow * p.W + (t0 >> 5);
-          mrow = *reinterpret_cast<const uint2*>(mp);
-        }
-        uint32_t ypk[BN / 2];
+        float xh[32], dh[32], xv[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + grp * 32), xh);
+        if (PASS2) tmem_ld32(tmem + lane_base + (uint32_t)((2 + b) * BN + grp * 32), dh);
+        if (ROWS) {
+          const float* sx = reinterpret_cast<const float*>(st + L.x_off) + (grp * 32) * BM + row;
 #pragma unroll
-        for (int h = 0; h < BN / 32; ++h) {
-          float xh[32], dh[32];
-          tmem_ld32(tmem + lane_base + col_d1[b] + h * 32, xh);
-          if (PASS2) tmem_ld32(tmem + lane_base + col_d2[b] + h * 32, dh);
-          float xv[32];
-          if (ROWS) {
+          for (int j = 0; j < 32; ++j) xv[j] = sx[j * BM];
+        } else {
+          // SWIZZLE_128B box of 32 columns: 16-byte chunk c of row r sits at chunk c ^ (r & 7)
+          const unsigned char* box = st + L.x_off + grp * (X_TILE / 2) + row * 128;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) xv[j] = sx[(h * 32 + j) * BM + row];
-          } else {
-            // two SWIZZLE_128B boxes of 32 columns; 16-byte chunk c of row r sits at chunk c ^ (r & 7)
-            const unsigned char* box = st + L.x_off + h * (X_TILE / 2) + row * 128;
-#pragma unroll
-            for (int c4 = 0; c4 < 8; ++c4) {
-              const float4 v = *reinterpret_cast<const float4*>(box + ((c4 ^ (row & 7)) << 4));
-              xv[4 * c4 + 0] = v.x; xv[4 * c4 + 1] = v.y; xv[4 * c4 + 2] = v.z; xv[4 * c4 + 3] = v.w;
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = h * 32 + j;
-            bool obs;
-            if (ROWS) obs = (smk[col * 4 + q] >> lane) & 1u;
-            else obs = ((h == 0 ? mrow.x : mrow.y) >> j) & 1u;
-            const bool valid = row_ok && (t0 + col < p.P_strm);
-            float y = 0.f;
-            if (valid) {
-              nslot += 1;
-              if (obs) {
-                nobs += 1;
-                const float e = xv[j] - xh[j];
-                if (isfinite(e)) {
-                  const float w = exp2f(-e * e * kexp);
-                  if (PASS2) {
-                    sden += w * dh[j] * dh[j];
-                  } else {
-                    y = w * e;
-                    sw += w;
-                    se2 += e * e;
-                    swe2 += y * e;
-                  }
-                } else {
-                  nnf += 1;
-                }
-              }
-            }
-            if (!PASS2) xv[j] = y;
-          }
-          if (!PASS2) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 2) ypk[(h * 32 + j) >> 1] = pack_bf16(xv[j], xv[j + 1]);
+          for (int c4 = 0; c4 < 8; ++c4) {
+            const float4 v = *reinterpret_cast<const float4*>(box + ((c4 ^ (row & 7)) << 4));
+            xv[4 * c4 + 0] = v.x; xv[4 * c4 + 1] = v.y; xv[4 * c4 + 2] = v.z; xv[4 * c4 + 3] = v.w;
           }
         }
         tc_fence_before();
         mbar_arrive(&d_empty[b]);
         mbar_arrive(&empty[s]);
+        const uint32_t seen = mword & vmask;
+        nslot += __popc(vmask);
+        nobs += __popc(seen);
+        // branch-free slot update (predicated selects keep the 32 slots independent)
+        uint32_t fin = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float e = xv[j] - xh[j];
+          const bool use = ((seen >> j) & 1u) && (fabsf(e) <= 3.402823466e38f);
+          fin |= use ? (1u << j) : 0u;
+          const float w = fast_ex2(e * e * nk);
+          const float uw = use ? w : 0.f;
+          if (PASS2) {
+            sden = fmaf(uw * dh[j], dh[j], sden);
+          } else {
+            const float y = uw * e;
+            sw += uw;
+            se2 = fmaf(use ? e : 0.f, e, se2);
+            swe2 = fmaf(y, e, swe2);
+            xv[j] = y;
+          }
+        }
+        nnf += __popc(seen & ~fin);
         if (!PASS2) {
+          uint32_t ypk[16];
+#pragma unroll
+          for (int j = 0; j < 32; j += 2) ypk[j >> 1] = pack_bf16(xv[j], xv[j + 1]);
           if (!mbar_wait(y_empty, (uint32_t)((it & 1) ^ 1), abort_flag)) { ok = false; break; }
           unsigned char* yrow = sm + L.y + row * 128;
 #pragma unroll
-          for (int c8 = 0; c8 < 8; ++c8) {
-            const uint4 v = make_uint4(ypk[4 * c8], ypk[4 * c8 + 1], ypk[4 * c8 + 2], ypk[4 * c8 + 3]);
-            *reinterpret_cast<uint4*>(yrow + ((c8 ^ (row & 7)) << 4)) = v;
+          for (int c = 0; c < 4; ++c) {
+            const uint4 v = make_uint4(ypk[4 * c], ypk[4 * c + 1], ypk[4 * c + 2], ypk[4 * c + 3]);
+            *reinterpret_cast<uint4*>(yrow + (((4 * grp + c) ^ (row & 7)) << 4)) = v;
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           mbar_arrive(y_full);
@@ -457,18 +451,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       if (!ok) break;
       if (!PASS2) {
-        // drain the segment's contraction: row `row` of T (Kp valid columns) -> partial slot c + rb
+        // drain the segment's contraction: this half of row `row` of T -> partial slot c + rb
         if (!mbar_wait(acc_full, (uint32_t)(g & 1), abort_flag)) { ok = false; break; }
         tc_fence_after();
         float* dst = p.Tpart + ((c + rb) * BM + row) * (int64_t)p.Kp;
+        float v[32];
+        tmem_ld32(tmem + lane_base + col_acc + grp * 32, v);
 #pragma unroll
-        for (int h = 0; h < KPAD / 32; ++h) {
-          float v[32];
-          tmem_ld32(tmem + lane_base + col_acc + h * 32, v);
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (h * 32 + j < p.Kp) dst[h * 32 + j] = row_ok ? v[j] : 0.f;
-        }
+        for (int j = 0; j < 32; ++j)
+          if (grp * 32 + j < p.Kp) dst[grp * 32 + j] = row_ok ? v[j] : 0.f;
         tc_fence_before();
         mbar_arrive(acc_empty);
       }
@@ -480,7 +471,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int f = 0; f < 7; ++f) {
       double x = fv[f];
       for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      if (lane == 0) red[q * 8 + f] = x;
+      if (lane == 0) red[(warp - 2) * 8 + f] = x;
     }
   }
   // ------------------------------------------------------------------ teardown
@@ -489,7 +480,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) {
     for (int f = 0; f < 7; ++f) {
       double x = 0.0;
-      for (int w = 0; w < 4; ++w) x += red[w * 8 + f];
+      for (int w = 0; w < NEPI; ++w) x += red[w * 8 + f];
       p.stat_part[c * 8 + f] = x;
     }
     p.stat_part[c * 8 + 7] = 0.0;
@@ -561,6 +552,47 @@ __global__ void k_mask_rows(const uint32_t* __restrict__ M, int64_t P_in, int64_
       }
     }
     out[e] = v;
+  }
+}
+
+// Transposed padded mask: MT[a][w] bit j = observation bit of (a, b = 32 w + j), i.e. the
+// bits of one inner index along the outer index.  One warp per (32 consecutive a, word w):
+// lane j fetches the 32-bit window of column b = 32 w + j starting at row a0, then 32 ballots
+// transpose the 32 x 32 bit block.
+__global__ void k_mask_transpose(const uint32_t* __restrict__ M, int64_t P_in, int64_t P_out, int64_t WT,
+                                 uint32_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nab = (P_in + 31) / 32;
+  const int64_t nwords = (P_in * P_out + 31) / 32;
+  for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < nab * WT; task += warps) {
+    const int64_t ab = task / WT, w = task % WT;
+    const int64_t a0 = ab * 32;
+    const int64_t b = 32 * w + lane;
+    uint32_t col = 0;
+    if (b < P_out) {
+      if (!M) {
+        const int64_t nb = imin(32, P_in - a0);
+        col = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
+      } else {
+        const int64_t bit = a0 + P_in * b;
+        const int64_t wd = bit >> 5;
+        const int sh = (int)(bit & 31);
+        const uint64_t lo = M[wd];
+        const uint64_t hi = (sh && wd + 1 < nwords) ? (uint64_t)M[wd + 1] : 0ull;
+        col = (uint32_t)(((hi << 32) | lo) >> sh);
+        const int64_t nb = imin(32, P_in - a0);
+        if (nb < 32) col &= (1u << nb) - 1u;
+      }
+    }
+    uint32_t mine = 0;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const uint32_t bits = __ballot_sync(0xffffffffu, (col >> r) & 1u);
+      if (lane == r) mine = bits;
+    }
+    const int64_t a = a0 + lane;
+    if (a < P_in) out[a * WT + w] = mine;
   }
 }
 
@@ -643,6 +675,15 @@ cudaError_t launch_mask_rows(const uint32_t* M, int64_t P_in, int64_t P_out, int
   return cudaGetLastError();
 }
 
+cudaError_t launch_mask_transpose(const uint32_t* M, int64_t P_in, int64_t P_out, int64_t WT, uint32_t* out,
+                                  cudaStream_t st) {
+  const int64_t tasks = ((P_in + 31) / 32) * WT;
+  const unsigned blocks = (unsigned)imin((tasks * 32 + 255) / 256, 8192);
+  tc::k_mask_transpose<<<blocks, 256, 0, st>>>(M, P_in, P_out, WT, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_slots(const float* part, int64_t RB, int64_t NT, int G, int64_t P_stat, int Kp,
                                 double* out, cudaStream_t st) {
   const int64_t n = P_stat * Kp;
@@ -656,11 +697,11 @@ cudaError_t launch_reduce_slots(const float* part, int64_t RB, int64_t NT, int G
 cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi, const __nv_bfloat16* S_lo,
                            const __nv_bfloat16* S_h, const __nv_bfloat16* T_hi, const __nv_bfloat16* T_lo,
                            const __nv_bfloat16* TT, int64_t ldT, const float* X, int64_t P_in, int64_t P_out,
-                           const uint32_t* Mrows, int64_t W, int64_t P_stat, int64_t P_strm, int Kp,
+                           const uint32_t* Mst, int64_t W, int64_t P_stat, int64_t P_strm, int Kp,
                            const double* sigma, float* Tpart, double* stat_part, int* err, int G,
                            cudaStream_t st) {
   using namespace tc;
-  if (Kp > KPAD || (P_in % 4) != 0 || (W % 4) != 0 || (ldT % 64) != 0) return cudaErrorInvalidValue;
+  if (Kp > KPAD || (P_in % 4) != 0 || (ldT % 64) != 0) return cudaErrorInvalidValue;
   CUtensorMap mS_hi, mS_lo, mS_h, mT_hi, mT_lo, mTT, mX, mM;
   const CUtensorMapDataType BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const CUtensorMapSwizzle SW = CU_TENSOR_MAP_SWIZZLE_128B;
@@ -672,8 +713,8 @@ cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi
             make_map(&mTT, BF, 2, TT, ldT, KPAD, ldT * 2, 64, KPAD, SW);
   if (rows_case) {
     ok = ok && make_map(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, P_in, P_out, P_in * 4, BM, BN,
-                        CU_TENSOR_MAP_SWIZZLE_NONE) &&
-         make_map(&mM, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, Mrows, W, P_out, W * 4, 4, BN, CU_TENSOR_MAP_SWIZZLE_NONE);
+                        CU_TENSOR_MAP_SWIZZLE_NONE);
+    mM = mX;
   } else {
     ok = ok && make_map(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, P_in, P_out, P_in * 4, 32, BM, SW);
     mM = mX;
@@ -688,7 +729,7 @@ cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi
   p.NT = (P_strm + BN - 1) / BN;
   p.U = p.RB * p.NT;
   p.G = (int)imin(G, p.U);
-  p.Mrows = Mrows;
+  p.Mst = Mst;
   p.W = W;
   p.sigma = sigma;
   p.Tpart = Tpart;
