@@ -151,24 +151,10 @@ def build_problem(w, torch, prec):
     return t, Xt, (Xh, Mh), (Xd, Md), c
 
 
-def run_ours(args, rank, world, local):
-    import torch
-    from paper_2305_09044_gb300 import synth
-    from paper_2305_09044_gb300.binding import kernel_launches
-    import __graft_entry__
-    __graft_entry__.build()
-    torch.cuda.set_device(local)
-    prec = args.precision or "fp32"
-    w = synth.WORKLOADS[WORKLOAD]
-    if world > 1:   # independent replicas: a different data seed per rank
-        import dataclasses
-        w = dataclasses.replace(w, data_seed=w.data_seed + 100 * rank, init_seed=w.init_seed + 100 * rank)
-    t, Xt, host, dev, corr = build_problem(w, torch, prec)
-    t.init_cores(w.init_seed)
-    slots_per_step = len(w.dims) * int(np.prod(w.dims))
-    stream = t.stream
-
-    for _ in range(max(args.warmup, 3)):
+def timed_steps(t, steps, warmup, world, local, torch, kernel_launches):
+    """Warm up, then time `steps` trd_step calls with CUDA events on the handle's stream;
+    the fused data passes are traced by the library (events around each launch)."""
+    for _ in range(max(warmup, 3)):
         t.step(sigma=-1.0)
     t.set_profiling(True)
     t.get_profile(reset=True)
@@ -178,19 +164,72 @@ def run_ours(args, rank, world, local):
     clocks.start()
     l0 = kernel_launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
+    ev0.record(t.stream)
+    for _ in range(steps):
         t.step(sigma=-1.0)
-    ev1.record(stream)
+    ev1.record(t.stream)
     torch.cuda.synchronize()
     launches = kernel_launches() - l0
     ck = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
     prof = t.get_profile(reset=True)
     t.set_profiling(False)
-    ms = _max_over_ranks(ms, world)
+    ms = _max_over_ranks(ev0.elapsed_time(ev1), world)
+    return ms, prof, launches, ck
+
+
+def roofline(prec, prof, w):
+    pk, src = peaks()
+    Kp = w.ranks[0] * w.ranks[len(w.dims) // 2]
+    n_slots = int(np.prod(w.dims))
+    launches_pass = prof["pass1_n"] + prof["pass2_n"]
+    pass_ms = (prof["pass1_ms"] + prof["pass2_ms"]) / max(launches_pass, 1)
+    hbm_bytes = n_slots * (4 + 1 / 8)                   # x (FP32) + mask bit per slot
+    if prec == "bf16":
+        achieved = hbm_bytes / (pass_ms / 1e3) / 1e9
+        roof = {"kernel": "k_pass_tc (fused tcgen05 data pass, passes 1+2)", "bound": "hbm",
+                "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback"}
+    else:
+        algo = n_slots * 4 * Kp                         # 2 Kp recon + 2 Kp contraction per slot
+        sm = pk.get("sm_max_mhz", 2070.0)
+        if prec == "fp32":
+            peak = 152 * 128 * 2 * sm * 1e6 / 1e12
+            psrc = f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm:.0f} MHz"
+        else:
+            peak, psrc = 1.25, "nominal GB300 FP64 rate"
+        achieved = algo / (pass_ms / 1e3) / 1e12
+        roof = {"kernel": "k_pass_simt (fused data pass, CUDA cores)", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": psrc}
+    roof["ms_per_launch"] = pass_ms
+    roof["launches"] = launches_pass
+    roof["algorithmic_bytes_per_launch"] = hbm_bytes
+    roof["hbm_gbs_achieved"] = hbm_bytes / (pass_ms / 1e3) / 1e9
+    return roof
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2305_09044_gb300 import TRD, synth
+    from paper_2305_09044_gb300.binding import kernel_launches
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    precs = [args.precision] if args.precision else ["bf16", "fp32"]
+    w = synth.WORKLOADS[WORKLOAD]
+    if world > 1:   # independent replicas: a different data seed per rank
+        import dataclasses
+        w = dataclasses.replace(w, data_seed=w.data_seed + 100 * rank, init_seed=w.init_seed + 100 * rank)
+    t, Xt, host, dev, corr = build_problem(w, torch, precs[0])
+    slots_per_step = len(w.dims) * int(np.prod(w.dims))
+
+    # headline path
+    t.init_cores(w.init_seed)
+    ms, prof, launches, ck = timed_steps(t, args.steps, args.warmup, world, local, torch, kernel_launches)
     ms_step = ms / args.steps
     value = world * slots_per_step * args.steps / (ms / 1e3)
+    prec = precs[0]
 
     # e2e through the public API with host buffers: H2D of X and mask from pinned memory,
     # one trd_step, the report read back (inside trd_step)
@@ -211,44 +250,28 @@ def run_ours(args, rank, world, local):
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "ms_per_step": e2e_s * 1e3 / args.steps}
 
-    # roofline of the dominant kernel (the fused data passes), from the in-region events
-    pk, src = peaks()
-    Kp = w.ranks[0] * w.ranks[len(w.dims) // 2]
-    n_slots = int(np.prod(w.dims))
-    launches_pass = prof["pass1_n"] + prof["pass2_n"]
-    pass_ms = (prof["pass1_ms"] + prof["pass2_ms"]) / max(launches_pass, 1)
-    if prec == "bf16":
-        algo = n_slots * (4 + 1 / 8)                    # x (FP32) + mask bit per slot
-        achieved = algo / (pass_ms / 1e3) / 1e9
-        roof = {"kernel": "fused data pass (tcgen05)", "bound": "hbm", "achieved": achieved,
-                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                "traffic": None, "peak_source": src}
-    else:
-        algo = n_slots * 4 * Kp                         # 2 Kp recon + 2 Kp contraction per slot
-        sm = pk.get("sm_max_mhz", 2070.0)
-        if prec == "fp32":
-            peak = 152 * 128 * 2 * sm * 1e6 / 1e12
-            psrc = f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm:.0f} MHz"
-        else:
-            peak, psrc = 1.25, "nominal GB300 FP64 rate"
-        achieved = algo / (pass_ms / 1e3) / 1e12
-        roof = {"kernel": "k_pass_simt (fused data pass, CUDA cores)", "bound": "alu",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": psrc}
-    roof["ms_per_launch"] = pass_ms
-    roof["launches"] = launches_pass
-    roof["algorithmic_per_launch"] = algo
-    roof["hbm_bytes_per_launch"] = n_slots * (4 + 1 / 8)
-    roof["hbm_gbs_achieved"] = roof["hbm_bytes_per_launch"] / (pass_ms / 1e3) / 1e9
-
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[prec],
            "data": "synthetic", "config": workload_config(w, prec), "iters_per_s": 1e3 / ms_step,
-           "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": ck}
-
+           "roofline": roofline(prec, prof, w), "e2e": e2e, "gpu_launches": launches, "clocks": ck}
     if rank == 0 and not args.no_converge:
         out["time_to_rel_err_1e-3"] = converge(t, Xt, w, args.converge_iters, torch)
+
+    # comparison path on the same device data (FP32 CUDA-core passes)
+    for other in precs[1:]:
+        t2 = TRD(w.dims, w.ranks, other)
+        t2.set_data(Xd, Md)
+        t2.init_cores(w.init_seed)
+        steps2 = max(3, args.steps // 4)
+        ms2, prof2, launches2, ck2 = timed_steps(t2, steps2, 3, world, local, torch, kernel_launches)
+        cmp_ = {"value": world * slots_per_step * steps2 / (ms2 / 1e3), "unit": UNIT, "steps": steps2,
+                "ms_per_step": ms2 / steps2, "iters_per_s": 1e3 * steps2 / ms2,
+                "roofline": roofline(other, prof2, w), "gpu_launches": launches2, "clocks": ck2}
+        if rank == 0 and not args.no_converge:
+            cmp_["time_to_rel_err_1e-3"] = converge(t2, Xt, w, args.converge_iters, torch)
+        out[other] = cmp_
+        t2.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, corr, budget_s=15.0)
     t.close()

@@ -47,9 +47,7 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 // implemented in merge.cu / sampled.cu / pass_tc.cu
-cudaError_t launch_reconstruct_mats(const double* A, const double* C, int64_t P_in, int64_t P_out,
-                                    int Kp, const float* Xref, float* out, double* err_part,
-                                    int parts, cudaStream_t st);
+
 
 }  // namespace trd
 
@@ -77,6 +75,7 @@ struct Extra {
   DevBuf errp;          // reconstruction error partials
   DevBuf tmpZ[kMaxN];   // cores given to trd_reconstruct_from
   DevBuf probe_xsq;
+  DevBuf Ework;         // FGMC factor partial sums
   // BF16 tensor-core operands and the padded mask rows of the current view
   DevBuf bShi, bSlo, bSh, bThi, bTlo, bTT;
   // observation bits re-laid per stationary index: [0] inner index along the outer one
@@ -235,7 +234,9 @@ trd_status sync_and_status(trd_handle* h) {
 
 // ------------------------------------------------------------------ FGMC
 trd_status refresh_E(trd_handle* h, int k) {
-  CK(launch_fgmc_E(h->Z[k], nullptr, h->I[k], h->R[k], h->R[(k + 1) % h->N], h->E[k], h->stream),
+  const int rk = h->R[k], rk1 = h->R[(k + 1) % h->N];
+  TRY(ensure(h, X_(h)->Ework, sizeof(double) * 16 * (size_t)rk * rk * rk1 * rk1));
+  CK(launch_fgmc_E(h->Z[k], nullptr, h->I[k], rk, rk1, h->E[k], (double*)X_(h)->Ework.p, h->stream),
      "fgmc factor");
   return TRD_OK;
 }
@@ -293,7 +294,7 @@ trd_status local_gram(trd_handle* h, int k) {
     TRY(ensure(h, x->Eloc[m], sizeof(double) * rm * rm * rm1 * rm1));
     const bool sampled = h->view.idx[m] != nullptr;
     CK(launch_fgmc_E(h->Z[m], h->view.idx[m], sampled ? h->view.dim[m] : h->I[m], rm, rm1,
-                     (double*)x->Eloc[m].p, h->stream), "local fgmc factor");
+                     (double*)x->Eloc[m].p, nullptr, h->stream), "local fgmc factor");
     E[m] = (double*)x->Eloc[m].p;
   }
   const int K = h->K[k];
@@ -497,13 +498,15 @@ trd_status run_gradient(trd_handle* h, int k) {
   const Chain post = make_chain(h, v, post0, post1);
   const int64_t n_pre = pre.n > 0 ? pre.count : 1;
   const int64_t n_post = post.n > 0 ? post.count : 1;
+  const bool dbl = is_fp64(h);
+  const size_t e = elt(h);
   if (pre.n > 0) {
-    TRY(ensure(h, h->pre, sizeof(double) * n_pre * mc * rk));
-    CK(launch_chain(pre, h->pre.p, true, false, mc * rk, h->stream), "merge prefix");
+    TRY(ensure(h, h->pre, e * n_pre * mc * rk));
+    CK(launch_chain(pre, h->pre.p, dbl, false, mc * rk, h->stream), "merge prefix");
   }
   if (post.n > 0) {
-    TRY(ensure(h, h->post, sizeof(double) * n_post * rk1 * mr));
-    CK(launch_chain(post, h->post.p, true, false, rk1 * mr, h->stream), "merge suffix");
+    TRY(ensure(h, h->post, e * n_post * rk1 * mr));
+    CK(launch_chain(post, h->post.p, dbl, false, rk1 * mr, h->stream), "merge suffix");
   }
   const int64_t npairs = n_pre * n_post;
   int64_t nsplit = (2 * (int64_t)h->num_sms + h->I[k] - 1) / h->I[k];
@@ -511,9 +514,9 @@ trd_status run_gradient(trd_handle* h, int k) {
   const int K = h->K[k];
   TRY(ensure(h, h->d, sizeof(double) * h->I[k] * K));
   if (nsplit > 1) TRY(ensure(h, h->dpart, sizeof(double) * nsplit * h->I[k] * K));
-  CK(launch_backcontract(h->Tsum.p, sp.Kp, sp.rows, mr, mc, pre.n > 0 ? (const double*)h->pre.p : nullptr,
-                         n_pre, post.n > 0 ? (const double*)h->post.p : nullptr, n_post, h->I[k], rk,
-                         rk1, (double*)h->dpart.p, (int)nsplit, (double*)h->d.p, h->stream),
+  CK(launch_backcontract(h->Tsum.p, sp.Kp, sp.rows, mr, mc, pre.n > 0 ? h->pre.p : nullptr, n_pre,
+                         post.n > 0 ? h->post.p : nullptr, n_post, h->I[k], rk, rk1, (double*)h->dpart.p,
+                         (int)nsplit, (double*)h->d.p, dbl, h->stream),
      "back-contraction");
   h->grad_k = k;
   return TRD_OK;
@@ -584,12 +587,17 @@ trd_status run_adaptive(trd_handle* h, double sigma_prev, const double* sigma_pr
   TRY(ensure(h, h->probe_keys, sizeof(uint64_t) * n));
   TRY(ensure(h, x->probe_xsq, sizeof(double) * n));
   TRY(ensure(h, h->probe_work, sizeof(double) * sigma_work_doubles()));
-  const char* meta = (const char*)x->meta.p;
-  CK(launch_probe_sigma((const double* const*)meta, h->N, (const int64_t*)(meta + 8 * kMaxN),
-                        (const int*)(meta + 16 * kMaxN), h->X, h->M, h->numel, is_fp64(h), sigma_prev,
-                        sigma_prev_dev,
-                        (double*)h->probe_vals.p, (uint64_t*)h->probe_keys.p, (double*)x->probe_xsq.p,
-                        (double*)h->probe_work.p, h->scal + S_SIGMA, h->stream),
+  // merged subchains of the full tensor for the current cores (same split rule as the passes)
+  const View fv = full_view(h);
+  const Split sp = choose_split(h, fv, 0);
+  const size_t e = elt(h);
+  TRY(ensure(h, x->recA, e * sp.P_in * sp.Kp));
+  TRY(ensure(h, x->recC, e * sp.P_out * sp.Kp));
+  CK(launch_chain(make_chain(h, fv, 0, sp.c), x->recA.p, is_fp64(h), false, sp.Kp, h->stream), "probe merge inner");
+  CK(launch_chain(make_chain(h, fv, sp.c, h->N), x->recC.p, is_fp64(h), true, sp.Kp, h->stream), "probe merge outer");
+  CK(launch_probe_sigma_merged(x->recA.p, x->recC.p, is_fp64(h), sp.Kp, sp.P_in, h->X, h->M, h->numel, sigma_prev,
+                               sigma_prev_dev, (double*)h->probe_vals.p, (uint64_t*)h->probe_keys.p,
+                               (double*)x->probe_xsq.p, (double*)h->probe_work.p, h->scal + S_SIGMA, h->stream),
      "adaptive width");
   h->sigma_set = true;
   return TRD_OK;
@@ -714,7 +722,7 @@ trd_status alloc_state(trd_handle* h) {
       chain = std::max(chain, (size_t)h->R[k] * h->R[k] * h->R[m] * h->R[m]);
   const int64_t IN = h->I[N - 1];
   TRY(ensure(h, h->G, sizeof(double) * maxK * maxK));
-  TRY(ensure(h, h->L, sizeof(double) * maxK * maxK));
+  TRY(ensure(h, h->L, sizeof(double) * (maxK * maxK + maxK)));
   TRY(ensure(h, h->T1, sizeof(double) * chain));
   TRY(ensure(h, h->T2, sizeof(double) * chain));
   TRY(ensure(h, h->d, sizeof(double) * maxIK));
@@ -835,7 +843,7 @@ void trd_destroy(trd_t* h) {
                     &h->D, &h->Dprev, &h->probe_keys, &h->probe_vals, &h->probe_work};
   for (DevBuf* b : bufs) free_buf(*b);
   Extra* x = X_(h);
-  DevBuf* xb[] = {&x->meta, &x->stat_sum2, &x->Gloc, &x->recA, &x->recC, &x->errp, &x->probe_xsq,
+  DevBuf* xb[] = {&x->Ework, &x->meta, &x->stat_sum2, &x->Gloc, &x->recA, &x->recC, &x->errp, &x->probe_xsq,
                   &x->bShi, &x->bSlo, &x->bSh, &x->bThi, &x->bTlo, &x->bTT, &x->Mst[0], &x->Mst[1]};
   for (DevBuf* b : xb) free_buf(*b);
   for (int k = 0; k < kMaxN; ++k) { free_buf(x->Eloc[k]); free_buf(x->tmpZ[k]); }
@@ -1102,15 +1110,16 @@ static trd_status reconstruct_impl(trd_t* h, const double* const* cores, float* 
   const View v = full_view(h);
   const Split sp = choose_split(h, v, 0);
   Extra* x = X_(h);
-  TRY(ensure(h, x->recA, sizeof(double) * sp.P_in * sp.Kp));
-  TRY(ensure(h, x->recC, sizeof(double) * sp.P_out * sp.Kp));
+  const bool dbl = is_fp64(h);
+  TRY(ensure(h, x->recA, elt(h) * sp.P_in * sp.Kp));
+  TRY(ensure(h, x->recC, elt(h) * sp.P_out * sp.Kp));
   const Chain inner = make_chain(h, v, 0, sp.c, -1, nullptr, cores);
   const Chain outer = make_chain(h, v, sp.c, h->N, -1, nullptr, cores);
-  CK(launch_chain(inner, x->recA.p, true, false, sp.Kp, h->stream), "merge inner");
-  CK(launch_chain(outer, x->recC.p, true, true, sp.Kp, h->stream), "merge outer");
+  CK(launch_chain(inner, x->recA.p, dbl, false, sp.Kp, h->stream), "merge inner");
+  CK(launch_chain(outer, x->recC.p, dbl, true, sp.Kp, h->stream), "merge outer");
   const int parts = 4 * h->num_sms;
   TRY(ensure(h, x->errp, sizeof(double) * 2 * parts));
-  CK(launch_reconstruct_mats((const double*)x->recA.p, (const double*)x->recC.p, sp.P_in, sp.P_out, sp.Kp,
+  CK(launch_reconstruct_mats(x->recA.p, x->recC.p, dbl, sp.P_in, sp.P_out, sp.Kp,
                              ref, out, ref ? (double*)x->errp.p : nullptr, parts, h->stream),
      "reconstruct");
   if (!ref) return sync_and_status(h);

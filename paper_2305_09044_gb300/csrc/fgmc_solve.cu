@@ -7,30 +7,69 @@ namespace trd {
 
 // ------------------------------------------------------------------ FGMC factor
 // E[(a r + a'), (b r1 + b')] = sum_{i in sel} Z(i)[a, b] Z(i)[a', b']  (= sum Z(i) (x) Z(i)),
-// Z(i)[a, b] at i*K + b*r + a.  sel = idx[0..n) or 0..n-1 when idx is null.
-__global__ void k_fgmc_E(const double* __restrict__ Z, const int32_t* __restrict__ idx, int64_t n,
-                         int r, int r1, double* __restrict__ E) {
+// Z(i)[a, b] at i*K + b*r + a.  sel = idx[0..n) or 0..n-1 when idx is null.  Slices are
+// staged through shared memory in chunks of 32; each thread owns output entries.
+__global__ void k_fgmc_E(const double* __restrict__ Z, const int32_t* __restrict__ idx, int64_t n_all,
+                         int r, int r1, int CH, double* __restrict__ E) {
+  // slice range of this block row (gridDim.y parts, contiguous)
+  const int64_t per = (n_all + gridDim.y - 1) / gridDim.y;
+  const int64_t qb = (int64_t)blockIdx.y * per;
+  const int64_t n = imax(0, imin(n_all, qb + per) - qb);
+  if (idx) idx += qb;
+  Z += idx ? 0 : qb * (int64_t)(r * r1);
+  extern __shared__ double zs[];
   const int rows = r * r, cols = r1 * r1, K = r * r1;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)rows * cols;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int row = (int)(e / cols), col = (int)(e % cols);
+  const int64_t tot = (int64_t)rows * cols;
+  const int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = e0 < tot;
+  int o1 = 0, o2 = 0;
+  if (active) {
+    const int row = (int)(e0 / cols), col = (int)(e0 % cols);
     const int a = row / r, a2 = row % r, b = col / r1, b2 = col % r1;
-    const int o1 = b * r + a, o2 = b2 * r + a2;
-    double s = 0.0;
-    for (int64_t q = 0; q < n; ++q) {
-      const int64_t i = idx ? (int64_t)idx[q] : q;
-      const double* zi = Z + i * K;
-      s = fma(zi[o1], zi[o2], s);
+    o1 = b * r + a;
+    o2 = b2 * r + a2;
+  }
+  double s = 0.0;
+  for (int64_t q0 = 0; q0 < n; q0 += CH) {
+    const int cnt = (int)imin(CH, n - q0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * K; e += blockDim.x) {
+      const int qq = e / K, kk = e % K;
+      const int64_t i = idx ? (int64_t)idx[q0 + qq] : q0 + qq;
+      zs[e] = Z[i * K + kk];
     }
-    E[e] = s;
+    __syncthreads();
+    if (active)
+      for (int qq = 0; qq < cnt; ++qq) s = fma(zs[qq * K + o1], zs[qq * K + o2], s);
+  }
+  if (active) E[(int64_t)blockIdx.y * tot + e0] = s;
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int parts, int64_t n, double* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < parts; ++q) s += part[(int64_t)q * n + i];
+    out[i] = s;
   }
 }
 
 cudaError_t launch_fgmc_E(const double* Z, const int32_t* idx, int64_t n, int rk, int rk1,
-                          double* E, cudaStream_t st) {
+                          double* E, double* work, cudaStream_t st) {
   const int64_t tot = (int64_t)rk * rk * rk1 * rk1;
-  const unsigned blocks = (unsigned)imin((tot + 127) / 128, 4096);
-  k_fgmc_E<<<blocks, 128, 0, st>>>(Z, idx, n, rk, rk1, E);
+  const unsigned blocks = (unsigned)((tot + 127) / 128);
+  // enough slice parts to cover the SMs; partial factors go to `work` ([parts][tot])
+  int parts = (int)imax(1, imin(imin(n / 8, 16), (2 * 152 + blocks - 1) / blocks));
+  if (!work) parts = 1;
+  const int K = rk * rk1;
+  const int CH = (int)imax(1, imin(32, (160 * 1024) / (K * 8)));
+  const size_t smem = (size_t)CH * K * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_fgmc_E, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(blocks, (unsigned)parts);
+  k_fgmc_E<<<grid, 128, smem, st>>>(Z, idx, n, rk, rk1, CH, parts > 1 ? work : E);
+  note_launch();
+  if (parts == 1) return cudaGetLastError();
+  k_sum_parts<<<(unsigned)imin((tot + 255) / 256, 4096), 256, 0, st>>>(work, parts, tot, E);
   note_launch();
   return cudaGetLastError();
 }
@@ -85,55 +124,79 @@ cudaError_t launch_phi(const double* T, int p, int q, double* G, cudaStream_t st
 }
 
 // ------------------------------------------------------------------ Cholesky of G + lambda I
-// One CTA, right-looking, lower triangle.  lambda >= 0 absolute, < 0 relative to tr(G)/K.
-// A non-positive or non-finite pivot sets DEV_SINGULAR and stops (L is then unusable).
+// One CTA, right-looking, lower triangle in shared memory when it fits (K <= 160), else in
+// the output array.  lambda >= 0 absolute, < 0 relative to tr(G)/K.  Per column: every
+// thread reads the pivot, the sub-diagonal column is scaled into a buffer, then the
+// trailing lower triangle is updated (two barriers per column).  A non-positive or
+// non-finite pivot sets DEV_SINGULAR and stops (L is then unusable).
 __global__ void k_cholesky(const double* __restrict__ G, int K, double lam_in, double* __restrict__ L,
                            double* __restrict__ scal, int* __restrict__ dstatus, int use_smem) {
   extern __shared__ double smc[];
-  __shared__ double s_lam;
-  __shared__ int s_bad;
+  __shared__ double s_red[32];
+  __shared__ double s_col[1024];
   double* W = use_smem ? smc : L;
   const int tid = threadIdx.x, nt = blockDim.x;
+  // lambda (trace reduction in parallel)
+  double tr = 0.0;
+  for (int i = tid; i < K; i += nt) tr += G[(int64_t)i * K + i];
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_down_sync(0xffffffffu, tr, o);
+  if ((tid & 31) == 0) s_red[tid >> 5] = tr;
+  __syncthreads();
   if (tid == 0) {
-    double lam = lam_in;
-    if (lam < 0) {
-      double tr = 0.0;
-      for (int i = 0; i < K; ++i) tr += G[(int64_t)i * K + i];
-      lam = -lam_in * tr / K;
-    }
-    s_lam = lam;
-    s_bad = 0;
-    scal[5] = lam;
+    double t = 0.0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) t += s_red[w];
+    s_red[0] = lam_in >= 0 ? lam_in : -lam_in * t / K;
+    scal[5] = s_red[0];
   }
   __syncthreads();
-  const double lam = s_lam;
+  const double lam = s_red[0];
   for (int e = tid; e < K * K; e += nt) {
     const int i = e / K, j = e % K;
     W[e] = j <= i ? G[e] + (i == j ? lam : 0.0) : 0.0;
   }
   __syncthreads();
+  // pivot j's square root and reciprocal are computed once, by thread 0 (which owns the
+  // diagonal element of the trailing update), and published through shared memory
+  __shared__ double s_dj, s_rj;
+  __shared__ int s_bad;
+  if (tid == 0) {
+    const double piv = W[0];
+    s_bad = !(piv > 0.0) || !isfinite(piv);
+    s_dj = s_bad ? 1.0 : sqrt(piv);
+    s_rj = 1.0 / s_dj;
+  }
+  __syncthreads();
+  bool bad = false;
   for (int j = 0; j < K; ++j) {
+    if (s_bad) { bad = true; break; }                  // uniform across threads
+    const double dj = s_dj, rj = s_rj;
+    for (int i = j + 1 + tid; i < K; i += nt) s_col[i] = W[(int64_t)i * K + j] * rj;
+    __syncthreads();
     if (tid == 0) {
-      const double piv = W[(int64_t)j * K + j];
-      if (!(piv > 0.0) || !isfinite(piv)) s_bad = 1;
-      else W[(int64_t)j * K + j] = sqrt(piv);
+      W[(int64_t)j * K + j] = dj;
+      L[(int64_t)K * K + j] = rj;       // reciprocal diagonal, used by the solves
     }
-    __syncthreads();
-    if (s_bad) break;
-    const double dj = W[(int64_t)j * K + j];
-    for (int i = j + 1 + tid; i < K; i += nt) W[(int64_t)i * K + j] /= dj;
-    __syncthreads();
-    const int n = K - j - 1;
-    for (int e = tid; e < n * n; e += nt) {
-      const int ii = e / n, mm = e % n;
-      if (mm <= ii) {
-        const int i = j + 1 + ii, m = j + 1 + mm;
-        W[(int64_t)i * K + m] -= W[(int64_t)i * K + j] * W[(int64_t)m * K + j];
+    for (int i = j + 1 + tid; i < K; i += nt) W[(int64_t)i * K + j] = s_col[i];
+    // trailing lower triangle, 16 x 16 thread tile (blockDim 256): thread (ti, tm) updates
+    // rows i = j+1+ti+16a and columns m = j+1+tm+16b with m <= i
+    {
+      const int ti = tid >> 4, tm = tid & 15;
+      for (int i = j + 1 + ti; i < K; i += 16) {
+        const double li = s_col[i];
+        double* Wi = W + (int64_t)i * K;
+        for (int m = j + 1 + tm; m <= i; m += 16) Wi[m] -= li * s_col[m];
       }
+    }
+    if (tid == 0 && j + 1 < K) {
+      // thread 0 updated W[j+1][j+1] above: prepare the next pivot
+      const double piv = W[(int64_t)(j + 1) * K + (j + 1)];
+      s_bad = !(piv > 0.0) || !isfinite(piv);
+      s_dj = s_bad ? 1.0 : sqrt(piv);
+      s_rj = 1.0 / s_dj;
     }
     __syncthreads();
   }
-  if (s_bad) {
+  if (bad) {
     if (tid == 0) atomicOr(dstatus, (int)DEV_SINGULAR);
     return;
   }
@@ -146,30 +209,41 @@ cudaError_t launch_cholesky(const double* G, int K, double lambda, double* L, do
   const size_t bytes = (size_t)K * K * sizeof(double);
   const bool sm = bytes <= 200 * 1024;
   if (sm) cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k_cholesky<<<1, 1024, sm ? bytes : 0, st>>>(G, K, lambda, L, scal, dstatus, sm ? 1 : 0);
+  k_cholesky<<<1, 256, sm ? bytes : 0, st>>>(G, K, lambda, L, scal, dstatus, sm ? 1 : 0);
   note_launch();
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ h = d (G + lambda I)^{-1}
 // One warp per row of d: forward substitution with L, then back substitution with L^T.
-__global__ void k_solve_rows(const double* __restrict__ L, const double* __restrict__ d,
-                             double* __restrict__ h, int K, int64_t rows) {
+// L is staged in shared memory when it fits (K <= 160), so each substitution step costs a
+// shared-memory load instead of an L2 round trip.
+__global__ void k_solve_rows(const double* __restrict__ Lg, const double* __restrict__ d,
+                             double* __restrict__ h, int K, int64_t rows, int stage_L) {
   extern __shared__ double sb[];
   const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double* L = Lg;
+  const double* rdiag = Lg + (int64_t)K * K;
   double* b = sb + (size_t)w * K;
+  if (stage_L) {
+    double* Ls = sb + (size_t)warps * K;
+    for (int e = threadIdx.x; e < K * K + K; e += blockDim.x) Ls[e] = Lg[e];
+    __syncthreads();
+    L = Ls;
+    rdiag = Ls + (int64_t)K * K;
+  }
   for (int64_t row = (int64_t)blockIdx.x * warps + w; row < rows; row += (int64_t)gridDim.x * warps) {
     for (int m = lane; m < K; m += 32) b[m] = d[row * K + m];
     __syncwarp();
     for (int j = 0; j < K; ++j) {
-      const double yj = b[j] / L[(int64_t)j * K + j];
+      const double yj = b[j] * rdiag[j];
       __syncwarp();
       if (lane == 0) b[j] = yj;
       for (int m = j + 1 + lane; m < K; m += 32) b[m] -= L[(int64_t)m * K + j] * yj;
       __syncwarp();
     }
     for (int j = K - 1; j >= 0; --j) {
-      const double hj = b[j] / L[(int64_t)j * K + j];
+      const double hj = b[j] * rdiag[j];
       __syncwarp();
       if (lane == 0) b[j] = hj;
       for (int m = lane; m < j; m += 32) b[m] -= L[(int64_t)j * K + m] * hj;
@@ -182,12 +256,13 @@ __global__ void k_solve_rows(const double* __restrict__ L, const double* __restr
 
 cudaError_t launch_solve_rows(const double* L, const double* d, double* h, int K, int64_t rows,
                               cudaStream_t st) {
-  const int warps = 8;
-  const size_t smem = (size_t)warps * K * sizeof(double);
+  const int warps = 1;
+  const bool stage = (size_t)K * K * sizeof(double) <= 160 * 1024;
+  const size_t smem = (size_t)warps * K * sizeof(double) + (stage ? (size_t)(K * K + K) * sizeof(double) : 0);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_solve_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const unsigned blocks = (unsigned)imin((rows + warps - 1) / warps, 4096);
-  k_solve_rows<<<blocks, warps * 32, smem, st>>>(L, d, h, K, rows);
+  const unsigned blocks = (unsigned)imin((rows + warps - 1) / warps, 8192);
+  k_solve_rows<<<blocks, warps * 32, smem, st>>>(L, d, h, K, rows, stage ? 1 : 0);
   note_launch();
   return cudaGetLastError();
 }

@@ -1,6 +1,8 @@
 // Subchain merges (Def. 2 / Thm. 1), the back-contraction of the weighted contraction into
 // the gradient of one core (Eq. sd / Eq. hatd), RStS gather (Sec. 3.2.2), fixed-order
 // reductions and full reconstruction (Def. 1).
+#include <algorithm>
+
 #include "trd_internal.cuh"
 
 namespace trd {
@@ -9,14 +11,14 @@ namespace trd {
 // One warp per multi-index p: M = Z_{m0}(i_0) Z_{m1}(i_1) ... (Def. 2 core merging), built
 // in shared memory (FP64), then written row-major (transposed = false) or column-major
 // (transposed = true) into row p of `out` (stride ld).
-template <typename Tout>
+template <typename Tc, typename Tout>
 __global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_t ld, int cap) {
-  extern __shared__ double smem[];
+  extern __shared__ __align__(16) unsigned char smem_chain[];
   const int warps = blockDim.x >> 5;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* Mb = smem + (size_t)w * 3 * cap;
-  double* Mn = Mb + cap;
-  double* Zs = Mn + cap;
+  Tc* Mb = reinterpret_cast<Tc*>(smem_chain) + (size_t)w * 3 * cap;
+  Tc* Mn = Mb + cap;
+  Tc* Zs = Mn + cap;
   for (int64_t p = (int64_t)blockIdx.x * warps + w; p < ch.count; p += (int64_t)gridDim.x * warps) {
     int64_t rem = p;
     int64_t sl[kMaxN];
@@ -30,7 +32,7 @@ __global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_
       const double* z = ch.core[0] + sl[0] * (int64_t)(R0 * C);
       for (int e = lane; e < R0 * C; e += 32) {
         const int a = e % R0, b = e / R0;     // source is column-major within the slice
-        Mb[a * C + b] = z[e];
+        Mb[a * C + b] = (Tc)z[e];
       }
     }
     __syncwarp();
@@ -39,17 +41,17 @@ __global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_
       const double* z = ch.core[j] + sl[j] * (int64_t)(Rj * Cj);
       for (int e = lane; e < Rj * Cj; e += 32) {
         const int c = e % Rj, b = e / Rj;
-        Zs[c * Cj + b] = z[e];
+        Zs[c * Cj + b] = (Tc)z[e];
       }
       __syncwarp();
       for (int e = lane; e < R0 * Cj; e += 32) {
         const int a = e / Cj, b = e % Cj;
-        double acc = 0.0;
+        Tc acc = Tc(0);
         for (int c = 0; c < C; ++c) acc = fma(Mb[a * C + c], Zs[c * Cj + b], acc);
         Mn[e] = acc;
       }
       __syncwarp();
-      double* t = Mb; Mb = Mn; Mn = t;
+      Tc* t = Mb; Mb = Mn; Mn = t;
       C = Cj;
       __syncwarp();
     }
@@ -63,6 +65,7 @@ __global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_
   }
 }
 
+// out_double: FP64 products and output; otherwise FP32 products and output.
 cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool transposed,
                          int64_t ld, cudaStream_t st) {
   if (ch.n <= 0 || ch.count <= 0) return cudaSuccess;
@@ -72,20 +75,20 @@ cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool trans
     cap = max(cap, ch.rows[j] * ch.cols[j]);
   }
   const int warps = 4;
-  const size_t smem = (size_t)warps * 3 * cap * sizeof(double);
   int64_t blocks = (ch.count + warps - 1) / warps;
   if (blocks > 65535LL * 8) blocks = 65535LL * 8;
   if (out_double) {
+    const size_t smem = (size_t)warps * 3 * cap * sizeof(double);
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_chain<double><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (double*)out, transposed, ld, cap);
-    note_launch();
+      cudaFuncSetAttribute(k_chain<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_chain<double, double><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (double*)out, transposed, ld, cap);
   } else {
+    const size_t smem = (size_t)warps * 3 * cap * sizeof(float);
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_chain<float><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (float*)out, transposed, ld, cap);
-    note_launch();
+      cudaFuncSetAttribute(k_chain<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_chain<float, float><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (float*)out, transposed, ld, cap);
   }
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -96,67 +99,93 @@ cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool trans
 // (ROWS case: Ct[delta, gamma] = T[s][gamma r_c + delta]; COLS case: At[gamma, delta] =
 // T[s][gamma r_c + delta]) and s = pre + n_pre (i_k + I_k post).  Pre / Post are the
 // products of the cores between the block boundary and core k (identity when empty).
-__global__ void k_backcontract(const double* __restrict__ T, int Kp, int rows_case, int mr, int mc,
-                               const double* __restrict__ pre, int64_t n_pre,
-                               const double* __restrict__ post, int64_t n_post, int64_t Ik,
+template <typename T>
+__global__ void k_backcontract(const double* __restrict__ Tm, int Kp, int rows_case, int mr, int mc,
+                               const T* __restrict__ pre, int64_t n_pre,
+                               const T* __restrict__ post, int64_t n_post, int64_t Ik,
                                int rk, int rk1, int64_t pairs_per_split,
                                double* __restrict__ out) {
-  __shared__ double sM[kMaxR * kMaxR];
-  __shared__ double sPre[kMaxR * kMaxR];
-  __shared__ double sPost[kMaxR * kMaxR];
-  __shared__ double sV[kMaxR * kMaxR];
+  // one warp per (pre, post) pair; warp-private shared buffers, no block barriers in the
+  // pair loop; per-lane accumulators, summed over warps in a fixed order at the end
+  extern __shared__ __align__(16) unsigned char smem_bc[];
+  const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int szM = mr * mc, szPre = mc * rk, szPost = rk1 * mr, szV = mr * rk;
+  const int per_warp = szM + szPre + szPost + szV;
+  T* sM = reinterpret_cast<T*>(smem_bc) + (size_t)w * per_warp;
+  T* sPre = sM + szM;
+  T* sPost = sPre + szPre;
+  T* sV = sPost + szPost;
   const int64_t ik = blockIdx.x;
   const int K = rk * rk1;
   const int64_t npairs = n_pre * n_post;
   const int64_t q0 = (int64_t)blockIdx.y * pairs_per_split;
   const int64_t q1 = min(npairs, q0 + pairs_per_split);
-  double acc[8];
+  T acc[32];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) acc[u] = 0.0;
-  for (int64_t q = q0; q < q1; ++q) {
+  for (int u = 0; u < 32; ++u) acc[u] = T(0);
+  for (int64_t q = q0 + w; q < q1; q += warps) {
     const int64_t ip = q % n_pre, iq = q / n_pre;
     const int64_t s = ip + n_pre * (ik + Ik * iq);
-    const double* Ts = T + s * (int64_t)Kp;
-    __syncthreads();
-    for (int e = threadIdx.x; e < mr * mc; e += blockDim.x) {
+    const double* Ts = Tm + s * (int64_t)Kp;
+    for (int e = lane; e < szM; e += 32) {
       const int i = e / mc, j = e % mc;
-      sM[e] = rows_case ? Ts[j * mr + i] : Ts[i * mc + j];
+      sM[e] = (T)(rows_case ? Ts[j * mr + i] : Ts[i * mc + j]);
     }
     if (pre)
-      for (int e = threadIdx.x; e < mc * rk; e += blockDim.x) sPre[e] = pre[ip * (int64_t)(mc * rk) + e];
+      for (int e = lane; e < szPre; e += 32) sPre[e] = pre[ip * (int64_t)szPre + e];
     if (post)
-      for (int e = threadIdx.x; e < rk1 * mr; e += blockDim.x) sPost[e] = post[iq * (int64_t)(rk1 * mr) + e];
-    __syncthreads();
+      for (int e = lane; e < szPost; e += 32) sPost[e] = post[iq * (int64_t)szPost + e];
+    __syncwarp();
     // V = M * Pre  (mr x rk)
-    for (int e = threadIdx.x; e < mr * rk; e += blockDim.x) {
+    for (int e = lane; e < szV; e += 32) {
       const int i = e / rk, a = e % rk;
-      double v;
+      T v;
       if (pre) {
-        v = 0.0;
+        v = T(0);
         for (int j = 0; j < mc; ++j) v = fma(sM[i * mc + j], sPre[j * rk + a], v);
       } else {
         v = sM[i * mc + a];
       }
       sV[e] = v;
     }
-    __syncthreads();
-    // U = Post * V  (rk1 x rk); thread owns entries e = beta*rk + alpha
-    int u = 0;
-    for (int e = threadIdx.x; e < K; e += blockDim.x, ++u) {
-      const int b = e / rk, a = e % rk;
-      double v;
-      if (post) {
-        v = 0.0;
-        for (int i = 0; i < mr; ++i) v = fma(sPost[b * mr + i], sV[i * rk + a], v);
-      } else {
-        v = sV[b * rk + a];
+    __syncwarp();
+    // U = Post * V  (rk1 x rk); lane owns entries e = lane + 32 u (e = beta*rk + alpha)
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      const int e = lane + 32 * u;
+      if (e < K) {
+        const int b = e / rk, a = e % rk;
+        T v;
+        if (post) {
+          v = T(0);
+          for (int i = 0; i < mr; ++i) v = fma(sPost[b * mr + i], sV[i * rk + a], v);
+        } else {
+          v = sV[b * rk + a];
+        }
+        acc[u] += v;
       }
-      acc[u] += v;
     }
+    __syncwarp();
   }
-  int u = 0;
+  // fixed-order sum over the warps of the block (reuses the block's shared memory)
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(smem_bc);
   double* o = out + ((int64_t)blockIdx.y * Ik + ik) * K;
-  for (int e = threadIdx.x; e < K; e += blockDim.x, ++u) o[e] = acc[u];
+  for (int base = 0; base < K; base += 32 * 32) {
+    // stage this chunk of every warp's accumulators
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      const int e = lane + 32 * u;
+      if (e >= base && e < base + 1024 && e < K) red[w * 1024 + (e - base)] = (double)acc[u];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 1024 && base + e < K; e += blockDim.x) {
+      double sum = 0.0;
+      for (int ww = 0; ww < warps; ++ww) sum += red[ww * 1024 + e];
+      o[base + e] = sum;
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void k_sum_splits(const double* __restrict__ part, int nsplit, int64_t n,
@@ -170,16 +199,29 @@ __global__ void k_sum_splits(const double* __restrict__ part, int nsplit, int64_
 }
 
 cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int mr, int mc,
-                                const double* pre, int64_t n_pre, const double* post,
+                                const void* pre, int64_t n_pre, const void* post,
                                 int64_t n_post, int64_t Ik, int rk, int rk1, double* dpart,
-                                int nsplit, double* d, cudaStream_t st) {
+                                int nsplit, double* d, bool fp64, cudaStream_t st) {
   const int64_t npairs = n_pre * n_post;
   const int64_t per = (npairs + nsplit - 1) / nsplit;
   const int threads = 128;
   dim3 grid((unsigned)Ik, (unsigned)nsplit);
   double* target = nsplit == 1 ? d : dpart;
-  k_backcontract<<<grid, threads, 0, st>>>((const double*)Tsum_d, Kp, rows_case ? 1 : 0, mr, mc,
-                                           pre, n_pre, post, n_post, Ik, rk, rk1, per, target);
+  const int per_warp = mr * mc + mc * rk + rk1 * mr + mr * rk;
+  const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+  const size_t smem = std::max((size_t)(threads / 32) * per_warp * esz, (size_t)(threads / 32) * 1024 * sizeof(double));
+  if (smem > 48 * 1024) {
+    cudaFuncSetAttribute(k_backcontract<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_backcontract<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  if (fp64)
+    k_backcontract<double><<<grid, threads, smem, st>>>((const double*)Tsum_d, Kp, rows_case ? 1 : 0, mr, mc,
+                                                     (const double*)pre, n_pre, (const double*)post, n_post,
+                                                     Ik, rk, rk1, per, target);
+  else
+    k_backcontract<float><<<grid, threads, smem, st>>>((const double*)Tsum_d, Kp, rows_case ? 1 : 0, mr, mc,
+                                                    (const float*)pre, n_pre, (const float*)post, n_post,
+                                                    Ik, rk, rk1, per, target);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || nsplit == 1) return e;
@@ -209,22 +251,14 @@ cudaError_t launch_reduce_T(const void* Tpart, bool is_double, int splits, int64
   return cudaGetLastError();
 }
 
-// stat_part[c][8] -> stat_sum[8], fixed order (one block of 256 threads, strided partial
-// sums then a fixed tree).
+// stat_part[c][8] -> stat_sum[8], fixed order: warp f sums field f (lane-strided partial
+// sums, then a fixed shuffle tree).
 __global__ void k_reduce_stats(const double* __restrict__ part, int ctas, double* __restrict__ out) {
-  __shared__ double sh[256];
-  for (int f = 0; f < 8; ++f) {
-    double s = 0.0;
-    for (int c = threadIdx.x; c < ctas; c += blockDim.x) s += part[(int64_t)c * 8 + f];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[f] = sh[0];
-    __syncthreads();
-  }
+  const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int c = lane; c < ctas; c += 32) s += part[(int64_t)c * 8 + f];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) out[f] = s;
 }
 
 cudaError_t launch_reduce_stats(const double* stat_part, int ctas, double* stat_sum,
@@ -237,7 +271,8 @@ cudaError_t launch_reduce_stats(const double* stat_part, int ctas, double* stat_
 // ------------------------------------------------------------------ reconstruction
 // out(a, b) = sum_kappa A[a][kappa] C[b][kappa] = Tr(A(a) C(b)) (Def. 1 via Thm. 1's split);
 // optional comparison with a reference tensor accumulates sum (xhat - ref)^2 and sum ref^2.
-__global__ void k_reconstruct(const double* __restrict__ A, const double* __restrict__ C,
+template <typename T>
+__global__ void k_reconstruct(const T* __restrict__ A, const T* __restrict__ C,
                               int64_t P_in, int64_t P_out, int Kp, const float* __restrict__ ref,
                               float* __restrict__ out, double* __restrict__ err_part) {
   __shared__ double sh[2][256];
@@ -246,14 +281,15 @@ __global__ void k_reconstruct(const double* __restrict__ A, const double* __rest
   for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
        l += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = l % P_in, b = l / P_in;
-    const double* Ar = A + a * Kp;
-    const double* Cr = C + b * Kp;
-    double v = 0.0;
+    const T* Ar = A + a * Kp;
+    const T* Cr = C + b * Kp;
+    T v = T(0);
     for (int k = 0; k < Kp; ++k) v = fma(Ar[k], Cr[k], v);
     if (out) out[l] = (float)v;
     if (ref) {
       const double r = (double)ref[l];
-      se += (v - r) * (v - r);
+      const double dv = (double)v - r;
+      se += dv * dv;
       sr += r * r;
     }
   }
@@ -274,10 +310,15 @@ __global__ void k_reconstruct(const double* __restrict__ A, const double* __rest
   }
 }
 
-cudaError_t launch_reconstruct_mats(const double* A, const double* C, int64_t P_in, int64_t P_out,
+cudaError_t launch_reconstruct_mats(const void* A, const void* C, bool fp64, int64_t P_in, int64_t P_out,
                                     int Kp, const float* Xref, float* out, double* err_part,
                                     int parts, cudaStream_t st) {
-  k_reconstruct<<<parts, 256, 0, st>>>(A, C, P_in, P_out, Kp, Xref, out, err_part);
+  if (fp64)
+    k_reconstruct<double><<<parts, 256, 0, st>>>((const double*)A, (const double*)C, P_in, P_out, Kp, Xref, out,
+                                                 err_part);
+  else
+    k_reconstruct<float><<<parts, 256, 0, st>>>((const float*)A, (const float*)C, P_in, P_out, Kp, Xref, out,
+                                                err_part);
   note_launch();
   return cudaGetLastError();
 }

@@ -91,6 +91,53 @@ __global__ void k_probe_resid(const double* const* __restrict__ Zp, int N, const
   }
 }
 
+// Residual at probe m from the merged subchains of the full tensor: with the modes cut into
+// an inner block (linear index a) and an outer block (b), x_hat = Tr(A(a) C(b)) =
+// sum_kappa A[a][kappa] C[b][kappa] (Thm. 1 with the ring cut in two).
+template <typename T>
+__global__ void k_probe_merged(const T* __restrict__ A, const T* __restrict__ C, int Kp, int64_t P_in,
+                               const float* __restrict__ X, const uint32_t* __restrict__ M, int64_t numel,
+                               int full, int64_t n, double* __restrict__ vals, uint64_t* __restrict__ keys,
+                               double* __restrict__ xsq) {
+  // one warp per group of 32 probes: lane m owns probe m of the group (index, data, output);
+  // the 32 dot products are computed cooperatively with coalesced row loads
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; g0 < n; g0 += warps * 32) {
+    const int64_t m = g0 + lane;
+    const bool live = m < n;
+    const int64_t lin = !live ? 0 : (full ? m : (int64_t)(sm64(kProbeSeed, (uint64_t)m) % (uint64_t)numel));
+    const bool obs = live && (M ? ((M[lin >> 5] >> (lin & 31)) & 1u) : true);
+    const float xf = live ? X[lin] : 0.f;
+    const int64_t a = lin % P_in, b = lin / P_in;
+    T mine = T(0);
+    for (int q = 0; q < 32; ++q) {
+      const int64_t aq = __shfl_sync(0xffffffffu, a, q), bq = __shfl_sync(0xffffffffu, b, q);
+      const T* Ar = A + aq * Kp;
+      const T* Cr = C + bq * Kp;
+      T part = T(0);
+      for (int k = lane; k < Kp; k += 32) part = fma(Ar[k], Cr[k], part);
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == q) mine = part;
+    }
+    if (!live) continue;
+    double val = 0.0, xs = 0.0;
+    uint64_t key = kExcluded;
+    if (obs) {
+      const T x = (T)xf;
+      const T e = x - mine;
+      if (isfinite((double)e)) {
+        val = (double)e;
+        key = dkey(val);
+        xs = (double)x * (double)x;
+      }
+    }
+    vals[m] = key == kExcluded ? 0.0 : val;
+    keys[m] = key;
+    xsq[m] = xs;
+  }
+}
+
 __global__ void k_float_keys(const float* __restrict__ r, int64_t n, double* __restrict__ vals,
                              uint64_t* __restrict__ keys, double* __restrict__ xsq) {
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n;
@@ -133,8 +180,16 @@ __global__ void k_probe_sums(const double* __restrict__ vals, const uint64_t* __
 // (as uint64 bits), hist at work + 64 as unsigned long long [4][256], parts at work + 64 + 1024.
 __global__ void k_finish_sums(const double* __restrict__ parts, int nb, double* __restrict__ work,
                               int second) {
+  // one warp: fixed-order strided partial sums, then a fixed shuffle tree
+  const int lane = threadIdx.x;
   double c = 0, s = 0, q = 0;
-  for (int b = 0; b < nb; ++b) { c += parts[b * 3]; s += parts[b * 3 + 1]; q += parts[b * 3 + 2]; }
+  for (int b = lane; b < nb; b += 32) { c += parts[b * 3]; s += parts[b * 3 + 1]; q += parts[b * 3 + 2]; }
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_down_sync(0xffffffffu, c, o);
+    s += __shfl_down_sync(0xffffffffu, s, o);
+    q += __shfl_down_sync(0xffffffffu, q, o);
+  }
+  if (lane != 0) return;
   if (!second) {
     work[0] = c;
     work[1] = c > 0 ? s / c : 0.0;
@@ -186,21 +241,36 @@ __global__ void k_select_hist(const uint64_t* __restrict__ keys, int64_t n, doub
   }
 }
 
+// One warp per target: inclusive scan of the 256 bin counts (8 per lane), find the bin
+// holding the target rank, narrow the prefix; then clear the histogram.
 __global__ void k_select_pick(double* __restrict__ work, int shift) {
-  const int t = threadIdx.x;
+  const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint64_t* u = reinterpret_cast<uint64_t*>(work);
   unsigned long long* gh = reinterpret_cast<unsigned long long*>(work + 64);
   if (t < 4) {
-    uint64_t rank = u[8 + t];
-    unsigned long long cum = 0;
-    int bin = 255;
-    for (int b = 0; b < 256; ++b) {
-      const unsigned long long c = gh[t * 256 + b];
-      if (cum + c > rank) { bin = b; break; }
-      cum += c;
+    const uint64_t rank = u[8 + t];
+    unsigned long long c[8], loc = 0;
+    for (int i = 0; i < 8; ++i) { c[i] = gh[t * 256 + lane * 8 + i]; loc += c[i]; }
+    unsigned long long incl = loc;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
     }
-    u[8 + t] = rank - cum;
-    u[12 + t] |= ((uint64_t)bin) << shift;
+    const unsigned long long excl = incl - loc;
+    // the lane whose range [excl, incl) holds the rank finds the bin
+    const bool mine = rank >= excl && rank < incl;
+    const unsigned who = __ballot_sync(0xffffffffu, mine);
+    if (mine) {
+      unsigned long long cum = excl;
+      int bin = lane * 8 + 7;
+      for (int i = 0; i < 8; ++i) {
+        if (cum + c[i] > rank) { bin = lane * 8 + i; break; }
+        cum += c[i];
+      }
+      u[8 + t] = rank - cum;
+      u[12 + t] |= ((uint64_t)bin) << shift;
+    }
+    (void)who;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 1024; i += blockDim.x) gh[i] = 0;
@@ -236,11 +306,11 @@ cudaError_t finish_sigma(const double* vals, const uint64_t* keys, const double*
   double* parts = work + 64 + 1024;
   k_probe_sums<<<nb, 256, 0, st>>>(vals, keys, xsq, n, nullptr, parts);
   note_launch();
-  k_finish_sums<<<1, 1, 0, st>>>(parts, nb, work, 0);
+  k_finish_sums<<<1, 32, 0, st>>>(parts, nb, work, 0);
   note_launch();
   k_probe_sums<<<nb, 256, 0, st>>>(vals, keys, xsq, n, work + 1, parts);
   note_launch();
-  k_finish_sums<<<1, 1, 0, st>>>(parts, nb, work, 1);
+  k_finish_sums<<<1, 32, 0, st>>>(parts, nb, work, 1);
   note_launch();
   k_select_init<<<1, 1, 0, st>>>(work);
   note_launch();
@@ -272,6 +342,25 @@ cudaError_t launch_probe_sigma(const double* const* Zdev_ptrs, int N, const int6
     k_probe_resid<double><<<blocks, 128, 0, st>>>(Zdev_ptrs, N, dim_dev, R_dev, X, M, numel, full, n, vals, keys, xsq);
   else
     k_probe_resid<float><<<blocks, 128, 0, st>>>(Zdev_ptrs, N, dim_dev, R_dev, X, M, numel, full, n, vals, keys, xsq);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return finish_sigma(vals, keys, xsq, n, -1.0, sigma_prev, sigma_prev_dev, work, sigma_out, st);
+}
+
+cudaError_t launch_probe_sigma_merged(const void* A, const void* C, bool fp64, int Kp, int64_t P_in,
+                                      const float* X, const uint32_t* M, int64_t numel, double sigma_prev,
+                                      const double* sigma_prev_dev, double* vals, uint64_t* keys, double* xsq,
+                                      double* work, double* sigma_out, cudaStream_t st) {
+  const bool full = numel <= kProbeMax;
+  const int64_t n = full ? numel : kProbeMax;
+  const unsigned blocks = (unsigned)imin((n + 255) / 256, 152 * 8);
+  if (fp64)
+    k_probe_merged<double><<<blocks, 256, 0, st>>>((const double*)A, (const double*)C, Kp, P_in, X, M, numel, full, n,
+                                                   vals, keys, xsq);
+  else
+    k_probe_merged<float><<<blocks, 256, 0, st>>>((const float*)A, (const float*)C, Kp, P_in, X, M, numel, full, n,
+                                                  vals, keys, xsq);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -166,14 +166,14 @@ trd_status ensure(trd_handle* h, DevBuf& b, size_t bytes);
 cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool transposed,
                          int64_t ld, cudaStream_t st);
 cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int mr, int mc,
-                                const double* pre, int64_t n_pre, const double* post,
+                                const void* pre, int64_t n_pre, const void* post,
                                 int64_t n_post, int64_t Ik, int rk, int rk1, double* dpart,
-                                int nsplit, double* d, cudaStream_t st);
+                                int nsplit, double* d, bool fp64, cudaStream_t st);
 cudaError_t launch_reduce_T(const void* Tpart, bool is_double, int splits, int64_t n,
                             double* Tsum, cudaStream_t st);
 cudaError_t launch_reduce_stats(const double* stat_part, int ctas, double* stat_sum,
                                 int* dstatus, cudaStream_t st);
-cudaError_t launch_reconstruct_mats(const double* A, const double* C, int64_t P_in, int64_t P_out,
+cudaError_t launch_reconstruct_mats(const void* A, const void* C, bool fp64, int64_t P_in, int64_t P_out,
                                     int Kp, const float* Xref, float* out, double* err_part,
                                     int parts, cudaStream_t st);
 cudaError_t launch_gather(const float* X, const uint32_t* M, int N, const int64_t* full_dim,
@@ -209,7 +209,7 @@ cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi
 
 // fgmc_solve.cu
 cudaError_t launch_fgmc_E(const double* Z, const int32_t* idx, int64_t n, int rk, int rk1,
-                          double* E, cudaStream_t st);
+                          double* E, double* work, cudaStream_t st);
 cudaError_t launch_dgemm(const double* A, const double* B, double* C, int M, int N, int K,
                          bool transB, cudaStream_t st);
 cudaError_t launch_phi(const double* T, int p, int q, double* G, cudaStream_t st);
@@ -233,6 +233,10 @@ cudaError_t launch_probe_sigma(const double* const* Zdev_ptrs, int N, const int6
                                bool fp64, double sigma_prev, const double* sigma_prev_dev,
                                double* vals, uint64_t* keys, double* xsq, double* work,
                                double* sigma_out, cudaStream_t st);
+cudaError_t launch_probe_sigma_merged(const void* A, const void* C, bool fp64, int Kp, int64_t P_in,
+                                      const float* X, const uint32_t* M, int64_t numel, double sigma_prev,
+                                      const double* sigma_prev_dev, double* vals, uint64_t* keys, double* xsq,
+                                      double* work, double* sigma_out, cudaStream_t st);
 cudaError_t launch_sigma_from_floats(const float* r, int64_t n, double x_obs_rms, double sigma_prev,
                                      double* vals, uint64_t* keys, double* xsq, double* work,
                                      double* sigma_out, cudaStream_t st);
