@@ -368,7 +368,7 @@ PassArgs pass_args(trd_handle* h) {
   return a;
 }
 
-trd_status run_pass1_tc(trd_handle* h, int k) {
+trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
   const Split& sp = h->split;
   Extra* x = X_(h);
   const int KP = tc_kpad();
@@ -400,11 +400,10 @@ trd_status run_pass1_tc(trd_handle* h, int k) {
   TRY(ensure(h, x->bSlo, b2 * sp.P_stat * KP));
   TRY(ensure(h, x->bThi, b2 * sp.P_strm * KP));
   TRY(ensure(h, x->bTlo, b2 * sp.P_strm * KP));
-  TRY(ensure(h, x->bTT, b2 * KP * ldT));
   CK(launch_tc_prep((const float*)h->Sst.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bShi.p,
-                    (__nv_bfloat16*)x->bSlo.p, nullptr, 0, h->stream), "bf16 stationary operands");
+                    (__nv_bfloat16*)x->bSlo.p, h->stream), "bf16 stationary operands");
   CK(launch_tc_prep((const float*)h->Sstr.p, sp.P_strm, sp.Kp, (__nv_bfloat16*)x->bThi.p,
-                    (__nv_bfloat16*)x->bTlo.p, (__nv_bfloat16*)x->bTT.p, ldT, h->stream), "bf16 streaming operands");
+                    (__nv_bfloat16*)x->bTlo.p, h->stream), "bf16 streaming operands");
   const int64_t RB = (sp.P_stat + tc_bm() - 1) / tc_bm();
   const int64_t NT = (sp.P_strm + tc_bn() - 1) / tc_bn();
   const int G = (int)imin(h->num_sms, RB * NT);
@@ -414,9 +413,9 @@ trd_status run_pass1_tc(trd_handle* h, int k) {
   TRY(ensure(h, h->Tsum, sizeof(double) * (size_t)sp.P_stat * sp.Kp));
   prof_begin(h);
   CK(launch_pass_tc(sp.rows, false, (const __nv_bfloat16*)x->bShi.p, (const __nv_bfloat16*)x->bSlo.p, nullptr,
-                    (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p, (const __nv_bfloat16*)x->bTT.p,
-                    ldT, v.X, sp.P_in, sp.P_out, (const uint32_t*)x->Mst[o].p, W, sp.P_stat, sp.P_strm, sp.Kp,
-                    h->scal + S_SIGMA, (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, G, h->stream),
+                    (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p, v.X, sp.P_in, sp.P_out, (const uint32_t*)x->Mst[o].p, W, sp.P_stat, sp.P_strm, sp.Kp,
+                    h->scal + S_SIGMA, (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, G, full_stats,
+                    h->stream),
      "tensor-core data pass 1");
   prof_end(h, 0);
   CK(launch_reduce_slots((const float*)h->Tpart.p, RB, NT, G, sp.P_stat, sp.Kp, (double*)h->Tsum.p, h->stream),
@@ -432,14 +431,14 @@ trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
   Extra* x = X_(h);
   TRY(build_merged(h, k, true));
   TRY(ensure(h, x->bSh, sizeof(__nv_bfloat16) * sp.P_stat * tc_kpad()));
-  CK(launch_tc_prep((const float*)h->Sh.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bSh.p, nullptr, nullptr, 0,
-                    h->stream), "bf16 step operands");
+  CK(launch_tc_prep((const float*)h->Sh.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bSh.p, nullptr, h->stream),
+     "bf16 step operands");
   prof_begin(h);
   CK(launch_pass_tc(sp.rows, true, (const __nv_bfloat16*)x->bShi.p, (const __nv_bfloat16*)x->bSlo.p,
                     (const __nv_bfloat16*)x->bSh.p, (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p,
-                    (const __nv_bfloat16*)x->bTT.p, x->ldT, h->view.X, sp.P_in, sp.P_out,
+                    h->view.X, sp.P_in, sp.P_out,
                     (const uint32_t*)x->Mst[x->mst_o].p, x->W, sp.P_stat, sp.P_strm, sp.Kp, h->scal + S_SIGMA,
-                    (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, x->tcG, h->stream),
+                    (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, x->tcG, false, h->stream),
      "tensor-core data pass 2");
   prof_end(h, 1);
   double* s2 = (double*)x->stat_sum2.p;
@@ -448,11 +447,11 @@ trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
   return TRD_OK;
 }
 
-trd_status run_pass1(trd_handle* h, int k) {
+trd_status run_pass1(trd_handle* h, int k, bool full_stats = true) {
   h->split = choose_split(h, h->view, k);
   const Split& sp = h->split;
   if (h->prec == TRD_BF16) {
-    TRY(run_pass1_tc(h, k));
+    TRY(run_pass1_tc(h, k, full_stats));
   } else {
     if (sp.Kp > 112 && is_fp64(h)) return set_err(h, TRD_ENOTIMPL, "FP64 path supports r_1 r_c <= 112");
     if (sp.Kp > 256) return set_err(h, TRD_ENOTIMPL, "data passes support r_1 r_c <= 256");
@@ -1073,7 +1072,7 @@ trd_status trd_step(trd_t* h, const trd_params* p, trd_report* rep) {
     } else if (h->sketched) {
       use_full_view(h);
     }
-    TRY(run_pass1(h, k));
+    TRY(run_pass1(h, k, false));
     CK(cudaMemcpyAsync(h->report_dev + R_OBJ + k, (double*)h->stat_sum.p + 2, sizeof(double),
                        cudaMemcpyDeviceToDevice, h->stream), "objective");
     TRY(run_gradient(h, k));

@@ -30,21 +30,24 @@ namespace tc {
 constexpr int BM = 128;        // UMMA M: stationary rows per block
 constexpr int BN = 64;         // streaming columns per tile
 constexpr int KPAD = 64;       // padded contraction length (one 128-byte swizzle atom)
-constexpr int STAGES = 3;
-constexpr int NEPI = 8;                    // epilogue warps: 4 TMEM lane quarters x 2 column halves
-constexpr int NTHREADS = 64 + 32 * NEPI;   // producer warp, MMA warp, epilogue warps
+constexpr int XS = 4;          // data-tile stages (released by the epilogue once read)
+constexpr int TS = 3;          // streaming-operand stages (released by the MMA commits)
+constexpr int NEPI = 8;        // epilogue warps: 4 TMEM lane quarters x NGRP column groups
+constexpr int NGRP = NEPI / 4;
+constexpr int CPW = BN / NGRP; // columns of a tile handled by one epilogue warp
+constexpr int NTHREADS = 64 + 32 * NEPI + 32;   // operand producer, MMA, epilogue, data producer
 constexpr int EPI_THREADS = 32 * NEPI;
+constexpr int XWARP = 2 + NEPI;                 // warp index of the data producer
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
 // shared-memory carve-up (bytes, every buffer 1024-aligned)
 constexpr int S_TILE = BM * KPAD * 2;          // 16 KB: one stationary operand
 constexpr int X_TILE = BN * BM * 4;            // 32 KB: one data tile
 constexpr int T_TILE = BN * KPAD * 2;          // 8 KB: one streaming operand
-constexpr int TT_TILE = KPAD * BN * 2;         // 8 KB: streaming operand, transposed
 constexpr int Y_TILE = BM * BN * 2;            // 16 KB: weighted residuals (A of GEMM 2)
 
 struct Layout {
-  int s_hi, s_lo, s_h, stage0, stage_bytes, x_off, thi_off, tlo_off, tt_off, m_off, y, bars, total;
+  int s_hi, s_lo, s_h, x0, t0, y, bars, total;
 };
 
 __host__ __device__ constexpr Layout layout(bool pass2) {
@@ -53,14 +56,8 @@ __host__ __device__ constexpr Layout layout(bool pass2) {
   L.s_hi = o; o += S_TILE;
   L.s_lo = o; o += S_TILE;
   L.s_h = o; if (pass2) o += S_TILE;
-  L.stage0 = o;
-  L.x_off = 0;
-  L.thi_off = X_TILE;
-  L.tlo_off = X_TILE + T_TILE;
-  L.tt_off = X_TILE + 2 * T_TILE;
-  L.m_off = 0;
-  L.stage_bytes = X_TILE + 2 * T_TILE + (pass2 ? 0 : TT_TILE);
-  o += STAGES * L.stage_bytes;
+  L.x0 = o; o += XS * X_TILE;
+  L.t0 = o; o += TS * 2 * T_TILE;      // per stage: hi tile then lo tile
   L.y = o; if (!pass2) o += Y_TILE;
   L.bars = o; o += 1024;
   L.total = o;
@@ -73,7 +70,7 @@ struct Params {
   int64_t RB, NT, U;         // stationary blocks, streaming tiles, units
   int G;                     // CTAs
   const uint32_t* Mst;       // mask bits of each stationary index along the streaming index
-  int64_t W;                 // words per mask row (multiple of 4)
+  int64_t W;                 // words per mask row
   const double* sigma;
   float* Tpart;              // [G + RB][BM][Kp]
   double* stat_part;         // [G][8]
@@ -147,6 +144,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+// columns-per-warp dispatch
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
+  if constexpr (N == 32) tmem_ld32(taddr, v);
+  else tmem_ld16(taddr, v);
+}
+
 // UMMA shared-memory descriptor: K-major, SWIZZLE_128B (8-row groups 1024 B apart).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
@@ -155,9 +170,22 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;             // SWIZZLE_128B
   return d;
 }
-// Instruction descriptor, kind::f16: D FP32, A/B BF16, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// UMMA shared-memory descriptor: MN-major, SWIZZLE_128B.  64 MN-contiguous elements per
+// 128-byte row, one row per K index, 8-row groups 1024 B apart (stride byte offset), and
+// 64-wide MN blocks `lbo` bytes apart (leading byte offset).
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor, kind::f16: D FP32, A/B BF16, A K-major, B K-major (b_mn = 0) or
+// MN-major (b_mn = 1), M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int b_mn = 0) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)b_mn << 16) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
 // 2^x on the special-function unit (ex2.approx, flush-to-zero); the weight needs only
@@ -174,28 +202,29 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 // ------------------------------------------------------------------ the kernel
-template <bool ROWS, bool PASS2>
+template <bool ROWS, bool PASS2, bool FULL>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_pass_tc(const __grid_constant__ CUtensorMap mS_hi, const __grid_constant__ CUtensorMap mS_lo,
               const __grid_constant__ CUtensorMap mS_h, const __grid_constant__ CUtensorMap mT_hi,
-              const __grid_constant__ CUtensorMap mT_lo, const __grid_constant__ CUtensorMap mTT,
-              const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mM,
+              const __grid_constant__ CUtensorMap mT_lo, const __grid_constant__ CUtensorMap mX,
               const Params p) {
   constexpr Layout L = layout(PASS2);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // align the dynamic window to 1024 bytes (the launcher over-allocates by 1 KB)
   unsigned char* sm = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L.bars);
-  uint64_t* full = bars;                  // [STAGES]
-  uint64_t* empty = bars + STAGES;        // [STAGES]
-  uint64_t* d_full = bars + 2 * STAGES;   // [2]
-  uint64_t* d_empty = d_full + 2;         // [2]
-  uint64_t* y_full = d_empty + 2;
-  uint64_t* y_empty = y_full + 1;
-  uint64_t* s_full = y_empty + 1;
-  uint64_t* s_empty = s_full + 1;
-  uint64_t* acc_full = s_empty + 1;
-  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* x_full = bars;                // [XS]  data tile landed (TMA)
+  uint64_t* x_empty = x_full + XS;        // [XS]  data tile read by every epilogue thread
+  uint64_t* t_full = x_empty + XS;        // [TS]  streaming operands landed (TMA)
+  uint64_t* t_empty = t_full + TS;        // [TS]  streaming operands consumed (MMA commit)
+  uint64_t* d_full = t_empty + TS;        // [2]   GEMM 1 (and the h product) done
+  uint64_t* d_empty = d_full + 2;         // [2]   accumulators read by the epilogue
+  uint64_t* y_full = d_empty + 2;         //       Y written
+  uint64_t* y_empty = y_full + 1;         //       GEMM 2 consumed Y
+  uint64_t* s_full = y_empty + 1;         //       stationary operands landed
+  uint64_t* s_empty = s_full + 1;         //       segment's MMAs done with them
+  uint64_t* acc_full = s_empty + 1;       //       segment's contraction complete
+  uint64_t* acc_empty = acc_full + 1;     //       contraction drained to global
   uint64_t* mma_done = acc_empty + 1;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(mma_done + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 2);
@@ -206,9 +235,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int64_t u_begin = c * p.U / p.G, u_end = (c + 1) * p.U / p.G;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1 + EPI_THREADS);
+    for (int s = 0; s < XS; ++s) {
+      mbar_init(&x_full[s], 1);
+      mbar_init(&x_empty[s], EPI_THREADS);
+    }
+    for (int s = 0; s < TS; ++s) {
+      mbar_init(&t_full[s], 1);
+      mbar_init(&t_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&d_full[b], 1);
@@ -239,13 +272,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t col_acc = 2u * BN;
 
   if (warp == 0) {
-    // ---------------------------------------------------------------- TMA producer
+    // ---------------------------------------------------------------- operand producer
     if (lane == 0) {
       int64_t it = 0;
       int g = 0;
       bool ok = true;
-      int last_phase[STAGES];
-      for (int s = 0; s < STAGES; ++s) last_phase[s] = -1;
+      int last_phase[TS];
+      for (int s = 0; s < TS; ++s) last_phase[s] = -1;
       int s_phase = -1;
       for (int64_t u = u_begin; u < u_end && ok; ++g) {
         const int64_t rb = u / p.NT;
@@ -258,40 +291,60 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tma_2d(sm + L.s_lo, &mS_lo, s_full, 0, (int)(rb * BM));
         if (PASS2) tma_2d(sm + L.s_h, &mS_h, s_full, 0, (int)(rb * BM));
         for (; u < seg_end; ++u, ++it) {
-          const int s = (int)(it % STAGES);
-          if (!mbar_wait(&empty[s], (uint32_t)(((it / STAGES) & 1) ^ 1), abort_flag)) { ok = false; break; }
+          const int s = (int)(it % TS);
+          if (!mbar_wait(&t_empty[s], (uint32_t)(((it / TS) & 1) ^ 1), abort_flag)) { ok = false; break; }
           const int t0 = (int)((u % p.NT) * BN);
-          unsigned char* st = sm + L.stage0 + s * L.stage_bytes;
-          const uint32_t bytes = X_TILE + 2 * T_TILE + (PASS2 ? 0 : TT_TILE);
-          mbar_expect_tx(&full[s], bytes);
-          last_phase[s] = (int)((it / STAGES) & 1);
-          tma_2d(st + L.thi_off, &mT_hi, &full[s], 0, t0);
-          tma_2d(st + L.tlo_off, &mT_lo, &full[s], 0, t0);
-          if (!PASS2) tma_2d(st + L.tt_off, &mTT, &full[s], t0, 0);
-          if (ROWS) {
-            tma_2d(st + L.x_off, &mX, &full[s], (int)(rb * BM), t0);
-          } else {
-            tma_2d(st + L.x_off, &mX, &full[s], t0, (int)(rb * BM));
-            tma_2d(st + L.x_off + X_TILE / 2, &mX, &full[s], t0 + 32, (int)(rb * BM));
-          }
+          unsigned char* tb = sm + L.t0 + s * 2 * T_TILE;
+          mbar_expect_tx(&t_full[s], 2 * T_TILE);
+          last_phase[s] = (int)((it / TS) & 1);
+          tma_2d(tb, &mT_hi, &t_full[s], 0, t0);
+          tma_2d(tb + T_TILE, &mT_lo, &t_full[s], 0, t0);
         }
       }
       if (!ok) {
         // drain: wait (bounded) for the last copies issued into every buffer
-        for (int s = 0; s < STAGES; ++s)
+        for (int s = 0; s < TS; ++s)
           if (last_phase[s] >= 0)
             for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
-              if (mbar_try(&full[s], (uint32_t)last_phase[s])) break;
+              if (mbar_try(&t_full[s], (uint32_t)last_phase[s])) break;
         if (s_phase >= 0)
           for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
             if (mbar_try(s_full, (uint32_t)s_phase)) break;
       }
     }
+  } else if (warp == XWARP) {
+    // ---------------------------------------------------------------- data producer
+    if (lane == 0) {
+      int64_t it = 0;
+      bool ok = true;
+      int last_phase[XS];
+      for (int s = 0; s < XS; ++s) last_phase[s] = -1;
+      for (int64_t u = u_begin; u < u_end; ++u, ++it) {
+        const int s = (int)(it % XS);
+        if (!mbar_wait(&x_empty[s], (uint32_t)(((it / XS) & 1) ^ 1), abort_flag)) { ok = false; break; }
+        const int64_t rb = u / p.NT;
+        const int t0 = (int)((u % p.NT) * BN);
+        unsigned char* xb = sm + L.x0 + s * X_TILE;
+        mbar_expect_tx(&x_full[s], X_TILE);
+        last_phase[s] = (int)((it / XS) & 1);
+        if (ROWS) {
+          tma_2d(xb, &mX, &x_full[s], (int)(rb * BM), t0);
+        } else {
+          tma_2d(xb, &mX, &x_full[s], t0, (int)(rb * BM));
+          tma_2d(xb + X_TILE / 2, &mX, &x_full[s], t0 + 32, (int)(rb * BM));
+        }
+      }
+      if (!ok)
+        for (int s = 0; s < XS; ++s)
+          if (last_phase[s] >= 0)
+            for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+              if (mbar_try(&x_full[s], (uint32_t)last_phase[s])) break;
+    }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       constexpr uint32_t ID1 = idesc_bf16(BM, BN);
-      constexpr uint32_t ID2 = idesc_bf16(BM, KPAD);
+      constexpr uint32_t ID2 = idesc_bf16(BM, KPAD, 1);    // B = streaming tile, MN-major
       const uint32_t a_hi = su32(sm + L.s_hi), a_lo = su32(sm + L.s_lo), a_h = su32(sm + L.s_h);
       const uint32_t ybuf = su32(sm + L.y);
       int64_t it = 0;
@@ -305,12 +358,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         int64_t prev = -1;        // tile whose GEMM 2 is pending
         bool first2 = true;
         for (; u < seg_end; ++u, ++it) {
-          const int s = (int)(it % STAGES), b = (int)(it & 1);
-          if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), abort_flag)) { ok = false; break; }
+          const int s = (int)(it % TS), b = (int)(it & 1);
+          if (!mbar_wait(&t_full[s], (uint32_t)((it / TS) & 1), abort_flag)) { ok = false; break; }
           if (!mbar_wait(&d_empty[b], (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t st = su32(sm + L.stage0 + s * L.stage_bytes);
-          const uint32_t b_hi = st + L.thi_off, b_lo = st + L.tlo_off;
+          const uint32_t b_hi = su32(sm + L.t0 + s * 2 * T_TILE), b_lo = b_hi + T_TILE;
           for (int kk = 0; kk < KPAD / 16; ++kk) {
             const uint32_t ko = kk * 32;
             tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_hi + ko), sdesc(b_hi + ko), ID1, kk > 0);
@@ -320,23 +372,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           tc_commit(&d_full[b]);
           if (PASS2) {
-            tc_commit(&empty[s]);
+            tc_commit(&t_empty[s]);
             continue;
           }
           if (prev >= 0) {
-            // GEMM 2 of the previous tile: T += Y * S_str (B = transposed streaming tile)
-            if (first2) {
-              if (g > 0 && !mbar_wait(acc_empty, (uint32_t)((g - 1) & 1), abort_flag)) { ok = false; break; }
-            }
+            // GEMM 2 of the previous tile: T += Y * S_str, B read MN-major from its hi tile
+            if (first2 && g > 0 && !mbar_wait(acc_empty, (uint32_t)((g - 1) & 1), abort_flag)) { ok = false; break; }
             if (!mbar_wait(y_full, (uint32_t)(prev & 1), abort_flag)) { ok = false; break; }
             tc_fence_after();
-            const int sp = (int)(prev % STAGES);
-            const uint32_t tt = su32(sm + L.stage0 + sp * L.stage_bytes + L.tt_off);
+            const int sp = (int)(prev % TS);
+            const uint32_t tp = su32(sm + L.t0 + sp * 2 * T_TILE);
             for (int kk = 0; kk < BN / 16; ++kk)
-              tc_mma(tmem + col_acc, sdesc(ybuf + kk * 32), sdesc(tt + kk * 32), ID2, (first2 && kk == 0) ? 0u : 1u);
+              tc_mma(tmem + col_acc, sdesc(ybuf + kk * 32), sdesc_mn(tp + kk * 2048, BN * 128), ID2,
+                     (first2 && kk == 0) ? 0u : 1u);
             first2 = false;
             tc_commit(y_empty);
-            tc_commit(&empty[sp]);
+            tc_commit(&t_empty[sp]);
           }
           prev = it;
         }
@@ -345,12 +396,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (first2 && g > 0 && !mbar_wait(acc_empty, (uint32_t)((g - 1) & 1), abort_flag)) { ok = false; break; }
           if (!mbar_wait(y_full, (uint32_t)(prev & 1), abort_flag)) { ok = false; break; }
           tc_fence_after();
-          const int sp = (int)(prev % STAGES);
-          const uint32_t tt = su32(sm + L.stage0 + sp * L.stage_bytes + L.tt_off);
+          const int sp = (int)(prev % TS);
+          const uint32_t tp = su32(sm + L.t0 + sp * 2 * T_TILE);
           for (int kk = 0; kk < BN / 16; ++kk)
-            tc_mma(tmem + col_acc, sdesc(ybuf + kk * 32), sdesc(tt + kk * 32), ID2, (first2 && kk == 0) ? 0u : 1u);
+            tc_mma(tmem + col_acc, sdesc(ybuf + kk * 32), sdesc_mn(tp + kk * 2048, BN * 128), ID2,
+                   (first2 && kk == 0) ? 0u : 1u);
           tc_commit(y_empty);
-          tc_commit(&empty[sp]);
+          tc_commit(&t_empty[sp]);
           tc_commit(acc_full);
         }
         tc_commit(s_empty);
@@ -361,8 +413,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (mbar_try(mma_done, 0)) break;
     }
   } else {
-    // ---------------------------------------------------------------- epilogue (8 warps)
-    // warp w (2..9) reads TMEM lane quarter q = w % 4 and column half grp of every tile
+    // ---------------------------------------------------------------- epilogue (NEPI warps)
+    // warp w (2..NEPI+1) reads TMEM lane quarter q = w % 4 and column group grp (CPW columns)
     const int q = warp & 3;
     const int grp = (warp - 2) >> 2;
     const int row = q * 32 + lane;          // stationary row within the block
@@ -370,6 +422,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const double sg = *p.sigma;
     // exp(-e^2 / (2 sigma^2)) = exp2(-e^2 * k), k = log2(e) / (2 sigma^2); sigma = inf -> k = 0
     const float nk = isinf(sg) ? 0.0f : (float)(-1.4426950408889634 / (2.0 * sg * sg));
+    constexpr uint32_t CMASK = CPW == 32 ? 0xffffffffu : ((1u << CPW) - 1u);
     float sw = 0.f, se2 = 0.f, swe2 = 0.f, sden = 0.f;
     uint32_t nobs = 0, nnf = 0, nslot = 0;
     int64_t it = 0;
@@ -381,69 +434,92 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t srow = rb * BM + row;
       const bool row_ok = srow < p.P_stat;
       const uint32_t* mrow = p.Mst + (row_ok ? srow : 0) * p.W;
+      const int c0 = grp * CPW;                 // first tile column of this warp
+      // observation bits: this thread's CPW bits of the next tile are fetched one tile ahead
+      uint32_t mnext = row_ok ? __ldg(mrow + (((u % p.NT) * BN + c0) >> 5)) : 0u;
       for (; u < seg_end; ++u, ++it) {
-        const int s = (int)(it % STAGES), b = (int)(it & 1);
+        const int xs = (int)(it % XS), b = (int)(it & 1);
         const int64_t t0 = (u % p.NT) * BN;
-        // this thread's 32 observation bits (issued before the waits to hide the latency)
-        const uint32_t mword = row_ok ? __ldg(mrow + (t0 >> 5) + grp) : 0u;
-        const int64_t nc = p.P_strm - t0 - 32 * grp;    // valid columns in this half
-        const uint32_t vmask = (!row_ok || nc <= 0) ? 0u : (nc >= 32 ? 0xffffffffu : ((1u << nc) - 1u));
-        if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), abort_flag)) { ok = false; break; }
-        if (!mbar_wait(&d_full[b], (uint32_t)((it >> 1) & 1), abort_flag)) { ok = false; break; }
-        tc_fence_after();
-        const unsigned char* st = sm + L.stage0 + s * L.stage_bytes;
-        float xh[32], dh[32], xv[32];
-        tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + grp * 32), xh);
-        if (PASS2) tmem_ld32(tmem + lane_base + (uint32_t)((2 + b) * BN + grp * 32), dh);
+        const uint32_t mword = (mnext >> ((t0 + c0) & 31)) & CMASK;
+        if (row_ok && u + 1 < seg_end) mnext = __ldg(mrow + ((t0 + BN + c0) >> 5));
+        const int64_t nc = p.P_strm - t0 - c0;  // valid columns for this warp
+        const uint32_t vmask = (!row_ok || nc <= 0) ? 0u : (nc >= CPW ? CMASK : ((1u << nc) - 1u));
+        if (!mbar_wait(&x_full[xs], (uint32_t)((it / XS) & 1), abort_flag)) { ok = false; break; }
+        const unsigned char* xt = sm + L.x0 + xs * X_TILE;
+        float xh[CPW], dh[CPW], xv[CPW];
         if (ROWS) {
-          const float* sx = reinterpret_cast<const float*>(st + L.x_off) + (grp * 32) * BM + row;
+          const float* sx = reinterpret_cast<const float*>(xt) + c0 * BM + row;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) xv[j] = sx[j * BM];
+          for (int j = 0; j < CPW; ++j) xv[j] = sx[j * BM];
         } else {
-          // SWIZZLE_128B box of 32 columns: 16-byte chunk c of row r sits at chunk c ^ (r & 7)
-          const unsigned char* box = st + L.x_off + grp * (X_TILE / 2) + row * 128;
+          // SWIZZLE_128B boxes of 32 columns: 16-byte chunk c of row r sits at chunk c ^ (r & 7)
+          const unsigned char* box = xt + (c0 >> 5) * (X_TILE / 2) + row * 128;
+          const int cb = (c0 & 31) >> 2;
 #pragma unroll
-          for (int c4 = 0; c4 < 8; ++c4) {
-            const float4 v = *reinterpret_cast<const float4*>(box + ((c4 ^ (row & 7)) << 4));
+          for (int c4 = 0; c4 < CPW / 4; ++c4) {
+            const float4 v = *reinterpret_cast<const float4*>(box + (((cb + c4) ^ (row & 7)) << 4));
             xv[4 * c4 + 0] = v.x; xv[4 * c4 + 1] = v.y; xv[4 * c4 + 2] = v.z; xv[4 * c4 + 3] = v.w;
           }
         }
+        mbar_arrive(&x_empty[xs]);
+        if (!mbar_wait(&d_full[b], (uint32_t)((it >> 1) & 1), abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        tmem_ld<CPW>(tmem + lane_base + (uint32_t)(b * BN + c0), xh);
+        if (PASS2) tmem_ld<CPW>(tmem + lane_base + (uint32_t)((2 + b) * BN + c0), dh);
         tc_fence_before();
         mbar_arrive(&d_empty[b]);
-        mbar_arrive(&empty[s]);
         const uint32_t seen = mword & vmask;
         nslot += __popc(vmask);
         nobs += __popc(seen);
-        // branch-free slot update (predicated selects keep the 32 slots independent)
-        uint32_t fin = 0;
+        // branch-free slot update (predicated selects keep the slots independent)
+        if (FULL) {
+          // exact statistics: sum w, sum e^2, sum w e^2 and a count of non-finite residuals
+          uint32_t fin = 0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float e = xv[j] - xh[j];
-          const bool use = ((seen >> j) & 1u) && (fabsf(e) <= 3.402823466e38f);
-          fin |= use ? (1u << j) : 0u;
-          const float w = fast_ex2(e * e * nk);
-          const float uw = use ? w : 0.f;
-          if (PASS2) {
-            sden = fmaf(uw * dh[j], dh[j], sden);
-          } else {
-            const float y = uw * e;
-            sw += uw;
-            se2 = fmaf(use ? e : 0.f, e, se2);
-            swe2 = fmaf(y, e, swe2);
-            xv[j] = y;
+          for (int j = 0; j < CPW; ++j) {
+            const float e = xv[j] - xh[j];
+            const bool use = ((seen >> j) & 1u) && (fabsf(e) <= 3.402823466e38f);
+            fin |= use ? (1u << j) : 0u;
+            const float w = fast_ex2(e * e * nk);
+            const float uw = use ? w : 0.f;
+            if (PASS2) {
+              sden = fmaf(uw * dh[j], dh[j], sden);
+            } else {
+              const float y = uw * e;
+              sw += uw;
+              se2 = fmaf(use ? e : 0.f, e, se2);
+              swe2 = fmaf(y, e, swe2);
+              xv[j] = y;
+            }
+          }
+          nnf += __popc(seen & ~fin);
+        } else {
+          // lean: only what the update needs (y, or den) and the objective sum w e^2; a
+          // non-finite residual on an observed slot propagates as NaN and rejects the step
+#pragma unroll
+          for (int j = 0; j < CPW; ++j) {
+            const float e = xv[j] - xh[j];
+            const float w = fast_ex2(e * e * nk);
+            const bool bit = (seen >> j) & 1u;
+            if (PASS2) {
+              sden += bit ? w * dh[j] * dh[j] : 0.f;
+            } else {
+              const float y = bit ? w * e : 0.f;
+              swe2 += bit ? y * e : 0.f;
+              xv[j] = y;
+            }
           }
         }
-        nnf += __popc(seen & ~fin);
         if (!PASS2) {
-          uint32_t ypk[16];
+          uint32_t ypk[CPW / 2];
 #pragma unroll
-          for (int j = 0; j < 32; j += 2) ypk[j >> 1] = pack_bf16(xv[j], xv[j + 1]);
+          for (int j = 0; j < CPW; j += 2) ypk[j >> 1] = pack_bf16(xv[j], xv[j + 1]);
           if (!mbar_wait(y_empty, (uint32_t)((it & 1) ^ 1), abort_flag)) { ok = false; break; }
           unsigned char* yrow = sm + L.y + row * 128;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const uint4 v = make_uint4(ypk[4 * c], ypk[4 * c + 1], ypk[4 * c + 2], ypk[4 * c + 3]);
-            *reinterpret_cast<uint4*>(yrow + (((4 * grp + c) ^ (row & 7)) << 4)) = v;
+          for (int cc = 0; cc < CPW / 8; ++cc) {
+            const uint4 v = make_uint4(ypk[4 * cc], ypk[4 * cc + 1], ypk[4 * cc + 2], ypk[4 * cc + 3]);
+            *reinterpret_cast<uint4*>(yrow + ((((c0 >> 3) + cc) ^ (row & 7)) << 4)) = v;
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           mbar_arrive(y_full);
@@ -451,19 +527,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       if (!ok) break;
       if (!PASS2) {
-        // drain the segment's contraction: this half of row `row` of T -> partial slot c + rb
+        // drain the segment's contraction: this warp's columns of row `row` of T -> slot c + rb
         if (!mbar_wait(acc_full, (uint32_t)(g & 1), abort_flag)) { ok = false; break; }
         tc_fence_after();
         float* dst = p.Tpart + ((c + rb) * BM + row) * (int64_t)p.Kp;
-        float v[32];
-        tmem_ld32(tmem + lane_base + col_acc + grp * 32, v);
+        constexpr int KPW = KPAD / NGRP;
+        float v[KPW];
+        tmem_ld<KPW>(tmem + lane_base + col_acc + grp * KPW, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (grp * 32 + j < p.Kp) dst[grp * 32 + j] = row_ok ? v[j] : 0.f;
+        for (int j = 0; j < KPW; ++j)
+          if (grp * KPW + j < p.Kp) dst[grp * KPW + j] = row_ok ? v[j] : 0.f;
         tc_fence_before();
         mbar_arrive(acc_empty);
       }
     }
+    if (!FULL) nnf = (isfinite(swe2) && isfinite(sden)) ? 0u : 1u;
     // statistics: warp shuffle, then one row per CTA (fixed order)
     const double fv[7] = {(double)sw, (double)se2, (double)swe2, (double)nobs, (double)nnf, (double)nslot,
                           (double)sden};
@@ -493,8 +571,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ------------------------------------------------------------------ operand preparation
-// BF16 hi/lo split of a merged matrix [rows][Kp] (float) into [rows][KPAD] (zero padded),
-// plus, for the streaming side, the transposed hi part [KPAD][ldT] (zero padded).
+// BF16 hi/lo split of a merged matrix [rows][Kp] (float) into [rows][KPAD] (zero padded).
 __global__ void k_split_rows(const float* __restrict__ src, int64_t rows, int Kp, __nv_bfloat16* __restrict__ hi,
                              __nv_bfloat16* __restrict__ lo) {
   const int64_t n = rows * KPAD;
@@ -505,24 +582,6 @@ __global__ void k_split_rows(const float* __restrict__ src, int64_t rows, int Kp
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     hi[e] = h;
     if (lo) lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
-  }
-}
-
-__global__ void k_transpose_hi(const float* __restrict__ src, int64_t rows, int Kp, int64_t ldT,
-                               __nv_bfloat16* __restrict__ dst) {
-  __shared__ float tile[32][33];
-  const int64_t r0 = (int64_t)blockIdx.x * 32;
-  const int k0 = blockIdx.y * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int64_t r = r0 + i;
-    const int k = k0 + threadIdx.x;
-    tile[i][threadIdx.x] = (r < rows && k < Kp) ? src[r * Kp + k] : 0.f;
-  }
-  __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int k = k0 + i;
-    const int64_t r = r0 + threadIdx.x;
-    if (k < KPAD && r < ldT) dst[(int64_t)k * ldT + r] = __float2bfloat16_rn(tile[threadIdx.x][i]);
   }
 }
 
@@ -655,14 +714,9 @@ int tc_bm() { return tc::BM; }
 int tc_bn() { return tc::BN; }
 
 cudaError_t launch_tc_prep(const float* src, int64_t rows, int Kp, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                           __nv_bfloat16* hiT, int64_t ldT, cudaStream_t st) {
+                           cudaStream_t st) {
   const int64_t n = rows * tc::KPAD;
   tc::k_split_rows<<<(unsigned)imin((n + 255) / 256, 8192), 256, 0, st>>>(src, rows, Kp, hi, lo);
-  note_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !hiT) return e;
-  dim3 grid((unsigned)((ldT + 31) / 32), (unsigned)((tc::KPAD + 31) / 32)), block(32, 8);
-  tc::k_transpose_hi<<<grid, block, 0, st>>>(src, rows, Kp, ldT, hiT);
   note_launch();
   return cudaGetLastError();
 }
@@ -692,33 +746,28 @@ cudaError_t launch_reduce_slots(const float* part, int64_t RB, int64_t NT, int G
   return cudaGetLastError();
 }
 
-// Launch one fused pass.  S operands: [P_stat][KPAD] bf16 (hi, lo, h); streaming: [P_strm][KPAD]
-// (hi, lo) and [KPAD][ldT] (hi transposed); X: [P_out][P_in] floats; Mrows: [P_out][W] words.
+// Launch one fused pass.  S operands: [P_stat][KPAD] bf16 (hi, lo, h); streaming operands:
+// [P_strm][KPAD] (hi, lo); X: [P_out][P_in] floats; Mst: [P_stat][W] mask words.
 cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi, const __nv_bfloat16* S_lo,
                            const __nv_bfloat16* S_h, const __nv_bfloat16* T_hi, const __nv_bfloat16* T_lo,
-                           const __nv_bfloat16* TT, int64_t ldT, const float* X, int64_t P_in, int64_t P_out,
-                           const uint32_t* Mst, int64_t W, int64_t P_stat, int64_t P_strm, int Kp,
-                           const double* sigma, float* Tpart, double* stat_part, int* err, int G,
-                           cudaStream_t st) {
+                           const float* X, int64_t P_in, int64_t P_out, const uint32_t* Mst, int64_t W,
+                           int64_t P_stat, int64_t P_strm, int Kp, const double* sigma, float* Tpart,
+                           double* stat_part, int* err, int G, bool full_stats, cudaStream_t st) {
   using namespace tc;
-  if (Kp > KPAD || (P_in % 4) != 0 || (ldT % 64) != 0) return cudaErrorInvalidValue;
-  CUtensorMap mS_hi, mS_lo, mS_h, mT_hi, mT_lo, mTT, mX, mM;
+  if (Kp > KPAD || (P_in % 4) != 0) return cudaErrorInvalidValue;
+  CUtensorMap mS_hi, mS_lo, mS_h, mT_hi, mT_lo, mX;
   const CUtensorMapDataType BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const CUtensorMapSwizzle SW = CU_TENSOR_MAP_SWIZZLE_128B;
   bool ok = make_map(&mS_hi, BF, 2, S_hi, KPAD, P_stat, KPAD * 2, 64, BM, SW) &&
             make_map(&mS_lo, BF, 2, S_lo, KPAD, P_stat, KPAD * 2, 64, BM, SW) &&
             make_map(&mS_h, BF, 2, pass2 ? S_h : S_hi, KPAD, P_stat, KPAD * 2, 64, BM, SW) &&
             make_map(&mT_hi, BF, 2, T_hi, KPAD, P_strm, KPAD * 2, 64, BN, SW) &&
-            make_map(&mT_lo, BF, 2, T_lo, KPAD, P_strm, KPAD * 2, 64, BN, SW) &&
-            make_map(&mTT, BF, 2, TT, ldT, KPAD, ldT * 2, 64, KPAD, SW);
-  if (rows_case) {
+            make_map(&mT_lo, BF, 2, T_lo, KPAD, P_strm, KPAD * 2, 64, BN, SW);
+  if (rows_case)
     ok = ok && make_map(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, P_in, P_out, P_in * 4, BM, BN,
                         CU_TENSOR_MAP_SWIZZLE_NONE);
-    mM = mX;
-  } else {
+  else
     ok = ok && make_map(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, P_in, P_out, P_in * 4, 32, BM, SW);
-    mM = mX;
-  }
   if (!ok) return cudaErrorInvalidValue;
   Params p;
   p.P_in = P_in;
@@ -740,12 +789,13 @@ cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi
   auto go = [&](auto kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<p.G, NTHREADS, smem, st>>>(mS_hi, mS_lo, mS_h, mT_hi, mT_lo, mTT, mX, mM, p);
+    kern<<<p.G, NTHREADS, smem, st>>>(mS_hi, mS_lo, mS_h, mT_hi, mT_lo, mX, p);
     note_launch();
     return cudaGetLastError();
   };
-  if (rows_case) return pass2 ? go(k_pass_tc<true, true>) : go(k_pass_tc<true, false>);
-  return pass2 ? go(k_pass_tc<false, true>) : go(k_pass_tc<false, false>);
+  if (pass2) return rows_case ? go(k_pass_tc<true, true, false>) : go(k_pass_tc<false, true, false>);
+  if (full_stats) return rows_case ? go(k_pass_tc<true, false, true>) : go(k_pass_tc<false, false, true>);
+  return rows_case ? go(k_pass_tc<true, false, false>) : go(k_pass_tc<false, false, false>);
 }
 
 }  // namespace trd

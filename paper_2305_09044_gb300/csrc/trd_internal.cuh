@@ -193,7 +193,7 @@ int tc_kpad();
 int tc_bm();
 int tc_bn();
 cudaError_t launch_tc_prep(const float* src, int64_t rows, int Kp, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                           __nv_bfloat16* hiT, int64_t ldT, cudaStream_t st);
+                           cudaStream_t st);
 cudaError_t launch_mask_rows(const uint32_t* M, int64_t P_in, int64_t P_out, int64_t W, uint32_t* out,
                              cudaStream_t st);
 cudaError_t launch_mask_transpose(const uint32_t* M, int64_t P_in, int64_t P_out, int64_t WT, uint32_t* out,
@@ -202,10 +202,9 @@ cudaError_t launch_reduce_slots(const float* part, int64_t RB, int64_t NT, int G
                                 double* out, cudaStream_t st);
 cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi, const __nv_bfloat16* S_lo,
                            const __nv_bfloat16* S_h, const __nv_bfloat16* T_hi, const __nv_bfloat16* T_lo,
-                           const __nv_bfloat16* TT, int64_t ldT, const float* X, int64_t P_in, int64_t P_out,
-                           const uint32_t* Mst, int64_t W, int64_t P_stat, int64_t P_strm, int Kp,
-                           const double* sigma, float* Tpart, double* stat_part, int* err, int G,
-                           cudaStream_t st);
+                           const float* X, int64_t P_in, int64_t P_out, const uint32_t* Mst, int64_t W,
+                           int64_t P_stat, int64_t P_strm, int Kp, const double* sigma, float* Tpart,
+                           double* stat_part, int* err, int G, bool full_stats, cudaStream_t st);
 
 // fgmc_solve.cu
 cudaError_t launch_fgmc_E(const double* Z, const int32_t* idx, int64_t n, int rk, int rk1,
