@@ -35,7 +35,7 @@ EXPORTS = [
     "trd_fgmc_gram", "trd_core_update", "trd_step", "trd_adaptive_sigma",
     "trd_sigma_from_residuals", "trd_reconstruct", "trd_reconstruct_from",
     "trd_recovery_error", "trd_sampled_fwd", "trd_sampled_bwd", "trd_set_profiling",
-    "trd_get_profile", "trd_kernel_launches",
+    "trd_get_profile", "trd_kernel_launches", "trd_sigma_from_residuals_noalloc",
 ]
 
 
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
         "trd_set_profiling": [vp, C.c_int],
         "trd_get_profile": [vp, C.c_int, P(dbl)],
         "trd_kernel_launches": [],
+        "trd_sigma_from_residuals_noalloc": [vp, i64, dbl, dbl, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

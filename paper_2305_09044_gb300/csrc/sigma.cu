@@ -4,6 +4,8 @@
 // Quartiles are type-7 (linear interpolation between order statistics); the order
 // statistics come from an exact, deterministic MSB-first radix select on order-preserving
 // 64-bit keys (8 passes of 8 bits, integer histograms).
+#include <mutex>
+
 #include "trd_internal.cuh"
 
 namespace trd {
@@ -377,4 +379,61 @@ cudaError_t launch_sigma_from_floats(const float* r, int64_t n, double x_obs_rms
   return finish_sigma(vals, keys, xsq, n, x_obs_rms, sigma_prev, nullptr, work, sigma_out, st);
 }
 
+// ------------------------------------------------------------------ allocation-free variant
+// Fixed scratch for trd_sigma_from_residuals_noalloc: room for NOALLOC_MAX residuals (values,
+// order keys and a zero x^2 column, 8 bytes each) plus the selection work area.  It is a
+// file-scope device array, so every GPU that loads the library holds it (about 24 MB) until
+// the process exits; all calls share it.
+constexpr int64_t NOALLOC_MAX = int64_t(1) << 20;
+constexpr size_t NOALLOC_WORK = 64 + 1024 + 256 * 3 + 64;   // doubles; equals sigma_work_doubles()
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_MAX * 24 + NOALLOC_WORK * 8];
+
+namespace {
+constexpr int NOALLOC_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[NOALLOC_DEVICES] = {};   // device address of the scratch, per device ordinal
+}  // namespace
+
 }  // namespace trd
+
+extern "C" trd_status trd_sigma_from_residuals_noalloc(const float* resid_dev, int64_t n, double x_obs_rms,
+                                                       double sigma_prev, double* sigma_out_dev,
+                                                       void* cuda_stream) {
+  using namespace trd;
+  if (!resid_dev || !sigma_out_dev || n < 1 || n > NOALLOC_MAX || !(x_obs_rms >= 0.0)) return TRD_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return TRD_ECUDA;
+  }
+  if (dev < 0 || dev >= NOALLOC_DEVICES) return TRD_EINVAL;
+  void* base = nullptr;
+  {
+    // one-time set-up per device (with that device current): the host-side name of the array
+    // is not a device address, so ask the runtime for the device address of this copy
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return TRD_ECUDA;
+      }
+      g_noalloc_addr[dev] = ptr;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  unsigned char* b = static_cast<unsigned char*>(base);
+  double* vals = reinterpret_cast<double*>(b);
+  uint64_t* keys = reinterpret_cast<uint64_t*>(b + NOALLOC_MAX * 8);
+  double* xsq = reinterpret_cast<double*>(b + NOALLOC_MAX * 16);
+  double* work = reinterpret_cast<double*>(b + NOALLOC_MAX * 24);
+  // every scratch word the selection reads is written first in this call (the histogram is
+  // cleared by the selection's own initialisation), so stale contents do not leak in
+  const cudaError_t e = launch_sigma_from_floats(resid_dev, n, x_obs_rms, sigma_prev, vals, keys, xsq, work,
+                                                 sigma_out_dev, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TRD_ECUDA;
+  }
+  return TRD_OK;
+}
