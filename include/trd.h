@@ -272,8 +272,8 @@ int64_t trd_kernel_launches(void);
  * loss = sum_m sigma^2 (1 - exp(-e_m^2 / (2 sigma^2))) (sigma > 0, finite).
  * fp64 = 0: cores, x and resid are float arrays and arithmetic is FP32 (FP64 sums);
  * fp64 = 1: all are double arrays and arithmetic is FP64.  resid_dev (DEVICE, M values,
- * nullable) receives e_m.  loss_out (host) receives the loss.  Indices are not checked on
- * the device: out-of-range indices are the caller's error (check with care). */
+ * nullable) receives e_m.  loss_out (host) receives the loss.  Entries with an index outside
+ * [0, I_k) are skipped and the call returns TRD_EINVAL. */
 trd_status trd_sampled_fwd(trd_t* handle, const void* const* cores_dev, const int32_t* idx_dev,
                            const void* x_dev, int64_t M, double sigma, int fp64,
                            void* resid_dev, double* loss_out);

@@ -465,3 +465,33 @@ def sampled_loss_grad(cores, idx: np.ndarray, x: np.ndarray, sigma: float):
                 S = S @ cores[j][:, idx[m, j], :]
             grads[k][:, idx[m, k], :] += -w[m] * e[m] * S.T
     return loss, e, w, grads
+
+
+def sampled_loss_grad_vec(cores, idx: np.ndarray, x: np.ndarray, sigma: float):
+    """Same quantities as sampled_loss_grad, with the per-entry products batched over the
+    entries (numpy matmul on stacks of slices) for large samples."""
+    N = len(cores)
+    idx = np.asarray(idx)
+    slices = [np.transpose(cores[k][:, idx[:, k], :], (1, 0, 2)) for k in range(N)]  # (M, r_k, r_k+1)
+    # prefix P_k = Z_1 ... Z_{k-1} and suffix Q_k = Z_{k+1} ... Z_N, per entry
+    M = idx.shape[0]
+    pre = [None] * N
+    P = np.broadcast_to(np.eye(cores[0].shape[0]), (M,) + (cores[0].shape[0],) * 2)
+    for k in range(N):
+        pre[k] = P
+        P = np.matmul(P, slices[k])
+    xhat = np.trace(P, axis1=1, axis2=2)
+    e = x - xhat
+    w = hq_weight(e, sigma)
+    loss = welsch_loss(e, sigma)
+    g = -w * e
+    grads = [np.zeros_like(Z) for Z in cores]
+    suf = np.broadcast_to(np.eye(cores[0].shape[0]), (M,) + (cores[0].shape[0],) * 2)
+    for k in range(N - 1, -1, -1):
+        # S^{!=k} = (Z_{k+1} ... Z_N)(Z_1 ... Z_{k-1}) = suf @ pre[k]
+        S = np.matmul(suf, pre[k])                          # (M, r_{k+1}, r_k)
+        contrib = g[:, None, None] * np.transpose(S, (0, 2, 1))
+        np.add.at(grads[k], (slice(None), idx[:, k], slice(None)),
+                  np.transpose(contrib, (1, 0, 2)))
+        suf = np.matmul(slices[k], suf)
+    return loss, e, w, grads

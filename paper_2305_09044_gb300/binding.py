@@ -318,6 +318,32 @@ class TRD:
         self._check(self.lib.trd_get_profile(self.h, 1 if reset else 0, out), "trd_get_profile")
         return {"pass1_ms": out[0], "pass1_n": int(out[1]), "pass2_ms": out[2], "pass2_n": int(out[3])}
 
+    # ------------------------------------------------------------------ sampled correntropy loss
+    def sampled_fwd(self, cores, idx, x, sigma: float, resid=None) -> float:
+        """cores: CUDA tensors in the library layout (I_k, r_{k+1}, r_k), all float32 or all
+        float64; idx: CUDA int32 (M, N); x: CUDA values (M,), same dtype as the cores."""
+        import torch
+        fp64 = cores[0].dtype == torch.float64
+        ptrs = (C.c_void_p * self.N)(*[_dptr(t) for t in cores])
+        out = C.c_double()
+        self._check(self.lib.trd_sampled_fwd(self.h, ptrs, C.c_void_p(_dptr(idx)), C.c_void_p(_dptr(x)),
+                                             idx.shape[0], sigma, 1 if fp64 else 0,
+                                             C.c_void_p(_dptr(resid)) if resid is not None else None,
+                                             C.byref(out)), "trd_sampled_fwd")
+        return out.value
+
+    def sampled_bwd(self, cores, idx, x, sigma: float, g_scale: float = 1.0, grads=None):
+        import torch
+        fp64 = cores[0].dtype == torch.float64
+        if grads is None:
+            grads = [torch.empty_like(t) for t in cores]
+        ptrs = (C.c_void_p * self.N)(*[_dptr(t) for t in cores])
+        gptrs = (C.c_void_p * self.N)(*[_dptr(t) for t in grads])
+        self._check(self.lib.trd_sampled_bwd(self.h, ptrs, C.c_void_p(_dptr(idx)), C.c_void_p(_dptr(x)),
+                                             idx.shape[0], sigma, 1 if fp64 else 0, g_scale, gptrs),
+                    "trd_sampled_bwd")
+        return grads
+
     def recovery_error(self, Xref) -> float:
         out = C.c_double()
         self._check(self.lib.trd_recovery_error(self.h, C.c_void_p(_dptr(Xref)), C.byref(out)),

@@ -76,6 +76,8 @@ struct Extra {
   DevBuf tmpZ[kMaxN];   // cores given to trd_reconstruct_from
   DevBuf probe_xsq;
   DevBuf Ework;         // FGMC factor partial sums
+  // sampled correntropy loss: cores in FP64, merged halves, their gradients, partials
+  DevBuf smpZ[kMaxN], smpA, smpC, smpGA, smpGC, smpGAd, smpGCd, smpPre, smpPost, smpDpart, smpD, smpLoss;
   // BF16 tensor-core operands and the padded mask rows of the current view
   DevBuf bShi, bSlo, bSh, bThi, bTlo, bTT;
   // observation bits re-laid per stationary index: [0] inner index along the outer one
@@ -227,7 +229,7 @@ trd_status sync_and_status(trd_handle* h) {
     if (st & DEV_SINGULAR) return set_err(h, TRD_ESINGULAR, "G + lambda I is not positive definite");
     if (st & DEV_NONFINITE) return set_err(h, TRD_ENONFINITE, "non-finite step size");
     if (st & DEV_TIMEOUT) return set_err(h, TRD_ETIMEOUT, "a device wait gave up");
-    if (st & DEV_BOUNDS) return set_err(h, TRD_EINVAL, "a device index check failed");
+    if (st & DEV_BOUNDS) return set_err(h, TRD_EINVAL, "an index was out of range (entries skipped)");
   }
   return TRD_OK;
 }
@@ -845,7 +847,10 @@ void trd_destroy(trd_t* h) {
   DevBuf* xb[] = {&x->Ework, &x->meta, &x->stat_sum2, &x->Gloc, &x->recA, &x->recC, &x->errp, &x->probe_xsq,
                   &x->bShi, &x->bSlo, &x->bSh, &x->bThi, &x->bTlo, &x->bTT, &x->Mst[0], &x->Mst[1]};
   for (DevBuf* b : xb) free_buf(*b);
-  for (int k = 0; k < kMaxN; ++k) { free_buf(x->Eloc[k]); free_buf(x->tmpZ[k]); }
+  for (int k = 0; k < kMaxN; ++k) { free_buf(x->Eloc[k]); free_buf(x->tmpZ[k]); free_buf(x->smpZ[k]); }
+  DevBuf* sb[] = {&x->smpA, &x->smpC, &x->smpGA, &x->smpGC, &x->smpGAd, &x->smpGCd, &x->smpPre, &x->smpPost,
+                  &x->smpDpart, &x->smpD, &x->smpLoss};
+  for (DevBuf* b : sb) free_buf(*b);
   for (auto& p : x->pending) { x->ev_pool.push_back(p.a); x->ev_pool.push_back(p.b); }
   if (x->ev_open) x->ev_pool.push_back(x->ev_open);
   for (cudaEvent_t e : x->ev_pool) cudaEventDestroy(e);
@@ -1183,5 +1188,134 @@ trd_status trd_get_profile(trd_t* h, int reset, double* out) {
 }
 
 int64_t trd_kernel_launches(void) { return launches_total(); }
+
+// ------------------------------------------------------------------ sampled correntropy loss
+static trd_status sampled_setup(trd_t* h, const void* const* cores_dev, int fp64, const double** Zc, Split& sp,
+                                Split2& s2) {
+  Extra* x = X_(h);
+  const View fv = full_view(h);
+  sp = choose_split(h, fv, 0);
+  s2.N = h->N;
+  s2.c = sp.c;
+  s2.err = h->dstatus;
+  for (int m = 0; m < h->N; ++m) s2.dim[m] = h->I[m];
+  int64_t st_in = 1, st_out = 1;
+  for (int m = 0; m < h->N; ++m) {
+    if (m < sp.c) { s2.sin[m] = st_in; s2.sout[m] = 0; st_in *= h->I[m]; }
+    else { s2.sin[m] = 0; s2.sout[m] = st_out; st_out *= h->I[m]; }
+  }
+  for (int k = 0; k < h->N; ++k) {
+    if (!cores_dev[k]) return set_err(h, TRD_EINVAL, "NULL core");
+    const int64_t n = h->I[k] * (int64_t)h->K[k];
+    if (fp64) {
+      Zc[k] = (const double*)cores_dev[k];
+    } else {
+      TRY(ensure(h, x->smpZ[k], sizeof(double) * n));
+      CK(launch_to_double((const float*)cores_dev[k], n, (double*)x->smpZ[k].p, h->stream), "core widening");
+      Zc[k] = (const double*)x->smpZ[k].p;
+    }
+  }
+  const size_t e = fp64 ? sizeof(double) : sizeof(float);
+  TRY(ensure(h, x->smpA, e * sp.P_in * sp.Kp));
+  TRY(ensure(h, x->smpC, e * sp.P_out * sp.Kp));
+  CK(launch_chain(make_chain(h, fv, 0, sp.c, -1, nullptr, Zc), x->smpA.p, fp64 != 0, false, sp.Kp, h->stream),
+     "merge inner block");
+  CK(launch_chain(make_chain(h, fv, sp.c, h->N, -1, nullptr, Zc), x->smpC.p, fp64 != 0, true, sp.Kp, h->stream),
+     "merge outer block");
+  return TRD_OK;
+}
+
+trd_status trd_sampled_fwd(trd_t* h, const void* const* cores_dev, const int32_t* idx_dev, const void* x_dev,
+                           int64_t M, double sigma, int fp64, void* resid_dev, double* loss_out) {
+  TRY(check_handle(h));
+  if (!cores_dev || !idx_dev || !x_dev || M < 1 || !loss_out || !(sigma > 0) || !isfinite(sigma))
+    return set_err(h, TRD_EINVAL, "bad arguments");
+  Extra* x = X_(h);
+  const double* Zc[kMaxN];
+  Split sp;
+  Split2 s2;
+  TRY(sampled_setup(h, cores_dev, fp64, Zc, sp, s2));
+  const int parts = 4 * h->num_sms;
+  TRY(ensure(h, x->smpLoss, sizeof(double) * parts));
+  CK(launch_sampled_kernel(x->smpA.p, x->smpC.p, fp64 != 0, sp.Kp, idx_dev, &s2, x_dev, M, sigma, resid_dev,
+                           (double*)x->smpLoss.p, parts, false, 0.0, nullptr, nullptr, h->stream),
+     "sampled forward");
+  std::vector<double> lp((size_t)parts);
+  CK(cudaMemcpyAsync(lp.data(), x->smpLoss.p, sizeof(double) * parts, cudaMemcpyDeviceToHost, h->stream),
+     "loss partials");
+  TRY(sync_and_status(h));
+  double loss = 0.0;
+  for (int i = 0; i < parts; ++i) loss += lp[(size_t)i];
+  *loss_out = loss;
+  return TRD_OK;
+}
+
+trd_status trd_sampled_bwd(trd_t* h, const void* const* cores_dev, const int32_t* idx_dev, const void* x_dev,
+                           int64_t M, double sigma, int fp64, double g_scale, void* const* grad_dev) {
+  TRY(check_handle(h));
+  if (!cores_dev || !idx_dev || !x_dev || M < 1 || !grad_dev || !(sigma > 0) || !isfinite(sigma))
+    return set_err(h, TRD_EINVAL, "bad arguments");
+  for (int k = 0; k < h->N; ++k)
+    if (!grad_dev[k]) return set_err(h, TRD_EINVAL, "NULL gradient buffer");
+  Extra* x = X_(h);
+  const double* Zc[kMaxN];
+  Split sp;
+  Split2 s2;
+  TRY(sampled_setup(h, cores_dev, fp64, Zc, sp, s2));
+  const bool dbl = fp64 != 0;
+  const size_t e = dbl ? sizeof(double) : sizeof(float);
+  TRY(ensure(h, x->smpGA, e * sp.P_in * sp.Kp));
+  TRY(ensure(h, x->smpGC, e * sp.P_out * sp.Kp));
+  CK(cudaMemsetAsync(x->smpGA.p, 0, e * sp.P_in * sp.Kp, h->stream), "clear gA");
+  CK(cudaMemsetAsync(x->smpGC.p, 0, e * sp.P_out * sp.Kp, h->stream), "clear gC");
+  const int parts = 4 * h->num_sms;
+  CK(launch_sampled_kernel(x->smpA.p, x->smpC.p, dbl, sp.Kp, idx_dev, &s2, x_dev, M, sigma, nullptr, nullptr, parts,
+                           true, g_scale, x->smpGA.p, x->smpGC.p, h->stream),
+     "sampled adjoint scatter");
+  // the back-contraction reads FP64 halves
+  const double* gAd = (const double*)x->smpGA.p;
+  const double* gCd = (const double*)x->smpGC.p;
+  if (!dbl) {
+    TRY(ensure(h, x->smpGAd, sizeof(double) * sp.P_in * sp.Kp));
+    TRY(ensure(h, x->smpGCd, sizeof(double) * sp.P_out * sp.Kp));
+    CK(launch_to_double((const float*)x->smpGA.p, sp.P_in * sp.Kp, (double*)x->smpGAd.p, h->stream), "widen gA");
+    CK(launch_to_double((const float*)x->smpGC.p, sp.P_out * sp.Kp, (double*)x->smpGCd.p, h->stream), "widen gC");
+    gAd = (const double*)x->smpGAd.p;
+    gCd = (const double*)x->smpGCd.p;
+  }
+  const View fv = full_view(h);
+  const int N = h->N, c = sp.c;
+  for (int k = 0; k < N; ++k) {
+    const bool rows = k < c;
+    const int rk = h->R[k], rk1 = h->R[(k + 1) % N];
+    int pre0, pre1, post0, post1, mr, mc;
+    if (rows) { pre0 = 0; pre1 = k; post0 = k + 1; post1 = c; mr = h->R[c]; mc = h->R[0]; }
+    else { pre0 = c; pre1 = k; post0 = k + 1; post1 = N; mr = h->R[0]; mc = h->R[c]; }
+    const Chain pre = make_chain(h, fv, pre0, pre1, -1, nullptr, Zc);
+    const Chain post = make_chain(h, fv, post0, post1, -1, nullptr, Zc);
+    const int64_t n_pre = pre.n > 0 ? pre.count : 1, n_post = post.n > 0 ? post.count : 1;
+    if (pre.n > 0) {
+      TRY(ensure(h, x->smpPre, e * n_pre * mc * rk));
+      CK(launch_chain(pre, x->smpPre.p, dbl, false, mc * rk, h->stream), "merge prefix");
+    }
+    if (post.n > 0) {
+      TRY(ensure(h, x->smpPost, e * n_post * rk1 * mr));
+      CK(launch_chain(post, x->smpPost.p, dbl, false, rk1 * mr, h->stream), "merge suffix");
+    }
+    const int64_t npairs = n_pre * n_post;
+    int64_t nsplit = (2 * (int64_t)h->num_sms + h->I[k] - 1) / h->I[k];
+    nsplit = imax(1, imin(nsplit, imin(npairs, 256)));
+    const int K = h->K[k];
+    TRY(ensure(h, x->smpD, sizeof(double) * h->I[k] * K));
+    if (nsplit > 1) TRY(ensure(h, x->smpDpart, sizeof(double) * nsplit * h->I[k] * K));
+    CK(launch_backcontract(rows ? (const void*)gAd : (const void*)gCd, sp.Kp, rows, mr, mc,
+                           pre.n > 0 ? x->smpPre.p : nullptr, n_pre, post.n > 0 ? x->smpPost.p : nullptr, n_post,
+                           h->I[k], rk, rk1, (double*)x->smpDpart.p, (int)nsplit, (double*)x->smpD.p, dbl, h->stream),
+       "adjoint back-contraction");
+    CK(launch_from_double((const double*)x->smpD.p, h->I[k] * (int64_t)K, grad_dev[k], dbl, h->stream),
+       "gradient store");
+  }
+  return sync_and_status(h);
+}
 
 }  // extern "C"

@@ -241,10 +241,19 @@ cudaError_t launch_sigma_from_floats(const float* r, int64_t n, double x_obs_rms
                                      double* sigma_out, cudaStream_t st);
 
 // sampled.cu
-cudaError_t launch_sampled(const void* const* cores, int N, const int* R, const int64_t* I,
-                           const int32_t* idx, const void* x, int64_t M, double sigma,
-                           bool fp64, void* resid, double* loss_part, int parts,
-                           void* const* grads, double g_scale, bool backward,
-                           cudaStream_t st);
+// Strides of each mode inside the inner (a) / outer (b) block of a two-block cut (0 if the mode
+// belongs to the other block).
+struct Split2 {
+  int N, c;
+  int64_t sin[kMaxN], sout[kMaxN];
+  int64_t dim[kMaxN];
+  int* err;                          // device status word (DEV_BOUNDS on a bad index)
+};
+cudaError_t launch_sampled_kernel(const void* A, const void* C, bool fp64, int Kp, const int32_t* idx,
+                                  const Split2* sp, const void* x, int64_t M, double sigma, void* resid,
+                                  double* loss_part, int parts, bool backward, double g_scale, void* gA, void* gC,
+                                  cudaStream_t st);
+cudaError_t launch_to_double(const float* src, int64_t n, double* dst, cudaStream_t st);
+cudaError_t launch_from_double(const double* src, int64_t n, void* dst, bool fp64, cudaStream_t st);
 
 }  // namespace trd

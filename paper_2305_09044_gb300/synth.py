@@ -150,10 +150,12 @@ def assemble(x_true, c: Corruption, kind: str = "uniform", scale: float = 10.0):
 
 
 def sample_entries(dims: Sequence[int], M: int, seed: int) -> np.ndarray:
-    """M distinct multi-indices (M x N, int32), uniform over the tensor, sorted by linear
-    index."""
+    """About M distinct multi-indices (rows of an int32 array, N columns), sorted by linear
+    index: each entry is kept independently with probability M / numel (a few draws more),
+    then the first M are returned (fewer when the draw falls short)."""
     rng = np.random.default_rng(seed)
     n = int(np.prod(dims))
-    lin = np.sort(rng.choice(n, size=M, replace=False))
+    p = min(1.0, M / n * 1.001 + 64.0 / n)
+    lin = np.flatnonzero(rng.random(n) < p)[:M]
     idx = np.stack(np.unravel_index(lin, dims, order="F"), axis=1)
-    return idx.astype(np.int32)
+    return np.ascontiguousarray(idx.astype(np.int32))

@@ -462,3 +462,19 @@ def test_sampled_adjoint_fd():
     num, ref = np.array(num), np.array(ref)
     assert np.linalg.norm(num - ref) <= 1e-6 * np.linalg.norm(ref)
     # Welsch-loss gradient = HQ gradient: at full sampling it is -d of Eq. sd with W fixed
+
+
+def test_sampled_vectorised_matches_loops():
+    """The batched form of the sampled loss and adjoint equals the per-entry loops."""
+    dims, ranks = (5, 4, 6, 3), (2, 3, 2, 2)
+    rng = np.random.default_rng(13)
+    cores = _rand_cores(rng, dims, ranks, 0.7)
+    lin = rng.choice(int(np.prod(dims)), 150, replace=False)
+    idx = np.stack(np.unravel_index(lin, dims, order="F"), axis=1)
+    x = rng.standard_normal(150)
+    a = O.sampled_loss_grad(cores, idx, x, 0.8)
+    b = O.sampled_loss_grad_vec(cores, idx, x, 0.8)
+    assert abs(a[0] - b[0]) < 1e-12 * abs(a[0])
+    assert np.allclose(a[1], b[1], rtol=0, atol=1e-13)
+    for ga, gb in zip(a[3], b[3]):
+        assert np.allclose(ga, gb, rtol=0, atol=1e-12)
