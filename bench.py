@@ -153,10 +153,12 @@ def build_problem(w, torch, prec):
 
 def timed_steps(t, steps, warmup, world, local, torch, kernel_launches):
     """Warm up, then time `steps` trd_step calls with CUDA events on the handle's stream;
-    the fused data passes are traced by the library (events around each launch)."""
+    inside the timed region only the fused data passes are traced by the library (events
+    around each launch, level 1).  A few more steps after it, traced at every phase
+    (level 2), give the per-phase breakdown; they are not part of the timing."""
     for _ in range(max(warmup, 3)):
         t.step(sigma=-1.0)
-    t.set_profiling(True)
+    t.set_profiling(1)
     t.get_profile(reset=True)
     _barrier(world)
     torch.cuda.synchronize()
@@ -172,7 +174,12 @@ def timed_steps(t, steps, warmup, world, local, torch, kernel_launches):
     launches = kernel_launches() - l0
     ck = clocks.stop()
     prof = t.get_profile(reset=True)
+    t.set_profiling(2)
+    for _ in range(3):
+        t.step(sigma=-1.0)
+    phases = t.get_profile(reset=True)
     t.set_profiling(False)
+    prof["phases_untimed"] = phases
     ms = _max_over_ranks(ev0.elapsed_time(ev1), world)
     return ms, prof, launches, ck
 
@@ -223,6 +230,12 @@ def roofline(prec, prof, w):
     roof["traffic"] = recorded_traffic(prec) if w.name == WORKLOAD else None
     roof["ms_per_launch"] = pass_ms
     roof["launches"] = launches_pass
+    ph = prof.get("phases_untimed", {})
+    steps = max(ph.get("stop_n", 0), 1)
+    # per-phase breakdown from the untimed steps traced at every phase (event overhead
+    # included there, so the phases add up to a little more than ms_per_step)
+    roof["phase_ms_per_step_untimed"] = {k[:-3]: round(v / steps, 4) for k, v in ph.items()
+                                         if k.endswith("_ms") and v > 0}
     roof["algorithmic_bytes_per_launch"] = hbm_bytes
     roof["hbm_gbs_achieved"] = hbm_bytes / (pass_ms / 1e3) / 1e9
     return roof

@@ -250,18 +250,31 @@ trd_status trd_recovery_error(trd_t* handle, const float* Xref_dev, double* err_
 
 /* ---------------------------------------------------------------- tracing */
 
-/* When `on` is nonzero the handle records CUDA events on its stream around every launch of
- * the fused data-pass kernels (pass 1: reconstruction, residual, weight and weighted
- * contraction; pass 2: the line-search pass).  Off by default. */
+/* Tracing level `on`: 0 off (default); 1 records CUDA events on the handle's stream around
+ * the two fused data-pass kernels only (phases 0 and 1, cheap enough for timed runs); 2 also
+ * around every other phase of a core update.  Phases: 0 the fused pass-1 kernel
+ * (reconstruction, residual, weight, weighted contraction), 1 the fused pass-2 kernel (line
+ * search), 2 operand merges and conversions, 3 reductions of partial results,
+ * 4 back-contraction into the gradient, 5 FGMC Gram, 6 LDL^T factorisation, 7 solves and
+ * <d,h>, 8 step size, core update and factor refresh, 9 adaptive width, 10 stopping
+ * quantity, 11 unused.  TRD_EINVAL for another level. */
 trd_status trd_set_profiling(trd_t* handle, int on);
 
-/* Synchronise the handle's stream and write out[0] = total milliseconds of the pass-1
- * launches recorded since the last reset, out[1] = their number, out[2] and out[3] the same
- * for pass 2 (host array of 4 doubles).  reset != 0 clears the totals afterwards. */
+/* Synchronise the handle's stream and write out[2q] = total milliseconds and out[2q+1] = the
+ * number of recorded intervals of phase q, for the 12 phases above (host array of 24
+ * doubles).  reset != 0 clears the totals afterwards. */
 trd_status trd_get_profile(trd_t* handle, int reset, double* out);
 
 /* Number of kernels the library has launched in this process (all handles). */
 int64_t trd_kernel_launches(void);
+
+/* Failure-detection self-test (no counterpart in the paper).  Runs, on the handle's stream,
+ * the bounded mbarrier wait that every role of the tensor-core data pass uses, on a fresh
+ * barrier whose phase completes only when `arrive` is nonzero, giving up after `limit`
+ * polls (1 <= limit <= 2^24).  Returns TRD_OK when the phase completed and TRD_ETIMEOUT when
+ * the wait gave up -- the status a stalled pass reports -- and leaves the handle usable in
+ * both cases.  TRD_EINVAL for a limit out of range. */
+trd_status trd_wait_selftest(trd_t* handle, int arrive, int64_t limit);
 
 /* ---------------------------------------------------------------- sampled correntropy */
 

@@ -36,6 +36,7 @@ EXPORTS = [
     "trd_sigma_from_residuals", "trd_reconstruct", "trd_reconstruct_from",
     "trd_recovery_error", "trd_sampled_fwd", "trd_sampled_bwd", "trd_set_profiling",
     "trd_get_profile", "trd_kernel_launches", "trd_sigma_from_residuals_noalloc",
+    "trd_wait_selftest",
 ]
 
 
@@ -104,6 +105,7 @@ def load(path: str = LIB_PATH):
         "trd_get_profile": [vp, C.c_int, P(dbl)],
         "trd_kernel_launches": [],
         "trd_sigma_from_residuals_noalloc": [vp, i64, dbl, dbl, vp, vp],
+        "trd_wait_selftest": [vp, C.c_int, i64],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -310,13 +312,23 @@ class TRD:
                     "trd_reconstruct_from")
         return out
 
-    def set_profiling(self, on: bool = True):
-        self._check(self.lib.trd_set_profiling(self.h, 1 if on else 0), "trd_set_profiling")
+    def set_profiling(self, on=True):
+        """Tracing level: False/0 off, 1 the data passes only, True/2 every phase."""
+        level = 2 if on is True else (0 if on is False else int(on))
+        self._check(self.lib.trd_set_profiling(self.h, level), "trd_set_profiling")
+
+    PHASES = ["pass1", "pass2", "merge", "reduce", "backcontract", "gram", "cholesky", "solve",
+              "update", "sigma", "stop", "other"]
 
     def get_profile(self, reset: bool = False) -> dict:
-        out = (C.c_double * 4)()
+        """Per-phase totals (ms) and counts of the traced intervals (see trd_get_profile)."""
+        out = (C.c_double * 24)()
         self._check(self.lib.trd_get_profile(self.h, 1 if reset else 0, out), "trd_get_profile")
-        return {"pass1_ms": out[0], "pass1_n": int(out[1]), "pass2_ms": out[2], "pass2_n": int(out[3])}
+        res = {}
+        for q, name in enumerate(self.PHASES):
+            res[name + "_ms"] = out[2 * q]
+            res[name + "_n"] = int(out[2 * q + 1])
+        return res
 
     # ------------------------------------------------------------------ sampled correntropy loss
     def sampled_fwd(self, cores, idx, x, sigma: float, resid=None) -> float:
@@ -343,6 +355,11 @@ class TRD:
                                              idx.shape[0], sigma, 1 if fp64 else 0, g_scale, gptrs),
                     "trd_sampled_bwd")
         return grads
+
+    def wait_selftest(self, arrive: bool, limit: int) -> int:
+        """Run the bounded device wait once (see trd_wait_selftest); returns the raw status
+        (TRD_OK or TRD_ETIMEOUT) instead of raising, so a test can check it."""
+        return int(self.lib.trd_wait_selftest(self.h, 1 if arrive else 0, int(limit)))
 
     def recovery_error(self, Xref) -> float:
         out = C.c_double()

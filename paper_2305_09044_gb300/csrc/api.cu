@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <atomic>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "trd_internal.cuh"
@@ -65,6 +66,22 @@ enum : int { S_SIGMA = 0, S_SIGMA_PREV = 1, S_NUM = 2, S_DEN = 3, S_ETA = 4, S_L
 // report_dev layout: [0..7] eta per core, [8..15] objective per core, [16] e, [17] sigma
 enum : int { R_ETA = 0, R_OBJ = 8, R_E = 16, R_SIGMA = 17 };
 
+// Identity of a merged half (inner block 0..c-1 or outer block c..N-1) of the current view:
+// which half, which view, and the versions of the cores in it.
+struct HalfTag {
+  bool valid = false;
+  int half = -1;
+  uint64_t view_gen = 0;
+  int c = 0, Kp = 0;
+  uint64_t ver[kMaxN] = {};
+  bool operator==(const HalfTag& o) const {
+    if (!valid || !o.valid || half != o.half || view_gen != o.view_gen || c != o.c || Kp != o.Kp) return false;
+    for (int m = 0; m < kMaxN; ++m)
+      if (ver[m] != o.ver[m]) return false;
+    return true;
+  }
+};
+
 // extra per-handle buffers that do not need to be visible to other units
 struct Extra {
   DevBuf meta;          // [N] core pointers, [N] dims (int64), [N] ranks (int)
@@ -74,7 +91,14 @@ struct Extra {
   DevBuf recA, recC;    // reconstruction operands
   DevBuf errp;          // reconstruction error partials
   DevBuf tmpZ[kMaxN];   // cores given to trd_reconstruct_from
-  DevBuf probe_xsq;
+  DevBuf probe_a, probe_b, probe_x;   // adaptive-width probe: inner / outer index, data
+  DevBuf dotpart, solve_ctr;          // per-row parts of <d, h>, completion counter
+  // what the merged-half buffers hold (FP32/FP64 h->Sst / h->Sstr, BF16 operands bS* / bT*)
+  HalfTag tagSst, tagSstr, tagBst, tagBstr;
+  uint64_t view_gen = 0;    // 0 = the full tensor; every drawn sketch gets a new number
+  uint64_t sketch_count = 0;
+  bool probe_ready = false;
+  int64_t probe_Pin = 0;
   DevBuf Ework;         // FGMC factor partial sums
   // sampled correntropy loss: cores in FP64, merged halves, their gradients, partials
   DevBuf smpZ[kMaxN], smpA, smpC, smpGA, smpGC, smpGAd, smpGCd, smpPre, smpPost, smpDpart, smpD, smpLoss;
@@ -86,17 +110,19 @@ struct Extra {
   const float* mst_X[2] = {nullptr, nullptr};
   const uint32_t* mst_M[2] = {nullptr, nullptr};
   int64_t mst_Pin[2] = {-1, -1}, mst_Pout[2] = {-1, -1};
+  uint64_t mst_gen[2] = {~0ull, ~0ull};   // view (sketch) the relayout was made for
   int64_t mst_W[2] = {0, 0};
   int64_t ldT = 0, W = 0;
   int mst_o = 0;
   int tcG = 0;
   // tracing: event pairs around data-pass launches (kind 0 = pass 1, 1 = pass 2)
-  bool prof = false;
+  int prof = 0;            // 0 off, 1 data passes, 2 every phase
   std::vector<cudaEvent_t> ev_pool;
   struct Pending { cudaEvent_t a, b; int kind; };
   std::vector<Pending> pending;
-  double prof_ms[2] = {0, 0};
-  int64_t prof_n[2] = {0, 0};
+  static constexpr int NPROF = 12;
+  double prof_ms[NPROF] = {};
+  int64_t prof_n[NPROF] = {};
   cudaEvent_t ev_open = nullptr;
 };
 
@@ -131,6 +157,24 @@ void prof_end(trd_handle* h, int kind) {
   x->pending.push_back({x->ev_open, b, kind});
   x->ev_open = nullptr;
 }
+
+// Phases of a core update timed by the tracing hook (kinds of event pairs).
+enum : int { P_PASS1 = 0, P_PASS2 = 1, P_MERGE = 2, P_REDUCE = 3, P_GRAD = 4, P_GRAM = 5, P_CHOL = 6,
+             P_SOLVE = 7, P_UPDATE = 8, P_SIGMA = 9, P_STOP = 10 };
+
+// RAII: events around a phase when tracing is on (phases never nest).
+// Phase scope: traced only at profiling level 2 (the data passes are traced from level 1).
+struct PScope {
+  trd_handle* h;
+  int kind;
+  bool on;
+  PScope(trd_handle* hh, int k) : h(hh), kind(k), on(X_(hh)->prof >= 2) {
+    if (on) prof_begin(h);
+  }
+  ~PScope() {
+    if (on) prof_end(h, kind);
+  }
+};
 
 // After a stream synchronisation: fold finished event pairs into the totals.
 void prof_harvest(trd_handle* h) {
@@ -320,26 +364,63 @@ trd_status reset_D0(trd_handle* h) {
 }
 
 // ------------------------------------------------------------------ data passes
+HalfTag half_tag(trd_handle* h, int half, const Split& sp) {
+  HalfTag t;
+  t.valid = true;
+  t.half = half;
+  t.view_gen = X_(h)->view_gen;
+  t.c = sp.c;
+  t.Kp = sp.Kp;
+  const int m0 = half == 0 ? 0 : sp.c, m1 = half == 0 ? sp.c : h->N;
+  for (int m = m0; m < m1; ++m) t.ver[m] = h->ver[m];
+  return t;
+}
+
+// Merged halves of the current view into h->Sst (the stationary role: the half holding
+// core k) and h->Sstr.  The two buffers keep what they hold between calls: a half whose cores
+// and view are unchanged is not merged again (buffers trade roles when k crosses the cut).
+trd_status build_halves(trd_handle* h, int k) {
+  Extra* x = X_(h);
+  const Split& sp = h->split;
+  const int hs = k < sp.c ? 0 : 1;
+  const HalfTag want_st = half_tag(h, hs, sp), want_str = half_tag(h, 1 - hs, sp);
+  if (x->tagSst == want_str || x->tagSstr == want_st) {
+    std::swap(h->Sst, h->Sstr);
+    std::swap(x->tagSst, x->tagSstr);
+  }
+  const size_t e = elt(h);
+  const bool dbl = is_fp64(h);
+  const void* pst = h->Sst.p;
+  const void* pstr = h->Sstr.p;
+  TRY(ensure(h, h->Sst, e * sp.P_stat * sp.Kp));
+  TRY(ensure(h, h->Sstr, e * sp.P_strm * sp.Kp));
+  if (h->Sst.p != pst) x->tagSst.valid = false;
+  if (h->Sstr.p != pstr) x->tagSstr.valid = false;
+  const View& v = h->view;
+  const Chain inner = make_chain(h, v, 0, sp.c), outer = make_chain(h, v, sp.c, h->N);
+  if (!(x->tagSst == want_st)) {
+    CK(launch_chain(hs == 0 ? inner : outer, h->Sst.p, dbl, hs == 1, sp.Kp, h->stream), "merge stationary half");
+    x->tagSst = want_st;
+  }
+  if (!(x->tagSstr == want_str)) {
+    CK(launch_chain(hs == 0 ? outer : inner, h->Sstr.p, dbl, hs == 0, sp.Kp, h->stream), "merge streaming half");
+    x->tagSstr = want_str;
+  }
+  return TRD_OK;
+}
+
 trd_status build_merged(trd_handle* h, int k, bool with_h) {
   const View& v = h->view;
   const Split& sp = h->split;
   const int c = sp.c, Kp = sp.Kp;
   const bool dbl = is_fp64(h);
   const size_t e = elt(h);
-  TRY(ensure(h, h->Sst, e * sp.P_stat * Kp));
-  TRY(ensure(h, h->Sstr, e * sp.P_strm * Kp));
-  const Chain inner = make_chain(h, v, 0, c, with_h ? k : -1, with_h ? (const double*)h->h.p : nullptr);
-  const Chain outer = make_chain(h, v, c, h->N, with_h ? k : -1, with_h ? (const double*)h->h.p : nullptr);
-  if (with_h) {
-    TRY(ensure(h, h->Sh, e * sp.P_stat * Kp));
-    if (sp.rows) CK(launch_chain(inner, h->Sh.p, dbl, false, Kp, h->stream), "merge A_h");
-    else CK(launch_chain(outer, h->Sh.p, dbl, true, Kp, h->stream), "merge C_h");
-    return TRD_OK;
-  }
-  void* A = sp.rows ? h->Sst.p : h->Sstr.p;
-  void* C = sp.rows ? h->Sstr.p : h->Sst.p;
-  CK(launch_chain(inner, A, dbl, false, Kp, h->stream), "merge inner block");
-  CK(launch_chain(outer, C, dbl, true, Kp, h->stream), "merge outer block");
+  if (!with_h) return build_halves(h, k);
+  const Chain inner = make_chain(h, v, 0, c, k, (const double*)h->h.p);
+  const Chain outer = make_chain(h, v, c, h->N, k, (const double*)h->h.p);
+  TRY(ensure(h, h->Sh, e * sp.P_stat * Kp));
+  if (sp.rows) CK(launch_chain(inner, h->Sh.p, dbl, false, Kp, h->stream), "merge A_h");
+  else CK(launch_chain(outer, h->Sh.p, dbl, true, Kp, h->stream), "merge C_h");
   return TRD_OK;
 }
 
@@ -370,19 +451,60 @@ PassArgs pass_args(trd_handle* h) {
   return a;
 }
 
+// BF16 hi/lo operands of the two merged halves (rows zero-padded to the tensor-core K),
+// cached like the halves themselves.
+trd_status tc_operands(trd_handle* h) {
+  const Split& sp = h->split;
+  Extra* x = X_(h);
+  const int KP = tc_kpad(sp.Kp);
+  if (x->tagBst == x->tagSstr || x->tagBstr == x->tagSst) {
+    std::swap(x->bShi, x->bThi);
+    std::swap(x->bSlo, x->bTlo);
+    std::swap(x->tagBst, x->tagBstr);
+  }
+  const size_t b2 = sizeof(__nv_bfloat16);
+  const void* p0 = x->bShi.p;
+  const void* p1 = x->bSlo.p;
+  const void* p2 = x->bThi.p;
+  const void* p3 = x->bTlo.p;
+  TRY(ensure(h, x->bShi, b2 * sp.P_stat * KP));
+  TRY(ensure(h, x->bSlo, b2 * sp.P_stat * KP));
+  TRY(ensure(h, x->bThi, b2 * sp.P_strm * KP));
+  TRY(ensure(h, x->bTlo, b2 * sp.P_strm * KP));
+  if (x->bShi.p != p0 || x->bSlo.p != p1) x->tagBst.valid = false;
+  if (x->bThi.p != p2 || x->bTlo.p != p3) x->tagBstr.valid = false;
+  if (!(x->tagBst == x->tagSst)) {
+    CK(launch_tc_prep((const float*)h->Sst.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bShi.p,
+                      (__nv_bfloat16*)x->bSlo.p, h->stream), "bf16 stationary operands");
+    x->tagBst = x->tagSst;
+  }
+  if (!(x->tagBstr == x->tagSstr)) {
+    CK(launch_tc_prep((const float*)h->Sstr.p, sp.P_strm, sp.Kp, (__nv_bfloat16*)x->bThi.p,
+                      (__nv_bfloat16*)x->bTlo.p, h->stream), "bf16 streaming operands");
+    x->tagBstr = x->tagSstr;
+  }
+  return TRD_OK;
+}
+
 trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
   const Split& sp = h->split;
   Extra* x = X_(h);
-  const int KP = tc_kpad();
-  if (sp.Kp > KP) return set_err(h, TRD_ENOTIMPL, "BF16 path supports r_1 r_c <= 64");
+  const int KP = tc_kpad(sp.Kp);
+  if (!KP) return set_err(h, TRD_ENOTIMPL, "BF16 path supports r_1 r_c <= 128");
   if (sp.P_in % 4) return set_err(h, TRD_ENOTIMPL, "BF16 path needs the inner block size to be a multiple of 4");
-  TRY(build_merged(h, k, false));
   const View& v = h->view;
-  // observation bits of every stationary index along the streaming index (cached)
+  const int64_t RB = (sp.P_stat + tc_bm() - 1) / tc_bm();
+  const int64_t NT = (sp.P_strm + tc_bn() - 1) / tc_bn();
+  const int G = (int)imin(h->num_sms, RB * NT);
   const int o = sp.rows ? 0 : 1;
   const int64_t nstat = sp.rows ? sp.P_in : sp.P_out, nstrm = sp.rows ? sp.P_out : sp.P_in;
   const int64_t W = ((nstrm + 31) / 32 + 3) / 4 * 4;
-  if (x->mst_X[o] != v.X || x->mst_M[o] != v.M || x->mst_Pin[o] != sp.P_in || x->mst_Pout[o] != sp.P_out) {
+  {
+  PScope ps(h, P_MERGE);
+  TRY(build_merged(h, k, false));
+  // observation bits of every stationary index along the streaming index (cached)
+  if (x->mst_X[o] != v.X || x->mst_M[o] != v.M || x->mst_Pin[o] != sp.P_in || x->mst_Pout[o] != sp.P_out ||
+      x->mst_gen[o] != x->view_gen) {
     TRY(ensure(h, x->Mst[o], sizeof(uint32_t) * (size_t)(nstat * W)));
     if (sp.rows)
       CK(launch_mask_transpose(v.M, sp.P_in, sp.P_out, W, (uint32_t*)x->Mst[o].p, h->stream), "mask layout");
@@ -392,23 +514,14 @@ trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
     x->mst_M[o] = v.M;
     x->mst_Pin[o] = sp.P_in;
     x->mst_Pout[o] = sp.P_out;
+    x->mst_gen[o] = x->view_gen;
   }
   x->W = W;
   x->mst_o = o;
   const int64_t ldT = (sp.P_strm + 63) / 64 * 64;
   x->ldT = ldT;
-  const size_t b2 = sizeof(__nv_bfloat16);
-  TRY(ensure(h, x->bShi, b2 * sp.P_stat * KP));
-  TRY(ensure(h, x->bSlo, b2 * sp.P_stat * KP));
-  TRY(ensure(h, x->bThi, b2 * sp.P_strm * KP));
-  TRY(ensure(h, x->bTlo, b2 * sp.P_strm * KP));
-  CK(launch_tc_prep((const float*)h->Sst.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bShi.p,
-                    (__nv_bfloat16*)x->bSlo.p, h->stream), "bf16 stationary operands");
-  CK(launch_tc_prep((const float*)h->Sstr.p, sp.P_strm, sp.Kp, (__nv_bfloat16*)x->bThi.p,
-                    (__nv_bfloat16*)x->bTlo.p, h->stream), "bf16 streaming operands");
-  const int64_t RB = (sp.P_stat + tc_bm() - 1) / tc_bm();
-  const int64_t NT = (sp.P_strm + tc_bn() - 1) / tc_bn();
-  const int G = (int)imin(h->num_sms, RB * NT);
+  TRY(tc_operands(h));
+  }
   x->tcG = G;
   TRY(ensure(h, h->Tpart, sizeof(float) * (size_t)(G + RB) * tc_bm() * sp.Kp));
   TRY(ensure(h, h->stat_part, sizeof(double) * 8 * (size_t)G));
@@ -420,6 +533,7 @@ trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
                     h->stream),
      "tensor-core data pass 1");
   prof_end(h, 0);
+  PScope ps(h, P_REDUCE);
   CK(launch_reduce_slots((const float*)h->Tpart.p, RB, NT, G, sp.P_stat, sp.Kp, (double*)h->Tsum.p, h->stream),
      "reduce contraction");
   CK(launch_reduce_stats((const double*)h->stat_part.p, G, (double*)h->stat_sum.p, h->dstatus, h->stream),
@@ -431,10 +545,15 @@ trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
 trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
   const Split& sp = h->split;
   Extra* x = X_(h);
-  TRY(build_merged(h, k, true));
-  TRY(ensure(h, x->bSh, sizeof(__nv_bfloat16) * sp.P_stat * tc_kpad()));
-  CK(launch_tc_prep((const float*)h->Sh.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bSh.p, nullptr, h->stream),
-     "bf16 step operands");
+  {
+    PScope ps(h, P_MERGE);
+    TRY(build_halves(h, k));      // normally cached: restores the roles of core k
+    TRY(tc_operands(h));
+    TRY(build_merged(h, k, true));
+    TRY(ensure(h, x->bSh, sizeof(__nv_bfloat16) * sp.P_stat * tc_kpad(sp.Kp)));
+    CK(launch_tc_prep((const float*)h->Sh.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bSh.p, nullptr, h->stream),
+       "bf16 step operands");
+  }
   prof_begin(h);
   CK(launch_pass_tc(sp.rows, true, (const __nv_bfloat16*)x->bShi.p, (const __nv_bfloat16*)x->bSlo.p,
                     (const __nv_bfloat16*)x->bSh.p, (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p,
@@ -443,6 +562,7 @@ trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
                     (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, x->tcG, false, h->stream),
      "tensor-core data pass 2");
   prof_end(h, 1);
+  PScope ps(h, P_REDUCE);
   double* s2 = (double*)x->stat_sum2.p;
   CK(launch_reduce_stats((const double*)h->stat_part.p, x->tcG, s2, h->dstatus, h->stream), "reduce den");
   *den = s2 + 6;
@@ -457,7 +577,10 @@ trd_status run_pass1(trd_handle* h, int k, bool full_stats = true) {
   } else {
     if (sp.Kp > 112 && is_fp64(h)) return set_err(h, TRD_ENOTIMPL, "FP64 path supports r_1 r_c <= 112");
     if (sp.Kp > 256) return set_err(h, TRD_ENOTIMPL, "data passes support r_1 r_c <= 256");
-    TRY(build_merged(h, k, false));
+    {
+      PScope ps(h, P_MERGE);
+      TRY(build_merged(h, k, false));
+    }
     int splits = choose_splits(h, sp);
     const int64_t gx = (sp.P_stat + 63) / 64;
     TRY(ensure(h, h->Tpart, elt(h) * (size_t)splits * sp.P_stat * sp.Kp));
@@ -470,6 +593,7 @@ trd_status run_pass1(trd_handle* h, int k, bool full_stats = true) {
     prof_end(h, 0);
     h->splits = used;
     h->ctas = ctas;
+    PScope ps(h, P_REDUCE);
     CK(launch_reduce_T(h->Tpart.p, is_fp64(h), used, sp.P_stat * (int64_t)sp.Kp, (double*)h->Tsum.p,
                        h->stream), "reduce contraction");
     CK(launch_reduce_stats((const double*)h->stat_part.p, ctas, (double*)h->stat_sum.p, h->dstatus,
@@ -483,6 +607,7 @@ trd_status run_pass1(trd_handle* h, int k, bool full_stats = true) {
 
 trd_status run_gradient(trd_handle* h, int k) {
   if (h->pass1_k != k) return set_err(h, TRD_EINVAL, "trd_residual_weights must run for this core first");
+  PScope ps(h, P_GRAD);
   const View& v = h->view;
   const Split& sp = h->split;
   const int N = h->N, c = sp.c;
@@ -530,26 +655,62 @@ trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int
   const int64_t n = h->I[k] * (int64_t)K;
   double* d = (double*)h->d.p;
   double* hh = (double*)h->h.p;
+  bool dot_done = false;
   if (gram == TRD_GRAM_NONE) {
     CK(cudaMemcpyAsync(hh, d, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream), "copy d");
   } else {
     const double* G;
-    if (gram == TRD_GRAM_LOCAL) {
-      TRY(local_gram(h, k));
-      G = (const double*)X_(h)->Gloc.p;
-    } else {
-      TRY(ensure_gram(h, k));
-      G = (const double*)h->G.p;
+    {
+      PScope ps(h, P_GRAM);
+      if (gram == TRD_GRAM_LOCAL) {
+        TRY(local_gram(h, k));
+        G = (const double*)X_(h)->Gloc.p;
+      } else {
+        TRY(ensure_gram(h, k));
+        G = (const double*)h->G.p;
+      }
     }
-    CK(launch_cholesky(G, K, lambda, (double*)h->L.p, h->scal, h->dstatus, h->stream), "cholesky");
-    CK(launch_solve_rows((const double*)h->L.p, d, hh, K, h->I[k], h->stream), "triangular solves");
+    if (ldl_fits(K)) {
+      // LDL^T (FP64), then h = d (L D L^T)^{-1} by row-parallel substitutions
+      double* Lcm = (double*)h->L.p;
+      double* Dinv = Lcm + (size_t)K * K;
+      {
+        PScope ps(h, P_CHOL);
+        CK(launch_ldl_factor(G, K, lambda, Lcm, Dinv, h->scal, h->dstatus, h->stream), "LDL^T factorisation");
+      }
+      PScope ps(h, P_SOLVE);
+      Extra* xs = X_(h);
+      TRY(ensure(h, xs->dotpart, sizeof(double) * (size_t)h->I[k]));
+      if (!xs->solve_ctr.p) {
+        TRY(ensure(h, xs->solve_ctr, 256));
+        CK(cudaMemsetAsync(xs->solve_ctr.p, 0, 256, h->stream), "counter");
+      }
+      CK(launch_ldl_solve(Lcm, Dinv, d, hh, K, h->I[k], (double*)xs->dotpart.p, (unsigned int*)xs->solve_ctr.p,
+                          h->scal + S_NUM, h->stream),
+         "triangular solves");
+      dot_done = true;
+    } else {
+      {
+        PScope ps(h, P_CHOL);
+        CK(launch_cholesky(G, K, lambda, (double*)h->L.p, h->scal, h->dstatus, h->stream), "cholesky");
+      }
+      PScope ps(h, P_SOLVE);
+      CK(launch_solve_rows((const double*)h->L.p, d, hh, K, h->I[k], h->stream), "triangular solves");
+    }
   }
-  CK(launch_dot(d, hh, n, h->scal + S_NUM, h->stream), "<d,h>");
+  if (!dot_done) {
+    PScope ps(h, P_SOLVE);
+    CK(launch_dot(d, hh, n, h->scal + S_NUM, h->stream), "<d,h>");
+  }
   double* den = h->scal + S_DEN;
   if (eta_fixed <= 0 && h->prec == TRD_BF16) {
     TRY(run_pass2_tc(h, k, &den));
   } else if (eta_fixed <= 0) {
-    TRY(build_merged(h, k, true));
+    {
+      PScope ps(h, P_MERGE);
+      TRY(build_halves(h, k));    // normally cached: restores the roles of core k
+      TRY(build_merged(h, k, true));
+    }
     int ctas = 0, used = 0;
     PassArgs a = pass_args(h);
     prof_begin(h);
@@ -560,6 +721,7 @@ trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int
     CK(launch_reduce_stats((const double*)h->stat_part.p, ctas, s2, h->dstatus, h->stream), "reduce den");
     den = s2 + 6;
   }
+  PScope psu(h, P_UPDATE);
   CK(launch_eta(h->scal + S_NUM, den, eta_fixed, h->dstatus, h->scal + S_ETA, eta_slot, h->stream),
      "step size");
   CK(launch_axpy_core(h->Z[k], hh, n, h->scal + S_ETA, h->stream), "core update");
@@ -582,23 +744,61 @@ trd_status set_sigma(trd_handle* h, double sigma) {
 
 trd_status run_adaptive(trd_handle* h, double sigma_prev, const double* sigma_prev_dev = nullptr) {
   if (!h->X) return set_err(h, TRD_EINVAL, "no data attached");
+  PScope ps(h, P_SIGMA);
   Extra* x = X_(h);
   const int64_t n = h->numel <= kProbeMax ? h->numel : kProbeMax;
-  TRY(ensure(h, h->probe_vals, sizeof(double) * n));
   TRY(ensure(h, h->probe_keys, sizeof(uint64_t) * n));
-  TRY(ensure(h, x->probe_xsq, sizeof(double) * n));
   TRY(ensure(h, h->probe_work, sizeof(double) * sigma_work_doubles()));
   // merged subchains of the full tensor for the current cores (same split rule as the passes)
   const View fv = full_view(h);
   const Split sp = choose_split(h, fv, 0);
-  const size_t e = elt(h);
-  TRY(ensure(h, x->recA, e * sp.P_in * sp.Kp));
-  TRY(ensure(h, x->recC, e * sp.P_out * sp.Kp));
-  CK(launch_chain(make_chain(h, fv, 0, sp.c), x->recA.p, is_fp64(h), false, sp.Kp, h->stream), "probe merge inner");
-  CK(launch_chain(make_chain(h, fv, sp.c, h->N), x->recC.p, is_fp64(h), true, sp.Kp, h->stream), "probe merge outer");
-  CK(launch_probe_sigma_merged(x->recA.p, x->recC.p, is_fp64(h), sp.Kp, sp.P_in, h->X, h->M, h->numel, sigma_prev,
-                               sigma_prev_dev, (double*)h->probe_vals.p, (uint64_t*)h->probe_keys.p,
-                               (double*)x->probe_xsq.p, (double*)h->probe_work.p, h->scal + S_SIGMA, h->stream),
+  if (sp.Kp > 256) return set_err(h, TRD_ENOTIMPL, "the adaptive width supports r_1 r_c <= 256");
+  if (!x->probe_ready || x->probe_Pin != sp.P_in) {
+    // the probe entries, their block indices and data depend only on X, the mask and the cut
+    TRY(ensure(h, x->probe_a, sizeof(int32_t) * n));
+    TRY(ensure(h, x->probe_b, sizeof(int32_t) * n));
+    TRY(ensure(h, x->probe_x, sizeof(float) * n));
+    const int64_t* lin_dev = nullptr;
+    if (h->numel > kProbeMax) {
+      // sorted probe positions, uploaded once per data set through the key buffer
+      std::vector<int64_t> lin;
+      probe_positions(h->numel, lin);
+      CK(cudaMemcpyAsync(h->probe_keys.p, lin.data(), sizeof(int64_t) * lin.size(), cudaMemcpyHostToDevice,
+                         h->stream), "probe upload");
+      CK(cudaStreamSynchronize(h->stream), "probe upload");
+      lin_dev = (const int64_t*)h->probe_keys.p;
+    }
+    CK(launch_probe_setup(h->X, h->M, lin_dev, n, sp.P_in, (int32_t*)x->probe_a.p, (int32_t*)x->probe_b.p,
+                          (float*)x->probe_x.p, h->stream), "probe set-up");
+    x->probe_ready = true;
+    x->probe_Pin = sp.P_in;
+  }
+  const void* A;
+  const void* Cm;
+  if (!h->sketched) {
+    // the full view is current: use (and leave behind) the cached halves, in the roles of
+    // the update of core 0; the split of a core update in progress is kept
+    const Split saved = h->split;
+    h->split = sp;
+    const trd_status st = build_halves(h, 0);
+    h->split = saved;
+    if (st != TRD_OK) return st;
+    A = h->Sst.p;
+    Cm = h->Sstr.p;
+  } else {
+    const size_t e = elt(h);
+    TRY(ensure(h, x->recA, e * sp.P_in * sp.Kp));
+    TRY(ensure(h, x->recC, e * sp.P_out * sp.Kp));
+    CK(launch_chain(make_chain(h, fv, 0, sp.c), x->recA.p, is_fp64(h), false, sp.Kp, h->stream), "probe merge inner");
+    CK(launch_chain(make_chain(h, fv, sp.c, h->N), x->recC.p, is_fp64(h), true, sp.Kp, h->stream),
+       "probe merge outer");
+    A = x->recA.p;
+    Cm = x->recC.p;
+  }
+  CK(launch_probe_sigma_merged(A, Cm, is_fp64(h), sp.Kp, (const int32_t*)x->probe_a.p,
+                               (const int32_t*)x->probe_b.p, (const float*)x->probe_x.p, n, sigma_prev,
+                               sigma_prev_dev, (uint64_t*)h->probe_keys.p, (double*)h->probe_work.p,
+                               h->scal + S_SIGMA, h->stream),
      "adaptive width");
   h->sigma_set = true;
   return TRD_OK;
@@ -608,6 +808,7 @@ trd_status use_full_view(trd_handle* h) {
   h->view = full_view(h);
   h->view_k = -1;
   h->sketched = false;
+  X_(h)->view_gen = 0;
   return TRD_OK;
 }
 
@@ -671,6 +872,7 @@ trd_status sample(trd_handle* h, int k, const int32_t* const* idx, const int32_t
   h->view = v;
   h->view_k = k;
   h->sketched = true;
+  X_(h)->view_gen = ++X_(h)->sketch_count;
   h->pass1_k = -1;
   h->grad_k = -1;
   return TRD_OK;
@@ -723,7 +925,7 @@ trd_status alloc_state(trd_handle* h) {
       chain = std::max(chain, (size_t)h->R[k] * h->R[k] * h->R[m] * h->R[m]);
   const int64_t IN = h->I[N - 1];
   TRY(ensure(h, h->G, sizeof(double) * maxK * maxK));
-  TRY(ensure(h, h->L, sizeof(double) * (maxK * maxK + maxK)));
+  TRY(ensure(h, h->L, sizeof(double) * (2 * maxK * maxK + maxK)));   // factor, D^{-1}, row-major copy
   TRY(ensure(h, h->T1, sizeof(double) * chain));
   TRY(ensure(h, h->T2, sizeof(double) * chain));
   TRY(ensure(h, h->d, sizeof(double) * maxIK));
@@ -841,11 +1043,13 @@ void trd_destroy(trd_t* h) {
   DevBuf* bufs[] = {&h->XI, &h->PI, &h->Sst, &h->Sstr, &h->Sh, &h->Sst_bf, &h->Sstr_bf, &h->Sh_bf,
                     &h->SstrT_bf, &h->SstT_bf, &h->Tpart, &h->Tsum, &h->stat_part, &h->stat_sum,
                     &h->pre, &h->post, &h->dpart, &h->d, &h->h, &h->G, &h->L, &h->T1, &h->T2,
-                    &h->D, &h->Dprev, &h->probe_keys, &h->probe_vals, &h->probe_work};
+                    &h->D, &h->Dprev, &h->probe_keys, &h->probe_work};
   for (DevBuf* b : bufs) free_buf(*b);
   Extra* x = X_(h);
-  DevBuf* xb[] = {&x->Ework, &x->meta, &x->stat_sum2, &x->Gloc, &x->recA, &x->recC, &x->errp, &x->probe_xsq,
-                  &x->bShi, &x->bSlo, &x->bSh, &x->bThi, &x->bTlo, &x->bTT, &x->Mst[0], &x->Mst[1]};
+  DevBuf* xb[] = {&x->Ework, &x->meta,    &x->stat_sum2, &x->Gloc,    &x->recA, &x->recC,
+                  &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr,
+                  &x->bShi,  &x->bSlo,    &x->bSh,       &x->bThi,    &x->bTlo,    &x->bTT,
+                  &x->Mst[0], &x->Mst[1]};
   for (DevBuf* b : xb) free_buf(*b);
   for (int k = 0; k < kMaxN; ++k) { free_buf(x->Eloc[k]); free_buf(x->tmpZ[k]); free_buf(x->smpZ[k]); }
   DevBuf* sb[] = {&x->smpA, &x->smpC, &x->smpGA, &x->smpGC, &x->smpGAd, &x->smpGCd, &x->smpPre, &x->smpPost,
@@ -870,6 +1074,7 @@ trd_status trd_set_data(trd_t* h, const float* X, const uint32_t* mask) {
     return set_err(h, TRD_EINVAL, "X and mask must be 16-byte aligned");
   h->X = X;
   h->M = mask;
+  X_(h)->probe_ready = false;
   h->numel = 1;
   for (int m = 0; m < h->N; ++m) h->numel *= h->I[m];
   use_full_view(h);
@@ -1020,14 +1225,10 @@ trd_status trd_sigma_from_residuals(trd_t* h, const float* r, int64_t n, double 
                                     double* sigma_out) {
   TRY(check_handle(h));
   if (!r || n < 1 || rms < 0 || !sigma_out) return set_err(h, TRD_EINVAL, "bad arguments");
-  Extra* x = X_(h);
-  TRY(ensure(h, h->probe_vals, sizeof(double) * n));
   TRY(ensure(h, h->probe_keys, sizeof(uint64_t) * n));
-  TRY(ensure(h, x->probe_xsq, sizeof(double) * n));
   TRY(ensure(h, h->probe_work, sizeof(double) * sigma_work_doubles()));
-  CK(launch_sigma_from_floats(r, n, rms, sigma_prev, (double*)h->probe_vals.p, (uint64_t*)h->probe_keys.p,
-                              (double*)x->probe_xsq.p, (double*)h->probe_work.p, h->scal + S_SIGMA + 8,
-                              h->stream), "sigma from residuals");
+  CK(launch_sigma_from_floats(r, n, rms, sigma_prev, (uint64_t*)h->probe_keys.p, (double*)h->probe_work.p,
+                              h->scal + S_SIGMA + 8, h->stream), "sigma from residuals");
   CK(cudaMemcpyAsync(h->host_pinned, h->scal + S_SIGMA + 8, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
      "sigma");
   TRY(sync_and_status(h));
@@ -1084,9 +1285,12 @@ trd_status trd_step(trd_t* h, const trd_params* p, trd_report* rep) {
     TRY(run_update(h, k, p->lambda, -1.0, p->gram, h->report_dev + R_ETA + k));
     slots += h->slots_last;
   }
+  {
+  PScope ps(h, P_STOP);
   TRY(compute_D(h, (double*)h->D.p));
   CK(launch_stop_error((const double*)h->D.p, (double*)h->Dprev.p, h->I[N - 1] * h->I[N - 1],
                        h->report_dev + R_E, h->stream), "stopping quantity");
+  }
   CK(cudaMemcpyAsync(h->report_dev + R_SIGMA, h->scal + S_SIGMA, sizeof(double), cudaMemcpyDeviceToDevice,
                      h->stream), "sigma");
   CK(cudaMemcpyAsync(h->host_pinned, h->report_dev, sizeof(double) * 32, cudaMemcpyDeviceToHost, h->stream),
@@ -1166,7 +1370,8 @@ trd_status trd_recovery_error(trd_t* h, const float* ref, double* err) {
 
 trd_status trd_set_profiling(trd_t* h, int on) {
   TRY(check_handle(h));
-  X_(h)->prof = on != 0;
+  if (on < 0 || on > 2) return set_err(h, TRD_EINVAL, "profiling level must be 0, 1 or 2");
+  X_(h)->prof = on;
   return TRD_OK;
 }
 
@@ -1176,18 +1381,25 @@ trd_status trd_get_profile(trd_t* h, int reset, double* out) {
   CK(cudaStreamSynchronize(h->stream), "stream synchronize");
   prof_harvest(h);
   Extra* x = X_(h);
-  out[0] = x->prof_ms[0];
-  out[1] = (double)x->prof_n[0];
-  out[2] = x->prof_ms[1];
-  out[3] = (double)x->prof_n[1];
-  if (reset) {
-    x->prof_ms[0] = x->prof_ms[1] = 0;
-    x->prof_n[0] = x->prof_n[1] = 0;
+  for (int q = 0; q < Extra::NPROF; ++q) {
+    out[2 * q] = x->prof_ms[q];
+    out[2 * q + 1] = (double)x->prof_n[q];
+    if (reset) {
+      x->prof_ms[q] = 0;
+      x->prof_n[q] = 0;
+    }
   }
   return TRD_OK;
 }
 
 int64_t trd_kernel_launches(void) { return launches_total(); }
+
+trd_status trd_wait_selftest(trd_t* h, int arrive, int64_t limit) {
+  TRY(check_handle(h));
+  if (limit < 1 || limit > (int64_t)1 << 24) return set_err(h, TRD_EINVAL, "limit out of range");
+  CK(launch_wait_selftest(arrive != 0, (uint32_t)limit, h->dstatus, h->stream), "wait self-test");
+  return sync_and_status(h);
+}
 
 // ------------------------------------------------------------------ sampled correntropy loss
 static trd_status sampled_setup(trd_t* h, const void* const* cores_dev, int fp64, const double** Zc, Split& sp,

@@ -76,29 +76,33 @@ cudaError_t launch_fgmc_E(const double* Z, const int32_t* idx, int64_t n, int rk
 
 // ------------------------------------------------------------------ FP64 GEMM (small)
 // C[M x N] = A[M x K] * B, B is K x N (transB = 0) or N x K (transB = 1); all row-major.
+// C = A B (or A B^T), FP64, 8 x 8 output tile per 64-thread block: the products here are
+// small (K <= 400), so spreading them over many SMs matters more than operand reuse (GB300's
+// FP64 issue rate per SM is low).
 __global__ void k_dgemm(const double* __restrict__ A, const double* __restrict__ B,
                         double* __restrict__ C, int M, int N, int K, int transB) {
-  __shared__ double sA[16][17], sB[16][17];
+  __shared__ double sA[8][9], sB[8][9];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
-  double acc = 0.0;
-  for (int k0 = 0; k0 < K; k0 += 16) {
+  const int row = blockIdx.y * 8 + ty, col = blockIdx.x * 8 + tx;
+  // four independent accumulators keep the dependent FP64 FMA chain short
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k0 = 0; k0 < K; k0 += 8) {
     sA[ty][tx] = (row < M && k0 + tx < K) ? A[(int64_t)row * K + k0 + tx] : 0.0;
-    const int bk = k0 + ty, bn = blockIdx.x * 16 + tx;
+    const int bk = k0 + ty, bn = blockIdx.x * 8 + tx;
     double bv = 0.0;
     if (bk < K && bn < N) bv = transB ? B[(int64_t)bn * K + bk] : B[(int64_t)bk * N + bn];
     sB[ty][tx] = bv;
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 16; ++k) acc = fma(sA[ty][k], sB[k][tx], acc);
+    for (int k = 0; k < 8; ++k) acc[k & 3] = fma(sA[ty][k], sB[k][tx], acc[k & 3]);
     __syncthreads();
   }
-  if (row < M && col < N) C[(int64_t)row * N + col] = acc;
+  if (row < M && col < N) C[(int64_t)row * N + col] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
 cudaError_t launch_dgemm(const double* A, const double* B, double* C, int M, int N, int K,
                          bool transB, cudaStream_t st) {
-  dim3 grid((N + 15) / 16, (M + 15) / 16), block(16, 16);
+  dim3 grid((N + 7) / 8, (M + 7) / 8), block(8, 8);
   k_dgemm<<<grid, block, 0, st>>>(A, B, C, M, N, K, transB ? 1 : 0);
   note_launch();
   return cudaGetLastError();
@@ -123,7 +127,271 @@ cudaError_t launch_phi(const double* T, int p, int q, double* G, cudaStream_t st
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ Cholesky of G + lambda I
+// ------------------------------------------------------------------ LDL^T of G + lambda I
+// FP64 throughout.  GB300 issues FP64 FMAs at about 1.6 per clock per SM with a dependent
+// latency near 70 clocks, so the factorisation is organised to keep every FP64 instruction
+// useful and the per-column critical path short:
+//  * one CTA; the lower triangle lives in registers, element e of the order "columns right
+//    to left, rows top to bottom" held by thread e % 256 -- the trailing part still active at
+//    column j is a prefix of that order, so every step is spread evenly over all threads;
+//  * no square roots (LDL^T), one reciprocal per pivot;
+//  * per column: update (one FMA per active element, the next pivot column first), publish
+//    the next column, one warp forms its reciprocal and scaled column, two barriers.
+
+// 1/p from the approximate FP32 reciprocal r0 and one step of the cubic iteration for the
+// reciprocal (Newton's iteration extended to third order):
+// with e = 1 - p r0, 1/p = r0 / (1 - e) = r0 (1 + e + e^2 + O(e^3)), and |e| <= 2^-22, so the
+// truncation error (~2^-66) is far below FP64 rounding.  Outside [1e-30, 1e30] (FP32 range
+// margins) the exact division is used.
+__device__ __forceinline__ double recip_fp64(double p) {
+  if (!(p > 1e-30 && p < 1e30)) return 1.0 / p;
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)p));   // relative error ~2^-23
+  const double r0 = (double)rf;
+  const double e = fma(-p, r0, 1.0);
+  return fma(r0, fma(e, e, e), r0);
+}
+
+constexpr int LDL_NT = 256;
+
+// Pivot step for column j (one warp): reciprocal of the pivot, scaled column
+// l_i = c_i / p (i > j) into s_l and into the column-major factor Lcm[j][i], D^{-1} entry;
+// flags a non-positive or non-finite pivot.
+__device__ __forceinline__ void ldl_pivot(int j, int K, const double* __restrict__ c, double* __restrict__ l,
+                                          double* __restrict__ Lcm, double* __restrict__ Dinv, int* s_bad,
+                                          int lane) {
+  const double p = c[j];
+  const bool bad = !(p > 0.0) || !isfinite(p);
+  const double r = bad ? 0.0 : recip_fp64(p);
+  for (int i = j + 1 + lane; i < K; i += 32) {
+    const double v = c[i] * r;
+    l[i] = v;
+    Lcm[(int64_t)j * K + i] = v;
+  }
+  if (lane == 0) {
+    Dinv[j] = r;
+    if (bad) *s_bad = 1;
+  }
+}
+
+// S = register slots per thread: K (K + 1) / 2 <= 256 S.
+template <int S>
+__global__ void __launch_bounds__(LDL_NT, 1)
+    k_ldl_factor(const double* __restrict__ G, int K, double lam_in, double* __restrict__ Lcm,
+                 double* __restrict__ Dinv, double* __restrict__ scal, int* __restrict__ dstatus) {
+  __shared__ double s_c[2][kLdlKmax];
+  __shared__ double s_l[2][kLdlKmax];
+  __shared__ double s_red[LDL_NT / 32];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wbase = tid & ~31;
+  double tr = 0.0;
+  for (int i = tid; i < K; i += LDL_NT) tr += G[(int64_t)i * K + i];
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_down_sync(0xffffffffu, tr, o);
+  if (lane == 0) s_red[warp] = tr;
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  double trace = 0.0;
+#pragma unroll
+  for (int w = 0; w < LDL_NT / 32; ++w) trace += s_red[w];
+  const double lam = lam_in >= 0 ? lam_in : -lam_in * trace / K;
+  if (tid == 0) scal[5] = lam;
+
+  // this thread's elements (i, m), i >= m, packed as i | m << 16; unused slots hold (0, 0),
+  // which is never updated or published
+  const int nel = K * (K + 1) / 2;
+  double w[S];
+  uint32_t im[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int e = tid + s * LDL_NT;
+    w[s] = 0.0;
+    im[s] = 0u;
+    if (e < nel) {
+      int q = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while ((q + 1) * (q + 2) / 2 <= e) ++q;
+      while (q * (q + 1) / 2 > e) --q;
+      const int m = K - 1 - q, i = m + (e - q * (q + 1) / 2);
+      w[s] = G[(int64_t)i * K + m] + (i == m ? lam : 0.0);
+      im[s] = (uint32_t)i | ((uint32_t)m << 16);
+      if (m == 0) s_c[0][i] = w[s];
+    }
+  }
+  __syncthreads();
+  if (warp == 0) ldl_pivot(0, K, s_c[0], s_l[0], Lcm, Dinv, &s_bad, lane);
+  __syncthreads();
+  for (int j = 0; j + 1 < K; ++j) {
+    if (s_bad) break;                       // uniform: read after a barrier
+    const double* cj = s_c[j & 1];
+    const double* lj = s_l[j & 1];
+    double* cn = s_c[(j + 1) & 1];
+    // active elements (columns > j) are the first nact of the order; a slot whose whole warp
+    // lies beyond them is skipped (warp-uniform), so no FP64 instruction is spent on it.
+    // Loads first, then the independent FMAs, then the publication of column j + 1.
+    const int nact = (K - 1 - j) * (K - j) / 2;
+    double li[S], cm[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      li[s] = 0.0;
+      cm[s] = 0.0;
+      if (s * LDL_NT + wbase < nact) {
+        const int i = (int)(im[s] & 0xFFFFu), m = (int)(im[s] >> 16);
+        if (m > j) {
+          li[s] = lj[i];
+          cm[s] = cj[m];
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      if (s * LDL_NT + wbase < nact) w[s] = fma(-li[s], cm[s], w[s]);
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      if (s * LDL_NT + wbase < nact && (int)(im[s] >> 16) == j + 1) cn[im[s] & 0xFFFFu] = w[s];
+    __syncthreads();
+    if (warp == 0) ldl_pivot(j + 1, K, cn, s_l[(j + 1) & 1], Lcm, Dinv, &s_bad, lane);
+    __syncthreads();
+  }
+  if (tid == 0 && s_bad) atomicOr(dstatus, (int)DEV_SINGULAR);
+}
+
+// h = d (L D L^T)^{-1}, one warp per row of d (I_k x K, row-major): v L^T = d (forward),
+// u = v D^{-1}, h L = u (backward), both in column-oriented form (the finished unknown is
+// broadcast by a shuffle and subtracted from the rest).  The factor is staged in shared
+// memory by asynchronous copies (column-major, padded column stride KP + 1 so that columns
+// and rows are both read without bank conflicts); only entries below the diagonal are used.
+// C = ceil(K / 32) entries per lane.
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc)
+               : "memory");
+}
+
+template <int C>
+__global__ void __launch_bounds__(32) k_ldl_solve(const double* __restrict__ Lcm, const double* __restrict__ Dinv,
+                                                  const double* __restrict__ d, double* __restrict__ h, int K,
+                                                  int64_t rows, double* __restrict__ dot_part,
+                                                  unsigned int* __restrict__ ctr, double* __restrict__ num) {
+  constexpr int KP = 32 * C, LD = KP + 1;
+  extern __shared__ double sL[];          // [K][LD]: sL[j * LD + i] = L[i][j]
+  double* sD = sL + (size_t)K * LD;       // [KP]
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < K; ++j)
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int i = c * 32 + lane;
+      if (i < K) cp_async8(sL + j * LD + i, Lcm + (int64_t)j * K + i);
+    }
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int i = c * 32 + lane;
+    sD[i] = i < K ? Dinv[i] : 0.0;
+  }
+  __syncwarp();
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const double* dr = d + row * K;
+    double s[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int i = c * 32 + lane;
+      s[c] = i < K ? dr[i] : 0.0;
+    }
+    // forward: v_j final at step j; v_i -= L[i][j] v_j for i > j
+#pragma unroll
+    for (int cc = 0; cc < C; ++cc) {
+      const int jend = imin(K, cc * 32 + 32);
+      for (int j = cc * 32; j < jend; ++j) {
+        const double v = __shfl_sync(0xffffffffu, s[cc], j & 31);
+        const double* col = sL + j * LD;
+#pragma unroll
+        for (int c = cc; c < C; ++c) {
+          const int i = c * 32 + lane;
+          const double l = (i > j && i < K) ? col[i] : 0.0;
+          s[c] = fma(-l, v, s[c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) s[c] *= sD[c * 32 + lane];
+    // backward: h_j final at step j (descending); h_i -= L[j][i] h_j for i < j
+#pragma unroll
+    for (int cc = C - 1; cc >= 0; --cc) {
+      const int jtop = imin(K, cc * 32 + 32) - 1;
+      for (int j = jtop; j >= cc * 32; --j) {
+        const double v = __shfl_sync(0xffffffffu, s[cc], j & 31);
+#pragma unroll
+        for (int c = 0; c <= cc; ++c) {
+          const int i = c * 32 + lane;
+          const double l = i < j ? sL[i * LD + j] : 0.0;
+          s[c] = fma(-l, v, s[c]);
+        }
+      }
+    }
+    double* hr = h + row * K;
+    double dh = 0.0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int i = c * 32 + lane;
+      if (i < K) {
+        hr[i] = s[c];
+        dh = fma(dr[i], s[c], dh);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) dh += __shfl_xor_sync(0xffffffffu, dh, o);
+    if (lane == 0) dot_part[row] = dh;
+  }
+  // <d, h>: the block that finishes last adds the per-row parts in row order and resets the
+  // completion counter for the next call
+  __shared__ int s_last;
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) s_last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+  __syncwarp();
+  if (!s_last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int64_t r = lane; r < rows; r += 32) t += __ldcg(dot_part + r);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if (lane == 0) {
+    *num = t;
+    *ctr = 0u;
+  }
+}
+
+cudaError_t launch_ldl_factor(const double* G, int K, double lambda, double* Lcm, double* Dinv, double* scal,
+                              int* dstatus, cudaStream_t st) {
+  if (K < 1 || K > kLdlKmax) return cudaErrorInvalidValue;
+  const int nel = K * (K + 1) / 2;
+  if (nel <= 9 * LDL_NT)
+    k_ldl_factor<9><<<1, LDL_NT, 0, st>>>(G, K, lambda, Lcm, Dinv, scal, dstatus);
+  else if (nel <= 20 * LDL_NT)
+    k_ldl_factor<20><<<1, LDL_NT, 0, st>>>(G, K, lambda, Lcm, Dinv, scal, dstatus);
+  else
+    k_ldl_factor<33><<<1, LDL_NT, 0, st>>>(G, K, lambda, Lcm, Dinv, scal, dstatus);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ldl_solve(const double* Lcm, const double* Dinv, const double* d, double* h, int K, int64_t rows,
+                             double* dot_part, unsigned int* ctr, double* num, cudaStream_t st) {
+  if (K < 1 || K > kLdlKmax || rows < 1) return rows == 0 ? cudaSuccess : cudaErrorInvalidValue;
+  const int C = (K + 31) / 32;
+  const size_t smem = ((size_t)K * (32 * C + 1) + 32 * C) * sizeof(double);
+  // one warp (block) per row of d (rows beyond 65535 share blocks)
+  const unsigned blocks = (unsigned)imin(rows, 65535);
+  void (*kern)(const double*, const double*, const double*, double*, int, int64_t, double*, unsigned int*,
+               double*) =
+      C == 1 ? k_ldl_solve<1> : C == 2 ? k_ldl_solve<2> : C == 3 ? k_ldl_solve<3> : k_ldl_solve<4>;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<blocks, 32, smem, st>>>(Lcm, Dinv, d, h, K, rows, dot_part, ctr, num);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Cholesky of G + lambda I (K > 128)
 // One CTA, right-looking, lower triangle in shared memory when it fits (K <= 160), else in
 // the output array.  lambda >= 0 absolute, < 0 relative to tr(G)/K.  Per column: every
 // thread reads the pivot, the sub-diagonal column is scaled into a buffer, then the
@@ -177,18 +445,22 @@ __global__ void k_cholesky(const double* __restrict__ G, int K, double lam_in, d
       L[(int64_t)K * K + j] = rj;       // reciprocal diagonal, used by the solves
     }
     for (int i = j + 1 + tid; i < K; i += nt) W[(int64_t)i * K + j] = s_col[i];
-    // trailing lower triangle, 16 x 16 thread tile (blockDim 256): thread (ti, tm) updates
-    // rows i = j+1+ti+16a and columns m = j+1+tm+16b with m <= i
+    // trailing lower triangle, packed: element e -> (ii, mm) with mm <= ii, so every lane of
+    // every warp does useful FP64 work (predicated-off lanes would still occupy the FP64 pipe)
     {
-      const int ti = tid >> 4, tm = tid & 15;
-      for (int i = j + 1 + ti; i < K; i += 16) {
-        const double li = s_col[i];
-        double* Wi = W + (int64_t)i * K;
-        for (int m = j + 1 + tm; m <= i; m += 16) Wi[m] -= li * s_col[m];
+      const int n = K - j - 1;
+      const int tri = n * (n + 1) / 2;
+      for (int e = tid; e < tri; e += nt) {
+        int ii = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+        while (ii * (ii + 1) / 2 > e) --ii;
+        const int mm = e - ii * (ii + 1) / 2;
+        const int i = j + 1 + ii, m = j + 1 + mm;
+        W[(int64_t)i * K + m] -= s_col[i] * s_col[m];
       }
     }
     if (tid == 0 && j + 1 < K) {
-      // thread 0 updated W[j+1][j+1] above: prepare the next pivot
+      // thread 0 updated W[j+1][j+1] above (packed element 0): prepare the next pivot
       const double piv = W[(int64_t)(j + 1) * K + (j + 1)];
       s_bad = !(piv > 0.0) || !isfinite(piv);
       s_dj = s_bad ? 1.0 : sqrt(piv);

@@ -14,8 +14,10 @@
 // partial contraction goes to slot c + rb of a partial buffer; a fixed-order reduction adds
 // the slots, so results are deterministic.
 //
-// Warp roles (192 threads): warp 0 TMA producer, warp 1 TMEM allocator + single-thread MMA
-// issuer, warps 2..5 epilogue (TMEM lane quarter = warp % 4).  Tiles move by TMA
+// Warp roles (352 threads): warp 0 operand producer (TMA), warp 1 TMEM allocator +
+// single-thread MMA issuer, warps 2..9 epilogue (TMEM lane quarter = warp % 4, two column
+// groups), warp 10 data producer (TMA of the X tiles).  The contraction is padded to
+// KP = 64 or 128 (r_1 r_c <= 128), stored as 64-wide K sub-tiles.  Tiles move by TMA
 // (cp.async.bulk.tensor) into 1024-byte aligned SWIZZLE_128B operand buffers; every mbarrier
 // wait is bounded: a wait that runs out sets an error word, all roles drain and the kernel
 // returns after freeing its TMEM.
@@ -29,40 +31,52 @@ namespace tc {
 
 constexpr int BM = 128;        // UMMA M: stationary rows per block
 constexpr int BN = 64;         // streaming columns per tile
-constexpr int KPAD = 64;       // padded contraction length (one 128-byte swizzle atom)
-constexpr int XS = 4;          // data-tile stages (released by the epilogue once read)
-constexpr int TS = 3;          // streaming-operand stages (released by the MMA commits)
 constexpr int NEPI = 8;        // epilogue warps: 4 TMEM lane quarters x NGRP column groups
 constexpr int NGRP = NEPI / 4;
 constexpr int CPW = BN / NGRP; // columns of a tile handled by one epilogue warp
+static_assert(CPW == 32, "the epilogue loads 32 accumulator columns per warp and tile");
 constexpr int NTHREADS = 64 + 32 * NEPI + 32;   // operand producer, MMA, epilogue, data producer
 constexpr int EPI_THREADS = 32 * NEPI;
 constexpr int XWARP = 2 + NEPI;                 // warp index of the data producer
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
-// shared-memory carve-up (bytes, every buffer 1024-aligned)
-constexpr int S_TILE = BM * KPAD * 2;          // 16 KB: one stationary operand
+// shared-memory carve-up (bytes, every buffer 1024-aligned).  Operands are stored as 64-wide
+// K sub-tiles (one 128-byte swizzle atom per row); KP = 64 or 128 is the padded contraction.
 constexpr int X_TILE = BN * BM * 4;            // 32 KB: one data tile
-constexpr int T_TILE = BN * KPAD * 2;          // 8 KB: one streaming operand
 constexpr int Y_TILE = BM * BN * 2;            // 16 KB: weighted residuals (A of GEMM 2)
+constexpr int SUB_S = BM * 64 * 2;             // 16 KB: one K sub-tile of a stationary operand
+constexpr int SUB_T = BN * 64 * 2;             // 8 KB: one K sub-tile of a streaming operand
+
+template <int KP>
+struct Cfg {
+  static constexpr int NSUB = KP / 64;
+  static constexpr int XS = KP == 64 ? 4 : 2;    // data-tile stages (released by the epilogue)
+  static constexpr int TS = KP == 64 ? 3 : 2;    // streaming-operand stages (released by MMA commits)
+  static constexpr int S_TILE = BM * KP * 2;     // one stationary operand
+  static constexpr int T_TILE = BN * KP * 2;     // one streaming operand
+};
 
 struct Layout {
   int s_hi, s_lo, s_h, x0, t0, y, bars, total;
 };
 
+template <int KP>
 __host__ __device__ constexpr Layout layout(bool pass2) {
+  using C = Cfg<KP>;
   Layout L{};
   int o = 0;
-  L.s_hi = o; o += S_TILE;
-  L.s_lo = o; o += S_TILE;
-  L.s_h = o; if (pass2) o += S_TILE;
-  L.x0 = o; o += XS * X_TILE;
-  L.t0 = o; o += TS * 2 * T_TILE;      // per stage: hi tile then lo tile
+  L.s_hi = o; o += C::S_TILE;
+  L.s_lo = o; o += C::S_TILE;
+  L.s_h = o; if (pass2) o += C::S_TILE;
+  L.x0 = o; o += C::XS * X_TILE;
+  L.t0 = o; o += C::TS * 2 * C::T_TILE;   // per stage: hi tile then lo tile
   L.y = o; if (!pass2) o += Y_TILE;
   L.bars = o; o += 1024;
   L.total = o;
   return L;
 }
+static_assert(layout<64>(false).total + 1024 <= 232448 && layout<64>(true).total + 1024 <= 232448, "smem");
+static_assert(layout<128>(false).total + 1024 <= 232448 && layout<128>(true).total + 1024 <= 232448, "smem");
 
 struct Params {
   int64_t P_in, P_stat, P_strm;
@@ -102,13 +116,16 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
 }
 // Bounded wait; false (and the abort flag set) when the limit is reached or another role
 // has aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
-  for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* b, uint32_t parity, volatile int* abort_flag, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_try(b, parity)) return true;
     if (*abort_flag) return false;
   }
   *abort_flag = 1;
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  return mbar_wait_n(b, parity, abort_flag, WAIT_LIMIT);
 }
 __device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
   asm volatile(
@@ -155,6 +172,43 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+// Split form: issue the load, do other work, then wait.  The wait names the destination
+// registers as operands so that no use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_issue32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait32(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait64(uint32_t* r, uint32_t* q) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31]), "+r"(q[0]), "+r"(q[1]), "+r"(q[2]), "+r"(q[3]),
+                 "+r"(q[4]), "+r"(q[5]), "+r"(q[6]), "+r"(q[7]), "+r"(q[8]), "+r"(q[9]), "+r"(q[10]), "+r"(q[11]),
+                 "+r"(q[12]), "+r"(q[13]), "+r"(q[14]), "+r"(q[15]), "+r"(q[16]), "+r"(q[17]), "+r"(q[18]),
+                 "+r"(q[19]), "+r"(q[20]), "+r"(q[21]), "+r"(q[22]), "+r"(q[23]), "+r"(q[24]), "+r"(q[25]),
+                 "+r"(q[26]), "+r"(q[27]), "+r"(q[28]), "+r"(q[29]), "+r"(q[30]), "+r"(q[31])
+               :
+               : "memory");
+}
+
 // columns-per-warp dispatch
 template <int N>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
@@ -202,13 +256,15 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 // ------------------------------------------------------------------ the kernel
-template <bool ROWS, bool PASS2, bool FULL>
+template <bool ROWS, bool PASS2, bool FULL, int KP>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_pass_tc(const __grid_constant__ CUtensorMap mS_hi, const __grid_constant__ CUtensorMap mS_lo,
               const __grid_constant__ CUtensorMap mS_h, const __grid_constant__ CUtensorMap mT_hi,
               const __grid_constant__ CUtensorMap mT_lo, const __grid_constant__ CUtensorMap mX,
               const Params p) {
-  constexpr Layout L = layout(PASS2);
+  constexpr int KPAD = KP, NSUB = Cfg<KP>::NSUB, XS = Cfg<KP>::XS, TS = Cfg<KP>::TS;
+  constexpr int S_TILE = Cfg<KP>::S_TILE, T_TILE = Cfg<KP>::T_TILE;
+  constexpr Layout L = layout<KP>(PASS2);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // align the dynamic window to 1024 bytes (the launcher over-allocates by 1 KB)
   unsigned char* sm = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
@@ -287,9 +343,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!ok) break;
         mbar_expect_tx(s_full, (PASS2 ? 3 : 2) * S_TILE);
         s_phase = g & 1;
-        tma_2d(sm + L.s_hi, &mS_hi, s_full, 0, (int)(rb * BM));
-        tma_2d(sm + L.s_lo, &mS_lo, s_full, 0, (int)(rb * BM));
-        if (PASS2) tma_2d(sm + L.s_h, &mS_h, s_full, 0, (int)(rb * BM));
+#pragma unroll
+        for (int sb = 0; sb < NSUB; ++sb) {
+          tma_2d(sm + L.s_hi + sb * SUB_S, &mS_hi, s_full, sb * 64, (int)(rb * BM));
+          tma_2d(sm + L.s_lo + sb * SUB_S, &mS_lo, s_full, sb * 64, (int)(rb * BM));
+          if (PASS2) tma_2d(sm + L.s_h + sb * SUB_S, &mS_h, s_full, sb * 64, (int)(rb * BM));
+        }
         for (; u < seg_end; ++u, ++it) {
           const int s = (int)(it % TS);
           if (!mbar_wait(&t_empty[s], (uint32_t)(((it / TS) & 1) ^ 1), abort_flag)) { ok = false; break; }
@@ -297,8 +356,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           unsigned char* tb = sm + L.t0 + s * 2 * T_TILE;
           mbar_expect_tx(&t_full[s], 2 * T_TILE);
           last_phase[s] = (int)((it / TS) & 1);
-          tma_2d(tb, &mT_hi, &t_full[s], 0, t0);
-          tma_2d(tb + T_TILE, &mT_lo, &t_full[s], 0, t0);
+#pragma unroll
+          for (int sb = 0; sb < NSUB; ++sb) {
+            tma_2d(tb + sb * SUB_T, &mT_hi, &t_full[s], sb * 64, t0);
+            tma_2d(tb + T_TILE + sb * SUB_T, &mT_lo, &t_full[s], sb * 64, t0);
+          }
         }
       }
       if (!ok) {
@@ -363,12 +425,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (!mbar_wait(&d_empty[b], (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t b_hi = su32(sm + L.t0 + s * 2 * T_TILE), b_lo = b_hi + T_TILE;
+#pragma unroll
           for (int kk = 0; kk < KPAD / 16; ++kk) {
-            const uint32_t ko = kk * 32;
-            tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_hi + ko), sdesc(b_hi + ko), ID1, kk > 0);
-            tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_hi + ko), sdesc(b_lo + ko), ID1, 1);
-            tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_lo + ko), sdesc(b_hi + ko), ID1, 1);
-            if (PASS2) tc_mma(tmem + (uint32_t)((2 + b) * BN), sdesc(a_h + ko), sdesc(b_hi + ko), ID1, kk > 0);
+            // K step kk: sub-tile kk / 4, 32-byte step kk % 4 inside its swizzle atom
+            const uint32_t ka = (uint32_t)((kk >> 2) * SUB_S + (kk & 3) * 32);
+            const uint32_t kb = (uint32_t)((kk >> 2) * SUB_T + (kk & 3) * 32);
+            tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_hi + ka), sdesc(b_hi + kb), ID1, kk > 0);
+            tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_hi + ka), sdesc(b_lo + kb), ID1, 1);
+            tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_lo + ka), sdesc(b_hi + kb), ID1, 1);
+            if (PASS2) tc_mma(tmem + (uint32_t)((2 + b) * BN), sdesc(a_h + ka), sdesc(b_hi + kb), ID1, kk > 0);
           }
           tc_commit(&d_full[b]);
           if (PASS2) {
@@ -444,7 +509,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (row_ok && u + 1 < seg_end) mnext = __ldg(mrow + ((t0 + BN + c0) >> 5));
         const int64_t nc = p.P_strm - t0 - c0;  // valid columns for this warp
         const uint32_t vmask = (!row_ok || nc <= 0) ? 0u : (nc >= CPW ? CMASK : ((1u << nc) - 1u));
-        if (!mbar_wait(&x_full[xs], (uint32_t)((it / XS) & 1), abort_flag)) { ok = false; break; }
+        // accumulators first: the TMEM loads are in flight while X is read from shared memory
+        if (!mbar_wait(&d_full[b], (uint32_t)((it >> 1) & 1), abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        uint32_t rx[32], rd[32];
+        tmem_issue32(tmem + lane_base + (uint32_t)(b * BN + c0), rx);
+        if (PASS2) tmem_issue32(tmem + lane_base + (uint32_t)((2 + b) * BN + c0), rd);
+        if (!mbar_wait(&x_full[xs], (uint32_t)((it / XS) & 1), abort_flag)) {
+          if (PASS2) tmem_wait64(rx, rd);
+          else tmem_wait32(rx);
+          ok = false;
+          break;
+        }
         const unsigned char* xt = sm + L.x0 + xs * X_TILE;
         float xh[CPW], dh[CPW], xv[CPW];
         if (ROWS) {
@@ -462,10 +538,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
         mbar_arrive(&x_empty[xs]);
-        if (!mbar_wait(&d_full[b], (uint32_t)((it >> 1) & 1), abort_flag)) { ok = false; break; }
-        tc_fence_after();
-        tmem_ld<CPW>(tmem + lane_base + (uint32_t)(b * BN + c0), xh);
-        if (PASS2) tmem_ld<CPW>(tmem + lane_base + (uint32_t)((2 + b) * BN + c0), dh);
+        if (PASS2) tmem_wait64(rx, rd);
+        else tmem_wait32(rx);
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+          xh[j] = __uint_as_float(rx[j]);
+          if (PASS2) dh[j] = __uint_as_float(rd[j]);
+        }
         tc_fence_before();
         mbar_arrive(&d_empty[b]);
         const uint32_t seen = mword & vmask;
@@ -480,15 +559,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const float e = xv[j] - xh[j];
             const bool use = ((seen >> j) & 1u) && (fabsf(e) <= 3.402823466e38f);
             fin |= use ? (1u << j) : 0u;
-            const float w = fast_ex2(e * e * nk);
-            const float uw = use ? w : 0.f;
+            // selects, not products with 0, so that a NaN stored at an unobserved slot stays out
+            const float eu = use ? e : 0.f;
+            const float uw = use ? fast_ex2(e * e * nk) : 0.f;
             if (PASS2) {
               sden = fmaf(uw * dh[j], dh[j], sden);
             } else {
-              const float y = uw * e;
+              const float y = uw * eu;
               sw += uw;
-              se2 = fmaf(use ? e : 0.f, e, se2);
-              swe2 = fmaf(y, e, swe2);
+              se2 = fmaf(eu, eu, se2);
+              swe2 = fmaf(y, eu, swe2);
               xv[j] = y;
             }
           }
@@ -531,12 +611,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(acc_full, (uint32_t)(g & 1), abort_flag)) { ok = false; break; }
         tc_fence_after();
         float* dst = p.Tpart + ((c + rb) * BM + row) * (int64_t)p.Kp;
-        constexpr int KPW = KPAD / NGRP;
-        float v[KPW];
-        tmem_ld<KPW>(tmem + lane_base + col_acc + grp * KPW, v);
+        constexpr int KPW = KPAD / NGRP;                  // 32 or 64 columns per warp
 #pragma unroll
-        for (int j = 0; j < KPW; ++j)
-          if (grp * KPW + j < p.Kp) dst[grp * KPW + j] = row_ok ? v[j] : 0.f;
+        for (int h0 = 0; h0 < KPW; h0 += 32) {
+          float v[32];
+          tmem_ld<32>(tmem + lane_base + col_acc + grp * KPW + h0, v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (grp * KPW + h0 + j < p.Kp) dst[grp * KPW + h0 + j] = row_ok ? v[j] : 0.f;
+        }
         tc_fence_before();
         mbar_arrive(acc_empty);
       }
@@ -570,14 +653,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+// Self-test of the bounded wait the pass uses: one thread waits (at most `limit` polls) for
+// phase 0 of a fresh barrier, which completes only if `arrive` is set.  A wait that gives up
+// is reported exactly as in the pass (DEV_TIMEOUT in the status word); nothing else is touched.
+__global__ void k_wait_selftest(int arrive, uint32_t limit, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_word;
+  if (threadIdx.x != 0) return;
+  abort_word = 0;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (arrive) mbar_arrive(&bar);
+  if (!mbar_wait_n(&bar, 0, reinterpret_cast<volatile int*>(&abort_word), limit)) atomicOr(err, (int)DEV_TIMEOUT);
+}
+
 // ------------------------------------------------------------------ operand preparation
-// BF16 hi/lo split of a merged matrix [rows][Kp] (float) into [rows][KPAD] (zero padded).
-__global__ void k_split_rows(const float* __restrict__ src, int64_t rows, int Kp, __nv_bfloat16* __restrict__ hi,
-                             __nv_bfloat16* __restrict__ lo) {
-  const int64_t n = rows * KPAD;
+// BF16 hi/lo split of a merged matrix [rows][Kp] (float) into [rows][kpad] (zero padded).
+__global__ void k_split_rows(const float* __restrict__ src, int64_t rows, int Kp, int kpad,
+                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int64_t n = rows * kpad;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / KPAD;
-    const int k = (int)(e % KPAD);
+    const int64_t r = e / kpad;
+    const int k = (int)(e % kpad);
     const float v = k < Kp ? src[r * Kp + k] : 0.f;
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     hi[e] = h;
@@ -709,14 +806,22 @@ bool make_map(CUtensorMap* m, CUtensorMapDataType dt, int esize, const void* bas
 }
 }  // namespace
 
-int tc_kpad() { return tc::KPAD; }
+int tc_kpad(int Kp) { return Kp <= 64 ? 64 : (Kp <= 128 ? 128 : 0); }
 int tc_bm() { return tc::BM; }
 int tc_bn() { return tc::BN; }
 
+cudaError_t launch_wait_selftest(bool arrive, uint32_t limit, int* err, cudaStream_t st) {
+  tc::k_wait_selftest<<<1, 32, 0, st>>>(arrive ? 1 : 0, limit, err);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tc_prep(const float* src, int64_t rows, int Kp, __nv_bfloat16* hi, __nv_bfloat16* lo,
                            cudaStream_t st) {
-  const int64_t n = rows * tc::KPAD;
-  tc::k_split_rows<<<(unsigned)imin((n + 255) / 256, 8192), 256, 0, st>>>(src, rows, Kp, hi, lo);
+  const int kpad = tc_kpad(Kp);
+  if (!kpad) return cudaErrorInvalidValue;
+  const int64_t n = rows * kpad;
+  tc::k_split_rows<<<(unsigned)imin((n + 255) / 256, 8192), 256, 0, st>>>(src, rows, Kp, kpad, hi, lo);
   note_launch();
   return cudaGetLastError();
 }
@@ -754,10 +859,12 @@ cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi
                            int64_t P_stat, int64_t P_strm, int Kp, const double* sigma, float* Tpart,
                            double* stat_part, int* err, int G, bool full_stats, cudaStream_t st) {
   using namespace tc;
-  if (Kp > KPAD || (P_in % 4) != 0) return cudaErrorInvalidValue;
+  const int KPAD = tc_kpad(Kp);
+  if (!KPAD || (P_in % 4) != 0) return cudaErrorInvalidValue;
   CUtensorMap mS_hi, mS_lo, mS_h, mT_hi, mT_lo, mX;
   const CUtensorMapDataType BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const CUtensorMapSwizzle SW = CU_TENSOR_MAP_SWIZZLE_128B;
+  // operand arrays [rows][KPAD] bf16, fetched as 64-wide sub-tiles (128-byte rows, SW128)
   bool ok = make_map(&mS_hi, BF, 2, S_hi, KPAD, P_stat, KPAD * 2, 64, BM, SW) &&
             make_map(&mS_lo, BF, 2, S_lo, KPAD, P_stat, KPAD * 2, 64, BM, SW) &&
             make_map(&mS_h, BF, 2, pass2 ? S_h : S_hi, KPAD, P_stat, KPAD * 2, 64, BM, SW) &&
@@ -784,7 +891,7 @@ cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi
   p.Tpart = Tpart;
   p.stat_part = stat_part;
   p.err = err;
-  const Layout L = layout(pass2);
+  const Layout L = KPAD == 64 ? layout<64>(pass2) : layout<128>(pass2);
   const size_t smem = (size_t)L.total + 1024;
   auto go = [&](auto kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -793,9 +900,16 @@ cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi
     note_launch();
     return cudaGetLastError();
   };
-  if (pass2) return rows_case ? go(k_pass_tc<true, true, false>) : go(k_pass_tc<false, true, false>);
-  if (full_stats) return rows_case ? go(k_pass_tc<true, false, true>) : go(k_pass_tc<false, false, true>);
-  return rows_case ? go(k_pass_tc<true, false, false>) : go(k_pass_tc<false, false, false>);
+  if (KPAD == 64) {
+    if (pass2) return rows_case ? go(k_pass_tc<true, true, false, 64>) : go(k_pass_tc<false, true, false, 64>);
+    if (full_stats)
+      return rows_case ? go(k_pass_tc<true, false, true, 64>) : go(k_pass_tc<false, false, true, 64>);
+    return rows_case ? go(k_pass_tc<true, false, false, 64>) : go(k_pass_tc<false, false, false, 64>);
+  }
+  if (pass2) return rows_case ? go(k_pass_tc<true, true, false, 128>) : go(k_pass_tc<false, true, false, 128>);
+  if (full_stats)
+    return rows_case ? go(k_pass_tc<true, false, true, 128>) : go(k_pass_tc<false, false, true, 128>);
+  return rows_case ? go(k_pass_tc<true, false, false, 128>) : go(k_pass_tc<false, false, false, 128>);
 }
 
 }  // namespace trd

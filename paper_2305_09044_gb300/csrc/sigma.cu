@@ -4,7 +4,9 @@
 // Quartiles are type-7 (linear interpolation between order statistics); the order
 // statistics come from an exact, deterministic MSB-first radix select on order-preserving
 // 64-bit keys (8 passes of 8 bits, integer histograms).
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "trd_internal.cuh"
 
@@ -30,270 +32,195 @@ __device__ inline double dval(uint64_t k) {
 
 constexpr uint64_t kExcluded = ~0ull;
 
-// Residual e = x - Tr(prod Z_j(i_j)) at probe m (or entry m when full), by the row-vector
-// chain: for each gamma, v = e_gamma^T Z_1(i_1) ... Z_N(i_N), x_hat += v[gamma].
-template <typename T>
-__global__ void k_probe_resid(const double* const* __restrict__ Zp, int N, const int64_t* __restrict__ dim,
-                              const int* __restrict__ R, const float* __restrict__ X,
-                              const uint32_t* __restrict__ M, int64_t numel, int full, int64_t n,
-                              double* __restrict__ vals, uint64_t* __restrict__ keys,
-                              double* __restrict__ xsq) {
-  __shared__ const double* Zs[kMaxN];
-  __shared__ int64_t Ds[kMaxN];
-  __shared__ int Rs[kMaxN];
-  if (threadIdx.x < N) {
-    Zs[threadIdx.x] = Zp[threadIdx.x];
-    Ds[threadIdx.x] = dim[threadIdx.x];
-    Rs[threadIdx.x] = R[threadIdx.x];
+// ------------------------------------------------------------------ selection chain
+// Work area (8-byte words):
+//   [0] n (included residuals)  [1] mean  [2] sum x^2  [3] population variance
+//   u[8..11]  remaining rank of each of the four target order statistics
+//   u[12..15] key prefix selected so far for each target
+//   u[16..23] completion counter of each kernel of the chain
+//   word 64:  uint32 histograms [8 digits][4 targets][256]
+//   word 64 + 4096: per-block partial sums [kSelBlocks][4] (count, sum e, sum x^2, sum (e-mean)^2)
+// The chain is: clear (memset) -> first kernel (residual keys, sums, digit-0 histogram) ->
+// seven digit kernels.  The last block of every kernel (completion counter) turns the complete
+// histogram into the next digit of each target; the last one also evaluates sigma.
+constexpr int kSelBlocks = 1216;
+constexpr int kSelThreads = 256;
+constexpr int kHistWord = 64;
+constexpr int kPartsWord = 64 + 4096;
+
+__device__ __forceinline__ unsigned int* sel_hist(double* work, int digit, int t) {
+  return reinterpret_cast<unsigned int*>(work + kHistWord) + (digit * 4 + t) * 256;
+}
+
+// Signals completion of this block; true in the block that completes last (which then sees
+// every other block's global writes and atomics).
+__device__ bool sel_last_block(double* work, int kernel) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long* ctr = reinterpret_cast<unsigned long long*>(work) + 16 + kernel;
+    s_last = atomicAdd(ctr, 1ull) == (unsigned long long)gridDim.x - 1;
   }
   __syncthreads();
-  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n;
-       m += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t lin = full ? m : (int64_t)(sm64(kProbeSeed, (uint64_t)m) % (uint64_t)numel);
-    const bool obs = M ? ((M[lin >> 5] >> (lin & 31)) & 1u) : true;
-    double val = 0.0, xs = 0.0;
-    uint64_t key = kExcluded;
-    if (obs) {
-      int64_t ii[kMaxN];
-      int64_t rem = lin;
-      for (int j = 0; j < N; ++j) { ii[j] = rem % Ds[j]; rem /= Ds[j]; }
-      const int r0 = Rs[0];
-      T xh = T(0);
-      for (int g = 0; g < r0; ++g) {
-        T v[kMaxR], u[kMaxR];
-        // v = row g of Z_0(i_0): Z_0(i)[g, b] at i*K + b*r0 + g
-        {
-          const int r1 = Rs[1 % N];
-          const double* z = Zs[0] + ii[0] * (int64_t)(r0 * r1);
-          for (int b = 0; b < r1; ++b) v[b] = (T)z[b * r0 + g];
-        }
-        for (int j = 1; j < N; ++j) {
-          const int rj = Rs[j], rj1 = Rs[(j + 1) % N];
-          const double* z = Zs[j] + ii[j] * (int64_t)(rj * rj1);
-          for (int b = 0; b < rj1; ++b) {
-            T s = T(0);
-            for (int a = 0; a < rj; ++a) s = fma(v[a], (T)z[b * rj + a], s);
-            u[b] = s;
-          }
-          for (int b = 0; b < rj1; ++b) v[b] = u[b];
-        }
-        xh += v[g];
-      }
-      const T x = (T)X[lin];
-      const T e = x - xh;
-      if (isfinite((double)e)) {
-        val = (double)e;
-        key = dkey(val);
-        xs = (double)x * (double)x;
-      }
-    }
-    vals[m] = key == kExcluded ? 0.0 : val;
-    keys[m] = key;
-    xsq[m] = xs;
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// Targets whose prefixes coincide share one histogram: alias[t] = first such target.
+__device__ __forceinline__ void sel_alias(const uint64_t* pre, int* alias) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    alias[t] = t;
+    for (int q = t - 1; q >= 0; --q)
+      if (pre[q] == pre[t]) alias[t] = q;
   }
 }
 
-// Residual at probe m from the merged subchains of the full tensor: with the modes cut into
-// an inner block (linear index a) and an outer block (b), x_hat = Tr(A(a) C(b)) =
-// sum_kappa A[a][kappa] C[b][kappa] (Thm. 1 with the ring cut in two).
-template <typename T>
-__global__ void k_probe_merged(const T* __restrict__ A, const T* __restrict__ C, int Kp, int64_t P_in,
-                               const float* __restrict__ X, const uint32_t* __restrict__ M, int64_t numel,
-                               int full, int64_t n, double* __restrict__ vals, uint64_t* __restrict__ keys,
-                               double* __restrict__ xsq) {
-  // one warp per group of 32 probes: lane m owns probe m of the group (index, data, output);
-  // the 32 dot products are computed cooperatively with coalesced row loads
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t g0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; g0 < n; g0 += warps * 32) {
-    const int64_t m = g0 + lane;
-    const bool live = m < n;
-    const int64_t lin = !live ? 0 : (full ? m : (int64_t)(sm64(kProbeSeed, (uint64_t)m) % (uint64_t)numel));
-    const bool obs = live && (M ? ((M[lin >> 5] >> (lin & 31)) & 1u) : true);
-    const float xf = live ? X[lin] : 0.f;
-    const int64_t a = lin % P_in, b = lin / P_in;
-    T mine = T(0);
-    for (int q = 0; q < 32; ++q) {
-      const int64_t aq = __shfl_sync(0xffffffffu, a, q), bq = __shfl_sync(0xffffffffu, b, q);
-      const T* Ar = A + aq * Kp;
-      const T* Cr = C + bq * Kp;
-      T part = T(0);
-      for (int k = lane; k < Kp; k += 32) part = fma(Ar[k], Cr[k], part);
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      if (lane == q) mine = part;
-    }
-    if (!live) continue;
-    double val = 0.0, xs = 0.0;
-    uint64_t key = kExcluded;
-    if (obs) {
-      const T x = (T)xf;
-      const T e = x - mine;
-      if (isfinite((double)e)) {
-        val = (double)e;
-        key = dkey(val);
-        xs = (double)x * (double)x;
-      }
-    }
-    vals[m] = key == kExcluded ? 0.0 : val;
-    keys[m] = key;
-    xsq[m] = xs;
-  }
-}
-
-__global__ void k_float_keys(const float* __restrict__ r, int64_t n, double* __restrict__ vals,
-                             uint64_t* __restrict__ keys, double* __restrict__ xsq) {
-  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n;
-       m += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)r[m];
-    const bool ok = isfinite(v);
-    vals[m] = ok ? v : 0.0;
-    keys[m] = ok ? dkey(v) : kExcluded;
-    xsq[m] = 0.0;
-  }
-}
-
-// Fixed-order sums over the probe: parts[b][4] = (count, sum e, sum x^2, sum (e - mean)^2).
-__global__ void k_probe_sums(const double* __restrict__ vals, const uint64_t* __restrict__ keys,
-                             const double* __restrict__ xsq, int64_t n, const double* __restrict__ mean,
-                             double* __restrict__ parts) {
-  __shared__ double sh[3][256];
-  double c = 0, s = 0, q = 0;
-  const double mu = mean ? *mean : 0.0;
-  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n;
-       m += (int64_t)gridDim.x * blockDim.x) {
-    if (keys[m] != kExcluded) {
-      c += 1.0;
-      if (mean) { const double d = vals[m] - mu; s = fma(d, d, s); }
-      else { s += vals[m]; q += xsq[m]; }
-    }
-  }
-  sh[0][threadIdx.x] = c; sh[1][threadIdx.x] = s; sh[2][threadIdx.x] = q;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int f = 0; f < 3; ++f) sh[f][threadIdx.x] += sh[f][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0)
-    for (int f = 0; f < 3; ++f) parts[blockIdx.x * 3 + f] = sh[f][0];
-}
-
-// work layout (doubles): [0] n, [1] mean, [2] sum x^2, [3] var, [8..11] ranks, [12..15] prefixes
-// (as uint64 bits), hist at work + 64 as unsigned long long [4][256], parts at work + 64 + 1024.
-__global__ void k_finish_sums(const double* __restrict__ parts, int nb, double* __restrict__ work,
-                              int second) {
-  // one warp: fixed-order strided partial sums, then a fixed shuffle tree
-  const int lane = threadIdx.x;
-  double c = 0, s = 0, q = 0;
-  for (int b = lane; b < nb; b += 32) { c += parts[b * 3]; s += parts[b * 3 + 1]; q += parts[b * 3 + 2]; }
-  for (int o = 16; o > 0; o >>= 1) {
-    c += __shfl_down_sync(0xffffffffu, c, o);
-    s += __shfl_down_sync(0xffffffffu, s, o);
-    q += __shfl_down_sync(0xffffffffu, q, o);
-  }
-  if (lane != 0) return;
-  if (!second) {
-    work[0] = c;
-    work[1] = c > 0 ? s / c : 0.0;
-    work[2] = q;
-  } else {
-    work[3] = c > 0 ? s / c : 0.0;
-  }
-}
-
-__global__ void k_select_init(double* __restrict__ work) {
-  const double n = work[0];
+// Last block, warps 0..3 (one per target): inclusive scan of the 256 counts of the target's
+// histogram (8 bins per lane), find the bin holding the remaining rank, narrow the prefix.
+__device__ void sel_pick(double* work, int digit) {
   uint64_t* u = reinterpret_cast<uint64_t*>(work);
-  const double ps[2] = {0.25, 0.75};
-  for (int q = 0; q < 2; ++q) {
-    double h = (n - 1.0) * ps[q];
-    if (h < 0) h = 0;
-    const double lo = floor(h);
-    const double hi = lo + 1.0 <= n - 1.0 ? lo + 1.0 : lo;
-    u[8 + 2 * q] = (uint64_t)lo;
-    u[9 + 2 * q] = (uint64_t)hi;
-  }
-  for (int t = 0; t < 4; ++t) u[12 + t] = 0;
-  unsigned long long* hist = reinterpret_cast<unsigned long long*>(work + 64);
-  for (int i = 0; i < 1024; ++i) hist[i] = 0;
-}
-
-__global__ void k_select_hist(const uint64_t* __restrict__ keys, int64_t n, double* __restrict__ work,
-                              int shift) {
-  __shared__ unsigned int h[4][256];
-  for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&h[0][0])[i] = 0;
-  __syncthreads();
-  const uint64_t* u = reinterpret_cast<const uint64_t*>(work);
-  uint64_t pre[4];
-  for (int t = 0; t < 4; ++t) pre[t] = u[12 + t];
-  const uint64_t himask = shift >= 56 ? 0ull : (~0ull << (shift + 8));
-  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n;
-       m += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = keys[m];
-    if (k == kExcluded) continue;
-    const unsigned dig = (unsigned)((k >> shift) & 0xffu);
-    for (int t = 0; t < 4; ++t)
-      if ((k & himask) == pre[t]) atomicAdd(&h[t][dig], 1u);
-  }
-  __syncthreads();
-  unsigned long long* gh = reinterpret_cast<unsigned long long*>(work + 64);
-  for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
-    const unsigned v = (&h[0][0])[i];
-    if (v) atomicAdd(&gh[i], (unsigned long long)v);
-  }
-}
-
-// One warp per target: inclusive scan of the 256 bin counts (8 per lane), find the bin
-// holding the target rank, narrow the prefix; then clear the histogram.
-__global__ void k_select_pick(double* __restrict__ work, int shift) {
   const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint64_t* u = reinterpret_cast<uint64_t*>(work);
-  unsigned long long* gh = reinterpret_cast<unsigned long long*>(work + 64);
+  uint64_t pre[4];
+  int alias[4];
+  for (int q = 0; q < 4; ++q) pre[q] = __ldcg(u + 12 + q);
+  sel_alias(pre, alias);
+  __syncthreads();                       // every warp has read the prefixes before any update
   if (t < 4) {
-    const uint64_t rank = u[8 + t];
-    unsigned long long c[8], loc = 0;
-    for (int i = 0; i < 8; ++i) { c[i] = gh[t * 256 + lane * 8 + i]; loc += c[i]; }
+    const unsigned int* h = sel_hist(work, digit, digit == 0 ? 0 : alias[t]);
+    const uint64_t rank = __ldcg(u + 8 + t);
+    unsigned int c[8];
+    unsigned long long loc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      c[i] = __ldcg(h + lane * 8 + i);
+      loc += c[i];
+    }
     unsigned long long incl = loc;
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += v;
     }
     const unsigned long long excl = incl - loc;
-    // the lane whose range [excl, incl) holds the rank finds the bin
-    const bool mine = rank >= excl && rank < incl;
-    const unsigned who = __ballot_sync(0xffffffffu, mine);
-    if (mine) {
+    if (rank >= excl && rank < incl) {
       unsigned long long cum = excl;
       int bin = lane * 8 + 7;
       for (int i = 0; i < 8; ++i) {
         if (cum + c[i] > rank) { bin = lane * 8 + i; break; }
         cum += c[i];
       }
+      const int shift = 56 - 8 * digit;
       u[8 + t] = rank - cum;
-      u[12 + t] |= ((uint64_t)bin) << shift;
+      u[12 + t] = pre[t] | ((uint64_t)bin << shift);
     }
-    (void)who;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 1024; i += blockDim.x) gh[i] = 0;
 }
 
-__global__ void k_sigma_final(double* __restrict__ work, double rms_override, double sigma_prev,
-                              const double* __restrict__ sigma_prev_dev, double* __restrict__ sigma_out) {
+// Fixed-order sum of field f of the per-block partials (last block; result in every thread).
+__device__ double sel_sum_parts(const double* work, int f, int nb) {
+  __shared__ double red[kSelThreads / 32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += __ldcg(work + kPartsWord + b * 4 + f);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+// Per-element step of the first kernel: key, partial sums, digit-0 histogram (warp-aggregated
+// shared-memory atomics).  Every lane of the warp calls it (valid = false for lanes without
+// an included residual).
+__device__ __forceinline__ void sel_consume(bool valid, double e, double x2, uint64_t* keys, int64_t m,
+                                            bool write, unsigned int* h0, double& c, double& se, double& sx) {
+  const uint64_t key = valid ? dkey(e) : kExcluded;
+  if (write) keys[m] = key;
+  if (valid) {
+    c += 1.0;
+    se += e;
+    sx += x2;
+  }
+  const unsigned dig = (unsigned)(key >> 56);
+  const unsigned act = __ballot_sync(0xffffffffu, valid);
+  if (valid) {
+    const unsigned peers = __match_any_sync(act, dig);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h0[dig], (unsigned)__popc(peers));
+  }
+}
+
+// End of the first kernel: block partials and histogram out; the last block sets n, mean,
+// sum x^2, the target ranks, and picks digit 0.
+__device__ void sel_first_finish(double* work, unsigned int* h0, double c, double se, double sx) {
+  __shared__ double red[3][kSelThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_down_sync(0xffffffffu, c, o);
+    se += __shfl_down_sync(0xffffffffu, se, o);
+    sx += __shfl_down_sync(0xffffffffu, sx, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = c;
+    red[1][threadIdx.x >> 5] = se;
+    red[2][threadIdx.x >> 5] = sx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, d = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; d += red[2][w]; }
+    double* part = work + kPartsWord + blockIdx.x * 4;
+    part[0] = a;
+    part[1] = b;
+    part[2] = d;
+  }
+  unsigned int* g0 = sel_hist(work, 0, 0);
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (h0[i]) atomicAdd(&g0[i], h0[i]);
+  if (!sel_last_block(work, 0)) return;
+  const double n = sel_sum_parts(work, 0, gridDim.x);
+  const double sum = sel_sum_parts(work, 1, gridDim.x);
+  const double sx2 = sel_sum_parts(work, 2, gridDim.x);
+  if (threadIdx.x == 0) {
+    work[0] = n;
+    work[1] = n > 0 ? sum / n : 0.0;
+    work[2] = sx2;
+    uint64_t* u = reinterpret_cast<uint64_t*>(work);
+    const double ps[2] = {0.25, 0.75};
+    for (int q = 0; q < 2; ++q) {
+      double hq = (n - 1.0) * ps[q];
+      if (hq < 0) hq = 0;
+      const double lo = floor(hq);
+      const double hi = lo + 1.0 <= n - 1.0 ? lo + 1.0 : lo;
+      u[8 + 2 * q] = (uint64_t)lo;
+      u[9 + 2 * q] = (uint64_t)hi;
+    }
+    for (int t = 0; t < 4; ++t) u[12 + t] = 0;
+  }
+  __syncthreads();
+  sel_pick(work, 0);
+}
+
+// sigma = max(1e-6 rms, 2 min(std, IQR / 1.349), 0.9 sigma_prev) from the selected keys (type-7
+// quartiles with numpy's interpolation form) and the sums.
+__device__ void sel_sigma(const double* work, double rms_override, double sigma_prev,
+                          const double* __restrict__ sigma_prev_dev, double* __restrict__ sigma_out) {
   if (sigma_prev_dev) sigma_prev = *sigma_prev_dev;
+  // L2 reads (ld.global.cg): these words were written earlier in this kernel
   const uint64_t* u = reinterpret_cast<const uint64_t*>(work);
-  const double n = work[0];
+  const double n = __ldcg(work);
   double q[2];
   const double ps[2] = {0.25, 0.75};
   for (int i = 0; i < 2; ++i) {
-    const double a = dval(u[12 + 2 * i]), b = dval(u[13 + 2 * i]);
+    const double a = dval(__ldcg(u + 12 + 2 * i)), b = dval(__ldcg(u + 13 + 2 * i));
     double h = (n - 1.0) * ps[i];
     if (h < 0) h = 0;
     const double f = h - floor(h);
     q[i] = f >= 0.5 ? b - (b - a) * (1.0 - f) : a + (b - a) * f;
   }
-  const double stdv = sqrt(work[3]);
-  const double rms = rms_override >= 0 ? rms_override : (n > 0 ? sqrt(work[2] / n) : 0.0);
+  const double stdv = sqrt(__ldcg(work + 3));
+  const double rms = rms_override >= 0 ? rms_override : (n > 0 ? sqrt(__ldcg(work + 2) / n) : 0.0);
   double s = 2.0 * fmin(stdv, (q[1] - q[0]) / 1.349);
   if (!(n > 0)) s = 0.0;
   s = fmax(s, 1e-6 * rms);
@@ -301,92 +228,239 @@ __global__ void k_sigma_final(double* __restrict__ work, double rms_override, do
   *sigma_out = s;
 }
 
-cudaError_t finish_sigma(const double* vals, const uint64_t* keys, const double* xsq, int64_t n,
-                         double rms_override, double sigma_prev, const double* sigma_prev_dev,
-                         double* work, double* sigma_out, cudaStream_t st) {
-  const int nb = 256;
-  double* parts = work + 64 + 1024;
-  k_probe_sums<<<nb, 256, 0, st>>>(vals, keys, xsq, n, nullptr, parts);
-  note_launch();
-  k_finish_sums<<<1, 32, 0, st>>>(parts, nb, work, 0);
-  note_launch();
-  k_probe_sums<<<nb, 256, 0, st>>>(vals, keys, xsq, n, work + 1, parts);
-  note_launch();
-  k_finish_sums<<<1, 32, 0, st>>>(parts, nb, work, 1);
-  note_launch();
-  k_select_init<<<1, 1, 0, st>>>(work);
-  note_launch();
-  for (int pass = 0; pass < 8; ++pass) {
-    const int shift = 56 - 8 * pass;
-    k_select_hist<<<(unsigned)imin((n + 255) / 256, 512), 256, 0, st>>>(keys, n, work, shift);
-    note_launch();
-    k_select_pick<<<1, 256, 0, st>>>(work, shift);
+// Digit d (1..7) of the four targets: histogram of the keys that match each target's prefix
+// (digit 1 also accumulates sum (e - mean)^2); the last block picks the digit, and after
+// digit 7 evaluates sigma.
+__global__ void __launch_bounds__(kSelThreads) k_sel_digit(const uint64_t* __restrict__ keys, int64_t n,
+                                                           double* __restrict__ work, int digit,
+                                                           double rms_override, double sigma_prev,
+                                                           const double* __restrict__ sigma_prev_dev,
+                                                           double* __restrict__ sigma_out) {
+  __shared__ unsigned int h[4][256];
+  for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&h[0][0])[i] = 0;
+  const uint64_t* u = reinterpret_cast<const uint64_t*>(work);
+  uint64_t pre[4];
+  int alias[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) pre[t] = __ldcg(u + 12 + t);
+  sel_alias(pre, alias);
+  const double mean = __ldcg(work + 1);
+  const int shift = 56 - 8 * digit;
+  const uint64_t himask = ~0ull << (shift + 8);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  double s2 = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t m0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); m0 < n; m0 += stride) {
+    const int64_t m = m0 + lane;
+    const uint64_t k = m < n ? keys[m] : kExcluded;
+    const bool valid = k != kExcluded;
+    if (digit == 1 && valid) {
+      const double d = dval(k) - mean;
+      s2 = fma(d, d, s2);
+    }
+    const unsigned dig = (unsigned)((k >> shift) & 0xffu);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (alias[t] != t) continue;                    // uniform across the block
+      const bool hit = valid && (k & himask) == pre[t];
+      const unsigned act = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const unsigned peers = __match_any_sync(act, dig);
+        if (lane == __ffs(peers) - 1) atomicAdd(&h[t][dig], (unsigned)__popc(peers));
+      }
+    }
+  }
+  if (digit == 1) {
+    __shared__ double red[kSelThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    if (lane == 0) red[threadIdx.x >> 5] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
+      work[kPartsWord + blockIdx.x * 4 + 3] = a;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if (alias[t] != t) continue;
+    unsigned int* g = sel_hist(work, digit, t);
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+      if (h[t][i]) atomicAdd(&g[i], h[t][i]);
+  }
+  if (!sel_last_block(work, digit)) return;
+  if (digit == 1) {
+    const double ss = sel_sum_parts(work, 3, gridDim.x);
+    if (threadIdx.x == 0) {
+      const double cnt = __ldcg(work);
+      work[3] = cnt > 0 ? ss / cnt : 0.0;
+    }
+    __syncthreads();
+  }
+  sel_pick(work, digit);
+  if (digit == 7 && threadIdx.x == 0) sel_sigma(work, rms_override, sigma_prev, sigma_prev_dev, sigma_out);
+}
+
+// First kernel on given residuals (floats): keys, sums, digit-0 histogram.
+__global__ void __launch_bounds__(kSelThreads) k_sel_floats(const float* __restrict__ r, int64_t n,
+                                                            uint64_t* __restrict__ keys, double* __restrict__ work) {
+  __shared__ unsigned int h0[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h0[i] = 0;
+  __syncthreads();
+  double c = 0, se = 0, sx = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t m0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); m0 < n; m0 += stride) {
+    const int64_t m = m0 + (threadIdx.x & 31);
+    const double v = m < n ? (double)r[m] : 0.0;
+    const bool valid = m < n && isfinite(v);
+    sel_consume(valid, v, 0.0, keys, m, m < n, h0, c, se, sx);
+  }
+  __syncthreads();
+  sel_first_finish(work, h0, c, se, sx);
+}
+
+// First kernel of the tensor rule: residuals at the probe entries from the merged subchains
+// of the full tensor, x_hat = sum_kappa A[a][kappa] C[b][kappa] (Thm. 1 with the ring cut in two).
+// Eight lanes per probe (each a strided part of the length-Kp dot product, then a 3-step
+// shuffle sum); probe m is described by pa[m] (inner index, -1 when unobserved), pb[m] and px[m].
+template <typename T>
+__global__ void __launch_bounds__(kSelThreads)
+    k_sel_probe(const T* __restrict__ A, const T* __restrict__ C, int Kp, const int32_t* __restrict__ pa,
+                const int32_t* __restrict__ pb, const float* __restrict__ px, int64_t n,
+                uint64_t* __restrict__ keys, double* __restrict__ work) {
+  __shared__ unsigned int h0[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h0[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, sub = lane & 7;
+  double c = 0, se = 0, sx = 0;
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  for (int64_t g0 = (((int64_t)blockIdx.x * blockDim.x) >> 3) + ((threadIdx.x & ~31) >> 3); g0 < n; g0 += stride) {
+    const int64_t m = g0 + (lane >> 3);           // this group's probe
+    const bool live = m < n;
+    const int32_t a = live ? pa[m] : -1;
+    const bool obs = a >= 0;
+    const float xf = obs ? px[m] : 0.f;
+    T part = T(0);
+    if (obs) {
+      const T* Ar = A + (int64_t)a * Kp;
+      const T* Cr = C + (int64_t)pb[m] * Kp;
+      // independent loads in flight (up to Kp = 256), two accumulators
+      T p2 = T(0);
+#pragma unroll
+      for (int q = 0; q < 32; q += 2) {
+        const int k0 = sub + 8 * q, k1 = k0 + 8;
+        if (k0 < Kp) part = fma(Ar[k0], Cr[k0], part);
+        if (k1 < Kp) p2 = fma(Ar[k1], Cr[k1], p2);
+      }
+      part += p2;
+    }
+    part += __shfl_xor_sync(0xffffffffu, part, 4);
+    part += __shfl_xor_sync(0xffffffffu, part, 2);
+    part += __shfl_xor_sync(0xffffffffu, part, 1);
+    double e = 0.0, x2 = 0.0;
+    bool valid = false;
+    if (obs && sub == 0) {
+      const T x = (T)xf;
+      const T et = x - part;
+      valid = isfinite((double)et);
+      e = (double)et;
+      x2 = (double)x * (double)x;
+    }
+    sel_consume(valid, e, x2, keys, m, live && sub == 0, h0, c, se, sx);
+  }
+  __syncthreads();
+  sel_first_finish(work, h0, c, se, sx);
+}
+
+// Probe description for the tensor rule: probe m is the entry lin[m] (all entries in order
+// when numel <= 2^20, else the SplitMix64(0x5eed, m) mod numel positions sorted ascending, so
+// that neighbouring probes share merged rows), split as lin = a + P_in b; pa = -1 when
+// unobserved.
+__global__ void k_probe_setup(const float* __restrict__ X, const uint32_t* __restrict__ M, const int64_t* __restrict__ lin_in,
+                              int64_t n, int64_t P_in, int32_t* __restrict__ pa, int32_t* __restrict__ pb,
+                              float* __restrict__ px) {
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lin = lin_in ? lin_in[m] : m;
+    const bool obs = M ? ((M[lin >> 5] >> (lin & 31)) & 1u) : true;
+    pa[m] = obs ? (int32_t)(lin % P_in) : -1;
+    pb[m] = (int32_t)(lin / P_in);
+    px[m] = X[lin];
+  }
+}
+
+cudaError_t run_digits(const uint64_t* keys, int64_t n, double* work, int nb, double rms_override, double sigma_prev,
+                       const double* sigma_prev_dev, double* sigma_out, cudaStream_t st) {
+  for (int d = 1; d < 8; ++d) {
+    k_sel_digit<<<nb, kSelThreads, 0, st>>>(keys, n, work, d, rms_override, sigma_prev, sigma_prev_dev, sigma_out);
     note_launch();
   }
-  k_sigma_final<<<1, 1, 0, st>>>(work, rms_override, sigma_prev, sigma_prev_dev, sigma_out);
+  return cudaGetLastError();
+}
+
+int sel_blocks(int64_t n) { return (int)imax(1, imin(kSelBlocks, (n + 4 * kSelThreads - 1) / (4 * kSelThreads))); }
+
+}  // namespace
+
+size_t sigma_work_doubles() { return (size_t)kPartsWord + (size_t)kSelBlocks * 4; }
+
+void probe_positions(int64_t numel, std::vector<int64_t>& lin) {
+  const int64_t n = numel <= kProbeMax ? numel : kProbeMax;
+  lin.resize((size_t)n);
+  if (numel <= kProbeMax) {
+    for (int64_t m = 0; m < n; ++m) lin[(size_t)m] = m;
+    return;
+  }
+  for (int64_t m = 0; m < n; ++m) lin[(size_t)m] = (int64_t)(sm64(kProbeSeed, (uint64_t)m) % (uint64_t)numel);
+  std::sort(lin.begin(), lin.end());
+}
+
+cudaError_t launch_probe_setup(const float* X, const uint32_t* M, const int64_t* lin_dev, int64_t n, int64_t P_in,
+                               int32_t* pa, int32_t* pb, float* px, cudaStream_t st) {
+  k_probe_setup<<<(unsigned)imin((n + 255) / 256, 4096), 256, 0, st>>>(X, M, lin_dev, n, P_in, pa, pb, px);
   note_launch();
   return cudaGetLastError();
 }
 
-}  // namespace
-
-size_t sigma_work_doubles() { return 64 + 1024 + 256 * 3 + 64; }
-
-cudaError_t launch_probe_sigma(const double* const* Zdev_ptrs, int N, const int64_t* dim_dev,
-                               const int* R_dev, const float* X, const uint32_t* M, int64_t numel,
-                               bool fp64, double sigma_prev, const double* sigma_prev_dev,
-                               double* vals, uint64_t* keys, double* xsq, double* work,
-                               double* sigma_out, cudaStream_t st) {
-  const bool full = numel <= kProbeMax;
-  const int64_t n = full ? numel : kProbeMax;
-  const unsigned blocks = (unsigned)imin((n + 127) / 128, 152 * 16);
-  if (fp64)
-    k_probe_resid<double><<<blocks, 128, 0, st>>>(Zdev_ptrs, N, dim_dev, R_dev, X, M, numel, full, n, vals, keys, xsq);
-  else
-    k_probe_resid<float><<<blocks, 128, 0, st>>>(Zdev_ptrs, N, dim_dev, R_dev, X, M, numel, full, n, vals, keys, xsq);
-  note_launch();
-  cudaError_t e = cudaGetLastError();
+cudaError_t launch_probe_sigma_merged(const void* A, const void* C, bool fp64, int Kp, const int32_t* pa,
+                                      const int32_t* pb, const float* px, int64_t n, double sigma_prev,
+                                      const double* sigma_prev_dev, uint64_t* keys, double* work,
+                                      double* sigma_out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(work, 0, sizeof(double) * kPartsWord, st);
   if (e != cudaSuccess) return e;
-  return finish_sigma(vals, keys, xsq, n, -1.0, sigma_prev, sigma_prev_dev, work, sigma_out, st);
+  // eight lanes per probe, about four probes per lane group
+  const int nb = (int)imax(1, imin(kSelBlocks, (n * 8 + 4 * kSelThreads - 1) / (4 * kSelThreads)));
+  if (fp64)
+    k_sel_probe<double><<<nb, kSelThreads, 0, st>>>((const double*)A, (const double*)C, Kp, pa, pb, px, n, keys, work);
+  else
+    k_sel_probe<float><<<nb, kSelThreads, 0, st>>>((const float*)A, (const float*)C, Kp, pa, pb, px, n, keys, work);
+  note_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return run_digits(keys, n, work, sel_blocks(n), -1.0, sigma_prev, sigma_prev_dev, sigma_out, st);
 }
 
-cudaError_t launch_probe_sigma_merged(const void* A, const void* C, bool fp64, int Kp, int64_t P_in,
-                                      const float* X, const uint32_t* M, int64_t numel, double sigma_prev,
-                                      const double* sigma_prev_dev, double* vals, uint64_t* keys, double* xsq,
-                                      double* work, double* sigma_out, cudaStream_t st) {
-  const bool full = numel <= kProbeMax;
-  const int64_t n = full ? numel : kProbeMax;
-  const unsigned blocks = (unsigned)imin((n + 255) / 256, 152 * 8);
-  if (fp64)
-    k_probe_merged<double><<<blocks, 256, 0, st>>>((const double*)A, (const double*)C, Kp, P_in, X, M, numel, full, n,
-                                                   vals, keys, xsq);
-  else
-    k_probe_merged<float><<<blocks, 256, 0, st>>>((const float*)A, (const float*)C, Kp, P_in, X, M, numel, full, n,
-                                                  vals, keys, xsq);
-  note_launch();
-  cudaError_t e = cudaGetLastError();
+cudaError_t launch_sigma_from_floats(const float* r, int64_t n, double x_obs_rms, double sigma_prev, uint64_t* keys,
+                                     double* work, double* sigma_out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(work, 0, sizeof(double) * kPartsWord, st);
   if (e != cudaSuccess) return e;
-  return finish_sigma(vals, keys, xsq, n, -1.0, sigma_prev, sigma_prev_dev, work, sigma_out, st);
-}
-
-cudaError_t launch_sigma_from_floats(const float* r, int64_t n, double x_obs_rms, double sigma_prev,
-                                     double* vals, uint64_t* keys, double* xsq, double* work,
-                                     double* sigma_out, cudaStream_t st) {
-  k_float_keys<<<(unsigned)imin((n + 255) / 256, 4096), 256, 0, st>>>(r, n, vals, keys, xsq);
+  const int nb = sel_blocks(n);
+  k_sel_floats<<<nb, kSelThreads, 0, st>>>(r, n, keys, work);
   note_launch();
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return finish_sigma(vals, keys, xsq, n, x_obs_rms, sigma_prev, nullptr, work, sigma_out, st);
+  return run_digits(keys, n, work, nb, x_obs_rms, sigma_prev, nullptr, sigma_out, st);
 }
 
 // ------------------------------------------------------------------ allocation-free variant
-// Fixed scratch for trd_sigma_from_residuals_noalloc: room for NOALLOC_MAX residuals (values,
-// order keys and a zero x^2 column, 8 bytes each) plus the selection work area.  It is a
-// file-scope device array, so every GPU that loads the library holds it (about 24 MB) until
-// the process exits; all calls share it.
+// Fixed scratch for trd_sigma_from_residuals_noalloc: room for the order keys of NOALLOC_MAX
+// residuals (8 bytes each) plus the selection work area.  It is a file-scope device array, so
+// every GPU that loads the library holds it (about 8.4 MB) until the process exits; all calls
+// share it.
 constexpr int64_t NOALLOC_MAX = int64_t(1) << 20;
-constexpr size_t NOALLOC_WORK = 64 + 1024 + 256 * 3 + 64;   // doubles; equals sigma_work_doubles()
-static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_MAX * 24 + NOALLOC_WORK * 8];
+constexpr size_t NOALLOC_WORK = kPartsWord + kSelBlocks * 4;   // doubles; equals sigma_work_doubles()
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_MAX * 8 + NOALLOC_WORK * 8];
 
 namespace {
 constexpr int NOALLOC_DEVICES = 64;
@@ -423,14 +497,12 @@ extern "C" trd_status trd_sigma_from_residuals_noalloc(const float* resid_dev, i
     base = g_noalloc_addr[dev];
   }
   unsigned char* b = static_cast<unsigned char*>(base);
-  double* vals = reinterpret_cast<double*>(b);
-  uint64_t* keys = reinterpret_cast<uint64_t*>(b + NOALLOC_MAX * 8);
-  double* xsq = reinterpret_cast<double*>(b + NOALLOC_MAX * 16);
-  double* work = reinterpret_cast<double*>(b + NOALLOC_MAX * 24);
-  // every scratch word the selection reads is written first in this call (the histogram is
-  // cleared by the selection's own initialisation), so stale contents do not leak in
-  const cudaError_t e = launch_sigma_from_floats(resid_dev, n, x_obs_rms, sigma_prev, vals, keys, xsq, work,
-                                                 sigma_out_dev, (cudaStream_t)cuda_stream);
+  uint64_t* keys = reinterpret_cast<uint64_t*>(b);
+  double* work = reinterpret_cast<double*>(b + NOALLOC_MAX * 8);
+  // every scratch word the selection reads is written first in this call (the counters and
+  // histograms are cleared at its start), so stale contents do not leak in
+  const cudaError_t e = launch_sigma_from_floats(resid_dev, n, x_obs_rms, sigma_prev, keys, work, sigma_out_dev,
+                                                 (cudaStream_t)cuda_stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return TRD_ECUDA;

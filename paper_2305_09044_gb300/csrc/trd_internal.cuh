@@ -140,7 +140,7 @@ struct trd_handle {
   trd::DevBuf Tpart, Tsum, stat_part, stat_sum;
   trd::DevBuf pre, post, dpart;      // back-contraction
   trd::DevBuf d, h, G, L, T1, T2, D, Dprev;
-  trd::DevBuf probe_keys, probe_vals, probe_work;
+  trd::DevBuf probe_keys, probe_work;
   bool merged_valid_st = false, merged_valid_str = false;
   uint64_t merged_ver[trd::kMaxN] = {};
   int merged_k = -1;
@@ -189,9 +189,10 @@ cudaError_t launch_pass_simt(const PassArgs& a, bool is_double, bool rows_case, 
                              int splits, int* ctas_out, int* splits_out, cudaStream_t st);
 
 // pass_tc.cu (tcgen05 BF16 data passes)
-int tc_kpad();
+int tc_kpad(int Kp);   // padded contraction of the tensor-core passes (0: unsupported)
 int tc_bm();
 int tc_bn();
+cudaError_t launch_wait_selftest(bool arrive, uint32_t limit, int* err, cudaStream_t st);
 cudaError_t launch_tc_prep(const float* src, int64_t rows, int Kp, __nv_bfloat16* hi, __nv_bfloat16* lo,
                            cudaStream_t st);
 cudaError_t launch_mask_rows(const uint32_t* M, int64_t P_in, int64_t P_out, int64_t W, uint32_t* out,
@@ -212,6 +213,14 @@ cudaError_t launch_fgmc_E(const double* Z, const int32_t* idx, int64_t n, int rk
 cudaError_t launch_dgemm(const double* A, const double* B, double* C, int M, int N, int K,
                          bool transB, cudaStream_t st);
 cudaError_t launch_phi(const double* T, int p, int q, double* G, cudaStream_t st);
+// one-CTA LDL^T (register-resident triangle) and the warp-per-row solve: K <= kLdlKmax
+constexpr int kLdlKmax = 128;
+inline bool ldl_fits(int K) { return K >= 1 && K <= kLdlKmax; }
+cudaError_t launch_ldl_factor(const double* G, int K, double lambda, double* Lcm, double* Dinv, double* scal,
+                              int* dstatus, cudaStream_t st);
+// also <d, h> into *num (per-row parts in dot_part[rows]; ctr: a zeroed counter word, left zero)
+cudaError_t launch_ldl_solve(const double* Lcm, const double* Dinv, const double* d, double* h, int K, int64_t rows,
+                             double* dot_part, unsigned int* ctr, double* num, cudaStream_t st);
 cudaError_t launch_cholesky(const double* G, int K, double lambda, double* L, double* scal,
                             int* dstatus, cudaStream_t st);
 cudaError_t launch_solve_rows(const double* L, const double* d, double* h, int K, int64_t rows,
@@ -227,18 +236,16 @@ cudaError_t launch_stop_error(const double* D, double* Dprev, int64_t n, double*
 
 // sigma.cu
 size_t sigma_work_doubles();
-cudaError_t launch_probe_sigma(const double* const* Zdev_ptrs, int N, const int64_t* dim_dev,
-                               const int* R_dev, const float* X, const uint32_t* M, int64_t numel,
-                               bool fp64, double sigma_prev, const double* sigma_prev_dev,
-                               double* vals, uint64_t* keys, double* xsq, double* work,
-                               double* sigma_out, cudaStream_t st);
-cudaError_t launch_probe_sigma_merged(const void* A, const void* C, bool fp64, int Kp, int64_t P_in,
-                                      const float* X, const uint32_t* M, int64_t numel, double sigma_prev,
-                                      const double* sigma_prev_dev, double* vals, uint64_t* keys, double* xsq,
-                                      double* work, double* sigma_out, cudaStream_t st);
-cudaError_t launch_sigma_from_floats(const float* r, int64_t n, double x_obs_rms, double sigma_prev,
-                                     double* vals, uint64_t* keys, double* xsq, double* work,
-                                     double* sigma_out, cudaStream_t st);
+// probe positions of the adaptive width (host): 0..numel-1, or 2^20 SplitMix64 draws, sorted
+void probe_positions(int64_t numel, std::vector<int64_t>& lin);
+cudaError_t launch_probe_setup(const float* X, const uint32_t* M, const int64_t* lin_dev, int64_t n, int64_t P_in,
+                               int32_t* pa, int32_t* pb, float* px, cudaStream_t st);
+cudaError_t launch_probe_sigma_merged(const void* A, const void* C, bool fp64, int Kp, const int32_t* pa,
+                                      const int32_t* pb, const float* px, int64_t n, double sigma_prev,
+                                      const double* sigma_prev_dev, uint64_t* keys, double* work,
+                                      double* sigma_out, cudaStream_t st);
+cudaError_t launch_sigma_from_floats(const float* r, int64_t n, double x_obs_rms, double sigma_prev, uint64_t* keys,
+                                     double* work, double* sigma_out, cudaStream_t st);
 
 // sampled.cu
 // Strides of each mode inside the inner (a) / outer (b) block of a two-block cut (0 if the mode

@@ -1,8 +1,9 @@
 """Parity of the tensor-core (tcgen05, BF16) data passes with the FP64 oracle (needs a GB300).
 
 Tolerance: 5e-3 relative (Frobenius) per step for d, eta and the core change.  Shapes keep
-r_1 r_c <= 64 and an inner block size that is a multiple of 4 (the path's limits) while
-leaving every tile ragged (no size is a multiple of the 128 x 64 tile).
+r_1 r_c <= 128 (contraction padded to 64 or 128) and an inner block size that is a multiple
+of 4 (the path's limits) while leaving every tile ragged (no size is a multiple of the
+128 x 64 tile).
 """
 import math
 
@@ -22,6 +23,8 @@ SHAPES = [
     ((52, 44, 30, 28), (4, 3, 4, 2)),       # small ranks, 2288 x 840
     ((64, 40, 36), (8, 8, 8)),              # order 3: 64 x 1440 (one ragged stationary block)
     ((20, 16, 12, 10, 9), (2, 3, 2, 2, 3)), # order 5: 320 x 1080
+    ((24, 20, 18, 16), (10, 10, 10, 10)),   # K' = 100 (padded to 128), K = 100
+    ((32, 28, 20, 12), (8, 8, 16, 8)),      # K' = 128, K = 64 / 128
 ]
 
 
@@ -128,3 +131,28 @@ def test_bf16_recovery_matches_oracle(torch_cuda):
     err_o = O.relative_error(cores, Xt)
     err_g = t.recovery_error(torch_cuda.from_numpy(flat(Xt)).cuda())
     assert abs(err_o - err_g) <= 1e-4, (err_o, err_g)
+
+
+@pytest.mark.parametrize("dims,ranks,s", [((16, 12, 12, 12, 12), (10, 10, 10, 10, 10), 8),
+                                           ((40, 33, 29, 21), (3, 2, 4, 2), 8)])
+def test_bf16_sketched_step_parity(torch_cuda, dims, ranks, s):
+    """SAWRTRD on the tensor-core path: RStS gather with the specified index draw, then the
+    per-step checks on the sketch (order 5 with ranks 10 is the 64^5 workload's shape class,
+    K' = 100 padded to 128)."""
+    t, X, P, Xt, keep = _make(torch_cuda, dims, ranks)
+    cores = O.init_cores(dims, ranks, seed=12)
+    sigma = 1.7
+    N = len(dims)
+    sizes = [s] * N
+    for k in range(N):
+        t.set_cores(cores)
+        sample = [O.draw_indices(3, 0, k, j, N, dims[j], sizes[j]) if j != k else None for j in range(N)]
+        t.sample_subtensor(k, sample)
+        st = O.core_update(X, P, cores, k, sigma, lam=-1e-10, sample=sample)
+        t.residual_weights(k, sigma)
+        d = t.core_gradient(k)
+        assert rel(d, st.d) <= TOL, (k, rel(d, st.d))
+        eta = t.core_update(k, -1e-10)
+        assert abs(eta - st.eta) <= TOL * abs(st.eta), (k, eta, st.eta)
+        assert rel(t.get_core(k) - cores[k], st.cores[k] - cores[k]) <= TOL
+        cores = st.cores

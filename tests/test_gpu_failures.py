@@ -1,0 +1,113 @@
+"""Failure detection on the GPU path, made on the host side or by a wait that runs out:
+a singular FGMC system (lambda = 0 with a zero core), a non-finite residual at an observed
+entry, NaN stored at unobserved entries (must be ignored), and the bounded device wait of
+the tensor-core pass giving up.  No test faults, traps or hangs the device; after every
+failure the same handle is used again and must give the oracle's result.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import trd_oracle as O
+
+from .helpers import flat, problem, rel
+
+pytestmark = pytest.mark.gpu
+
+DIMS, RANKS = (24, 20, 16, 12), (3, 2, 3, 2)
+TOL = {"fp64": 1e-10, "fp32": 1e-4, "bf16": 5e-3}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_09044_gb300 import build
+    build.build()
+    return torch
+
+
+def _handle(torch, prec, X, words):
+    from paper_2305_09044_gb300 import TRD
+    t = TRD(DIMS, RANKS, prec)
+    xd = torch.from_numpy(flat(X)).cuda()
+    md = torch.from_numpy(words.view(np.int32)).cuda()
+    t.set_data(xd, md)
+    return t, (xd, md)
+
+
+def _update_matches_oracle(t, X, P, cores, k, tol, sigma=1.5):
+    t.set_cores(cores)
+    st = O.core_update(X, P, cores, k, sigma, lam=-1e-10)
+    t.residual_weights(k, sigma)
+    t.core_gradient(k)
+    eta = t.core_update(k, -1e-10)
+    assert abs(eta - st.eta) <= tol * abs(st.eta)
+    assert rel(t.get_core(k) - cores[k], st.cores[k] - cores[k]) <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_singular_system_is_reported_and_step_rejected(torch_cuda, prec):
+    """A zero core makes every Gram G^{!=k} (k != that core) zero; with lambda = 0 the
+    factorisation meets a zero pivot: TRD_ESINGULAR, eta forced to 0, core unchanged."""
+    from paper_2305_09044_gb300 import TrdError, binding
+    X, P, words, truth, Xt = problem(DIMS, RANKS, 0.3, 0.1, 41)
+    t, keep = _handle(torch_cuda, prec, X, words)
+    cores = O.init_cores(DIMS, RANKS, seed=5)
+    broken = [c.copy() for c in cores]
+    broken[2][:] = 0.0
+    t.set_cores(broken)
+    t.residual_weights(0, 1.5)
+    t.core_gradient(0)
+    with pytest.raises(TrdError) as ei:
+        t.core_update(0, 0.0)
+    assert ei.value.status == binding.TRD_ESINGULAR
+    assert np.array_equal(t.get_core(0), broken[0])
+    _update_matches_oracle(t, X, P, cores, 1, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_nonfinite_observed_entry_is_reported(torch_cuda, prec):
+    from paper_2305_09044_gb300 import TrdError, binding
+    X, P, words, truth, Xt = problem(DIMS, RANKS, 0.3, 0.1, 42)
+    obs = np.flatnonzero(flat(P) > 0)
+    Xbad = flat(X).copy()
+    Xbad[obs[[3, len(obs) // 2]]] = [np.nan, np.inf]
+    t, keep = _handle(torch_cuda, prec, Xbad.reshape(X.shape, order="F"), words)
+    cores = O.init_cores(DIMS, RANKS, seed=6)
+    t.set_cores(cores)
+    s = t.residual_weights(1, 1.5, raise_nonfinite=False)
+    assert s["n_nonfinite"] == 2 and s["n_obs"] == len(obs)
+    with pytest.raises(TrdError) as ei:
+        t.residual_weights(1, 1.5)
+    assert ei.value.status == binding.TRD_ENONFINITE
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_nan_at_unobserved_entries_is_ignored(torch_cuda, prec):
+    """Unobserved entries take no part in the method (P masks them, Eq. 6): storing NaN
+    there changes nothing."""
+    X, P, words, truth, Xt = problem(DIMS, RANKS, 0.3, 0.1, 43)
+    Xn = np.where(P > 0, X, np.nan)
+    t, keep = _handle(torch_cuda, prec, Xn, words)
+    cores = O.init_cores(DIMS, RANKS, seed=7)
+    for k in (0, 3):
+        _update_matches_oracle(t, X, P, cores, k, TOL[prec])
+        t.set_cores(cores)
+        s = t.residual_weights(k, 1.5)
+        assert s["n_nonfinite"] == 0 and math.isfinite(s["sum_we2"])
+
+
+def test_device_wait_gives_up_with_status(torch_cuda):
+    """The bounded mbarrier wait of the tensor-core pass, on a barrier nothing arrives on,
+    gives up after its limit and reports TRD_ETIMEOUT; the handle stays usable."""
+    from paper_2305_09044_gb300 import binding
+    X, P, words, truth, Xt = problem(DIMS, RANKS, 0.3, 0.1, 44)
+    t, keep = _handle(torch_cuda, "bf16", X, words)
+    assert t.wait_selftest(True, 1 << 10) == binding.TRD_OK
+    assert t.wait_selftest(False, 1 << 12) == binding.TRD_ETIMEOUT
+    assert t.wait_selftest(False, 0) == binding.TRD_EINVAL
+    assert t.wait_selftest(True, 1 << 10) == binding.TRD_OK
+    _update_matches_oracle(t, X, P, O.init_cores(DIMS, RANKS, seed=8), 2, TOL["bf16"])

@@ -234,3 +234,25 @@ def test_trajectory_sketched_fp32(torch_cuda):
         for k in range(4):
             assert abs(r["eta"][k] - steps[k].eta) <= 1e-4 * abs(steps[k].eta)
     assert rel(O.reconstruct(t.get_cores()), O.reconstruct(cores)) <= 1e-4
+
+
+@pytest.mark.parametrize("prec,dims,ranks", [("fp64", (12, 10, 9, 8), (10, 10, 10, 10)),
+                                             ("fp32", (10, 9, 8, 7), (8, 16, 8, 16)),
+                                             ("fp32", (9, 8, 7, 6, 5), (11, 11, 11, 11, 11))])
+def test_scaled_step_large_gram(torch_cuda, prec, dims, ranks):
+    """K = r_k r_{k+1} of 100, 128 and 121: the FP64 LDL^T factorisation and the
+    row-parallel solves of the scaled step (Eq. sg, Eq. hI) at the Gram sizes of the 64^5 rank-10
+    workload and beyond, against the oracle's Cholesky, from identical state."""
+    t, X, P, Xt, keep = _make(torch_cuda, dims, ranks, prec)
+    cores = O.init_cores(dims, ranks, seed=13)
+    sigma = 2.0
+    for k in range(len(dims)):
+        t.set_cores(cores)
+        st = O.core_update(X, P, cores, k, sigma, lam=-1e-10)
+        t.residual_weights(k, sigma)
+        d = t.core_gradient(k)
+        assert rel(d, st.d) <= TOL[prec]
+        eta = t.core_update(k, -1e-10)
+        assert abs(eta - st.eta) <= TOL[prec] * 10 * abs(st.eta), (k, eta, st.eta)
+        assert rel(t.get_core(k) - cores[k], st.cores[k] - cores[k]) <= TOL[prec] * 10
+        cores = st.cores
