@@ -55,7 +55,9 @@ typedef enum {
   TRD_FP64 = 0,  /* SIMT FP64 data passes (small problems, debugging) */
   TRD_FP32 = 1,  /* SIMT FP32 data passes, FP32 accumulation */
   TRD_BF16 = 2   /* tcgen05 tensor cores: split-BF16 reconstruction, BF16 gradient and
-                    line-search products, FP32 accumulation; residual and weight in FP32 */
+                    line-search products, FP32 accumulation; residual and weight in FP32;
+                    r_1 r_{c+1} <= 128 (c = the cut of the ring) and an inner block size that
+                    is a multiple of 4, else TRD_ENOTIMPL */
 } trd_precision;
 
 typedef enum {
@@ -186,7 +188,7 @@ trd_status trd_core_gradient(trd_t* handle, int k, double* d_host);
 trd_status trd_fgmc_gram(trd_t* handle, int k, double* G_host);
 
 /* Step 'update Z_k' (Eq. hI, Eq. ftrbcn and the exact line search): h = d (G + lambda I)^-1
- * by FP64 Cholesky; eta = <d,h> / ||sqrt(W) o P o (h B^T)||^2 on the sketch when eta <= 0
+ * in FP64 (LDL^T factorisation and substitutions for K_k <= 128, Cholesky above); eta = <d,h> / ||sqrt(W) o P o (h B^T)||^2 on the sketch when eta <= 0
  * (second data pass, W recomputed from the same residuals), else the given eta;
  * Z_k <- Z_k + eta fold(h) (update-sign reading); refreshes core k's FGMC factor.
  * lambda >= 0 absolute, < 0 means |lambda| tr(G)/K.  `gram` is a trd_gram_kind.
@@ -265,8 +267,17 @@ trd_status trd_set_profiling(trd_t* handle, int on);
  * doubles).  reset != 0 clears the totals afterwards. */
 trd_status trd_get_profile(trd_t* handle, int reset, double* out);
 
-/* Number of kernels the library has launched in this process (all handles). */
+/* Number of kernels the library has launched in this process (all handles); a replayed
+ * step graph counts its kernel nodes. */
 int64_t trd_kernel_launches(void);
+
+/* Execution option (no counterpart in the paper).  With `on` nonzero (the default) an
+ * unsketched trd_step that repeats the previous step's arguments, with no other state-changing
+ * call in between, is captured once as a CUDA graph and then replayed: the same kernels in the
+ * same order on the same buffers, launched as one graph.  Any other call that changes the
+ * handle's state (data, cores, sketch, single-core steps, tracing level) ends the replay; the
+ * next steps run eagerly and are captured again.  on = 0 always runs eagerly. */
+trd_status trd_set_graphs(trd_t* handle, int on);
 
 /* Failure-detection self-test (no counterpart in the paper).  Runs, on the handle's stream,
  * the bounded mbarrier wait that every role of the tensor-core data pass uses, on a fresh

@@ -36,7 +36,7 @@ EXPORTS = [
     "trd_sigma_from_residuals", "trd_reconstruct", "trd_reconstruct_from",
     "trd_recovery_error", "trd_sampled_fwd", "trd_sampled_bwd", "trd_set_profiling",
     "trd_get_profile", "trd_kernel_launches", "trd_sigma_from_residuals_noalloc",
-    "trd_wait_selftest",
+    "trd_wait_selftest", "trd_set_graphs",
 ]
 
 
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
         "trd_kernel_launches": [],
         "trd_sigma_from_residuals_noalloc": [vp, i64, dbl, dbl, vp, vp],
         "trd_wait_selftest": [vp, C.c_int, i64],
+        "trd_set_graphs": [vp, C.c_int],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -355,6 +356,10 @@ class TRD:
                                              idx.shape[0], sigma, 1 if fp64 else 0, g_scale, gptrs),
                     "trd_sampled_bwd")
         return grads
+
+    def set_graphs(self, on: bool = True):
+        """Capture and replay repeated unsketched steps as a CUDA graph (default on)."""
+        self._check(self.lib.trd_set_graphs(self.h, 1 if on else 0), "trd_set_graphs")
 
     def wait_selftest(self, arrive: bool, limit: int) -> int:
         """Run the bounded device wait once (see trd_wait_selftest); returns the raw status

@@ -45,6 +45,7 @@ trd_status ensure(trd_handle* h, DevBuf& b, size_t bytes) {
 
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 // implemented in merge.cu / sampled.cu / pass_tc.cu
@@ -93,6 +94,7 @@ struct Extra {
   DevBuf tmpZ[kMaxN];   // cores given to trd_reconstruct_from
   DevBuf probe_a, probe_b, probe_x;   // adaptive-width probe: inner / outer index, data
   DevBuf dotpart, solve_ctr;          // per-row parts of <d, h>, completion counter
+  DevBuf probe_cand;                  // selection candidates of the adaptive width
   // what the merged-half buffers hold (FP32/FP64 h->Sst / h->Sstr, BF16 operands bS* / bT*)
   HalfTag tagSst, tagSstr, tagBst, tagBstr;
   uint64_t view_gen = 0;    // 0 = the full tensor; every drawn sketch gets a new number
@@ -117,6 +119,24 @@ struct Extra {
   int tcG = 0;
   // tracing: event pairs around data-pass launches (kind 0 = pass 1, 1 = pass 2)
   int prof = 0;            // 0 off, 1 data passes, 2 every phase
+  // CUDA graph of a full (unsketched) trd_step: captured on the second consecutive step with
+  // the same arguments and nothing else called in between, then replayed until another call
+  // touches the handle
+  struct GraphKey {
+    double sigma = 0, lambda = 0;
+    int gram = -1, prof = -1;
+    bool operator==(const GraphKey& o) const {
+      return sigma == o.sigma && lambda == o.lambda && gram == o.gram && prof == o.prof;
+    }
+  } gkey;
+  bool graphs_enabled = true;
+  bool graph_ok = false;
+  int steady = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_kernels = 0, graph_slots = 0;
+  struct EvNodes { cudaGraphNode_t a, b; int kind; };
+  std::vector<EvNodes> graph_ev;
   std::vector<cudaEvent_t> ev_pool;
   struct Pending { cudaEvent_t a, b; int kind; };
   std::vector<Pending> pending;
@@ -162,8 +182,8 @@ void prof_end(trd_handle* h, int kind) {
 enum : int { P_PASS1 = 0, P_PASS2 = 1, P_MERGE = 2, P_REDUCE = 3, P_GRAD = 4, P_GRAM = 5, P_CHOL = 6,
              P_SOLVE = 7, P_UPDATE = 8, P_SIGMA = 9, P_STOP = 10 };
 
-// RAII: events around a phase when tracing is on (phases never nest).
-// Phase scope: traced only at profiling level 2 (the data passes are traced from level 1).
+// RAII phase scope: events around a phase, only at tracing level 2 (the data passes are traced
+// from level 1); phases never nest.
 struct PScope {
   trd_handle* h;
   int kind;
@@ -192,6 +212,23 @@ void prof_harvest(trd_handle* h) {
   }
   x->pending.clear();
 }
+void drop_graph(Extra* x) {
+  if (x->graph_exec) cudaGraphExecDestroy(x->graph_exec);
+  if (x->graph) cudaGraphDestroy(x->graph);
+  x->graph_exec = nullptr;
+  x->graph = nullptr;
+  x->graph_ok = false;
+  x->graph_ev.clear();
+}
+
+// Any call other than trd_step (and pure queries) ends graph replay: the captured step
+// assumes the device state that the previous step left behind.
+void touch(trd_handle* h) {
+  Extra* x = X_(h);
+  x->steady = 0;
+  if (x->graph_ok || x->graph) drop_graph(x);
+}
+
 size_t elt(const trd_handle* h) { return is_fp64(h) ? sizeof(double) : sizeof(float); }
 
 // Balanced split of the view's modes into [0, c) and [c, N).
@@ -795,10 +832,11 @@ trd_status run_adaptive(trd_handle* h, double sigma_prev, const double* sigma_pr
     A = x->recA.p;
     Cm = x->recC.p;
   }
+  TRY(ensure(h, x->probe_cand, sizeof(uint64_t) * n));
   CK(launch_probe_sigma_merged(A, Cm, is_fp64(h), sp.Kp, (const int32_t*)x->probe_a.p,
                                (const int32_t*)x->probe_b.p, (const float*)x->probe_x.p, n, sigma_prev,
-                               sigma_prev_dev, (uint64_t*)h->probe_keys.p, (double*)h->probe_work.p,
-                               h->scal + S_SIGMA, h->stream),
+                               sigma_prev_dev, (uint64_t*)h->probe_keys.p, (uint64_t*)x->probe_cand.p,
+                               (double*)h->probe_work.p, h->scal + S_SIGMA, h->stream),
      "adaptive width");
   h->sigma_set = true;
   return TRD_OK;
@@ -1035,6 +1073,7 @@ trd_status trd_create(trd_t** out, int N, const int64_t* I, const int32_t* R, in
 void trd_destroy(trd_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  drop_graph(X_(h));
   for (int k = 0; k < kMaxN; ++k) {
     if (h->Z[k]) cudaFree(h->Z[k]);
     if (h->E[k]) cudaFree(h->E[k]);
@@ -1047,7 +1086,7 @@ void trd_destroy(trd_t* h) {
   for (DevBuf* b : bufs) free_buf(*b);
   Extra* x = X_(h);
   DevBuf* xb[] = {&x->Ework, &x->meta,    &x->stat_sum2, &x->Gloc,    &x->recA, &x->recC,
-                  &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr,
+                  &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr, &x->probe_cand,
                   &x->bShi,  &x->bSlo,    &x->bSh,       &x->bThi,    &x->bTlo,    &x->bTT,
                   &x->Mst[0], &x->Mst[1]};
   for (DevBuf* b : xb) free_buf(*b);
@@ -1069,6 +1108,7 @@ void trd_destroy(trd_t* h) {
 
 trd_status trd_set_data(trd_t* h, const float* X, const uint32_t* mask) {
   TRY(check_handle(h));
+  touch(h);
   if (!X) return set_err(h, TRD_EINVAL, "X must not be NULL");
   if (((uintptr_t)X & 15) || ((uintptr_t)mask & 15))
     return set_err(h, TRD_EINVAL, "X and mask must be 16-byte aligned");
@@ -1084,6 +1124,7 @@ trd_status trd_set_data(trd_t* h, const float* X, const uint32_t* mask) {
 
 trd_status trd_init_cores(trd_t* h, uint64_t seed, double stddev) {
   TRY(check_handle(h));
+  touch(h);
   const int N = h->N;
   uint64_t base = 0;
   for (int k = 0; k < N; ++k) {
@@ -1113,6 +1154,7 @@ trd_status trd_init_cores(trd_t* h, uint64_t seed, double stddev) {
 
 trd_status trd_set_core(trd_t* h, int k, const double* core) {
   TRY(check_handle(h));
+  touch(h);
   TRY(check_k(h, k));
   if (!core) return set_err(h, TRD_EINVAL, "NULL core");
   CK(cudaMemcpyAsync(h->Z[k], core, sizeof(double) * h->I[k] * h->K[k], cudaMemcpyHostToDevice, h->stream),
@@ -1135,6 +1177,7 @@ trd_status trd_get_core(trd_t* h, int k, double* core) {
 
 trd_status trd_reset_iteration(trd_t* h, int32_t t) {
   TRY(check_handle(h));
+  touch(h);
   h->t = t;
   TRY(reset_D0(h));
   return sync_and_status(h);
@@ -1149,6 +1192,7 @@ trd_status trd_draw_indices(uint64_t seed, int32_t t, int k, int j, int N, int64
 
 trd_status trd_sample_subtensor(trd_t* h, int k, const int32_t* const* idx, const int32_t* s) {
   TRY(check_handle(h));
+  touch(h);
   TRY(check_k(h, k));
   if (idx && !s) return set_err(h, TRD_EINVAL, "sizes missing");
   return sample(h, k, idx, s);
@@ -1156,6 +1200,7 @@ trd_status trd_sample_subtensor(trd_t* h, int k, const int32_t* const* idx, cons
 
 trd_status trd_residual_weights(trd_t* h, int k, double sigma, trd_resid_stats* out) {
   TRY(check_handle(h));
+  touch(h);
   TRY(check_k(h, k));
   if (!h->X) return set_err(h, TRD_EINVAL, "no data attached");
   if (h->sketched && h->view_k != k) return set_err(h, TRD_EINVAL, "the current sketch was drawn for another core");
@@ -1179,6 +1224,7 @@ trd_status trd_residual_weights(trd_t* h, int k, double sigma, trd_resid_stats* 
 
 trd_status trd_core_gradient(trd_t* h, int k, double* d_host) {
   TRY(check_handle(h));
+  touch(h);
   TRY(check_k(h, k));
   TRY(run_gradient(h, k));
   if (!d_host) return TRD_OK;
@@ -1189,6 +1235,7 @@ trd_status trd_core_gradient(trd_t* h, int k, double* d_host) {
 
 trd_status trd_fgmc_gram(trd_t* h, int k, double* G_host) {
   TRY(check_handle(h));
+  touch(h);
   TRY(check_k(h, k));
   TRY(ensure_gram(h, k));
   if (!G_host) return TRD_OK;
@@ -1199,6 +1246,7 @@ trd_status trd_fgmc_gram(trd_t* h, int k, double* G_host) {
 
 trd_status trd_core_update(trd_t* h, int k, double lambda, double eta, int gram, double* eta_out) {
   TRY(check_handle(h));
+  touch(h);
   TRY(check_k(h, k));
   if (gram < TRD_GRAM_GLOBAL || gram > TRD_GRAM_NONE) return set_err(h, TRD_EINVAL, "bad gram kind");
   TRY(run_update(h, k, lambda, eta, gram, nullptr));
@@ -1212,6 +1260,7 @@ trd_status trd_core_update(trd_t* h, int k, double lambda, double eta, int gram,
 
 trd_status trd_adaptive_sigma(trd_t* h, double sigma_prev, double* sigma_out) {
   TRY(check_handle(h));
+  touch(h);
   TRY(run_adaptive(h, sigma_prev));
   if (!sigma_out) return TRD_OK;
   CK(cudaMemcpyAsync(h->host_pinned, h->scal + S_SIGMA, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
@@ -1227,8 +1276,10 @@ trd_status trd_sigma_from_residuals(trd_t* h, const float* r, int64_t n, double 
   if (!r || n < 1 || rms < 0 || !sigma_out) return set_err(h, TRD_EINVAL, "bad arguments");
   TRY(ensure(h, h->probe_keys, sizeof(uint64_t) * n));
   TRY(ensure(h, h->probe_work, sizeof(double) * sigma_work_doubles()));
-  CK(launch_sigma_from_floats(r, n, rms, sigma_prev, (uint64_t*)h->probe_keys.p, (double*)h->probe_work.p,
-                              h->scal + S_SIGMA + 8, h->stream), "sigma from residuals");
+  TRY(ensure(h, X_(h)->probe_cand, sizeof(uint64_t) * n));
+  CK(launch_sigma_from_floats(r, n, rms, sigma_prev, (uint64_t*)h->probe_keys.p, (uint64_t*)X_(h)->probe_cand.p,
+                              (double*)h->probe_work.p, h->scal + S_SIGMA + 8, h->stream),
+     "sigma from residuals");
   CK(cudaMemcpyAsync(h->host_pinned, h->scal + S_SIGMA + 8, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
      "sigma");
   TRY(sync_and_status(h));
@@ -1236,13 +1287,14 @@ trd_status trd_sigma_from_residuals(trd_t* h, const float* r, int64_t n, double 
   return TRD_OK;
 }
 
-trd_status trd_step(trd_t* h, const trd_params* p, trd_report* rep) {
-  TRY(check_handle(h));
-  if (!p) return set_err(h, TRD_EINVAL, "NULL params");
-  if (!h->X) return set_err(h, TRD_EINVAL, "no data attached");
-  if (p->gram < TRD_GRAM_GLOBAL || p->gram > TRD_GRAM_NONE) return set_err(h, TRD_EINVAL, "bad gram kind");
+}  // extern "C"
+
+namespace {
+
+// The device work of one outer iteration (Algorithm 1, every core once), enqueued on the
+// handle's stream without any host synchronisation, so that it can be captured as a graph.
+trd_status step_device(trd_handle* h, const trd_params* p, int64_t* slots_out) {
   const int N = h->N;
-  if (!h->have_D0) TRY(reset_D0(h));
   if (p->sigma > 0) {
     TRY(set_sigma(h, p->sigma));
   } else {
@@ -1257,7 +1309,6 @@ trd_status trd_step(trd_t* h, const trd_params* p, trd_report* rep) {
     }
   }
   int64_t slots = 0;
-  std::vector<int32_t> idxbuf;
   for (int k = 0; k < N; ++k) {
     bool sketch = false;
     for (int m = 0; m < N; ++m)
@@ -1286,13 +1337,149 @@ trd_status trd_step(trd_t* h, const trd_params* p, trd_report* rep) {
     slots += h->slots_last;
   }
   {
-  PScope ps(h, P_STOP);
-  TRY(compute_D(h, (double*)h->D.p));
-  CK(launch_stop_error((const double*)h->D.p, (double*)h->Dprev.p, h->I[N - 1] * h->I[N - 1],
-                       h->report_dev + R_E, h->stream), "stopping quantity");
+    PScope ps(h, P_STOP);
+    TRY(compute_D(h, (double*)h->D.p));
+    CK(launch_stop_error((const double*)h->D.p, (double*)h->Dprev.p, h->I[N - 1] * h->I[N - 1],
+                         h->report_dev + R_E, h->stream), "stopping quantity");
   }
   CK(cudaMemcpyAsync(h->report_dev + R_SIGMA, h->scal + S_SIGMA, sizeof(double), cudaMemcpyDeviceToDevice,
                      h->stream), "sigma");
+  *slots_out = slots;
+  return TRD_OK;
+}
+
+// Host-side state after a step whose device work ran without the host logic (graph replay):
+// every core changed once; cached merges, Gram and pass results are treated as stale.
+void after_replay(trd_handle* h) {
+  for (int k = 0; k < h->N; ++k) h->ver[k]++;
+  h->pass1_k = -1;
+  h->grad_k = -1;
+  h->gram_k = -1;
+}
+
+// Capture one step into a graph, instantiate it and launch it (this launch is the step).  On
+// any failure the capture is abandoned, every cache is invalidated (the host logic ran but
+// nothing was executed) and the step runs eagerly instead.
+trd_status capture_step(trd_handle* h, const trd_params* p, int64_t* slots) {
+  Extra* x = X_(h);
+  drop_graph(x);
+  const size_t pend0 = x->pending.size();
+  bool ok = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+  trd_status st = ok ? step_device(h, p, slots) : TRD_ECUDA;
+  cudaGraph_t g = nullptr;
+  if (ok) ok = cudaStreamEndCapture(h->stream, &g) == cudaSuccess && st == TRD_OK && g;
+  if (ok) ok = cudaGraphInstantiate(&x->graph_exec, g, 0) == cudaSuccess;
+  if (ok) {
+    x->graph = g;
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    x->graph_kernels = 0;
+    std::vector<std::pair<cudaEvent_t, cudaGraphNode_t>> evn;
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess) continue;
+      if (ty == cudaGraphNodeTypeKernel) ++x->graph_kernels;
+      if (ty == cudaGraphNodeTypeEventRecord) {
+        cudaEvent_t ev = nullptr;
+        if (cudaGraphEventRecordNodeGetEvent(nd, &ev) == cudaSuccess) evn.push_back({ev, nd});
+      }
+    }
+    auto node_of = [&](cudaEvent_t ev) -> cudaGraphNode_t {
+      for (auto& q : evn)
+        if (q.first == ev) return q.second;
+      return nullptr;
+    };
+    for (size_t i = pend0; i < x->pending.size() && ok; ++i) {
+      const cudaGraphNode_t na = node_of(x->pending[i].a), nb = node_of(x->pending[i].b);
+      if (!na || !nb) ok = false;
+      else x->graph_ev.push_back({na, nb, x->pending[i].kind});
+    }
+  }
+  if (ok) ok = cudaGraphLaunch(x->graph_exec, h->stream) == cudaSuccess;
+  if (ok) {
+    x->graph_slots = *slots;
+    x->graph_ok = true;
+    return TRD_OK;
+  }
+  // abandon: nothing of this step ran
+  cudaGetLastError();
+  if (!x->graph && g) cudaGraphDestroy(g);
+  drop_graph(x);
+  for (size_t i = pend0; i < x->pending.size(); ++i) {
+    x->ev_pool.push_back(x->pending[i].a);
+    x->ev_pool.push_back(x->pending[i].b);
+  }
+  x->pending.resize(pend0);
+  x->tagSst.valid = x->tagSstr.valid = x->tagBst.valid = x->tagBstr.valid = false;
+  h->pass1_k = h->grad_k = h->gram_k = -1;
+  for (int k = 0; k < h->N; ++k) h->ver[k]++;
+  x->graphs_enabled = false;
+  h->err.clear();
+  return step_device(h, p, slots);
+}
+
+// Replay the captured step; with tracing level 1 every replay records its data-pass
+// intervals on fresh events.
+trd_status replay_step(trd_handle* h) {
+  Extra* x = X_(h);
+  for (const auto& q : x->graph_ev) {
+    cudaEvent_t a = pool_event(x), b = pool_event(x);
+    if (!a || !b ||
+        cudaGraphExecEventRecordNodeSetEvent(x->graph_exec, q.a, a) != cudaSuccess ||
+        cudaGraphExecEventRecordNodeSetEvent(x->graph_exec, q.b, b) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(h, TRD_ECUDA, "graph event update failed");
+    }
+    x->pending.push_back({a, b, q.kind});
+  }
+  CK(cudaGraphLaunch(x->graph_exec, h->stream), "graph launch");
+  note_launches(x->graph_kernels);
+  after_replay(h);
+  return TRD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+trd_status trd_step(trd_t* h, const trd_params* p, trd_report* rep) {
+  TRY(check_handle(h));
+  if (!p) return set_err(h, TRD_EINVAL, "NULL params");
+  if (!h->X) return set_err(h, TRD_EINVAL, "no data attached");
+  if (p->gram < TRD_GRAM_GLOBAL || p->gram > TRD_GRAM_NONE) return set_err(h, TRD_EINVAL, "bad gram kind");
+  const int N = h->N;
+  Extra* x = X_(h);
+  if (!h->have_D0) {
+    touch(h);
+    TRY(reset_D0(h));
+  }
+  bool any_sketch = false;
+  for (int m = 0; m < N; ++m)
+    if (p->sketch[m] > 0 && p->sketch[m] < h->I[m]) any_sketch = true;
+  Extra::GraphKey key;
+  key.sigma = p->sigma > 0 ? p->sigma : -1.0;
+  key.lambda = p->lambda;
+  key.gram = p->gram;
+  key.prof = x->prof;
+  // graphs: unsketched steps (a sketch is drawn on the host every step), tracing level <= 1
+  const bool graphable = x->graphs_enabled && !any_sketch && !h->sketched && x->prof <= 1 && h->t > 0;
+  int64_t slots = 0;
+  if (graphable && x->graph_ok && x->gkey == key) {
+    TRY(replay_step(h));
+    slots = x->graph_slots;
+  } else {
+    if (x->graph_ok || x->graph) drop_graph(x);
+    const bool same = x->gkey == key;
+    if (graphable && same && x->steady >= 1) {
+      TRY(capture_step(h, p, &slots));
+    } else {
+      TRY(step_device(h, p, &slots));
+    }
+    x->steady = graphable ? (same ? x->steady + 1 : 1) : 0;
+    x->gkey = key;
+  }
   CK(cudaMemcpyAsync(h->host_pinned, h->report_dev, sizeof(double) * 32, cudaMemcpyDeviceToHost, h->stream),
      "report");
   trd_status st = sync_and_status(h);
@@ -1370,6 +1557,7 @@ trd_status trd_recovery_error(trd_t* h, const float* ref, double* err) {
 
 trd_status trd_set_profiling(trd_t* h, int on) {
   TRY(check_handle(h));
+  touch(h);
   if (on < 0 || on > 2) return set_err(h, TRD_EINVAL, "profiling level must be 0, 1 or 2");
   X_(h)->prof = on;
   return TRD_OK;
@@ -1393,6 +1581,13 @@ trd_status trd_get_profile(trd_t* h, int reset, double* out) {
 }
 
 int64_t trd_kernel_launches(void) { return launches_total(); }
+
+trd_status trd_set_graphs(trd_t* h, int on) {
+  TRY(check_handle(h));
+  touch(h);
+  X_(h)->graphs_enabled = on != 0;
+  return TRD_OK;
+}
 
 trd_status trd_wait_selftest(trd_t* h, int arrive, int64_t limit) {
   TRY(check_handle(h));
@@ -1440,6 +1635,7 @@ static trd_status sampled_setup(trd_t* h, const void* const* cores_dev, int fp64
 trd_status trd_sampled_fwd(trd_t* h, const void* const* cores_dev, const int32_t* idx_dev, const void* x_dev,
                            int64_t M, double sigma, int fp64, void* resid_dev, double* loss_out) {
   TRY(check_handle(h));
+  touch(h);
   if (!cores_dev || !idx_dev || !x_dev || M < 1 || !loss_out || !(sigma > 0) || !isfinite(sigma))
     return set_err(h, TRD_EINVAL, "bad arguments");
   Extra* x = X_(h);
@@ -1465,6 +1661,7 @@ trd_status trd_sampled_fwd(trd_t* h, const void* const* cores_dev, const int32_t
 trd_status trd_sampled_bwd(trd_t* h, const void* const* cores_dev, const int32_t* idx_dev, const void* x_dev,
                            int64_t M, double sigma, int fp64, double g_scale, void* const* grad_dev) {
   TRY(check_handle(h));
+  touch(h);
   if (!cores_dev || !idx_dev || !x_dev || M < 1 || !grad_dev || !(sigma > 0) || !isfinite(sigma))
     return set_err(h, TRD_EINVAL, "bad arguments");
   for (int k = 0; k < h->N; ++k)

@@ -138,16 +138,15 @@ cudaError_t launch_phi(const double* T, int p, int q, double* G, cudaStream_t st
 //  * per column: update (one FMA per active element, the next pivot column first), publish
 //    the next column, one warp forms its reciprocal and scaled column, two barriers.
 
-// 1/p from the approximate FP32 reciprocal r0 and one step of the cubic iteration for the
-// reciprocal (Newton's iteration extended to third order):
-// with e = 1 - p r0, 1/p = r0 / (1 - e) = r0 (1 + e + e^2 + O(e^3)), and |e| <= 2^-22, so the
-// truncation error (~2^-66) is far below FP64 rounding.  Outside [1e-30, 1e30] (FP32 range
-// margins) the exact division is used.
+// 1/p from the hardware's approximate FP64 reciprocal r0 (rcp.approx.ftz.f64) and one step of
+// the cubic iteration for the reciprocal (Newton's iteration extended to third order): with
+// e = 1 - p r0, 1/p = r0 / (1 - e) = r0 (1 + e + e^2 + O(e^3)).  The seed's relative error is
+// far below 2^-18, so e^3 is below FP64 rounding.  Outside [1e-300, 1e300] the exact division
+// is used (flush-to-zero seed).
 __device__ __forceinline__ double recip_fp64(double p) {
-  if (!(p > 1e-30 && p < 1e30)) return 1.0 / p;
-  float rf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)p));   // relative error ~2^-23
-  const double r0 = (double)rf;
+  if (!(p > 1e-300 && p < 1e300)) return 1.0 / p;
+  double r0;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(p));
   const double e = fma(-p, r0, 1.0);
   return fma(r0, fma(e, e, e), r0);
 }
@@ -227,26 +226,29 @@ __global__ void __launch_bounds__(LDL_NT, 1)
     // active elements (columns > j) are the first nact of the order; a slot whose whole warp
     // lies beyond them is skipped (warp-uniform), so no FP64 instruction is spent on it.
     // Loads first, then the independent FMAs, then the publication of column j + 1.
+    // The warp's active slots are a prefix s < s_end; the loops leave by a (warp-uniform)
+    // branch so that no FP64 instruction is even issued for a retired slot.
     const int nact = (K - 1 - j) * (K - j) / 2;
+    const int s_end = nact > wbase ? imin(S, (nact - wbase + LDL_NT - 1) / LDL_NT) : 0;
     double li[S], cm[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      li[s] = 0.0;
-      cm[s] = 0.0;
-      if (s * LDL_NT + wbase < nact) {
-        const int i = (int)(im[s] & 0xFFFFu), m = (int)(im[s] >> 16);
-        if (m > j) {
-          li[s] = lj[i];
-          cm[s] = cj[m];
-        }
-      }
+      if (s >= s_end) break;
+      const int i = (int)(im[s] & 0xFFFFu), m = (int)(im[s] >> 16);
+      const bool act = m > j;
+      li[s] = act ? lj[i] : 0.0;
+      cm[s] = act ? cj[m] : 0.0;
     }
 #pragma unroll
-    for (int s = 0; s < S; ++s)
-      if (s * LDL_NT + wbase < nact) w[s] = fma(-li[s], cm[s], w[s]);
+    for (int s = 0; s < S; ++s) {
+      if (s >= s_end) break;
+      w[s] = fma(-li[s], cm[s], w[s]);
+    }
 #pragma unroll
-    for (int s = 0; s < S; ++s)
-      if (s * LDL_NT + wbase < nact && (int)(im[s] >> 16) == j + 1) cn[im[s] & 0xFFFFu] = w[s];
+    for (int s = 0; s < S; ++s) {
+      if (s >= s_end) break;
+      if ((int)(im[s] >> 16) == j + 1) cn[im[s] & 0xFFFFu] = w[s];
+    }
     __syncthreads();
     if (warp == 0) ldl_pivot(j + 1, K, cn, s_l[(j + 1) & 1], Lcm, Dinv, &s_bad, lane);
     __syncthreads();

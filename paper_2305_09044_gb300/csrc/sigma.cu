@@ -38,11 +38,13 @@ constexpr uint64_t kExcluded = ~0ull;
 //   u[8..11]  remaining rank of each of the four target order statistics
 //   u[12..15] key prefix selected so far for each target
 //   u[16..23] completion counter of each kernel of the chain
+//   u[24]     number of candidates appended by the compaction
 //   word 64:  uint32 histograms [8 digits][4 targets][256]
 //   word 64 + 4096: per-block partial sums [kSelBlocks][4] (count, sum e, sum x^2, sum (e-mean)^2)
 // The chain is: clear (memset) -> first kernel (residual keys, sums, digit-0 histogram) ->
-// seven digit kernels.  The last block of every kernel (completion counter) turns the complete
-// histogram into the next digit of each target; the last one also evaluates sigma.
+// digit 1 -> digit 2 (the last block of each kernel, found by a completion counter, turns the
+// complete histogram into the next digit of each target) -> compaction of the keys still
+// matching a target's 24-bit prefix -> one block for digits 3..7 and sigma.
 constexpr int kSelBlocks = 1216;
 constexpr int kSelThreads = 256;
 constexpr int kHistWord = 64;
@@ -228,14 +230,13 @@ __device__ void sel_sigma(const double* work, double rms_override, double sigma_
   *sigma_out = s;
 }
 
-// Digit d (1..7) of the four targets: histogram of the keys that match each target's prefix
-// (digit 1 also accumulates sum (e - mean)^2); the last block picks the digit, and after
-// digit 7 evaluates sigma.
+// Digit d (1 or 2) of the four targets: histogram of the keys that match each target's
+// prefix (digit 1 also accumulates sum (e - mean)^2); the last block picks the digit.  Each
+// warp takes chunks of 32 x kSelBatch consecutive keys, all loads issued before use.
+constexpr int kSelBatch = 8;
+
 __global__ void __launch_bounds__(kSelThreads) k_sel_digit(const uint64_t* __restrict__ keys, int64_t n,
-                                                           double* __restrict__ work, int digit,
-                                                           double rms_override, double sigma_prev,
-                                                           const double* __restrict__ sigma_prev_dev,
-                                                           double* __restrict__ sigma_out) {
+                                                           double* __restrict__ work, int digit) {
   __shared__ unsigned int h[4][256];
   for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&h[0][0])[i] = 0;
   const uint64_t* u = reinterpret_cast<const uint64_t*>(work);
@@ -249,25 +250,35 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_digit(const uint64_t* __res
   const uint64_t himask = ~0ull << (shift + 8);
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
   double s2 = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t m0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); m0 < n; m0 += stride) {
-    const int64_t m = m0 + lane;
-    const uint64_t k = m < n ? keys[m] : kExcluded;
-    const bool valid = k != kExcluded;
-    if (digit == 1 && valid) {
-      const double d = dval(k) - mean;
-      s2 = fma(d, d, s2);
-    }
-    const unsigned dig = (unsigned)((k >> shift) & 0xffu);
+  const int64_t chunk = 32 * kSelBatch;
+  for (int64_t c0 = ((int64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * chunk; c0 < n;
+       c0 += (int64_t)gridDim.x * wpb * chunk) {
+    uint64_t kb[kSelBatch];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      if (alias[t] != t) continue;                    // uniform across the block
-      const bool hit = valid && (k & himask) == pre[t];
-      const unsigned act = __ballot_sync(0xffffffffu, hit);
-      if (hit) {
-        const unsigned peers = __match_any_sync(act, dig);
-        if (lane == __ffs(peers) - 1) atomicAdd(&h[t][dig], (unsigned)__popc(peers));
+    for (int q = 0; q < kSelBatch; ++q) {
+      const int64_t m = c0 + q * 32 + lane;
+      kb[q] = m < n ? keys[m] : kExcluded;
+    }
+#pragma unroll
+    for (int q = 0; q < kSelBatch; ++q) {
+      const uint64_t k = kb[q];
+      const bool valid = k != kExcluded;
+      if (digit == 1 && valid) {
+        const double d = dval(k) - mean;
+        s2 = fma(d, d, s2);
+      }
+      const unsigned dig = (unsigned)((k >> shift) & 0xffu);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (alias[t] != t) continue;                    // uniform across the block
+        const bool hit = valid && (k & himask) == pre[t];
+        const unsigned act = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const unsigned peers = __match_any_sync(act, dig);
+          if (lane == __ffs(peers) - 1) atomicAdd(&h[t][dig], (unsigned)__popc(peers));
+        }
       }
     }
   }
@@ -300,7 +311,124 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_digit(const uint64_t* __res
     __syncthreads();
   }
   sel_pick(work, digit);
-  if (digit == 7 && threadIdx.x == 0) sel_sigma(work, rms_override, sigma_prev, sigma_prev_dev, sigma_out);
+}
+
+// After three digits: the keys that still match a target's 24-bit prefix (a small fraction)
+// are appended to cand[] (warp-aggregated atomic count in u[24]; their order is irrelevant).
+__global__ void __launch_bounds__(kSelThreads) k_sel_compact(const uint64_t* __restrict__ keys, int64_t n,
+                                                             double* __restrict__ work, uint64_t* __restrict__ cand) {
+  uint64_t* u = reinterpret_cast<uint64_t*>(work);
+  uint64_t pre[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) pre[t] = __ldcg(u + 12 + t);
+  const uint64_t himask = ~0ull << 40;
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  const int64_t chunk = 32 * kSelBatch;
+  for (int64_t c0 = ((int64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * chunk; c0 < n;
+       c0 += (int64_t)gridDim.x * wpb * chunk) {
+    uint64_t kb[kSelBatch];
+#pragma unroll
+    for (int q = 0; q < kSelBatch; ++q) {
+      const int64_t m = c0 + q * 32 + lane;
+      kb[q] = m < n ? keys[m] : kExcluded;
+    }
+#pragma unroll
+    for (int q = 0; q < kSelBatch; ++q) {
+      const uint64_t k = kb[q];
+      const uint64_t hk = k & himask;
+      const bool hit = k != kExcluded && (hk == pre[0] || hk == pre[1] || hk == pre[2] || hk == pre[3]);
+      const unsigned act = __ballot_sync(0xffffffffu, hit);
+      if (act) {
+        unsigned long long base = 0;
+        if (lane == __ffs(act) - 1) base = atomicAdd(reinterpret_cast<unsigned long long*>(u + 24), (unsigned long long)__popc(act));
+        base = __shfl_sync(0xffffffffu, base, __ffs(act) - 1);
+        if (hit) cand[base + __popc(act & ((1u << lane) - 1u))] = k;
+      }
+    }
+  }
+}
+
+// One block: digits 3..7 over the candidates (shared-memory histograms), then sigma.
+constexpr int kFinThreads = 1024;
+__global__ void __launch_bounds__(kFinThreads) k_sel_finish(const uint64_t* __restrict__ cand, double* __restrict__ work,
+                                                            double rms_override, double sigma_prev,
+                                                            const double* __restrict__ sigma_prev_dev,
+                                                            double* __restrict__ sigma_out) {
+  __shared__ unsigned int h[4][256];
+  __shared__ uint64_t s_pre[4], s_rank[4];
+  uint64_t* u = reinterpret_cast<uint64_t*>(work);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < 4) {
+    s_pre[tid] = __ldcg(u + 12 + tid);
+    s_rank[tid] = __ldcg(u + 8 + tid);
+  }
+  const int64_t cnt = (int64_t)__ldcg(u + 24);
+  __syncthreads();
+  for (int digit = 3; digit < 8; ++digit) {
+    for (int i = tid; i < 1024; i += blockDim.x) (&h[0][0])[i] = 0;
+    uint64_t pre[4];
+    int alias[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) pre[t] = s_pre[t];
+    sel_alias(pre, alias);
+    const int shift = 56 - 8 * digit;
+    const uint64_t himask = ~0ull << (shift + 8);
+    __syncthreads();
+    for (int64_t c0 = (int64_t)warp * 32; c0 < cnt; c0 += blockDim.x) {
+      const int64_t c = c0 + lane;
+      const uint64_t k = c < cnt ? __ldcg(cand + c) : kExcluded;
+      const bool valid = k != kExcluded;
+      const unsigned dig = (unsigned)((k >> shift) & 0xffu);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (alias[t] != t) continue;
+        const bool hit = valid && (k & himask) == pre[t];
+        const unsigned act = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const unsigned peers = __match_any_sync(act, dig);
+          if (lane == __ffs(peers) - 1) atomicAdd(&h[t][dig], (unsigned)__popc(peers));
+        }
+      }
+    }
+    __syncthreads();
+    if (warp < 4) {
+      const int t = warp;
+      const unsigned int* ht = h[alias[t]];
+      const uint64_t rank = s_rank[t];
+      unsigned int cb[8];
+      unsigned long long loc = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        cb[i] = ht[lane * 8 + i];
+        loc += cb[i];
+      }
+      unsigned long long incl = loc;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const unsigned long long excl = incl - loc;
+      if (rank >= excl && rank < incl) {
+        unsigned long long cum = excl;
+        int bin = lane * 8 + 7;
+        for (int i = 0; i < 8; ++i) {
+          if (cum + cb[i] > rank) { bin = lane * 8 + i; break; }
+          cum += cb[i];
+        }
+        s_rank[t] = rank - cum;
+        s_pre[t] = pre[t] | ((uint64_t)bin << shift);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int t = 0; t < 4; ++t) {
+      u[8 + t] = s_rank[t];
+      u[12 + t] = s_pre[t];
+    }
+    sel_sigma(work, rms_override, sigma_prev, sigma_prev_dev, sigma_out);
+  }
 }
 
 // First kernel on given residuals (floats): keys, sums, digit-0 histogram.
@@ -325,7 +453,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_floats(const float* __restr
 // of the full tensor, x_hat = sum_kappa A[a][kappa] C[b][kappa] (Thm. 1 with the ring cut in two).
 // Eight lanes per probe (each a strided part of the length-Kp dot product, then a 3-step
 // shuffle sum); probe m is described by pa[m] (inner index, -1 when unobserved), pb[m] and px[m].
-template <typename T>
+template <typename T, bool VEC4>
 __global__ void __launch_bounds__(kSelThreads)
     k_sel_probe(const T* __restrict__ A, const T* __restrict__ C, int Kp, const int32_t* __restrict__ pa,
                 const int32_t* __restrict__ pb, const float* __restrict__ px, int64_t n,
@@ -346,15 +474,21 @@ __global__ void __launch_bounds__(kSelThreads)
     if (obs) {
       const T* Ar = A + (int64_t)a * Kp;
       const T* Cr = C + (int64_t)pb[m] * Kp;
-      // independent loads in flight (up to Kp = 256), two accumulators
-      T p2 = T(0);
-#pragma unroll
-      for (int q = 0; q < 32; q += 2) {
-        const int k0 = sub + 8 * q, k1 = k0 + 8;
-        if (k0 < Kp) part = fma(Ar[k0], Cr[k0], part);
-        if (k1 < Kp) p2 = fma(Ar[k1], Cr[k1], p2);
+      if constexpr (VEC4) {
+        // 16-byte loads (Kp a multiple of 4): lane sub takes float4 chunks sub, sub + 8, ...
+        const float4* A4 = reinterpret_cast<const float4*>(Ar);
+        const float4* C4 = reinterpret_cast<const float4*>(Cr);
+        for (int v = sub; v < (Kp >> 2); v += 8) {
+          const float4 x = A4[v], y = C4[v];
+          part = fma(x.x, y.x, part);
+          part = fma(x.y, y.y, part);
+          part = fma(x.z, y.z, part);
+          part = fma(x.w, y.w, part);
+        }
+      } else {
+#pragma unroll 4
+        for (int k = sub; k < Kp; k += 8) part = fma(Ar[k], Cr[k], part);
       }
-      part += p2;
     }
     part += __shfl_xor_sync(0xffffffffu, part, 4);
     part += __shfl_xor_sync(0xffffffffu, part, 2);
@@ -390,12 +524,17 @@ __global__ void k_probe_setup(const float* __restrict__ X, const uint32_t* __res
   }
 }
 
-cudaError_t run_digits(const uint64_t* keys, int64_t n, double* work, int nb, double rms_override, double sigma_prev,
-                       const double* sigma_prev_dev, double* sigma_out, cudaStream_t st) {
-  for (int d = 1; d < 8; ++d) {
-    k_sel_digit<<<nb, kSelThreads, 0, st>>>(keys, n, work, d, rms_override, sigma_prev, sigma_prev_dev, sigma_out);
-    note_launch();
-  }
+cudaError_t run_digits(const uint64_t* keys, int64_t n, double* work, uint64_t* cand, double rms_override,
+                       double sigma_prev, const double* sigma_prev_dev, double* sigma_out, cudaStream_t st) {
+  const int nb = (int)imax(1, imin(kSelBlocks, (n + 32 * kSelBatch * 8 - 1) / (32 * kSelBatch * 8)));
+  k_sel_digit<<<nb, kSelThreads, 0, st>>>(keys, n, work, 1);
+  note_launch();
+  k_sel_digit<<<nb, kSelThreads, 0, st>>>(keys, n, work, 2);
+  note_launch();
+  k_sel_compact<<<nb, kSelThreads, 0, st>>>(keys, n, work, cand);
+  note_launch();
+  k_sel_finish<<<1, kFinThreads, 0, st>>>(cand, work, rms_override, sigma_prev, sigma_prev_dev, sigma_out);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -425,24 +564,29 @@ cudaError_t launch_probe_setup(const float* X, const uint32_t* M, const int64_t*
 
 cudaError_t launch_probe_sigma_merged(const void* A, const void* C, bool fp64, int Kp, const int32_t* pa,
                                       const int32_t* pb, const float* px, int64_t n, double sigma_prev,
-                                      const double* sigma_prev_dev, uint64_t* keys, double* work,
+                                      const double* sigma_prev_dev, uint64_t* keys, uint64_t* cand, double* work,
                                       double* sigma_out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(double) * kPartsWord, st);
   if (e != cudaSuccess) return e;
   // eight lanes per probe, about four probes per lane group
   const int nb = (int)imax(1, imin(kSelBlocks, (n * 8 + 4 * kSelThreads - 1) / (4 * kSelThreads)));
   if (fp64)
-    k_sel_probe<double><<<nb, kSelThreads, 0, st>>>((const double*)A, (const double*)C, Kp, pa, pb, px, n, keys, work);
+    k_sel_probe<double, false><<<nb, kSelThreads, 0, st>>>((const double*)A, (const double*)C, Kp, pa, pb, px, n,
+                                                           keys, work);
+  else if (Kp % 4 == 0)
+    k_sel_probe<float, true><<<nb, kSelThreads, 0, st>>>((const float*)A, (const float*)C, Kp, pa, pb, px, n, keys,
+                                                         work);
   else
-    k_sel_probe<float><<<nb, kSelThreads, 0, st>>>((const float*)A, (const float*)C, Kp, pa, pb, px, n, keys, work);
+    k_sel_probe<float, false><<<nb, kSelThreads, 0, st>>>((const float*)A, (const float*)C, Kp, pa, pb, px, n,
+                                                          keys, work);
   note_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return run_digits(keys, n, work, sel_blocks(n), -1.0, sigma_prev, sigma_prev_dev, sigma_out, st);
+  return run_digits(keys, n, work, cand, -1.0, sigma_prev, sigma_prev_dev, sigma_out, st);
 }
 
 cudaError_t launch_sigma_from_floats(const float* r, int64_t n, double x_obs_rms, double sigma_prev, uint64_t* keys,
-                                     double* work, double* sigma_out, cudaStream_t st) {
+                                     uint64_t* cand, double* work, double* sigma_out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(double) * kPartsWord, st);
   if (e != cudaSuccess) return e;
   const int nb = sel_blocks(n);
@@ -450,17 +594,17 @@ cudaError_t launch_sigma_from_floats(const float* r, int64_t n, double x_obs_rms
   note_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return run_digits(keys, n, work, nb, x_obs_rms, sigma_prev, nullptr, sigma_out, st);
+  return run_digits(keys, n, work, cand, x_obs_rms, sigma_prev, nullptr, sigma_out, st);
 }
 
 // ------------------------------------------------------------------ allocation-free variant
 // Fixed scratch for trd_sigma_from_residuals_noalloc: room for the order keys of NOALLOC_MAX
-// residuals (8 bytes each) plus the selection work area.  It is a file-scope device array, so
-// every GPU that loads the library holds it (about 8.4 MB) until the process exits; all calls
-// share it.
+// residuals and as many selection candidates (8 bytes each) plus the selection work area.
+// It is a file-scope device array, so every GPU that loads the library holds it (about
+// 16.8 MB) until the process exits; all calls share it.
 constexpr int64_t NOALLOC_MAX = int64_t(1) << 20;
 constexpr size_t NOALLOC_WORK = kPartsWord + kSelBlocks * 4;   // doubles; equals sigma_work_doubles()
-static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_MAX * 8 + NOALLOC_WORK * 8];
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_MAX * 16 + NOALLOC_WORK * 8];
 
 namespace {
 constexpr int NOALLOC_DEVICES = 64;
@@ -498,11 +642,12 @@ extern "C" trd_status trd_sigma_from_residuals_noalloc(const float* resid_dev, i
   }
   unsigned char* b = static_cast<unsigned char*>(base);
   uint64_t* keys = reinterpret_cast<uint64_t*>(b);
-  double* work = reinterpret_cast<double*>(b + NOALLOC_MAX * 8);
+  uint64_t* cand = reinterpret_cast<uint64_t*>(b + NOALLOC_MAX * 8);
+  double* work = reinterpret_cast<double*>(b + NOALLOC_MAX * 16);
   // every scratch word the selection reads is written first in this call (the counters and
   // histograms are cleared at its start), so stale contents do not leak in
-  const cudaError_t e = launch_sigma_from_floats(resid_dev, n, x_obs_rms, sigma_prev, keys, work, sigma_out_dev,
-                                                 (cudaStream_t)cuda_stream);
+  const cudaError_t e = launch_sigma_from_floats(resid_dev, n, x_obs_rms, sigma_prev, keys, cand, work,
+                                                 sigma_out_dev, (cudaStream_t)cuda_stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return TRD_ECUDA;

@@ -154,6 +154,7 @@ namespace trd {
 // ------------------------------------------------------------------ launch accounting
 // Every kernel launch in the library bumps this counter (read by trd_kernel_launches).
 void note_launch();
+void note_launches(int64_t n);
 int64_t launches_total();
 
 // ------------------------------------------------------------------ host helpers (api)
@@ -240,12 +241,13 @@ size_t sigma_work_doubles();
 void probe_positions(int64_t numel, std::vector<int64_t>& lin);
 cudaError_t launch_probe_setup(const float* X, const uint32_t* M, const int64_t* lin_dev, int64_t n, int64_t P_in,
                                int32_t* pa, int32_t* pb, float* px, cudaStream_t st);
+// keys and cand: n 64-bit words each (order keys, selection candidates)
 cudaError_t launch_probe_sigma_merged(const void* A, const void* C, bool fp64, int Kp, const int32_t* pa,
                                       const int32_t* pb, const float* px, int64_t n, double sigma_prev,
-                                      const double* sigma_prev_dev, uint64_t* keys, double* work,
+                                      const double* sigma_prev_dev, uint64_t* keys, uint64_t* cand, double* work,
                                       double* sigma_out, cudaStream_t st);
 cudaError_t launch_sigma_from_floats(const float* r, int64_t n, double x_obs_rms, double sigma_prev, uint64_t* keys,
-                                     double* work, double* sigma_out, cudaStream_t st);
+                                     uint64_t* cand, double* work, double* sigma_out, cudaStream_t st);
 
 // sampled.cu
 // Strides of each mode inside the inner (a) / outer (b) block of a two-block cut (0 if the mode
