@@ -293,6 +293,7 @@ def run_ours(args, rank, world, local):
            "roofline": roofline(prec, prof, w), "e2e": e2e, "gpu_launches": launches, "clocks": ck}
     if rank == 0 and not args.no_converge:
         out["time_to_rel_err_1e-3"] = converge(t, Xt, w, args.converge_iters, torch)
+    out["row_sampling"] = row_sampling(t, w, torch)
 
     # comparison path on the same device data (FP32 CUDA-core passes)
     for other in precs[1:]:
@@ -313,6 +314,37 @@ def run_ours(args, rank, world, local):
     t.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def row_sampling(t, w, torch, J=1 << 16, updates=8):
+    """The uniform-row-sampling variant (the paper's ablation): per core update, J rows of the
+    subchain unfolding drawn i.i.d. uniformly (numpy, seeded), the fibres gathered, then the
+    residual / gradient / scaled-step / line-search path on them.  Device time of the whole
+    update (gather included) with CUDA events; the host draw and index upload are outside."""
+    rng = np.random.default_rng(w.sample_seed + 17)
+    N = len(w.dims)
+    stream = t.stream
+    total, slots = 0.0, 0
+    for q in range(updates + 2):
+        k = q % N
+        rows = np.stack([rng.integers(0, w.dims[m], J) if m != k else np.zeros(J, dtype=np.int64)
+                         for m in range(N)], axis=1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        t.sample_rows(k, rows)
+        t.residual_weights(k, 2.0)
+        t.core_gradient(k)
+        t.core_update(k, -1e-10)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if q >= 2:                       # two warm-up updates
+            total += a.elapsed_time(b)
+            slots += w.dims[k] * J
+    t.sample_subtensor(0, None)
+    return {"value": slots / (total / 1e3), "unit": UNIT, "rows_per_update": J, "updates": updates,
+            "ms_per_update": total / updates, "note": "one core update per timed interval (sample gather, "
+            "both data passes, gradient, FGMC Gram, LDL^T solve, line search); sigma fixed at 2"}
 
 
 def converge(t, Xt, w, iters, torch):

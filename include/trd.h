@@ -164,6 +164,17 @@ trd_status trd_sample_subtensor(trd_t* handle, int k, const int32_t* const* idx,
 trd_status trd_draw_indices(uint64_t seed, int32_t t, int k, int j, int N, int64_t I,
                             int32_t s, int32_t* out);
 
+/* Uniform row sampling (the paper's 'uniform row sampling' ablation, Sec. 5): instead of
+ * the RStS sketch, the update of core k uses J sampled rows of Z^{!=k}_[2], i.e. the
+ * multi-indices rows[j * N + m] (HOST, J x N int32, row-major; column k is ignored; each
+ * 0 <= rows[j N + m] < I_m; duplicates allowed), and the matching columns of X_[k] and P_[k]
+ * (the J fibres along mode k, gathered here).  The next trd_residual_weights /
+ * trd_core_gradient / trd_core_update for core k work on this sample (gradient of Eq. hatd
+ * with the sampled rows; FGMC Gram of the full cores; line search on the sample); any other
+ * sampling call or trd_step ends it.  TRD_EINVAL for an index out of range;
+ * TRD_ENOTIMPL for the local Gram on this sample. */
+trd_status trd_sample_rows(trd_t* handle, int k, const int32_t* rows, int64_t J);
+
 /* Steps 'update W' and the first half of 'compute d' for core k on the current sketch:
  * reconstruct X_hat_I[k] = Z_{k(2)} (Z^{!=k}_{I[2]})^T (Thm. 1), residual e = x - x_hat on
  * observed slots, HQ weight w = exp(-e^2/(2 sigma^2)) (Eq. updatew, sign reading) and the

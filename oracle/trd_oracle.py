@@ -181,6 +181,27 @@ def reconstruct_unfold(cores: Sequence[np.ndarray]) -> np.ndarray:
     return X1.reshape([Z.shape[1] for Z in cores], order="F")
 
 
+def reconstruct_chunks(cores: Sequence[np.ndarray], c: int, cols: int):
+    """Def. 1 for tensors too large to form a subchain of N - 1 cores: cut the ring after
+    core c, merge both halves (Def. 2), A = Z^{(1..c)} of shape (r_1, P_in, r_{c+1}) and
+    C = Z^{(c+1..N)} of shape (r_{c+1}, P_out, r_1); then X(a + P_in b) = Tr(A(a) C(b)) =
+    sum_{x,z} A[x, a, z] C[z, b, x].  Yields (start, values) for consecutive column blocks
+    of `cols` outer indices b, in linear (i_1 fastest) order."""
+    A = cores[0]
+    for Z in cores[1:c]:
+        A = merge(A, Z)
+    C = cores[c]
+    for Z in cores[c + 1:]:
+        C = merge(C, Z)
+    r1, P_in, rc = A.shape
+    P_out = C.shape[1]
+    Ahat = A.transpose(1, 0, 2).reshape(P_in, r1 * rc)          # [a, x rc + z]
+    for b0 in range(0, P_out, cols):
+        b1 = min(P_out, b0 + cols)
+        Chat = C[:, b0:b1, :].transpose(1, 2, 0).reshape(b1 - b0, r1 * rc)   # [b, x rc + z]
+        yield b0 * P_in, (Ahat @ Chat.T).reshape(-1, order="F")
+
+
 def entry(cores: Sequence[np.ndarray], idx: Sequence[int]) -> float:
     """Def. 1 for one entry, by explicit matrix products."""
     M = np.eye(cores[0].shape[0])
@@ -368,6 +389,85 @@ def core_update(X: np.ndarray, P: np.ndarray, cores: List[np.ndarray], k: int, s
                     lam=lam_used, sum_w=float(np.sum(W[obs])),
                     sum_e2=float(np.sum(E[obs] ** 2)), n_obs=int(obs.sum()),
                     objective=float(0.5 * np.sum(W * Pk * E * E)))
+
+
+def sampled_rows(cores: Sequence[np.ndarray], k: int, rows: np.ndarray) -> np.ndarray:
+    """Rows of Z^{!=k}_[2] at the multi-indices `rows` (J x N integer array, column k
+    ignored): S(j) = Z_{k+1}(i_{k+1}) ... Z_N(i_N) Z_1(i_1) ... Z_{k-1}(i_{k-1}) (Thm. 1
+    order), unfolded as in cyclic_unfold2: B[j, a + b r_k] = S(j)[b, a].  Shape J x K."""
+    N = len(cores)
+    order = [(k + 1 + m) % N for m in range(N - 1)]
+    S = cores[order[0]][:, rows[:, order[0]], :]                       # (r_{k+1}, J, .)
+    for m in order[1:]:
+        S = np.einsum("ajb,bjc->ajc", S, cores[m][:, rows[:, m], :])   # slice products per j
+    return cyclic_unfold2(S)
+
+
+def row_fibres(X: np.ndarray, k: int, rows: np.ndarray) -> np.ndarray:
+    """Columns of X_[k] at the sampled multi-indices: F[i, j] = X(rows[j] with i_k = i)."""
+    idx = tuple(rows[:, m] for m in range(X.ndim))
+    out = np.empty((X.shape[k], rows.shape[0]), dtype=np.float64)
+    for i in range(X.shape[k]):
+        full = list(idx)
+        full[k] = np.full(rows.shape[0], i)
+        out[i] = X[tuple(full)]
+    return out
+
+
+def core_update_rows(X: np.ndarray, P: np.ndarray, cores: List[np.ndarray], k: int, sigma: float,
+                     rows: np.ndarray, lam: float = -1e-10, eta: Optional[float] = None,
+                     gram: str = "global") -> CoreStep:
+    """Ablation 'uniform row sampling' (Sec. 5, ablation experiments): Z^{!=k}_{I[2]} is a set
+    of sampled rows of Z^{!=k}_[2] (the multi-indices `rows`, J x N, column k ignored)
+    instead of the RStS sketch; X_{I[k]} and P_{I[k]} are the matching columns of X_[k] and
+    P_[k].  Every other step as in core_update (Eq. updatew, Eq. hatd, Eq. hI, line search)."""
+    rk, rk1 = cores[k].shape[0], cores[k].shape[2]
+    B = sampled_rows(cores, k, rows)                           # Z^{!=k}_{I[2]}
+    Xk = row_fibres(X, k, rows)                                # X_{I[k]}
+    Pk = row_fibres(P.astype(np.float64), k, rows)
+    Zk2 = mode2(cores[k])
+    E = Xk - Zk2 @ B.T                                         # Thm. 1
+    W = hq_weight(E, sigma)                                    # Eq. updatew
+    d = (W * Pk * E) @ B                                       # Eq. hatd
+    if gram == "global":
+        G = fgmc_gram(cores, k)
+    elif gram == "local":
+        G = B.T @ B
+    elif gram == "none":
+        G = None
+    else:
+        raise ValueError(gram)
+    if G is None:
+        lam_used, h = 0.0, d.copy()
+    else:
+        lam_used = resolve_lambda(lam, G)
+        h = right_solve_spd(d, G + lam_used * np.eye(G.shape[0]))
+    num = float(np.sum(d * h))
+    HB = h @ B.T
+    den = float(np.sum(W * Pk * HB * HB))
+    eta_used = (num / den if den > 0 else 0.0) if eta is None else float(eta)
+    new = list(cores)
+    new[k] = fold2(Zk2 + eta_used * h, rk, rk1)
+    obs = Pk > 0
+    return CoreStep(cores=new, d=d, G=G, h=h, num=num, den=den, eta=eta_used, lam=lam_used,
+                    sum_w=float(np.sum(W[obs])), sum_e2=float(np.sum(E[obs] ** 2)),
+                    n_obs=int(obs.sum()), objective=float(0.5 * np.sum(W * Pk * E * E)))
+
+
+def draw_rows(seed: int, t: int, k: int, dims: Sequence[int], J: int) -> np.ndarray:
+    """J multi-indices drawn i.i.d. uniformly (with replacement) for core update k of
+    iteration t: entry m of row j is z mod I_m with z = output (j (N + 1) + m) of the
+    SplitMix64 stream keyed by output (t N + k) N + N of the seed's stream (the RStS keys use
+    outputs (t N + k) N + j, j < N); column k is 0."""
+    N = len(dims)
+    key = splitmix64_mix((seed + ((t * N + k) * N + N + 1) * GOLDEN_GAMMA) & _M64)
+    z = splitmix64_stream(key, J * (N + 1))
+    out = np.zeros((J, N), dtype=np.int64)
+    for j in range(J):
+        for m in range(N):
+            if m != k:
+                out[j, m] = z[j * (N + 1) + m] % dims[m]
+    return out
 
 
 def weighted_objective(X, P, cores, W=None):

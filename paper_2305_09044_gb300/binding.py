@@ -36,7 +36,7 @@ EXPORTS = [
     "trd_sigma_from_residuals", "trd_reconstruct", "trd_reconstruct_from",
     "trd_recovery_error", "trd_sampled_fwd", "trd_sampled_bwd", "trd_set_profiling",
     "trd_get_profile", "trd_kernel_launches", "trd_sigma_from_residuals_noalloc",
-    "trd_wait_selftest", "trd_set_graphs",
+    "trd_wait_selftest", "trd_set_graphs", "trd_sample_rows",
 ]
 
 
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
         "trd_sigma_from_residuals_noalloc": [vp, i64, dbl, dbl, vp, vp],
         "trd_wait_selftest": [vp, C.c_int, i64],
         "trd_set_graphs": [vp, C.c_int],
+        "trd_sample_rows": [vp, C.c_int, P(i32), i64],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -246,6 +247,15 @@ class TRD:
                                         for m, a in enumerate(arrs)])
         self._keep = arrs
         self._check(self.lib.trd_sample_subtensor(self.h, k, ptrs, sizes), "trd_sample_subtensor")
+
+    def sample_rows(self, k: int, rows: np.ndarray):
+        """Uniform row sampling for core k: rows is a (J, N) integer array of multi-indices
+        (column k ignored); see trd_sample_rows."""
+        r = np.ascontiguousarray(np.asarray(rows, dtype=np.int32))
+        if r.ndim != 2 or r.shape[1] != self.N:
+            raise ValueError("rows must have shape (J, N)")
+        self._check(self.lib.trd_sample_rows(self.h, k, r.ctypes.data_as(C.POINTER(C.c_int32)), r.shape[0]),
+                    "trd_sample_rows")
 
     def residual_weights(self, k: int, sigma: float, raise_nonfinite: bool = True) -> dict:
         s = ResidStats()

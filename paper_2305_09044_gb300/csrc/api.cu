@@ -95,6 +95,12 @@ struct Extra {
   DevBuf probe_a, probe_b, probe_x;   // adaptive-width probe: inner / outer index, data
   DevBuf dotpart, solve_ctr;          // per-row parts of <d, h>, completion counter
   DevBuf probe_cand;                  // selection candidates of the adaptive width
+  // uniform row sampling (trd_sample_rows): J multi-indices of the modes other than row_k
+  bool row_view = false;
+  int row_k = -1;
+  int64_t rows_J = 0;
+  DevBuf rows_dev;
+  uint64_t rows_gen = ~0ull, rows_ver[kMaxN] = {};   // what h->Sst / h->Sstr hold
   // what the merged-half buffers hold (FP32/FP64 h->Sst / h->Sstr, BF16 operands bS* / bT*)
   HalfTag tagSst, tagSstr, tagBst, tagBstr;
   uint64_t view_gen = 0;    // 0 = the full tensor; every drawn sketch gets a new number
@@ -129,6 +135,13 @@ struct Extra {
       return sigma == o.sigma && lambda == o.lambda && gram == o.gram && prof == o.prof;
     }
   } gkey;
+  // FGMC Gram + LDL^T of core k on a side stream while the data pass of core k runs (they
+  // depend only on the other cores); the first pass then leaves kSideSMs SMs free
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int pre_k = -1;            // core whose factor is being prepared on the side stream
+  double pre_lambda = 0;
+  int reserve_sms = 0;       // SMs the next tensor-core pass leaves to the side stream
   bool graphs_enabled = true;
   bool graph_ok = false;
   int steady = 0;
@@ -226,6 +239,7 @@ void drop_graph(Extra* x) {
 void touch(trd_handle* h) {
   Extra* x = X_(h);
   x->steady = 0;
+  x->pre_k = -1;
   if (x->graph_ok || x->graph) drop_graph(x);
 }
 
@@ -413,11 +427,61 @@ HalfTag half_tag(trd_handle* h, int half, const Split& sp) {
   return t;
 }
 
+// Row sampling: the stationary operand is Z_{k(2)} itself (I_k x K), the streaming one the
+// sampled rows B (J x K); the contraction index is alpha + beta r_k on both sides.
+Split row_split(const trd_handle* h, int k, int64_t J) {
+  Split sp;
+  sp.c = 1;
+  sp.P_in = h->I[k];
+  sp.P_out = J;
+  sp.Kp = h->K[k];
+  sp.rows = true;
+  sp.P_stat = sp.P_in;
+  sp.P_strm = J;
+  return sp;
+}
+
+RowsArgs rows_args(const trd_handle* h, int k, int64_t J) {
+  RowsArgs a;
+  a.N = h->N;
+  a.k = k;
+  a.Ik = h->I[k];
+  a.J = J;
+  int64_t st = 1;
+  for (int m = 0; m < h->N; ++m) {
+    a.stride[m] = st;
+    st *= h->I[m];
+    a.R[m] = h->R[m];
+    a.Z[m] = h->Z[m];
+  }
+  return a;
+}
+
+trd_status build_rows_operands(trd_handle* h, int k) {
+  Extra* x = X_(h);
+  bool fresh = x->rows_gen == x->view_gen;
+  for (int m = 0; m < h->N && fresh; ++m) fresh = x->rows_ver[m] == h->ver[m];
+  if (fresh) return TRD_OK;
+  const int64_t J = x->rows_J;
+  const size_t e = elt(h);
+  TRY(ensure(h, h->Sst, e * h->I[k] * h->K[k]));
+  TRY(ensure(h, h->Sstr, e * J * h->K[k]));
+  // Z_{k(2)} is the core's own layout (row i, column alpha + beta r_k)
+  CK(launch_from_double(h->Z[k], h->I[k] * (int64_t)h->K[k], h->Sst.p, is_fp64(h), h->stream), "Z_k operand");
+  CK(launch_rows_chain(rows_args(h, k, J), (const int32_t*)x->rows_dev.p, h->Sstr.p, is_fp64(h), h->stream),
+     "sampled rows");
+  x->tagSst.valid = x->tagSstr.valid = x->tagBst.valid = x->tagBstr.valid = false;
+  x->rows_gen = x->view_gen;
+  for (int m = 0; m < h->N; ++m) x->rows_ver[m] = h->ver[m];
+  return TRD_OK;
+}
+
 // Merged halves of the current view into h->Sst (the stationary role: the half holding
 // core k) and h->Sstr.  The two buffers keep what they hold between calls: a half whose cores
 // and view are unchanged is not merged again (buffers trade roles when k crosses the cut).
 trd_status build_halves(trd_handle* h, int k) {
   Extra* x = X_(h);
+  if (x->row_view) return build_rows_operands(h, k);
   const Split& sp = h->split;
   const int hs = k < sp.c ? 0 : 1;
   const HalfTag want_st = half_tag(h, hs, sp), want_str = half_tag(h, 1 - hs, sp);
@@ -453,6 +517,12 @@ trd_status build_merged(trd_handle* h, int k, bool with_h) {
   const bool dbl = is_fp64(h);
   const size_t e = elt(h);
   if (!with_h) return build_halves(h, k);
+  if (X_(h)->row_view) {
+    // the step direction h (I_k x K, same layout as Z_{k(2)}) is the stationary operand
+    TRY(ensure(h, h->Sh, e * sp.P_stat * Kp));
+    CK(launch_from_double((const double*)h->h.p, sp.P_stat * (int64_t)Kp, h->Sh.p, dbl, h->stream), "h operand");
+    return TRD_OK;
+  }
   const Chain inner = make_chain(h, v, 0, c, k, (const double*)h->h.p);
   const Chain outer = make_chain(h, v, c, h->N, k, (const double*)h->h.p);
   TRY(ensure(h, h->Sh, e * sp.P_stat * Kp));
@@ -532,7 +602,7 @@ trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
   const View& v = h->view;
   const int64_t RB = (sp.P_stat + tc_bm() - 1) / tc_bm();
   const int64_t NT = (sp.P_strm + tc_bn() - 1) / tc_bn();
-  const int G = (int)imin(h->num_sms, RB * NT);
+  const int G = (int)imin(imax(1, h->num_sms - x->reserve_sms), RB * NT);
   const int o = sp.rows ? 0 : 1;
   const int64_t nstat = sp.rows ? sp.P_in : sp.P_out, nstrm = sp.rows ? sp.P_out : sp.P_in;
   const int64_t W = ((nstrm + 31) / 32 + 3) / 4 * 4;
@@ -607,7 +677,9 @@ trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
 }
 
 trd_status run_pass1(trd_handle* h, int k, bool full_stats = true) {
-  h->split = choose_split(h, h->view, k);
+  if (X_(h)->row_view && X_(h)->row_k != k)
+    return set_err(h, TRD_EINVAL, "the current row sample was drawn for another core");
+  h->split = X_(h)->row_view ? row_split(h, k, X_(h)->rows_J) : choose_split(h, h->view, k);
   const Split& sp = h->split;
   if (h->prec == TRD_BF16) {
     TRY(run_pass1_tc(h, k, full_stats));
@@ -645,6 +717,14 @@ trd_status run_pass1(trd_handle* h, int k, bool full_stats = true) {
 trd_status run_gradient(trd_handle* h, int k) {
   if (h->pass1_k != k) return set_err(h, TRD_EINVAL, "trd_residual_weights must run for this core first");
   PScope ps(h, P_GRAD);
+  if (X_(h)->row_view) {
+    // T = Y B is the gradient itself (I_k x K, column alpha + beta r_k)
+    TRY(ensure(h, h->d, sizeof(double) * h->I[k] * h->K[k]));
+    CK(cudaMemcpyAsync(h->d.p, h->Tsum.p, sizeof(double) * h->I[k] * h->K[k], cudaMemcpyDeviceToDevice, h->stream),
+       "gradient");
+    h->grad_k = k;
+    return TRD_OK;
+  }
   const View& v = h->view;
   const Split& sp = h->split;
   const int N = h->N, c = sp.c;
@@ -685,9 +765,65 @@ trd_status run_gradient(trd_handle* h, int k) {
   return TRD_OK;
 }
 
+// Fork: the FGMC Gram of core k and its LDL^T factorisation on the side stream, ordered after
+// everything already on the main stream (the other cores are final for this update).  The
+// join is in run_update.  Falls back (returns false) when not applicable.
+constexpr int kSideSMs = 2;
+bool prefactor(trd_handle* h, int k, double lambda) {
+  Extra* x = X_(h);
+  const int K = h->K[k];
+  if (!ldl_fits(K) || h->N < 3) return false;
+  if (!x->side) {
+    if (cudaStreamCreateWithFlags(&x->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  if (!x->solve_ctr.p) {
+    if (ensure(h, x->solve_ctr, 256) != TRD_OK) return false;
+    if (cudaMemsetAsync(x->solve_ctr.p, 0, 256, h->stream) != cudaSuccess) return false;
+  }
+  if (cudaEventRecord(x->ev_fork, h->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(x->side, x->ev_fork, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaStream_t main_stream = h->stream;
+  h->stream = x->side;       // the phase scopes below trace the side stream
+  trd_status st;
+  {
+    PScope ps(h, P_GRAM);
+    st = ensure_gram(h, k);
+  }
+  if (st == TRD_OK) {
+    PScope ps(h, P_CHOL);
+    double* Lcm = (double*)h->L.p;
+    if (launch_ldl_factor((const double*)h->G.p, K, lambda, Lcm, Lcm + (size_t)K * K, h->scal, h->dstatus,
+                          x->side) != cudaSuccess)
+      st = TRD_ECUDA;
+  }
+  const bool ok = st == TRD_OK && cudaEventRecord(x->ev_join, x->side) == cudaSuccess;
+  h->stream = main_stream;
+  if (!ok) {
+    // join whatever was forked, then let run_update compute everything on the main stream
+    cudaGetLastError();
+    cudaEventRecord(x->ev_join, x->side);
+    cudaStreamWaitEvent(h->stream, x->ev_join, 0);
+    h->gram_k = -1;
+    return false;
+  }
+  x->pre_k = k;
+  x->pre_lambda = lambda;
+  return true;
+}
+
 trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int gram,
                       double* eta_slot) {
   if (h->grad_k != k) return set_err(h, TRD_EINVAL, "trd_core_gradient must run for this core first");
+  if (gram == TRD_GRAM_LOCAL && X_(h)->row_view)
+    return set_err(h, TRD_ENOTIMPL, "the local Gram is defined for the RStS sketch, not for sampled rows");
   const int K = h->K[k];
   const int64_t n = h->I[k] * (int64_t)K;
   double* d = (double*)h->d.p;
@@ -695,6 +831,19 @@ trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int
   bool dot_done = false;
   if (gram == TRD_GRAM_NONE) {
     CK(cudaMemcpyAsync(hh, d, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream), "copy d");
+  } else if (X_(h)->pre_k == k && X_(h)->pre_lambda == lambda && gram == TRD_GRAM_GLOBAL && ldl_fits(K)) {
+    // G and its factor were prepared on the side stream during this core's data pass
+    Extra* xs = X_(h);
+    xs->pre_k = -1;
+    CK(cudaStreamWaitEvent(h->stream, xs->ev_join, 0), "join side stream");
+    double* Lcm = (double*)h->L.p;
+    double* Dinv = Lcm + (size_t)K * K;
+    PScope ps(h, P_SOLVE);
+    TRY(ensure(h, xs->dotpart, sizeof(double) * (size_t)h->I[k]));
+    CK(launch_ldl_solve(Lcm, Dinv, d, hh, K, h->I[k], (double*)xs->dotpart.p, (unsigned int*)xs->solve_ctr.p,
+                        h->scal + S_NUM, h->stream),
+       "triangular solves");
+    dot_done = true;
   } else {
     const double* G;
     {
@@ -847,6 +996,7 @@ trd_status use_full_view(trd_handle* h) {
   h->view_k = -1;
   h->sketched = false;
   X_(h)->view_gen = 0;
+  X_(h)->row_view = false;
   return TRD_OK;
 }
 
@@ -911,6 +1061,7 @@ trd_status sample(trd_handle* h, int k, const int32_t* const* idx, const int32_t
   h->view_k = k;
   h->sketched = true;
   X_(h)->view_gen = ++X_(h)->sketch_count;
+  X_(h)->row_view = false;
   h->pass1_k = -1;
   h->grad_k = -1;
   return TRD_OK;
@@ -1073,6 +1224,15 @@ trd_status trd_create(trd_t** out, int N, const int64_t* I, const int32_t* R, in
 void trd_destroy(trd_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  {
+    Extra* x = X_(h);
+    if (x->side) {
+      cudaStreamSynchronize(x->side);
+      cudaStreamDestroy(x->side);
+    }
+    if (x->ev_fork) cudaEventDestroy(x->ev_fork);
+    if (x->ev_join) cudaEventDestroy(x->ev_join);
+  }
   drop_graph(X_(h));
   for (int k = 0; k < kMaxN; ++k) {
     if (h->Z[k]) cudaFree(h->Z[k]);
@@ -1086,7 +1246,7 @@ void trd_destroy(trd_t* h) {
   for (DevBuf* b : bufs) free_buf(*b);
   Extra* x = X_(h);
   DevBuf* xb[] = {&x->Ework, &x->meta,    &x->stat_sum2, &x->Gloc,    &x->recA, &x->recC,
-                  &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr, &x->probe_cand,
+                  &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr, &x->probe_cand, &x->rows_dev,
                   &x->bShi,  &x->bSlo,    &x->bSh,       &x->bThi,    &x->bTlo,    &x->bTT,
                   &x->Mst[0], &x->Mst[1]};
   for (DevBuf* b : xb) free_buf(*b);
@@ -1196,6 +1356,48 @@ trd_status trd_sample_subtensor(trd_t* h, int k, const int32_t* const* idx, cons
   TRY(check_k(h, k));
   if (idx && !s) return set_err(h, TRD_EINVAL, "sizes missing");
   return sample(h, k, idx, s);
+}
+
+trd_status trd_sample_rows(trd_t* h, int k, const int32_t* rows, int64_t J) {
+  TRY(check_handle(h));
+  touch(h);
+  TRY(check_k(h, k));
+  if (!h->X) return set_err(h, TRD_EINVAL, "no data attached");
+  if (!rows || J < 1 || J > ((int64_t)1 << 31) / (h->N > 0 ? h->N : 1))
+    return set_err(h, TRD_EINVAL, "rows must be a host array of J >= 1 multi-indices");
+  const int N = h->N;
+  for (int64_t j = 0; j < J; ++j)
+    for (int m = 0; m < N; ++m)
+      if (m != k && (rows[j * N + m] < 0 || rows[j * N + m] >= h->I[m]))
+        return set_err(h, TRD_EINVAL, "a sampled index is out of range");
+  Extra* x = X_(h);
+  const int64_t n = h->I[k] * J;
+  const int64_t words = ((n + 31) / 32 + 3) / 4 * 4;
+  TRY(ensure(h, x->rows_dev, sizeof(int32_t) * (size_t)(J * N)));
+  TRY(ensure(h, h->XI, sizeof(float) * (size_t)n));
+  TRY(ensure(h, h->PI, sizeof(uint32_t) * (size_t)words));
+  CK(cudaMemcpyAsync(x->rows_dev.p, rows, sizeof(int32_t) * (size_t)(J * N), cudaMemcpyHostToDevice, h->stream),
+     "rows upload");
+  CK(cudaMemsetAsync(h->PI.p, 0, sizeof(uint32_t) * (size_t)words, h->stream), "mask clear");
+  CK(launch_gather_rows(h->X, h->M, rows_args(h, k, J), (const int32_t*)x->rows_dev.p, (float*)h->XI.p,
+                        (uint32_t*)h->PI.p, h->stream),
+     "row gather");
+  View v;
+  v.X = (const float*)h->XI.p;
+  v.M = (const uint32_t*)h->PI.p;
+  v.N = N;
+  v.numel = n;
+  for (int m = 0; m < N; ++m) v.dim[m] = h->I[m];
+  h->view = v;
+  h->view_k = k;
+  h->sketched = true;
+  x->view_gen = ++x->sketch_count;
+  x->row_view = true;
+  x->row_k = k;
+  x->rows_J = J;
+  h->pass1_k = -1;
+  h->grad_k = -1;
+  return sync_and_status(h);   // the host rows may be released on return
 }
 
 trd_status trd_residual_weights(trd_t* h, int k, double sigma, trd_resid_stats* out) {
@@ -1329,7 +1531,13 @@ trd_status step_device(trd_handle* h, const trd_params* p, int64_t* slots_out) {
     } else if (h->sketched) {
       use_full_view(h);
     }
-    TRY(run_pass1(h, k, false));
+    Extra* x = X_(h);
+    x->pre_k = -1;
+    x->reserve_sms = 0;
+    if (p->gram == TRD_GRAM_GLOBAL && prefactor(h, k, p->lambda)) x->reserve_sms = kSideSMs;
+    const trd_status s1 = run_pass1(h, k, false);
+    x->reserve_sms = 0;
+    TRY(s1);
     CK(cudaMemcpyAsync(h->report_dev + R_OBJ + k, (double*)h->stat_sum.p + 2, sizeof(double),
                        cudaMemcpyDeviceToDevice, h->stream), "objective");
     TRY(run_gradient(h, k));

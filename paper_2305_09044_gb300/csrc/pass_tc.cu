@@ -47,11 +47,15 @@ constexpr int Y_TILE = BM * BN * 2;            // 16 KB: weighted residuals (A o
 constexpr int SUB_S = BM * 64 * 2;             // 16 KB: one K sub-tile of a stationary operand
 constexpr int SUB_T = BN * 64 * 2;             // 8 KB: one K sub-tile of a streaming operand
 
+constexpr int ND = 4;          // GEMM-1 accumulator buffers in TMEM (the MMA runs ahead of the epilogue)
+constexpr int NY = 2;          // weighted-residual (Y) buffers
+constexpr uint32_t TMEM_COLS = 512;
+
 template <int KP>
 struct Cfg {
   static constexpr int NSUB = KP / 64;
-  static constexpr int XS = KP == 64 ? 4 : 2;    // data-tile stages (released by the epilogue)
-  static constexpr int TS = KP == 64 ? 3 : 2;    // streaming-operand stages (released by MMA commits)
+  static constexpr int XS = KP == 64 ? 3 : 2;    // data-tile stages (released by the epilogue)
+  static constexpr int TS = KP == 64 ? 4 : 2;    // streaming-operand stages (released by MMA commits)
   static constexpr int S_TILE = BM * KP * 2;     // one stationary operand
   static constexpr int T_TILE = BN * KP * 2;     // one streaming operand
 };
@@ -70,7 +74,7 @@ __host__ __device__ constexpr Layout layout(bool pass2) {
   L.s_h = o; if (pass2) o += C::S_TILE;
   L.x0 = o; o += C::XS * X_TILE;
   L.t0 = o; o += C::TS * 2 * C::T_TILE;   // per stage: hi tile then lo tile
-  L.y = o; if (!pass2) o += Y_TILE;
+  L.y = o; if (!pass2) o += NY * Y_TILE;
   L.bars = o; o += 1024;
   L.total = o;
   return L;
@@ -116,6 +120,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
 }
 // Bounded wait; false (and the abort flag set) when the limit is reached or another role
 // has aborted.
+// Non-blocking probe of a phase (for the MMA issuer, which polls two streams of work).
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool mbar_wait_n(uint64_t* b, uint32_t parity, volatile int* abort_flag, uint32_t limit) {
   for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_try(b, parity)) return true;
@@ -273,12 +288,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* x_empty = x_full + XS;        // [XS]  data tile read by every epilogue thread
   uint64_t* t_full = x_empty + XS;        // [TS]  streaming operands landed (TMA)
   uint64_t* t_empty = t_full + TS;        // [TS]  streaming operands consumed (MMA commit)
-  uint64_t* d_full = t_empty + TS;        // [2]   GEMM 1 (and the h product) done
-  uint64_t* d_empty = d_full + 2;         // [2]   accumulators read by the epilogue
-  uint64_t* y_full = d_empty + 2;         //       Y written
-  uint64_t* y_empty = y_full + 1;         //       GEMM 2 consumed Y
-  uint64_t* s_full = y_empty + 1;         //       stationary operands landed
-  uint64_t* s_empty = s_full + 1;         //       segment's MMAs done with them
+  uint64_t* d_full = t_empty + TS;        // [ND]  GEMM 1 (and the h product) done
+  uint64_t* d_empty = d_full + ND;        // [ND]  accumulators read by the epilogue
+  uint64_t* y_full = d_empty + ND;        // [NY]  Y written
+  uint64_t* y_empty = y_full + NY;        // [NY]  GEMM 2 consumed Y
+  uint64_t* s_full = y_empty + NY;        //       stationary operands landed
+  uint64_t* s_empty = s_full + 1;         //       segment's GEMM-1 MMAs done with them
   uint64_t* acc_full = s_empty + 1;       //       segment's contraction complete
   uint64_t* acc_empty = acc_full + 1;     //       contraction drained to global
   uint64_t* mma_done = acc_empty + 1;
@@ -299,12 +314,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&t_full[s], 1);
       mbar_init(&t_empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < ND; ++b) {
       mbar_init(&d_full[b], 1);
       mbar_init(&d_empty[b], EPI_THREADS);
     }
-    mbar_init(y_full, EPI_THREADS);
-    mbar_init(y_empty, 1);
+    for (int b = 0; b < NY; ++b) {
+      mbar_init(&y_full[b], EPI_THREADS);
+      mbar_init(&y_empty[b], 1);
+    }
     mbar_init(s_full, 1);
     mbar_init(s_empty, 1);
     mbar_init(acc_full, 1);
@@ -313,7 +330,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  constexpr uint32_t TMEM_COLS = 256;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
                  "r"(TMEM_COLS)
@@ -324,8 +340,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  // TMEM columns: D1[b] at b*BN, D2[b] (pass 2) at (2 + b)*BN, T accumulator at 2*BN
-  const uint32_t col_acc = 2u * BN;
+  // TMEM columns: D1[b] at b BN (b < ND), then D2[b] (pass 2) at (ND + b) BN or the T
+  // accumulator (pass 1) at ND BN
+  const uint32_t col_acc = (uint32_t)(ND * BN);
 
   if (warp == 0) {
     // ---------------------------------------------------------------- operand producer
@@ -349,10 +366,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tma_2d(sm + L.s_lo + sb * SUB_S, &mS_lo, s_full, sb * 64, (int)(rb * BM));
           if (PASS2) tma_2d(sm + L.s_h + sb * SUB_S, &mS_h, s_full, sb * 64, (int)(rb * BM));
         }
-        for (; u < seg_end; ++u, ++it) {
+        for (int64_t tc = u - rb * p.NT; u < seg_end; ++u, ++it, ++tc) {
           const int s = (int)(it % TS);
           if (!mbar_wait(&t_empty[s], (uint32_t)(((it / TS) & 1) ^ 1), abort_flag)) { ok = false; break; }
-          const int t0 = (int)((u % p.NT) * BN);
+          const int t0 = (int)(tc * BN);
           unsigned char* tb = sm + L.t0 + s * 2 * T_TILE;
           mbar_expect_tx(&t_full[s], 2 * T_TILE);
           last_phase[s] = (int)((it / TS) & 1);
@@ -381,11 +398,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       int last_phase[XS];
       for (int s = 0; s < XS; ++s) last_phase[s] = -1;
+      int64_t rb = u_begin / p.NT, tc = u_begin - rb * p.NT;   // running block / tile counters
       for (int64_t u = u_begin; u < u_end; ++u, ++it) {
         const int s = (int)(it % XS);
         if (!mbar_wait(&x_empty[s], (uint32_t)(((it / XS) & 1) ^ 1), abort_flag)) { ok = false; break; }
-        const int64_t rb = u / p.NT;
-        const int t0 = (int)((u % p.NT) * BN);
+        const int t0 = (int)(tc * BN);
         unsigned char* xb = sm + L.x0 + s * X_TILE;
         mbar_expect_tx(&x_full[s], X_TILE);
         last_phase[s] = (int)((it / XS) & 1);
@@ -394,6 +411,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         } else {
           tma_2d(xb, &mX, &x_full[s], t0, (int)(rb * BM));
           tma_2d(xb + X_TILE / 2, &mX, &x_full[s], t0 + 32, (int)(rb * BM));
+        }
+        if (++tc == p.NT) {
+          tc = 0;
+          ++rb;
         }
       }
       if (!ok)
@@ -409,68 +430,80 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       constexpr uint32_t ID2 = idesc_bf16(BM, KPAD, 1);    // B = streaming tile, MN-major
       const uint32_t a_hi = su32(sm + L.s_hi), a_lo = su32(sm + L.s_lo), a_h = su32(sm + L.s_h);
       const uint32_t ybuf = su32(sm + L.y);
-      int64_t it = 0;
-      int g = 0;
-      bool ok = true;
-      for (int64_t u = u_begin; u < u_end && ok; ++g) {
-        const int64_t rb = u / p.NT;
-        const int64_t seg_end = imin(u_end, (rb + 1) * p.NT);
-        if (!mbar_wait(s_full, (uint32_t)(g & 1), abort_flag)) { ok = false; break; }
-        tc_fence_after();
-        int64_t prev = -1;        // tile whose GEMM 2 is pending
-        bool first2 = true;
-        for (; u < seg_end; ++u, ++it) {
-          const int s = (int)(it % TS), b = (int)(it & 1);
-          if (!mbar_wait(&t_full[s], (uint32_t)((it / TS) & 1), abort_flag)) { ok = false; break; }
-          if (!mbar_wait(&d_empty[b], (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag)) { ok = false; break; }
-          tc_fence_after();
-          const uint32_t b_hi = su32(sm + L.t0 + s * 2 * T_TILE), b_lo = b_hi + T_TILE;
-#pragma unroll
-          for (int kk = 0; kk < KPAD / 16; ++kk) {
-            // K step kk: sub-tile kk / 4, 32-byte step kk % 4 inside its swizzle atom
-            const uint32_t ka = (uint32_t)((kk >> 2) * SUB_S + (kk & 3) * 32);
-            const uint32_t kb = (uint32_t)((kk >> 2) * SUB_T + (kk & 3) * 32);
-            tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_hi + ka), sdesc(b_hi + kb), ID1, kk > 0);
-            tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_hi + ka), sdesc(b_lo + kb), ID1, 1);
-            tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_lo + ka), sdesc(b_hi + kb), ID1, 1);
-            if (PASS2) tc_mma(tmem + (uint32_t)((2 + b) * BN), sdesc(a_h + ka), sdesc(b_hi + kb), ID1, kk > 0);
-          }
-          tc_commit(&d_full[b]);
-          if (PASS2) {
-            tc_commit(&t_empty[s]);
-            continue;
-          }
-          if (prev >= 0) {
-            // GEMM 2 of the previous tile: T += Y * S_str, B read MN-major from its hi tile
-            if (first2 && g > 0 && !mbar_wait(acc_empty, (uint32_t)((g - 1) & 1), abort_flag)) { ok = false; break; }
-            if (!mbar_wait(y_full, (uint32_t)(prev & 1), abort_flag)) { ok = false; break; }
+      // Two streams of work, polled without blocking: GEMM 1 of tile i1 (as soon as its
+      // streaming operands, a free accumulator buffer and the segment's stationary operands
+      // are there) and GEMM 2 of tile i2 < i1 (as soon as the epilogue has written its Y).
+      // A segment is the run of tiles of one stationary block.
+      const int64_t ntiles = u_end - u_begin;
+      const int64_t first_end = imin(u_end, (u_begin / p.NT + 1) * p.NT);
+      int64_t i1 = 0, u1 = u_begin, seg1_end = first_end;
+      int64_t i2 = 0, u2 = u_begin, seg2_end = first_end;
+      int g1 = 0, g2 = 0;
+      bool need_s = true, first2 = true, ok = true;
+      uint32_t idle = 0;
+      while (ok && (PASS2 ? i1 < ntiles : i2 < ntiles)) {
+        bool moved = false;
+        if (i1 < ntiles) {
+          const int s = (int)(i1 % TS), b = (int)(i1 & (ND - 1));
+          if ((!need_s || mbar_test(s_full, (uint32_t)(g1 & 1))) &&
+              mbar_test(&t_full[s], (uint32_t)((i1 / TS) & 1)) &&
+              mbar_test(&d_empty[b], (uint32_t)(((i1 / ND) & 1) ^ 1))) {
             tc_fence_after();
-            const int sp = (int)(prev % TS);
-            const uint32_t tp = su32(sm + L.t0 + sp * 2 * T_TILE);
-            for (int kk = 0; kk < BN / 16; ++kk)
-              tc_mma(tmem + col_acc, sdesc(ybuf + kk * 32), sdesc_mn(tp + kk * 2048, BN * 128), ID2,
-                     (first2 && kk == 0) ? 0u : 1u);
-            first2 = false;
-            tc_commit(y_empty);
-            tc_commit(&t_empty[sp]);
+            const uint32_t b_hi = su32(sm + L.t0 + s * 2 * T_TILE), b_lo = b_hi + T_TILE;
+#pragma unroll
+            for (int kk = 0; kk < KPAD / 16; ++kk) {
+              // K step kk: sub-tile kk / 4, 32-byte step kk % 4 inside its swizzle atom
+              const uint32_t ka = (uint32_t)((kk >> 2) * SUB_S + (kk & 3) * 32);
+              const uint32_t kb = (uint32_t)((kk >> 2) * SUB_T + (kk & 3) * 32);
+              tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_hi + ka), sdesc(b_hi + kb), ID1, kk > 0);
+              tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_hi + ka), sdesc(b_lo + kb), ID1, 1);
+              tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_lo + ka), sdesc(b_hi + kb), ID1, 1);
+              if (PASS2)
+                tc_mma(tmem + (uint32_t)((ND + b) * BN), sdesc(a_h + ka), sdesc(b_hi + kb), ID1, kk > 0);
+            }
+            tc_commit(&d_full[b]);
+            if (PASS2) tc_commit(&t_empty[s]);
+            need_s = false;
+            ++i1;
+            if (++u1 == seg1_end) {
+              tc_commit(s_empty);     // the segment's GEMM-1 MMAs: its stationary operands may go
+              ++g1;
+              need_s = true;
+              seg1_end = imin(u_end, seg1_end + p.NT);
+            }
+            moved = true;
           }
-          prev = it;
         }
-        if (!ok) break;
-        if (!PASS2 && prev >= 0) {
-          if (first2 && g > 0 && !mbar_wait(acc_empty, (uint32_t)((g - 1) & 1), abort_flag)) { ok = false; break; }
-          if (!mbar_wait(y_full, (uint32_t)(prev & 1), abort_flag)) { ok = false; break; }
-          tc_fence_after();
-          const int sp = (int)(prev % TS);
-          const uint32_t tp = su32(sm + L.t0 + sp * 2 * T_TILE);
-          for (int kk = 0; kk < BN / 16; ++kk)
-            tc_mma(tmem + col_acc, sdesc(ybuf + kk * 32), sdesc_mn(tp + kk * 2048, BN * 128), ID2,
-                   (first2 && kk == 0) ? 0u : 1u);
-          tc_commit(y_empty);
-          tc_commit(&t_empty[sp]);
-          tc_commit(acc_full);
+        if (!PASS2 && i2 < i1) {
+          const int s = (int)(i2 % TS), yb = (int)(i2 & (NY - 1));
+          if ((!first2 || g2 == 0 || mbar_test(acc_empty, (uint32_t)((g2 - 1) & 1))) &&
+              mbar_test(&y_full[yb], (uint32_t)((i2 / NY) & 1))) {
+            tc_fence_after();
+            // GEMM 2: T += Y * S_str, B read MN-major from the tile's hi operand
+            const uint32_t tp = su32(sm + L.t0 + s * 2 * T_TILE);
+#pragma unroll
+            for (int kk = 0; kk < BN / 16; ++kk)
+              tc_mma(tmem + col_acc, sdesc(ybuf + yb * Y_TILE + kk * 32), sdesc_mn(tp + kk * 2048, BN * 128), ID2,
+                     (first2 && kk == 0) ? 0u : 1u);
+            tc_commit(&y_empty[yb]);
+            tc_commit(&t_empty[s]);
+            first2 = false;
+            ++i2;
+            if (++u2 == seg2_end) {
+              tc_commit(acc_full);
+              ++g2;
+              first2 = true;
+              seg2_end = imin(u_end, seg2_end + p.NT);
+            }
+            moved = true;
+          }
         }
-        tc_commit(s_empty);
+        if (moved) {
+          idle = 0;
+        } else if (++idle >= WAIT_LIMIT || *abort_flag) {
+          *abort_flag = 1;
+          ok = false;
+        }
       }
       // every issued MMA has finished before TMEM can be released
       tc_commit(mma_done);
@@ -500,21 +533,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const bool row_ok = srow < p.P_stat;
       const uint32_t* mrow = p.Mst + (row_ok ? srow : 0) * p.W;
       const int c0 = grp * CPW;                 // first tile column of this warp
-      // observation bits: this thread's CPW bits of the next tile are fetched one tile ahead
-      uint32_t mnext = row_ok ? __ldg(mrow + (((u % p.NT) * BN + c0) >> 5)) : 0u;
-      for (; u < seg_end; ++u, ++it) {
-        const int xs = (int)(it % XS), b = (int)(it & 1);
-        const int64_t t0 = (u % p.NT) * BN;
-        const uint32_t mword = (mnext >> ((t0 + c0) & 31)) & CMASK;
-        if (row_ok && u + 1 < seg_end) mnext = __ldg(mrow + ((t0 + BN + c0) >> 5));
+      // observation bits: this thread's 32 bits of a tile are one mask word (CPW = 32, tiles
+      // 64 columns apart), fetched three tiles ahead (the words of one warp lie in 32
+      // different mask rows, so each fetch has the full L2 latency)
+      // tiles of this segment are tc0 .. tc_end - 1 of stationary block rb (no divisions in
+      // the tile loop)
+      const int64_t tc0 = u - rb * p.NT, tc_end = seg_end - rb * p.NT;
+      auto mword_of = [&](int64_t tt) -> uint32_t {
+        return (row_ok && tt < tc_end) ? __ldg(mrow + ((tt * BN + c0) >> 5)) : 0u;
+      };
+      uint32_t mq0 = mword_of(tc0), mq1 = mword_of(tc0 + 1), mq2 = mword_of(tc0 + 2);
+      for (int64_t tc = tc0; u < seg_end; ++u, ++it, ++tc) {
+        const int xs = (int)(it % XS), b = (int)(it & (ND - 1)), yb = (int)(it & (NY - 1));
+        const int64_t t0 = tc * BN;
+        const uint32_t mword = mq0;
+        mq0 = mq1;
+        mq1 = mq2;
+        mq2 = mword_of(tc + 3);
         const int64_t nc = p.P_strm - t0 - c0;  // valid columns for this warp
         const uint32_t vmask = (!row_ok || nc <= 0) ? 0u : (nc >= CPW ? CMASK : ((1u << nc) - 1u));
         // accumulators first: the TMEM loads are in flight while X is read from shared memory
-        if (!mbar_wait(&d_full[b], (uint32_t)((it >> 1) & 1), abort_flag)) { ok = false; break; }
+        if (!mbar_wait(&d_full[b], (uint32_t)((it / ND) & 1), abort_flag)) { ok = false; break; }
         tc_fence_after();
         uint32_t rx[32], rd[32];
         tmem_issue32(tmem + lane_base + (uint32_t)(b * BN + c0), rx);
-        if (PASS2) tmem_issue32(tmem + lane_base + (uint32_t)((2 + b) * BN + c0), rd);
+        if (PASS2) tmem_issue32(tmem + lane_base + (uint32_t)((ND + b) * BN + c0), rd);
         if (!mbar_wait(&x_full[xs], (uint32_t)((it / XS) & 1), abort_flag)) {
           if (PASS2) tmem_wait64(rx, rd);
           else tmem_wait32(rx);
@@ -594,15 +637,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           uint32_t ypk[CPW / 2];
 #pragma unroll
           for (int j = 0; j < CPW; j += 2) ypk[j >> 1] = pack_bf16(xv[j], xv[j + 1]);
-          if (!mbar_wait(y_empty, (uint32_t)((it & 1) ^ 1), abort_flag)) { ok = false; break; }
-          unsigned char* yrow = sm + L.y + row * 128;
+          if (!mbar_wait(&y_empty[yb], (uint32_t)(((it / NY) & 1) ^ 1), abort_flag)) { ok = false; break; }
+          unsigned char* yrow = sm + L.y + yb * Y_TILE + row * 128;
 #pragma unroll
           for (int cc = 0; cc < CPW / 8; ++cc) {
             const uint4 v = make_uint4(ypk[4 * cc], ypk[4 * cc + 1], ypk[4 * cc + 2], ypk[4 * cc + 3]);
             *reinterpret_cast<uint4*>(yrow + ((((c0 >> 3) + cc) ^ (row & 7)) << 4)) = v;
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_arrive(y_full);
+          mbar_arrive(&y_full[yb]);
         }
       }
       if (!ok) break;

@@ -249,6 +249,18 @@ cudaError_t launch_probe_sigma_merged(const void* A, const void* C, bool fp64, i
 cudaError_t launch_sigma_from_floats(const float* r, int64_t n, double x_obs_rms, double sigma_prev, uint64_t* keys,
                                      uint64_t* cand, double* work, double* sigma_out, cudaStream_t st);
 
+// rows.cu (uniform row sampling of the subchain unfolding)
+struct RowsArgs {
+  int N = 0, k = 0;
+  int64_t Ik = 0, J = 0;
+  int64_t stride[kMaxN] = {};        // linear stride of each mode in X
+  int R[kMaxN] = {};
+  const double* Z[kMaxN] = {};       // FP64 master cores
+};
+cudaError_t launch_gather_rows(const float* X, const uint32_t* M, const RowsArgs& a, const int32_t* rows, float* XI,
+                               uint32_t* PI, cudaStream_t st);
+cudaError_t launch_rows_chain(const RowsArgs& a, const int32_t* rows, void* B, bool fp64, cudaStream_t st);
+
 // sampled.cu
 // Strides of each mode inside the inner (a) / outer (b) block of a two-block cut (0 if the mode
 // belongs to the other block).

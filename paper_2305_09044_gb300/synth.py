@@ -149,6 +149,41 @@ def assemble(x_true, c: Corruption, kind: str = "uniform", scale: float = 10.0):
     return x
 
 
+def corruption_chunks(w: Workload, chunk: int = 1 << 26):
+    """Chunked form of the corruption draw for tensors too large for whole-tensor arrays:
+    yields (start, mask, outlier, u, noise) over consecutive linear-index ranges.  Each
+    component has its own generator (mask: data_seed + 7, outlier: + 11, u: + 12, noise:
+    + 13), drawn sequentially chunk after chunk, so the result does not depend on `chunk`.
+    Same distributions as draw_corruption; a different stream from it."""
+    n = int(np.prod(w.dims))
+    g_mask = np.random.default_rng(w.data_seed + 7)
+    g_out = np.random.default_rng(w.data_seed + 11)
+    g_u = np.random.default_rng(w.data_seed + 12)
+    g_noise = np.random.default_rng(w.data_seed + 13) if w.noise_var > 0 else None
+    for s in range(0, n, chunk):
+        c = min(chunk, n - s)
+        mask = g_mask.random(c) < (1.0 - w.missing)
+        outl = g_out.random(c) < w.outlier_frac
+        if w.outlier_kind == "saltpepper":
+            u = np.where(g_u.random(c) < 0.5, -1.0, 1.0)
+        else:
+            outl &= mask
+            u = g_u.uniform(-1.0, 1.0, c)
+        noise = math.sqrt(w.noise_var) * g_noise.standard_normal(c) if g_noise is not None else None
+        yield s, mask, outl, u, noise
+
+
+def assemble_chunk(x_true, outl, u, noise, kind: str, std: float, lo: float, hi: float,
+                   scale: float = 10.0):
+    """assemble() for one chunk, with the clean tensor's std / min / max given."""
+    x = np.array(x_true, dtype=np.float64, copy=True)
+    if noise is not None:
+        x = x + noise
+    if kind == "saltpepper":
+        return np.where(outl, np.where(u > 0, hi, lo), x)
+    return np.where(outl, scale * std * u, x)
+
+
 def sample_entries(dims: Sequence[int], M: int, seed: int) -> np.ndarray:
     """About M distinct multi-indices (rows of an int32 array, N columns), sorted by linear
     index: each entry is kept independently with probability M / numel (a few draws more),

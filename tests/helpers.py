@@ -31,3 +31,30 @@ def rel(a, b):
 def flat(X):
     """Linear (i_1 fastest) float32 vector of a tensor."""
     return np.asarray(X, dtype=np.float32).reshape(-1, order="F")
+
+
+def big_problem(w, cut: int, cols: int):
+    """Full-size workload `w` built chunk by chunk (for tensors of ~1e9 entries): the clean
+    tensor from the oracle's two-half reconstruction of the seeded true cores, the
+    corruption from synth.corruption_chunks.  Returns (X float32 flat, mask bool flat,
+    true cores); arrays are in linear order (i_1 fastest)."""
+    dims = tuple(w.dims)
+    n = int(np.prod(dims))
+    truth = synth.gaussian_cores(dims, w.ranks, w.data_seed, w.smooth_modes, w.smooth_width)
+    Xc = np.empty(n, dtype=np.float32)
+    s1 = s2 = 0.0
+    lo, hi = math.inf, -math.inf
+    for s, v in O.reconstruct_chunks(truth, cut, cols):
+        Xc[s:s + v.size] = v
+        s1 += float(v.sum())
+        s2 += float(np.dot(v, v))
+        lo, hi = min(lo, float(v.min())), max(hi, float(v.max()))
+    std = math.sqrt(max(s2 / n - (s1 / n) ** 2, 0.0))
+    X = np.empty(n, dtype=np.float32)
+    mask = np.empty(n, dtype=bool)
+    for s, m, o, u, nz in synth.corruption_chunks(w):
+        e = s + m.size
+        X[s:e] = synth.assemble_chunk(Xc[s:e].astype(np.float64), o, u, nz, w.outlier_kind, std, lo, hi)
+        mask[s:e] = m
+    del Xc
+    return X, mask, truth

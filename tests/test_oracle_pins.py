@@ -478,3 +478,64 @@ def test_sampled_vectorised_matches_loops():
     assert np.allclose(a[1], b[1], rtol=0, atol=1e-13)
     for ga, gb in zip(a[3], b[3]):
         assert np.allclose(ga, gb, rtol=0, atol=1e-12)
+
+
+def test_reconstruct_chunks_equals_definition():
+    """The chunked two-half reconstruction equals Def. 1 (explicit trace of the product of
+    slices) on a small ring with mixed ranks, for every cut and a ragged column block."""
+    rng = np.random.default_rng(17)
+    dims, ranks = (4, 3, 5, 2), (2, 3, 1, 2)
+    cores = [rng.standard_normal((ranks[k], dims[k], ranks[(k + 1) % 4])) for k in range(4)]
+    want = np.array([O.entry(cores, np.unravel_index(l, dims, order="F")) for l in range(int(np.prod(dims)))])
+    for c in (1, 2, 3):
+        got = np.empty_like(want)
+        for s, v in O.reconstruct_chunks(cores, c, cols=3):
+            got[s:s + v.size] = v
+        assert np.allclose(got, want, rtol=1e-13, atol=1e-13)
+
+
+def _all_rows(dims, k):
+    grids = np.meshgrid(*[np.arange(I) if m != k else np.zeros(1, dtype=int) for m, I in enumerate(dims)],
+                        indexing="ij")
+    return np.stack([g.reshape(-1) for g in grids], axis=1).astype(np.int64)
+
+
+def test_row_sampling_with_every_row_is_the_full_step():
+    """Uniform row sampling (Sec. 5 ablation) with every row of Z^{!=k}_[2] sampled once is
+    the unsampled AWRTRD step (any row order); sampling every row twice doubles d and leaves
+    the updated core unchanged (the exact line search absorbs the factor)."""
+    rng = np.random.default_rng(23)
+    dims, ranks = (5, 4, 3, 4), (2, 3, 2, 2)
+    cores = [rng.standard_normal((ranks[k], dims[k], ranks[(k + 1) % 4])) for k in range(4)]
+    X = O.reconstruct(cores) + 0.3 * rng.standard_normal(dims)
+    P = (rng.random(dims) < 0.7).astype(np.float64)
+    for k in range(4):
+        full = O.core_update(X, P, cores, k, 1.2, lam=-1e-10)
+        rows = _all_rows(dims, k)[rng.permutation(int(np.prod(dims)) // dims[k])]
+        once = O.core_update_rows(X, P, cores, k, 1.2, rows, lam=-1e-10)
+        assert np.allclose(once.d, full.d, rtol=1e-12, atol=1e-12)
+        assert abs(once.eta - full.eta) <= 1e-12 * abs(full.eta)
+        assert np.allclose(once.cores[k], full.cores[k], rtol=1e-12, atol=1e-12)
+        twice = O.core_update_rows(X, P, cores, k, 1.2, np.concatenate([rows, rows]), lam=-1e-10)
+        assert np.allclose(twice.d, 2 * full.d, rtol=1e-12, atol=1e-12)
+        assert np.allclose(twice.cores[k], full.cores[k], rtol=1e-11, atol=1e-12)
+
+
+def test_sampled_rows_brute_force():
+    """Each sampled row of Z^{!=k}_[2] equals the explicit slice product of Thm. 1."""
+    rng = np.random.default_rng(29)
+    dims, ranks = (3, 4, 2, 5), (2, 3, 1, 2)
+    cores = [rng.standard_normal((ranks[k], dims[k], ranks[(k + 1) % 4])) for k in range(4)]
+    for k in range(4):
+        rows = O.draw_rows(11, 2, k, dims, 7)
+        assert rows.shape == (7, 4) and np.all(rows[:, k] == 0)
+        assert all(np.all((rows[:, m] >= 0) & (rows[:, m] < dims[m])) for m in range(4))
+        B = O.sampled_rows(cores, k, rows)
+        rk, rk1 = ranks[k], ranks[(k + 1) % 4]
+        for j in range(7):
+            S = np.eye(rk1)
+            for m in [(k + 1 + q) % 4 for q in range(3)]:
+                S = S @ cores[m][:, rows[j, m], :]
+            for a in range(rk):
+                for b in range(rk1):
+                    assert abs(B[j, a + b * rk] - S[b, a]) <= 1e-13
