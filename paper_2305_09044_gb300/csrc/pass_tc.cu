@@ -43,7 +43,7 @@ constexpr uint32_t WAIT_LIMIT = 1u << 24;
 // shared-memory carve-up (bytes, every buffer 1024-aligned).  Operands are stored as 64-wide
 // K sub-tiles (one 128-byte swizzle atom per row); KP = 64 or 128 is the padded contraction.
 constexpr int X_TILE = BN * BM * 4;            // 32 KB: one data tile
-constexpr int Y_TILE = BM * BN * 2;            // 16 KB: weighted residuals (A of GEMM 2)
+constexpr int Y_COLS = BN / 2;                 // TMEM columns of one Y buffer (BF16 pairs)
 constexpr int SUB_S = BM * 64 * 2;             // 16 KB: one K sub-tile of a stationary operand
 constexpr int SUB_T = BN * 64 * 2;             // 8 KB: one K sub-tile of a streaming operand
 
@@ -54,7 +54,8 @@ constexpr uint32_t TMEM_COLS = 512;
 template <int KP>
 struct Cfg {
   static constexpr int NSUB = KP / 64;
-  static constexpr int XS = KP == 64 ? 3 : 2;    // data-tile stages (released by the epilogue)
+  // data-tile stages (released by the epilogue): as many as shared memory allows
+  __host__ __device__ static constexpr int xs(bool pass2) { return KP == 64 ? (pass2 ? 3 : 4) : (pass2 ? 2 : 3); }
   static constexpr int TS = KP == 64 ? 4 : 2;    // streaming-operand stages (released by MMA commits)
   static constexpr int S_TILE = BM * KP * 2;     // one stationary operand
   static constexpr int T_TILE = BN * KP * 2;     // one streaming operand
@@ -72,9 +73,9 @@ __host__ __device__ constexpr Layout layout(bool pass2) {
   L.s_hi = o; o += C::S_TILE;
   L.s_lo = o; o += C::S_TILE;
   L.s_h = o; if (pass2) o += C::S_TILE;
-  L.x0 = o; o += C::XS * X_TILE;
+  L.x0 = o; o += C::xs(pass2) * X_TILE;
   L.t0 = o; o += C::TS * 2 * C::T_TILE;   // per stage: hi tile then lo tile
-  L.y = o; if (!pass2) o += NY * Y_TILE;
+  L.y = o;                              // (Y lives in TMEM)
   L.bars = o; o += 1024;
   L.total = o;
   return L;
@@ -161,6 +162,24 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+// GEMM with the A operand in tensor memory (rows = lanes, K along columns, two BF16 per column).
+__device__ __forceinline__ void tc_mma_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// 16 columns of this thread's lane from 16 registers; completed by tmem_wait_st.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
   asm volatile(
@@ -277,7 +296,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const __grid_constant__ CUtensorMap mS_h, const __grid_constant__ CUtensorMap mT_hi,
               const __grid_constant__ CUtensorMap mT_lo, const __grid_constant__ CUtensorMap mX,
               const Params p) {
-  constexpr int KPAD = KP, NSUB = Cfg<KP>::NSUB, XS = Cfg<KP>::XS, TS = Cfg<KP>::TS;
+  constexpr int KPAD = KP, NSUB = Cfg<KP>::NSUB, XS = Cfg<KP>::xs(PASS2), TS = Cfg<KP>::TS;
   constexpr int S_TILE = Cfg<KP>::S_TILE, T_TILE = Cfg<KP>::T_TILE;
   constexpr Layout L = layout<KP>(PASS2);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -340,9 +359,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  // TMEM columns: D1[b] at b BN (b < ND), then D2[b] (pass 2) at (ND + b) BN or the T
-  // accumulator (pass 1) at ND BN
+  // TMEM columns: D1[b] at b BN (b < ND), then D2[b] (pass 2) at (ND + b) BN or, in pass 1,
+  // the T accumulator at ND BN (KPAD columns) followed by the NY weighted-residual buffers Y
+  // (BF16 pairs, Y_COLS columns each; the A operand of GEMM 2)
   const uint32_t col_acc = (uint32_t)(ND * BN);
+  const uint32_t col_y = col_acc + (uint32_t)KPAD;
+  static_assert(ND * BN + KPAD + NY * Y_COLS <= (int)TMEM_COLS, "TMEM columns");
 
   if (warp == 0) {
     // ---------------------------------------------------------------- operand producer
@@ -429,7 +451,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       constexpr uint32_t ID1 = idesc_bf16(BM, BN);
       constexpr uint32_t ID2 = idesc_bf16(BM, KPAD, 1);    // B = streaming tile, MN-major
       const uint32_t a_hi = su32(sm + L.s_hi), a_lo = su32(sm + L.s_lo), a_h = su32(sm + L.s_h);
-      const uint32_t ybuf = su32(sm + L.y);
       // Two streams of work, polled without blocking: GEMM 1 of tile i1 (as soon as its
       // streaming operands, a free accumulator buffer and the segment's stationary operands
       // are there) and GEMM 2 of tile i2 < i1 (as soon as the epilogue has written its Y).
@@ -483,8 +504,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t tp = su32(sm + L.t0 + s * 2 * T_TILE);
 #pragma unroll
             for (int kk = 0; kk < BN / 16; ++kk)
-              tc_mma(tmem + col_acc, sdesc(ybuf + yb * Y_TILE + kk * 32), sdesc_mn(tp + kk * 2048, BN * 128), ID2,
-                     (first2 && kk == 0) ? 0u : 1u);
+              tc_mma_ta(tmem + col_acc, tmem + col_y + (uint32_t)(yb * Y_COLS + kk * 8),
+                        sdesc_mn(tp + kk * 2048, BN * 128), ID2, (first2 && kk == 0) ? 0u : 1u);
             tc_commit(&y_empty[yb]);
             tc_commit(&t_empty[s]);
             first2 = false;
@@ -520,6 +541,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const double sg = *p.sigma;
     // exp(-e^2 / (2 sigma^2)) = exp2(-e^2 * k), k = log2(e) / (2 sigma^2); sigma = inf -> k = 0
     const float nk = isinf(sg) ? 0.0f : (float)(-1.4426950408889634 / (2.0 * sg * sg));
+    // exp(-e^2 / (2 sigma^2)) = exp2(-(e s)^2) with s = sqrt(log2(e) / (2 sigma^2))
+    const float sk = isinf(sg) ? 0.0f : (float)sqrt(1.4426950408889634 / (2.0 * sg * sg));
     constexpr uint32_t CMASK = CPW == 32 ? 0xffffffffu : ((1u << CPW) - 1u);
     float sw = 0.f, se2 = 0.f, swe2 = 0.f, sden = 0.f;
     uint32_t nobs = 0, nnf = 0, nslot = 0;
@@ -618,17 +641,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           nnf += __popc(seen & ~fin);
         } else {
           // lean: only what the update needs (y, or den) and the objective sum w e^2; a
-          // non-finite residual on an observed slot propagates as NaN and rejects the step
+          // non-finite residual on an observed slot propagates as NaN and rejects the step.
+          // Pass 1 masks the residual first (e' = 0 off the mask, so w(e') = 1 and y = w e' = 0
+          // without further selects); pass 2 masks the weight.
 #pragma unroll
           for (int j = 0; j < CPW; ++j) {
-            const float e = xv[j] - xh[j];
-            const float w = fast_ex2(e * e * nk);
             const bool bit = (seen >> j) & 1u;
             if (PASS2) {
-              sden += bit ? w * dh[j] * dh[j] : 0.f;
+              const float t = (xv[j] - xh[j]) * sk;
+              const float w = bit ? fast_ex2(-(t * t)) : 0.f;
+              sden = fmaf(w * dh[j], dh[j], sden);
             } else {
-              const float y = bit ? w * e : 0.f;
-              swe2 += bit ? y * e : 0.f;
+              const float e = bit ? xv[j] - xh[j] : 0.f;
+              const float t = e * sk;
+              const float y = fast_ex2(-(t * t)) * e;
+              swe2 = fmaf(y, e, swe2);
               xv[j] = y;
             }
           }
@@ -638,13 +665,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int j = 0; j < CPW; j += 2) ypk[j >> 1] = pack_bf16(xv[j], xv[j + 1]);
           if (!mbar_wait(&y_empty[yb], (uint32_t)(((it / NY) & 1) ^ 1), abort_flag)) { ok = false; break; }
-          unsigned char* yrow = sm + L.y + yb * Y_TILE + row * 128;
-#pragma unroll
-          for (int cc = 0; cc < CPW / 8; ++cc) {
-            const uint4 v = make_uint4(ypk[4 * cc], ypk[4 * cc + 1], ypk[4 * cc + 2], ypk[4 * cc + 3]);
-            *reinterpret_cast<uint4*>(yrow + ((((c0 >> 3) + cc) ^ (row & 7)) << 4)) = v;
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          // this warp's 32 residuals of row `row` -> 16 columns of Y buffer yb in TMEM
+          tmem_st16(tmem + lane_base + col_y + (uint32_t)(yb * Y_COLS + (c0 >> 1)), ypk);
+          tmem_wait_st();
+          tc_fence_before();
           mbar_arrive(&y_full[yb]);
         }
       }
