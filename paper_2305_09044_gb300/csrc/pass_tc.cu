@@ -35,9 +35,11 @@ constexpr int NEPI = 8;        // epilogue warps: 4 TMEM lane quarters x NGRP co
 constexpr int NGRP = NEPI / 4;
 constexpr int CPW = BN / NGRP; // columns of a tile handled by one epilogue warp
 static_assert(CPW == 32, "the epilogue loads 32 accumulator columns per warp and tile");
-constexpr int NTHREADS = 64 + 32 * NEPI + 32;   // operand producer, MMA, epilogue, data producer
+constexpr int NTHREADS = 64 + 32 * NEPI + 64;   // operand producer, GEMM-1 issuer, epilogue, data
+                                                // producer, GEMM-2 issuer
 constexpr int EPI_THREADS = 32 * NEPI;
 constexpr int XWARP = 2 + NEPI;                 // warp index of the data producer
+constexpr int G2WARP = 3 + NEPI;                // warp index of the GEMM-2 issuer
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
 // shared-memory carve-up (bytes, every buffer 1024-aligned).  Operands are stored as 64-wide
@@ -48,7 +50,7 @@ constexpr int SUB_S = BM * 64 * 2;             // 16 KB: one K sub-tile of a sta
 constexpr int SUB_T = BN * 64 * 2;             // 8 KB: one K sub-tile of a streaming operand
 
 constexpr int ND = 4;          // GEMM-1 accumulator buffers in TMEM (the MMA runs ahead of the epilogue)
-constexpr int NY = 2;          // weighted-residual (Y) buffers
+constexpr int NY = 4;          // weighted-residual (Y) buffers
 constexpr uint32_t TMEM_COLS = 512;
 
 template <int KP>
@@ -149,6 +151,27 @@ __device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, uint64
           su32(dst)),
       "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y)
       : "memory");
+}
+// The same copy with an L2 eviction-priority hint (a policy from createpolicy): the streamed
+// data tensor is read once per pass (evict first), the merged operands are re-read by every
+// CTA (evict last).
+__device__ __forceinline__ void tma_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                            uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(su32(dst)),
+      "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -331,10 +354,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int s = 0; s < TS; ++s) {
       mbar_init(&t_full[s], 1);
-      mbar_init(&t_empty[s], 1);
+      mbar_init(&t_empty[s], PASS2 ? 2 : 1);   // pass 2: both issuers read the tile
     }
     for (int b = 0; b < ND; ++b) {
-      mbar_init(&d_full[b], 1);
+      mbar_init(&d_full[b], PASS2 ? 2 : 1);    // pass 2: X_hat and the step product
       mbar_init(&d_empty[b], EPI_THREADS);
     }
     for (int b = 0; b < NY; ++b) {
@@ -342,10 +365,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&y_empty[b], 1);
     }
     mbar_init(s_full, 1);
-    mbar_init(s_empty, 1);
+    mbar_init(s_empty, PASS2 ? 2 : 1);       // pass 2: both issuers read the stationary tiles
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, EPI_THREADS);
-    mbar_init(mma_done, 1);
+    mbar_init(mma_done, 2);            // one commit from each issuer
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -369,6 +392,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0) {
     // ---------------------------------------------------------------- operand producer
     if (lane == 0) {
+      const uint64_t keep = policy_evict_last();
       int64_t it = 0;
       int g = 0;
       bool ok = true;
@@ -384,9 +408,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         s_phase = g & 1;
 #pragma unroll
         for (int sb = 0; sb < NSUB; ++sb) {
-          tma_2d(sm + L.s_hi + sb * SUB_S, &mS_hi, s_full, sb * 64, (int)(rb * BM));
-          tma_2d(sm + L.s_lo + sb * SUB_S, &mS_lo, s_full, sb * 64, (int)(rb * BM));
-          if (PASS2) tma_2d(sm + L.s_h + sb * SUB_S, &mS_h, s_full, sb * 64, (int)(rb * BM));
+          tma_2d_hint(sm + L.s_hi + sb * SUB_S, &mS_hi, s_full, sb * 64, (int)(rb * BM), keep);
+          tma_2d_hint(sm + L.s_lo + sb * SUB_S, &mS_lo, s_full, sb * 64, (int)(rb * BM), keep);
+          if (PASS2) tma_2d_hint(sm + L.s_h + sb * SUB_S, &mS_h, s_full, sb * 64, (int)(rb * BM), keep);
         }
         for (int64_t tc = u - rb * p.NT; u < seg_end; ++u, ++it, ++tc) {
           const int s = (int)(it % TS);
@@ -397,8 +421,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           last_phase[s] = (int)((it / TS) & 1);
 #pragma unroll
           for (int sb = 0; sb < NSUB; ++sb) {
-            tma_2d(tb + sb * SUB_T, &mT_hi, &t_full[s], sb * 64, t0);
-            tma_2d(tb + T_TILE + sb * SUB_T, &mT_lo, &t_full[s], sb * 64, t0);
+            tma_2d_hint(tb + sb * SUB_T, &mT_hi, &t_full[s], sb * 64, t0, keep);
+            tma_2d_hint(tb + T_TILE + sb * SUB_T, &mT_lo, &t_full[s], sb * 64, t0, keep);
           }
         }
       }
@@ -416,6 +440,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else if (warp == XWARP) {
     // ---------------------------------------------------------------- data producer
     if (lane == 0) {
+      const uint64_t stream_once = policy_evict_first();
       int64_t it = 0;
       bool ok = true;
       int last_phase[XS];
@@ -429,10 +454,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_expect_tx(&x_full[s], X_TILE);
         last_phase[s] = (int)((it / XS) & 1);
         if (ROWS) {
-          tma_2d(xb, &mX, &x_full[s], (int)(rb * BM), t0);
+          tma_2d_hint(xb, &mX, &x_full[s], (int)(rb * BM), t0, stream_once);
         } else {
-          tma_2d(xb, &mX, &x_full[s], t0, (int)(rb * BM));
-          tma_2d(xb + X_TILE / 2, &mX, &x_full[s], t0 + 32, (int)(rb * BM));
+          tma_2d_hint(xb, &mX, &x_full[s], t0, (int)(rb * BM), stream_once);
+          tma_2d_hint(xb + X_TILE / 2, &mX, &x_full[s], t0 + 32, (int)(rb * BM), stream_once);
         }
         if (++tc == p.NT) {
           tc = 0;
@@ -446,90 +471,115 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               if (mbar_try(&x_full[s], (uint32_t)last_phase[s])) break;
     }
   } else if (warp == 1) {
-    // ---------------------------------------------------------------- MMA issuer
+    // ---------------------------------------------------------------- GEMM-1 issuer
+    // X_hat tiles (and, in pass 2, the step-direction product) into the ND accumulator
+    // buffers, as soon as a tile's streaming operands and a free buffer are there
     if (lane == 0) {
       constexpr uint32_t ID1 = idesc_bf16(BM, BN);
-      constexpr uint32_t ID2 = idesc_bf16(BM, KPAD, 1);    // B = streaming tile, MN-major
-      const uint32_t a_hi = su32(sm + L.s_hi), a_lo = su32(sm + L.s_lo), a_h = su32(sm + L.s_h);
-      // Two streams of work, polled without blocking: GEMM 1 of tile i1 (as soon as its
-      // streaming operands, a free accumulator buffer and the segment's stationary operands
-      // are there) and GEMM 2 of tile i2 < i1 (as soon as the epilogue has written its Y).
-      // A segment is the run of tiles of one stationary block.
-      const int64_t ntiles = u_end - u_begin;
-      const int64_t first_end = imin(u_end, (u_begin / p.NT + 1) * p.NT);
-      int64_t i1 = 0, u1 = u_begin, seg1_end = first_end;
-      int64_t i2 = 0, u2 = u_begin, seg2_end = first_end;
-      int g1 = 0, g2 = 0;
-      bool need_s = true, first2 = true, ok = true;
-      uint32_t idle = 0;
-      while (ok && (PASS2 ? i1 < ntiles : i2 < ntiles)) {
-        bool moved = false;
-        if (i1 < ntiles) {
-          const int s = (int)(i1 % TS), b = (int)(i1 & (ND - 1));
-          if ((!need_s || mbar_test(s_full, (uint32_t)(g1 & 1))) &&
-              mbar_test(&t_full[s], (uint32_t)((i1 / TS) & 1)) &&
-              mbar_test(&d_empty[b], (uint32_t)(((i1 / ND) & 1) ^ 1))) {
-            tc_fence_after();
-            const uint32_t b_hi = su32(sm + L.t0 + s * 2 * T_TILE), b_lo = b_hi + T_TILE;
+      // shared-memory descriptors built once; a K step only adds its byte offset / 16 to the
+      // start-address field (addresses stay below 2^18, so the 14-bit field cannot carry)
+      const uint64_t dA_hi = sdesc(su32(sm + L.s_hi)), dA_lo = sdesc(su32(sm + L.s_lo));
+      int64_t it = 0;
+      int g = 0;
+      bool ok = true;
+      for (int64_t u = u_begin; u < u_end && ok; ++g) {
+        const int64_t rb = u / p.NT;
+        const int64_t seg_end = imin(u_end, (rb + 1) * p.NT);
+        if (!mbar_wait(s_full, (uint32_t)(g & 1), abort_flag)) { ok = false; break; }
+        for (; u < seg_end; ++u, ++it) {
+          const int s = (int)(it % TS), b = (int)(it & (ND - 1));
+          if (!mbar_wait(&t_full[s], (uint32_t)((it / TS) & 1), abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&d_empty[b], (uint32_t)(((it / ND) & 1) ^ 1), abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint64_t dB_hi = sdesc(su32(sm + L.t0 + s * 2 * T_TILE));
+          const uint64_t dB_lo = dB_hi + (uint64_t)(T_TILE >> 4);
+          const uint32_t d1 = tmem + (uint32_t)(b * BN);
 #pragma unroll
-            for (int kk = 0; kk < KPAD / 16; ++kk) {
-              // K step kk: sub-tile kk / 4, 32-byte step kk % 4 inside its swizzle atom
-              const uint32_t ka = (uint32_t)((kk >> 2) * SUB_S + (kk & 3) * 32);
-              const uint32_t kb = (uint32_t)((kk >> 2) * SUB_T + (kk & 3) * 32);
-              tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_hi + ka), sdesc(b_hi + kb), ID1, kk > 0);
-              tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_hi + ka), sdesc(b_lo + kb), ID1, 1);
-              tc_mma(tmem + (uint32_t)(b * BN), sdesc(a_lo + ka), sdesc(b_hi + kb), ID1, 1);
-              if (PASS2)
-                tc_mma(tmem + (uint32_t)((ND + b) * BN), sdesc(a_h + ka), sdesc(b_hi + kb), ID1, kk > 0);
-            }
-            tc_commit(&d_full[b]);
-            if (PASS2) tc_commit(&t_empty[s]);
-            need_s = false;
-            ++i1;
-            if (++u1 == seg1_end) {
-              tc_commit(s_empty);     // the segment's GEMM-1 MMAs: its stationary operands may go
-              ++g1;
-              need_s = true;
-              seg1_end = imin(u_end, seg1_end + p.NT);
-            }
-            moved = true;
+          for (int kk = 0; kk < KPAD / 16; ++kk) {
+            // K step kk: sub-tile kk / 4, 32-byte step kk % 4 inside its swizzle atom
+            const uint64_t ka = (uint64_t)(((kk >> 2) * SUB_S + (kk & 3) * 32) >> 4);
+            const uint64_t kb = (uint64_t)(((kk >> 2) * SUB_T + (kk & 3) * 32) >> 4);
+            tc_mma(d1, dA_hi + ka, dB_hi + kb, ID1, kk > 0);
+            tc_mma(d1, dA_hi + ka, dB_lo + kb, ID1, 1);
+            tc_mma(d1, dA_lo + ka, dB_hi + kb, ID1, 1);
           }
+          tc_commit(&d_full[b]);
+          if (PASS2) tc_commit(&t_empty[s]);   // pass 1: released by the GEMM-2 issuer
         }
-        if (!PASS2 && i2 < i1) {
-          const int s = (int)(i2 % TS), yb = (int)(i2 & (NY - 1));
-          if ((!first2 || g2 == 0 || mbar_test(acc_empty, (uint32_t)((g2 - 1) & 1))) &&
-              mbar_test(&y_full[yb], (uint32_t)((i2 / NY) & 1))) {
-            tc_fence_after();
-            // GEMM 2: T += Y * S_str, B read MN-major from the tile's hi operand
-            const uint32_t tp = su32(sm + L.t0 + s * 2 * T_TILE);
-#pragma unroll
-            for (int kk = 0; kk < BN / 16; ++kk)
-              tc_mma_ta(tmem + col_acc, tmem + col_y + (uint32_t)(yb * Y_COLS + kk * 8),
-                        sdesc_mn(tp + kk * 2048, BN * 128), ID2, (first2 && kk == 0) ? 0u : 1u);
-            tc_commit(&y_empty[yb]);
-            tc_commit(&t_empty[s]);
-            first2 = false;
-            ++i2;
-            if (++u2 == seg2_end) {
-              tc_commit(acc_full);
-              ++g2;
-              first2 = true;
-              seg2_end = imin(u_end, seg2_end + p.NT);
-            }
-            moved = true;
-          }
-        }
-        if (moved) {
-          idle = 0;
-        } else if (++idle >= WAIT_LIMIT || *abort_flag) {
-          *abort_flag = 1;
-          ok = false;
-        }
+        if (!ok) break;
+        tc_commit(s_empty);                     // the segment's stationary operands may go
       }
       // every issued MMA has finished before TMEM can be released
       tc_commit(mma_done);
       for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
         if (mbar_try(mma_done, 0)) break;
+    }
+  } else if (warp == G2WARP) {
+    // ---------------------------------------------------------------- GEMM-2 issuer
+    // T += Y S_str per tile once the epilogue has written Y (which it does after reading the
+    // tile's GEMM-1 result, so GEMM 1 of the tile has completed); releases the tile's
+    // streaming operands and Y buffer; a segment's T is complete after its last tile
+    if (lane == 0 && PASS2) {
+      // pass 2: D2 = S_h S_str^T (plain BF16) into the second accumulator of each buffer slot
+      constexpr uint32_t ID1 = idesc_bf16(BM, BN);
+      const uint64_t dA_h = sdesc(su32(sm + L.s_h));
+      int64_t it = 0;
+      int g = 0;
+      bool ok = true;
+      for (int64_t u = u_begin; u < u_end && ok; ++g) {
+        const int64_t rb = u / p.NT;
+        const int64_t seg_end = imin(u_end, (rb + 1) * p.NT);
+        if (!mbar_wait(s_full, (uint32_t)(g & 1), abort_flag)) { ok = false; break; }
+        for (; u < seg_end; ++u, ++it) {
+          const int s = (int)(it % TS), b = (int)(it & (ND - 1));
+          if (!mbar_wait(&t_full[s], (uint32_t)((it / TS) & 1), abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&d_empty[b], (uint32_t)(((it / ND) & 1) ^ 1), abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint64_t dB_hi = sdesc(su32(sm + L.t0 + s * 2 * T_TILE));
+          const uint32_t d2 = tmem + (uint32_t)((ND + b) * BN);
+#pragma unroll
+          for (int kk = 0; kk < KPAD / 16; ++kk) {
+            const uint64_t ka = (uint64_t)(((kk >> 2) * SUB_S + (kk & 3) * 32) >> 4);
+            const uint64_t kb = (uint64_t)(((kk >> 2) * SUB_T + (kk & 3) * 32) >> 4);
+            tc_mma(d2, dA_h + ka, dB_hi + kb, ID1, kk > 0);
+          }
+          tc_commit(&d_full[b]);
+          tc_commit(&t_empty[s]);
+        }
+        if (!ok) break;
+        tc_commit(s_empty);
+      }
+    }
+    if (lane == 0) {
+      if (!PASS2) {
+        constexpr uint32_t ID2 = idesc_bf16(BM, KPAD, 1);    // B = streaming tile, MN-major
+        int64_t it = 0;
+        int g = 0;
+        bool ok = true;
+        for (int64_t u = u_begin; u < u_end && ok; ++g) {
+          const int64_t rb = u / p.NT;
+          const int64_t seg_end = imin(u_end, (rb + 1) * p.NT);
+          bool first2 = true;
+          for (; u < seg_end; ++u, ++it) {
+            const int s = (int)(it % TS), yb = (int)(it & (NY - 1));
+            if (first2 && g > 0 && !mbar_wait(acc_empty, (uint32_t)((g - 1) & 1), abort_flag)) { ok = false; break; }
+            if (!mbar_wait(&y_full[yb], (uint32_t)((it / NY) & 1), abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint64_t dT = sdesc_mn(su32(sm + L.t0 + s * 2 * T_TILE), BN * 128);
+            const uint32_t ay = tmem + col_y + (uint32_t)(yb * Y_COLS);
+#pragma unroll
+            for (int kk = 0; kk < BN / 16; ++kk)
+              tc_mma_ta(tmem + col_acc, ay + (uint32_t)(kk * 8), dT + (uint64_t)(kk * (2048 >> 4)), ID2,
+                        (first2 && kk == 0) ? 0u : 1u);
+            tc_commit(&y_empty[yb]);
+            tc_commit(&t_empty[s]);
+            first2 = false;
+          }
+          if (!ok) break;
+          tc_commit(acc_full);
+        }
+      }
+      tc_commit(mma_done);
     }
   } else {
     // ---------------------------------------------------------------- epilogue (NEPI warps)
