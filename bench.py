@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--precision", default=None, choices=[None, "bf16", "fp32", "fp64"])
     ap.add_argument("--no-converge", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the row-sampling variant's measurement")
     ap.add_argument("--converge-iters", type=int, default=60)
     return ap.parse_args()
 
@@ -293,7 +294,8 @@ def run_ours(args, rank, world, local):
            "roofline": roofline(prec, prof, w), "e2e": e2e, "gpu_launches": launches, "clocks": ck}
     if rank == 0 and not args.no_converge:
         out["time_to_rel_err_1e-3"] = converge(t, Xt, w, args.converge_iters, torch)
-    out["row_sampling"] = row_sampling(t, w, torch)
+    if not args.no_rows:
+        out["row_sampling"] = row_sampling(t, w, torch)
 
     # comparison path on the same device data (FP32 CUDA-core passes)
     for other in precs[1:]:

@@ -661,6 +661,13 @@ trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
     CK(launch_tc_prep((const float*)h->Sh.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bSh.p, nullptr, h->stream),
        "bf16 step operands");
   }
+  // the side stream has joined: the line-search pass takes every SM (its per-CTA partials are
+  // summed by the update kernel over the same count)
+  {
+    const int64_t units = ((sp.P_stat + tc_bm() - 1) / tc_bm()) * ((sp.P_strm + tc_bn() - 1) / tc_bn());
+    x->tcG = (int)imin(h->num_sms, units);
+    TRY(ensure(h, h->stat_part, sizeof(double) * 8 * (size_t)x->tcG));
+  }
   prof_begin(h);
   CK(launch_pass_tc(sp.rows, true, (const __nv_bfloat16*)x->bShi.p, (const __nv_bfloat16*)x->bSlo.p,
                     (const __nv_bfloat16*)x->bSh.p, (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p,
@@ -669,10 +676,8 @@ trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
                     (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, x->tcG, false, h->stream),
      "tensor-core data pass 2");
   prof_end(h, 1);
-  PScope ps(h, P_REDUCE);
-  double* s2 = (double*)x->stat_sum2.p;
-  CK(launch_reduce_stats((const double*)h->stat_part.p, x->tcG, s2, h->dstatus, h->stream), "reduce den");
-  *den = s2 + 6;
+  // the line-search denominator is summed from the per-CTA partials by the update kernel
+  *den = nullptr;
   return TRD_OK;
 }
 
@@ -908,9 +913,11 @@ trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int
     den = s2 + 6;
   }
   PScope psu(h, P_UPDATE);
-  CK(launch_eta(h->scal + S_NUM, den, eta_fixed, h->dstatus, h->scal + S_ETA, eta_slot, h->stream),
-     "step size");
-  CK(launch_axpy_core(h->Z[k], hh, n, h->scal + S_ETA, h->stream), "core update");
+  const bool from_parts = eta_fixed <= 0 && den == nullptr;   // tensor-core line search
+  CK(launch_step_update(h->Z[k], hh, n, h->scal + S_NUM, from_parts ? (const double*)h->stat_part.p : nullptr,
+                        from_parts ? X_(h)->tcG : 0, den, eta_fixed, h->dstatus, h->scal + S_ETA, eta_slot,
+                        h->stream),
+     "step size and core update");
   h->ver[k]++;
   TRY(refresh_E(h, k));
   h->grad_k = -1;

@@ -590,6 +590,53 @@ cudaError_t launch_eta(const double* num, const double* den, double fixed_eta, i
   return cudaGetLastError();
 }
 
+// Step size and update in one launch: every block forms eta = <d,h> / den (den summed from the
+// line-search pass's per-CTA partials in the same fixed order as the statistics reduction,
+// field 6, or read from `den`), forced to 0 on a flagged or non-finite step; block 0 records
+// it; then Z_k <- Z_k + eta fold(h) (update-sign reading of Eq. updatessd / Eq. ftrbcn).
+__global__ void k_step_update(double* __restrict__ Z, const double* __restrict__ h, int64_t n,
+                              const double* __restrict__ num, const double* __restrict__ part, int ctas,
+                              const double* __restrict__ den_in, double fixed_eta, int* dstatus,
+                              double* __restrict__ eta_out, double* __restrict__ eta_slot) {
+  __shared__ double s_eta;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double dn = 0.0;
+    if (part) {
+      for (int c = lane; c < ctas; c += 32) dn += part[(int64_t)c * 8 + 6];
+      for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(0xffffffffu, dn, o);
+    } else if (den_in) {
+      dn = *den_in;
+    }
+    if (lane == 0) {
+      double eta = fixed_eta > 0 ? fixed_eta : (dn > 0 ? *num / dn : 0.0);
+      const bool finite = isfinite(eta);
+      if (!finite) eta = 0.0;
+      if (*dstatus & (DEV_SINGULAR | DEV_NONFINITE)) eta = 0.0;
+      if (blockIdx.x == 0) {
+        if (!finite) atomicOr(dstatus, (int)DEV_NONFINITE);
+        *eta_out = eta;
+        if (eta_slot) *eta_slot = eta;
+      }
+      s_eta = eta;
+    }
+  }
+  __syncthreads();
+  const double e = s_eta;
+  if (e == 0.0) return;   // a rejected step leaves the core untouched (h may be non-finite)
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    Z[i] = fma(e, h[i], Z[i]);
+}
+
+cudaError_t launch_step_update(double* Z, const double* h, int64_t n, const double* num, const double* part, int ctas,
+                               const double* den, double fixed_eta, int* dstatus, double* eta, double* eta_slot,
+                               cudaStream_t st) {
+  k_step_update<<<(unsigned)imin((n + 255) / 256, 1024), 256, 0, st>>>(Z, h, n, num, part, ctas, den, fixed_eta,
+                                                                      dstatus, eta, eta_slot);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // Z_k <- Z_k + eta fold(h)   (update-sign reading of Eq. updatessd / Eq. ftrbcn)
 __global__ void k_axpy_core(double* __restrict__ Z, const double* __restrict__ h, int64_t n,
                             const double* __restrict__ eta) {

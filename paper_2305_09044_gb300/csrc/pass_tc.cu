@@ -869,23 +869,34 @@ __global__ void k_mask_transpose(const uint32_t* __restrict__ M, int64_t P_in, i
   }
 }
 
+// T of stationary block rb = sum of the partial slots c + rb of the CTAs c whose unit range
+// [c U / G, (c + 1) U / G) meets the block's units [rb NT, (rb + 1) NT), in CTA order.  One
+// block per (stationary block, 256 entries of its BM x Kp tile); the CTA range is found once
+// per block.
 __global__ void k_reduce_slots(const float* __restrict__ part, int64_t RB, int64_t NT, int G, int64_t P_stat,
                                int Kp, double* __restrict__ out) {
-  const int64_t U = RB * NT;
-  const int64_t n = P_stat * Kp;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t srow = e / Kp;
-    const int k = (int)(e % Kp);
-    const int64_t rb = srow / BM, r = srow % BM;
-    const int64_t ulo = rb * NT, uhi = (rb + 1) * NT;
-    // CTAs whose unit range [cU/G, (c+1)U/G) meets [ulo, uhi)
+  __shared__ int64_t s_c0, s_c1;
+  const int64_t rb = blockIdx.x;
+  if (threadIdx.x == 0) {
+    const int64_t U = RB * NT, ulo = rb * NT, uhi = (rb + 1) * NT;
     int64_t c0 = (ulo * G) / U;
     while (c0 > 0 && (c0 * U) / G > ulo) --c0;
     while (((c0 + 1) * U) / G <= ulo) ++c0;
-    double s = 0.0;
-    for (int64_t cc = c0; cc < G && (cc * U) / G < uhi; ++cc) s += (double)part[((cc + rb) * BM + r) * Kp + k];
-    out[e] = s;
+    int64_t c1 = c0;
+    while (c1 < G && (c1 * U) / G < uhi) ++c1;
+    s_c0 = c0;
+    s_c1 = c1;
   }
+  __syncthreads();
+  const int64_t c0 = s_c0, c1 = s_c1;
+  const int e = blockIdx.y * blockDim.x + threadIdx.x;
+  if (e >= BM * Kp) return;
+  const int r = e / Kp, k = e % Kp;
+  const int64_t srow = rb * BM + r;
+  if (srow >= P_stat) return;
+  double s = 0.0;
+  for (int64_t cc = c0; cc < c1; ++cc) s += (double)part[((cc + rb) * BM + r) * Kp + k];
+  out[srow * Kp + k] = s;
 }
 
 }  // namespace tc
@@ -962,8 +973,8 @@ cudaError_t launch_mask_transpose(const uint32_t* M, int64_t P_in, int64_t P_out
 
 cudaError_t launch_reduce_slots(const float* part, int64_t RB, int64_t NT, int G, int64_t P_stat, int Kp,
                                 double* out, cudaStream_t st) {
-  const int64_t n = P_stat * Kp;
-  tc::k_reduce_slots<<<(unsigned)imin((n + 255) / 256, 8192), 256, 0, st>>>(part, RB, NT, G, P_stat, Kp, out);
+  const dim3 grid((unsigned)RB, (unsigned)((tc::BM * Kp + 255) / 256));
+  tc::k_reduce_slots<<<grid, 256, 0, st>>>(part, RB, NT, G, P_stat, Kp, out);
   note_launch();
   return cudaGetLastError();
 }

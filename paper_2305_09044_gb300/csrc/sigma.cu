@@ -451,8 +451,9 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_floats(const float* __restr
 
 // First kernel of the tensor rule: residuals at the probe entries from the merged subchains
 // of the full tensor, x_hat = sum_kappa A[a][kappa] C[b][kappa] (Thm. 1 with the ring cut in two).
-// Eight lanes per probe (each a strided part of the length-Kp dot product, then a 3-step
-// shuffle sum); probe m is described by pa[m] (inner index, -1 when unobserved), pb[m] and px[m].
+// One lane per probe (probe m is described by pa[m] (inner index, -1 when unobserved), pb[m]
+// and px[m]); each lane streams its two rows in chunks of 16 values with all loads of a chunk
+// issued before its FMAs, so a warp keeps many independent L2 reads in flight.
 template <typename T, bool VEC4>
 __global__ void __launch_bounds__(kSelThreads)
     k_sel_probe(const T* __restrict__ A, const T* __restrict__ C, int Kp, const int32_t* __restrict__ pa,
@@ -461,48 +462,67 @@ __global__ void __launch_bounds__(kSelThreads)
   __shared__ unsigned int h0[256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) h0[i] = 0;
   __syncthreads();
-  const int lane = threadIdx.x & 31, sub = lane & 7;
+  const int lane = threadIdx.x & 31;
   double c = 0, se = 0, sx = 0;
-  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 3;
-  for (int64_t g0 = (((int64_t)blockIdx.x * blockDim.x) >> 3) + ((threadIdx.x & ~31) >> 3); g0 < n; g0 += stride) {
-    const int64_t m = g0 + (lane >> 3);           // this group's probe
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t m0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); m0 < n; m0 += stride) {
+    const int64_t m = m0 + lane;
     const bool live = m < n;
     const int32_t a = live ? pa[m] : -1;
     const bool obs = a >= 0;
+    const int32_t bi = obs ? pb[m] : 0;
     const float xf = obs ? px[m] : 0.f;
-    T part = T(0);
+    T p0 = T(0), p1 = T(0);
     if (obs) {
       const T* Ar = A + (int64_t)a * Kp;
-      const T* Cr = C + (int64_t)pb[m] * Kp;
+      const T* Cr = C + (int64_t)bi * Kp;
       if constexpr (VEC4) {
-        // 16-byte loads (Kp a multiple of 4): lane sub takes float4 chunks sub, sub + 8, ...
         const float4* A4 = reinterpret_cast<const float4*>(Ar);
         const float4* C4 = reinterpret_cast<const float4*>(Cr);
-        for (int v = sub; v < (Kp >> 2); v += 8) {
-          const float4 x = A4[v], y = C4[v];
-          part = fma(x.x, y.x, part);
-          part = fma(x.y, y.y, part);
-          part = fma(x.z, y.z, part);
-          part = fma(x.w, y.w, part);
+        const int nv = Kp >> 2;
+        for (int v0 = 0; v0 < nv; v0 += 4) {
+          float4 xa[4], xc[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const bool in = v0 + q < nv;
+            xa[q] = in ? A4[v0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            xc[q] = in ? C4[v0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            p0 = fma(xa[q].x, xc[q].x, p0);
+            p1 = fma(xa[q].y, xc[q].y, p1);
+            p0 = fma(xa[q].z, xc[q].z, p0);
+            p1 = fma(xa[q].w, xc[q].w, p1);
+          }
         }
       } else {
-#pragma unroll 4
-        for (int k = sub; k < Kp; k += 8) part = fma(Ar[k], Cr[k], part);
+        for (int k0 = 0; k0 < Kp; k0 += 8) {
+          T xa[8], xc[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const bool in = k0 + q < Kp;
+            xa[q] = in ? Ar[k0 + q] : T(0);
+            xc[q] = in ? Cr[k0 + q] : T(0);
+          }
+#pragma unroll
+          for (int q = 0; q < 8; q += 2) {
+            p0 = fma(xa[q], xc[q], p0);
+            p1 = fma(xa[q + 1], xc[q + 1], p1);
+          }
+        }
       }
     }
-    part += __shfl_xor_sync(0xffffffffu, part, 4);
-    part += __shfl_xor_sync(0xffffffffu, part, 2);
-    part += __shfl_xor_sync(0xffffffffu, part, 1);
     double e = 0.0, x2 = 0.0;
     bool valid = false;
-    if (obs && sub == 0) {
+    if (obs) {
       const T x = (T)xf;
-      const T et = x - part;
+      const T et = x - (p0 + p1);
       valid = isfinite((double)et);
       e = (double)et;
       x2 = (double)x * (double)x;
     }
-    sel_consume(valid, e, x2, keys, m, live && sub == 0, h0, c, se, sx);
+    sel_consume(valid, e, x2, keys, m, live, h0, c, se, sx);
   }
   __syncthreads();
   sel_first_finish(work, h0, c, se, sx);
@@ -568,8 +588,8 @@ cudaError_t launch_probe_sigma_merged(const void* A, const void* C, bool fp64, i
                                       double* sigma_out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(double) * kPartsWord, st);
   if (e != cudaSuccess) return e;
-  // eight lanes per probe, about four probes per lane group
-  const int nb = (int)imax(1, imin(kSelBlocks, (n * 8 + 4 * kSelThreads - 1) / (4 * kSelThreads)));
+  // one lane per probe, a few probes per lane
+  const int nb = (int)imax(1, imin(kSelBlocks, (n + 2 * kSelThreads - 1) / (2 * kSelThreads)));
   if (fp64)
     k_sel_probe<double, false><<<nb, kSelThreads, 0, st>>>((const double*)A, (const double*)C, Kp, pa, pb, px, n,
                                                            keys, work);
