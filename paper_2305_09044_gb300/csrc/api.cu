@@ -95,6 +95,7 @@ struct Extra {
   DevBuf probe_a, probe_b, probe_x;   // adaptive-width probe: inner / outer index, data
   DevBuf dotpart, solve_ctr;          // per-row parts of <d, h>, completion counter
   DevBuf probe_cand;                  // selection candidates of the adaptive width
+  SlotSrc slots;                      // partial slots of the last tensor-core pass 1
   // uniform row sampling (trd_sample_rows): J multi-indices of the modes other than row_k
   bool row_view = false;
   int row_k = -1;
@@ -485,9 +486,17 @@ trd_status build_halves(trd_handle* h, int k) {
   const Split& sp = h->split;
   const int hs = k < sp.c ? 0 : 1;
   const HalfTag want_st = half_tag(h, hs, sp), want_str = half_tag(h, 1 - hs, sp);
+  // BF16 handles: the tensor-core operands (hi/lo, KP-wide rows) are written by the same
+  // merge and trade roles together with the FP32 halves
+  const int KP = h->prec == TRD_BF16 ? tc_kpad(sp.Kp) : 0;
   if (x->tagSst == want_str || x->tagSstr == want_st) {
     std::swap(h->Sst, h->Sstr);
     std::swap(x->tagSst, x->tagSstr);
+    if (KP) {
+      std::swap(x->bShi, x->bThi);
+      std::swap(x->bSlo, x->bTlo);
+      std::swap(x->tagBst, x->tagBstr);
+    }
   }
   const size_t e = elt(h);
   const bool dbl = is_fp64(h);
@@ -497,20 +506,36 @@ trd_status build_halves(trd_handle* h, int k) {
   TRY(ensure(h, h->Sstr, e * sp.P_strm * sp.Kp));
   if (h->Sst.p != pst) x->tagSst.valid = false;
   if (h->Sstr.p != pstr) x->tagSstr.valid = false;
+  if (KP) {
+    const size_t b2 = sizeof(__nv_bfloat16);
+    const void* q[4] = {x->bShi.p, x->bSlo.p, x->bThi.p, x->bTlo.p};
+    TRY(ensure(h, x->bShi, b2 * sp.P_stat * KP));
+    TRY(ensure(h, x->bSlo, b2 * sp.P_stat * KP));
+    TRY(ensure(h, x->bThi, b2 * sp.P_strm * KP));
+    TRY(ensure(h, x->bTlo, b2 * sp.P_strm * KP));
+    if (x->bShi.p != q[0] || x->bSlo.p != q[1]) x->tagBst.valid = false;
+    if (x->bThi.p != q[2] || x->bTlo.p != q[3]) x->tagBstr.valid = false;
+  }
   const View& v = h->view;
   const Chain inner = make_chain(h, v, 0, sp.c), outer = make_chain(h, v, sp.c, h->N);
-  if (!(x->tagSst == want_st)) {
-    CK(launch_chain(hs == 0 ? inner : outer, h->Sst.p, dbl, hs == 1, sp.Kp, h->stream), "merge stationary half");
+  if (!(x->tagSst == want_st) || (KP && !(x->tagBst == want_st))) {
+    CK(launch_chain(hs == 0 ? inner : outer, h->Sst.p, dbl, hs == 1, sp.Kp, h->stream,
+                    KP ? (__nv_bfloat16*)x->bShi.p : nullptr, KP ? (__nv_bfloat16*)x->bSlo.p : nullptr, KP),
+       "merge stationary half");
     x->tagSst = want_st;
+    if (KP) x->tagBst = want_st;
   }
-  if (!(x->tagSstr == want_str)) {
-    CK(launch_chain(hs == 0 ? outer : inner, h->Sstr.p, dbl, hs == 0, sp.Kp, h->stream), "merge streaming half");
+  if (!(x->tagSstr == want_str) || (KP && !(x->tagBstr == want_str))) {
+    CK(launch_chain(hs == 0 ? outer : inner, h->Sstr.p, dbl, hs == 0, sp.Kp, h->stream,
+                    KP ? (__nv_bfloat16*)x->bThi.p : nullptr, KP ? (__nv_bfloat16*)x->bTlo.p : nullptr, KP),
+       "merge streaming half");
     x->tagSstr = want_str;
+    if (KP) x->tagBstr = want_str;
   }
   return TRD_OK;
 }
 
-trd_status build_merged(trd_handle* h, int k, bool with_h) {
+trd_status build_merged(trd_handle* h, int k, bool with_h, __nv_bfloat16* bf16_h = nullptr, int kpad = 0) {
   const View& v = h->view;
   const Split& sp = h->split;
   const int c = sp.c, Kp = sp.Kp;
@@ -525,6 +550,12 @@ trd_status build_merged(trd_handle* h, int k, bool with_h) {
   }
   const Chain inner = make_chain(h, v, 0, c, k, (const double*)h->h.p);
   const Chain outer = make_chain(h, v, c, h->N, k, (const double*)h->h.p);
+  if (bf16_h) {
+    // tensor-core path: only the BF16 operand of the step direction is needed
+    if (sp.rows) CK(launch_chain(inner, nullptr, dbl, false, Kp, h->stream, bf16_h, nullptr, kpad), "merge A_h");
+    else CK(launch_chain(outer, nullptr, dbl, true, Kp, h->stream, bf16_h, nullptr, kpad), "merge C_h");
+    return TRD_OK;
+  }
   TRY(ensure(h, h->Sh, e * sp.P_stat * Kp));
   if (sp.rows) CK(launch_chain(inner, h->Sh.p, dbl, false, Kp, h->stream), "merge A_h");
   else CK(launch_chain(outer, h->Sh.p, dbl, true, Kp, h->stream), "merge C_h");
@@ -641,8 +672,12 @@ trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
      "tensor-core data pass 1");
   prof_end(h, 0);
   PScope ps(h, P_REDUCE);
-  CK(launch_reduce_slots((const float*)h->Tpart.p, RB, NT, G, sp.P_stat, sp.Kp, (double*)h->Tsum.p, h->stream),
-     "reduce contraction");
+  // the back-contraction sums the partial slots itself; the row-sampling gradient is the
+  // reduced contraction, so it is formed here
+  x->slots = SlotSrc{(const float*)h->Tpart.p, RB, NT, (int64_t)tc_bm(), G};
+  if (x->row_view)
+    CK(launch_reduce_slots((const float*)h->Tpart.p, RB, NT, G, sp.P_stat, sp.Kp, (double*)h->Tsum.p, h->stream),
+       "reduce contraction");
   CK(launch_reduce_stats((const double*)h->stat_part.p, G, (double*)h->stat_sum.p, h->dstatus, h->stream),
      "reduce statistics");
   h->ctas = G;
@@ -656,10 +691,14 @@ trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
     PScope ps(h, P_MERGE);
     TRY(build_halves(h, k));      // normally cached: restores the roles of core k
     TRY(tc_operands(h));
-    TRY(build_merged(h, k, true));
     TRY(ensure(h, x->bSh, sizeof(__nv_bfloat16) * sp.P_stat * tc_kpad(sp.Kp)));
-    CK(launch_tc_prep((const float*)h->Sh.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bSh.p, nullptr, h->stream),
-       "bf16 step operands");
+    if (x->row_view) {
+      TRY(build_merged(h, k, true));
+      CK(launch_tc_prep((const float*)h->Sh.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bSh.p, nullptr, h->stream),
+         "bf16 step operands");
+    } else {
+      TRY(build_merged(h, k, true, (__nv_bfloat16*)x->bSh.p, tc_kpad(sp.Kp)));
+    }
   }
   // the side stream has joined: the line-search pass takes every SM (its per-CTA partials are
   // summed by the update kernel over the same count)
@@ -764,7 +803,8 @@ trd_status run_gradient(trd_handle* h, int k) {
   if (nsplit > 1) TRY(ensure(h, h->dpart, sizeof(double) * nsplit * h->I[k] * K));
   CK(launch_backcontract(h->Tsum.p, sp.Kp, sp.rows, mr, mc, pre.n > 0 ? h->pre.p : nullptr, n_pre,
                          post.n > 0 ? h->post.p : nullptr, n_post, h->I[k], rk, rk1, (double*)h->dpart.p,
-                         (int)nsplit, (double*)h->d.p, dbl, h->stream),
+                         (int)nsplit, (double*)h->d.p, dbl, h->stream,
+                         h->prec == TRD_BF16 ? &X_(h)->slots : nullptr),
      "back-contraction");
   h->grad_k = k;
   return TRD_OK;

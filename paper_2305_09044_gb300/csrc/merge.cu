@@ -9,10 +9,13 @@ namespace trd {
 
 // ------------------------------------------------------------------ chain products
 // One warp per multi-index p: M = Z_{m0}(i_0) Z_{m1}(i_1) ... (Def. 2 core merging), built
-// in shared memory (FP64), then written row-major (transposed = false) or column-major
-// (transposed = true) into row p of `out` (stride ld).
+// in shared memory, then written row-major (transposed = false) or column-major
+// (transposed = true) into row p of `out` (stride ld; skipped when out is null) and, when
+// `hi` is given, as the BF16 tensor-core operand: hi = bf16(v), lo = bf16(v - hi) (lo
+// optional), rows of kpad entries with zero padding.
 template <typename Tc, typename Tout>
-__global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_t ld, int cap) {
+__global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_t ld, int cap,
+                        __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int kpad) {
   extern __shared__ __align__(16) unsigned char smem_chain[];
   const int warps = blockDim.x >> 5;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -55,19 +58,30 @@ __global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_
       C = Cj;
       __syncwarp();
     }
-    Tout* o = out + p * ld;
     for (int e = lane; e < R0 * C; e += 32) {
       const int a = e / C, b = e % C;
-      if (transposed) o[b * R0 + a] = (Tout)Mb[e];
-      else o[e] = (Tout)Mb[e];
+      const int pos = transposed ? b * R0 + a : e;
+      const Tout v = (Tout)Mb[e];
+      if (out) out[p * ld + pos] = v;
+      if (hi) {
+        const float f = (float)v;
+        const __nv_bfloat16 vh = __float2bfloat16_rn(f);
+        hi[p * kpad + pos] = vh;
+        if (lo) lo[p * kpad + pos] = __float2bfloat16_rn(f - __bfloat162float(vh));
+      }
     }
+    if (hi)
+      for (int e = R0 * C + lane; e < kpad; e += 32) {
+        hi[p * kpad + e] = __float2bfloat16_rn(0.f);
+        if (lo) lo[p * kpad + e] = __float2bfloat16_rn(0.f);
+      }
     __syncwarp();
   }
 }
 
 // out_double: FP64 products and output; otherwise FP32 products and output.
 cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool transposed,
-                         int64_t ld, cudaStream_t st) {
+                         int64_t ld, cudaStream_t st, __nv_bfloat16* hi, __nv_bfloat16* lo, int kpad) {
   if (ch.n <= 0 || ch.count <= 0) return cudaSuccess;
   int cap = 1;
   for (int j = 0; j < ch.n; ++j) {
@@ -81,12 +95,14 @@ cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool trans
     const size_t smem = (size_t)warps * 3 * cap * sizeof(double);
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_chain<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_chain<double, double><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (double*)out, transposed, ld, cap);
+    k_chain<double, double><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (double*)out, transposed, ld, cap,
+                                                                       hi, lo, kpad);
   } else {
     const size_t smem = (size_t)warps * 3 * cap * sizeof(float);
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_chain<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_chain<float, float><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (float*)out, transposed, ld, cap);
+    k_chain<float, float><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (float*)out, transposed, ld, cap, hi,
+                                                                     lo, kpad);
   }
   note_launch();
   return cudaGetLastError();
@@ -99,8 +115,11 @@ cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool trans
 // (ROWS case: Ct[delta, gamma] = T[s][gamma r_c + delta]; COLS case: At[gamma, delta] =
 // T[s][gamma r_c + delta]) and s = pre + n_pre (i_k + I_k post).  Pre / Post are the
 // products of the cores between the block boundary and core k (identity when empty).
+// The reduced contraction row s is read from Tm (FP64, [P_stat][Kp]) or, when sl.part is
+// given, summed in CTA order from the tensor-core pass's partial slots (FP32, the sum of slots
+// c + rb over the CTAs c whose unit range meets stationary block rb = s / BM).
 template <typename T>
-__global__ void k_backcontract(const double* __restrict__ Tm, int Kp, int rows_case, int mr, int mc,
+__global__ void k_backcontract(const double* __restrict__ Tm, SlotSrc sl, int Kp, int rows_case, int mr, int mc,
                                const T* __restrict__ pre, int64_t n_pre,
                                const T* __restrict__ post, int64_t n_post, int64_t Ik,
                                int rk, int rk1, int64_t pairs_per_split,
@@ -126,10 +145,26 @@ __global__ void k_backcontract(const double* __restrict__ Tm, int Kp, int rows_c
   for (int64_t q = q0 + w; q < q1; q += warps) {
     const int64_t ip = q % n_pre, iq = q / n_pre;
     const int64_t s = ip + n_pre * (ik + Ik * iq);
-    const double* Ts = Tm + s * (int64_t)Kp;
-    for (int e = lane; e < szM; e += 32) {
-      const int i = e / mc, j = e % mc;
-      sM[e] = (T)(rows_case ? Ts[j * mr + i] : Ts[i * mc + j]);
+    if (sl.part) {
+      const int64_t rb = s / sl.bm, r = s % sl.bm;
+      const int64_t U = sl.RB * sl.NT, ulo = rb * sl.NT, uhi = (rb + 1) * sl.NT;
+      int64_t c0 = (ulo * sl.G) / U;
+      while (c0 > 0 && (c0 * U) / sl.G > ulo) --c0;
+      while (((c0 + 1) * U) / sl.G <= ulo) ++c0;
+      for (int e = lane; e < szM; e += 32) {
+        const int i = e / mc, j = e % mc;
+        const int q = rows_case ? j * mr + i : i * mc + j;
+        double v = 0.0;
+        for (int64_t cc = c0; cc < sl.G && (cc * U) / sl.G < uhi; ++cc)
+          v += (double)sl.part[((cc + rb) * sl.bm + r) * Kp + q];
+        sM[e] = (T)v;
+      }
+    } else {
+      const double* Ts = Tm + s * (int64_t)Kp;
+      for (int e = lane; e < szM; e += 32) {
+        const int i = e / mc, j = e % mc;
+        sM[e] = (T)(rows_case ? Ts[j * mr + i] : Ts[i * mc + j]);
+      }
     }
     if (pre)
       for (int e = lane; e < szPre; e += 32) sPre[e] = pre[ip * (int64_t)szPre + e];
@@ -201,7 +236,8 @@ __global__ void k_sum_splits(const double* __restrict__ part, int nsplit, int64_
 cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int mr, int mc,
                                 const void* pre, int64_t n_pre, const void* post,
                                 int64_t n_post, int64_t Ik, int rk, int rk1, double* dpart,
-                                int nsplit, double* d, bool fp64, cudaStream_t st) {
+                                int nsplit, double* d, bool fp64, cudaStream_t st, const SlotSrc* slots) {
+  const SlotSrc sl = slots ? *slots : SlotSrc{};
   const int64_t npairs = n_pre * n_post;
   const int64_t per = (npairs + nsplit - 1) / nsplit;
   const int threads = 128;
@@ -215,11 +251,11 @@ cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int 
     cudaFuncSetAttribute(k_backcontract<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   if (fp64)
-    k_backcontract<double><<<grid, threads, smem, st>>>((const double*)Tsum_d, Kp, rows_case ? 1 : 0, mr, mc,
+    k_backcontract<double><<<grid, threads, smem, st>>>((const double*)Tsum_d, sl, Kp, rows_case ? 1 : 0, mr, mc,
                                                      (const double*)pre, n_pre, (const double*)post, n_post,
                                                      Ik, rk, rk1, per, target);
   else
-    k_backcontract<float><<<grid, threads, smem, st>>>((const double*)Tsum_d, Kp, rows_case ? 1 : 0, mr, mc,
+    k_backcontract<float><<<grid, threads, smem, st>>>((const double*)Tsum_d, sl, Kp, rows_case ? 1 : 0, mr, mc,
                                                     (const float*)pre, n_pre, (const float*)post, n_post,
                                                     Ik, rk, rk1, per, target);
   note_launch();

@@ -164,12 +164,20 @@ trd_status ensure(trd_handle* h, DevBuf& b, size_t bytes);
 
 // ------------------------------------------------------------------ launchers
 // merge.cu
-cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool transposed,
-                         int64_t ld, cudaStream_t st);
+// out may be null when only the BF16 operand (hi, lo optional, kpad-wide rows) is wanted
+cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool transposed, int64_t ld, cudaStream_t st,
+                         __nv_bfloat16* hi = nullptr, __nv_bfloat16* lo = nullptr, int kpad = 0);
+// partial slots of the tensor-core pass (see k_reduce_slots), read by the back-contraction
+struct SlotSrc {
+  const float* part = nullptr;
+  int64_t RB = 0, NT = 0, bm = 0;
+  int G = 0;
+};
 cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int mr, int mc,
                                 const void* pre, int64_t n_pre, const void* post,
                                 int64_t n_post, int64_t Ik, int rk, int rk1, double* dpart,
-                                int nsplit, double* d, bool fp64, cudaStream_t st);
+                                int nsplit, double* d, bool fp64, cudaStream_t st,
+                                const SlotSrc* slots = nullptr);
 cudaError_t launch_reduce_T(const void* Tpart, bool is_double, int splits, int64_t n,
                             double* Tsum, cudaStream_t st);
 cudaError_t launch_reduce_stats(const double* stat_part, int ctas, double* stat_sum,
