@@ -266,26 +266,55 @@ def run_ours(args, rank, world, local):
     value = world * slots_per_step * args.steps / (ms / 1e3)
     prec = precs[0]
 
-    # e2e through the public API with host buffers: H2D of X and mask from pinned memory,
-    # one trd_step, the report read back (inside trd_step)
+    # e2e through the public API with host buffers.  Every step's X and mask are copied from
+    # pinned host memory into one of two device buffer pairs on a copy stream while the
+    # previous step computes (double buffering); the step attaches its pair (trd_set_data,
+    # which drops everything derived from the old contents, so the mask re-layout and the
+    # probe values are recomputed every step and the steps run eagerly, without graph
+    # replay), runs, and reads its report back (inside trd_step).
     Xh, Mh = host
     Xd, Md = dev
+    pairs = [(Xd, Md), (torch.empty_like(Xd), torch.empty_like(Md))]
     h2d = Xh.numel() * 4 + Mh.numel() * 4
     d2h = 32 * 8
-    for _ in range(3):          # same warm-up as the device-timed steps (eager, capture)
-        t.step(sigma=-1.0)
+    copy_stream = torch.cuda.Stream()
+    main_stream = torch.cuda.current_stream()
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    released = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def upload(j):
+        copy_stream.wait_event(released[j])
+        with torch.cuda.stream(copy_stream):
+            pairs[j][0].copy_(Xh, non_blocking=True)
+            pairs[j][1].copy_(Mh, non_blocking=True)
+            copied[j].record(copy_stream)
+
+    def e2e_steps(n):
+        for j in range(2):
+            released[j].record(main_stream)
+        upload(0)
+        for i in range(n):
+            j = i % 2
+            main_stream.wait_event(copied[j])
+            t.set_data(*pairs[j])
+            if i + 1 < n:
+                upload(1 - j)
+            t.step(sigma=-1.0)
+            released[j].record(main_stream)
+
+    e2e_steps(3)                # warm-up: same calls as the timed steps
     torch.cuda.synchronize()
     _barrier(world)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        Xd.copy_(Xh, non_blocking=True)
-        Md.copy_(Mh, non_blocking=True)
-        t.step(sigma=-1.0)
+    e2e_steps(args.steps)
     torch.cuda.synchronize()
     e2e_s = _max_over_ranks((time.perf_counter() - t0) * 1e3, world) / 1e3
     e2e = {"value": world * slots_per_step * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "ms_per_step": e2e_s * 1e3 / args.steps}
+           "ms_per_step": e2e_s * 1e3 / args.steps,
+           "note": "per step: H2D of X and mask from pinned memory (double-buffered, overlapping the "
+                   "previous step), trd_set_data, trd_step with its report read back"}
+    t.set_data(Xd, Md)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,

@@ -126,7 +126,10 @@ const char* trd_status_string(trd_status status);
 /* Attach the data tensor X (Eq. TRWOPT) and its observation mask P (Eq. TRWOPT; bit-packed,
  * ceil(prod I / 32) words, 1 = observed).  Both are DEVICE pointers, borrowed: X is prod(I)
  * floats in the linear order above, 16-byte aligned.  mask may be NULL, meaning fully
- * observed.  Resets any sketch.  Errors: TRD_EINVAL (NULL X, misalignment). */
+ * observed.  Resets any sketch.  The library caches what it derives from the contents (the
+ * mask re-laid for the data passes, the adaptive width's probe values); after changing the
+ * contents behind the same pointers, call trd_set_data again, which drops those caches (and
+ * ends CUDA-graph replay of trd_step).  Errors: TRD_EINVAL (NULL X, misalignment). */
 trd_status trd_set_data(trd_t* handle, const float* X_dev, const uint32_t* mask_dev);
 
 /* Initialise all cores i.i.d. Gaussian (Algorithm 1, 'initialize Z_k'; the law is a

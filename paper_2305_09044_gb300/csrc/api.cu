@@ -94,6 +94,7 @@ struct Extra {
   DevBuf tmpZ[kMaxN];   // cores given to trd_reconstruct_from
   DevBuf probe_a, probe_b, probe_x;   // adaptive-width probe: inner / outer index, data
   DevBuf dotpart, solve_ctr;          // per-row parts of <d, h>, completion counter
+  DevBuf bc_ctr;                      // per-row completion counters of the back-contraction
   DevBuf probe_cand;                  // selection candidates of the adaptive width
   SlotSrc slots;                      // partial slots of the last tensor-core pass 1
   // uniform row sampling (trd_sample_rows): J multi-indices of the modes other than row_k
@@ -108,6 +109,8 @@ struct Extra {
   uint64_t sketch_count = 0;
   bool probe_ready = false;
   int64_t probe_Pin = 0;
+  DevBuf probe_lin;                   // sorted probe positions (drawn once per tensor size)
+  int64_t probe_lin_n = -1;
   DevBuf Ework;         // FGMC factor partial sums
   // sampled correntropy loss: cores in FP64, merged halves, their gradients, partials
   DevBuf smpZ[kMaxN], smpA, smpC, smpGA, smpGC, smpGAd, smpGCd, smpPre, smpPost, smpDpart, smpD, smpLoss;
@@ -279,6 +282,7 @@ Chain make_chain(const trd_handle* h, const View& v, int m0, int m1, int ksub = 
   for (int j = 0; j < ch.n; ++j) {
     const int m = m0 + j;
     ch.core[j] = (m == ksub && subst) ? subst : (cores ? cores[m] : h->Z[m]);
+    ch.coref[j] = ((m == ksub && subst) || cores) ? nullptr : h->Zf[m];
     ch.idx[j] = v.idx[m];
     ch.dim[j] = v.dim[m];
     ch.rows[j] = h->R[m];
@@ -454,6 +458,7 @@ RowsArgs rows_args(const trd_handle* h, int k, int64_t J) {
     st *= h->I[m];
     a.R[m] = h->R[m];
     a.Z[m] = h->Z[m];
+    a.Zf[m] = h->Zf[m];
   }
   return a;
 }
@@ -758,6 +763,30 @@ trd_status run_pass1(trd_handle* h, int k, bool full_stats = true) {
   return TRD_OK;
 }
 
+// a one-core subchain product, read in place by the back-contraction
+BcCore bc_core(const Chain& ch) {
+  BcCore c;
+  if (ch.n == 1) {
+    c.core = ch.core[0];
+    c.coref = ch.coref[0];
+    c.idx = ch.idx[0];
+  }
+  return c;
+}
+
+// split count of the back-contraction: about two (pre, post) pairs per warp of a block
+int64_t bc_splits(int64_t npairs) { return imax(1, imin((npairs + 7) / 8, 256)); }
+
+// zeroed completion counters for n rows (each launch's last block resets its row's counter)
+trd_status bc_counters(trd_handle* h, int64_t n) {
+  Extra* x = X_(h);
+  const size_t bytes = sizeof(unsigned) * (size_t)n;
+  if (x->bc_ctr.p && x->bc_ctr.bytes >= bytes) return TRD_OK;
+  TRY(ensure(h, x->bc_ctr, bytes));
+  CK(cudaMemsetAsync(x->bc_ctr.p, 0, x->bc_ctr.bytes, h->stream), "counter");
+  return TRD_OK;
+}
+
 trd_status run_gradient(trd_handle* h, int k) {
   if (h->pass1_k != k) return set_err(h, TRD_EINVAL, "trd_residual_weights must run for this core first");
   PScope ps(h, P_GRAD);
@@ -787,24 +816,24 @@ trd_status run_gradient(trd_handle* h, int k) {
   const int64_t n_post = post.n > 0 ? post.count : 1;
   const bool dbl = is_fp64(h);
   const size_t e = elt(h);
-  if (pre.n > 0) {
+  // one-core products are read from the cores by the back-contraction itself
+  if (pre.n > 1) {
     TRY(ensure(h, h->pre, e * n_pre * mc * rk));
     CK(launch_chain(pre, h->pre.p, dbl, false, mc * rk, h->stream), "merge prefix");
   }
-  if (post.n > 0) {
+  if (post.n > 1) {
     TRY(ensure(h, h->post, e * n_post * rk1 * mr));
     CK(launch_chain(post, h->post.p, dbl, false, rk1 * mr, h->stream), "merge suffix");
   }
-  const int64_t npairs = n_pre * n_post;
-  int64_t nsplit = (2 * (int64_t)h->num_sms + h->I[k] - 1) / h->I[k];
-  nsplit = imax(1, imin(nsplit, imin(npairs, 256)));
+  const int64_t nsplit = bc_splits(n_pre * n_post);
   const int K = h->K[k];
   TRY(ensure(h, h->d, sizeof(double) * h->I[k] * K));
   if (nsplit > 1) TRY(ensure(h, h->dpart, sizeof(double) * nsplit * h->I[k] * K));
-  CK(launch_backcontract(h->Tsum.p, sp.Kp, sp.rows, mr, mc, pre.n > 0 ? h->pre.p : nullptr, n_pre,
-                         post.n > 0 ? h->post.p : nullptr, n_post, h->I[k], rk, rk1, (double*)h->dpart.p,
-                         (int)nsplit, (double*)h->d.p, dbl, h->stream,
-                         h->prec == TRD_BF16 ? &X_(h)->slots : nullptr),
+  TRY(bc_counters(h, h->I[k]));
+  CK(launch_backcontract(h->Tsum.p, sp.Kp, sp.rows, mr, mc, pre.n > 1 ? h->pre.p : nullptr, n_pre,
+                         post.n > 1 ? h->post.p : nullptr, n_post, h->I[k], rk, rk1, (double*)h->dpart.p,
+                         (int)nsplit, (double*)h->d.p, (unsigned*)X_(h)->bc_ctr.p, dbl, h->stream,
+                         h->prec == TRD_BF16 ? &X_(h)->slots : nullptr, bc_core(pre), bc_core(post)),
      "back-contraction");
   h->grad_k = k;
   return TRD_OK;
@@ -954,7 +983,7 @@ trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int
   }
   PScope psu(h, P_UPDATE);
   const bool from_parts = eta_fixed <= 0 && den == nullptr;   // tensor-core line search
-  CK(launch_step_update(h->Z[k], hh, n, h->scal + S_NUM, from_parts ? (const double*)h->stat_part.p : nullptr,
+  CK(launch_step_update(h->Z[k], h->Zf[k], hh, n, h->scal + S_NUM, from_parts ? (const double*)h->stat_part.p : nullptr,
                         from_parts ? X_(h)->tcG : 0, den, eta_fixed, h->dstatus, h->scal + S_ETA, eta_slot,
                         h->stream),
      "step size and core update");
@@ -993,13 +1022,18 @@ trd_status run_adaptive(trd_handle* h, double sigma_prev, const double* sigma_pr
     TRY(ensure(h, x->probe_x, sizeof(float) * n));
     const int64_t* lin_dev = nullptr;
     if (h->numel > kProbeMax) {
-      // sorted probe positions, uploaded once per data set through the key buffer
-      std::vector<int64_t> lin;
-      probe_positions(h->numel, lin);
-      CK(cudaMemcpyAsync(h->probe_keys.p, lin.data(), sizeof(int64_t) * lin.size(), cudaMemcpyHostToDevice,
-                         h->stream), "probe upload");
-      CK(cudaStreamSynchronize(h->stream), "probe upload");
-      lin_dev = (const int64_t*)h->probe_keys.p;
+      // sorted probe positions: they depend only on the tensor size, so they are drawn and
+      // uploaded once and kept for later data sets of that size
+      if (x->probe_lin_n != h->numel) {
+        std::vector<int64_t> lin;
+        probe_positions(h->numel, lin);
+        TRY(ensure(h, x->probe_lin, sizeof(int64_t) * lin.size()));
+        CK(cudaMemcpyAsync(x->probe_lin.p, lin.data(), sizeof(int64_t) * lin.size(), cudaMemcpyHostToDevice,
+                           h->stream), "probe upload");
+        CK(cudaStreamSynchronize(h->stream), "probe upload");
+        x->probe_lin_n = h->numel;
+      }
+      lin_dev = (const int64_t*)x->probe_lin.p;
     }
     CK(launch_probe_setup(h->X, h->M, lin_dev, n, sp.P_in, (int32_t*)x->probe_a.p, (int32_t*)x->probe_b.p,
                           (float*)x->probe_x.p, h->stream), "probe set-up");
@@ -1148,11 +1182,13 @@ trd_status alloc_state(trd_handle* h) {
     maxK = std::max(maxK, h->K[k]);
     maxIK = std::max(maxIK, h->I[k] * (int64_t)h->K[k]);
     if (cudaMalloc(&h->Z[k], sizeof(double) * h->I[k] * h->K[k]) != cudaSuccess ||
+        cudaMalloc(&h->Zf[k], sizeof(float) * h->I[k] * h->K[k]) != cudaSuccess ||
         cudaMalloc(&h->E[k], sizeof(double) * (size_t)rk * rk * rk1 * rk1) != cudaSuccess) {
       cudaGetLastError();
       return set_err(h, TRD_ENOMEM, "core allocation failed");
     }
     cudaMemsetAsync(h->Z[k], 0, sizeof(double) * h->I[k] * h->K[k], h->stream);
+    cudaMemsetAsync(h->Zf[k], 0, sizeof(float) * h->I[k] * h->K[k], h->stream);
   }
   // chain buffers hold p^2 x q^2 intermediates: bound by maxR^4
   size_t chain = 1;
@@ -1283,6 +1319,7 @@ void trd_destroy(trd_t* h) {
   drop_graph(X_(h));
   for (int k = 0; k < kMaxN; ++k) {
     if (h->Z[k]) cudaFree(h->Z[k]);
+    if (h->Zf[k]) cudaFree(h->Zf[k]);
     if (h->E[k]) cudaFree(h->E[k]);
     if (h->idx_dev[k]) cudaFree(h->idx_dev[k]);
   }
@@ -1293,7 +1330,7 @@ void trd_destroy(trd_t* h) {
   for (DevBuf* b : bufs) free_buf(*b);
   Extra* x = X_(h);
   DevBuf* xb[] = {&x->Ework, &x->meta,    &x->stat_sum2, &x->Gloc,    &x->recA, &x->recC,
-                  &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr, &x->probe_cand, &x->rows_dev,
+                  &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr, &x->bc_ctr, &x->probe_lin, &x->probe_cand, &x->rows_dev,
                   &x->bShi,  &x->bSlo,    &x->bSh,       &x->bThi,    &x->bTlo,    &x->bTT,
                   &x->Mst[0], &x->Mst[1]};
   for (DevBuf* b : xb) free_buf(*b);
@@ -1321,7 +1358,9 @@ trd_status trd_set_data(trd_t* h, const float* X, const uint32_t* mask) {
     return set_err(h, TRD_EINVAL, "X and mask must be 16-byte aligned");
   h->X = X;
   h->M = mask;
+  // the contents may have changed behind the same pointers: drop everything derived from them
   X_(h)->probe_ready = false;
+  X_(h)->mst_X[0] = X_(h)->mst_X[1] = nullptr;
   h->numel = 1;
   for (int m = 0; m < h->N; ++m) h->numel *= h->I[m];
   use_full_view(h);
@@ -1348,6 +1387,7 @@ trd_status trd_init_cores(trd_t* h, uint64_t seed, double stddev) {
       v[(size_t)f] = sd * (sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2));
     }
     CK(cudaMemcpyAsync(h->Z[k], v.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream), "core upload");
+    CK(launch_from_double(h->Z[k], n, h->Zf[k], false, h->stream), "FP32 core copy");
     CK(cudaStreamSynchronize(h->stream), "sync");
     h->ver[k]++;
     TRY(refresh_E(h, k));
@@ -1366,6 +1406,7 @@ trd_status trd_set_core(trd_t* h, int k, const double* core) {
   if (!core) return set_err(h, TRD_EINVAL, "NULL core");
   CK(cudaMemcpyAsync(h->Z[k], core, sizeof(double) * h->I[k] * h->K[k], cudaMemcpyHostToDevice, h->stream),
      "core upload");
+  CK(launch_from_double(h->Z[k], h->I[k] * (int64_t)h->K[k], h->Zf[k], false, h->stream), "FP32 core copy");
   CK(cudaStreamSynchronize(h->stream), "sync");
   h->ver[k]++;
   h->pass1_k = h->grad_k = -1;
@@ -1544,6 +1585,10 @@ namespace {
 // handle's stream without any host synchronisation, so that it can be captured as a graph.
 trd_status step_device(trd_handle* h, const trd_params* p, int64_t* slots_out) {
   const int N = h->N;
+  // the Gram of core 0 depends only on the cores of the previous iteration: fork it before the
+  // adaptive width, whose kernels it then overlaps
+  X_(h)->pre_k = -1;
+  const bool early = p->gram == TRD_GRAM_GLOBAL && prefactor(h, 0, p->lambda);
   if (p->sigma > 0) {
     TRY(set_sigma(h, p->sigma));
   } else {
@@ -1579,9 +1624,11 @@ trd_status step_device(trd_handle* h, const trd_params* p, int64_t* slots_out) {
       use_full_view(h);
     }
     Extra* x = X_(h);
-    x->pre_k = -1;
     x->reserve_sms = 0;
-    if (p->gram == TRD_GRAM_GLOBAL && prefactor(h, k, p->lambda)) x->reserve_sms = kSideSMs;
+    if (!(k == 0 && early)) {
+      x->pre_k = -1;
+      if (p->gram == TRD_GRAM_GLOBAL && prefactor(h, k, p->lambda)) x->reserve_sms = kSideSMs;
+    }
     const trd_status s1 = run_pass1(h, k, false);
     x->reserve_sms = 0;
     TRY(s1);
@@ -1958,23 +2005,23 @@ trd_status trd_sampled_bwd(trd_t* h, const void* const* cores_dev, const int32_t
     const Chain pre = make_chain(h, fv, pre0, pre1, -1, nullptr, Zc);
     const Chain post = make_chain(h, fv, post0, post1, -1, nullptr, Zc);
     const int64_t n_pre = pre.n > 0 ? pre.count : 1, n_post = post.n > 0 ? post.count : 1;
-    if (pre.n > 0) {
+    if (pre.n > 1) {
       TRY(ensure(h, x->smpPre, e * n_pre * mc * rk));
       CK(launch_chain(pre, x->smpPre.p, dbl, false, mc * rk, h->stream), "merge prefix");
     }
-    if (post.n > 0) {
+    if (post.n > 1) {
       TRY(ensure(h, x->smpPost, e * n_post * rk1 * mr));
       CK(launch_chain(post, x->smpPost.p, dbl, false, rk1 * mr, h->stream), "merge suffix");
     }
-    const int64_t npairs = n_pre * n_post;
-    int64_t nsplit = (2 * (int64_t)h->num_sms + h->I[k] - 1) / h->I[k];
-    nsplit = imax(1, imin(nsplit, imin(npairs, 256)));
+    const int64_t nsplit = bc_splits(n_pre * n_post);
     const int K = h->K[k];
     TRY(ensure(h, x->smpD, sizeof(double) * h->I[k] * K));
     if (nsplit > 1) TRY(ensure(h, x->smpDpart, sizeof(double) * nsplit * h->I[k] * K));
+    TRY(bc_counters(h, h->I[k]));
     CK(launch_backcontract(rows ? (const void*)gAd : (const void*)gCd, sp.Kp, rows, mr, mc,
-                           pre.n > 0 ? x->smpPre.p : nullptr, n_pre, post.n > 0 ? x->smpPost.p : nullptr, n_post,
-                           h->I[k], rk, rk1, (double*)x->smpDpart.p, (int)nsplit, (double*)x->smpD.p, dbl, h->stream),
+                           pre.n > 1 ? x->smpPre.p : nullptr, n_pre, post.n > 1 ? x->smpPost.p : nullptr, n_post,
+                           h->I[k], rk, rk1, (double*)x->smpDpart.p, (int)nsplit, (double*)x->smpD.p,
+                           (unsigned*)x->bc_ctr.p, dbl, h->stream, nullptr, bc_core(pre), bc_core(post)),
        "adjoint back-contraction");
     CK(launch_from_double((const double*)x->smpD.p, h->I[k] * (int64_t)K, grad_dev[k], dbl, h->stream),
        "gradient store");

@@ -593,8 +593,9 @@ cudaError_t launch_eta(const double* num, const double* den, double fixed_eta, i
 // Step size and update in one launch: every block forms eta = <d,h> / den (den summed from the
 // line-search pass's per-CTA partials in the same fixed order as the statistics reduction,
 // field 6, or read from `den`), forced to 0 on a flagged or non-finite step; block 0 records
-// it; then Z_k <- Z_k + eta fold(h) (update-sign reading of Eq. updatessd / Eq. ftrbcn).
-__global__ void k_step_update(double* __restrict__ Z, const double* __restrict__ h, int64_t n,
+// it; then Z_k <- Z_k + eta fold(h) (update-sign reading of Eq. updatessd / Eq. ftrbcn), and
+// the FP32 copy of the core follows.
+__global__ void k_step_update(double* __restrict__ Z, float* __restrict__ Zf, const double* __restrict__ h, int64_t n,
                               const double* __restrict__ num, const double* __restrict__ part, int ctas,
                               const double* __restrict__ den_in, double fixed_eta, int* dstatus,
                               double* __restrict__ eta_out, double* __restrict__ eta_slot) {
@@ -624,64 +625,69 @@ __global__ void k_step_update(double* __restrict__ Z, const double* __restrict__
   __syncthreads();
   const double e = s_eta;
   if (e == 0.0) return;   // a rejected step leaves the core untouched (h may be non-finite)
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    Z[i] = fma(e, h[i], Z[i]);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double z = fma(e, h[i], Z[i]);
+    Z[i] = z;
+    Zf[i] = (float)z;
+  }
 }
 
-cudaError_t launch_step_update(double* Z, const double* h, int64_t n, const double* num, const double* part, int ctas,
-                               const double* den, double fixed_eta, int* dstatus, double* eta, double* eta_slot,
-                               cudaStream_t st) {
-  k_step_update<<<(unsigned)imin((n + 255) / 256, 1024), 256, 0, st>>>(Z, h, n, num, part, ctas, den, fixed_eta,
-                                                                      dstatus, eta, eta_slot);
-  note_launch();
-  return cudaGetLastError();
-}
-
-// Z_k <- Z_k + eta fold(h)   (update-sign reading of Eq. updatessd / Eq. ftrbcn)
-__global__ void k_axpy_core(double* __restrict__ Z, const double* __restrict__ h, int64_t n,
-                            const double* __restrict__ eta) {
-  const double e = *eta;
-  if (e == 0.0) return;   // a rejected step leaves the core untouched (h may be non-finite)
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    Z[i] = fma(e, h[i], Z[i]);
-}
-
-cudaError_t launch_axpy_core(double* Z, const double* h, int64_t n, const double* eta,
-                             cudaStream_t st) {
-  k_axpy_core<<<(unsigned)imin((n + 255) / 256, 4096), 256, 0, st>>>(Z, h, n, eta);
+cudaError_t launch_step_update(double* Z, float* Zf, const double* h, int64_t n, const double* num, const double* part,
+                               int ctas, const double* den, double fixed_eta, int* dstatus, double* eta,
+                               double* eta_slot, cudaStream_t st) {
+  k_step_update<<<(unsigned)imin((n + 255) / 256, 1024), 256, 0, st>>>(Z, Zf, h, n, num, part, ctas, den,
+                                                                      fixed_eta, dstatus, eta, eta_slot);
   note_launch();
   return cudaGetLastError();
 }
 
 // e = ||D - Dprev||_F / ||D||_F, then Dprev <- D  (Algorithm 1 stopping quantity)
-__global__ void k_stop_error(const double* __restrict__ D, double* __restrict__ Dprev, int64_t n,
-                             double* __restrict__ e_out) {
-  __shared__ double s1[256], s2[256];
-  double a = 0.0, b = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double dd = D[i] - Dprev[i];
-    a = fma(dd, dd, a);
-    b = fma(D[i], D[i], b);
+__global__ void __launch_bounds__(1024) k_stop_error(const double* __restrict__ D, double* __restrict__ Dprev,
+                                                     int64_t n, double* __restrict__ e_out) {
+  // one block; two independent partial sums per thread and quantity, a fixed-order
+  // shuffle/shared reduction, then D is kept for the next iteration
+  __shared__ double s1[32], s2[32];
+  double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+  const int64_t step = blockDim.x;
+  int64_t i = threadIdx.x;
+  for (; i + step < n; i += 2 * step) {
+    const double x0 = D[i], y0 = Dprev[i], x1 = D[i + step], y1 = Dprev[i + step];
+    a0 = fma(x0 - y0, x0 - y0, a0);
+    b0 = fma(x0, x0, b0);
+    a1 = fma(x1 - y1, x1 - y1, a1);
+    b1 = fma(x1, x1, b1);
   }
-  s1[threadIdx.x] = a;
-  s2[threadIdx.x] = b;
+  if (i < n) {
+    const double x0 = D[i], y0 = Dprev[i];
+    a0 = fma(x0 - y0, x0 - y0, a0);
+    b0 = fma(x0, x0, b0);
+  }
+  double a = a0 + a1, b = b0 + b1;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s1[w] = a;
+    s2[w] = b;
+  }
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      s1[threadIdx.x] += s1[threadIdx.x + w];
-      s2[threadIdx.x] += s2[threadIdx.x + w];
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      sa += s1[q];
+      sb += s2[q];
     }
-    __syncthreads();
+    *e_out = sb > 0 ? sqrt(sa / sb) : 0.0;
   }
-  if (threadIdx.x == 0) *e_out = s2[0] > 0 ? sqrt(s1[0] / s2[0]) : 0.0;
   __syncthreads();
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Dprev[i] = D[i];
+  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) Dprev[q] = D[q];
 }
 
 cudaError_t launch_stop_error(const double* D, double* Dprev, int64_t n, double* e_out,
                               cudaStream_t st) {
-  k_stop_error<<<1, 256, 0, st>>>(D, Dprev, n, e_out);
+  k_stop_error<<<1, 1024, 0, st>>>(D, Dprev, n, e_out);
   note_launch();
   return cudaGetLastError();
 }

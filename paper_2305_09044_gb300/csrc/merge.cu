@@ -12,7 +12,22 @@ namespace trd {
 // in shared memory, then written row-major (transposed = false) or column-major
 // (transposed = true) into row p of `out` (stride ld; skipped when out is null) and, when
 // `hi` is given, as the BF16 tensor-core operand: hi = bf16(v), lo = bf16(v - hi) (lo
-// optional), rows of kpad entries with zero padding.
+// optional), rows of kpad entries with zero padding.  Products are kept column-major like
+// the core slices, so slices are copied with all lanes and no index arithmetic; the FP32
+// kernel reads the FP32 core copies when they exist (FP64-to-FP32 conversion, like integer
+// division, goes through a unit that issues near the FP64 rate on this GPU).
+template <typename Tc>
+__device__ __forceinline__ void chain_slice(const Chain& ch, int j, int64_t sl, int n, Tc* dst, int lane) {
+  const float* zf = sizeof(Tc) == 4 ? ch.coref[j] : nullptr;
+  if (zf) {
+    zf += sl * (int64_t)n;
+    for (int e = lane; e < n; e += 32) dst[e] = (Tc)zf[e];
+  } else {
+    const double* z = ch.core[j] + sl * (int64_t)n;
+    for (int e = lane; e < n; e += 32) dst[e] = (Tc)z[e];
+  }
+}
+
 template <typename Tc, typename Tout>
 __global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_t ld, int cap,
                         __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int kpad) {
@@ -26,42 +41,32 @@ __global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_
     int64_t rem = p;
     int64_t sl[kMaxN];
     for (int j = 0; j < ch.n; ++j) {
-      const int64_t i = rem % ch.dim[j];
-      rem /= ch.dim[j];
+      int64_t i;
+      rem = qdivmod(rem, ch.dim[j], i);
       sl[j] = ch.idx[j] ? (int64_t)ch.idx[j][i] : i;
     }
-    int R0 = ch.rows[0], C = ch.cols[0];
-    {
-      const double* z = ch.core[0] + sl[0] * (int64_t)(R0 * C);
-      for (int e = lane; e < R0 * C; e += 32) {
-        const int a = e % R0, b = e / R0;     // source is column-major within the slice
-        Mb[a * C + b] = (Tc)z[e];
-      }
-    }
+    const int R0 = ch.rows[0];
+    int C = ch.cols[0];
+    // M(a, c) at Mb[c R0 + a]; slice j element (c, b) at Zs[b R_j + c] (the core layout)
+    chain_slice(ch, 0, sl[0], R0 * C, Mb, lane);
     __syncwarp();
     for (int j = 1; j < ch.n; ++j) {
-      const int Rj = ch.rows[j], Cj = ch.cols[j];
-      const double* z = ch.core[j] + sl[j] * (int64_t)(Rj * Cj);
-      for (int e = lane; e < Rj * Cj; e += 32) {
-        const int c = e % Rj, b = e / Rj;
-        Zs[c * Cj + b] = (Tc)z[e];
-      }
+      const int Rj = ch.rows[j], Cj = ch.cols[j];     // Rj == C
+      chain_slice(ch, j, sl[j], Rj * Cj, Zs, lane);
       __syncwarp();
-      for (int e = lane; e < R0 * Cj; e += 32) {
-        const int a = e / Cj, b = e % Cj;
-        Tc acc = Tc(0);
-        for (int c = 0; c < C; ++c) acc = fma(Mb[a * C + c], Zs[c * Cj + b], acc);
-        Mn[e] = acc;
-      }
+      for (int b = 0; b < Cj; ++b)
+        for (int a = lane; a < R0; a += 32) {
+          Tc acc = Tc(0);
+          for (int c = 0; c < C; ++c) acc = fma(Mb[c * R0 + a], Zs[b * Rj + c], acc);
+          Mn[b * R0 + a] = acc;
+        }
       __syncwarp();
       Tc* t = Mb; Mb = Mn; Mn = t;
       C = Cj;
-      __syncwarp();
     }
-    for (int e = lane; e < R0 * C; e += 32) {
-      const int a = e / C, b = e % C;
-      const int pos = transposed ? b * R0 + a : e;
-      const Tout v = (Tout)Mb[e];
+    // entry (a, b) goes to position b R0 + a (transposed) or a C + b
+    auto emit = [&](int src, int pos) {
+      const Tout v = (Tout)Mb[src];
       if (out) out[p * ld + pos] = v;
       if (hi) {
         const float f = (float)v;
@@ -69,6 +74,12 @@ __global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_
         hi[p * kpad + pos] = vh;
         if (lo) lo[p * kpad + pos] = __float2bfloat16_rn(f - __bfloat162float(vh));
       }
+    };
+    if (transposed) {
+      for (int e = lane; e < R0 * C; e += 32) emit(e, e);
+    } else {
+      for (int b = 0; b < C; ++b)
+        for (int a = lane; a < R0; a += 32) emit(b * R0 + a, a * C + b);
     }
     if (hi)
       for (int e = R0 * C + lane; e < kpad; e += 32) {
@@ -114,155 +125,244 @@ cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool trans
 // where M(s) is the r x r matrix held in row s of the reduced weighted contraction
 // (ROWS case: Ct[delta, gamma] = T[s][gamma r_c + delta]; COLS case: At[gamma, delta] =
 // T[s][gamma r_c + delta]) and s = pre + n_pre (i_k + I_k post).  Pre / Post are the
-// products of the cores between the block boundary and core k (identity when empty).
+// products of the cores between the block boundary and core k (identity when empty); a
+// product of one core is read from the core itself (BcCore) instead of a merged buffer.
 // The reduced contraction row s is read from Tm (FP64, [P_stat][Kp]) or, when sl.part is
 // given, summed in CTA order from the tensor-core pass's partial slots (FP32, the sum of slots
-// c + rb over the CTAs c whose unit range meets stationary block rb = s / BM).
-template <typename T>
+// c + rb over the CTAs c whose unit range meets stationary block rb = s / BM).  Block (ik, y)
+// sums pairs [y P, (y + 1) P); with several splits the last block of ik to finish adds the
+// split partials in split order, so the result does not depend on the block schedule.
+template <typename T, int UK>
 __global__ void k_backcontract(const double* __restrict__ Tm, SlotSrc sl, int Kp, int rows_case, int mr, int mc,
                                const T* __restrict__ pre, int64_t n_pre,
-                               const T* __restrict__ post, int64_t n_post, int64_t Ik,
-                               int rk, int rk1, int64_t pairs_per_split,
-                               double* __restrict__ out) {
+                               const T* __restrict__ post, int64_t n_post, BcCore preC, BcCore postC,
+                               int64_t Ik, int rk, int rk1, int64_t pairs_per_split,
+                               double* __restrict__ part_out, double* __restrict__ d,
+                               unsigned* __restrict__ ctr, int work_bytes, int tab_rb) {
   // one warp per (pre, post) pair; warp-private shared buffers, no block barriers in the
-  // pair loop; per-lane accumulators, summed over warps in a fixed order at the end
+  // pair loop; per-lane accumulators, summed over warps in a fixed order at the end.  The
+  // index maps of the small matrix loops (and the CTA range of each stationary block) are
+  // tabulated once per block: integer division runs through the conversion unit, whose
+  // rate on this GPU is close to the FP64 rate.
   extern __shared__ __align__(16) unsigned char smem_bc[];
+  __shared__ int s_last;
   const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int szM = mr * mc, szPre = mc * rk, szPost = rk1 * mr, szV = mr * rk;
+  const int K = rk * rk1;
   const int per_warp = szM + szPre + szPost + szV;
   T* sM = reinterpret_cast<T*>(smem_bc) + (size_t)w * per_warp;
   T* sPre = sM + szM;
   T* sPost = sPre + szPre;
   T* sV = sPost + szPost;
+  int2* tC = reinterpret_cast<int2*>(smem_bc + work_bytes);   // [tab_rb] (first CTA, CTA count)
+  int* tM = reinterpret_cast<int*>(tC + tab_rb);              // slot offset of M entry e
+  int* tPre = tM + szM;                                       // core offset of Pre entry e
+  int* tPost = tPre + szPre;                                  // core offset of Post entry e
+  int* tV = tPost + szPost;                                   // (i mc) | a << 16 of V entry e
+  int* tU = tV + szV;                                         // (b mr) | a << 16 of U entry e
+  for (int e = threadIdx.x; e < szM; e += blockDim.x) {
+    const int i = e / mc, j = e % mc;
+    tM[e] = rows_case ? j * mr + i : i * mc + j;
+  }
+  for (int e = threadIdx.x; e < szPre; e += blockDim.x) tPre[e] = (e % rk) * mc + e / rk;
+  for (int e = threadIdx.x; e < szPost; e += blockDim.x) tPost[e] = (e % mr) * rk1 + e / mr;
+  for (int e = threadIdx.x; e < szV; e += blockDim.x) tV[e] = (e / rk) * mc | (e % rk) << 16;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) tU[e] = (e / rk) * mr | (e % rk) << 16;
+  const int64_t U = sl.RB * sl.NT, G = sl.G;
+  // CTA c covers units [floor(c U / G), floor((c + 1) U / G)); CTAs c0 .. c1 - 1 meet block rb
+  auto cta_range = [&](int64_t rb, int& c0o, int& nco) {
+    const int64_t ulo = rb * sl.NT, uhi = ulo + sl.NT;
+    int64_t c0 = (ulo * G) / U;
+    while (c0 > 0 && c0 * U >= (ulo + 1) * G) --c0;
+    while ((c0 + 1) * U < (ulo + 1) * G) ++c0;
+    int64_t c1 = c0 + 1;
+    while (c1 < G && c1 * U < uhi * G) ++c1;
+    c0o = (int)c0;
+    nco = (int)(c1 - c0);
+  };
+  for (int rb = threadIdx.x; rb < tab_rb; rb += blockDim.x) {
+    int c0, nc;
+    cta_range(rb, c0, nc);
+    tC[rb] = make_int2(c0, nc);
+  }
+  __syncthreads();
   const int64_t ik = blockIdx.x;
-  const int K = rk * rk1;
   const int64_t npairs = n_pre * n_post;
   const int64_t q0 = (int64_t)blockIdx.y * pairs_per_split;
   const int64_t q1 = min(npairs, q0 + pairs_per_split);
-  T acc[32];
+  const bool has_pre = pre || preC.core, has_post = post || postC.core;
+  const int64_t cs = sl.bm * Kp;
+  T acc[UK];                                   // entries lane + 32 u of this warp's sum
 #pragma unroll
-  for (int u = 0; u < 32; ++u) acc[u] = T(0);
+  for (int u = 0; u < UK; ++u) acc[u] = T(0);
+  int64_t ip;
+  int64_t iq = qdivmod(q0 + w, n_pre, ip);
   for (int64_t q = q0 + w; q < q1; q += warps) {
-    const int64_t ip = q % n_pre, iq = q / n_pre;
     const int64_t s = ip + n_pre * (ik + Ik * iq);
     if (sl.part) {
-      const int64_t rb = s / sl.bm, r = s % sl.bm;
-      const int64_t U = sl.RB * sl.NT, ulo = rb * sl.NT, uhi = (rb + 1) * sl.NT;
-      int64_t c0 = (ulo * sl.G) / U;
-      while (c0 > 0 && (c0 * U) / sl.G > ulo) --c0;
-      while (((c0 + 1) * U) / sl.G <= ulo) ++c0;
+      int64_t rb, r;
+      if (sl.bm_shift >= 0) {
+        rb = s >> sl.bm_shift;
+        r = s - (rb << sl.bm_shift);
+      } else {
+        rb = qdivmod(s, sl.bm, r);
+      }
+      int c0, nc;
+      if (rb < tab_rb) {
+        const int2 t = tC[rb];
+        c0 = t.x;
+        nc = t.y;
+      } else {
+        cta_range(rb, c0, nc);
+      }
+      const float* src = sl.part + ((c0 + rb) * sl.bm + r) * Kp;
       for (int e = lane; e < szM; e += 32) {
-        const int i = e / mc, j = e % mc;
-        const int q = rows_case ? j * mr + i : i * mc + j;
-        double v = 0.0;
-        for (int64_t cc = c0; cc < sl.G && (cc * U) / sl.G < uhi; ++cc)
-          v += (double)sl.part[((cc + rb) * sl.bm + r) * Kp + q];
+        const float* a = src + tM[e];
+        float v = a[0];
+        for (int t = 1; t < nc; ++t) v += a[t * cs];
         sM[e] = (T)v;
       }
     } else {
       const double* Ts = Tm + s * (int64_t)Kp;
-      for (int e = lane; e < szM; e += 32) {
-        const int i = e / mc, j = e % mc;
-        sM[e] = (T)(rows_case ? Ts[j * mr + i] : Ts[i * mc + j]);
+      for (int e = lane; e < szM; e += 32) sM[e] = (T)Ts[tM[e]];
+    }
+    if (pre) {
+      for (int e = lane; e < szPre; e += 32) sPre[e] = pre[ip * (int64_t)szPre + e];
+    } else if (preC.core) {
+      // Pre(ip)[j][a] = Z(ip)[j, a], slice stored column-major (mc x rk)
+      const int64_t off = (preC.idx ? (int64_t)preC.idx[ip] : ip) * (int64_t)szPre;
+      if (sizeof(T) == 4 && preC.coref) {
+        for (int e = lane; e < szPre; e += 32) sPre[e] = (T)preC.coref[off + tPre[e]];
+      } else {
+        for (int e = lane; e < szPre; e += 32) sPre[e] = (T)preC.core[off + tPre[e]];
       }
     }
-    if (pre)
-      for (int e = lane; e < szPre; e += 32) sPre[e] = pre[ip * (int64_t)szPre + e];
-    if (post)
+    if (post) {
       for (int e = lane; e < szPost; e += 32) sPost[e] = post[iq * (int64_t)szPost + e];
+    } else if (postC.core) {
+      // Post(iq)[b][i] = Z(iq)[b, i], slice stored column-major (rk1 x mr)
+      const int64_t off = (postC.idx ? (int64_t)postC.idx[iq] : iq) * (int64_t)szPost;
+      if (sizeof(T) == 4 && postC.coref) {
+        for (int e = lane; e < szPost; e += 32) sPost[e] = (T)postC.coref[off + tPost[e]];
+      } else {
+        for (int e = lane; e < szPost; e += 32) sPost[e] = (T)postC.core[off + tPost[e]];
+      }
+    }
     __syncwarp();
     // V = M * Pre  (mr x rk)
     for (int e = lane; e < szV; e += 32) {
-      const int i = e / rk, a = e % rk;
+      const int tv = tV[e], imc = tv & 0xffff, a = tv >> 16;
       T v;
-      if (pre) {
+      if (has_pre) {
         v = T(0);
-        for (int j = 0; j < mc; ++j) v = fma(sM[i * mc + j], sPre[j * rk + a], v);
+        for (int j = 0; j < mc; ++j) v = fma(sM[imc + j], sPre[j * rk + a], v);
       } else {
-        v = sM[i * mc + a];
+        v = sM[imc + a];
       }
       sV[e] = v;
     }
     __syncwarp();
     // U = Post * V  (rk1 x rk); lane owns entries e = lane + 32 u (e = beta*rk + alpha)
 #pragma unroll
-    for (int u = 0; u < 32; ++u) {
+    for (int u = 0; u < UK; ++u) {
       const int e = lane + 32 * u;
       if (e < K) {
-        const int b = e / rk, a = e % rk;
+        const int tu = tU[e], bmr = tu & 0xffff, a = tu >> 16;
         T v;
-        if (post) {
+        if (has_post) {
           v = T(0);
-          for (int i = 0; i < mr; ++i) v = fma(sPost[b * mr + i], sV[i * rk + a], v);
+          for (int i = 0; i < mr; ++i) v = fma(sPost[bmr + i], sV[i * rk + a], v);
         } else {
-          v = sV[b * rk + a];
+          v = sV[e];                          // Post = identity: U = V
         }
         acc[u] += v;
       }
     }
     __syncwarp();
+    ip += warps;
+    while (ip >= n_pre) {
+      ip -= n_pre;
+      ++iq;
+    }
   }
-  // fixed-order sum over the warps of the block (reuses the block's shared memory)
+  // fixed-order sum over the warps of the block (reuses the block's work area)
   __syncthreads();
   double* red = reinterpret_cast<double*>(smem_bc);
-  double* o = out + ((int64_t)blockIdx.y * Ik + ik) * K;
-  for (int base = 0; base < K; base += 32 * 32) {
+  const bool split = gridDim.y > 1;
+  double* o = split ? part_out + ((int64_t)blockIdx.y * Ik + ik) * K : d + ik * K;
+  const int KC = K < 1024 ? K : 1024;          // staged chunk (the work area holds warps x KC)
+  for (int base = 0; base < K; base += KC) {
     // stage this chunk of every warp's accumulators
 #pragma unroll
-    for (int u = 0; u < 32; ++u) {
+    for (int u = 0; u < UK; ++u) {
       const int e = lane + 32 * u;
-      if (e >= base && e < base + 1024 && e < K) red[w * 1024 + (e - base)] = (double)acc[u];
+      if (e >= base && e < base + KC && e < K) red[w * KC + (e - base)] = (double)acc[u];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 1024 && base + e < K; e += blockDim.x) {
+    for (int e = threadIdx.x; e < KC && base + e < K; e += blockDim.x) {
       double sum = 0.0;
-      for (int ww = 0; ww < warps; ++ww) sum += red[ww * 1024 + e];
+      for (int ww = 0; ww < warps; ++ww) sum += red[ww * KC + e];
       o[base + e] = sum;
     }
     __syncthreads();
   }
-}
-
-__global__ void k_sum_splits(const double* __restrict__ part, int nsplit, int64_t n,
-                             double* __restrict__ out) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < nsplit; ++j) s += part[(int64_t)j * n + i];
-    out[i] = s;
+  if (!split) return;
+  __threadfence();
+  if (threadIdx.x == 0) s_last = atomicAdd(ctr + ik, 1u) == gridDim.y - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    double sum = 0.0;
+    for (unsigned y = 0; y < gridDim.y; ++y) sum += __ldcg(part_out + ((int64_t)y * Ik + ik) * K + e);
+    d[ik * K + e] = sum;
   }
+  if (threadIdx.x == 0) ctr[ik] = 0u;
 }
 
 cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int mr, int mc,
                                 const void* pre, int64_t n_pre, const void* post,
                                 int64_t n_post, int64_t Ik, int rk, int rk1, double* dpart,
-                                int nsplit, double* d, bool fp64, cudaStream_t st, const SlotSrc* slots) {
-  const SlotSrc sl = slots ? *slots : SlotSrc{};
+                                int nsplit, double* d, unsigned* ctr, bool fp64, cudaStream_t st,
+                                const SlotSrc* slots, BcCore preC, BcCore postC) {
+  SlotSrc sl = slots ? *slots : SlotSrc{};
+  if (sl.part) {
+    sl.bm_shift = -1;
+    for (int b = 0; b < 31; ++b)
+      if (((int64_t)1 << b) == sl.bm) sl.bm_shift = b;
+  }
   const int64_t npairs = n_pre * n_post;
   const int64_t per = (npairs + nsplit - 1) / nsplit;
+  nsplit = (int)((npairs + per - 1) / per);
   const int threads = 128;
   dim3 grid((unsigned)Ik, (unsigned)nsplit);
-  double* target = nsplit == 1 ? d : dpart;
   const int per_warp = mr * mc + mc * rk + rk1 * mr + mr * rk;
   const size_t esz = fp64 ? sizeof(double) : sizeof(float);
-  const size_t smem = std::max((size_t)(threads / 32) * per_warp * esz, (size_t)(threads / 32) * 1024 * sizeof(double));
-  if (smem > 48 * 1024) {
-    cudaFuncSetAttribute(k_backcontract<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_backcontract<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int K = rk * rk1;
+  if (K > 1024) return cudaErrorInvalidValue;
+  const size_t work = std::max((size_t)(threads / 32) * per_warp * esz,
+                               (size_t)(threads / 32) * std::min(K, 1024) * sizeof(double));
+  const int tab_rb = (sl.part && sl.RB <= 4096) ? (int)sl.RB : 0;
+  const size_t tables = (size_t)tab_rb * 8 + sizeof(int) * (size_t)(mr * mc + mc * rk + rk1 * mr + mr * rk + K);
+  const size_t smem = (work + 15) / 16 * 16 + tables;
+  const int wb = (int)((work + 15) / 16 * 16);
+  auto go = [&](auto kern, auto tag) -> cudaError_t {
+    using E = decltype(tag);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, threads, smem, st>>>((const double*)Tsum_d, sl, Kp, rows_case ? 1 : 0, mr, mc, (const E*)pre, n_pre,
+                                      (const E*)post, n_post, preC, postC, Ik, rk, rk1, per, dpart, d, ctr, wb,
+                                      tab_rb);
+    return cudaSuccess;
+  };
+  if (fp64) {
+    if (K <= 64) go(k_backcontract<double, 2>, 0.0);
+    else if (K <= 256) go(k_backcontract<double, 8>, 0.0);
+    else go(k_backcontract<double, 32>, 0.0);
+  } else {
+    if (K <= 64) go(k_backcontract<float, 2>, 0.0f);
+    else if (K <= 256) go(k_backcontract<float, 8>, 0.0f);
+    else go(k_backcontract<float, 32>, 0.0f);
   }
-  if (fp64)
-    k_backcontract<double><<<grid, threads, smem, st>>>((const double*)Tsum_d, sl, Kp, rows_case ? 1 : 0, mr, mc,
-                                                     (const double*)pre, n_pre, (const double*)post, n_post,
-                                                     Ik, rk, rk1, per, target);
-  else
-    k_backcontract<float><<<grid, threads, smem, st>>>((const double*)Tsum_d, sl, Kp, rows_case ? 1 : 0, mr, mc,
-                                                    (const float*)pre, n_pre, (const float*)post, n_post,
-                                                    Ik, rk, rk1, per, target);
-  note_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || nsplit == 1) return e;
-  const int64_t n = Ik * rk * rk1;
-  k_sum_splits<<<(unsigned)imin((n + 255) / 256, 4096), 256, 0, st>>>(dpart, nsplit, n, d);
   note_launch();
   return cudaGetLastError();
 }
@@ -307,27 +407,73 @@ cudaError_t launch_reduce_stats(const double* stat_part, int ctas, double* stat_
 // ------------------------------------------------------------------ reconstruction
 // out(a, b) = sum_kappa A[a][kappa] C[b][kappa] = Tr(A(a) C(b)) (Def. 1 via Thm. 1's split);
 // optional comparison with a reference tensor accumulates sum (xhat - ref)^2 and sum ref^2.
+// X_hat(a, b) = <A[a], C[b]> over 64 x 64 output tiles (rows of A and C staged in shared
+// memory, 4 x 4 register micro-tiles, lanes along a so that the output is written
+// coalesced), optionally against ref: per-tile partial sums of (x_hat - ref)^2 and ref^2,
+// then per-block FP64 partials in err_part[2 block], [2 block + 1].
 template <typename T>
-__global__ void k_reconstruct(const T* __restrict__ A, const T* __restrict__ C,
-                              int64_t P_in, int64_t P_out, int Kp, const float* __restrict__ ref,
-                              float* __restrict__ out, double* __restrict__ err_part) {
+__global__ void __launch_bounds__(256) k_reconstruct(const T* __restrict__ A, const T* __restrict__ C,
+                                                     int64_t P_in, int64_t P_out, int Kp,
+                                                     const float* __restrict__ ref, float* __restrict__ out,
+                                                     double* __restrict__ err_part) {
+  extern __shared__ __align__(16) unsigned char smem_rec[];
   __shared__ double sh[2][256];
+  const int KP1 = Kp | 1;
+  T* sA = reinterpret_cast<T*>(smem_rec);   // [64][KP1]
+  T* sC = sA + 64 * KP1;                    // [64][KP1]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t na = (P_in + 63) / 64, nb = (P_out + 63) / 64;
+  const RowCol stage_rc(tid, 256, Kp);
   double se = 0.0, sr = 0.0;
-  const int64_t n = P_in * P_out;
-  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
-       l += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t a = l % P_in, b = l / P_in;
-    const T* Ar = A + a * Kp;
-    const T* Cr = C + b * Kp;
-    T v = T(0);
-    for (int k = 0; k < Kp; ++k) v = fma(Ar[k], Cr[k], v);
-    if (out) out[l] = (float)v;
-    if (ref) {
-      const double r = (double)ref[l];
-      const double dv = (double)v - r;
-      se += dv * dv;
-      sr += r * r;
+  for (int64_t t = blockIdx.x; t < na * nb; t += gridDim.x) {
+    int64_t ta;
+    const int64_t tb = qdivmod(t, na, ta);
+    const int64_t a0 = ta * 64, b0 = tb * 64;
+    __syncthreads();
+    for (RowCol rc = stage_rc; rc.r < 64; rc.next()) {
+      const int64_t a = a0 + rc.r, b = b0 + rc.r;
+      sA[rc.r * KP1 + rc.c] = a < P_in ? A[a * Kp + rc.c] : T(0);
+      sC[rc.r * KP1 + rc.c] = b < P_out ? C[b * Kp + rc.c] : T(0);
     }
+    __syncthreads();
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int k = 0; k < Kp; ++k) {
+      T av[4], cv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = sA[(tx + 16 * i) * KP1 + k];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cv[j] = sC[(ty + 16 * j) * KP1 + k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], cv[j], acc[i][j]);
+    }
+    T tse = T(0), tsr = T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t b = b0 + ty + 16 * j;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int64_t a = a0 + tx + 16 * i;
+        if (a < P_in && b < P_out) {
+          const int64_t l = a + P_in * b;
+          const T v = acc[i][j];
+          if (out) out[l] = (float)v;
+          if (ref) {
+            const T r = (T)ref[l];
+            const T dv = v - r;
+            tse = fma(dv, dv, tse);
+            tsr = fma(r, r, tsr);
+          }
+        }
+      }
+    }
+    se += (double)tse;
+    sr += (double)tsr;
   }
   if (!err_part) return;
   sh[0][threadIdx.x] = se;
@@ -349,12 +495,19 @@ __global__ void k_reconstruct(const T* __restrict__ A, const T* __restrict__ C,
 cudaError_t launch_reconstruct_mats(const void* A, const void* C, bool fp64, int64_t P_in, int64_t P_out,
                                     int Kp, const float* Xref, float* out, double* err_part,
                                     int parts, cudaStream_t st) {
-  if (fp64)
-    k_reconstruct<double><<<parts, 256, 0, st>>>((const double*)A, (const double*)C, P_in, P_out, Kp, Xref, out,
-                                                 err_part);
-  else
-    k_reconstruct<float><<<parts, 256, 0, st>>>((const float*)A, (const float*)C, P_in, P_out, Kp, Xref, out,
-                                                err_part);
+  const size_t smem = (size_t)2 * 64 * (Kp | 1) * (fp64 ? sizeof(double) : sizeof(float));
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (fp64) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_reconstruct<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_reconstruct<double><<<parts, 256, smem, st>>>((const double*)A, (const double*)C, P_in, P_out, Kp, Xref,
+                                                    out, err_part);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_reconstruct<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_reconstruct<float><<<parts, 256, smem, st>>>((const float*)A, (const float*)C, P_in, P_out, Kp, Xref, out,
+                                                   err_part);
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -385,8 +538,8 @@ __global__ void k_gather(GatherArgs g) {
     if (l < g.numel) {
       int64_t rem = l, full = 0;
       for (int m = 0; m < g.N; ++m) {
-        const int64_t i = rem % g.sdim[m];
-        rem /= g.sdim[m];
+        int64_t i;
+        rem = qdivmod(rem, g.sdim[m], i);
         const int64_t fi = g.idx[m] ? (int64_t)g.idx[m][i] : i;
         full += fi * g.fstride[m];
       }
@@ -441,8 +594,9 @@ __global__ void k_to_bf16_split(const T* __restrict__ src, int64_t rows, int Kp,
   const int64_t n = rows * ld_dst;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / ld_dst;
-    const int c = (int)(e % ld_dst);
+    int64_t cc;
+    const int64_t r = qdivmod(e, ld_dst, cc);
+    const int c = (int)cc;
     const float v = c < Kp ? (float)src[r * ld_src + c] : 0.0f;
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));

@@ -26,6 +26,7 @@ constexpr int BM = 64, BN = 64, NT = 256;
 __device__ __forceinline__ float texp(float x) { return expf(x); }
 __device__ __forceinline__ double texp(double x) { return exp(x); }
 
+
 template <typename T, int KJ, bool ROWS, bool PASS2>
 __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -42,8 +43,8 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
   const T* Sh = reinterpret_cast<const T*>(p.Sh);
   const T* Sstr = reinterpret_cast<const T*>(p.Sstr);
 
-  for (int e = tid; e < BM * Kp; e += NT) {
-    const int r = e / Kp, c = e % Kp;
+  for (RowCol rc(tid, NT, Kp); rc.r < BM; rc.next()) {
+    const int r = rc.r, c = rc.c;
     const int64_t s = s0 + r;
     sS[r * KPAD + c] = s < p.P_stat ? Sst[s * p.ld + c] : T(0);
     if (PASS2) sH[r * KPAD + c] = s < p.P_stat ? Sh[s * p.ld + c] : T(0);
@@ -56,7 +57,11 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < KJ; ++j) tacc[i][j] = T(0);
-  double st_w = 0, st_e2 = 0, st_we2 = 0, st_obs = 0, st_nf = 0, st_slots = 0, st_den = 0;
+  // statistics: FP32 partial sums per tile (FP64 for the FP64 path), integer counts, widened
+  // and added into FP64 once per tile
+  double st_w = 0, st_e2 = 0, st_we2 = 0, st_den = 0;
+  int64_t st_obs = 0, st_nf = 0, st_slots = 0;
+  const RowCol tile_rc(tid, NT, Kp);
 
   const int64_t ntiles = (p.P_strm + BN - 1) / BN;
   const int64_t tb = (int64_t)blockIdx.y * p.tiles_per_split;
@@ -64,8 +69,8 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
   for (int64_t tile = tb; tile < te; ++tile) {
     const int64_t t0 = tile * BN;
     __syncthreads();
-    for (int e = tid; e < BN * Kp; e += NT) {
-      const int r = e / Kp, c = e % Kp;
+    for (RowCol rc = tile_rc; rc.r < BN; rc.next()) {
+      const int r = rc.r, c = rc.c;
       const int64_t t = t0 + r;
       sT[r * KPAD + c] = t < p.P_strm ? Sstr[t * p.ld + c] : T(0);
     }
@@ -98,6 +103,8 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
           if (PASS2) dacc[i][j] = fma(hv[i], tv[j], dacc[i][j]);
         }
     }
+    T tw = T(0), te2 = T(0), twe2 = T(0), tden = T(0);
+    int tobs = 0, tnf = 0, tslots = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -109,27 +116,37 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
         if (s < p.P_stat && t < p.P_strm) {
           const int64_t lin = ROWS ? s + p.P_in * t : t + p.P_in * s;
           const bool obs = p.M ? ((p.M[lin >> 5] >> (lin & 31)) & 1u) : true;
-          st_slots += 1.0;
+          ++tslots;
           if (obs) {
-            st_obs += 1.0;
+            ++tobs;
             const T e = (T)p.X[lin] - acc[i][j];
             if (isfinite(e)) {
               const T w = texp(-e * e * inv2s2);
               if (PASS2) {
-                st_den += (double)w * (double)dacc[i][j] * (double)dacc[i][j];
+                tden = fma(w * dacc[i][j], dacc[i][j], tden);
               } else {
                 y = w * e;
-                st_w += (double)w;
-                st_e2 += (double)e * (double)e;
-                st_we2 += (double)(w * e) * (double)e;
+                tw += w;
+                te2 = fma(e, e, te2);
+                twe2 = fma(y, e, twe2);
               }
             } else {
-              st_nf += 1.0;
+              ++tnf;
             }
           }
         }
         if (!PASS2) sY[r * SYLD + c] = y;
       }
+    st_slots += tslots;
+    st_obs += tobs;
+    st_nf += tnf;
+    if (PASS2) {
+      st_den += (double)tden;
+    } else {
+      st_w += (double)tw;
+      st_e2 += (double)te2;
+      st_we2 += (double)twe2;
+    }
     if (!PASS2) {
       __syncthreads();
       for (int tt = 0; tt < BN; ++tt) {
@@ -160,7 +177,7 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
   }
   // fixed-order block reduction of the statistics
   __shared__ double red[7][NT / 32];
-  double v[7] = {st_w, st_e2, st_we2, st_obs, st_nf, st_slots, st_den};
+  double v[7] = {st_w, st_e2, st_we2, (double)st_obs, (double)st_nf, (double)st_slots, st_den};
 #pragma unroll
   for (int f = 0; f < 7; ++f) {
     double x = v[f];

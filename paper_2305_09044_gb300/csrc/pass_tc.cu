@@ -790,8 +790,9 @@ __global__ void k_split_rows(const float* __restrict__ src, int64_t rows, int Kp
                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
   const int64_t n = rows * kpad;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / kpad;
-    const int k = (int)(e % kpad);
+    int64_t kk;
+    const int64_t r = qdivmod(e, kpad, kk);
+    const int k = (int)kk;
     const float v = k < Kp ? src[r * Kp + k] : 0.f;
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     hi[e] = h;
@@ -804,8 +805,10 @@ __global__ void k_split_rows(const float* __restrict__ src, int64_t rows, int Kp
 __global__ void k_mask_rows(const uint32_t* __restrict__ M, int64_t P_in, int64_t P_out, int64_t W,
                             uint32_t* __restrict__ out) {
   const int64_t n = P_out * W;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = e / W, w = e % W;
+  const int step = gridDim.x * blockDim.x, e0 = blockIdx.x * blockDim.x + threadIdx.x;
+  RowCol rc(e0, step, (int)W);
+  for (int64_t e = e0; e < n; e += step, rc.next()) {
+    const int64_t b = rc.r, w = rc.c;
     const int64_t a0 = 32 * w;
     uint32_t v = 0;
     if (a0 < P_in) {
@@ -838,8 +841,10 @@ __global__ void k_mask_transpose(const uint32_t* __restrict__ M, int64_t P_in, i
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t nab = (P_in + 31) / 32;
   const int64_t nwords = (P_in * P_out + 31) / 32;
-  for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < nab * WT; task += warps) {
-    const int64_t ab = task / WT, w = task % WT;
+  const int task0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  RowCol rc(task0, (int)warps, (int)WT);
+  for (int64_t task = task0; task < nab * WT; task += warps, rc.next()) {
+    const int64_t ab = rc.r, w = rc.c;
     const int64_t a0 = ab * 32;
     const int64_t b = 32 * w + lane;
     uint32_t col = 0;

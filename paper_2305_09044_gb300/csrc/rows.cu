@@ -21,7 +21,8 @@ __global__ void k_gather_rows(const float* __restrict__ X, const uint32_t* __res
        p += (int64_t)gridDim.x * blockDim.x) {
     bool bit = false;
     if (p < n) {
-      const int64_t i = p % a.Ik, j = p / a.Ik;
+      int64_t i;
+      const int64_t j = qdivmod(p, a.Ik, i);
       int64_t lin = i * a.stride[a.k];
       for (int m = 0; m < a.N; ++m)
         if (m != a.k) lin += (int64_t)rows[j * a.N + m] * a.stride[m];
@@ -34,48 +35,54 @@ __global__ void k_gather_rows(const float* __restrict__ X, const uint32_t* __res
 }
 
 // B(j): one warp per sampled row; the running product (r_{k+1} x r_m, at most CAP = max r^2
-// entries) and its successor live in the warp's shared-memory buffers.
+// entries, column-major like the core slices), its successor and the next core slice live
+// in the warp's shared-memory buffers.  Slices are copied with all lanes and no index
+// arithmetic; the FP32 kernel reads the FP32 core copies.
+template <typename T>
+__device__ __forceinline__ void rows_slice(const RowsArgs& a, int m, int64_t i, int n, T* dst, int lane) {
+  const float* zf = sizeof(T) == 4 ? a.Zf[m] : nullptr;
+  if (zf) {
+    for (int e = lane; e < n; e += 32) dst[e] = (T)zf[i * n + e];
+  } else {
+    for (int e = lane; e < n; e += 32) dst[e] = (T)a.Z[m][i * n + e];
+  }
+}
+
 template <typename T>
 __global__ void k_rows_chain(RowsArgs a, const int32_t* __restrict__ rows, T* __restrict__ B, int CAP) {
   extern __shared__ __align__(16) unsigned char smem_rows[];
   const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* cur = reinterpret_cast<T*>(smem_rows) + (size_t)w * 2 * CAP;
+  T* cur = reinterpret_cast<T*>(smem_rows) + (size_t)w * 3 * CAP;
   T* nxt = cur + CAP;
+  T* zs = nxt + CAP;
   const int N = a.N, k = a.k;
   const int rk = a.R[k], rk1 = a.R[(k + 1) % N];
   for (int64_t j = (int64_t)blockIdx.x * warps + w; j < a.J; j += (int64_t)gridDim.x * warps) {
-    // first slice: Z_{k+1}(i), r_{k+1} x r_{k+2}; slice element (t, c) at i K_m + c r_m + t
+    // first slice: Z_{k+1}(i), r_{k+1} x r_{k+2}; element (t, c) at c r_{k+1} + t
     int m = (k + 1) % N;
-    int rows_cur = a.R[m], cols_cur = a.R[(m + 1) % N];
-    {
-      const double* z = a.Z[m] + (int64_t)rows[j * N + m] * rows_cur * cols_cur;
-      for (int e = lane; e < rows_cur * cols_cur; e += 32) {
-        const int t = e / cols_cur, c = e % cols_cur;
-        cur[e] = (T)z[c * rows_cur + t];
-      }
-    }
+    const int rows_cur = a.R[m];
+    int cols_cur = a.R[(m + 1) % N];
+    rows_slice(a, m, (int64_t)rows[j * N + m], rows_cur * cols_cur, cur, lane);
     __syncwarp();
     for (int q = 2; q < N; ++q) {
       m = (k + q) % N;
       const int rm = a.R[m], rm1 = a.R[(m + 1) % N];     // rm == cols_cur
-      const double* z = a.Z[m] + (int64_t)rows[j * N + m] * rm * rm1;
-      for (int e = lane; e < rows_cur * rm1; e += 32) {
-        const int t = e / rm1, c = e % rm1;
-        T s = T(0);
-        for (int u = 0; u < rm; ++u) s = fma(cur[t * cols_cur + u], (T)z[c * rm + u], s);
-        nxt[e] = s;
-      }
+      rows_slice(a, m, (int64_t)rows[j * N + m], rm * rm1, zs, lane);
       __syncwarp();
-      for (int e = lane; e < rows_cur * rm1; e += 32) cur[e] = nxt[e];
+      for (int c = 0; c < rm1; ++c)
+        for (int t = lane; t < rows_cur; t += 32) {
+          T s = T(0);
+          for (int u = 0; u < rm; ++u) s = fma(cur[u * rows_cur + t], zs[c * rm + u], s);
+          nxt[c * rows_cur + t] = s;
+        }
+      __syncwarp();
+      T* tmp = cur; cur = nxt; nxt = tmp;
       cols_cur = rm1;
-      __syncwarp();
     }
-    // S(j) is r_{k+1} x r_k: B[j][alpha + beta r_k] = S[beta][alpha]
+    // S(j) is r_{k+1} x r_k, S[beta][alpha] at alpha r_{k+1} + beta: B[j][alpha + beta r_k]
     T* out = B + j * (int64_t)(rk * rk1);
-    for (int e = lane; e < rk * rk1; e += 32) {
-      const int alpha = e % rk, beta = e / rk;
-      out[e] = cur[beta * rk + alpha];
-    }
+    for (int beta = 0; beta < rk1; ++beta)
+      for (int alpha = lane; alpha < rk; alpha += 32) out[alpha + beta * rk] = cur[alpha * rk1 + beta];
     __syncwarp();
   }
 }
@@ -96,7 +103,7 @@ cudaError_t launch_rows_chain(const RowsArgs& a, const int32_t* rows, void* B, b
   int rmax = 1;
   for (int m = 0; m < a.N; ++m) rmax = (int)imax(rmax, a.R[m]);
   const int cap = rmax * rmax;
-  const size_t per = (size_t)2 * cap;
+  const size_t per = (size_t)3 * cap;
   if (fp64) {
     const size_t smem = warps * per * sizeof(double);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_rows_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -8,6 +8,8 @@
 #include <mutex>
 #include <vector>
 
+#include <type_traits>
+
 #include "trd_internal.cuh"
 
 namespace trd {
@@ -23,6 +25,24 @@ __host__ __device__ inline uint64_t sm64(uint64_t seed, uint64_t m) {
 
 __device__ inline uint64_t dkey(double v) {
   const uint64_t b = (uint64_t)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+// dkey((double)f) for a finite float, from the bits alone (no FP64 instruction): the double
+// has the float's sign, the exponent rebiased by 1023 - 127 and the fraction shifted up by 29;
+// a subnormal float is normalised first.
+__device__ inline uint64_t fkey(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t sgn = (uint64_t)(u >> 31) << 63;
+  const uint32_t E = (u >> 23) & 0xffu, M = u & 0x7fffffu;
+  uint64_t b;
+  if (E != 0) {
+    b = sgn | ((uint64_t)(E + 896u) << 52) | ((uint64_t)M << 29);
+  } else if (M == 0) {
+    b = sgn;
+  } else {
+    const int p = 31 - __clz((int)M);          // leading bit: value = 1.x * 2^(p - 149)
+    b = sgn | ((uint64_t)(p + 874) << 52) | (((uint64_t)M << (52 - p)) & 0xfffffffffffffull);
+  }
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 __device__ inline double dval(uint64_t k) {
@@ -143,6 +163,26 @@ __device__ __forceinline__ void sel_consume(bool valid, double e, double x2, uin
   if (write) keys[m] = key;
   if (valid) {
     c += 1.0;
+    se += e;
+    sx += x2;
+  }
+  const unsigned dig = (unsigned)(key >> 56);
+  const unsigned act = __ballot_sync(0xffffffffu, valid);
+  if (valid) {
+    const unsigned peers = __match_any_sync(act, dig);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h0[dig], (unsigned)__popc(peers));
+  }
+}
+
+// sel_consume for FP32 residuals: the same key (fkey) and histogram, the lane's count and sums
+// kept in integer / FP32 registers (a lane takes a handful of probes) and widened once at the
+// end, so the per-probe work issues no FP64 instruction.
+__device__ __forceinline__ void sel_consume_f(bool valid, float e, float x2, uint64_t* keys, int64_t m,
+                                              bool write, unsigned int* h0, uint32_t& c, float& se, float& sx) {
+  const uint64_t key = valid ? fkey(e) : kExcluded;
+  if (write) keys[m] = key;
+  if (valid) {
+    c += 1u;
     se += e;
     sx += x2;
   }
@@ -452,9 +492,9 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_floats(const float* __restr
 // First kernel of the tensor rule: residuals at the probe entries from the merged subchains
 // of the full tensor, x_hat = sum_kappa A[a][kappa] C[b][kappa] (Thm. 1 with the ring cut in two).
 // One lane per probe (probe m is described by pa[m] (inner index, -1 when unobserved), pb[m]
-// and px[m]); each lane streams its two rows in chunks of 16 values with all loads of a chunk
-// issued before its FMAs, so a warp keeps many independent L2 reads in flight.
-template <typename T, bool VEC4>
+// and px[m]); each lane streams its two rows in chunks of 8 values with all loads of a chunk
+// issued before its FMAs.  Used when Kp is not a multiple of the 16-byte vector width.
+template <typename T>
 __global__ void __launch_bounds__(kSelThreads)
     k_sel_probe(const T* __restrict__ A, const T* __restrict__ C, int Kp, const int32_t* __restrict__ pa,
                 const int32_t* __restrict__ pb, const float* __restrict__ px, int64_t n,
@@ -476,40 +516,18 @@ __global__ void __launch_bounds__(kSelThreads)
     if (obs) {
       const T* Ar = A + (int64_t)a * Kp;
       const T* Cr = C + (int64_t)bi * Kp;
-      if constexpr (VEC4) {
-        const float4* A4 = reinterpret_cast<const float4*>(Ar);
-        const float4* C4 = reinterpret_cast<const float4*>(Cr);
-        const int nv = Kp >> 2;
-        for (int v0 = 0; v0 < nv; v0 += 4) {
-          float4 xa[4], xc[4];
+      for (int k0 = 0; k0 < Kp; k0 += 8) {
+        T xa[8], xc[8];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const bool in = v0 + q < nv;
-            xa[q] = in ? A4[v0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
-            xc[q] = in ? C4[v0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            p0 = fma(xa[q].x, xc[q].x, p0);
-            p1 = fma(xa[q].y, xc[q].y, p1);
-            p0 = fma(xa[q].z, xc[q].z, p0);
-            p1 = fma(xa[q].w, xc[q].w, p1);
-          }
+        for (int q = 0; q < 8; ++q) {
+          const bool in = k0 + q < Kp;
+          xa[q] = in ? Ar[k0 + q] : T(0);
+          xc[q] = in ? Cr[k0 + q] : T(0);
         }
-      } else {
-        for (int k0 = 0; k0 < Kp; k0 += 8) {
-          T xa[8], xc[8];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const bool in = k0 + q < Kp;
-            xa[q] = in ? Ar[k0 + q] : T(0);
-            xc[q] = in ? Cr[k0 + q] : T(0);
-          }
-#pragma unroll
-          for (int q = 0; q < 8; q += 2) {
-            p0 = fma(xa[q], xc[q], p0);
-            p1 = fma(xa[q + 1], xc[q + 1], p1);
-          }
+        for (int q = 0; q < 8; q += 2) {
+          p0 = fma(xa[q], xc[q], p0);
+          p1 = fma(xa[q + 1], xc[q + 1], p1);
         }
       }
     }
@@ -528,6 +546,110 @@ __global__ void __launch_bounds__(kSelThreads)
   sel_first_finish(work, h0, c, se, sx);
 }
 
+// Sixteen lanes per probe: a half warp reads the two merged rows of one probe with 16-byte
+// loads (a 64-entry FP32 row is one load per lane), four probes' loads in flight at a time,
+// and a shuffle tree inside the half warp sums the lane partials.  The warp takes its 32
+// probes m0 + j in two columns (half h owns probes 16 h + s, s = 0..15), so that lane j ends
+// up holding the reconstruction of its own probe.  Needs Kp a multiple of 16 / sizeof(T).
+template <typename T>
+__global__ void __launch_bounds__(kSelThreads)
+    k_sel_probe16(const T* __restrict__ A, const T* __restrict__ C, int Kp, const int32_t* __restrict__ pa,
+                  const int32_t* __restrict__ pb, const float* __restrict__ px, int64_t n,
+                  uint64_t* __restrict__ keys, double* __restrict__ work) {
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int VW = 16 / sizeof(T);
+  __shared__ unsigned int h0[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h0[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, sub = lane & 15, half = lane & 16;
+  const int nv = Kp / VW;
+  double c = 0, se = 0, sx = 0;
+  uint32_t cf = 0;
+  float sef = 0.f, sxf = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t m0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); m0 < n; m0 += stride) {
+    const int64_t m = m0 + lane;
+    const bool live = m < n;
+    const int32_t a = live ? pa[m] : -1;
+    const bool obs = a >= 0;
+    const int32_t bi = obs ? pb[m] : 0;
+    const float xf = obs ? px[m] : 0.f;
+    T mine = T(0);
+#pragma unroll
+    for (int s0 = 0; s0 < 16; s0 += 4) {
+      int32_t as[4], bs[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        as[q] = __shfl_sync(0xffffffffu, a, half + s0 + q);
+        bs[q] = __shfl_sync(0xffffffffu, bi, half + s0 + q);
+      }
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+      for (int v = sub; v < nv; v += 16) {
+        V xa[4], xc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (as[q] >= 0) {
+            xa[q] = reinterpret_cast<const V*>(A + (int64_t)as[q] * Kp)[v];
+            xc[q] = reinterpret_cast<const V*>(C + (int64_t)bs[q] * Kp)[v];
+          } else {
+            xa[q] = V{};
+            xc[q] = V{};
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if constexpr (VW == 4) {
+            acc[q] = fma(xa[q].x, xc[q].x, acc[q]);
+            acc[q] = fma(xa[q].y, xc[q].y, acc[q]);
+            acc[q] = fma(xa[q].z, xc[q].z, acc[q]);
+            acc[q] = fma(xa[q].w, xc[q].w, acc[q]);
+          } else {
+            acc[q] = fma(xa[q].x, xc[q].x, acc[q]);
+            acc[q] = fma(xa[q].y, xc[q].y, acc[q]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        T t = acc[q];
+        t += __shfl_xor_sync(0xffffffffu, t, 8);
+        t += __shfl_xor_sync(0xffffffffu, t, 4);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        if (sub == s0 + q) mine = t;
+      }
+    }
+    if constexpr (VW == 4) {
+      float e = 0.f, x2 = 0.f;
+      bool valid = false;
+      if (obs) {
+        e = xf - mine;
+        valid = isfinite(e);
+        x2 = xf * xf;
+      }
+      sel_consume_f(valid, e, x2, keys, m, live, h0, cf, sef, sxf);
+    } else {
+      double e = 0.0, x2 = 0.0;
+      bool valid = false;
+      if (obs) {
+        const T x = (T)xf;
+        const T et = x - mine;
+        valid = isfinite((double)et);
+        e = (double)et;
+        x2 = (double)x * (double)x;
+      }
+      sel_consume(valid, e, x2, keys, m, live, h0, c, se, sx);
+    }
+  }
+  if constexpr (VW == 4) {
+    c = (double)cf;
+    se = (double)sef;
+    sx = (double)sxf;
+  }
+  __syncthreads();
+  sel_first_finish(work, h0, c, se, sx);
+}
+
 // Probe description for the tensor rule: probe m is the entry lin[m] (all entries in order
 // when numel <= 2^20, else the SplitMix64(0x5eed, m) mod numel positions sorted ascending, so
 // that neighbouring probes share merged rows), split as lin = a + P_in b; pa = -1 when
@@ -538,8 +660,10 @@ __global__ void k_probe_setup(const float* __restrict__ X, const uint32_t* __res
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x) {
     const int64_t lin = lin_in ? lin_in[m] : m;
     const bool obs = M ? ((M[lin >> 5] >> (lin & 31)) & 1u) : true;
-    pa[m] = obs ? (int32_t)(lin % P_in) : -1;
-    pb[m] = (int32_t)(lin / P_in);
+    int64_t a;
+    const int64_t b = qdivmod(lin, P_in, a);
+    pa[m] = obs ? (int32_t)a : -1;
+    pb[m] = (int32_t)b;
     px[m] = X[lin];
   }
 }
@@ -590,14 +714,17 @@ cudaError_t launch_probe_sigma_merged(const void* A, const void* C, bool fp64, i
   if (e != cudaSuccess) return e;
   // one lane per probe, a few probes per lane
   const int nb = (int)imax(1, imin(kSelBlocks, (n + 2 * kSelThreads - 1) / (2 * kSelThreads)));
-  if (fp64)
-    k_sel_probe<double, false><<<nb, kSelThreads, 0, st>>>((const double*)A, (const double*)C, Kp, pa, pb, px, n,
+  if (fp64 && Kp % 2 == 0)
+    k_sel_probe16<double><<<nb, kSelThreads, 0, st>>>((const double*)A, (const double*)C, Kp, pa, pb, px, n, keys,
+                                                      work);
+  else if (fp64)
+    k_sel_probe<double><<<nb, kSelThreads, 0, st>>>((const double*)A, (const double*)C, Kp, pa, pb, px, n,
                                                            keys, work);
   else if (Kp % 4 == 0)
-    k_sel_probe<float, true><<<nb, kSelThreads, 0, st>>>((const float*)A, (const float*)C, Kp, pa, pb, px, n, keys,
-                                                         work);
+    k_sel_probe16<float><<<nb, kSelThreads, 0, st>>>((const float*)A, (const float*)C, Kp, pa, pb, px, n, keys,
+                                                     work);
   else
-    k_sel_probe<float, false><<<nb, kSelThreads, 0, st>>>((const float*)A, (const float*)C, Kp, pa, pb, px, n,
+    k_sel_probe<float><<<nb, kSelThreads, 0, st>>>((const float*)A, (const float*)C, Kp, pa, pb, px, n,
                                                           keys, work);
   note_launch();
   e = cudaGetLastError();

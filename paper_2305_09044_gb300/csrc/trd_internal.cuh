@@ -18,6 +18,33 @@ constexpr int64_t kProbeMax = int64_t(1) << 20;   // adaptive-width probe size
 constexpr uint64_t kProbeSeed = 0x5eedull;
 
 __host__ __device__ inline int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
+// Quotient and remainder of non-negative 64-bit integers through the 32-bit divider when both
+// operands fit in 32 bits: the general 64-bit division is a long routine on the FP64 unit,
+// which on this GPU issues at a small fraction of the FP32 rate.
+__device__ __forceinline__ int64_t qdiv(int64_t n, int64_t d) {
+  return ((uint64_t)n | (uint64_t)d) <= 0xffffffffull ? (int64_t)((uint32_t)n / (uint32_t)d) : n / d;
+}
+__device__ __forceinline__ int64_t qdivmod(int64_t n, int64_t d, int64_t& r) {
+  const int64_t q = qdiv(n, d);
+  r = n - q * d;
+  return q;
+}
+
+// Walks e = e0, e0 + step, ... over a row-major matrix with rows of length n as (row, col),
+// with one division at the start instead of one per element (integer division goes through
+// the conversion unit, which on this GPU issues near the FP64 rate).
+struct RowCol {
+  int r, c, dr, dc, n;
+  __device__ RowCol(int e0, int step, int n_) : r(e0 / n_), c(e0 % n_), dr(step / n_), dc(step % n_), n(n_) {}
+  __device__ void next() {
+    r += dr;
+    c += dc;
+    if (c >= n) {
+      c -= n;
+      ++r;
+    }
+  }
+};
 __host__ __device__ inline int64_t imax(int64_t a, int64_t b) { return a > b ? a : b; }
 
 // ------------------------------------------------------------------ device-side status
@@ -36,6 +63,7 @@ enum DevStatus : int {
 struct Chain {
   int n = 0;                         // number of cores (0 = identity)
   const double* core[kMaxN] = {};
+  const float* coref[kMaxN] = {};    // FP32 copy of core[j] (nullptr = convert from core[j])
   const int32_t* idx[kMaxN] = {};    // digit -> core slice (nullptr = identity)
   int64_t dim[kMaxN] = {};           // extent of each digit
   int rows[kMaxN] = {}, cols[kMaxN] = {};
@@ -105,6 +133,7 @@ struct trd_handle {
 
   // cores (FP64 master, mode-2 row-major) and FGMC factors E_k (r_k^2 x r_{k+1}^2)
   double* Z[trd::kMaxN] = {};
+  float* Zf[trd::kMaxN] = {};          // FP32 copies of the cores, kept in step with Z
   double* E[trd::kMaxN] = {};
   uint64_t ver[trd::kMaxN] = {};     // core versions
 
@@ -167,17 +196,25 @@ trd_status ensure(trd_handle* h, DevBuf& b, size_t bytes);
 // out may be null when only the BF16 operand (hi, lo optional, kpad-wide rows) is wanted
 cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool transposed, int64_t ld, cudaStream_t st,
                          __nv_bfloat16* hi = nullptr, __nv_bfloat16* lo = nullptr, int kpad = 0);
+// one core read in place of a merged one-core chain: slice idx[i] (identity when null)
+struct BcCore {
+  const double* core = nullptr;
+  const float* coref = nullptr;      // FP32 copy (read by the FP32 kernel when present)
+  const int32_t* idx = nullptr;
+};
 // partial slots of the tensor-core pass (see k_reduce_slots), read by the back-contraction
 struct SlotSrc {
   const float* part = nullptr;
   int64_t RB = 0, NT = 0, bm = 0;
   int G = 0;
+  int bm_shift = -1;                 // log2(bm) when bm is a power of two (set at launch)
 };
 cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int mr, int mc,
                                 const void* pre, int64_t n_pre, const void* post,
                                 int64_t n_post, int64_t Ik, int rk, int rk1, double* dpart,
-                                int nsplit, double* d, bool fp64, cudaStream_t st,
-                                const SlotSrc* slots = nullptr);
+                                int nsplit, double* d, unsigned* ctr, bool fp64, cudaStream_t st,
+                                const SlotSrc* slots = nullptr, BcCore preC = BcCore{},
+                                BcCore postC = BcCore{});
 cudaError_t launch_reduce_T(const void* Tpart, bool is_double, int splits, int64_t n,
                             double* Tsum, cudaStream_t st);
 cudaError_t launch_reduce_stats(const double* stat_part, int ctas, double* stat_sum,
@@ -239,11 +276,9 @@ cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* out,
 cudaError_t launch_eta(const double* num, const double* den, double fixed_eta, int* dstatus,
                        double* eta, double* eta_slot, cudaStream_t st);
 // eta (from <d,h> and the line-search partials or a reduced den, or fixed) and Z += eta h
-cudaError_t launch_step_update(double* Z, const double* h, int64_t n, const double* num, const double* part, int ctas,
+cudaError_t launch_step_update(double* Z, float* Zf, const double* h, int64_t n, const double* num, const double* part, int ctas,
                                const double* den, double fixed_eta, int* dstatus, double* eta, double* eta_slot,
                                cudaStream_t st);
-cudaError_t launch_axpy_core(double* Z, const double* h, int64_t n, const double* eta,
-                             cudaStream_t st);
 cudaError_t launch_stop_error(const double* D, double* Dprev, int64_t n, double* e_out,
                               cudaStream_t st);
 
@@ -268,6 +303,7 @@ struct RowsArgs {
   int64_t stride[kMaxN] = {};        // linear stride of each mode in X
   int R[kMaxN] = {};
   const double* Z[kMaxN] = {};       // FP64 master cores
+  const float* Zf[kMaxN] = {};       // their FP32 copies
 };
 cudaError_t launch_gather_rows(const float* X, const uint32_t* M, const RowsArgs& a, const int32_t* rows, float* XI,
                                uint32_t* PI, cudaStream_t st);

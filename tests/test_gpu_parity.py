@@ -284,3 +284,40 @@ def test_graph_replay_equals_eager(torch_cuda, prec):
         assert a["e"] == b["e"] and a["sigma"] == b["sigma"] and a["eta"] == b["eta"], (a, b)
     for za, zb in zip(ca, cb):
         assert np.array_equal(za, zb)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_reattach_after_content_change(torch_cuda, prec):
+    """New contents written behind the attached pointers and re-attached with trd_set_data
+    give the same steps as a fresh handle on the new data: nothing derived from the old
+    contents (mask layouts, probe values) survives the re-attach."""
+    from paper_2305_09044_gb300 import TRD
+    dims, ranks = (32, 24, 16, 16), (2, 3, 2, 2)
+    Xa, _, wa, _, _ = problem(dims, ranks, 0.3, 0.1, 61)
+    Xb, _, wb, _, _ = problem(dims, ranks, 0.5, 0.2, 62)
+    assert not np.array_equal(wa, wb)
+    Xd = torch_cuda.from_numpy(flat(Xa)).cuda()
+    Md = torch_cuda.from_numpy(wa.view(np.int32)).cuda()
+    t = TRD(dims, ranks, prec)
+    t.set_data(Xd, Md)
+    t.init_cores(9)
+    for _ in range(3):
+        t.step(sigma=-1.0)                      # caches and a captured graph for the old data
+    cores = t.get_cores()
+    Xd.copy_(torch_cuda.from_numpy(flat(Xb)))
+    Md.copy_(torch_cuda.from_numpy(wb.view(np.int32)))
+    t.set_data(Xd, Md)
+    u = TRD(dims, ranks, prec)
+    Xe = torch_cuda.from_numpy(flat(Xb)).cuda()
+    Me = torch_cuda.from_numpy(wb.view(np.int32)).cuda()
+    u.set_data(Xe, Me)
+    for k, z in enumerate(cores):
+        u.set_core(k, z)
+    assert t.adaptive_sigma() == u.adaptive_sigma()      # probe values of the new contents
+    ra = [t.step(sigma=2.0) for _ in range(3)]           # mask layouts of the new contents
+    rb = [u.step(sigma=2.0) for _ in range(3)]
+    for a, b in zip(ra, rb):
+        assert a["e"] == b["e"] and a["eta"] == b["eta"] and a["objective"] == b["objective"], (a, b)
+    for za, zb in zip(t.get_cores(), u.get_cores()):
+        assert np.array_equal(za, zb)
