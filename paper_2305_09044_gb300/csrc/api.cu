@@ -112,6 +112,14 @@ struct Extra {
   DevBuf probe_lin;                   // sorted probe positions (drawn once per tensor size)
   int64_t probe_lin_n = -1;
   DevBuf Ework;         // FGMC factor partial sums
+  // FGMC chain prefix Q = E_{k+1} ... E_{k+N-2} for the Gram of core q_k, prepared during the
+  // update of core q_k - 1 (which changes only E_{q_k - 1}, the chain's last factor)
+  DevBuf Qb[2];
+  bool e_stale[kMaxN] = {};   // core updated, FGMC factor not yet refreshed (done by the next
+                              // Gram, normally on the side stream)
+  const double* q_ptr = nullptr;
+  int q_k = -1, q_cols = 0;
+  uint64_t q_ver[kMaxN] = {};
   // sampled correntropy loss: cores in FP64, merged halves, their gradients, partials
   DevBuf smpZ[kMaxN], smpA, smpC, smpGA, smpGC, smpGAd, smpGCd, smpPre, smpPost, smpDpart, smpD, smpLoss;
   // BF16 tensor-core operands and the padded mask rows of the current view
@@ -143,6 +151,8 @@ struct Extra {
   // depend only on the other cores); the first pass then leaves kSideSMs SMs free
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_tail = nullptr;   // after the side stream's last work (chain prefix)
+  bool side_tail = false;          // side work after the last join not yet waited for
   int pre_k = -1;            // core whose factor is being prepared on the side stream
   double pre_lambda = 0;
   int reserve_sms = 0;       // SMs the next tensor-core pass leaves to the side stream
@@ -343,6 +353,17 @@ trd_status refresh_E(trd_handle* h, int k) {
   return TRD_OK;
 }
 
+// Refresh the FGMC factors of updated cores on the current stream before any Gram reads them.
+trd_status fresh_E(trd_handle* h) {
+  Extra* x = X_(h);
+  for (int m = 0; m < h->N; ++m)
+    if (x->e_stale[m]) {
+      TRY(refresh_E(h, m));
+      x->e_stale[m] = false;
+    }
+  return TRD_OK;
+}
+
 // G^{!=k} = Phi(E_{k+1} ... E_{k-1}) into `G` from the factors `E` (Prop. 2, E-form).
 trd_status gram_chain(trd_handle* h, int k, double* const* E, double* G) {
   const int N = h->N;
@@ -376,11 +397,61 @@ bool gram_valid(const trd_handle* h, int k) {
   return true;
 }
 
+bool q_valid(trd_handle* h, int k) {
+  const Extra* x = X_(h);
+  if (x->q_k != k || !x->q_ptr || h->N < 3) return false;
+  for (int q = 1; q <= h->N - 2; ++q)
+    if (x->q_ver[(k + q) % h->N] != h->ver[(k + q) % h->N]) return false;
+  return true;
+}
+
+// Q = E_{k+1} ... E_{k+N-2} into the prefix buffers (N - 3 products; Q = E_{k+1} for N = 3).
+trd_status build_q(trd_handle* h, int k) {
+  Extra* x = X_(h);
+  const int N = h->N;
+  if (N < 3) return TRD_OK;
+  TRY(fresh_E(h));
+  size_t chain = 1;
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) chain = std::max(chain, (size_t)h->R[a] * h->R[a] * h->R[b] * h->R[b]);
+  TRY(ensure(h, x->Qb[0], sizeof(double) * chain));
+  TRY(ensure(h, x->Qb[1], sizeof(double) * chain));
+  const int m0 = (k + 1) % N;
+  const double* cur = h->E[m0];
+  const int rows = h->R[m0] * h->R[m0];
+  int cols = h->R[(m0 + 1) % N] * h->R[(m0 + 1) % N];
+  int which = 0;
+  for (int q = 2; q <= N - 2; ++q) {
+    const int m = (k + q) % N;
+    const int rm1 = h->R[(m + 1) % N];
+    double* out = (double*)x->Qb[which].p;
+    which ^= 1;
+    CK(launch_dgemm(cur, h->E[m], out, rows, rm1 * rm1, cols, false, h->stream), "fgmc prefix");
+    cur = out;
+    cols = rm1 * rm1;
+  }
+  x->q_ptr = cur;
+  x->q_k = k;
+  x->q_cols = cols;
+  for (int q = 1; q <= N - 2; ++q) x->q_ver[(k + q) % N] = h->ver[(k + q) % N];
+  return TRD_OK;
+}
+
 trd_status ensure_gram(trd_handle* h, int k) {
   if (gram_valid(h, k)) return TRD_OK;
-  double* E[kMaxN];
-  for (int m = 0; m < h->N; ++m) E[m] = h->E[m];
-  TRY(gram_chain(h, k, E, (double*)h->G.p));
+  TRY(fresh_E(h));
+  if (q_valid(h, k)) {
+    // G = Phi(Q E_{k-1}): the prefix was formed during the previous core's update
+    const Extra* x = X_(h);
+    const int N = h->N, ml = (k + N - 1) % N;
+    const int rows = h->R[(k + 1) % N] * h->R[(k + 1) % N], cols = h->R[k] * h->R[k];
+    CK(launch_dgemm(x->q_ptr, h->E[ml], (double*)h->T1.p, rows, cols, x->q_cols, false, h->stream), "fgmc chain");
+    CK(launch_phi((const double*)h->T1.p, h->R[(k + 1) % N], h->R[k], (double*)h->G.p, h->stream), "fgmc realign");
+  } else {
+    double* E[kMaxN];
+    for (int m = 0; m < h->N; ++m) E[m] = h->E[m];
+    TRY(gram_chain(h, k, E, (double*)h->G.p));
+  }
   h->gram_k = k;
   for (int m = 0; m < h->N; ++m) h->gram_ver[m] = h->ver[m];
   return TRD_OK;
@@ -774,8 +845,12 @@ BcCore bc_core(const Chain& ch) {
   return c;
 }
 
-// split count of the back-contraction: about two (pre, post) pairs per warp of a block
-int64_t bc_splits(int64_t npairs) { return imax(1, imin((npairs + 7) / 8, 256)); }
+// split count of the back-contraction: about two (pre, post) pairs per warp of a block, and
+// no more blocks than stay resident at once (eight per SM), so that one wave covers the grid
+int64_t bc_splits(const trd_handle* h, int64_t npairs, int64_t rows) {
+  const int64_t resident = 8 * (int64_t)h->num_sms;
+  return imax(1, imin(imin((npairs + 7) / 8, 256), resident / imax(1, rows)));
+}
 
 // zeroed completion counters for n rows (each launch's last block resets its row's counter)
 trd_status bc_counters(trd_handle* h, int64_t n) {
@@ -825,7 +900,7 @@ trd_status run_gradient(trd_handle* h, int k) {
     TRY(ensure(h, h->post, e * n_post * rk1 * mr));
     CK(launch_chain(post, h->post.p, dbl, false, rk1 * mr, h->stream), "merge suffix");
   }
-  const int64_t nsplit = bc_splits(n_pre * n_post);
+  const int64_t nsplit = bc_splits(h, n_pre * n_post, h->I[k]);
   const int K = h->K[k];
   TRY(ensure(h, h->d, sizeof(double) * h->I[k] * K));
   if (nsplit > 1) TRY(ensure(h, h->dpart, sizeof(double) * nsplit * h->I[k] * K));
@@ -850,7 +925,8 @@ bool prefactor(trd_handle* h, int k, double lambda) {
   if (!x->side) {
     if (cudaStreamCreateWithFlags(&x->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&x->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&x->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&x->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x->ev_tail, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
@@ -879,6 +955,16 @@ bool prefactor(trd_handle* h, int k, double lambda) {
       st = TRD_ECUDA;
   }
   const bool ok = st == TRD_OK && cudaEventRecord(x->ev_join, x->side) == cudaSuccess;
+  // the next core's chain prefix does not involve E_k: form it behind the join, so that it
+  // overlaps the rest of this update
+  if (ok) {
+    if (build_q(h, (k + 1) % h->N) != TRD_OK || cudaEventRecord(x->ev_tail, x->side) != cudaSuccess) {
+      cudaGetLastError();
+      x->q_k = -1;
+      cudaEventRecord(x->ev_tail, x->side);
+    }
+    x->side_tail = true;
+  }
   h->stream = main_stream;
   if (!ok) {
     // join whatever was forked, then let run_update compute everything on the main stream
@@ -988,7 +1074,7 @@ trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int
                         h->stream),
      "step size and core update");
   h->ver[k]++;
-  TRY(refresh_E(h, k));
+  X_(h)->e_stale[k] = true;   // E_k only feeds the other cores' Grams: refreshed there
   h->grad_k = -1;
   h->pass1_k = -1;
   return TRD_OK;
@@ -1315,6 +1401,7 @@ void trd_destroy(trd_t* h) {
     }
     if (x->ev_fork) cudaEventDestroy(x->ev_fork);
     if (x->ev_join) cudaEventDestroy(x->ev_join);
+    if (x->ev_tail) cudaEventDestroy(x->ev_tail);
   }
   drop_graph(X_(h));
   for (int k = 0; k < kMaxN; ++k) {
@@ -1330,7 +1417,7 @@ void trd_destroy(trd_t* h) {
   for (DevBuf* b : bufs) free_buf(*b);
   Extra* x = X_(h);
   DevBuf* xb[] = {&x->Ework, &x->meta,    &x->stat_sum2, &x->Gloc,    &x->recA, &x->recC,
-                  &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr, &x->bc_ctr, &x->probe_lin, &x->probe_cand, &x->rows_dev,
+                  &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr, &x->bc_ctr, &x->probe_lin, &x->Qb[0], &x->Qb[1], &x->probe_cand, &x->rows_dev,
                   &x->bShi,  &x->bSlo,    &x->bSh,       &x->bThi,    &x->bTlo,    &x->bTT,
                   &x->Mst[0], &x->Mst[1]};
   for (DevBuf* b : xb) free_buf(*b);
@@ -1391,6 +1478,7 @@ trd_status trd_init_cores(trd_t* h, uint64_t seed, double stddev) {
     CK(cudaStreamSynchronize(h->stream), "sync");
     h->ver[k]++;
     TRY(refresh_E(h, k));
+    X_(h)->e_stale[k] = false;
     base += (uint64_t)n;
   }
   h->t = 0;
@@ -1411,6 +1499,7 @@ trd_status trd_set_core(trd_t* h, int k, const double* core) {
   h->ver[k]++;
   h->pass1_k = h->grad_k = -1;
   TRY(refresh_E(h, k));
+  X_(h)->e_stale[k] = false;
   return sync_and_status(h);
 }
 
@@ -1637,6 +1726,11 @@ trd_status step_device(trd_handle* h, const trd_params* p, int64_t* slots_out) {
     TRY(run_gradient(h, k));
     TRY(run_update(h, k, p->lambda, -1.0, p->gram, h->report_dev + R_ETA + k));
     slots += h->slots_last;
+  }
+  if (X_(h)->side_tail) {
+    // the step ends with everything it forked joined (also required by stream capture)
+    CK(cudaStreamWaitEvent(h->stream, X_(h)->ev_tail, 0), "join side stream");
+    X_(h)->side_tail = false;
   }
   {
     PScope ps(h, P_STOP);
@@ -2013,7 +2107,7 @@ trd_status trd_sampled_bwd(trd_t* h, const void* const* cores_dev, const int32_t
       TRY(ensure(h, x->smpPost, e * n_post * rk1 * mr));
       CK(launch_chain(post, x->smpPost.p, dbl, false, rk1 * mr, h->stream), "merge suffix");
     }
-    const int64_t nsplit = bc_splits(n_pre * n_post);
+    const int64_t nsplit = bc_splits(h, n_pre * n_post, h->I[k]);
     const int K = h->K[k];
     TRY(ensure(h, x->smpD, sizeof(double) * h->I[k] * K));
     if (nsplit > 1) TRY(ensure(h, x->smpDpart, sizeof(double) * nsplit * h->I[k] * K));

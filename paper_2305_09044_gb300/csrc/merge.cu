@@ -28,65 +28,92 @@ __device__ __forceinline__ void chain_slice(const Chain& ch, int j, int64_t sl, 
   }
 }
 
-template <typename Tc, typename Tout>
+// NC: the chain length as a compile-time constant (1..4; 0 = read from ch.n), so that the
+// digit arithmetic stays in registers and the per-core parameters are static operands.
+template <typename Tc, typename Tout, int NC>
 __global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_t ld, int cap,
                         __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int kpad) {
+  constexpr int JMAX = NC > 0 ? NC : kMaxN;
+  const int n = NC > 0 ? NC : ch.n;
   extern __shared__ __align__(16) unsigned char smem_chain[];
   const int warps = blockDim.x >> 5;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Tc* Mb = reinterpret_cast<Tc*>(smem_chain) + (size_t)w * 3 * cap;
   Tc* Mn = Mb + cap;
   Tc* Zs = Mn + cap;
-  for (int64_t p = (int64_t)blockIdx.x * warps + w; p < ch.count; p += (int64_t)gridDim.x * warps) {
-    int64_t rem = p;
-    int64_t sl[kMaxN];
-    for (int j = 0; j < ch.n; ++j) {
-      int64_t i;
-      rem = qdivmod(rem, ch.dim[j], i);
-      sl[j] = ch.idx[j] ? (int64_t)ch.idx[j][i] : i;
+  // maps shared by every p: output position pos <- column-major entry of the product, and
+  // column-major entry e -> (row e mod R0, column e / R0) packed as a | b << 16
+  int* tOut = reinterpret_cast<int*>(reinterpret_cast<Tc*>(smem_chain) + (size_t)warps * 3 * cap);
+  int* tAB = tOut + cap;
+  const int R0 = ch.rows[0], CN = ch.cols[n - 1];
+  for (int pos = threadIdx.x; pos < R0 * CN; pos += blockDim.x)
+    tOut[pos] = transposed ? pos : (pos % CN) * R0 + pos / CN;
+  for (int e = threadIdx.x; e < cap; e += blockDim.x) tAB[e] = (e % R0) | (e / R0) << 16;
+  __syncthreads();
+  // digits of this warp's first p and of the stride between its p's (mixed radix, digit 0
+  // fastest), advanced by digit-wise addition with carries
+  const int64_t stride = (int64_t)gridDim.x * warps;
+  int64_t dig[JMAX], sdig[JMAX];
+  {
+    int64_t rem = (int64_t)blockIdx.x * warps + w, rs = stride;
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+      if (j >= n) break;
+      rem = qdivmod(rem, ch.dim[j], dig[j]);
+      rs = qdivmod(rs, ch.dim[j], sdig[j]);
     }
-    const int R0 = ch.rows[0];
+  }
+  for (int64_t p = (int64_t)blockIdx.x * warps + w; p < ch.count; p += stride) {
     int C = ch.cols[0];
     // M(a, c) at Mb[c R0 + a]; slice j element (c, b) at Zs[b R_j + c] (the core layout)
-    chain_slice(ch, 0, sl[0], R0 * C, Mb, lane);
+    chain_slice(ch, 0, ch.idx[0] ? (int64_t)ch.idx[0][dig[0]] : dig[0], R0 * C, Mb, lane);
     __syncwarp();
-    for (int j = 1; j < ch.n; ++j) {
+#pragma unroll
+    for (int j = 1; j < JMAX; ++j) {
+      if (j >= n) break;
       const int Rj = ch.rows[j], Cj = ch.cols[j];     // Rj == C
-      chain_slice(ch, j, sl[j], Rj * Cj, Zs, lane);
+      chain_slice(ch, j, ch.idx[j] ? (int64_t)ch.idx[j][dig[j]] : dig[j], Rj * Cj, Zs, lane);
       __syncwarp();
-      for (int b = 0; b < Cj; ++b)
-        for (int a = lane; a < R0; a += 32) {
-          Tc acc = Tc(0);
-          for (int c = 0; c < C; ++c) acc = fma(Mb[c * R0 + a], Zs[b * Rj + c], acc);
-          Mn[b * R0 + a] = acc;
-        }
+      for (int e = lane; e < R0 * Cj; e += 32) {
+        const int ab = tAB[e], a = ab & 0xffff, b = ab >> 16;
+        const Tc* mrow = Mb + a;
+        const Tc* zcol = Zs + b * Rj;
+        Tc acc = Tc(0);
+        for (int c = 0; c < C; ++c) acc = fma(mrow[c * R0], zcol[c], acc);
+        Mn[e] = acc;
+      }
       __syncwarp();
       Tc* t = Mb; Mb = Mn; Mn = t;
       C = Cj;
     }
     // entry (a, b) goes to position b R0 + a (transposed) or a C + b
-    auto emit = [&](int src, int pos) {
-      const Tout v = (Tout)Mb[src];
+    for (int pos = lane; pos < R0 * C; pos += 32) {
+      const Tout v = (Tout)Mb[tOut[pos]];
       if (out) out[p * ld + pos] = v;
       if (hi) {
         const float f = (float)v;
-        const __nv_bfloat16 vh = __float2bfloat16_rn(f);
+        const __nv_bfloat16 vh = bf16_rn(f);
         hi[p * kpad + pos] = vh;
-        if (lo) lo[p * kpad + pos] = __float2bfloat16_rn(f - __bfloat162float(vh));
+        if (lo) lo[p * kpad + pos] = bf16_rn(f - __bfloat162float(vh));
       }
-    };
-    if (transposed) {
-      for (int e = lane; e < R0 * C; e += 32) emit(e, e);
-    } else {
-      for (int b = 0; b < C; ++b)
-        for (int a = lane; a < R0; a += 32) emit(b * R0 + a, a * C + b);
     }
     if (hi)
       for (int e = R0 * C + lane; e < kpad; e += 32) {
-        hi[p * kpad + e] = __float2bfloat16_rn(0.f);
-        if (lo) lo[p * kpad + e] = __float2bfloat16_rn(0.f);
+        hi[p * kpad + e] = bf16_rn(0.f);
+        if (lo) lo[p * kpad + e] = bf16_rn(0.f);
       }
     __syncwarp();
+    int64_t carry = 0;
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+      if (j >= n) break;
+      dig[j] += sdig[j] + carry;
+      carry = 0;
+      while (dig[j] >= ch.dim[j]) {
+        dig[j] -= ch.dim[j];
+        ++carry;
+      }
+    }
   }
 }
 
@@ -99,21 +126,35 @@ cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool trans
     cap = max(cap, ch.rows[0] * ch.cols[j]);
     cap = max(cap, ch.rows[j] * ch.cols[j]);
   }
+  // a few multi-indices per warp, so that the per-warp set-up is shared
   const int warps = 4;
-  int64_t blocks = (ch.count + warps - 1) / warps;
-  if (blocks > 65535LL * 8) blocks = 65535LL * 8;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = imax(1, imin((ch.count + warps - 1) / warps, (int64_t)sms * 8));
+  const size_t tab = sizeof(int) * (size_t)2 * cap;
+  auto go = [&](auto kern, size_t esz, auto* o) {
+    const size_t smem = (size_t)warps * 3 * cap * esz + tab;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<(unsigned)blocks, warps * 32, smem, st>>>(ch, o, transposed, ld, cap, hi, lo, kpad);
+  };
   if (out_double) {
-    const size_t smem = (size_t)warps * 3 * cap * sizeof(double);
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_chain<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_chain<double, double><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (double*)out, transposed, ld, cap,
-                                                                       hi, lo, kpad);
+    double* o = (double*)out;
+    switch (ch.n) {
+      case 1: go(k_chain<double, double, 1>, sizeof(double), o); break;
+      case 2: go(k_chain<double, double, 2>, sizeof(double), o); break;
+      case 3: go(k_chain<double, double, 3>, sizeof(double), o); break;
+      case 4: go(k_chain<double, double, 4>, sizeof(double), o); break;
+      default: go(k_chain<double, double, 0>, sizeof(double), o);
+    }
   } else {
-    const size_t smem = (size_t)warps * 3 * cap * sizeof(float);
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_chain<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_chain<float, float><<<(unsigned)blocks, warps * 32, smem, st>>>(ch, (float*)out, transposed, ld, cap, hi,
-                                                                     lo, kpad);
+    float* o = (float*)out;
+    switch (ch.n) {
+      case 1: go(k_chain<float, float, 1>, sizeof(float), o); break;
+      case 2: go(k_chain<float, float, 2>, sizeof(float), o); break;
+      case 3: go(k_chain<float, float, 3>, sizeof(float), o); break;
+      case 4: go(k_chain<float, float, 4>, sizeof(float), o); break;
+      default: go(k_chain<float, float, 0>, sizeof(float), o);
+    }
   }
   note_launch();
   return cudaGetLastError();
@@ -592,14 +633,14 @@ __global__ void k_to_bf16_split(const T* __restrict__ src, int64_t rows, int Kp,
                                 __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                                 __nv_bfloat16* __restrict__ hiT, int64_t ldT, int64_t ld_dst) {
   const int64_t n = rows * ld_dst;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t cc;
-    const int64_t r = qdivmod(e, ld_dst, cc);
-    const int c = (int)cc;
+  const int step = gridDim.x * blockDim.x, e0 = blockIdx.x * blockDim.x + threadIdx.x;
+  RowCol rc(e0, step, (int)ld_dst);
+  for (int64_t e = e0; e < n; e += step, rc.next()) {
+    const int64_t r = rc.r;
+    const int c = rc.c;
     const float v = c < Kp ? (float)src[r * ld_src + c] : 0.0f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    const __nv_bfloat16 h = bf16_rn(v);
+    const __nv_bfloat16 l = bf16_rn(v - __bfloat162float(h));
     hi[e] = h;
     if (lo) lo[e] = l;
     if (hiT && c < Kp) hiT[(int64_t)c * ldT + r] = h;

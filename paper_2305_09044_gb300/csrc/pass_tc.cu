@@ -789,14 +789,15 @@ __global__ void k_wait_selftest(int arrive, uint32_t limit, int* err) {
 __global__ void k_split_rows(const float* __restrict__ src, int64_t rows, int Kp, int kpad,
                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
   const int64_t n = rows * kpad;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t kk;
-    const int64_t r = qdivmod(e, kpad, kk);
-    const int k = (int)kk;
+  const int step = gridDim.x * blockDim.x, e0 = blockIdx.x * blockDim.x + threadIdx.x;
+  RowCol rc(e0, step, kpad);
+  for (int64_t e = e0; e < n; e += step, rc.next()) {
+    const int64_t r = rc.r;
+    const int k = rc.c;
     const float v = k < Kp ? src[r * Kp + k] : 0.f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 h = bf16_rn(v);
     hi[e] = h;
-    if (lo) lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+    if (lo) lo[e] = bf16_rn(v - __bfloat162float(h));
   }
 }
 

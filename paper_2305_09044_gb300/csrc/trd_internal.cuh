@@ -30,6 +30,9 @@ __device__ __forceinline__ int64_t qdivmod(int64_t n, int64_t d, int64_t& r) {
   return q;
 }
 
+// BF16 rounding (round to nearest even) through the packed conversion instruction.
+__device__ __forceinline__ __nv_bfloat16 bf16_rn(float f) { return __floats2bfloat162_rn(f, 0.f).x; }
+
 // Walks e = e0, e0 + step, ... over a row-major matrix with rows of length n as (row, col),
 // with one division at the start instead of one per element (integer division goes through
 // the conversion unit, which on this GPU issues near the FP64 rate).
