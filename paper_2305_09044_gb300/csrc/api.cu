@@ -638,12 +638,25 @@ trd_status build_merged(trd_handle* h, int k, bool with_h, __nv_bfloat16* bf16_h
   return TRD_OK;
 }
 
+// Column splits of the CUDA-core pass: the grid (row blocks x splits) should fill whole waves
+// of resident CTAs; among 1..16 splits take the best filled last wave (the fewest splits on
+// ties), since a grid just above a wave doubles the time.
 int choose_splits(const trd_handle* h, const Split& sp) {
   const int64_t gx = (sp.P_stat + 63) / 64;
   const int64_t tiles = (sp.P_strm + 63) / 64;
-  int64_t s = (2 * (int64_t)h->num_sms + gx - 1) / gx;
-  s = imax(1, imin(s, tiles));
-  return (int)s;
+  const int64_t resident = (int64_t)simt_blocks_per_sm(is_fp64(h), sp.rows, sp.Kp) * h->num_sms;
+  int64_t best = 1;
+  double best_eff = -1.0;
+  for (int64_t s = 1; s <= imin(16, tiles); ++s) {
+    const int64_t blocks = gx * s;
+    const int64_t waves = (blocks + resident - 1) / resident;
+    const double eff = (double)blocks / (double)(waves * resident);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = s;
+    }
+  }
+  return (int)best;
 }
 
 PassArgs pass_args(trd_handle* h) {

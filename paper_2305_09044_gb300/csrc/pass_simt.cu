@@ -27,21 +27,71 @@ __device__ __forceinline__ float texp(float x) { return expf(x); }
 __device__ __forceinline__ double texp(double x) { return exp(x); }
 
 
+// cp.async copies into shared memory; src_bytes below the copy size zero-fill the rest (0:
+// nothing is read)
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+constexpr int XLD = 80;   // X tile line stride (floats): 16-byte rows, the two half-warps on disjoint banks
+
+// On the FP32 path with K' <= 128 the X tile, its mask words and the streaming operand are
+// double-buffered: the next tile's are prefetched by cp.async during the current one.
+// Otherwise (two copies of the wider rows do not fit) one X buffer is filled at the start of
+// each tile, behind the reconstruction arithmetic, and the streaming operand is loaded
+// directly.
+template <typename T>
+__host__ __device__ constexpr bool simt_dbt(int Kp) { return sizeof(T) == 4 && Kp <= 128; }
+
+// Shared-memory bytes of one CTA (the layout of k_pass_simt).
+template <typename T>
+__host__ __device__ constexpr size_t simt_smem(int Kp, bool rows, bool pass2) {
+  const int KPAD = Kp | 1;
+  const int syld = rows ? BN + 1 : BN + 16;
+  const int bufs = simt_dbt<T>(Kp) ? 2 : 1;
+  return (size_t)((pass2 ? 2 : 1) * BM * KPAD + bufs * BN * KPAD + (pass2 ? 0 : BM * syld)) * sizeof(T) +
+         (size_t)bufs * BN * XLD * sizeof(float) + (size_t)bufs * 256 * sizeof(uint32_t);
+}
+
 template <typename T, int KJ, bool ROWS, bool PASS2>
 __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int SYLD = ROWS ? BN + 1 : BN + 16;
   const int Kp = p.Kp;
+  const bool DBT = simt_dbt<T>(Kp);
   const int KPAD = Kp | 1;
-  T* sS = reinterpret_cast<T*>(smraw);           // [BM][KPAD] stationary rows
-  T* sH = sS + BM * KPAD;                        // [BM][KPAD] stationary rows with h (pass 2)
-  T* sT = PASS2 ? sH + BM * KPAD : sS + BM * KPAD;  // [BN][KPAD] streaming tile
-  T* sY = sT + BN * KPAD;                        // [BM][SYLD] weighted residuals (pass 1)
+  // X tiles and mask words of the next streaming tile are prefetched by cp.async while the
+  // current one is computed (line L of a tile: streaming index L (ROWS) or stationary index L,
+  // 64 consecutive entries of X along it; its mask bits come as 3 words and a bit offset)
+  const int nbuf = DBT ? 2 : 1;
+  float* sX = reinterpret_cast<float*>(smraw);                      // [nbuf][BN][XLD]
+  uint32_t* sMk = reinterpret_cast<uint32_t*>(sX + nbuf * BN * XLD); // [nbuf][64][4]
+  T* sS = reinterpret_cast<T*>(sMk + nbuf * 256);                   // [BM][KPAD] stationary rows
+  T* sH = sS + BM * KPAD;                                        // [BM][KPAD] with h (pass 2)
+  T* sT0 = PASS2 ? sH + BM * KPAD : sS + BM * KPAD;              // [DBT ? 2 : 1][BN][KPAD]
+  T* sY = sT0 + (DBT ? 2 : 1) * BN * KPAD;                       // [BM][SYLD] weighted residuals
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t s0 = (int64_t)blockIdx.x * BM;
   const T* Sst = reinterpret_cast<const T*>(p.Sst);
   const T* Sh = reinterpret_cast<const T*>(p.Sh);
   const T* Sstr = reinterpret_cast<const T*>(p.Sstr);
+  const int64_t nwords = (p.P_in * (ROWS ? p.P_strm : p.P_stat) + 31) / 32;
+  const bool vec = (p.P_in & 3) == 0;   // 16-byte X rows
 
   for (RowCol rc(tid, NT, Kp); rc.r < BM; rc.next()) {
     const int r = rc.r, c = rc.c;
@@ -62,21 +112,83 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
   double st_w = 0, st_e2 = 0, st_we2 = 0, st_den = 0;
   int64_t st_obs = 0, st_nf = 0, st_slots = 0;
   const RowCol tile_rc(tid, NT, Kp);
+  const int64_t s_valid = imin(BM, p.P_stat - s0);
 
   const int64_t ntiles = (p.P_strm + BN - 1) / BN;
   const int64_t tb = (int64_t)blockIdx.y * p.tiles_per_split;
   const int64_t te = imin(ntiles, tb + p.tiles_per_split);
-  for (int64_t tile = tb; tile < te; ++tile) {
-    const int64_t t0 = tile * BN;
-    __syncthreads();
+
+  auto load_T = [&](int64_t t0, T* dst, bool async) {
     for (RowCol rc = tile_rc; rc.r < BN; rc.next()) {
-      const int r = rc.r, c = rc.c;
-      const int64_t t = t0 + r;
-      sT[r * KPAD + c] = t < p.P_strm ? Sstr[t * p.ld + c] : T(0);
+      const int64_t t = t0 + rc.r;
+      const bool in = t < p.P_strm;
+      if (async) {
+        const T* src = in ? Sstr + t * p.ld + rc.c : Sstr;
+        if (sizeof(T) == 4) cp_async4(dst + rc.r * KPAD + rc.c, src, in ? 4 : 0);
+        else cp_async8(dst + rc.r * KPAD + rc.c, src, in ? 8 : 0);
+      } else {
+        dst[rc.r * KPAD + rc.c] = in ? Sstr[t * p.ld + rc.c] : T(0);
+      }
     }
+  };
+  auto issue = [&](int64_t tile, int buf) {
+    const int64_t t0 = tile * BN;
+    const int64_t t_valid = imin(BN, p.P_strm - t0);
+    const int64_t lines = ROWS ? t_valid : s_valid, along = ROWS ? s_valid : t_valid;
+    float* dx = sX + buf * BN * XLD;
+    if (vec) {
+      for (int q = tid; q < BN * 16; q += NT) {
+        const int L = q >> 4, e = (q & 15) * 4;
+        if (L < lines) {
+          const int64_t base = ROWS ? s0 + p.P_in * (t0 + L) : t0 + p.P_in * (s0 + L);
+          const int nv = (int)imax(0, imin(4, along - e));
+          cp_async16(dx + L * XLD + e, nv > 0 ? p.X + base + e : p.X, nv * 4);
+        }
+      }
+    } else {
+      for (int q = tid; q < BN * 64; q += NT) {
+        const int L = q >> 6, e = q & 63;
+        if (L < lines && e < along) {
+          const int64_t base = ROWS ? s0 + p.P_in * (t0 + L) : t0 + p.P_in * (s0 + L);
+          cp_async4(dx + L * XLD + e, p.X + base + e, 4);
+        }
+      }
+    }
+    if (p.M) {
+      const int L = tid >> 2, k = tid & 3;
+      if (L < lines) {
+        const int64_t base = ROWS ? s0 + p.P_in * (t0 + L) : t0 + p.P_in * (s0 + L);
+        uint32_t* dm = sMk + buf * 256 + tid;
+        if (k < 3) {
+          const int64_t w = (base >> 5) + k;
+          if (w < nwords) cp_async4(dm, p.M + w, 4);
+        } else {
+          *dm = (uint32_t)(base & 31);
+        }
+      }
+    }
+    if (DBT) load_T(t0, sT0 + buf * BN * KPAD, true);
+  };
+
+  if (DBT) {
+    issue(tb, 0);
+    cp_async_commit();
+  }
+  for (int64_t tile = tb; tile < te; ++tile) {
+    const int buf = DBT ? (int)((tile - tb) & 1) : 0;
+    const int64_t t0 = tile * BN;
+    if (DBT) {
+      if (tile + 1 < te) issue(tile + 1, buf ^ 1);
+    } else {
+      issue(tile, 0);
+    }
+    cp_async_commit();
+    T* sT = sT0 + buf * BN * KPAD;
+    if (DBT) cp_async_wait1();
+    else load_T(t0, sT, false);
     __syncthreads();
     // micro-tile: the thread index that runs along the memory-contiguous direction of X
-    // is tx, so global loads of x are coalesced
+    // is tx, so the X tile is read from shared memory without bank conflicts
     T acc[4][4], dacc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -103,6 +215,12 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
           if (PASS2) dacc[i][j] = fma(hv[i], tv[j], dacc[i][j]);
         }
     }
+    if (!DBT) {
+      cp_async_wait0();
+      __syncthreads();
+    }
+    const float* xt = sX + buf * BN * XLD;
+    const uint32_t* mk = sMk + buf * 256;
     T tw = T(0), te2 = T(0), twe2 = T(0), tden = T(0);
     int tobs = 0, tnf = 0, tslots = 0;
 #pragma unroll
@@ -114,21 +232,25 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
         const int64_t s = s0 + r, t = t0 + c;
         T y = T(0);
         if (s < p.P_stat && t < p.P_strm) {
-          const int64_t lin = ROWS ? s + p.P_in * t : t + p.P_in * s;
-          const bool obs = p.M ? ((p.M[lin >> 5] >> (lin & 31)) & 1u) : true;
+          const int L = ROWS ? c : r, e = ROWS ? r : c;
+          bool obs = true;
+          if (p.M) {
+            const int q = (int)mk[L * 4 + 3] + e;
+            obs = (mk[L * 4 + (q >> 5)] >> (q & 31)) & 1u;
+          }
           ++tslots;
           if (obs) {
             ++tobs;
-            const T e = (T)p.X[lin] - acc[i][j];
-            if (isfinite(e)) {
-              const T w = texp(-e * e * inv2s2);
+            const T ev = (T)xt[L * XLD + e] - acc[i][j];
+            if (isfinite(ev)) {
+              const T w = texp(-ev * ev * inv2s2);
               if (PASS2) {
                 tden = fma(w * dacc[i][j], dacc[i][j], tden);
               } else {
-                y = w * e;
+                y = w * ev;
                 tw += w;
-                te2 = fma(e, e, te2);
-                twe2 = fma(y, e, twe2);
+                te2 = fma(ev, ev, te2);
+                twe2 = fma(y, ev, twe2);
               }
             } else {
               ++tnf;
@@ -162,6 +284,7 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
         }
       }
     }
+    __syncthreads();   // this tile's buffers are refilled by the next iteration
   }
   if (!PASS2) {
     T* Tp = reinterpret_cast<T*>(p.Tpart) + (int64_t)blockIdx.y * p.P_stat * Kp;
@@ -193,11 +316,24 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
   if (tid == 7) p.stat_part[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 8 + 7] = 0.0;
 }
 
+// Resident CTAs per SM of the pass-1 kernel (registers and shared memory), for the grid size.
+template <typename T, int KJ>
+int blocks_per_sm_kj(int Kp, bool rows) {
+  const size_t smem = simt_smem<T>(Kp, rows, false);
+  int n = 0;
+  auto q = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, smem) != cudaSuccess) n = 0;
+  };
+  if (rows) q(k_pass_simt<T, KJ, true, false>);
+  else q(k_pass_simt<T, KJ, false, false>);
+  cudaGetLastError();
+  return n > 0 ? n : 1;
+}
+
 template <typename T, int KJ>
 cudaError_t launch_kj(const PassArgs& a, bool rows, bool pass2, dim3 grid, cudaStream_t st) {
-  const int KPAD = a.Kp | 1;
-  const int syld = rows ? BN + 1 : BN + 16;
-  const size_t smem = (size_t)((pass2 ? 2 : 1) * BM * KPAD + BN * KPAD + (pass2 ? 0 : BM * syld)) * sizeof(T);
+  const size_t smem = simt_smem<T>(a.Kp, rows, pass2);
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -209,6 +345,19 @@ cudaError_t launch_kj(const PassArgs& a, bool rows, bool pass2, dim3 grid, cudaS
   return pass2 ? go(k_pass_simt<T, KJ, false, true>) : go(k_pass_simt<T, KJ, false, false>);
 }
 }  // namespace
+
+int simt_blocks_per_sm(bool is_double, bool rows_case, int Kp) {
+  const int kj = (Kp + 15) / 16;
+  if (is_double) {
+    if (kj <= 1) return blocks_per_sm_kj<double, 1>(Kp, rows_case);
+    if (kj <= 4) return blocks_per_sm_kj<double, 4>(Kp, rows_case);
+    return blocks_per_sm_kj<double, 7>(Kp, rows_case);
+  }
+  if (kj <= 1) return blocks_per_sm_kj<float, 1>(Kp, rows_case);
+  if (kj <= 4) return blocks_per_sm_kj<float, 4>(Kp, rows_case);
+  if (kj <= 7) return blocks_per_sm_kj<float, 7>(Kp, rows_case);
+  return blocks_per_sm_kj<float, 16>(Kp, rows_case);
+}
 
 cudaError_t launch_pass_simt(const PassArgs& a_in, bool is_double, bool rows_case, bool pass2,
                              int splits, int* ctas_out, int* splits_out, cudaStream_t st) {

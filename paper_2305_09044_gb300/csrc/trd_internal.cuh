@@ -234,6 +234,7 @@ cudaError_t launch_to_bf16_split(const void* src, bool src_double, int64_t rows,
                                  cudaStream_t st);
 
 // pass_simt.cu
+int simt_blocks_per_sm(bool is_double, bool rows_case, int Kp);   // resident pass-1 CTAs per SM
 cudaError_t launch_pass_simt(const PassArgs& a, bool is_double, bool rows_case, bool pass2,
                              int splits, int* ctas_out, int* splits_out, cudaStream_t st);
 
