@@ -97,6 +97,7 @@ struct Extra {
   DevBuf bc_ctr;                      // per-row completion counters of the back-contraction
   DevBuf probe_cand;                  // selection candidates of the adaptive width
   SlotSrc slots;                      // partial slots of the last tensor-core pass 1
+  double* obj_slot = nullptr;         // report slot for the objective of the next pass 1
   // uniform row sampling (trd_sample_rows): J multi-indices of the modes other than row_k
   bool row_view = false;
   int row_k = -1;
@@ -767,7 +768,8 @@ trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
   if (x->row_view)
     CK(launch_reduce_slots((const float*)h->Tpart.p, RB, NT, G, sp.P_stat, sp.Kp, (double*)h->Tsum.p, h->stream),
        "reduce contraction");
-  CK(launch_reduce_stats((const double*)h->stat_part.p, G, (double*)h->stat_sum.p, h->dstatus, h->stream),
+  CK(launch_reduce_stats((const double*)h->stat_part.p, G, (double*)h->stat_sum.p, h->dstatus, h->stream,
+                         x->obj_slot),
      "reduce statistics");
   h->ctas = G;
   return TRD_OK;
@@ -838,8 +840,9 @@ trd_status run_pass1(trd_handle* h, int k, bool full_stats = true) {
     PScope ps(h, P_REDUCE);
     CK(launch_reduce_T(h->Tpart.p, is_fp64(h), used, sp.P_stat * (int64_t)sp.Kp, (double*)h->Tsum.p,
                        h->stream), "reduce contraction");
-    CK(launch_reduce_stats((const double*)h->stat_part.p, ctas, (double*)h->stat_sum.p, h->dstatus,
-                           h->stream), "reduce statistics");
+    CK(launch_reduce_stats((const double*)h->stat_part.p, ctas, (double*)h->stat_sum.p, h->dstatus, h->stream,
+                           X_(h)->obj_slot),
+       "reduce statistics");
   }
   h->pass1_k = k;
   h->grad_k = -1;
@@ -1731,11 +1734,11 @@ trd_status step_device(trd_handle* h, const trd_params* p, int64_t* slots_out) {
       x->pre_k = -1;
       if (p->gram == TRD_GRAM_GLOBAL && prefactor(h, k, p->lambda)) x->reserve_sms = kSideSMs;
     }
+    x->obj_slot = h->report_dev + R_OBJ + k;   // the statistics reduction writes the objective
     const trd_status s1 = run_pass1(h, k, false);
     x->reserve_sms = 0;
+    x->obj_slot = nullptr;
     TRY(s1);
-    CK(cudaMemcpyAsync(h->report_dev + R_OBJ + k, (double*)h->stat_sum.p + 2, sizeof(double),
-                       cudaMemcpyDeviceToDevice, h->stream), "objective");
     TRY(run_gradient(h, k));
     TRY(run_update(h, k, p->lambda, -1.0, p->gram, h->report_dev + R_ETA + k));
     slots += h->slots_last;

@@ -430,17 +430,23 @@ cudaError_t launch_reduce_T(const void* Tpart, bool is_double, int splits, int64
 
 // stat_part[c][8] -> stat_sum[8], fixed order: warp f sums field f (lane-strided partial
 // sums, then a fixed shuffle tree).
-__global__ void k_reduce_stats(const double* __restrict__ part, int ctas, double* __restrict__ out) {
+// Field f of the per-CTA statistics summed by warp f in a fixed order; the objective sum
+// (field 2) is also written to `obj` when given (the step report's slot).
+__global__ void k_reduce_stats(const double* __restrict__ part, int ctas, double* __restrict__ out,
+                               double* __restrict__ obj) {
   const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double s = 0.0;
   for (int c = lane; c < ctas; c += 32) s += part[(int64_t)c * 8 + f];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) out[f] = s;
+  if (lane == 0) {
+    out[f] = s;
+    if (f == 2 && obj) *obj = s;
+  }
 }
 
 cudaError_t launch_reduce_stats(const double* stat_part, int ctas, double* stat_sum,
-                                int* /*dstatus*/, cudaStream_t st) {
-  k_reduce_stats<<<1, 256, 0, st>>>(stat_part, ctas, stat_sum);
+                                int* /*dstatus*/, cudaStream_t st, double* obj) {
+  k_reduce_stats<<<1, 256, 0, st>>>(stat_part, ctas, stat_sum, obj);
   note_launch();
   return cudaGetLastError();
 }

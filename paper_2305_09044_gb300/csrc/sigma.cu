@@ -310,15 +310,16 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_digit(const uint64_t* __res
         s2 = fma(d, d, s2);
       }
       const unsigned dig = (unsigned)((k >> shift) & 0xffu);
+      // the distinct prefixes of one digit are disjoint, so a key counts for at most one
+      // target: one aggregated histogram update per key
+      int tk = -1;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        if (alias[t] != t) continue;                    // uniform across the block
-        const bool hit = valid && (k & himask) == pre[t];
-        const unsigned act = __ballot_sync(0xffffffffu, hit);
-        if (hit) {
-          const unsigned peers = __match_any_sync(act, dig);
-          if (lane == __ffs(peers) - 1) atomicAdd(&h[t][dig], (unsigned)__popc(peers));
-        }
+      for (int t = 0; t < 4; ++t)
+        if (alias[t] == t && valid && (k & himask) == pre[t]) tk = t;
+      const unsigned act = __ballot_sync(0xffffffffu, tk >= 0);
+      if (tk >= 0) {
+        const unsigned peers = __match_any_sync(act, (unsigned)tk << 8 | dig);
+        if (lane == __ffs(peers) - 1) atomicAdd(&h[tk][dig], (unsigned)__popc(peers));
       }
     }
   }

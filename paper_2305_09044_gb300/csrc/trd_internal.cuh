@@ -221,7 +221,7 @@ cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int 
 cudaError_t launch_reduce_T(const void* Tpart, bool is_double, int splits, int64_t n,
                             double* Tsum, cudaStream_t st);
 cudaError_t launch_reduce_stats(const double* stat_part, int ctas, double* stat_sum,
-                                int* dstatus, cudaStream_t st);
+                                int* dstatus, cudaStream_t st, double* obj = nullptr);
 cudaError_t launch_reconstruct_mats(const void* A, const void* C, bool fp64, int64_t P_in, int64_t P_out,
                                     int Kp, const float* Xref, float* out, double* err_part,
                                     int parts, cudaStream_t st);
