@@ -16,6 +16,8 @@
 // each CTA keeps its 64 stationary rows resident and streams a contiguous range of
 // streaming tiles.  Partial contractions and statistics are written per CTA and reduced
 // in a fixed order (no atomics), so results are bitwise reproducible.
+#include <type_traits>
+
 #include "trd_internal.cuh"
 
 namespace trd {
@@ -58,23 +60,36 @@ constexpr int XLD = 80;   // X tile line stride (floats): 16-byte rows, the two 
 template <typename T>
 __host__ __device__ constexpr bool simt_dbt(int Kp) { return sizeof(T) == 4 && Kp <= 128; }
 
+// Row stride of the operand tiles in shared memory: whole 16-byte chunks (vector loads along
+// K'), an odd number of them, so that 16 consecutive rows read at one K' offset fall on
+// distinct banks; the padding columns hold zeros.
+template <typename T>
+__host__ __device__ constexpr int simt_kpad(int Kp) {
+  const int U = 16 / (int)sizeof(T);
+  const int k = (Kp + U - 1) / U * U;
+  return ((k / U) % 2 == 0) ? k + U : k;
+}
+constexpr int SYLD = BN + 4;   // weighted-residual rows: 16-byte aligned, two rows on distinct banks
+
 // Shared-memory bytes of one CTA (the layout of k_pass_simt).
 template <typename T>
 __host__ __device__ constexpr size_t simt_smem(int Kp, bool rows, bool pass2) {
-  const int KPAD = Kp | 1;
-  const int syld = rows ? BN + 1 : BN + 16;
+  const int KPAD = simt_kpad<T>(Kp);
+  const int syld = SYLD;
   const int bufs = simt_dbt<T>(Kp) ? 2 : 1;
   return (size_t)((pass2 ? 2 : 1) * BM * KPAD + bufs * BN * KPAD + (pass2 ? 0 : BM * syld)) * sizeof(T) +
          (size_t)bufs * BN * XLD * sizeof(float) + (size_t)bufs * 256 * sizeof(uint32_t);
 }
 
-template <typename T, int KJ, bool ROWS, bool PASS2>
+// KM: groups of 16 U-wide column chunks of the contraction per thread (U = 16 / sizeof(T)).
+template <typename T, int KM, bool ROWS, bool PASS2>
 __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int SYLD = ROWS ? BN + 1 : BN + 16;
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int U = 16 / sizeof(T);
   const int Kp = p.Kp;
   const bool DBT = simt_dbt<T>(Kp);
-  const int KPAD = Kp | 1;
+  const int KPAD = simt_kpad<T>(Kp);
   // X tiles and mask words of the next streaming tile are prefetched by cp.async while the
   // current one is computed (line L of a tile: streaming index L (ROWS) or stationary index L,
   // 64 consecutive entries of X along it; its mask bits come as 3 words and a bit offset)
@@ -93,35 +108,49 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
   const int64_t nwords = (p.P_in * (ROWS ? p.P_strm : p.P_stat) + 31) / 32;
   const bool vec = (p.P_in & 3) == 0;   // 16-byte X rows
 
-  for (RowCol rc(tid, NT, Kp); rc.r < BM; rc.next()) {
+  for (RowCol rc(tid, NT, KPAD); rc.r < BM; rc.next()) {
     const int r = rc.r, c = rc.c;
     const int64_t s = s0 + r;
-    sS[r * KPAD + c] = s < p.P_stat ? Sst[s * p.ld + c] : T(0);
-    if (PASS2) sH[r * KPAD + c] = s < p.P_stat ? Sh[s * p.ld + c] : T(0);
+    const bool in = s < p.P_stat && c < Kp;
+    sS[r * KPAD + c] = in ? Sst[s * p.ld + c] : T(0);
+    if (PASS2) sH[r * KPAD + c] = in ? Sh[s * p.ld + c] : T(0);
   }
   const double sig = *p.sigma;
   const T inv2s2 = isinf(sig) ? T(0) : T(1.0 / (2.0 * sig * sig));
 
-  T tacc[4][KJ];
+  // gradient accumulators: rows ty + 16 i, columns U (tx + 16 m) + u
+  T tacc[4][KM * U];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < KJ; ++j) tacc[i][j] = T(0);
+    for (int j = 0; j < KM * U; ++j) tacc[i][j] = T(0);
   // statistics: FP32 partial sums per tile (FP64 for the FP64 path), integer counts, widened
   // and added into FP64 once per tile
   double st_w = 0, st_e2 = 0, st_we2 = 0, st_den = 0;
   int64_t st_obs = 0, st_nf = 0, st_slots = 0;
-  const RowCol tile_rc(tid, NT, Kp);
+  const RowCol tile_rc(tid, NT, KPAD);
+  const int nchunk = KPAD / U;                   // 16-byte chunks per operand row
+  const bool vecT = (p.ld % U) == 0;             // streaming rows 16-byte aligned in memory
   const int64_t s_valid = imin(BM, p.P_stat - s0);
 
   const int64_t ntiles = (p.P_strm + BN - 1) / BN;
   const int64_t tb = (int64_t)blockIdx.y * p.tiles_per_split;
   const int64_t te = imin(ntiles, tb + p.tiles_per_split);
 
+  // streaming rows t0 .. t0 + 63 into dst [BN][KPAD] (zeros beyond P_strm and beyond K')
   auto load_T = [&](int64_t t0, T* dst, bool async) {
+    if (async && vecT) {
+      for (int q = tid; q < BN * nchunk; q += NT) {
+        const int r = q / nchunk, c = (q - r * nchunk) * U;
+        const int64_t t = t0 + r;
+        const int nv = (t < p.P_strm) ? (int)imax(0, imin(U, Kp - c)) : 0;
+        cp_async16(dst + r * KPAD + c, nv > 0 ? Sstr + t * p.ld + c : Sstr, nv * (int)sizeof(T));
+      }
+      return;
+    }
     for (RowCol rc = tile_rc; rc.r < BN; rc.next()) {
       const int64_t t = t0 + rc.r;
-      const bool in = t < p.P_strm;
+      const bool in = t < p.P_strm && rc.c < Kp;
       if (async) {
         const T* src = in ? Sstr + t * p.ld + rc.c : Sstr;
         if (sizeof(T) == 4) cp_async4(dst + rc.r * KPAD + rc.c, src, in ? 4 : 0);
@@ -194,25 +223,33 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) { acc[i][j] = T(0); dacc[i][j] = T(0); }
-    for (int k = 0; k < Kp; ++k) {
-      T sv[4], hv[4], tv[4];
+    // 16-byte loads along K' (U values per load; the zero padding adds nothing)
+    for (int k = 0; k < KPAD; k += U) {
+      V sv[4], hv[4], tv[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int r = ROWS ? tx + 16 * i : ty + 16 * i;
-        sv[i] = sS[r * KPAD + k];
-        if (PASS2) hv[i] = sH[r * KPAD + k];
+        sv[i] = *reinterpret_cast<const V*>(sS + r * KPAD + k);
+        if (PASS2) hv[i] = *reinterpret_cast<const V*>(sH + r * KPAD + k);
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int c = ROWS ? ty + 16 * j : tx + 16 * j;
-        tv[j] = sT[c * KPAD + k];
+        tv[j] = *reinterpret_cast<const V*>(sT + c * KPAD + k);
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          acc[i][j] = fma(sv[i], tv[j], acc[i][j]);
-          if (PASS2) dacc[i][j] = fma(hv[i], tv[j], dacc[i][j]);
+          const T* a = reinterpret_cast<const T*>(&sv[i]);
+          const T* b = reinterpret_cast<const T*>(&tv[j]);
+#pragma unroll
+          for (int u = 0; u < U; ++u) acc[i][j] = fma(a[u], b[u], acc[i][j]);
+          if (PASS2) {
+            const T* hh = reinterpret_cast<const T*>(&hv[i]);
+#pragma unroll
+            for (int u = 0; u < U; ++u) dacc[i][j] = fma(hh[u], b[u], dacc[i][j]);
+          }
         }
     }
     if (!DBT) {
@@ -271,16 +308,28 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
     }
     if (!PASS2) {
       __syncthreads();
-      for (int tt = 0; tt < BN; ++tt) {
-        T yv[4];
+      // T(s, c) += sum_t Y(s, t) S_str(t, c): rows s = ty + 16 i, columns U (tx + 16 m) + u,
+      // U streaming indices per step (vector loads of Y rows and of S_str column chunks)
+      for (int tt = 0; tt < BN; tt += U) {
+        V yv[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) yv[i] = sY[(ty + 16 * i) * SYLD + tt];
+        for (int i = 0; i < 4; ++i) yv[i] = *reinterpret_cast<const V*>(sY + (ty + 16 * i) * SYLD + tt);
 #pragma unroll
-        for (int j = 0; j < KJ; ++j) {
-          const int c = tx + 16 * j;
-          const T cv = c < Kp ? sT[tt * KPAD + c] : T(0);
+        for (int q = 0; q < U; ++q) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) tacc[i][j] = fma(yv[i], cv, tacc[i][j]);
+          for (int m = 0; m < KM; ++m) {
+            const int c = U * (tx + 16 * m);
+            V cv;
+            if (c < KPAD) cv = *reinterpret_cast<const V*>(sT + (tt + q) * KPAD + c);
+            else cv = V{};
+            const T* cc = reinterpret_cast<const T*>(&cv);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const T y = reinterpret_cast<const T*>(&yv[i])[q];
+#pragma unroll
+              for (int u = 0; u < U; ++u) tacc[i][m * U + u] = fma(y, cc[u], tacc[i][m * U + u]);
+            }
+          }
         }
       }
     }
@@ -292,10 +341,12 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
     for (int i = 0; i < 4; ++i) {
       const int64_t s = s0 + ty + 16 * i;
 #pragma unroll
-      for (int j = 0; j < KJ; ++j) {
-        const int c = tx + 16 * j;
-        if (s < p.P_stat && c < Kp) Tp[s * Kp + c] = tacc[i][j];
-      }
+      for (int m = 0; m < KM; ++m)
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int c = U * (tx + 16 * m) + u;
+          if (s < p.P_stat && c < Kp) Tp[s * Kp + c] = tacc[i][m * U + u];
+        }
     }
   }
   // fixed-order block reduction of the statistics
@@ -317,7 +368,7 @@ __global__ void __launch_bounds__(NT) k_pass_simt(const PassArgs p) {
 }
 
 // Resident CTAs per SM of the pass-1 kernel (registers and shared memory), for the grid size.
-template <typename T, int KJ>
+template <typename T, int KM>
 int blocks_per_sm_kj(int Kp, bool rows) {
   const size_t smem = simt_smem<T>(Kp, rows, false);
   int n = 0;
@@ -325,13 +376,13 @@ int blocks_per_sm_kj(int Kp, bool rows) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, smem) != cudaSuccess) n = 0;
   };
-  if (rows) q(k_pass_simt<T, KJ, true, false>);
-  else q(k_pass_simt<T, KJ, false, false>);
+  if (rows) q(k_pass_simt<T, KM, true, false>);
+  else q(k_pass_simt<T, KM, false, false>);
   cudaGetLastError();
   return n > 0 ? n : 1;
 }
 
-template <typename T, int KJ>
+template <typename T, int KM>
 cudaError_t launch_kj(const PassArgs& a, bool rows, bool pass2, dim3 grid, cudaStream_t st) {
   const size_t smem = simt_smem<T>(a.Kp, rows, pass2);
   if (smem > 226 * 1024) return cudaErrorInvalidValue;
@@ -341,22 +392,27 @@ cudaError_t launch_kj(const PassArgs& a, bool rows, bool pass2, dim3 grid, cudaS
     note_launch();
     return cudaGetLastError();
   };
-  if (rows) return pass2 ? go(k_pass_simt<T, KJ, true, true>) : go(k_pass_simt<T, KJ, true, false>);
-  return pass2 ? go(k_pass_simt<T, KJ, false, true>) : go(k_pass_simt<T, KJ, false, false>);
+  if (rows) return pass2 ? go(k_pass_simt<T, KM, true, true>) : go(k_pass_simt<T, KM, true, false>);
+  return pass2 ? go(k_pass_simt<T, KM, false, true>) : go(k_pass_simt<T, KM, false, false>);
 }
 }  // namespace
 
+// column groups of the gradient accumulators: 16 threads x U columns per group
+inline int simt_km(bool is_double, int Kp) {
+  const int per = 16 * (is_double ? 2 : 4);
+  return (Kp + per - 1) / per;
+}
+
 int simt_blocks_per_sm(bool is_double, bool rows_case, int Kp) {
-  const int kj = (Kp + 15) / 16;
+  const int km = simt_km(is_double, Kp);
   if (is_double) {
-    if (kj <= 1) return blocks_per_sm_kj<double, 1>(Kp, rows_case);
-    if (kj <= 4) return blocks_per_sm_kj<double, 4>(Kp, rows_case);
-    return blocks_per_sm_kj<double, 7>(Kp, rows_case);
+    if (km <= 1) return blocks_per_sm_kj<double, 1>(Kp, rows_case);
+    if (km <= 2) return blocks_per_sm_kj<double, 2>(Kp, rows_case);
+    return blocks_per_sm_kj<double, 4>(Kp, rows_case);
   }
-  if (kj <= 1) return blocks_per_sm_kj<float, 1>(Kp, rows_case);
-  if (kj <= 4) return blocks_per_sm_kj<float, 4>(Kp, rows_case);
-  if (kj <= 7) return blocks_per_sm_kj<float, 7>(Kp, rows_case);
-  return blocks_per_sm_kj<float, 16>(Kp, rows_case);
+  if (km <= 1) return blocks_per_sm_kj<float, 1>(Kp, rows_case);
+  if (km <= 2) return blocks_per_sm_kj<float, 2>(Kp, rows_case);
+  return blocks_per_sm_kj<float, 4>(Kp, rows_case);
 }
 
 cudaError_t launch_pass_simt(const PassArgs& a_in, bool is_double, bool rows_case, bool pass2,
@@ -370,17 +426,16 @@ cudaError_t launch_pass_simt(const PassArgs& a_in, bool is_double, bool rows_cas
   dim3 grid((unsigned)((a.P_stat + BM - 1) / BM), (unsigned)splits);
   if (ctas_out) *ctas_out = (int)(grid.x * grid.y);
   if (splits_out) *splits_out = splits;
-  const int kj = (a.Kp + 15) / 16;
+  const int km = simt_km(is_double, a.Kp);
   if (is_double) {
-    if (kj <= 1) return launch_kj<double, 1>(a, rows_case, pass2, grid, st);
-    if (kj <= 4) return launch_kj<double, 4>(a, rows_case, pass2, grid, st);
-    if (kj <= 7) return launch_kj<double, 7>(a, rows_case, pass2, grid, st);
+    if (km <= 1) return launch_kj<double, 1>(a, rows_case, pass2, grid, st);
+    if (km <= 2) return launch_kj<double, 2>(a, rows_case, pass2, grid, st);
+    if (km <= 4) return launch_kj<double, 4>(a, rows_case, pass2, grid, st);
     return cudaErrorInvalidValue;
   }
-  if (kj <= 1) return launch_kj<float, 1>(a, rows_case, pass2, grid, st);
-  if (kj <= 4) return launch_kj<float, 4>(a, rows_case, pass2, grid, st);
-  if (kj <= 7) return launch_kj<float, 7>(a, rows_case, pass2, grid, st);
-  if (kj <= 16) return launch_kj<float, 16>(a, rows_case, pass2, grid, st);
+  if (km <= 1) return launch_kj<float, 1>(a, rows_case, pass2, grid, st);
+  if (km <= 2) return launch_kj<float, 2>(a, rows_case, pass2, grid, st);
+  if (km <= 4) return launch_kj<float, 4>(a, rows_case, pass2, grid, st);
   return cudaErrorInvalidValue;
 }
 
