@@ -95,6 +95,7 @@ struct Extra {
   DevBuf probe_a, probe_b, probe_x;   // adaptive-width probe: inner / outer index, data
   DevBuf dotpart, solve_ctr;          // per-row parts of <d, h>, completion counter
   DevBuf bc_ctr;                      // per-row completion counters of the back-contraction
+  DevBuf stop_part, stop_ctr;         // stopping quantity: per-block sums, completion counter
   DevBuf probe_cand;                  // selection candidates of the adaptive width
   SlotSrc slots;                      // partial slots of the last tensor-core pass 1
   double* obj_slot = nullptr;         // report slot for the objective of the next pass 1
@@ -1433,7 +1434,7 @@ void trd_destroy(trd_t* h) {
   for (DevBuf* b : bufs) free_buf(*b);
   Extra* x = X_(h);
   DevBuf* xb[] = {&x->Ework, &x->meta,    &x->stat_sum2, &x->Gloc,    &x->recA, &x->recC,
-                  &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr, &x->bc_ctr, &x->probe_lin, &x->Qb[0], &x->Qb[1], &x->probe_cand, &x->rows_dev,
+                  &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr, &x->bc_ctr, &x->stop_part, &x->stop_ctr, &x->probe_lin, &x->Qb[0], &x->Qb[1], &x->probe_cand, &x->rows_dev,
                   &x->bShi,  &x->bSlo,    &x->bSh,       &x->bThi,    &x->bTlo,    &x->bTT,
                   &x->Mst[0], &x->Mst[1]};
   for (DevBuf* b : xb) free_buf(*b);
@@ -1751,8 +1752,15 @@ trd_status step_device(trd_handle* h, const trd_params* p, int64_t* slots_out) {
   {
     PScope ps(h, P_STOP);
     TRY(compute_D(h, (double*)h->D.p));
+    Extra* xs = X_(h);
+    if (!xs->stop_ctr.p) {
+      TRY(ensure(h, xs->stop_ctr, 256));
+      CK(cudaMemsetAsync(xs->stop_ctr.p, 0, 256, h->stream), "counter");
+    }
+    TRY(ensure(h, xs->stop_part, sizeof(double) * 2 * kStopBlocks));
     CK(launch_stop_error((const double*)h->D.p, (double*)h->Dprev.p, h->I[N - 1] * h->I[N - 1],
-                         h->report_dev + R_E, h->stream), "stopping quantity");
+                         (double*)xs->stop_part.p, (unsigned int*)xs->stop_ctr.p, h->report_dev + R_E, h->stream),
+       "stopping quantity");
   }
   CK(cudaMemcpyAsync(h->report_dev + R_SIGMA, h->scal + S_SIGMA, sizeof(double), cudaMemcpyDeviceToDevice,
                      h->stream), "sigma");

@@ -268,29 +268,27 @@ __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
                : "memory");
 }
 
+// One row per warp, LDL_SW warps per block sharing one staged L.  One warp per block (so per
+// SM) measured fastest: the substitutions are bound by the SM's FP64 issue rate, and rows
+// spread over SMs get the most of it.
+constexpr int LDL_SW = 1;
 template <int C>
-__global__ void __launch_bounds__(32) k_ldl_solve(const double* __restrict__ Lcm, const double* __restrict__ Dinv,
+__global__ void __launch_bounds__(32 * LDL_SW) k_ldl_solve(const double* __restrict__ Lcm, const double* __restrict__ Dinv,
                                                   const double* __restrict__ d, double* __restrict__ h, int K,
                                                   int64_t rows, double* __restrict__ dot_part,
                                                   unsigned int* __restrict__ ctr, double* __restrict__ num) {
   constexpr int KP = 32 * C, LD = KP + 1;
   extern __shared__ double sL[];          // [K][LD]: sL[j * LD + i] = L[i][j]
   double* sD = sL + (size_t)K * LD;       // [KP]
-  const int lane = threadIdx.x & 31;
-  for (int j = 0; j < K; ++j)
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const int i = c * 32 + lane;
-      if (i < K) cp_async8(sL + j * LD + i, Lcm + (int64_t)j * K + i);
-    }
-  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
-#pragma unroll
-  for (int c = 0; c < C; ++c) {
-    const int i = c * 32 + lane;
-    sD[i] = i < K ? Dinv[i] : 0.0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < K * KP; e += blockDim.x) {
+    const int j = e / KP, i = e - j * KP;
+    if (i < K) cp_async8(sL + j * LD + i, Lcm + (int64_t)j * K + i);
   }
-  __syncwarp();
-  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+  for (int i = threadIdx.x; i < KP; i += blockDim.x) sD[i] = i < K ? Dinv[i] : 0.0;
+  __syncthreads();
+  for (int64_t row = (int64_t)blockIdx.x * LDL_SW + w; row < rows; row += (int64_t)gridDim.x * LDL_SW) {
     const double* dr = d + row * K;
     double s[C];
 #pragma unroll
@@ -346,10 +344,10 @@ __global__ void __launch_bounds__(32) k_ldl_solve(const double* __restrict__ Lcm
   // completion counter for the next call
   __shared__ int s_last;
   __threadfence();
-  __syncwarp();
-  if (lane == 0) s_last = atomicAdd(ctr, 1u) == gridDim.x - 1;
-  __syncwarp();
-  if (!s_last) return;
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last || w != 0) return;
   __threadfence();
   double t = 0.0;
   for (int64_t r = lane; r < rows; r += 32) t += __ldcg(dot_part + r);
@@ -379,8 +377,8 @@ cudaError_t launch_ldl_solve(const double* Lcm, const double* Dinv, const double
   if (K < 1 || K > kLdlKmax || rows < 1) return rows == 0 ? cudaSuccess : cudaErrorInvalidValue;
   const int C = (K + 31) / 32;
   const size_t smem = ((size_t)K * (32 * C + 1) + 32 * C) * sizeof(double);
-  // one warp (block) per row of d (rows beyond 65535 share blocks)
-  const unsigned blocks = (unsigned)imin(rows, 65535);
+  // one warp per row of d, LDL_SW rows per block (rows beyond the grid share blocks)
+  const unsigned blocks = (unsigned)imin((rows + LDL_SW - 1) / LDL_SW, 65535);
   void (*kern)(const double*, const double*, const double*, double*, int, int64_t, double*, unsigned int*,
                double*) =
       C == 1 ? k_ldl_solve<1> : C == 2 ? k_ldl_solve<2> : C == 3 ? k_ldl_solve<3> : k_ldl_solve<4>;
@@ -388,7 +386,7 @@ cudaError_t launch_ldl_solve(const double* Lcm, const double* Dinv, const double
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<blocks, 32, smem, st>>>(Lcm, Dinv, d, h, K, rows, dot_part, ctr, num);
+  kern<<<blocks, 32 * LDL_SW, smem, st>>>(Lcm, Dinv, d, h, K, rows, dot_part, ctr, num);
   note_launch();
   return cudaGetLastError();
 }
@@ -641,28 +639,22 @@ cudaError_t launch_step_update(double* Z, float* Zf, const double* h, int64_t n,
   return cudaGetLastError();
 }
 
-// e = ||D - Dprev||_F / ||D||_F, then Dprev <- D  (Algorithm 1 stopping quantity)
-__global__ void __launch_bounds__(1024) k_stop_error(const double* __restrict__ D, double* __restrict__ Dprev,
-                                                     int64_t n, double* __restrict__ e_out) {
-  // one block; two independent partial sums per thread and quantity, a fixed-order
-  // shuffle/shared reduction, then D is kept for the next iteration
-  __shared__ double s1[32], s2[32];
-  double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
-  const int64_t step = blockDim.x;
-  int64_t i = threadIdx.x;
-  for (; i + step < n; i += 2 * step) {
-    const double x0 = D[i], y0 = Dprev[i], x1 = D[i + step], y1 = Dprev[i + step];
-    a0 = fma(x0 - y0, x0 - y0, a0);
-    b0 = fma(x0, x0, b0);
-    a1 = fma(x1 - y1, x1 - y1, a1);
-    b1 = fma(x1, x1, b1);
+// e = ||D - Dprev||_F / ||D||_F, then Dprev <- D  (Algorithm 1 stopping quantity).  Spread
+// over many blocks (the FP64 work of one SM would take several microseconds): each block
+// writes its partial sums to part[2 b], part[2 b + 1] and keeps D for the next iteration; the
+// last block to finish adds the partials in block order (counter *ctr is reset by it).
+__global__ void __launch_bounds__(256) k_stop_error(const double* __restrict__ D, double* __restrict__ Dprev,
+                                                    int64_t n, double* __restrict__ part,
+                                                    unsigned int* __restrict__ ctr, double* __restrict__ e_out) {
+  __shared__ double s1[8], s2[8];
+  __shared__ int s_last;
+  double a = 0.0, b = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = D[i], dd = x - Dprev[i];
+    a = fma(dd, dd, a);
+    b = fma(x, x, b);
+    Dprev[i] = x;
   }
-  if (i < n) {
-    const double x0 = D[i], y0 = Dprev[i];
-    a0 = fma(x0 - y0, x0 - y0, a0);
-    b0 = fma(x0, x0, b0);
-  }
-  double a = a0 + a1, b = b0 + b1;
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, o);
     b += __shfl_down_sync(0xffffffffu, b, o);
@@ -679,15 +671,27 @@ __global__ void __launch_bounds__(1024) k_stop_error(const double* __restrict__ 
       sa += s1[q];
       sb += s2[q];
     }
-    *e_out = sb > 0 ? sqrt(sa / sb) : 0.0;
+    part[2 * blockIdx.x] = sa;
+    part[2 * blockIdx.x + 1] = sb;
+    __threadfence();
+    s_last = atomicAdd(ctr, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) Dprev[q] = D[q];
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double sa = 0.0, sb = 0.0;
+  for (unsigned q = 0; q < gridDim.x; ++q) {
+    sa += __ldcg(part + 2 * q);
+    sb += __ldcg(part + 2 * q + 1);
+  }
+  *e_out = sb > 0 ? sqrt(sa / sb) : 0.0;
+  *ctr = 0u;
 }
 
-cudaError_t launch_stop_error(const double* D, double* Dprev, int64_t n, double* e_out,
-                              cudaStream_t st) {
-  k_stop_error<<<1, 1024, 0, st>>>(D, Dprev, n, e_out);
+cudaError_t launch_stop_error(const double* D, double* Dprev, int64_t n, double* part, unsigned int* ctr,
+                              double* e_out, cudaStream_t st) {
+  const unsigned blocks = (unsigned)imax(1, imin((n + 255) / 256, kStopBlocks));
+  k_stop_error<<<blocks, 256, 0, st>>>(D, Dprev, n, part, ctr, e_out);
   note_launch();
   return cudaGetLastError();
 }

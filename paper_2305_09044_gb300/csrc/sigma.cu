@@ -60,7 +60,7 @@ constexpr uint64_t kExcluded = ~0ull;
 //   u[16..23] completion counter of each kernel of the chain
 //   u[24]     number of candidates appended by the compaction
 //   word 64:  uint32 histograms [8 digits][4 targets][256]
-//   word 64 + 4096: per-block partial sums [kSelBlocks][4] (count, sum e, sum x^2, sum (e-mean)^2)
+//   word 64 + 4096: per-block partial sums [kSelBlocks][4] (count, sum e, sum x^2, sum e^2)
 // The chain is: clear (memset) -> first kernel (residual keys, sums, digit-0 histogram) ->
 // digit 1 -> digit 2 (the last block of each kernel, found by a completion counter, turns the
 // complete histogram into the next digit of each target) -> compaction of the keys still
@@ -158,13 +158,15 @@ __device__ double sel_sum_parts(const double* work, int f, int nb) {
 // shared-memory atomics).  Every lane of the warp calls it (valid = false for lanes without
 // an included residual).
 __device__ __forceinline__ void sel_consume(bool valid, double e, double x2, uint64_t* keys, int64_t m,
-                                            bool write, unsigned int* h0, double& c, double& se, double& sx) {
+                                            bool write, unsigned int* h0, double& c, double& se, double& sx,
+                                            double& s2) {
   const uint64_t key = valid ? dkey(e) : kExcluded;
   if (write) keys[m] = key;
   if (valid) {
     c += 1.0;
     se += e;
     sx += x2;
+    s2 = fma(e, e, s2);
   }
   const unsigned dig = (unsigned)(key >> 56);
   const unsigned act = __ballot_sync(0xffffffffu, valid);
@@ -178,13 +180,15 @@ __device__ __forceinline__ void sel_consume(bool valid, double e, double x2, uin
 // kept in integer / FP32 registers (a lane takes a handful of probes) and widened once at the
 // end, so the per-probe work issues no FP64 instruction.
 __device__ __forceinline__ void sel_consume_f(bool valid, float e, float x2, uint64_t* keys, int64_t m,
-                                              bool write, unsigned int* h0, uint32_t& c, float& se, float& sx) {
+                                              bool write, unsigned int* h0, uint32_t& c, float& se, float& sx,
+                                              float& s2) {
   const uint64_t key = valid ? fkey(e) : kExcluded;
   if (write) keys[m] = key;
   if (valid) {
     c += 1u;
     se += e;
     sx += x2;
+    s2 = fmaf(e, e, s2);
   }
   const unsigned dig = (unsigned)(key >> 56);
   const unsigned act = __ballot_sync(0xffffffffu, valid);
@@ -196,26 +200,29 @@ __device__ __forceinline__ void sel_consume_f(bool valid, float e, float x2, uin
 
 // End of the first kernel: block partials and histogram out; the last block sets n, mean,
 // sum x^2, the target ranks, and picks digit 0.
-__device__ void sel_first_finish(double* work, unsigned int* h0, double c, double se, double sx) {
-  __shared__ double red[3][kSelThreads / 32];
+__device__ void sel_first_finish(double* work, unsigned int* h0, double c, double se, double sx, double s2) {
+  __shared__ double red[4][kSelThreads / 32];
   for (int o = 16; o > 0; o >>= 1) {
     c += __shfl_down_sync(0xffffffffu, c, o);
     se += __shfl_down_sync(0xffffffffu, se, o);
     sx += __shfl_down_sync(0xffffffffu, sx, o);
+    s2 += __shfl_down_sync(0xffffffffu, s2, o);
   }
   if ((threadIdx.x & 31) == 0) {
     red[0][threadIdx.x >> 5] = c;
     red[1][threadIdx.x >> 5] = se;
     red[2][threadIdx.x >> 5] = sx;
+    red[3][threadIdx.x >> 5] = s2;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0, b = 0, d = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; d += red[2][w]; }
+    double a = 0, b = 0, d = 0, q = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; d += red[2][w]; q += red[3][w]; }
     double* part = work + kPartsWord + blockIdx.x * 4;
     part[0] = a;
     part[1] = b;
     part[2] = d;
+    part[3] = q;
   }
   unsigned int* g0 = sel_hist(work, 0, 0);
   for (int i = threadIdx.x; i < 256; i += blockDim.x)
@@ -224,10 +231,14 @@ __device__ void sel_first_finish(double* work, unsigned int* h0, double c, doubl
   const double n = sel_sum_parts(work, 0, gridDim.x);
   const double sum = sel_sum_parts(work, 1, gridDim.x);
   const double sx2 = sel_sum_parts(work, 2, gridDim.x);
+  const double se2 = sel_sum_parts(work, 3, gridDim.x);
   if (threadIdx.x == 0) {
+    const double mean = n > 0 ? sum / n : 0.0;
     work[0] = n;
-    work[1] = n > 0 ? sum / n : 0.0;
+    work[1] = mean;
     work[2] = sx2;
+    // population variance in one pass (the residual mean is small against their spread)
+    work[3] = n > 0 ? fmax(0.0, se2 / n - mean * mean) : 0.0;
     uint64_t* u = reinterpret_cast<uint64_t*>(work);
     const double ps[2] = {0.25, 0.75};
     for (int q = 0; q < 2; ++q) {
@@ -285,13 +296,11 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_digit(const uint64_t* __res
 #pragma unroll
   for (int t = 0; t < 4; ++t) pre[t] = __ldcg(u + 12 + t);
   sel_alias(pre, alias);
-  const double mean = __ldcg(work + 1);
   const int shift = 56 - 8 * digit;
   const uint64_t himask = ~0ull << (shift + 8);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t wpb = blockDim.x >> 5;
-  double s2 = 0.0;
   const int64_t chunk = 32 * kSelBatch;
   for (int64_t c0 = ((int64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * chunk; c0 < n;
        c0 += (int64_t)gridDim.x * wpb * chunk) {
@@ -305,10 +314,6 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_digit(const uint64_t* __res
     for (int q = 0; q < kSelBatch; ++q) {
       const uint64_t k = kb[q];
       const bool valid = k != kExcluded;
-      if (digit == 1 && valid) {
-        const double d = dval(k) - mean;
-        s2 = fma(d, d, s2);
-      }
       const unsigned dig = (unsigned)((k >> shift) & 0xffu);
       // the distinct prefixes of one digit are disjoint, so a key counts for at most one
       // target: one aggregated histogram update per key
@@ -323,17 +328,6 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_digit(const uint64_t* __res
       }
     }
   }
-  if (digit == 1) {
-    __shared__ double red[kSelThreads / 32];
-    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_down_sync(0xffffffffu, s2, o);
-    if (lane == 0) red[threadIdx.x >> 5] = s2;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double a = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
-      work[kPartsWord + blockIdx.x * 4 + 3] = a;
-    }
-  }
   __syncthreads();
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
@@ -343,14 +337,6 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_digit(const uint64_t* __res
       if (h[t][i]) atomicAdd(&g[i], h[t][i]);
   }
   if (!sel_last_block(work, digit)) return;
-  if (digit == 1) {
-    const double ss = sel_sum_parts(work, 3, gridDim.x);
-    if (threadIdx.x == 0) {
-      const double cnt = __ldcg(work);
-      work[3] = cnt > 0 ? ss / cnt : 0.0;
-    }
-    __syncthreads();
-  }
   sel_pick(work, digit);
 }
 
@@ -478,16 +464,16 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_floats(const float* __restr
   __shared__ unsigned int h0[256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) h0[i] = 0;
   __syncthreads();
-  double c = 0, se = 0, sx = 0;
+  double c = 0, se = 0, sx = 0, s2 = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t m0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); m0 < n; m0 += stride) {
     const int64_t m = m0 + (threadIdx.x & 31);
     const double v = m < n ? (double)r[m] : 0.0;
     const bool valid = m < n && isfinite(v);
-    sel_consume(valid, v, 0.0, keys, m, m < n, h0, c, se, sx);
+    sel_consume(valid, v, 0.0, keys, m, m < n, h0, c, se, sx, s2);
   }
   __syncthreads();
-  sel_first_finish(work, h0, c, se, sx);
+  sel_first_finish(work, h0, c, se, sx, s2);
 }
 
 // First kernel of the tensor rule: residuals at the probe entries from the merged subchains
@@ -504,7 +490,7 @@ __global__ void __launch_bounds__(kSelThreads)
   for (int i = threadIdx.x; i < 256; i += blockDim.x) h0[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  double c = 0, se = 0, sx = 0;
+  double c = 0, se = 0, sx = 0, s2 = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t m0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); m0 < n; m0 += stride) {
     const int64_t m = m0 + lane;
@@ -541,10 +527,10 @@ __global__ void __launch_bounds__(kSelThreads)
       e = (double)et;
       x2 = (double)x * (double)x;
     }
-    sel_consume(valid, e, x2, keys, m, live, h0, c, se, sx);
+    sel_consume(valid, e, x2, keys, m, live, h0, c, se, sx, s2);
   }
   __syncthreads();
-  sel_first_finish(work, h0, c, se, sx);
+  sel_first_finish(work, h0, c, se, sx, s2);
 }
 
 // Sixteen lanes per probe: a half warp reads the two merged rows of one probe with 16-byte
@@ -564,9 +550,9 @@ __global__ void __launch_bounds__(kSelThreads)
   __syncthreads();
   const int lane = threadIdx.x & 31, sub = lane & 15, half = lane & 16;
   const int nv = Kp / VW;
-  double c = 0, se = 0, sx = 0;
+  double c = 0, se = 0, sx = 0, s2 = 0;
   uint32_t cf = 0;
-  float sef = 0.f, sxf = 0.f;
+  float sef = 0.f, sxf = 0.f, s2f = 0.f;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t m0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); m0 < n; m0 += stride) {
     const int64_t m = m0 + lane;
@@ -628,7 +614,7 @@ __global__ void __launch_bounds__(kSelThreads)
         valid = isfinite(e);
         x2 = xf * xf;
       }
-      sel_consume_f(valid, e, x2, keys, m, live, h0, cf, sef, sxf);
+      sel_consume_f(valid, e, x2, keys, m, live, h0, cf, sef, sxf, s2f);
     } else {
       double e = 0.0, x2 = 0.0;
       bool valid = false;
@@ -639,16 +625,17 @@ __global__ void __launch_bounds__(kSelThreads)
         e = (double)et;
         x2 = (double)x * (double)x;
       }
-      sel_consume(valid, e, x2, keys, m, live, h0, c, se, sx);
+      sel_consume(valid, e, x2, keys, m, live, h0, c, se, sx, s2);
     }
   }
   if constexpr (VW == 4) {
     c = (double)cf;
     se = (double)sef;
     sx = (double)sxf;
+    s2 = (double)s2f;
   }
   __syncthreads();
-  sel_first_finish(work, h0, c, se, sx);
+  sel_first_finish(work, h0, c, se, sx, s2);
 }
 
 // Probe description for the tensor rule: probe m is the entry lin[m] (all entries in order

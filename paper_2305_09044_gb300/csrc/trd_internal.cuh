@@ -283,8 +283,9 @@ cudaError_t launch_eta(const double* num, const double* den, double fixed_eta, i
 cudaError_t launch_step_update(double* Z, float* Zf, const double* h, int64_t n, const double* num, const double* part, int ctas,
                                const double* den, double fixed_eta, int* dstatus, double* eta, double* eta_slot,
                                cudaStream_t st);
-cudaError_t launch_stop_error(const double* D, double* Dprev, int64_t n, double* e_out,
-                              cudaStream_t st);
+constexpr int kStopBlocks = 152;     // most blocks of the stopping-quantity kernel
+cudaError_t launch_stop_error(const double* D, double* Dprev, int64_t n, double* part, unsigned int* ctr,
+                              double* e_out, cudaStream_t st);
 
 // sigma.cu
 size_t sigma_work_doubles();
