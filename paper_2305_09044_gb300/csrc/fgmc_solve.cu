@@ -560,34 +560,6 @@ cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* out,
   return cudaGetLastError();
 }
 
-// eta = <d,h> / den (exact line search of Sec. 3.2) unless a fixed step is given; any
-// earlier device error (singular Gram, non-finite values) forces eta = 0 so the core is
-// left unchanged.  eta_slot (nullable) receives a copy for the iteration report.
-__global__ void k_eta(const double* num, const double* den, double fixed_eta, int* dstatus,
-                      double* eta_out, double* eta_slot) {
-  double eta;
-  if (fixed_eta > 0) {
-    eta = fixed_eta;
-  } else {
-    const double dn = *den;
-    eta = dn > 0 ? *num / dn : 0.0;
-  }
-  if (!isfinite(eta)) {
-    atomicOr(dstatus, (int)DEV_NONFINITE);
-    eta = 0.0;
-  }
-  if (*dstatus & (DEV_SINGULAR | DEV_NONFINITE)) eta = 0.0;
-  *eta_out = eta;
-  if (eta_slot) *eta_slot = eta;
-}
-
-cudaError_t launch_eta(const double* num, const double* den, double fixed_eta, int* dstatus,
-                       double* eta, double* eta_slot, cudaStream_t st) {
-  k_eta<<<1, 1, 0, st>>>(num, den, fixed_eta, dstatus, eta, eta_slot);
-  note_launch();
-  return cudaGetLastError();
-}
-
 // Step size and update in one launch: every block forms eta = <d,h> / den (den summed from the
 // line-search pass's per-CTA partials in the same fixed order as the statistics reduction,
 // field 6, or read from `den`), forced to 0 on a flagged or non-finite step; block 0 records

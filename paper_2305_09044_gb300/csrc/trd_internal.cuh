@@ -277,8 +277,6 @@ cudaError_t launch_solve_rows(const double* L, const double* d, double* h, int K
                               cudaStream_t st);
 cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* out,
                        cudaStream_t st);
-cudaError_t launch_eta(const double* num, const double* den, double fixed_eta, int* dstatus,
-                       double* eta, double* eta_slot, cudaStream_t st);
 // eta (from <d,h> and the line-search partials or a reduced den, or fixed) and Z += eta h
 cudaError_t launch_step_update(double* Z, float* Zf, const double* h, int64_t n, const double* num, const double* part, int ctas,
                                const double* den, double fixed_eta, int* dstatus, double* eta, double* eta_slot,
