@@ -252,10 +252,7 @@ def run_ours(args, rank, world, local):
     __graft_entry__.build()
     torch.cuda.set_device(local)
     precs = [args.precision] if args.precision else ["bf16", "fp32"]
-    w = synth.WORKLOADS[WORKLOAD]
-    if world > 1:   # independent replicas: a different data seed per rank
-        import dataclasses
-        w = dataclasses.replace(w, data_seed=w.data_seed + 100 * rank, init_seed=w.init_seed + 100 * rank)
+    w = replica_workload(synth.WORKLOADS[WORKLOAD], rank, world)
     t, Xt, host, dev, corr = build_problem(w, torch, precs[0])
     slots_per_step = len(w.dims) * int(np.prod(w.dims))
 
@@ -263,7 +260,7 @@ def run_ours(args, rank, world, local):
     t.init_cores(w.init_seed)
     ms, prof, launches, ck = timed_steps(t, args.steps, args.warmup, world, local, torch, kernel_launches)
     ms_step = ms / args.steps
-    value = world * slots_per_step * args.steps / (ms / 1e3)
+    value = job_throughput(world, slots_per_step, args.steps, ms)
     prec = precs[0]
 
     # e2e through the public API with host buffers.  Every step's X and mask are copied from
@@ -309,7 +306,7 @@ def run_ours(args, rank, world, local):
     e2e_steps(args.steps)
     torch.cuda.synchronize()
     e2e_s = _max_over_ranks((time.perf_counter() - t0) * 1e3, world) / 1e3
-    e2e = {"value": world * slots_per_step * args.steps / e2e_s, "unit": UNIT,
+    e2e = {"value": job_throughput(world, slots_per_step, args.steps, e2e_s * 1e3), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "ms_per_step": e2e_s * 1e3 / args.steps,
            "note": "per step: H2D of X and mask from pinned memory (double-buffered, overlapping the "
@@ -333,7 +330,7 @@ def run_ours(args, rank, world, local):
         t2.init_cores(w.init_seed)
         steps2 = max(3, args.steps // 4)
         ms2, prof2, launches2, ck2 = timed_steps(t2, steps2, 3, world, local, torch, kernel_launches)
-        cmp_ = {"value": world * slots_per_step * steps2 / (ms2 / 1e3), "unit": UNIT, "steps": steps2,
+        cmp_ = {"value": job_throughput(world, slots_per_step, steps2, ms2), "unit": UNIT, "steps": steps2,
                 "ms_per_step": ms2 / steps2, "iters_per_s": 1e3 * steps2 / ms2,
                 "roofline": roofline(other, prof2, w), "gpu_launches": launches2, "clocks": ck2}
         if rank == 0 and not args.no_converge:
@@ -472,6 +469,20 @@ def run_reference(args, rank, world):
 
 # ----------------------------------------------------------------------------- dist helpers
 _pg = None
+
+
+def replica_workload(w, rank, world):
+    """N > 1 runs independent replicas (the path does not shard): rank r solves its own
+    problem, drawn with data and initialisation seeds offset by 100 r."""
+    if world <= 1:
+        return w
+    import dataclasses
+    return dataclasses.replace(w, data_seed=w.data_seed + 100 * rank, init_seed=w.init_seed + 100 * rank)
+
+
+def job_throughput(world, slots_per_step, steps, ms_max):
+    """Whole-job sampled entries per second: every rank's slots over the slowest rank's time."""
+    return world * slots_per_step * steps / (ms_max / 1e3)
 
 
 def _init_dist(world):
