@@ -105,8 +105,10 @@ typedef struct {
 
 /* Create a handle for an order-N tensor (3 <= N <= TRD_MAX_ORDER) with mode sizes I[0..N-1]
  * (each >= 1, product < 2^40) and ring ranks R[0..N-1] (Def. 1, 1 <= r_k <= TRD_MAX_RANK).
- * `precision` is a trd_precision.  `cuda_stream` is a cudaStream_t (NULL = legacy default
- * stream) on which every call is ordered; it must outlive the handle.  Allocates the
+ * `precision` is a trd_precision.  `cuda_stream` is a cudaStream_t on which every call is
+ * ordered; it must outlive the handle.  NULL (the legacy default stream) gives the handle
+ * its own blocking stream, which keeps the legacy stream's implicit ordering with the
+ * caller's work and can be captured into a CUDA graph (the legacy stream cannot).  Allocates the
  * library's own device state (cores, FGMC factors, work buffers); no data is copied.
  * Errors: TRD_EINVAL (shape), TRD_ENOMEM, TRD_ECUDA (no usable device). */
 trd_status trd_create(trd_t** handle, int N, const int64_t* I, const int32_t* R,
@@ -128,8 +130,8 @@ const char* trd_status_string(trd_status status);
  * floats in the linear order above, 16-byte aligned.  mask may be NULL, meaning fully
  * observed.  Resets any sketch.  The library caches what it derives from the contents (the
  * mask re-laid for the data passes, the adaptive width's probe values); after changing the
- * contents behind the same pointers, call trd_set_data again, which drops those caches (and
- * ends CUDA-graph replay of trd_step).  Errors: TRD_EINVAL (NULL X, misalignment). */
+ * contents behind the same pointers, call trd_set_data again, which drops those caches, has
+ * the merged subchains formed again from the cores, and ends CUDA-graph replay of trd_step.  Errors: TRD_EINVAL (NULL X, misalignment). */
 trd_status trd_set_data(trd_t* handle, const float* X_dev, const uint32_t* mask_dev);
 
 /* Initialise all cores i.i.d. Gaussian (Algorithm 1, 'initialize Z_k'; the law is a

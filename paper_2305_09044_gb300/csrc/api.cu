@@ -99,6 +99,8 @@ struct Extra {
   DevBuf probe_cand;                  // selection candidates of the adaptive width
   SlotSrc slots;                      // partial slots of the last tensor-core pass 1
   double* obj_slot = nullptr;         // report slot for the objective of the next pass 1
+  int adv_k = -1;                     // core whose FP32 step operand S_h is ready for the
+                                      // in-place advance of its merged half (BF16 path)
   // uniform row sampling (trd_sample_rows): J multi-indices of the modes other than row_k
   bool row_view = false;
   int row_k = -1;
@@ -107,6 +109,8 @@ struct Extra {
   uint64_t rows_gen = ~0ull, rows_ver[kMaxN] = {};   // what h->Sst / h->Sstr hold
   // what the merged-half buffers hold (FP32/FP64 h->Sst / h->Sstr, BF16 operands bS* / bT*)
   HalfTag tagSst, tagSstr, tagBst, tagBstr;
+  bool graph_tag_cur[4] = {};   // which of the four tags were current at the end of the capture
+  bool own_stream = false;      // the handle created h->stream (the caller passed NULL)
   uint64_t view_gen = 0;    // 0 = the full tensor; every drawn sketch gets a new number
   uint64_t sketch_count = 0;
   bool probe_ready = false;
@@ -613,7 +617,8 @@ trd_status build_halves(trd_handle* h, int k) {
   return TRD_OK;
 }
 
-trd_status build_merged(trd_handle* h, int k, bool with_h, __nv_bfloat16* bf16_h = nullptr, int kpad = 0) {
+trd_status build_merged(trd_handle* h, int k, bool with_h, __nv_bfloat16* bf16_h = nullptr, int kpad = 0,
+                        void* fp32_h = nullptr) {
   const View& v = h->view;
   const Split& sp = h->split;
   const int c = sp.c, Kp = sp.Kp;
@@ -629,9 +634,10 @@ trd_status build_merged(trd_handle* h, int k, bool with_h, __nv_bfloat16* bf16_h
   const Chain inner = make_chain(h, v, 0, c, k, (const double*)h->h.p);
   const Chain outer = make_chain(h, v, c, h->N, k, (const double*)h->h.p);
   if (bf16_h) {
-    // tensor-core path: only the BF16 operand of the step direction is needed
-    if (sp.rows) CK(launch_chain(inner, nullptr, dbl, false, Kp, h->stream, bf16_h, nullptr, kpad), "merge A_h");
-    else CK(launch_chain(outer, nullptr, dbl, true, Kp, h->stream, bf16_h, nullptr, kpad), "merge C_h");
+    // tensor-core path: the BF16 operand of the step direction (and, when asked, its FP32 form
+    // for advancing the merged half in place after the step)
+    if (sp.rows) CK(launch_chain(inner, fp32_h, dbl, false, Kp, h->stream, bf16_h, nullptr, kpad), "merge A_h");
+    else CK(launch_chain(outer, fp32_h, dbl, true, Kp, h->stream, bf16_h, nullptr, kpad), "merge C_h");
     return TRD_OK;
   }
   TRY(ensure(h, h->Sh, e * sp.P_stat * Kp));
@@ -789,7 +795,11 @@ trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
       CK(launch_tc_prep((const float*)h->Sh.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bSh.p, nullptr, h->stream),
          "bf16 step operands");
     } else {
-      TRY(build_merged(h, k, true, (__nv_bfloat16*)x->bSh.p, tc_kpad(sp.Kp)));
+      // the step operand in FP32 too: after the step the stationary half (which holds core k)
+      // is advanced in place, S += eta S_h, instead of being merged again
+      TRY(ensure(h, h->Sh, sizeof(float) * sp.P_stat * sp.Kp));
+      TRY(build_merged(h, k, true, (__nv_bfloat16*)x->bSh.p, tc_kpad(sp.Kp), h->Sh.p));
+      x->adv_k = k;
     }
   }
   // the side stream has joined: the line-search pass takes every SM (its per-CTA partials are
@@ -1086,11 +1096,30 @@ trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int
   }
   PScope psu(h, P_UPDATE);
   const bool from_parts = eta_fixed <= 0 && den == nullptr;   // tensor-core line search
+  // BF16 path with the step operand in FP32 at hand: the stationary half (it holds core k)
+  // advances in place with the core, and its tags follow the new core version
+  Extra* xa = X_(h);
+  const Split& spa = h->split;
+  const bool advance = from_parts && xa->adv_k == k && h->prec == TRD_BF16 && !xa->row_view &&
+                       xa->tagSst.valid && xa->tagBst.valid && xa->tagSst == xa->tagBst &&
+                       xa->tagSst.half == (k < spa.c ? 0 : 1);
+  HalfAdvance adv;
+  if (advance) {
+    adv.S = (float*)h->Sst.p;
+    adv.Sh = (const float*)h->Sh.p;
+    adv.n = spa.P_stat * (int64_t)spa.Kp;
+    adv.Kp = spa.Kp;
+    adv.kpad = tc_kpad(spa.Kp);
+    adv.hi = (__nv_bfloat16*)xa->bShi.p;
+    adv.lo = (__nv_bfloat16*)xa->bSlo.p;
+  }
+  xa->adv_k = -1;
   CK(launch_step_update(h->Z[k], h->Zf[k], hh, n, h->scal + S_NUM, from_parts ? (const double*)h->stat_part.p : nullptr,
                         from_parts ? X_(h)->tcG : 0, den, eta_fixed, h->dstatus, h->scal + S_ETA, eta_slot,
-                        h->stream),
+                        h->stream, adv),
      "step size and core update");
   h->ver[k]++;
+  if (advance) xa->tagSst.ver[k] = xa->tagBst.ver[k] = h->ver[k];
   X_(h)->e_stale[k] = true;   // E_k only feeds the other cores' Grams: refreshed there
   h->grad_k = -1;
   h->pass1_k = -1;
@@ -1395,6 +1424,16 @@ trd_status trd_create(trd_t** out, int N, const int64_t* I, const int32_t* R, in
   for (int m = 0; m < N; ++m) { h->I[m] = I[m]; h->R[m] = R[m]; }
   h->prec = precision;
   h->stream = (cudaStream_t)cuda_stream;
+  if (!h->stream) {
+    // a blocking stream of the handle's own: ordered with the legacy stream like the caller
+    // expects, and capturable into a graph
+    if (cudaStreamCreate(&h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      delete hf;
+      return TRD_ECUDA;
+    }
+    X_(h)->own_stream = true;
+  }
   cudaGetDevice(&h->device);
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (h->num_sms < 1) h->num_sms = 1;
@@ -1450,6 +1489,7 @@ void trd_destroy(trd_t* h) {
   if (h->report_dev) cudaFree(h->report_dev);
   if (h->host_pinned) cudaFreeHost(h->host_pinned);
   if (h->idx_pinned) cudaFreeHost(h->idx_pinned);
+  if (x->own_stream && h->stream) cudaStreamDestroy(h->stream);
   cudaGetLastError();
   delete reinterpret_cast<trd_handle_full*>(h);
 }
@@ -1462,9 +1502,12 @@ trd_status trd_set_data(trd_t* h, const float* X, const uint32_t* mask) {
     return set_err(h, TRD_EINVAL, "X and mask must be 16-byte aligned");
   h->X = X;
   h->M = mask;
-  // the contents may have changed behind the same pointers: drop everything derived from them
+  // the contents may have changed behind the same pointers: drop everything derived from them;
+  // the merged halves are merged again from the cores as well (a fresh start for the BF16
+  // path's in-place advances)
   X_(h)->probe_ready = false;
   X_(h)->mst_X[0] = X_(h)->mst_X[1] = nullptr;
+  X_(h)->tagSst.valid = X_(h)->tagSstr.valid = X_(h)->tagBst.valid = X_(h)->tagBstr.valid = false;
   h->numel = 1;
   for (int m = 0; m < h->N; ++m) h->numel *= h->I[m];
   use_full_view(h);
@@ -1768,10 +1811,32 @@ trd_status step_device(trd_handle* h, const trd_params* p, int64_t* slots_out) {
   return TRD_OK;
 }
 
+// Whether a merged-half tag describes the current cores (it was merged or advanced in
+// place for their versions).
+bool tag_current(const trd_handle* h, const HalfTag& t) {
+  if (!t.valid) return false;
+  const int m0 = t.half == 0 ? 0 : t.c, m1 = t.half == 0 ? t.c : h->N;
+  for (int m = m0; m < m1; ++m)
+    if (t.ver[m] != h->ver[m]) return false;
+  return true;
+}
+
 // Host-side state after a step whose device work ran without the host logic (graph replay):
-// every core changed once; cached merges, Gram and pass results are treated as stale.
+// every core changed once; Gram and pass results are treated as stale. A merged half that
+// was current at the end of the captured step is current again after the replay (the replay
+// advanced it in place exactly as the captured step did), so its tag follows the versions.
 void after_replay(trd_handle* h) {
+  Extra* x = X_(h);
+  HalfTag* tags[4] = {&x->tagSst, &x->tagSstr, &x->tagBst, &x->tagBstr};
+  bool cur[4];
+  for (int i = 0; i < 4; ++i) cur[i] = x->graph_tag_cur[i] && tag_current(h, *tags[i]);
   for (int k = 0; k < h->N; ++k) h->ver[k]++;
+  for (int i = 0; i < 4; ++i) {
+    if (!cur[i]) continue;
+    HalfTag& t = *tags[i];
+    const int m0 = t.half == 0 ? 0 : t.c, m1 = t.half == 0 ? t.c : h->N;
+    for (int m = m0; m < m1; ++m) t.ver[m] = h->ver[m];
+  }
   h->pass1_k = -1;
   h->grad_k = -1;
   h->gram_k = -1;
@@ -1786,6 +1851,10 @@ trd_status capture_step(trd_handle* h, const trd_params* p, int64_t* slots) {
   const size_t pend0 = x->pending.size();
   bool ok = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
   trd_status st = ok ? step_device(h, p, slots) : TRD_ECUDA;
+  {
+    const HalfTag* tags[4] = {&x->tagSst, &x->tagSstr, &x->tagBst, &x->tagBstr};
+    for (int i = 0; i < 4; ++i) x->graph_tag_cur[i] = tag_current(h, *tags[i]);
+  }
   cudaGraph_t g = nullptr;
   if (ok) ok = cudaStreamEndCapture(h->stream, &g) == cudaSuccess && st == TRD_OK && g;
   if (ok) ok = cudaGraphInstantiate(&x->graph_exec, g, 0) == cudaSuccess;

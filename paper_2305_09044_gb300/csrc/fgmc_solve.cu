@@ -564,8 +564,11 @@ cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* out,
 // line-search pass's per-CTA partials in the same fixed order as the statistics reduction,
 // field 6, or read from `den`), forced to 0 on a flagged or non-finite step; block 0 records
 // it; then Z_k <- Z_k + eta fold(h) (update-sign reading of Eq. updatessd / Eq. ftrbcn), and
-// the FP32 copy of the core follows.
-__global__ void k_step_update(double* __restrict__ Z, float* __restrict__ Zf, const double* __restrict__ h, int64_t n,
+// the FP32 copy of the core follows.  With adv.S, the merged half that holds core k moves
+// with it: the half is linear in core k, so S += eta S_h equals merging it again (up to FP32
+// rounding), and its BF16 hi/lo operand rows are written again.
+__global__ void k_step_update(double* __restrict__ Z, float* __restrict__ Zf, HalfAdvance adv,
+                              const double* __restrict__ h, int64_t n,
                               const double* __restrict__ num, const double* __restrict__ part, int ctas,
                               const double* __restrict__ den_in, double fixed_eta, int* dstatus,
                               double* __restrict__ eta_out, double* __restrict__ eta_slot) {
@@ -600,13 +603,26 @@ __global__ void k_step_update(double* __restrict__ Z, float* __restrict__ Zf, co
     Z[i] = z;
     Zf[i] = (float)z;
   }
+  if (!adv.S) return;
+  const float ef = (float)e;
+  const int step = gridDim.x * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  RowCol rc(i0, step, adv.Kp);
+  for (int64_t i = i0; i < adv.n; i += step, rc.next()) {
+    const float v = fmaf(ef, adv.Sh[i], adv.S[i]);
+    adv.S[i] = v;
+    const __nv_bfloat16 vh = bf16_rn(v);
+    const int64_t q = (int64_t)rc.r * adv.kpad + rc.c;
+    adv.hi[q] = vh;
+    adv.lo[q] = bf16_rn(v - __bfloat162float(vh));
+  }
 }
 
 cudaError_t launch_step_update(double* Z, float* Zf, const double* h, int64_t n, const double* num, const double* part,
                                int ctas, const double* den, double fixed_eta, int* dstatus, double* eta,
-                               double* eta_slot, cudaStream_t st) {
-  k_step_update<<<(unsigned)imin((n + 255) / 256, 1024), 256, 0, st>>>(Z, Zf, h, n, num, part, ctas, den,
-                                                                      fixed_eta, dstatus, eta, eta_slot);
+                               double* eta_slot, cudaStream_t st, const HalfAdvance& adv) {
+  const int64_t work = adv.S ? imax(n, adv.n) : n;
+  k_step_update<<<(unsigned)imin((work + 255) / 256, 1024), 256, 0, st>>>(Z, Zf, adv, h, n, num, part, ctas, den,
+                                                                         fixed_eta, dstatus, eta, eta_slot);
   note_launch();
   return cudaGetLastError();
 }

@@ -278,9 +278,20 @@ cudaError_t launch_solve_rows(const double* L, const double* d, double* h, int K
 cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* out,
                        cudaStream_t st);
 // eta (from <d,h> and the line-search partials or a reduced den, or fixed) and Z += eta h
+// In-place advance of the merged half that holds the updated core (BF16 path): S += eta S_h
+// on [n / Kp][Kp] FP32 rows, with the BF16 hi/lo operand rows [kpad] written again.
+struct HalfAdvance {
+  float* S = nullptr;
+  const float* Sh = nullptr;
+  int64_t n = 0;
+  int Kp = 0, kpad = 0;
+  __nv_bfloat16* hi = nullptr;
+  __nv_bfloat16* lo = nullptr;
+};
 cudaError_t launch_step_update(double* Z, float* Zf, const double* h, int64_t n, const double* num, const double* part, int ctas,
                                const double* den, double fixed_eta, int* dstatus, double* eta, double* eta_slot,
-                               cudaStream_t st);
+                               cudaStream_t st,
+                               const HalfAdvance& adv = HalfAdvance{});
 constexpr int kStopBlocks = 152;     // most blocks of the stopping-quantity kernel
 cudaError_t launch_stop_error(const double* D, double* Dprev, int64_t n, double* part, unsigned int* ctr,
                               double* e_out, cudaStream_t st);
