@@ -620,9 +620,13 @@ __global__ void k_step_update(double* __restrict__ Z, float* __restrict__ Zf, Ha
 cudaError_t launch_step_update(double* Z, float* Zf, const double* h, int64_t n, const double* num, const double* part,
                                int ctas, const double* den, double fixed_eta, int* dstatus, double* eta,
                                double* eta_slot, cudaStream_t st, const HalfAdvance& adv) {
+  // every block forms eta itself (FP64, a few dozen operations in one warp): keep the grid
+  // to two blocks per SM so that this stays small next to the element work
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t work = adv.S ? imax(n, adv.n) : n;
-  k_step_update<<<(unsigned)imin((work + 255) / 256, 1024), 256, 0, st>>>(Z, Zf, adv, h, n, num, part, ctas, den,
-                                                                         fixed_eta, dstatus, eta, eta_slot);
+  k_step_update<<<(unsigned)imax(1, imin((work + 255) / 256, 2 * (int64_t)sms)), 256, 0, st>>>(
+      Z, Zf, adv, h, n, num, part, ctas, den, fixed_eta, dstatus, eta, eta_slot);
   note_launch();
   return cudaGetLastError();
 }
