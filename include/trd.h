@@ -206,7 +206,8 @@ trd_status trd_fgmc_gram(trd_t* handle, int k, double* G_host);
 /* Step 'update Z_k' (Eq. hI, Eq. ftrbcn and the exact line search): h = d (G + lambda I)^-1
  * in FP64 (LDL^T factorisation and substitutions for K_k <= 128, Cholesky above); eta = <d,h> / ||sqrt(W) o P o (h B^T)||^2 on the sketch when eta <= 0
  * (second data pass, W recomputed from the same residuals), else the given eta;
- * Z_k <- Z_k + eta fold(h) (update-sign reading); refreshes core k's FGMC factor.
+ * Z_k <- Z_k + eta fold(h) (update-sign reading); core k's FGMC factor is refreshed
+ * before the next Gram that uses it.
  * lambda >= 0 absolute, < 0 means |lambda| tr(G)/K.  `gram` is a trd_gram_kind.
  * eta_out (host, nullable) receives the step used.  Needs trd_core_gradient for k; runs
  * trd_fgmc_gram itself when needed.  Errors: TRD_ESINGULAR, TRD_ENONFINITE. */
