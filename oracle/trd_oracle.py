@@ -497,6 +497,14 @@ def relative_error(cores, X_true) -> float:
     return float(np.linalg.norm(reconstruct(cores) - X_true) / np.linalg.norm(X_true))
 
 
+def psnr(X_hat, X_ref, peak: float = 1.0) -> float:
+    """Peak signal-to-noise ratio between the recovered and the original data, the quality
+    measure of Sec. 5: 10 log10(peak^2 / MSE) with MSE the mean squared difference over all
+    entries (peak = 1 for data rescaled to [0, 1]; +inf for identical tensors)."""
+    mse = float(np.mean((np.asarray(X_hat, dtype=np.float64) - np.asarray(X_ref, dtype=np.float64)) ** 2))
+    return math.inf if mse == 0.0 else 10.0 * math.log10(peak * peak / mse)
+
+
 # ----------------------------------------------------------------------------------------
 # Adaptive kernel width (Sec. 5 cites a rule it does not state).  PARITY UNPINNED.
 # ----------------------------------------------------------------------------------------

@@ -17,6 +17,10 @@ the orders 3-5, TR ranks 3-20, 20-80 % missing and 10-20 % outliers of its exper
   cfg64   64^5, ranks 10, 70 % missing, 10 % outliers; sketch 24 per non-updated mode
   video   1024 x 1024 x 256, ranks 16, smooth modes 1-2, 80 % missing, 15 % salt-and-pepper
   grad128 128^4, ranks 20, 10 % outliers, 2^24 sampled observed entries
+  image   3 x 1352 x 2000 (a colour image, channel mode first so that the ring's cut keeps
+          r_1 r_c = 60), ranks (3, 20, 20), 70 % missing (completion), noise from the
+          two-component mixture 0.8 N(0, 1e-3) + 0.2 N(0, 0.5) on the [0, 1] scale (here
+          scaled by the clean tensor's range), PSNR against the clean tensor
 """
 from __future__ import annotations
 
@@ -34,7 +38,9 @@ class Workload:
     ranks: Tuple[int, ...]
     missing: float                  # fraction of entries unobserved
     outlier_frac: float             # fraction of observed entries replaced
-    outlier_kind: str = "uniform"   # 'uniform' U[-10 std, 10 std] or 'saltpepper'
+    outlier_kind: str = "uniform"   # 'uniform' U[-10 std, 10 std], 'saltpepper' or 'gmm'
+                                    # (every entry noisy; outlier_frac = weight of the wide
+                                    # component)
     noise_var: float = 0.0          # additive Gaussian noise variance
     sketch: Optional[int] = None    # RStS size per non-updated mode (None: full tensor)
     smooth_modes: Tuple[int, ...] = ()
@@ -57,7 +63,12 @@ WORKLOADS = {
                       smooth_width=8.0, data_seed=1004, init_seed=2004, sample_seed=3004),
     "grad128": Workload("grad128", (128,) * 4, (20,) * 4, 0.0, 0.1,
                         data_seed=1005, init_seed=2005, sample_seed=3005, n_sampled=1 << 24),
+    "image": Workload("image", (3, 1352, 2000), (3, 20, 20), 0.7, 0.2, outlier_kind="gmm",
+                      data_seed=1006, init_seed=2006, sample_seed=3006),
 }
+
+# variances of the two mixture components of the 'gmm' noise, on data rescaled to [0, 1]
+GMM_VARS = (1e-3, 0.5)
 
 
 def gaussian_cores(dims: Sequence[int], ranks: Sequence[int], seed: int,
@@ -123,6 +134,9 @@ def draw_corruption(w: Workload, dims: Optional[Sequence[int]] = None) -> Corrup
     if w.outlier_kind == "saltpepper":
         # salt-and-pepper hits entries whether observed or not; only observed ones matter
         u = np.where(rng.random(n) < 0.5, -1.0, 1.0).reshape(dims, order="F")
+    elif w.outlier_kind == "gmm":
+        # every entry gets mixture noise: outl picks the wide component, u is N(0, 1)
+        u = rng.standard_normal(n).reshape(dims, order="F")
     else:
         outl &= mask
         u = rng.uniform(-1.0, 1.0, n).reshape(dims, order="F")
@@ -143,6 +157,11 @@ def assemble(x_true, c: Corruption, kind: str = "uniform", scale: float = 10.0):
     if kind == "saltpepper":
         hi, lo = float(np.max(x_true)), float(np.min(x_true))
         x = np.where(c.outlier, np.where(c.outlier_u > 0, hi, lo), x)
+    elif kind == "gmm":
+        # mixture noise on the [0, 1] scale: standard deviations times the clean range
+        rng_ = float(np.max(x_true)) - float(np.min(x_true))
+        sd = np.where(c.outlier, math.sqrt(GMM_VARS[1]), math.sqrt(GMM_VARS[0]))
+        x = x + rng_ * sd * c.outlier_u
     else:
         std = float(np.std(x_true))
         x = np.where(c.outlier, scale * std * c.outlier_u, x)

@@ -539,3 +539,21 @@ def test_sampled_rows_brute_force():
             for a in range(rk):
                 for b in range(rk1):
                     assert abs(B[j, a + b * rk] - S[b, a]) <= 1e-13
+
+
+def test_psnr_closed_forms():
+    """Sec. 5's quality measure against values that follow from its definition alone: a
+    uniform error delta on data of peak 1 gives 20 log10(1 / delta) dB (20 dB for 0.1,
+    60 dB for 1e-3); identical tensors give +inf; scaling data, error and peak together
+    leaves it unchanged; errors on a fraction f of the entries add 10 log10(1 / f) dB."""
+    rng = np.random.default_rng(3)
+    X = rng.random((4, 5, 6))
+    assert O.psnr(X + 0.1, X) == pytest.approx(20.0, abs=1e-10)
+    assert O.psnr(X - 1e-3, X) == pytest.approx(60.0, abs=1e-9)
+    assert O.psnr(X, X) == math.inf
+    E = rng.standard_normal(X.shape) * 0.05
+    assert O.psnr(7.0 * (X + E), 7.0 * X, peak=7.0) == pytest.approx(O.psnr(X + E, X), abs=1e-9)
+    Y = X.copy()
+    flat = Y.reshape(-1)
+    flat[: flat.size // 4] += 0.1                 # a quarter of the entries off by 0.1
+    assert O.psnr(Y, X) == pytest.approx(20.0 + 10.0 * math.log10(4.0), abs=1e-9)
