@@ -267,6 +267,13 @@ trd_status trd_reconstruct_from(trd_t* handle, const double* const* cores_host, 
 /* ||X_hat - X_ref||_F / ||X_ref||_F over all entries, X_ref a DEVICE tensor (floats). */
 trd_status trd_recovery_error(trd_t* handle, const float* Xref_dev, double* err_out);
 
+/* Peak signal-to-noise ratio of the current reconstruction against X_ref (Sec. 5, the quality
+ * measure of the image and video completion experiments): 10 log10(peak^2 / MSE), the mean taken
+ * over all prod(I_n) entries.  X_ref is a DEVICE tensor of floats in the layout of trd_set_data.
+ * peak > 0 is the signal range (1 for data scaled to [0, 1]).  *psnr_out = +inf when the
+ * reconstruction equals X_ref.  TRD_EINVAL on NULL or a peak that is not positive and finite. */
+trd_status trd_psnr(trd_t* handle, const float* Xref_dev, double peak, double* psnr_out);
+
 /* ---------------------------------------------------------------- tracing */
 
 /* Tracing level `on`: 0 off (default); 1 records CUDA events on the handle's stream around

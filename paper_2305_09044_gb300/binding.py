@@ -36,7 +36,7 @@ EXPORTS = [
     "trd_sigma_from_residuals", "trd_reconstruct", "trd_reconstruct_from",
     "trd_recovery_error", "trd_sampled_fwd", "trd_sampled_bwd", "trd_set_profiling",
     "trd_get_profile", "trd_kernel_launches", "trd_sigma_from_residuals_noalloc",
-    "trd_wait_selftest", "trd_set_graphs", "trd_sample_rows",
+    "trd_wait_selftest", "trd_set_graphs", "trd_sample_rows", "trd_psnr",
 ]
 
 
@@ -108,6 +108,7 @@ def load(path: str = LIB_PATH):
         "trd_wait_selftest": [vp, C.c_int, i64],
         "trd_set_graphs": [vp, C.c_int],
         "trd_sample_rows": [vp, C.c_int, P(i32), i64],
+        "trd_psnr": [vp, vp, dbl, P(dbl)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -380,4 +381,11 @@ class TRD:
         out = C.c_double()
         self._check(self.lib.trd_recovery_error(self.h, C.c_void_p(_dptr(Xref)), C.byref(out)),
                     "trd_recovery_error")
+        return out.value
+
+    def psnr(self, Xref, peak: float = 1.0) -> float:
+        """PSNR (dB) of the current reconstruction against the device tensor Xref."""
+        out = C.c_double()
+        self._check(self.lib.trd_psnr(self.h, C.c_void_p(_dptr(Xref)), float(peak), C.byref(out)),
+                    "trd_psnr")
         return out.value

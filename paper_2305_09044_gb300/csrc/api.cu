@@ -1989,6 +1989,7 @@ trd_status trd_step(trd_t* h, const trd_params* p, trd_report* rep) {
 }
 
 // ------------------------------------------------------------------ reconstruction helpers
+/* err_out, when ref is given, receives {sum (x_hat - ref)^2, sum ref^2} over every entry. */
 static trd_status reconstruct_impl(trd_t* h, const double* const* cores, float* out, const float* ref,
                                    double* err_out) {
   const View v = full_view(h);
@@ -2013,7 +2014,8 @@ static trd_status reconstruct_impl(trd_t* h, const double* const* cores, float* 
   TRY(sync_and_status(h));
   double se = 0, sr = 0;
   for (int i = 0; i < parts; ++i) { se += hp[2 * i]; sr += hp[2 * i + 1]; }
-  *err_out = sr > 0 ? sqrt(se / sr) : sqrt(se);
+  err_out[0] = se;
+  err_out[1] = sr;
   return TRD_OK;
 }
 
@@ -2041,7 +2043,22 @@ trd_status trd_reconstruct_from(trd_t* h, const double* const* cores_host, float
 trd_status trd_recovery_error(trd_t* h, const float* ref, double* err) {
   TRY(check_handle(h));
   if (!ref || !err) return set_err(h, TRD_EINVAL, "NULL argument");
-  return reconstruct_impl(h, nullptr, nullptr, ref, err);
+  double s[2];
+  TRY(reconstruct_impl(h, nullptr, nullptr, ref, s));
+  *err = s[1] > 0 ? sqrt(s[0] / s[1]) : sqrt(s[0]);
+  return TRD_OK;
+}
+
+trd_status trd_psnr(trd_t* h, const float* ref, double peak, double* psnr_out) {
+  TRY(check_handle(h));
+  if (!ref || !psnr_out) return set_err(h, TRD_EINVAL, "NULL argument");
+  if (!(peak > 0) || !isfinite(peak)) return set_err(h, TRD_EINVAL, "peak must be positive and finite");
+  double s[2];
+  TRY(reconstruct_impl(h, nullptr, nullptr, ref, s));
+  double numel = 1;
+  for (int k = 0; k < h->N; ++k) numel *= (double)h->I[k];
+  *psnr_out = s[0] > 0 ? 10.0 * log10(peak * peak * numel / s[0]) : INFINITY;
+  return TRD_OK;
 }
 
 trd_status trd_set_profiling(trd_t* h, int on) {

@@ -18,9 +18,10 @@ the orders 3-5, TR ranks 3-20, 20-80 % missing and 10-20 % outliers of its exper
   video   1024 x 1024 x 256, ranks 16, smooth modes 1-2, 80 % missing, 15 % salt-and-pepper
   grad128 128^4, ranks 20, 10 % outliers, 2^24 sampled observed entries
   image   3 x 1352 x 2000 (a colour image, channel mode first so that the ring's cut keeps
-          r_1 r_c = 60), ranks (3, 20, 20), 70 % missing (completion), noise from the
-          two-component mixture 0.8 N(0, 1e-3) + 0.2 N(0, 0.5) on the [0, 1] scale (here
-          scaled by the clean tensor's range), PSNR against the clean tensor
+          r_1 r_c = 60), ranks (3, 20, 20), fully observed (decomposition), noise on every
+          entry from the two-component mixture 0.8 N(0, 1e-3) + 0.2 N(0, 0.5) on the [0, 1]
+          scale (here scaled by the clean tensor's range), PSNR against the clean tensor
+  imagec  the same image tensor and noise with 70 % of the entries missing (completion)
 """
 from __future__ import annotations
 
@@ -63,8 +64,10 @@ WORKLOADS = {
                       smooth_width=8.0, data_seed=1004, init_seed=2004, sample_seed=3004),
     "grad128": Workload("grad128", (128,) * 4, (20,) * 4, 0.0, 0.1,
                         data_seed=1005, init_seed=2005, sample_seed=3005, n_sampled=1 << 24),
-    "image": Workload("image", (3, 1352, 2000), (3, 20, 20), 0.7, 0.2, outlier_kind="gmm",
+    "image": Workload("image", (3, 1352, 2000), (3, 20, 20), 0.0, 0.2, outlier_kind="gmm",
                       data_seed=1006, init_seed=2006, sample_seed=3006),
+    "imagec": Workload("imagec", (3, 1352, 2000), (3, 20, 20), 0.7, 0.2, outlier_kind="gmm",
+                       data_seed=1006, init_seed=2006, sample_seed=3006),
 }
 
 # variances of the two mixture components of the 'gmm' noise, on data rescaled to [0, 1]
