@@ -406,8 +406,17 @@ def image_quality(name, prec, torch, max_iters=30, tol=1e-3):
         e = r["e"]
         it += 1
         trace.append(t.psnr(Xt, peak))
+    # two more steps traced at every phase, after the measured run (not part of it)
+    t.set_profiling(2)
+    t.get_profile(reset=True)
+    for _ in range(2):
+        t.step(sigma=-1.0)
+    ph = t.get_profile(reset=True)
+    t.set_profiling(False)
     t.close()
-    return {"workload": w.name, "dims": list(w.dims), "ranks": list(w.ranks), "missing": w.missing,
+    return {"phase_ms_per_step_untimed": {k[:-3]: round(v / 2, 4) for k, v in ph.items()
+                                          if k.endswith("_ms") and v > 0},
+            "workload": w.name, "dims": list(w.dims), "ranks": list(w.ranks), "missing": w.missing,
             "noise": "0.8 N(0, 1e-3) + 0.2 N(0, 0.5) on the [0, 1] scale", "precision": prec,
             "psnr_noisy_observed_db": noisy, "psnr_init_db": trace[0], "psnr_db": trace[-1],
             "iters": it, "e": e, "seconds": total / 1e3,

@@ -53,9 +53,77 @@ __global__ void k_sum_parts(const double* __restrict__ part, int parts, int64_t 
   }
 }
 
+// The same factor for large K = r r1 (all slices, no index list), as the realigned Gram of the
+// slice matrix: with Z viewed as an I x K row-major matrix (row i = Z(i), column x = b r + a),
+// P = Z^T Z is K x K and E[(a r + a'), (b r1 + b')] = P[b r + a, b' r + a'].  P is symmetric, so
+// only its 32 x 32 tiles on and below the diagonal are formed (tile pair q -> (tp, tq), tq <= tp),
+// each written to both of its places in E.  The slice range is split over gridDim.y parts so
+// that the I K^2 / 2 FMAs spread over all SMs; part p writes out[p * tot ...] (summed after, in
+// part order: the result does not depend on scheduling).  256 threads, 2 x 2 outputs each.
+__global__ void __launch_bounds__(256) k_fgmc_E_gram(const double* __restrict__ Z, int64_t n_all, int r, int r1,
+                                                     double* __restrict__ out) {
+  constexpr int T = 32, CH = 32;
+  __shared__ double sa[CH][T + 1], sb[CH][T + 1];
+  const int K = r * r1;
+  const int64_t tot = (int64_t)K * K;
+  const int q = blockIdx.x;
+  int tp = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+  while ((tp + 1) * (tp + 2) / 2 <= q) ++tp;
+  while (tp * (tp + 1) / 2 > q) --tp;
+  const int tq = q - tp * (tp + 1) / 2;
+  const int x0 = tp * T, y0 = tq * T;
+  const int64_t per = (n_all + gridDim.y - 1) / gridDim.y;
+  const int64_t i0 = (int64_t)blockIdx.y * per;
+  const int64_t i1 = imin(n_all, i0 + per);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int64_t c0 = i0; c0 < i1; c0 += CH) {
+    const int cnt = (int)imin(CH, i1 - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < CH * T; e += 256) {
+      const int ii = e >> 5, cc = e & 31;
+      const bool ok = ii < cnt;
+      sa[ii][cc] = ok && x0 + cc < K ? Z[(c0 + ii) * K + x0 + cc] : 0.0;
+      sb[ii][cc] = ok && y0 + cc < K ? Z[(c0 + ii) * K + y0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int ii = 0; ii < CH; ++ii) {
+      const double a0 = sa[ii][ty], a1 = sa[ii][ty + 16];
+      const double b0 = sb[ii][tx], b1 = sb[ii][tx + 16];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+  }
+  double* o = out + (int64_t)blockIdx.y * tot;
+  const int cols = r1 * r1;
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int x = x0 + ty + 16 * u, y = y0 + tx + 16 * v;
+      if (x >= K || y >= K || (tp == tq && y > x)) continue;
+      const int a = x % r, b = x / r, a2 = y % r, b2 = y / r;
+      o[(int64_t)(a * r + a2) * cols + (b * r1 + b2)] = acc[u][v];
+      if (x != y) o[(int64_t)(a2 * r + a) * cols + (b2 * r1 + b)] = acc[u][v];
+    }
+}
+
 cudaError_t launch_fgmc_E(const double* Z, const int32_t* idx, int64_t n, int rk, int rk1,
                           double* E, double* work, cudaStream_t st) {
   const int64_t tot = (int64_t)rk * rk * rk1 * rk1;
+  if (!idx && work && rk * rk1 > kLdlKmax) {
+    const int nt = (rk * rk1 + 31) / 32, pairs = nt * (nt + 1) / 2;
+    const int parts = (int)imax(1, imin(imin(16, (n + 63) / 64), (2 * 152 + pairs - 1) / pairs));
+    k_fgmc_E_gram<<<dim3((unsigned)pairs, (unsigned)parts), 256, 0, st>>>(Z, n, rk, rk1, parts > 1 ? work : E);
+    note_launch();
+    if (parts == 1) return cudaGetLastError();
+    k_sum_parts<<<(unsigned)imin((tot + 255) / 256, 4096), 256, 0, st>>>(work, parts, tot, E);
+    note_launch();
+    return cudaGetLastError();
+  }
   const unsigned blocks = (unsigned)((tot + 127) / 128);
   // enough slice parts to cover the SMs; partial factors go to `work` ([parts][tot])
   int parts = (int)imax(1, imin(imin(n / 8, 16), (2 * 152 + blocks - 1) / blocks));
@@ -392,118 +460,193 @@ cudaError_t launch_ldl_solve(const double* Lcm, const double* Dinv, const double
 }
 
 // ------------------------------------------------------------------ Cholesky of G + lambda I (K > 128)
-// One CTA, right-looking, lower triangle in shared memory when it fits (K <= 160), else in
-// the output array.  lambda >= 0 absolute, < 0 relative to tr(G)/K.  Per column: every
-// thread reads the pivot, the sub-diagonal column is scaled into a buffer, then the
-// trailing lower triangle is updated (two barriers per column).  A non-positive or
-// non-finite pivot sets DEV_SINGULAR and stops (L is then unusable).
-__global__ void k_cholesky(const double* __restrict__ G, int K, double lam_in, double* __restrict__ L,
-                           double* __restrict__ scal, int* __restrict__ dstatus, int use_smem) {
-  extern __shared__ double smc[];
-  __shared__ double s_red[32];
-  __shared__ double s_col[1024];
-  double* W = use_smem ? smc : L;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  // lambda (trace reduction in parallel)
+// Blocked right-looking Cholesky (G + lambda I = L L^T, FP64) for the Gram sizes beyond the
+// register-resident LDL^T (K > 128), spread over the GPU: per panel of 32 columns, one warp
+// factors the diagonal block in registers, one warp per row solves the panel below it against
+// that block, and CTAs of 32 x 32 tiles apply the symmetric rank-32 update to the trailing
+// lower triangle.  GB300's FP64 rate per SM is low, so the K^3 / 6 update FMAs must not sit on
+// one SM.  Output: L row-major lower (diagonal = sqrt of the pivot) in L[0, K^2), the reciprocal
+// diagonal in L[K^2, K^2 + K), the column-major copy of L in L[K^2 + K, 2 K^2 + K) (so that both
+// substitutions read L with unit stride).  lambda >= 0 absolute, < 0 relative to tr(G) / K.  A
+// non-positive or non-finite pivot sets DEV_SINGULAR; the later kernels see it and do nothing.
+constexpr int BCH_NB = 32;
+
+__global__ void k_bchol_init(const double* __restrict__ G, int K, double lam_in, double* __restrict__ W,
+                             double* __restrict__ scal) {
+  __shared__ double s_red[8];
+  __shared__ double s_lam;
+  const int tid = threadIdx.x;
   double tr = 0.0;
-  for (int i = tid; i < K; i += nt) tr += G[(int64_t)i * K + i];
+  for (int i = tid; i < K; i += blockDim.x) tr += G[(int64_t)i * K + i];
   for (int o = 16; o > 0; o >>= 1) tr += __shfl_down_sync(0xffffffffu, tr, o);
   if ((tid & 31) == 0) s_red[tid >> 5] = tr;
   __syncthreads();
   if (tid == 0) {
     double t = 0.0;
-    for (int w = 0; w < (nt + 31) / 32; ++w) t += s_red[w];
-    s_red[0] = lam_in >= 0 ? lam_in : -lam_in * t / K;
-    scal[5] = s_red[0];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
+    s_lam = lam_in >= 0 ? lam_in : -lam_in * t / K;
+    if (blockIdx.x == 0) scal[5] = s_lam;
   }
   __syncthreads();
-  const double lam = s_red[0];
-  for (int e = tid; e < K * K; e += nt) {
-    const int i = e / K, j = e % K;
-    W[e] = j <= i ? G[e] + (i == j ? lam : 0.0) : 0.0;
+  const double lam = s_lam;
+  const int64_t n = (int64_t)K * K;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + tid; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / K), m = (int)(e - (int64_t)i * K);
+    if (m <= i) W[e] = G[e] + (i == m ? lam : 0.0);
   }
-  __syncthreads();
-  // pivot j's square root and reciprocal are computed once, by thread 0 (which owns the
-  // diagonal element of the trailing update), and published through shared memory
-  __shared__ double s_dj, s_rj;
-  __shared__ int s_bad;
-  if (tid == 0) {
-    const double piv = W[0];
-    s_bad = !(piv > 0.0) || !isfinite(piv);
-    s_dj = s_bad ? 1.0 : sqrt(piv);
-    s_rj = 1.0 / s_dj;
-  }
-  __syncthreads();
+}
+
+// one warp: lane i holds row j0 + i of the diagonal block (columns j0 .. j0 + 31)
+__global__ void __launch_bounds__(32) k_bchol_diag(double* __restrict__ W, double* __restrict__ rdiag, int K,
+                                                   int j0, int* __restrict__ dstatus) {
+  if (*(volatile int*)dstatus & DEV_SINGULAR) return;
+  const int lane = threadIdx.x;
+  const int nb = imin(BCH_NB, K - j0);
+  const bool live = lane < nb;
+  const double* row = W + (int64_t)(j0 + lane) * K + j0;
+  double a[BCH_NB];
+#pragma unroll
+  for (int m = 0; m < BCH_NB; ++m) a[m] = live ? (m <= lane ? row[m] : 0.0) : (m == lane ? 1.0 : 0.0);
   bool bad = false;
-  for (int j = 0; j < K; ++j) {
-    if (s_bad) { bad = true; break; }                  // uniform across threads
-    const double dj = s_dj, rj = s_rj;
-    for (int i = j + 1 + tid; i < K; i += nt) s_col[i] = W[(int64_t)i * K + j] * rj;
-    __syncthreads();
-    if (tid == 0) {
-      W[(int64_t)j * K + j] = dj;
-      L[(int64_t)K * K + j] = rj;       // reciprocal diagonal, used by the solves
+  double myr = 1.0;
+#pragma unroll
+  for (int j = 0; j < BCH_NB; ++j) {
+    const double piv = __shfl_sync(0xffffffffu, a[j], j);
+    bad |= !(piv > 0.0) || !isfinite(piv);
+    const double dj = bad ? 1.0 : sqrt(piv);
+    const double rj = 1.0 / dj;
+    if (lane > j) a[j] *= rj;
+    if (lane == j) { a[j] = dj; myr = rj; }
+#pragma unroll
+    for (int m = j + 1; m < BCH_NB; ++m) {
+      const double lmj = __shfl_sync(0xffffffffu, a[j], m);
+      if (lane >= m) a[m] = fma(-a[j], lmj, a[m]);
     }
-    for (int i = j + 1 + tid; i < K; i += nt) W[(int64_t)i * K + j] = s_col[i];
-    // trailing lower triangle, packed: element e -> (ii, mm) with mm <= ii, so every lane of
-    // every warp does useful FP64 work (predicated-off lanes would still occupy the FP64 pipe)
-    {
-      const int n = K - j - 1;
-      const int tri = n * (n + 1) / 2;
-      for (int e = tid; e < tri; e += nt) {
-        int ii = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-        while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
-        while (ii * (ii + 1) / 2 > e) --ii;
-        const int mm = e - ii * (ii + 1) / 2;
-        const int i = j + 1 + ii, m = j + 1 + mm;
-        W[(int64_t)i * K + m] -= s_col[i] * s_col[m];
-      }
-    }
-    if (tid == 0 && j + 1 < K) {
-      // thread 0 updated W[j+1][j+1] above (packed element 0): prepare the next pivot
-      const double piv = W[(int64_t)(j + 1) * K + (j + 1)];
-      s_bad = !(piv > 0.0) || !isfinite(piv);
-      s_dj = s_bad ? 1.0 : sqrt(piv);
-      s_rj = 1.0 / s_dj;
-    }
-    __syncthreads();
   }
   if (bad) {
-    if (tid == 0) atomicOr(dstatus, (int)DEV_SINGULAR);
+    if (lane == 0) atomicOr(dstatus, (int)DEV_SINGULAR);
     return;
   }
-  if (use_smem)
-    for (int e = tid; e < K * K; e += nt) L[e] = W[e];
+  if (live) {
+    double* wr = W + (int64_t)(j0 + lane) * K + j0;
+#pragma unroll
+    for (int m = 0; m < BCH_NB; ++m)
+      if (m <= lane) wr[m] = a[m];
+    rdiag[j0 + lane] = myr;
+  }
+}
+
+// rows i >= j0 + 32: row i of the panel, x, solves x L11^T = a (forward substitution in the
+// column-oriented form: x_t is final at step t and is subtracted from the later entries)
+__global__ void __launch_bounds__(256) k_bchol_panel(double* __restrict__ W, const double* __restrict__ rdiag,
+                                                     int K, int j0, const int* __restrict__ dstatus) {
+  if (*(volatile const int*)dstatus & DEV_SINGULAR) return;
+  __shared__ double sL[BCH_NB][BCH_NB + 1];
+  __shared__ double sr[BCH_NB];
+  for (int e = threadIdx.x; e < BCH_NB * BCH_NB; e += blockDim.x) {
+    const int i = e / BCH_NB, m = e % BCH_NB;
+    sL[i][m] = m <= i ? W[(int64_t)(j0 + i) * K + j0 + m] : 0.0;
+  }
+  if (threadIdx.x < BCH_NB) sr[threadIdx.x] = rdiag[j0 + threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  for (int i = j0 + BCH_NB + blockIdx.x * warps + (threadIdx.x >> 5); i < K; i += gridDim.x * warps) {
+    double* wr = W + (int64_t)i * K + j0;
+    double a = wr[lane];
+#pragma unroll
+    for (int t = 0; t < BCH_NB; ++t) {
+      const double xt = __shfl_sync(0xffffffffu, a, t) * sr[t];
+      if (lane == t) a = xt;
+      if (lane > t) a = fma(-xt, sL[lane][t], a);
+    }
+    wr[lane] = a;
+  }
+}
+
+// trailing update A22 -= L21 L21^T on the lower triangle, one 32 x 32 tile per CTA; tile q of
+// the packed lower triangle of tiles -> (bi, bj), bj <= bi
+__global__ void __launch_bounds__(256) k_bchol_update(double* __restrict__ W, int K, int j0,
+                                                      const int* __restrict__ dstatus) {
+  if (*(volatile const int*)dstatus & DEV_SINGULAR) return;
+  __shared__ double sa[BCH_NB][BCH_NB + 1];
+  __shared__ double sb[BCH_NB][BCH_NB + 1];
+  const int q = blockIdx.x;
+  int bi = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+  while ((bi + 1) * (bi + 2) / 2 <= q) ++bi;
+  while (bi * (bi + 1) / 2 > q) --bi;
+  const int bj = q - bi * (bi + 1) / 2;
+  const int base = j0 + BCH_NB;
+  const int r0 = base + bi * BCH_NB, c0 = base + bj * BCH_NB;
+  for (int e = threadIdx.x; e < BCH_NB * BCH_NB; e += blockDim.x) {
+    const int i = e / BCH_NB, t = e % BCH_NB;
+    sa[i][t] = r0 + i < K ? W[(int64_t)(r0 + i) * K + j0 + t] : 0.0;
+    sb[i][t] = c0 + i < K ? W[(int64_t)(c0 + i) * K + j0 + t] : 0.0;
+  }
+  __syncthreads();
+  const int m = threadIdx.x & 31;
+  for (int i = threadIdx.x >> 5; i < BCH_NB; i += blockDim.x >> 5) {
+    const int gi = r0 + i, gm = c0 + m;
+    if (gi >= K || gm >= K || gm > gi) continue;
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < BCH_NB; ++t) acc = fma(sa[i][t], sb[m][t], acc);
+    W[(int64_t)gi * K + gm] -= acc;
+  }
+}
+
+// column-major copy of the lower triangle: Lc[j K + i] = L[i][j], i >= j (32 x 32 tiles)
+__global__ void __launch_bounds__(256) k_bchol_colcopy(const double* __restrict__ W, double* __restrict__ Lc,
+                                                       int K, const int* __restrict__ dstatus) {
+  if (*(volatile const int*)dstatus & DEV_SINGULAR) return;
+  __shared__ double t[BCH_NB][BCH_NB + 1];
+  const int i0 = blockIdx.y * BCH_NB, j0 = blockIdx.x * BCH_NB;
+  if (j0 > i0) return;
+  for (int e = threadIdx.x; e < BCH_NB * BCH_NB; e += blockDim.x) {
+    const int r = e / BCH_NB, c = e % BCH_NB;
+    if (i0 + r < K && j0 + c < K) t[r][c] = W[(int64_t)(i0 + r) * K + j0 + c];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < BCH_NB * BCH_NB; e += blockDim.x) {
+    const int c = e / BCH_NB, r = e % BCH_NB;
+    if (i0 + r < K && j0 + c < K && i0 + r >= j0 + c) Lc[(int64_t)(j0 + c) * K + i0 + r] = t[r][c];
+  }
 }
 
 cudaError_t launch_cholesky(const double* G, int K, double lambda, double* L, double* scal,
                             int* dstatus, cudaStream_t st) {
-  const size_t bytes = (size_t)K * K * sizeof(double);
-  const bool sm = bytes <= 200 * 1024;
-  if (sm) cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k_cholesky<<<1, 256, sm ? bytes : 0, st>>>(G, K, lambda, L, scal, dstatus, sm ? 1 : 0);
+  double* rdiag = L + (int64_t)K * K;
+  double* Lc = rdiag + K;
+  const int64_t n = (int64_t)K * K;
+  k_bchol_init<<<(unsigned)imin((n + 255) / 256, 1024), 256, 0, st>>>(G, K, lambda, L, scal);
+  note_launch();
+  for (int j0 = 0; j0 < K; j0 += BCH_NB) {
+    k_bchol_diag<<<1, 32, 0, st>>>(L, rdiag, K, j0, dstatus);
+    note_launch();
+    const int rest = K - j0 - BCH_NB;
+    if (rest <= 0) break;
+    k_bchol_panel<<<(unsigned)imin((rest + 7) / 8, 1024), 256, 0, st>>>(L, rdiag, K, j0, dstatus);
+    note_launch();
+    const int nt = (rest + BCH_NB - 1) / BCH_NB;
+    k_bchol_update<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(L, K, j0, dstatus);
+    note_launch();
+  }
+  const unsigned tb = (unsigned)((K + BCH_NB - 1) / BCH_NB);
+  k_bchol_colcopy<<<dim3(tb, tb), 256, 0, st>>>(L, Lc, K, dstatus);
   note_launch();
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ h = d (G + lambda I)^{-1}
-// One warp per row of d: forward substitution with L, then back substitution with L^T.
-// L is staged in shared memory when it fits (K <= 160), so each substitution step costs a
-// shared-memory load instead of an L2 round trip.
-__global__ void k_solve_rows(const double* __restrict__ Lg, const double* __restrict__ d,
-                             double* __restrict__ h, int K, int64_t rows, int stage_L) {
+// One warp per row of d: forward substitution with L (column j of L read from the column-major
+// copy), then back substitution with L^T (row j of L), both with unit stride across the lanes.
+// The factor comes from L2 (K > 128: too large for shared memory).
+__global__ void k_solve_rows(const double* __restrict__ L, const double* __restrict__ d,
+                             double* __restrict__ h, int K, int64_t rows) {
   extern __shared__ double sb[];
   const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const double* L = Lg;
-  const double* rdiag = Lg + (int64_t)K * K;
+  const double* rdiag = L + (int64_t)K * K;
+  const double* Lc = rdiag + K;
   double* b = sb + (size_t)w * K;
-  if (stage_L) {
-    double* Ls = sb + (size_t)warps * K;
-    for (int e = threadIdx.x; e < K * K + K; e += blockDim.x) Ls[e] = Lg[e];
-    __syncthreads();
-    L = Ls;
-    rdiag = Ls + (int64_t)K * K;
-  }
   for (int64_t row = (int64_t)blockIdx.x * warps + w; row < rows; row += (int64_t)gridDim.x * warps) {
     for (int m = lane; m < K; m += 32) b[m] = d[row * K + m];
     __syncwarp();
@@ -511,14 +654,16 @@ __global__ void k_solve_rows(const double* __restrict__ Lg, const double* __rest
       const double yj = b[j] * rdiag[j];
       __syncwarp();
       if (lane == 0) b[j] = yj;
-      for (int m = j + 1 + lane; m < K; m += 32) b[m] -= L[(int64_t)m * K + j] * yj;
+      const double* col = Lc + (int64_t)j * K;
+      for (int m = j + 1 + lane; m < K; m += 32) b[m] -= col[m] * yj;
       __syncwarp();
     }
     for (int j = K - 1; j >= 0; --j) {
       const double hj = b[j] * rdiag[j];
       __syncwarp();
       if (lane == 0) b[j] = hj;
-      for (int m = lane; m < j; m += 32) b[m] -= L[(int64_t)j * K + m] * hj;
+      const double* rw = L + (int64_t)j * K;
+      for (int m = lane; m < j; m += 32) b[m] -= rw[m] * hj;
       __syncwarp();
     }
     for (int m = lane; m < K; m += 32) h[row * K + m] = b[m];
@@ -529,12 +674,11 @@ __global__ void k_solve_rows(const double* __restrict__ Lg, const double* __rest
 cudaError_t launch_solve_rows(const double* L, const double* d, double* h, int K, int64_t rows,
                               cudaStream_t st) {
   const int warps = 1;
-  const bool stage = (size_t)K * K * sizeof(double) <= 160 * 1024;
-  const size_t smem = (size_t)warps * K * sizeof(double) + (stage ? (size_t)(K * K + K) * sizeof(double) : 0);
+  const size_t smem = (size_t)warps * K * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_solve_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const unsigned blocks = (unsigned)imin((rows + warps - 1) / warps, 8192);
-  k_solve_rows<<<blocks, warps * 32, smem, st>>>(L, d, h, K, rows, stage ? 1 : 0);
+  k_solve_rows<<<blocks, warps * 32, smem, st>>>(L, d, h, K, rows);
   note_launch();
   return cudaGetLastError();
 }

@@ -29,9 +29,9 @@ def torch_cuda():
     return torch
 
 
-def _handle(torch, prec, X, words):
+def _handle(torch, prec, X, words, dims=DIMS, ranks=RANKS):
     from paper_2305_09044_gb300 import TRD
-    t = TRD(DIMS, RANKS, prec)
+    t = TRD(dims, ranks, prec)
     xd = torch.from_numpy(flat(X)).cuda()
     md = torch.from_numpy(words.view(np.int32)).cuda()
     t.set_data(xd, md)
@@ -66,6 +66,28 @@ def test_singular_system_is_reported_and_step_rejected(torch_cuda, prec):
     assert ei.value.status == binding.TRD_ESINGULAR
     assert np.array_equal(t.get_core(0), broken[0])
     _update_matches_oracle(t, X, P, cores, 1, TOL[prec])
+
+
+def test_singular_system_blocked_cholesky(torch_cuda):
+    """The same failure at K = 204 (ranks (4, 12, 17, 4)), where the blocked multi-CTA
+    Cholesky factors the Gram: the zero pivot is met in the first diagonal block, the later
+    panels are skipped, the step is rejected, and the next update of that core is the
+    oracle's."""
+    from paper_2305_09044_gb300 import TrdError, binding
+    dims, ranks = (5, 24, 22, 6), (4, 12, 17, 4)
+    X, P, words, truth, Xt = problem(dims, ranks, 0.3, 0.1, 43)
+    t, keep = _handle(torch_cuda, "fp64", X, words, dims, ranks)
+    cores = O.init_cores(dims, ranks, seed=6)
+    broken = [c.copy() for c in cores]
+    broken[3][:] = 0.0
+    t.set_cores(broken)
+    t.residual_weights(1, 1.5)
+    t.core_gradient(1)
+    with pytest.raises(TrdError) as ei:
+        t.core_update(1, 0.0)
+    assert ei.value.status == binding.TRD_ESINGULAR
+    assert np.array_equal(t.get_core(1), broken[1])
+    _update_matches_oracle(t, X, P, cores, 1, TOL["fp64"])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])

@@ -238,11 +238,16 @@ def test_trajectory_sketched_fp32(torch_cuda):
 
 @pytest.mark.parametrize("prec,dims,ranks", [("fp64", (12, 10, 9, 8), (10, 10, 10, 10)),
                                              ("fp32", (10, 9, 8, 7), (8, 16, 8, 16)),
-                                             ("fp32", (9, 8, 7, 6, 5), (11, 11, 11, 11, 11))])
+                                             ("fp32", (9, 8, 7, 6, 5), (11, 11, 11, 11, 11)),
+                                             ("fp64", (8, 20, 120), (3, 20, 20)),
+                                             ("fp64", (5, 24, 22, 6), (4, 12, 17, 4))])
 def test_scaled_step_large_gram(torch_cuda, prec, dims, ranks):
     """K = r_k r_{k+1} of 100, 128 and 121: the FP64 LDL^T factorisation and the
     row-parallel solves of the scaled step (Eq. sg, Eq. hI) at the Gram sizes of the 64^5 rank-10
-    workload and beyond, against the oracle's Cholesky, from identical state."""
+    workload and beyond, against the oracle's Cholesky, from identical state.  K = 400 (the
+    image ranks (3, 20, 20)) and 204 take the blocked multi-CTA Cholesky, both with a ragged
+    last panel, and the FGMC factor of their r_k r_{k+1} > 128 cores comes from the tiled
+    slice-Gram kernel (compared here through G^{!=k}, 1e-12)."""
     t, X, P, Xt, keep = _make(torch_cuda, dims, ranks, prec)
     cores = O.init_cores(dims, ranks, seed=13)
     sigma = 2.0
@@ -252,6 +257,7 @@ def test_scaled_step_large_gram(torch_cuda, prec, dims, ranks):
         t.residual_weights(k, sigma)
         d = t.core_gradient(k)
         assert rel(d, st.d) <= TOL[prec]
+        assert rel(t.fgmc_gram(k), st.G) <= 1e-12
         eta = t.core_update(k, -1e-10)
         assert abs(eta - st.eta) <= TOL[prec] * 10 * abs(st.eta), (k, eta, st.eta)
         assert rel(t.get_core(k) - cores[k], st.cores[k] - cores[k]) <= TOL[prec] * 10
