@@ -271,6 +271,8 @@ cudaError_t launch_ldl_factor(const double* G, int K, double lambda, double* Lcm
 // also <d, h> into *num (per-row parts in dot_part[rows]; ctr: a zeroed counter word, left zero)
 cudaError_t launch_ldl_solve(const double* Lcm, const double* Dinv, const double* d, double* h, int K, int64_t rows,
                              double* dot_part, unsigned int* ctr, double* num, cudaStream_t st);
+// blocked multi-CTA Cholesky for K > kLdlKmax; L holds 2 K^2 + K doubles: the row-major lower
+// factor, its reciprocal diagonal, its column-major copy (read by launch_solve_rows)
 cudaError_t launch_cholesky(const double* G, int K, double lambda, double* L, double* scal,
                             int* dstatus, cudaStream_t st);
 cudaError_t launch_solve_rows(const double* L, const double* d, double* h, int K, int64_t rows,
