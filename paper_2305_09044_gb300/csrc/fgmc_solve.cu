@@ -496,6 +496,23 @@ __global__ void k_bchol_init(const double* __restrict__ G, int K, double lam_in,
   }
 }
 
+// 1/sqrt(p) for the pivots of the blocked Cholesky: FP32 seed (rsqrtf, relative error below
+// 2^-21) refined by two Newton steps for the inverse square root, y <- y + y (1 - p y^2) / 2,
+// each of which squares the relative error, so the result is within a few ulp of FP64.  Kept
+// off the exact square root and division, whose long dependent sequences would sit on the
+// critical path of every pivot.  Outside [1e-30, 1e30] (beyond the FP32 seed's range) the
+// exact expression is used.
+__device__ __noinline__ double rsqrt_exact(double p) { return 1.0 / sqrt(p); }
+
+__device__ __forceinline__ double rsqrt_pivot(double p) {
+  if (!(p >= 1e-30 && p <= 1e30)) return rsqrt_exact(p);
+  double y = (double)rsqrtf((float)p);
+  double e = fma(-p * y, y, 1.0);
+  y = fma(0.5 * y, e, y);
+  e = fma(-p * y, y, 1.0);
+  return fma(0.5 * y, e, y);
+}
+
 // one warp: lane i holds row j0 + i of the diagonal block (columns j0 .. j0 + 31)
 __global__ void __launch_bounds__(32) k_bchol_diag(double* __restrict__ W, double* __restrict__ rdiag, int K,
                                                    int j0, int* __restrict__ dstatus) {
@@ -513,8 +530,8 @@ __global__ void __launch_bounds__(32) k_bchol_diag(double* __restrict__ W, doubl
   for (int j = 0; j < BCH_NB; ++j) {
     const double piv = __shfl_sync(0xffffffffu, a[j], j);
     bad |= !(piv > 0.0) || !isfinite(piv);
-    const double dj = bad ? 1.0 : sqrt(piv);
-    const double rj = 1.0 / dj;
+    const double rj = bad ? 1.0 : rsqrt_pivot(piv);
+    const double dj = bad ? 1.0 : piv * rj;
     if (lane > j) a[j] *= rj;
     if (lane == j) { a[j] = dj; myr = rj; }
 #pragma unroll
