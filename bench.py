@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--precision", default=None, choices=[None, "bf16", "fp32", "fp64"])
     ap.add_argument("--no-converge", action="store_true")
     ap.add_argument("--no-image", action="store_true", help="skip the image-shaped PSNR runs")
+    ap.add_argument("--image-only", action="store_true",
+                    help="run only the image-shaped PSNR runs and print them as one JSON line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the row-sampling variant's measurement")
     ap.add_argument("--converge-iters", type=int, default=60)
@@ -561,6 +563,16 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.image_only:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        torch.cuda.set_device(local)
+        prec = args.precision or "bf16"
+        if rank == 0:
+            print(json.dumps({"image": [image_quality(n, prec, torch) for n in ("image", "imagec")]}),
+                  flush=True)
         return
     _init_dist(world)
     run_ours(args, rank, world, local)
