@@ -188,6 +188,8 @@ def corruption_chunks(w: Workload, chunk: int = 1 << 26):
         outl = g_out.random(c) < w.outlier_frac
         if w.outlier_kind == "saltpepper":
             u = np.where(g_u.random(c) < 0.5, -1.0, 1.0)
+        elif w.outlier_kind == "gmm":
+            u = g_u.standard_normal(c)
         else:
             outl &= mask
             u = g_u.uniform(-1.0, 1.0, c)
@@ -203,6 +205,9 @@ def assemble_chunk(x_true, outl, u, noise, kind: str, std: float, lo: float, hi:
         x = x + noise
     if kind == "saltpepper":
         return np.where(outl, np.where(u > 0, hi, lo), x)
+    if kind == "gmm":
+        sd = np.where(outl, math.sqrt(GMM_VARS[1]), math.sqrt(GMM_VARS[0]))
+        return x + (hi - lo) * sd * u
     return np.where(outl, scale * std * u, x)
 
 

@@ -587,3 +587,34 @@ def test_mixture_noise_decomposition_raises_psnr():
         runs[mode] = O.psnr(O.reconstruct(cores), Xt, peak)
     assert runs["adaptive"] > max(noisy, p0) + 10.0, (noisy, p0, runs)
     assert runs["adaptive"] > runs["ls"] + 5.0, runs
+
+
+def test_mixture_noise_generators():
+    """The two-component mixture noise (Sec. 5 image experiments) drawn whole-tensor and in
+    chunks: every entry noisy, a fraction outlier_frac from the wide component, component
+    variances GMM_VARS on the [0, 1] scale (relative to the clean range); the chunked draw
+    does not depend on the chunk size."""
+    from paper_2305_09044_gb300 import synth
+    dims = (3, 200, 300)
+    w = synth.Workload("g", dims, (2, 2, 2), 0.5, 0.2, outlier_kind="gmm", data_seed=5)
+    rng = np.random.default_rng(0)
+    Xt = rng.random(dims) * 4.0 - 1.0
+    lo, hi = float(Xt.min()), float(Xt.max())
+    c = synth.draw_corruption(w)
+    N_whole = (synth.assemble(Xt, c, kind="gmm") - Xt) / (hi - lo)
+    flat_t = Xt.reshape(-1, order="F")
+    parts = {}
+    for chunk in (1 << 12, 1 << 16):
+        N = np.empty(flat_t.size)
+        O_ = np.empty(flat_t.size, dtype=bool)
+        for s, m, o, u, nz in synth.corruption_chunks(w, chunk):
+            e = s + m.size
+            N[s:e] = (synth.assemble_chunk(flat_t[s:e], o, u, nz, "gmm", 0.0, lo, hi) - flat_t[s:e]) / (hi - lo)
+            O_[s:e] = o
+        parts[chunk] = (N, O_)
+    assert np.array_equal(parts[1 << 12][0], parts[1 << 16][0])
+    for N, O_ in [(N_whole.reshape(-1, order="F"), c.outlier.reshape(-1, order="F")), parts[1 << 16]]:
+        assert abs(O_.mean() - 0.2) < 0.01
+        assert np.all(N != 0.0)
+        assert abs(np.var(N[O_]) / synth.GMM_VARS[1] - 1) < 0.05
+        assert abs(np.var(N[~O_]) / synth.GMM_VARS[0] - 1) < 0.05
