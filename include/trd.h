@@ -236,22 +236,25 @@ trd_status trd_sigma_from_residuals(trd_t* handle, const float* resid_dev, int64
                                     double x_obs_rms, double sigma_prev, double* sigma_out);
 
 /* Allocation-free form of trd_sigma_from_residuals, for callers that cannot allocate device
- * memory: code running while a CUDA stream is being captured into a graph (where allocation
- * calls are not permitted), and hosts that own all device memory through their own allocator
- * and forbid libraries from calling cudaMalloc.  It needs no handle and allocates nothing: its
- * work space is a fixed device array built into the library (about 24 MB, held on every GPU
- * that loads the library until the process exits).  The paper has no counterpart; this is an
+ * memory: hosts that own all device memory through their own allocator or memory pool and
+ * forbid libraries from calling cudaMalloc, processes held to a fixed device-memory budget
+ * in which a late allocation could fail, and latency-bound loops that cannot afford the
+ * device-wide synchronisation cudaMalloc and cudaFree may imply.  It needs no handle and
+ * allocates nothing: its work space is a fixed device array built into the library (about
+ * 16.8 MB: 2^20 x 16 bytes of keys and candidates plus a 72 KB work area), held on every GPU
+ * that loads the library until the process exits.  The paper has no counterpart; this is an
  * interface convenience only.
  *   resid_dev      DEVICE array of n float residuals, 1 <= n <= 2^20 (larger n: TRD_EINVAL)
- *   x_obs_rms      rms of the observed data, >= 0 (floor of the width)
+ *   x_obs_rms      rms of the observed data, >= 0 (floor of the width; NaN: TRD_EINVAL)
  *   sigma_prev     previous width (<= 0 or inf disables the 0.9 limiter)
  *   sigma_out_dev  DEVICE pointer receiving the width (one double), written on the stream
  *   cuda_stream    cudaStream_t the work is ordered on (NULL = legacy default stream)
  * The first call on each device looks up the array's device address with that device
  * current; make that first call before any stream capture begins.  All calls share the
- * array: calls whose work may overlap on the GPU (different streams, or different host
- * threads on the same device) race and must be serialised by the caller.  The call does not
- * synchronise; it returns TRD_EINVAL for bad arguments and TRD_ECUDA when a launch fails. */
+ * array and every call clears what must start at zero: calls whose work may overlap on the
+ * GPU (different streams, or different host threads on the same device) race and must be
+ * serialised by the caller.  The call does not synchronise; it returns TRD_EINVAL for bad
+ * arguments and TRD_ECUDA when a launch fails. */
 trd_status trd_sigma_from_residuals_noalloc(const float* resid_dev, int64_t n, double x_obs_rms,
                                             double sigma_prev, double* sigma_out_dev,
                                             void* cuda_stream);

@@ -139,6 +139,15 @@ struct Extra {
   uint64_t mst_gen[2] = {~0ull, ~0ull};   // view (sketch) the relayout was made for
   int64_t mst_W[2] = {0, 0};
   int64_t ldT = 0, W = 0;
+  // the view's data re-laid with a row stride that is a multiple of 4 floats, for the
+  // tensor-core passes when the inner block size P_in is not (TMA row strides are multiples
+  // of 16 bytes); cached per view like the mask rows
+  DevBuf Xpad;
+  const float* xpad_src = nullptr;
+  uint64_t xpad_gen = ~0ull;
+  int64_t xpad_Pin = -1, xpad_Pout = -1;
+  const float* Xtc = nullptr;   // data operand of the tensor-core passes (view.X or Xpad)
+  int64_t ldx = 0;
   int mst_o = 0;
   int tcG = 0;
   // tracing: event pairs around data-pass launches (kind 0 = pass 1, 1 = pass 2)
@@ -726,7 +735,6 @@ trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
   Extra* x = X_(h);
   const int KP = tc_kpad(sp.Kp);
   if (!KP) return set_err(h, TRD_ENOTIMPL, "BF16 path supports r_1 r_c <= 128");
-  if (sp.P_in % 4) return set_err(h, TRD_ENOTIMPL, "BF16 path needs the inner block size to be a multiple of 4");
   const View& v = h->view;
   const int64_t RB = (sp.P_stat + tc_bm() - 1) / tc_bm();
   const int64_t NT = (sp.P_strm + tc_bn() - 1) / tc_bn();
@@ -753,6 +761,22 @@ trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
   }
   x->W = W;
   x->mst_o = o;
+  if (sp.P_in % 4 == 0) {
+    x->Xtc = v.X;
+    x->ldx = sp.P_in;
+  } else {
+    const int64_t ld = (sp.P_in + 3) / 4 * 4;
+    if (x->xpad_src != v.X || x->xpad_gen != x->view_gen || x->xpad_Pin != sp.P_in || x->xpad_Pout != sp.P_out) {
+      TRY(ensure(h, x->Xpad, sizeof(float) * (size_t)(ld * sp.P_out)));
+      CK(launch_pad_rows(v.X, sp.P_in, sp.P_out, ld, (float*)x->Xpad.p, h->stream), "padded data rows");
+      x->xpad_src = v.X;
+      x->xpad_gen = x->view_gen;
+      x->xpad_Pin = sp.P_in;
+      x->xpad_Pout = sp.P_out;
+    }
+    x->Xtc = (const float*)x->Xpad.p;
+    x->ldx = ld;
+  }
   const int64_t ldT = (sp.P_strm + 63) / 64 * 64;
   x->ldT = ldT;
   TRY(tc_operands(h));
@@ -763,7 +787,7 @@ trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
   TRY(ensure(h, h->Tsum, sizeof(double) * (size_t)sp.P_stat * sp.Kp));
   prof_begin(h);
   CK(launch_pass_tc(sp.rows, false, (const __nv_bfloat16*)x->bShi.p, (const __nv_bfloat16*)x->bSlo.p, nullptr,
-                    (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p, v.X, sp.P_in, sp.P_out, (const uint32_t*)x->Mst[o].p, W, sp.P_stat, sp.P_strm, sp.Kp,
+                    (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p, x->Xtc, sp.P_in, x->ldx, sp.P_out, (const uint32_t*)x->Mst[o].p, W, sp.P_stat, sp.P_strm, sp.Kp,
                     h->scal + S_SIGMA, (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, G, full_stats,
                     h->stream),
      "tensor-core data pass 1");
@@ -812,7 +836,7 @@ trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
   prof_begin(h);
   CK(launch_pass_tc(sp.rows, true, (const __nv_bfloat16*)x->bShi.p, (const __nv_bfloat16*)x->bSlo.p,
                     (const __nv_bfloat16*)x->bSh.p, (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p,
-                    h->view.X, sp.P_in, sp.P_out,
+                    x->Xtc, sp.P_in, x->ldx, sp.P_out,
                     (const uint32_t*)x->Mst[x->mst_o].p, x->W, sp.P_stat, sp.P_strm, sp.Kp, h->scal + S_SIGMA,
                     (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, x->tcG, false, h->stream),
      "tensor-core data pass 2");
@@ -1507,6 +1531,7 @@ trd_status trd_set_data(trd_t* h, const float* X, const uint32_t* mask) {
   // path's in-place advances)
   X_(h)->probe_ready = false;
   X_(h)->mst_X[0] = X_(h)->mst_X[1] = nullptr;
+  X_(h)->xpad_src = nullptr;
   X_(h)->tagSst.valid = X_(h)->tagSstr.valid = X_(h)->tagBst.valid = X_(h)->tagBstr.valid = false;
   h->numel = 1;
   for (int m = 0; m < h->N; ++m) h->numel *= h->I[m];
@@ -1712,7 +1737,7 @@ trd_status trd_adaptive_sigma(trd_t* h, double sigma_prev, double* sigma_out) {
 trd_status trd_sigma_from_residuals(trd_t* h, const float* r, int64_t n, double rms, double sigma_prev,
                                     double* sigma_out) {
   TRY(check_handle(h));
-  if (!r || n < 1 || rms < 0 || !sigma_out) return set_err(h, TRD_EINVAL, "bad arguments");
+  if (!r || n < 1 || !(rms >= 0) || !sigma_out) return set_err(h, TRD_EINVAL, "bad arguments");
   TRY(ensure(h, h->probe_keys, sizeof(uint64_t) * n));
   TRY(ensure(h, h->probe_work, sizeof(double) * sigma_work_doubles()));
   TRY(ensure(h, X_(h)->probe_cand, sizeof(uint64_t) * n));

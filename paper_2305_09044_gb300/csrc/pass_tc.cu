@@ -801,6 +801,19 @@ __global__ void k_split_rows(const float* __restrict__ src, int64_t rows, int Kp
   }
 }
 
+// Rows of the data tensor re-laid with a padded stride: out[b][a] = X[b P_in + a] for
+// a < P_in, 0 for P_in <= a < ld (TMA needs row strides that are multiples of 16 bytes).
+__global__ void k_pad_rows(const float* __restrict__ X, int64_t P_in, int64_t P_out, int64_t ld,
+                           float* __restrict__ out) {
+  const int64_t n = P_out * ld;
+  const int step = gridDim.x * blockDim.x, e0 = blockIdx.x * blockDim.x + threadIdx.x;
+  RowCol rc(e0, step, (int)ld);
+  for (int64_t e = e0; e < n; e += step, rc.next()) {
+    const int64_t b = rc.r, a = rc.c;
+    out[e] = a < P_in ? X[b * P_in + a] : 0.f;
+  }
+}
+
 // Padded mask rows: Mrows[b][w] = bits [P_in b + 32 w, P_in b + 32 w + 32) of the packed mask
 // (bits at or beyond P_in are zero).
 __global__ void k_mask_rows(const uint32_t* __restrict__ M, int64_t P_in, int64_t P_out, int64_t W,
@@ -960,6 +973,13 @@ cudaError_t launch_tc_prep(const float* src, int64_t rows, int Kp, __nv_bfloat16
   return cudaGetLastError();
 }
 
+cudaError_t launch_pad_rows(const float* X, int64_t P_in, int64_t P_out, int64_t ld, float* out, cudaStream_t st) {
+  const int64_t n = P_out * ld;
+  tc::k_pad_rows<<<(unsigned)imin((n + 255) / 256, 8192), 256, 0, st>>>(X, P_in, P_out, ld, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mask_rows(const uint32_t* M, int64_t P_in, int64_t P_out, int64_t W, uint32_t* out,
                              cudaStream_t st) {
   const int64_t n = P_out * W;
@@ -989,12 +1009,13 @@ cudaError_t launch_reduce_slots(const float* part, int64_t RB, int64_t NT, int G
 // [P_strm][KPAD] (hi, lo); X: [P_out][P_in] floats; Mst: [P_stat][W] mask words.
 cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi, const __nv_bfloat16* S_lo,
                            const __nv_bfloat16* S_h, const __nv_bfloat16* T_hi, const __nv_bfloat16* T_lo,
-                           const float* X, int64_t P_in, int64_t P_out, const uint32_t* Mst, int64_t W,
+                           const float* X, int64_t P_in, int64_t ldx, int64_t P_out, const uint32_t* Mst, int64_t W,
                            int64_t P_stat, int64_t P_strm, int Kp, const double* sigma, float* Tpart,
                            double* stat_part, int* err, int G, bool full_stats, cudaStream_t st) {
   using namespace tc;
   const int KPAD = tc_kpad(Kp);
-  if (!KPAD || (P_in % 4) != 0) return cudaErrorInvalidValue;
+  // TMA row strides must be multiples of 16 bytes: callers pass X re-laid with ldx % 4 == 0
+  if (!KPAD || (ldx % 4) != 0 || ldx < P_in || ((uintptr_t)X & 15)) return cudaErrorInvalidValue;
   CUtensorMap mS_hi, mS_lo, mS_h, mT_hi, mT_lo, mX;
   const CUtensorMapDataType BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const CUtensorMapSwizzle SW = CU_TENSOR_MAP_SWIZZLE_128B;
@@ -1005,10 +1026,10 @@ cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi
             make_map(&mT_hi, BF, 2, T_hi, KPAD, P_strm, KPAD * 2, 64, BN, SW) &&
             make_map(&mT_lo, BF, 2, T_lo, KPAD, P_strm, KPAD * 2, 64, BN, SW);
   if (rows_case)
-    ok = ok && make_map(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, P_in, P_out, P_in * 4, BM, BN,
+    ok = ok && make_map(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, P_in, P_out, ldx * 4, BM, BN,
                         CU_TENSOR_MAP_SWIZZLE_NONE);
   else
-    ok = ok && make_map(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, P_in, P_out, P_in * 4, 32, BM, SW);
+    ok = ok && make_map(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, P_in, P_out, ldx * 4, 32, BM, SW);
   if (!ok) return cudaErrorInvalidValue;
   Params p;
   p.P_in = P_in;

@@ -253,9 +253,10 @@ cudaError_t launch_reduce_slots(const float* part, int64_t RB, int64_t NT, int G
                                 double* out, cudaStream_t st);
 cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi, const __nv_bfloat16* S_lo,
                            const __nv_bfloat16* S_h, const __nv_bfloat16* T_hi, const __nv_bfloat16* T_lo,
-                           const float* X, int64_t P_in, int64_t P_out, const uint32_t* Mst, int64_t W,
+                           const float* X, int64_t P_in, int64_t ldx, int64_t P_out, const uint32_t* Mst, int64_t W,
                            int64_t P_stat, int64_t P_strm, int Kp, const double* sigma, float* Tpart,
                            double* stat_part, int* err, int G, bool full_stats, cudaStream_t st);
+cudaError_t launch_pad_rows(const float* X, int64_t P_in, int64_t P_out, int64_t ld, float* out, cudaStream_t st);
 
 // fgmc_solve.cu
 cudaError_t launch_fgmc_E(const double* Z, const int32_t* idx, int64_t n, int rk, int rk1,

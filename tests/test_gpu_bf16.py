@@ -1,9 +1,9 @@
 """Parity of the tensor-core (tcgen05, BF16) data passes with the FP64 oracle (needs a GB300).
 
 Tolerance: 5e-3 relative (Frobenius) per step for d, eta and the core change.  Shapes keep
-r_1 r_c <= 128 (contraction padded to 64 or 128) and an inner block size that is a multiple
-of 4 (the path's limits) while leaving every tile ragged (no size is a multiple of the
-128 x 64 tile).
+r_1 r_c <= 128 (contraction padded to 64 or 128) while leaving every tile ragged (no size is
+a multiple of the 128 x 64 tile); inner block sizes that are not multiples of 4 take the
+re-laid data rows.
 """
 import math
 
@@ -25,6 +25,8 @@ SHAPES = [
     ((20, 16, 12, 10, 9), (2, 3, 2, 2, 3)), # order 5: 320 x 1080
     ((24, 20, 18, 16), (10, 10, 10, 10)),   # K' = 100 (padded to 128), K = 100
     ((32, 28, 20, 12), (8, 8, 16, 8)),      # K' = 128, K = 64 / 128
+    ((23, 17, 9, 13), (2, 3, 4, 3)),        # odd inner block 391: data rows re-laid with stride 392
+    ((30, 26, 22), (3, 2, 3)),              # inner block 30 (order 3)
 ]
 
 

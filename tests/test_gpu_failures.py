@@ -133,3 +133,14 @@ def test_device_wait_gives_up_with_status(torch_cuda):
     assert t.wait_selftest(False, 0) == binding.TRD_EINVAL
     assert t.wait_selftest(True, 1 << 10) == binding.TRD_OK
     _update_matches_oracle(t, X, P, O.init_cores(DIMS, RANKS, seed=8), 2, TOL["bf16"])
+
+
+def test_width_rejects_nan_floor(torch_cuda):
+    """A NaN rms of the observed data (the floor of the adaptive width) is rejected with
+    TRD_EINVAL by the handle path, as by the allocation-free form; the handle stays usable."""
+    from paper_2305_09044_gb300 import TRD, TrdError
+    t = TRD((4, 4, 4), (1, 1, 1), "fp32")
+    rd = torch_cuda.ones(100, dtype=torch_cuda.float32, device="cuda")
+    with pytest.raises(TrdError):
+        t.sigma_from_residuals(rd, float("nan"), -1.0)
+    assert t.sigma_from_residuals(rd, 1.0, -1.0) > 0

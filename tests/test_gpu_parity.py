@@ -59,16 +59,16 @@ def test_core_step_parity_full(torch_cuda, prec, dims, ranks):
         st = O.core_update(X, P, cores, k, sigma, lam=-1e-10)
         s = t.residual_weights(k, sigma)
         assert s["n_obs"] == st.n_obs and s["n_slots"] == X.size
-        assert abs(s["sum_w"] - st.sum_w) <= TOL[prec] * st.sum_w * 10
-        assert abs(s["sum_we2"] - 2 * st.objective) <= TOL[prec] * 2 * st.objective * 10
+        assert abs(s["sum_w"] - st.sum_w) <= TOL[prec] * st.sum_w
+        assert abs(s["sum_we2"] - 2 * st.objective) <= TOL[prec] * 2 * st.objective
         d = t.core_gradient(k)
         assert rel(d, st.d) <= TOL[prec], (k, rel(d, st.d))
         G = t.fgmc_gram(k)
         assert rel(G, st.G) <= 1e-12
         eta = t.core_update(k, -1e-10)
-        assert abs(eta - st.eta) <= TOL[prec] * 10 * abs(st.eta), (eta, st.eta)
+        assert abs(eta - st.eta) <= TOL[prec] * abs(st.eta), (eta, st.eta)
         Znew = t.get_core(k)
-        assert rel(Znew - cores[k], st.cores[k] - cores[k]) <= TOL[prec] * 10
+        assert rel(Znew - cores[k], st.cores[k] - cores[k]) <= TOL[prec]
         cores = st.cores
 
 
@@ -93,17 +93,20 @@ def test_core_step_parity_sketched(torch_cuda, prec, dims, ranks, s):
         d = t.core_gradient(k)
         assert rel(d, st.d) <= TOL[prec], (k, rel(d, st.d))
         eta = t.core_update(k, -1e-10)
-        assert abs(eta - st.eta) <= TOL[prec] * 10 * abs(st.eta)
+        assert abs(eta - st.eta) <= TOL[prec] * abs(st.eta)
         assert rel(t.get_core(k), st.cores[k]) <= TOL[prec]
+        assert rel(t.get_core(k) - cores[k], st.cores[k] - cores[k]) <= TOL[prec]
         cores = st.cores
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 @pytest.mark.parametrize("gram", ["local", "none"])
-def test_ablation_variants(torch_cuda, gram):
+def test_ablation_variants(torch_cuda, gram, prec):
     """Ablations of Sec. 5.1: 'local scaled term' (Gram of the sampled cores) and
-    'gradient descent' (h = d) on a sketch."""
-    dims, ranks, s = (30, 26, 22), (3, 2, 3), 9
-    t, X, P, Xt, keep = _make(torch_cuda, dims, ranks, "fp64", seed=9)
+    'gradient descent' (h = d) on a sketch, on every precision of the data passes."""
+    dims, ranks, s = (30, 26, 24), (3, 2, 3), 12
+    tol = {"fp64": 1e-10, "fp32": 1e-5, "bf16": 5e-3}[prec]
+    t, X, P, Xt, keep = _make(torch_cuda, dims, ranks, prec, seed=9)
     cores = O.init_cores(dims, ranks, seed=13)
     for k in range(3):
         t.set_cores(cores)
@@ -113,8 +116,8 @@ def test_ablation_variants(torch_cuda, gram):
         t.residual_weights(k, 1.0)
         t.core_gradient(k)
         eta = t.core_update(k, -1e-10, gram=gram)
-        assert abs(eta - st.eta) <= 1e-9 * abs(st.eta)
-        assert rel(t.get_core(k), st.cores[k]) <= 1e-10
+        assert abs(eta - st.eta) <= tol * abs(st.eta), (k, eta, st.eta)
+        assert rel(t.get_core(k) - cores[k], st.cores[k] - cores[k]) <= tol
         cores = st.cores
 
 
@@ -232,7 +235,7 @@ def test_trajectory_sketched_fp32(torch_cuda):
         cores, e, D, steps = O.sawrtrd_iteration(X, P, cores, 1.5, it, sizes=sizes, seed=31, D_prev=D)
         r = t.step(sketch=[12] * 4, sigma=1.5, seed=31)
         for k in range(4):
-            assert abs(r["eta"][k] - steps[k].eta) <= 1e-4 * abs(steps[k].eta)
+            assert abs(r["eta"][k] - steps[k].eta) <= 1e-5 * abs(steps[k].eta), (it, k)
     assert rel(O.reconstruct(t.get_cores()), O.reconstruct(cores)) <= 1e-4
 
 
@@ -259,8 +262,8 @@ def test_scaled_step_large_gram(torch_cuda, prec, dims, ranks):
         assert rel(d, st.d) <= TOL[prec]
         assert rel(t.fgmc_gram(k), st.G) <= 1e-12
         eta = t.core_update(k, -1e-10)
-        assert abs(eta - st.eta) <= TOL[prec] * 10 * abs(st.eta), (k, eta, st.eta)
-        assert rel(t.get_core(k) - cores[k], st.cores[k] - cores[k]) <= TOL[prec] * 10
+        assert abs(eta - st.eta) <= TOL[prec] * abs(st.eta), (k, eta, st.eta)
+        assert rel(t.get_core(k) - cores[k], st.cores[k] - cores[k]) <= TOL[prec]
         cores = st.cores
 
 

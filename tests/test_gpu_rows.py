@@ -47,8 +47,8 @@ def test_row_sampled_step_parity(torch_cuda, prec, dims, ranks, J):
         d = t.core_gradient(k)
         assert rel(d, st.d) <= tol, (k, rel(d, st.d))
         eta = t.core_update(k, -1e-10)
-        assert abs(eta - st.eta) <= tol * 10 * abs(st.eta), (k, eta, st.eta)
-        assert rel(t.get_core(k) - cores[k], st.cores[k] - cores[k]) <= tol * 10
+        assert abs(eta - st.eta) <= tol * abs(st.eta), (k, eta, st.eta)
+        assert rel(t.get_core(k) - cores[k], st.cores[k] - cores[k]) <= tol
         cores = st.cores
 
 

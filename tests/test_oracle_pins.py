@@ -343,6 +343,93 @@ def test_exact_line_search_is_minimiser():
         cores = st.cores
 
 
+# ---------------------------------------------------------------- ablation variants (Sec. 5.1)
+
+def _sketch_problem(seed):
+    dims, ranks = (6, 5, 7, 4), (2, 3, 2, 2)
+    rng = np.random.default_rng(seed)
+    cores = _rand_cores(rng, dims, ranks, 0.9)
+    X = O.reconstruct(_rand_cores(rng, dims, ranks, 0.9)) + 0.2 * rng.standard_normal(dims)
+    P = (rng.random(dims) < 0.7).astype(float)
+    return dims, ranks, cores, X, P, rng
+
+
+def test_local_gram_with_full_sketch_is_global_step():
+    """'Local scaled term' ablation: with a sketch that keeps every index of every mode the
+    sampled subchain is the whole Z^{!=k}_[2], so its Gram is the FGMC Gram of Prop. 2 and the
+    whole step (G, h, eta, new core) is the paper's global step."""
+    dims, ranks, cores, X, P, rng = _sketch_problem(41)
+    for k in range(4):
+        full = [None if m == k else np.arange(dims[m]) for m in range(4)]
+        loc = O.core_update(X, P, cores, k, 1.1, lam=-1e-10, sample=full, gram="local")
+        glo = O.core_update(X, P, cores, k, 1.1, lam=-1e-10)
+        assert np.linalg.norm(loc.G - glo.G) <= 1e-12 * np.linalg.norm(glo.G)
+        assert np.linalg.norm(loc.h - glo.h) <= 1e-10 * np.linalg.norm(glo.h)
+        assert abs(loc.eta - glo.eta) <= 1e-10 * abs(glo.eta)
+        assert np.linalg.norm(loc.cores[k] - glo.cores[k]) <= 1e-10 * np.linalg.norm(glo.cores[k])
+        cores = glo.cores
+
+
+def test_local_gram_is_bruteforce_gram_of_sampled_subchain():
+    """On a real sketch the local Gram is sum_j b_j b_j^T over the SAMPLED slices only: b_j
+    from the Thm. 1 slice product of the sampled cores by plain loops (a Gram formed from the
+    full cores, or with the wrong column order, fails), and h solves h (G + lambda I) = d."""
+    dims, ranks, cores, X, P, rng = _sketch_problem(42)
+    for k in range(4):
+        idx = [None if m == k else np.sort(rng.choice(dims[m], size=3, replace=False)) for m in range(4)]
+        st = O.core_update(X, P, cores, k, 0.9, lam=-1e-10, sample=idx, gram="local")
+        rk, rk1 = ranks[k], ranks[(k + 1) % 4]
+        K = rk * rk1
+        G = np.zeros((K, K))
+        others = [m for m in range(4) if m != k]
+        for pick in itertools.product(*[list(idx[m]) for m in others]):
+            full_idx = [0] * 4
+            for m, i in zip(others, pick):
+                full_idx[m] = int(i)
+            S = _subchain_slice_py(cores, k, full_idx)         # r_{k+1} x r_k
+            b = np.array([S[bb, a] for bb in range(rk1) for a in range(rk)])
+            G += np.outer(b, b)
+        assert np.linalg.norm(st.G - G) <= 1e-12 * np.linalg.norm(G)
+        assert np.linalg.norm(st.G - O.fgmc_gram(cores, k)) > 1e-3 * np.linalg.norm(G)
+        lam = 1e-10 * np.trace(G) / K
+        assert np.linalg.norm(st.h @ (G + lam * np.eye(K)) - st.d) <= 1e-10 * np.linalg.norm(st.d)
+        cores = st.cores
+
+
+@pytest.mark.parametrize("sketched", [False, True])
+def test_gradient_descent_ablation_exact_step(sketched):
+    """'Gradient descent' ablation: h = d, and eta is the exact minimiser of the weighted
+    objective along d with W held fixed (Sec. 3.2 exact line search).  The objective is a
+    parabola in eta, so its vertex from three evaluations of the loss at eta = 0, 1, 2
+    (reconstructed from the cores, independent of the step's own products) must equal eta."""
+    dims, ranks, cores, X, P, rng = _sketch_problem(43)
+    sigma = 0.8
+    for k in range(4):
+        if sketched:
+            idx = [np.arange(dims[m]) if m == k else np.sort(rng.choice(dims[m], size=3, replace=False))
+                   for m in range(4)]
+            XI, PI = X[np.ix_(*idx)], P[np.ix_(*idx)]
+            sample = [None if m == k else idx[m] for m in range(4)]
+        else:
+            idx = [np.arange(d) for d in dims]
+            XI, PI, sample = X, P, None
+        st = O.core_update(X, P, cores, k, sigma, sample=sample, gram="none")
+        assert st.G is None and np.array_equal(st.h, st.d)
+        sampled = [cores[m][:, idx[m], :] for m in range(4)]
+        W = O.hq_weight(XI - O.reconstruct(sampled), sigma)
+
+        def f(eta):
+            cs = list(sampled)
+            cs[k] = O.fold2(O.mode2(cores[k]) + eta * st.d, ranks[k], ranks[(k + 1) % 4])
+            return _half_sq_loss(XI, PI, W, cs)
+
+        f0, f1, f2 = f(0.0), f(1.0), f(2.0)
+        vertex = (3 * f0 - 4 * f1 + f2) / (2 * (f0 - 2 * f1 + f2))
+        assert abs(st.eta - vertex) <= 1e-8 * abs(vertex)
+        assert f(st.eta) <= f0
+        cores = st.cores
+
+
 def test_stop_matrix_is_gram_of_unfolding():
     dims, ranks = (3, 4, 5), (2, 3, 2)
     rng = np.random.default_rng(11)

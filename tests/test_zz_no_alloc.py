@@ -2,9 +2,10 @@
 kernel width as the handle-based trd_sigma_from_residuals, twice in a row on the same
 inputs, while the fixed device array it works in is shared between calls.
 
-Callers of the allocation-free entry point cannot allocate device memory themselves (code
-inside a CUDA-graph capture, hosts that own all device memory through their own
-allocator), which is why the entry point takes no handle.  This file is collected last so a
+Callers of the allocation-free entry point cannot allocate device memory themselves (hosts
+that own all device memory through their own allocator, fixed device-memory budgets, loops
+that cannot take cudaMalloc's implicit synchronisation), which is why the entry point takes
+no handle.  This file is collected last so a
 run that stops at the first failure has already run every other test."""
 import ctypes as C
 
@@ -58,3 +59,5 @@ def test_noalloc_rejects_oversize_and_bad_arguments(env):
     assert lib.trd_sigma_from_residuals_noalloc(C.c_void_p(rd.data_ptr()), 0, 1.0, -1.0,
                                                 C.c_void_p(out.data_ptr()), s) == 1
     assert lib.trd_sigma_from_residuals_noalloc(None, 16, 1.0, -1.0, C.c_void_p(out.data_ptr()), s) == 1
+    assert lib.trd_sigma_from_residuals_noalloc(C.c_void_p(rd.data_ptr()), 16, float("nan"), -1.0,
+                                                C.c_void_p(out.data_ptr()), s) == 1
