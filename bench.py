@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=None, choices=[None, "bf16", "fp32", "fp64"])
+    ap.add_argument("--precision", default=None, choices=[None, "bf16", "tf32x3", "fp32", "fp64"])
     ap.add_argument("--no-converge", action="store_true")
     ap.add_argument("--no-image", action="store_true", help="skip the image-shaped PSNR runs")
     ap.add_argument("--image-only", action="store_true",
@@ -53,6 +53,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the row-sampling variant's measurement")
     ap.add_argument("--converge-iters", type=int, default=60)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other north-star configurations (30^3, 64^5, 1024x1024x256, sampled 128^4)")
+    ap.add_argument("--configs-only", action="store_true",
+                    help="run only the other configurations and print them as one JSON line")
+    ap.add_argument("--cpu-budget", type=float, default=3.0,
+                    help="seconds of oracle work per configuration and thread setting (0: skip)")
+    ap.add_argument("--oracle-probe", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-budget", type=float, default=3.0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -208,25 +216,38 @@ def recorded_traffic(prec):
     return None
 
 
-def roofline(prec, prof, w):
+def roofline(prec, prof, w, measured=None):
     pk, src = peaks()
     Kp = w.ranks[0] * w.ranks[len(w.dims) // 2]
     n_slots = int(np.prod(w.dims))
     launches_pass = prof["pass1_n"] + prof["pass2_n"]
     pass_ms = (prof["pass1_ms"] + prof["pass2_ms"]) / max(launches_pass, 1)
     hbm_bytes = n_slots * (4 + 1 / 8)                   # x (FP32) + mask bit per slot
-    if prec == "bf16":
+    if prec in ("bf16", "tf32x3"):
         achieved = hbm_bytes / (pass_ms / 1e3) / 1e9
-        roof = {"kernel": "k_pass_tc (fused tcgen05 data pass, passes 1+2)", "bound": "hbm",
+        kname = ("k_pass_tc (fused tcgen05 data pass, passes 1+2)" if prec == "bf16" else
+                 "k_pass_tc TF32 (fused tcgen05 data pass, 3-term TF32 products, passes 1+2)")
+        roof = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": None,
                 "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback"}
+        if prec == "tf32x3" and measured and measured.get("tf32_tflops"):
+            # executed tensor work: 3 product terms of 2 K' flops in each of the two GEMMs per slot
+            fl = n_slots * 3 * 4 * Kp
+            roof["tensor_tflops_executed"] = fl / (pass_ms / 1e3) / 1e12
+            roof["tensor_peak_tf32_measured"] = measured["tf32_tflops"]
+            roof["tensor_frac_executed"] = roof["tensor_tflops_executed"] / measured["tf32_tflops"]
     else:
         algo = n_slots * 4 * Kp                         # 2 Kp recon + 2 Kp contraction per slot
         sm = pk.get("sm_max_mhz", 2070.0)
-        if prec == "fp32":
+        if prec == "fp32" and measured and measured.get("fp32_simt_tflops"):
+            peak = measured["fp32_simt_tflops"]
+            psrc = "measured in this run: cuBLAS FP32 GEMM with TF32 off (" + measured["how"] + ")"
+        elif prec == "fp32":
             peak = 152 * 128 * 2 * sm * 1e6 / 1e12
             psrc = f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm:.0f} MHz"
+        elif measured and measured.get("fp64_tflops"):
+            peak, psrc = measured["fp64_tflops"], "measured in this run: cuBLAS FP64 GEMM"
         else:
             peak, psrc = 1.25, "nominal GB300 FP64 rate"
         achieved = algo / (pass_ms / 1e3) / 1e12
@@ -254,7 +275,8 @@ def run_ours(args, rank, world, local):
     import __graft_entry__
     __graft_entry__.build()
     torch.cuda.set_device(local)
-    precs = [args.precision] if args.precision else ["bf16", "fp32"]
+    precs = [args.precision] if args.precision else ["bf16", "tf32x3", "fp32"]
+    measured = measure_peaks(torch) if rank == 0 else None
     w = replica_workload(synth.WORKLOADS[WORKLOAD], rank, world)
     t, Xt, host, dev, corr = build_problem(w, torch, precs[0])
     slots_per_step = len(w.dims) * int(np.prod(w.dims))
@@ -320,7 +342,9 @@ def run_ours(args, rank, world, local):
            "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[prec],
            "data": "synthetic", "config": workload_config(w, prec), "iters_per_s": 1e3 / ms_step,
-           "roofline": roofline(prec, prof, w), "e2e": e2e, "gpu_launches": launches, "clocks": ck}
+           "roofline": roofline(prec, prof, w, measured), "e2e": e2e, "gpu_launches": launches, "clocks": ck}
+    if measured:
+        out["peaks_measured_here"] = measured
     if rank == 0 and not args.no_converge:
         out["time_to_rel_err_1e-3"] = converge(t, Xt, w, args.converge_iters, torch)
     if not args.no_rows:
@@ -337,16 +361,37 @@ def run_ours(args, rank, world, local):
         ms2, prof2, launches2, ck2 = timed_steps(t2, steps2, 3, world, local, torch, kernel_launches)
         cmp_ = {"value": job_throughput(world, slots_per_step, steps2, ms2), "unit": UNIT, "steps": steps2,
                 "ms_per_step": ms2 / steps2, "iters_per_s": 1e3 * steps2 / ms2,
-                "roofline": roofline(other, prof2, w), "gpu_launches": launches2, "clocks": ck2}
+                "roofline": roofline(other, prof2, w, measured), "gpu_launches": launches2, "clocks": ck2}
         if rank == 0 and not args.no_converge:
             cmp_["time_to_rel_err_1e-3"] = converge(t2, Xt, w, args.converge_iters, torch)
         out[other] = cmp_
         t2.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, corr, budget_s=15.0)
+        if args.cpu_budget > 0:
+            out["cpu_baseline"]["threads"] = {"one_thread": oracle_probe("subtensor", WORKLOAD, 1, args.cpu_budget),
+                                              "all_cores": oracle_probe("subtensor", WORKLOAD, os.cpu_count() or 1,
+                                                                        args.cpu_budget)}
     t.close()
+    del host, dev, Xt
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_configs:
+        out["configs"] = other_configs(args, torch, measured)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def other_configs(args, torch, measured):
+    """The other spec configurations on this GPU (each with its own roofline and CPU
+    baseline): 30^3 FP64 trajectory, 64^5 and 1024 x 1024 x 256 RStS iterations, sampled
+    128^4 forward + backward."""
+    pk, _ = peaks()
+    budget = 0.0 if args.no_cpu_baseline else args.cpu_budget
+    res = {"tiny3": run_tiny(torch, pk, budget)}
+    res["cfg64"] = run_sketched(torch, pk, "cfg64", ["bf16"], 10, budget, conv_iters=60, conv_budget=6.0)
+    res["video"] = run_sketched(torch, pk, "video", ["bf16", "fp32"], 10, budget, conv_iters=60, conv_budget=6.0)
+    res["grad128"] = run_sampled(torch, pk, 5, budget)
+    return res
 
 
 def row_sampling(t, w, torch, J=1 << 16, updates=8):
@@ -443,6 +488,399 @@ def converge(t, Xt, w, iters, torch):
         if err <= 1e-3:
             return {"reached": True, "iters": it + 1, "seconds": total / 1e3, "rel_err": err}
     return {"reached": False, "iters": iters, "seconds": total / 1e3, "rel_err": err}
+
+
+# ----------------------------------------------------------------------------- other configurations
+def measure_peaks(torch):
+    """Denominators that MEASURED_PEAKS.json does not hold, measured here the same way (a
+    library GEMM, best of five CUDA-event timed runs after two warm-ups): FP64, FP32 on the CUDA
+    cores (TF32 off) and TF32.  Only the denominators come from library code."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dtype, n, tf32 in (("fp64_tflops", torch.float64, 4096, False),
+                                     ("fp32_simt_tflops", torch.float32, 8192, False),
+                                     ("tf32_tflops", torch.float32, 8192, True)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device="cuda", dtype=dtype)
+            b = torch.randn(n, n, device="cuda", dtype=dtype)
+            for _ in range(2):
+                torch.matmul(a, b)
+            best = math.inf
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            out[name] = 2.0 * n ** 3 / best / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    out["how"] = ("torch.matmul (cuBLAS) n^3 GEMM, 2 n^3 flops, best of 5: FP64 n = 4096, FP32 with TF32 "
+                  "off and TF32 n = 8192; on this run's GPU")
+    return out
+
+
+def device_problem(w, torch, prec, chunk=1 << 26):
+    """Seeded synthetic tensor built on the device, for the ~1e9-entry workloads: X_true =
+    R(Z_true) by the library's reconstruction kernel (cores from the workload generator), then
+    the workload's corruption drawn chunk by chunk by torch's seeded device generator (same
+    distributions as the host recipe: Bernoulli mask, outliers U[-10 std, 10 std] on observed
+    entries or salt-and-pepper at the clean tensor's max / min, additive Gaussian noise), and
+    the mask bit-packed on the device."""
+    from paper_2305_09044_gb300 import TRD, synth
+    truth = synth.gaussian_cores(w.dims, w.ranks, w.data_seed, w.smooth_modes, w.smooth_width)
+    t = TRD(w.dims, w.ranks, prec)
+    Xt = t.reconstruct_from(truth)
+    n = Xt.numel()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(w.data_seed)
+    std = float(Xt.std())
+    lo, hi = float(Xt.min()), float(Xt.max())
+    X = torch.empty_like(Xt)
+    words = ((n + 31) // 32 + 3) // 4 * 4
+    M = torch.zeros(words, dtype=torch.int32, device="cuda")
+    shifts = torch.arange(32, device="cuda", dtype=torch.int64)
+    for s in range(0, n, chunk):
+        c = min(chunk, n - s)
+        m = torch.rand(c, generator=g, device="cuda") < (1.0 - w.missing)
+        out = torch.rand(c, generator=g, device="cuda") < w.outlier_frac
+        u = torch.rand(c, generator=g, device="cuda") * 2.0 - 1.0
+        x = Xt[s:s + c]
+        if w.noise_var > 0:
+            x = x + math.sqrt(w.noise_var) * torch.randn(c, generator=g, device="cuda")
+        if w.outlier_kind == "saltpepper":
+            x = torch.where(out, torch.where(u > 0, torch.full_like(x, hi), torch.full_like(x, lo)), x)
+        else:
+            x = torch.where(out & m, 10.0 * std * u, x)
+        X[s:s + c] = x
+        pad = (-c) % 32
+        mb = torch.nn.functional.pad(m, (0, pad)).view(-1, 32).to(torch.int64)
+        packed = ((mb << shifts).sum(dim=1) & 0xFFFFFFFF)
+        packed = torch.where(packed >= 2 ** 31, packed - 2 ** 32, packed).to(torch.int32)
+        M[s // 32: s // 32 + packed.numel()] = packed
+        del m, out, u, x, mb, packed
+    t.set_data(X, M)
+    return t, Xt, X, M
+
+
+def oracle_probe(kind, name, threads, budget_s):
+    """Time the FP64 oracle on a bounded sample of workload `name` in a child process limited
+    to `threads` BLAS/OpenMP threads (the thread count of numpy's BLAS is fixed at its import).
+    Returns the child's JSON result."""
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[var] = str(threads)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-probe", f"{kind}:{name}",
+                        "--oracle-budget", str(budget_s)], env=env, capture_output=True, text=True,
+                       timeout=600)
+    for line in r.stdout.splitlines()[::-1]:
+        if line.startswith("{"):
+            res = json.loads(line)
+            res["threads"] = threads
+            return res
+    return {"error": (r.stderr or r.stdout)[-300:], "threads": threads}
+
+
+def oracle_probe_main(spec, budget_s):
+    """Child side of oracle_probe: one bounded sample of the named workload."""
+    from oracle import trd_oracle as O
+    from paper_2305_09044_gb300 import synth
+    kind, name = spec.split(":")
+    w = synth.WORKLOADS[name]
+    t0 = time.perf_counter()
+    if kind == "trajectory":
+        # the 30^3 workload: full oracle iterations (Algorithm 1) with the adaptive width
+        truth = synth.gaussian_cores(w.dims, w.ranks, w.data_seed)
+        Xt = O.reconstruct_unfold(truth)
+        c = synth.draw_corruption(w)
+        X = synth.assemble(Xt, c).astype(np.float32).astype(np.float64)
+        P = c.mask.astype(np.float64)
+        cores = O.init_cores(w.dims, w.ranks, seed=w.init_seed)
+        obs = P > 0
+        rms = float(np.sqrt(np.mean(X[obs] ** 2)))
+        D, sigma, its = O.D_matrix(cores), None, 0
+        t0 = time.perf_counter()
+        while its < 100 and (its == 0 or time.perf_counter() - t0 < budget_s):
+            sigma = O.adaptive_sigma((X - O.reconstruct(cores))[obs], rms, sigma)
+            cores, e, D, steps = O.sawrtrd_iteration(X, P, cores, sigma, its, D_prev=D)
+            its += 1
+        dt = time.perf_counter() - t0
+        print(json.dumps({"unit": "iterations/s", "value": its / dt, "iters": its, "seconds": dt,
+                          "sample": f"{its} oracle iterations of Algorithm 1 on the full 30^3 workload"}))
+        return
+    if kind == "sketch":
+        # one RStS core update per sample on a synthetic tensor of the workload's sketch shape
+        # (the gathered sketch itself: dims I_k x s^(N-1)), repeated within the budget
+        N = len(w.dims)
+        rng = np.random.default_rng(w.data_seed)
+        k = 1
+        sdims = [w.dims[m] if m == k else min(w.sketch, w.dims[m]) for m in range(N)]
+        cores = O.init_cores(sdims, w.ranks, seed=w.init_seed)
+        X = O.reconstruct_unfold([c * 1.01 for c in cores]) + 0.01 * rng.standard_normal(sdims)
+        P = (rng.random(sdims) < 1.0 - w.missing).astype(np.float64)
+        slots = int(np.prod(sdims))
+        done = 0
+        t0 = time.perf_counter()
+        while done == 0 or time.perf_counter() - t0 < budget_s:
+            O.core_update(X, P, cores, k, 2.0)
+            done += 1
+        dt = time.perf_counter() - t0
+        print(json.dumps({"unit": UNIT, "value": done * slots / dt, "updates": done, "seconds": dt,
+                          "sample": f"{done} oracle core updates (k = {k + 1}) on a {'x'.join(map(str, sdims))} "
+                                    f"sketch-shaped tensor (TR ranks {w.ranks[0]})"}))
+        return
+    if kind == "sampled":
+        # the sampled loss and its gradient at a subset of the workload's entries
+        Msub = 1 << 14
+        cores = O.init_cores(w.dims, w.ranks, seed=w.init_seed)
+        rng = np.random.default_rng(w.sample_seed)
+        idx = np.stack([rng.integers(0, d, Msub) for d in w.dims], axis=1)
+        x = rng.standard_normal(Msub)
+        done = 0
+        t0 = time.perf_counter()
+        while done == 0 or time.perf_counter() - t0 < budget_s:
+            O.sampled_loss_grad_vec(cores, idx, x, 1.0)
+            done += 1
+        dt = time.perf_counter() - t0
+        print(json.dumps({"unit": "sampled entries/s (fwd+bwd)", "value": done * Msub / dt, "evals": done,
+                          "seconds": dt, "sample": f"{done} oracle loss+gradient evaluations at {Msub} sampled "
+                                                    f"entries of the {'x'.join(map(str, w.dims))} rank-{w.ranks[0]} model"}))
+        return
+    if kind == "subtensor":
+        X, P, cores, sigma, sub = oracle_sample(w, None)
+        slots = int(np.prod(sub))
+        done, k = 0, 0
+        t0 = time.perf_counter()
+        while done == 0 or time.perf_counter() - t0 < budget_s:
+            cores = O.core_update(X, P, cores, k % len(sub), sigma).cores
+            done += 1
+            k += 1
+        dt = time.perf_counter() - t0
+        print(json.dumps({"unit": UNIT, "value": done * slots / dt, "updates": done, "seconds": dt,
+                          "sample": f"{done} oracle core updates on the {'x'.join(map(str, sub))} sub-tensor"}))
+        return
+    raise ValueError(kind)
+
+
+def cpu_pair(kind, name, budget_s):
+    """The oracle at 1 thread and at every host core."""
+    ncores = os.cpu_count() or 1
+    one = oracle_probe(kind, name, 1, budget_s)
+    allc = oracle_probe(kind, name, ncores, budget_s)
+    return {"kind": "oracle", "cores": ncores, "one_thread": one, "all_cores": allc}
+
+
+def timed_device_steps(t, steps, warmup, torch, step_kw):
+    """CUDA-event time of `steps` trd_step calls after `warmup` (tracing off), then a few
+    untimed steps traced at every phase for the breakdown; returns ms per step and phases."""
+    from paper_2305_09044_gb300.binding import kernel_launches
+    for _ in range(warmup):
+        t.step(**step_kw)
+    torch.cuda.synchronize()
+    l0 = kernel_launches()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(t.stream)
+    for _ in range(steps):
+        t.step(**step_kw)
+    b.record(t.stream)
+    torch.cuda.synchronize()
+    launches = (kernel_launches() - l0) / steps
+    ms = a.elapsed_time(b) / steps
+    t.set_profiling(2)
+    t.get_profile(reset=True)
+    for _ in range(2):
+        t.step(**step_kw)
+    ph = t.get_profile(reset=True)
+    t.set_profiling(False)
+    return ms, ph, launches
+
+
+def converge_steps(t, Xt, step_kw, max_iters, budget_s, torch):
+    """Device time from a fresh initialisation until ||R(Z) - X_true|| / ||X_true|| <= 1e-3
+    (evaluated outside the timed steps), at most max_iters iterations or budget_s of device time."""
+    stream = t.stream
+    total, err, it = 0.0, t.recovery_error(Xt), 0
+    while it < max_iters and total < budget_s * 1e3:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        t.step(**step_kw)
+        b.record(stream)
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b)
+        it += 1
+        err = t.recovery_error(Xt)
+        if err <= 1e-3:
+            return {"reached": True, "iters": it, "seconds": total / 1e3, "rel_err": err}
+    return {"reached": False, "iters": it, "seconds": total / 1e3, "rel_err": err}
+
+
+def phase_summary(ph, steps=2):
+    return {k[:-3]: round(v / steps, 4) for k, v in ph.items() if k.endswith("_ms") and v > 0}
+
+
+def pass_roofline(ph, slots_per_pass, pk, label, steps=2, Kp=None, tf32_peak=None):
+    """Fused data passes of the traced steps: algorithmic bytes (x and the mask bit per slot)
+    over the average pass time, against the measured HBM copy bandwidth; for the TF32 passes
+    also the executed tensor flops (3 product terms) against the measured TF32 peak."""
+    n = ph.get("pass1_n", 0) + ph.get("pass2_n", 0)
+    if n == 0:
+        return None
+    ms = (ph["pass1_ms"] + ph["pass2_ms"]) / n
+    byt = slots_per_pass * (4 + 1 / 8)
+    gbs = byt / (ms / 1e3) / 1e9
+    r = {"kernel": label, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+         "frac": gbs / pk["hbm_gbs"], "ms_per_launch": ms, "launches": n, "algorithmic_bytes_per_launch": byt}
+    if Kp and tf32_peak:
+        fl = slots_per_pass * 3 * 4 * Kp
+        r["tensor_tflops_executed"] = fl / (ms / 1e3) / 1e12
+        r["tensor_frac_of_tf32"] = r["tensor_tflops_executed"] / tf32_peak
+    return r
+
+
+def run_tiny(torch, pk, budget):
+    """North-star configuration 1: 30^3 rank 3, 30 % missing, 10 % outliers, adaptive width,
+    100 iterations on the FP64 path (launch-latency bound)."""
+    from paper_2305_09044_gb300 import TRD, synth
+    w = synth.WORKLOADS["tiny3"]
+    t, Xt, host, dev, corr = build_problem(w, torch, "fp64")
+    t.init_cores(w.init_seed)
+    kw = {"sigma": -1.0}
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(t.stream)
+    for _ in range(100):
+        t.step(**kw)
+    b.record(t.stream)
+    torch.cuda.synchronize()
+    ms100 = a.elapsed_time(b)
+    err = t.recovery_error(Xt)
+    ms, ph, launches = timed_device_steps(t, 20, 3, torch, kw)
+    t.close()
+    slots = 3 * 27000
+    res = {"workload": "tiny3: 30^3 TR ranks 3, 30% missing, 10% outliers, adaptive sigma, FP64, 100 iterations",
+           "precision": "fp64", "seconds_100_iters": ms100 / 1e3, "iters_per_s": 100 / (ms100 / 1e3),
+           "ms_per_iter_steady": ms, "sampled_entries_per_s": slots / (ms / 1e3),
+           "kernel_launches_per_iter": launches, "rel_err_after_100": err,
+           "roofline": {"bound": "latency", "note": "27,000-slot passes: every kernel is a few microseconds; the "
+                        "iteration is bound by the chain of dependent launches (replayed as one CUDA graph)",
+                        "us_per_launch": ms * 1e3 / max(launches, 1)},
+           "phase_ms_per_step_untimed": phase_summary(ph)}
+    if budget:
+        res["cpu_baseline"] = cpu_pair("trajectory", "tiny3", budget)
+    return res
+
+
+def run_sketched(torch, pk, name, precs, steps, budget, conv_iters, conv_budget):
+    """North-star configurations 3 (64^5 rank 10, sketch 24 per non-updated mode) and 4
+    (1024 x 1024 x 256 rank 16, sketch 128 x 128 x full): SAWRTRD iterations with the RStS
+    gather inside every core update; iterations/s, sampled entries/s, per-phase times, the
+    gather's and the data passes' rooflines, and time to recovery error 1e-3 per precision."""
+    from paper_2305_09044_gb300 import synth
+    w = synth.WORKLOADS[name]
+    N = len(w.dims)
+    slots = [int(np.prod([w.dims[m] if m == k else min(w.sketch, w.dims[m]) for m in range(N)]))
+             for k in range(N)]
+    kw = {"sketch": [w.sketch] * N, "sigma": -1.0, "seed": w.sample_seed}
+    out = {"workload": f"{w.name}: {'x'.join(map(str, w.dims))} TR ranks {w.ranks[0]}, "
+                       f"{int(w.missing * 100)}% missing, {int(w.outlier_frac * 100)}% "
+                       f"{'salt-and-pepper' if w.outlier_kind == 'saltpepper' else 'outliers U[-10 std,10 std]'}, "
+                       f"RStS sketch {w.sketch} per non-updated mode, adaptive sigma",
+           "slots_per_iteration": sum(slots),
+           "data": "synthetic; corruption drawn on the device by torch's seeded generator"}
+    t, Xt, X, M = device_problem(w, torch, precs[0])
+    for prec in precs:
+        if prec != precs[0]:
+            t.close()
+            from paper_2305_09044_gb300 import TRD
+            t = TRD(w.dims, w.ranks, prec)
+            t.set_data(X, M)
+        t.init_cores(w.init_seed)
+        ms, ph, launches = timed_device_steps(t, steps, 3, torch, kw)
+        # average per core update of the traced steps
+        gather_ms = ph.get("gather_ms", 0.0) / max(ph.get("gather_n", 1), 1)
+        gbytes = np.mean(slots) * (4 + 1 / 8) * 2          # read x + bit, write x_I + bit
+        leg = {"ms_per_iter": ms, "iters_per_s": 1e3 / ms, "sampled_entries_per_s": sum(slots) / (ms / 1e3),
+               "kernel_launches_per_iter": launches, "phase_ms_per_step_untimed": phase_summary(ph)}
+        leg["roofline_pass"] = pass_roofline(ph, np.mean(slots), pk,
+                                             f"fused data pass ({prec})", Kp=None)
+        if gather_ms > 0:
+            leg["roofline_gather"] = {"kernel": "k_gather (RStS sketch X_I, P_I)", "bound": "hbm",
+                                      "achieved": gbytes / (gather_ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                                      "unit": "GB/s", "frac": gbytes / (gather_ms / 1e3) / 1e9 / pk["hbm_gbs"],
+                                      "ms_per_launch": gather_ms,
+                                      "algorithmic_bytes_per_launch": gbytes}
+        t.init_cores(w.init_seed)
+        leg["time_to_rel_err_1e-3"] = converge_steps(t, Xt, kw, conv_iters, conv_budget, torch)
+        out[prec] = leg
+    t.close()
+    del Xt, X, M
+    torch.cuda.empty_cache()
+    if budget:
+        out["cpu_baseline"] = cpu_pair("sketch", name, budget)
+    return out
+
+
+def run_sampled(torch, pk, steps, budget):
+    """North-star configuration 5: sampled correntropy loss of a 128^4 rank-20 TR model at
+    2^24 observed entries (10 % outliers), forward + hand-written adjoint through the C ABI,
+    FP32; forward+backward evaluations per second and sampled entries per second."""
+    from paper_2305_09044_gb300 import TRD, synth, binding
+    w = synth.WORKLOADS["grad128"]
+    t, Xt, X, M = device_problem(w, torch, "fp32")
+    n = X.numel()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(w.sample_seed)
+    lin = torch.randperm(n, generator=g, device="cuda")[: w.n_sampled].sort().values
+    idx = torch.empty((lin.numel(), 4), dtype=torch.int32, device="cuda")
+    rem = lin.clone()
+    for m, d in enumerate(w.dims):
+        idx[:, m] = (rem % d).to(torch.int32)
+        rem //= d
+    x = X[lin].contiguous()
+    del rem, lin, Xt, M
+    cores = [torch.from_numpy(np.ascontiguousarray(Z.transpose(1, 2, 0))).float().cuda()
+             for Z in synth.gaussian_cores(w.dims, w.ranks, w.init_seed)]
+    sigma = 1.0
+    grads = [torch.empty_like(c) for c in cores]
+    for _ in range(3):
+        t.sampled_fwd(cores, idx, x, sigma)
+        t.sampled_bwd(cores, idx, x, sigma, 1.0, grads)
+    torch.cuda.synchronize()
+    a, b, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    fwd_ms = bwd_ms = 0.0
+    for _ in range(steps):
+        a.record(t.stream)
+        t.sampled_fwd(cores, idx, x, sigma)
+        b.record(t.stream)
+        t.sampled_bwd(cores, idx, x, sigma, 1.0, grads)
+        c2.record(t.stream)
+        torch.cuda.synchronize()
+        fwd_ms += a.elapsed_time(b)
+        bwd_ms += b.elapsed_time(c2)
+    fwd_ms /= steps
+    bwd_ms /= steps
+    Mn = int(idx.shape[0])
+    K = w.ranks[0] * w.ranks[2]
+    # per entry: index (16 B) + value (4 B) from HBM; two K-float slices of the merged halves
+    # (the halves are 2 x 16,384 x 400 floats = 52 MB, L2-resident)
+    hbm = Mn * 20
+    l2 = Mn * 2 * K * 4
+    res = {"workload": "grad128: 128^4 TR ranks 20, 10% outliers, 2^24 sampled entries, FP32",
+           "entries": Mn, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+           "fwd_bwd_per_s": 1e3 / (fwd_ms + bwd_ms), "sampled_entries_per_s": Mn / ((fwd_ms + bwd_ms) / 1e3),
+           "roofline": {"kernel": "k_sampled (forward and adjoint)", "bound": "l2",
+                        "hbm_bytes_per_fwd": hbm, "l2_slice_bytes_per_fwd": l2,
+                        "l2_gbs_fwd": l2 / (fwd_ms / 1e3) / 1e9,
+                        "hbm_frac_fwd": hbm / (fwd_ms / 1e3) / 1e9 / pk["hbm_gbs"]}}
+    t.close()
+    del x, idx, X
+    torch.cuda.empty_cache()
+    if budget:
+        res["cpu_baseline"] = cpu_pair("sampled", "grad128", budget)
+    return res
 
 
 # ----------------------------------------------------------------------------- oracle
@@ -560,9 +998,22 @@ def _max_over_ranks(x, world):
 
 def main():
     args = parse()
+    if args.oracle_probe:
+        oracle_probe_main(args.oracle_probe, args.oracle_budget)
+        return
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.configs_only:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        torch.cuda.set_device(local)
+        if rank == 0:
+            measured = measure_peaks(torch)
+            print(json.dumps({"peaks_measured_here": measured, "configs": other_configs(args, torch, measured)}),
+                  flush=True)
         return
     if args.image_only:
         import torch

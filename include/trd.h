@@ -51,13 +51,21 @@ typedef enum {
   TRD_ENOTIMPL = 7     /* combination not implemented (e.g. precision for this shape) */
 } trd_status;
 
+/* Arithmetic of the two data passes (reconstruction, residual and weight, weighted
+ * contraction of Eq. hatd, line-search product).  FGMC, the factorisation, the solves and the
+ * step size are FP64 in every mode.  K' = r_1 r_{c+1} is the contraction width of the data
+ * passes (c = the cut of the ring into two merged halves, chosen per view). */
 typedef enum {
-  TRD_FP64 = 0,  /* SIMT FP64 data passes (small problems, debugging) */
-  TRD_FP32 = 1,  /* SIMT FP32 data passes, FP32 accumulation */
-  TRD_BF16 = 2   /* tcgen05 tensor cores: split-BF16 reconstruction, BF16 gradient and
-                    line-search products, FP32 accumulation; residual and weight in FP32;
-                    r_1 r_{c+1} <= 128 (c = the cut of the ring) and an inner block size that
-                    is a multiple of 4, else TRD_ENOTIMPL */
+  TRD_FP64 = 0,   /* CUDA-core FP64 data passes (small problems, debugging); K' <= 112 */
+  TRD_FP32 = 1,   /* CUDA-core FP32 data passes, FP32 accumulation; K' <= 256 */
+  TRD_BF16 = 2,   /* tcgen05 tensor cores, mixed BF16: the reconstruction in 3-term split BF16
+                     (hi*hi + hi*lo + lo*hi), the gradient and line-search products in one
+                     BF16 term, FP32 accumulation; residual and weight in FP32; K' <= 256,
+                     else TRD_ENOTIMPL */
+  TRD_TF32X3 = 3  /* tcgen05 tensor cores, TF32 with the 3-term split of both operands in every
+                     product (about 22 significant bits per operand: FP32-level accuracy),
+                     FP32 accumulation; K' <= 64 on the tensor cores, wider contractions run
+                     the FP32 CUDA-core passes */
 } trd_precision;
 
 typedef enum {
@@ -214,6 +222,27 @@ trd_status trd_fgmc_gram(trd_t* handle, int k, double* G_host);
 trd_status trd_core_update(trd_t* handle, int k, double lambda, double eta, int gram,
                            double* eta_out);
 
+/* Partitioned core update (the exchange step of a multi-GPU update; no counterpart call in
+ * the paper, whose d, G and step size are global sums): when the observed columns of X_[k]
+ * are split across handles (for example one handle per GPU, each on a slab of one non-updated
+ * mode selected with trd_sample_subtensor), d of Eq. hatd and the line-search denominator
+ * are sums of per-handle partial sums, while G, h and <d, h> are the same on every handle
+ * once d is.  A partitioned update of core k is: trd_residual_weights and trd_core_gradient
+ * on every handle (partial d), an all-reduce (sum) of d by the caller, trd_set_gradient with
+ * the summed d, trd_line_search_terms (<d, h> and the partial denominator), an all-reduce of
+ * the denominators, and trd_core_update with the fixed step eta = <d, h> / sum of
+ * denominators.
+ *
+ * trd_set_gradient: replace the device gradient of core k by d_host (HOST, I_k x K_k, layout
+ * above).  Needs trd_residual_weights for k on this handle (the view of the line search).
+ * trd_line_search_terms: h = d (G + lambda I)^-1 (as trd_core_update, `gram` a
+ * trd_gram_kind), then *num_out = <d, h> and *den_out = sum w (h B^T)^2 over this handle's
+ * view (the second data pass, W recomputed); the core is not changed.  Needs a gradient for
+ * k.  Both synchronise.  Errors: TRD_EINVAL (order of calls, NULL), TRD_ESINGULAR. */
+trd_status trd_set_gradient(trd_t* handle, int k, const double* d_host);
+trd_status trd_line_search_terms(trd_t* handle, int k, double lambda, int gram, double* num_out,
+                                 double* den_out);
+
 /* One outer iteration of Algorithm 1: adaptive width (if params->sigma <= 0), then for
  * k = 1..N: index draw + RStS gather (if sketched), residual/weights/gradient pass, FGMC
  * Gram, scaled update with exact line search; then D^t = Z_{N(2)} G^{!=N} Z_{N(2)}^T and
@@ -286,7 +315,7 @@ trd_status trd_psnr(trd_t* handle, const float* Xref_dev, double peak, double* p
  * search), 2 operand merges and conversions, 3 reductions of partial results,
  * 4 back-contraction into the gradient, 5 FGMC Gram, 6 LDL^T factorisation, 7 solves and
  * <d,h>, 8 step size, core update and factor refresh, 9 adaptive width, 10 stopping
- * quantity, 11 unused.  TRD_EINVAL for another level. */
+ * quantity, 11 the RStS gather of the sketch.  TRD_EINVAL for another level. */
 trd_status trd_set_profiling(trd_t* handle, int on);
 
 /* Synchronise the handle's stream and write out[2q] = total milliseconds and out[2q+1] = the

@@ -20,7 +20,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libtrd.so")
 
 TRD_OK, TRD_EINVAL, TRD_ENOMEM, TRD_ECUDA, TRD_ESINGULAR, TRD_ENONFINITE, TRD_ETIMEOUT, TRD_ENOTIMPL = range(8)
-PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "tf32x3": 3}
 GRAMS = {"global": 0, "local": 1, "none": 2}
 MAX_ORDER = 8
 
@@ -36,7 +36,8 @@ EXPORTS = [
     "trd_sigma_from_residuals", "trd_reconstruct", "trd_reconstruct_from",
     "trd_recovery_error", "trd_sampled_fwd", "trd_sampled_bwd", "trd_set_profiling",
     "trd_get_profile", "trd_kernel_launches", "trd_sigma_from_residuals_noalloc",
-    "trd_wait_selftest", "trd_set_graphs", "trd_sample_rows", "trd_psnr",
+    "trd_wait_selftest", "trd_set_graphs", "trd_sample_rows", "trd_psnr", "trd_set_gradient",
+    "trd_line_search_terms",
 ]
 
 
@@ -109,6 +110,8 @@ def load(path: str = LIB_PATH):
         "trd_set_graphs": [vp, C.c_int],
         "trd_sample_rows": [vp, C.c_int, P(i32), i64],
         "trd_psnr": [vp, vp, dbl, P(dbl)],
+        "trd_set_gradient": [vp, C.c_int, P(dbl)],
+        "trd_line_search_terms": [vp, C.c_int, dbl, C.c_int, P(dbl), P(dbl)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -283,6 +286,21 @@ class TRD:
                     "trd_core_update")
         return out.value
 
+    def set_gradient(self, k: int, d: np.ndarray):
+        """Replace the device gradient of core k (I_k x K) by d (the summed partial gradients of
+        a partitioned update)."""
+        a = np.ascontiguousarray(d, dtype=np.float64)
+        assert a.shape == (self.dims[k], self.K(k))
+        self._check(self.lib.trd_set_gradient(self.h, k, a.ctypes.data_as(C.POINTER(C.c_double))),
+                    "trd_set_gradient")
+
+    def line_search_terms(self, k: int, lam: float = -1e-10, gram: str = "global"):
+        """(<d, h>, this handle's line-search denominator) without changing core k."""
+        num, den = C.c_double(), C.c_double()
+        self._check(self.lib.trd_line_search_terms(self.h, k, lam, GRAMS[gram], C.byref(num), C.byref(den)),
+                    "trd_line_search_terms")
+        return num.value, den.value
+
     def step(self, sketch: Optional[Sequence[int]] = None, sigma: float = -1.0,
              lam: float = -1e-10, seed: int = 0, gram: str = "global") -> dict:
         p = Params()
@@ -330,7 +348,7 @@ class TRD:
         self._check(self.lib.trd_set_profiling(self.h, level), "trd_set_profiling")
 
     PHASES = ["pass1", "pass2", "merge", "reduce", "backcontract", "gram", "cholesky", "solve",
-              "update", "sigma", "stop", "other"]
+              "update", "sigma", "stop", "gather"]
 
     def get_profile(self, reset: bool = False) -> dict:
         """Per-phase totals (ms) and counts of the traced intervals (see trd_get_profile)."""

@@ -139,6 +139,20 @@ struct Extra {
   uint64_t mst_gen[2] = {~0ull, ~0ull};   // view (sketch) the relayout was made for
   int64_t mst_W[2] = {0, 0};
   int64_t ldT = 0, W = 0;
+  bool tc_pass = false;         // the last pass 1 ran on the tensor cores
+  // RStS index staging: a ring of pinned host slots, each reused only after the event recorded
+  // behind its previous upload has completed (no host synchronisation per core update)
+  static constexpr int kIdxSlots = 4;
+  int32_t* idx_ring = nullptr;
+  size_t idx_ring_cap = 0;      // int32 entries per slot
+  cudaEvent_t idx_ev[kIdxSlots] = {};
+  bool idx_ev_live[kIdxSlots] = {};
+  int idx_slot = 0;
+  DevBuf gbase;                 // RStS gather: offset in X of every fibre of the sketch
+  DevBuf bShlo;                 // TF32: lo split of the step operand
+  DevBuf bTThi, bTTlo;          // TF32: streaming splits transposed ([kpad][ldTT]), GEMM-2 operand
+  HalfTag tagBTT;               // which merged half the transposed splits hold
+  int64_t ldTT = 0;
   // the view's data re-laid with a row stride that is a multiple of 4 floats, for the
   // tensor-core passes when the inner block size P_in is not (TMA row strides are multiples
   // of 16 bytes); cached per view like the mask rows
@@ -191,6 +205,12 @@ struct Extra {
 Extra* X_(trd_handle* h);
 
 bool is_fp64(const trd_handle* h) { return h->prec == TRD_FP64; }
+bool is_tf32(const trd_handle* h) { return h->prec == TRD_TF32X3; }
+// the data passes of this contraction width run on the tensor cores (BF16 up to K' = 256,
+// TF32 up to K' = 64); FP64, FP32 and wider TF32 contractions run the CUDA-core passes
+bool tc_fits(const trd_handle* h, int Kp) {
+  return (h->prec == TRD_BF16 || h->prec == TRD_TF32X3) && tc_kpad(Kp, is_tf32(h)) != 0;
+}
 
 cudaEvent_t pool_event(Extra* x) {
   if (!x->ev_pool.empty()) {
@@ -222,7 +242,7 @@ void prof_end(trd_handle* h, int kind) {
 
 // Phases of a core update timed by the tracing hook (kinds of event pairs).
 enum : int { P_PASS1 = 0, P_PASS2 = 1, P_MERGE = 2, P_REDUCE = 3, P_GRAD = 4, P_GRAM = 5, P_CHOL = 6,
-             P_SOLVE = 7, P_UPDATE = 8, P_SIGMA = 9, P_STOP = 10 };
+             P_SOLVE = 7, P_UPDATE = 8, P_SIGMA = 9, P_STOP = 10, P_GATHER = 11 };
 
 // RAII phase scope: events around a phase, only at tracing level 2 (the data passes are traced
 // from level 1); phases never nest.
@@ -579,7 +599,7 @@ trd_status build_halves(trd_handle* h, int k) {
   const HalfTag want_st = half_tag(h, hs, sp), want_str = half_tag(h, 1 - hs, sp);
   // BF16 handles: the tensor-core operands (hi/lo, KP-wide rows) are written by the same
   // merge and trade roles together with the FP32 halves
-  const int KP = h->prec == TRD_BF16 ? tc_kpad(sp.Kp) : 0;
+  const int KP = (h->prec == TRD_BF16 && tc_fits(h, sp.Kp)) ? tc_kpad(sp.Kp, false) : 0;
   if (x->tagSst == want_str || x->tagSstr == want_st) {
     std::swap(h->Sst, h->Sstr);
     std::swap(x->tagSst, x->tagSstr);
@@ -700,13 +720,14 @@ PassArgs pass_args(trd_handle* h) {
 trd_status tc_operands(trd_handle* h) {
   const Split& sp = h->split;
   Extra* x = X_(h);
-  const int KP = tc_kpad(sp.Kp);
+  const bool tf = is_tf32(h);
+  const int KP = tc_kpad(sp.Kp, tf);
   if (x->tagBst == x->tagSstr || x->tagBstr == x->tagSst) {
     std::swap(x->bShi, x->bThi);
     std::swap(x->bSlo, x->bTlo);
     std::swap(x->tagBst, x->tagBstr);
   }
-  const size_t b2 = sizeof(__nv_bfloat16);
+  const size_t b2 = tf ? sizeof(float) : sizeof(__nv_bfloat16);
   const void* p0 = x->bShi.p;
   const void* p1 = x->bSlo.p;
   const void* p2 = x->bThi.p;
@@ -718,13 +739,33 @@ trd_status tc_operands(trd_handle* h) {
   if (x->bShi.p != p0 || x->bSlo.p != p1) x->tagBst.valid = false;
   if (x->bThi.p != p2 || x->bTlo.p != p3) x->tagBstr.valid = false;
   if (!(x->tagBst == x->tagSst)) {
-    CK(launch_tc_prep((const float*)h->Sst.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bShi.p,
-                      (__nv_bfloat16*)x->bSlo.p, h->stream), "bf16 stationary operands");
+    if (tf)
+      CK(launch_tc_prep_tf32((const float*)h->Sst.p, sp.P_stat, sp.Kp, (float*)x->bShi.p, (float*)x->bSlo.p,
+                             h->stream), "tf32 stationary operands");
+    else
+      CK(launch_tc_prep((const float*)h->Sst.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bShi.p,
+                        (__nv_bfloat16*)x->bSlo.p, h->stream), "bf16 stationary operands");
     x->tagBst = x->tagSst;
   }
-  if (!(x->tagBstr == x->tagSstr)) {
-    CK(launch_tc_prep((const float*)h->Sstr.p, sp.P_strm, sp.Kp, (__nv_bfloat16*)x->bThi.p,
-                      (__nv_bfloat16*)x->bTlo.p, h->stream), "bf16 streaming operands");
+  if (tf) {
+    const int64_t ld = (sp.P_strm + 3) / 4 * 4;
+    const void* q0 = x->bTThi.p;
+    const void* q1 = x->bTTlo.p;
+    TRY(ensure(h, x->bTThi, sizeof(float) * (size_t)(KP * ld)));
+    TRY(ensure(h, x->bTTlo, sizeof(float) * (size_t)(KP * ld)));
+    if (x->bTThi.p != q0 || x->bTTlo.p != q1 || x->ldTT != ld) x->tagBTT.valid = false;
+    x->ldTT = ld;
+  }
+  if (!(x->tagBstr == x->tagSstr) || (tf && !(x->tagBTT == x->tagSstr))) {
+    if (tf) {
+      CK(launch_tc_prep_tf32((const float*)h->Sstr.p, sp.P_strm, sp.Kp, (float*)x->bThi.p, (float*)x->bTlo.p,
+                             h->stream, (float*)x->bTThi.p, (float*)x->bTTlo.p, x->ldTT),
+         "tf32 streaming operands");
+      x->tagBTT = x->tagSstr;
+    }
+    else
+      CK(launch_tc_prep((const float*)h->Sstr.p, sp.P_strm, sp.Kp, (__nv_bfloat16*)x->bThi.p,
+                        (__nv_bfloat16*)x->bTlo.p, h->stream), "bf16 streaming operands");
     x->tagBstr = x->tagSstr;
   }
   return TRD_OK;
@@ -733,11 +774,11 @@ trd_status tc_operands(trd_handle* h) {
 trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
   const Split& sp = h->split;
   Extra* x = X_(h);
-  const int KP = tc_kpad(sp.Kp);
-  if (!KP) return set_err(h, TRD_ENOTIMPL, "BF16 path supports r_1 r_c <= 128");
+  const int KP = tc_kpad(sp.Kp, is_tf32(h));
+  if (!KP) return set_err(h, TRD_ENOTIMPL, "tensor-core path supports r_1 r_c <= 256 (BF16) / 64 (TF32)");
   const View& v = h->view;
   const int64_t RB = (sp.P_stat + tc_bm() - 1) / tc_bm();
-  const int64_t NT = (sp.P_strm + tc_bn() - 1) / tc_bn();
+  const int64_t NT = (sp.P_strm + tc_bn(KP, is_tf32(h)) - 1) / tc_bn(KP, is_tf32(h));
   const int G = (int)imin(imax(1, h->num_sms - x->reserve_sms), RB * NT);
   const int o = sp.rows ? 0 : 1;
   const int64_t nstat = sp.rows ? sp.P_in : sp.P_out, nstrm = sp.rows ? sp.P_out : sp.P_in;
@@ -786,8 +827,17 @@ trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
   TRY(ensure(h, h->stat_part, sizeof(double) * 8 * (size_t)G));
   TRY(ensure(h, h->Tsum, sizeof(double) * (size_t)sp.P_stat * sp.Kp));
   prof_begin(h);
-  CK(launch_pass_tc(sp.rows, false, (const __nv_bfloat16*)x->bShi.p, (const __nv_bfloat16*)x->bSlo.p, nullptr,
-                    (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p, x->Xtc, sp.P_in, x->ldx, sp.P_out, (const uint32_t*)x->Mst[o].p, W, sp.P_stat, sp.P_strm, sp.Kp,
+  PassOperands ops;
+  ops.S_hi = x->bShi.p;
+  ops.S_lo = x->bSlo.p;
+  ops.T_hi = x->bThi.p;
+  ops.T_lo = x->bTlo.p;
+  if (is_tf32(h)) {
+    ops.T_hiT = x->bTThi.p;
+    ops.T_loT = x->bTTlo.p;
+    ops.ldT = x->ldTT;
+  }
+  CK(launch_pass_tc(is_tf32(h), sp.rows, false, ops, x->Xtc, sp.P_in, x->ldx, sp.P_out, (const uint32_t*)x->Mst[o].p, W, sp.P_stat, sp.P_strm, sp.Kp,
                     h->scal + S_SIGMA, (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, G, full_stats,
                     h->stream),
      "tensor-core data pass 1");
@@ -809,34 +859,50 @@ trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
 trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
   const Split& sp = h->split;
   Extra* x = X_(h);
+  const bool tf = is_tf32(h);
+  const int KP = tc_kpad(sp.Kp, tf);
   {
     PScope ps(h, P_MERGE);
     TRY(build_halves(h, k));      // normally cached: restores the roles of core k
     TRY(tc_operands(h));
-    TRY(ensure(h, x->bSh, sizeof(__nv_bfloat16) * sp.P_stat * tc_kpad(sp.Kp)));
-    if (x->row_view) {
+    if (tf) {
+      // TF32: the step operand merged in FP32 and split into TF32 hi / lo rows
+      TRY(ensure(h, x->bSh, sizeof(float) * sp.P_stat * KP));
+      TRY(ensure(h, x->bShlo, sizeof(float) * sp.P_stat * KP));
+      TRY(build_merged(h, k, true));
+      CK(launch_tc_prep_tf32((const float*)h->Sh.p, sp.P_stat, sp.Kp, (float*)x->bSh.p, (float*)x->bShlo.p,
+                             h->stream), "tf32 step operands");
+    } else if (x->row_view) {
+      TRY(ensure(h, x->bSh, sizeof(__nv_bfloat16) * sp.P_stat * KP));
       TRY(build_merged(h, k, true));
       CK(launch_tc_prep((const float*)h->Sh.p, sp.P_stat, sp.Kp, (__nv_bfloat16*)x->bSh.p, nullptr, h->stream),
          "bf16 step operands");
     } else {
       // the step operand in FP32 too: after the step the stationary half (which holds core k)
       // is advanced in place, S += eta S_h, instead of being merged again
+      TRY(ensure(h, x->bSh, sizeof(__nv_bfloat16) * sp.P_stat * KP));
       TRY(ensure(h, h->Sh, sizeof(float) * sp.P_stat * sp.Kp));
-      TRY(build_merged(h, k, true, (__nv_bfloat16*)x->bSh.p, tc_kpad(sp.Kp), h->Sh.p));
+      TRY(build_merged(h, k, true, (__nv_bfloat16*)x->bSh.p, KP, h->Sh.p));
       x->adv_k = k;
     }
   }
   // the side stream has joined: the line-search pass takes every SM (its per-CTA partials are
   // summed by the update kernel over the same count)
   {
-    const int64_t units = ((sp.P_stat + tc_bm() - 1) / tc_bm()) * ((sp.P_strm + tc_bn() - 1) / tc_bn());
+    const int BN = tc_bn(KP, tf);
+    const int64_t units = ((sp.P_stat + tc_bm() - 1) / tc_bm()) * ((sp.P_strm + BN - 1) / BN);
     x->tcG = (int)imin(h->num_sms, units);
     TRY(ensure(h, h->stat_part, sizeof(double) * 8 * (size_t)x->tcG));
   }
+  PassOperands ops;
+  ops.S_hi = x->bShi.p;
+  ops.S_lo = x->bSlo.p;
+  ops.S_h = x->bSh.p;
+  ops.S_h_lo = tf ? x->bShlo.p : nullptr;
+  ops.T_hi = x->bThi.p;
+  ops.T_lo = x->bTlo.p;
   prof_begin(h);
-  CK(launch_pass_tc(sp.rows, true, (const __nv_bfloat16*)x->bShi.p, (const __nv_bfloat16*)x->bSlo.p,
-                    (const __nv_bfloat16*)x->bSh.p, (const __nv_bfloat16*)x->bThi.p, (const __nv_bfloat16*)x->bTlo.p,
-                    x->Xtc, sp.P_in, x->ldx, sp.P_out,
+  CK(launch_pass_tc(tf, sp.rows, true, ops, x->Xtc, sp.P_in, x->ldx, sp.P_out,
                     (const uint32_t*)x->Mst[x->mst_o].p, x->W, sp.P_stat, sp.P_strm, sp.Kp, h->scal + S_SIGMA,
                     (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, x->tcG, false, h->stream),
      "tensor-core data pass 2");
@@ -851,7 +917,10 @@ trd_status run_pass1(trd_handle* h, int k, bool full_stats = true) {
     return set_err(h, TRD_EINVAL, "the current row sample was drawn for another core");
   h->split = X_(h)->row_view ? row_split(h, k, X_(h)->rows_J) : choose_split(h, h->view, k);
   const Split& sp = h->split;
-  if (h->prec == TRD_BF16) {
+  X_(h)->tc_pass = tc_fits(h, sp.Kp);
+  if (h->prec == TRD_BF16 && !X_(h)->tc_pass)
+    return set_err(h, TRD_ENOTIMPL, "BF16 path supports r_1 r_c <= 256");
+  if (X_(h)->tc_pass) {
     TRY(run_pass1_tc(h, k, full_stats));
   } else {
     if (sp.Kp > 112 && is_fp64(h)) return set_err(h, TRD_ENOTIMPL, "FP64 path supports r_1 r_c <= 112");
@@ -959,7 +1028,7 @@ trd_status run_gradient(trd_handle* h, int k) {
   CK(launch_backcontract(h->Tsum.p, sp.Kp, sp.rows, mr, mc, pre.n > 1 ? h->pre.p : nullptr, n_pre,
                          post.n > 1 ? h->post.p : nullptr, n_post, h->I[k], rk, rk1, (double*)h->dpart.p,
                          (int)nsplit, (double*)h->d.p, (unsigned*)X_(h)->bc_ctr.p, dbl, h->stream,
-                         h->prec == TRD_BF16 ? &X_(h)->slots : nullptr, bc_core(pre), bc_core(post)),
+                         X_(h)->tc_pass ? &X_(h)->slots : nullptr, bc_core(pre), bc_core(post)),
      "back-contraction");
   h->grad_k = k;
   return TRD_OK;
@@ -1030,8 +1099,11 @@ bool prefactor(trd_handle* h, int k, double lambda) {
   return true;
 }
 
+// terms (host, nullable): instead of updating the core, return <d, h> and this handle's
+// line-search denominator sum w (h B^T)^2 over its own view (the exchange step of a
+// partitioned update) in terms[0], terms[1].
 trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int gram,
-                      double* eta_slot) {
+                      double* eta_slot, double* terms = nullptr) {
   if (h->grad_k != k) return set_err(h, TRD_EINVAL, "trd_core_gradient must run for this core first");
   if (gram == TRD_GRAM_LOCAL && X_(h)->row_view)
     return set_err(h, TRD_ENOTIMPL, "the local Gram is defined for the RStS sketch, not for sampled rows");
@@ -1100,7 +1172,7 @@ trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int
     CK(launch_dot(d, hh, n, h->scal + S_NUM, h->stream), "<d,h>");
   }
   double* den = h->scal + S_DEN;
-  if (eta_fixed <= 0 && h->prec == TRD_BF16) {
+  if (eta_fixed <= 0 && X_(h)->tc_pass) {
     TRY(run_pass2_tc(h, k, &den));
   } else if (eta_fixed <= 0) {
     {
@@ -1118,6 +1190,21 @@ trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int
     CK(launch_reduce_stats((const double*)h->stat_part.p, ctas, s2, h->dstatus, h->stream), "reduce den");
     den = s2 + 6;
   }
+  if (terms) {
+    double* s2 = (double*)X_(h)->stat_sum2.p;
+    if (!den) {
+      // tensor-core line search: the per-CTA partials are summed here instead of in the update
+      CK(launch_reduce_stats((const double*)h->stat_part.p, X_(h)->tcG, s2, h->dstatus, h->stream), "reduce den");
+      den = s2 + 6;
+    }
+    CK(cudaMemcpyAsync(h->host_pinned, h->scal + S_NUM, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "num");
+    CK(cudaMemcpyAsync(h->host_pinned + 1, den, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "den");
+    TRY(sync_and_status(h));
+    terms[0] = h->host_pinned[0];
+    terms[1] = h->host_pinned[1];
+    X_(h)->adv_k = -1;
+    return TRD_OK;
+  }
   PScope psu(h, P_UPDATE);
   const bool from_parts = eta_fixed <= 0 && den == nullptr;   // tensor-core line search
   // BF16 path with the step operand in FP32 at hand: the stationary half (it holds core k)
@@ -1133,7 +1220,7 @@ trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int
     adv.Sh = (const float*)h->Sh.p;
     adv.n = spa.P_stat * (int64_t)spa.Kp;
     adv.Kp = spa.Kp;
-    adv.kpad = tc_kpad(spa.Kp);
+    adv.kpad = tc_kpad(spa.Kp, false);
     adv.hi = (__nv_bfloat16*)xa->bShi.p;
     adv.lo = (__nv_bfloat16*)xa->bSlo.p;
   }
@@ -1244,19 +1331,29 @@ trd_status sample(trd_handle* h, int k, const int32_t* const* idx, const int32_t
   View v = full_view(h);
   size_t off = 0;
   const size_t need = [&] { size_t t = 0; for (int m = 0; m < N; ++m) t += (size_t)h->I[m]; return t; }();
-  if (h->idx_pinned_cap < need) {
-    if (h->idx_pinned) cudaFreeHost(h->idx_pinned);
-    h->idx_pinned = nullptr;
-    h->idx_pinned_cap = 0;
+  Extra* xr = X_(h);
+  if (xr->idx_ring_cap < need) {
+    // (re)allocate the staging ring: wait for every upload still reading the old one
     CK(cudaStreamSynchronize(h->stream), "sync");
-    if (cudaMallocHost(&h->idx_pinned, need * sizeof(int32_t)) != cudaSuccess) {
+    if (xr->idx_ring) cudaFreeHost(xr->idx_ring);
+    xr->idx_ring = nullptr;
+    xr->idx_ring_cap = 0;
+    if (cudaMallocHost(&xr->idx_ring, need * Extra::kIdxSlots * sizeof(int32_t)) != cudaSuccess) {
       cudaGetLastError();
       return set_err(h, TRD_ENOMEM, "pinned allocation failed");
     }
-    h->idx_pinned_cap = need;
+    xr->idx_ring_cap = need;
+    for (int q = 0; q < Extra::kIdxSlots; ++q) xr->idx_ev_live[q] = false;
   }
-  // the pinned staging area is reused: wait for any earlier upload from it
-  CK(cudaStreamSynchronize(h->stream), "sync before index upload");
+  const int slot = xr->idx_slot;
+  xr->idx_slot = (slot + 1) % Extra::kIdxSlots;
+  if (!xr->idx_ev[slot] && cudaEventCreateWithFlags(&xr->idx_ev[slot], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(h, TRD_ECUDA, "event creation failed");
+  }
+  // this slot's previous upload has been read by the copy engine
+  if (xr->idx_ev_live[slot]) CK(cudaEventSynchronize(xr->idx_ev[slot]), "index staging slot");
+  int32_t* stage = xr->idx_ring + (size_t)slot * xr->idx_ring_cap;
   bool any = false;
   for (int m = 0; m < N; ++m) {
     if (m == k || !idx[m]) continue;
@@ -1277,13 +1374,17 @@ trd_status sample(trd_handle* h, int k, const int32_t* const* idx, const int32_t
       }
       h->idx_cap[m] = (size_t)h->I[m];
     }
-    memcpy(h->idx_pinned + off, idx[m], sizeof(int32_t) * sm);
-    CK(cudaMemcpyAsync(h->idx_dev[m], h->idx_pinned + off, sizeof(int32_t) * sm, cudaMemcpyHostToDevice,
+    memcpy(stage + off, idx[m], sizeof(int32_t) * sm);
+    CK(cudaMemcpyAsync(h->idx_dev[m], stage + off, sizeof(int32_t) * sm, cudaMemcpyHostToDevice,
                        h->stream), "index upload");
     off += sm;
     v.dim[m] = sm;
     v.idx[m] = h->idx_dev[m];
     any = true;
+  }
+  if (off > 0) {
+    CK(cudaEventRecord(xr->idx_ev[slot], h->stream), "index staging event");
+    xr->idx_ev_live[slot] = true;
   }
   if (!any) return use_full_view(h);
   v.numel = 1;
@@ -1291,7 +1392,12 @@ trd_status sample(trd_handle* h, int k, const int32_t* const* idx, const int32_t
   const int64_t words = ((v.numel + 31) / 32 + 3) / 4 * 4;
   TRY(ensure(h, h->XI, sizeof(float) * (size_t)v.numel));
   TRY(ensure(h, h->PI, sizeof(uint32_t) * (size_t)words));
-  CK(launch_gather(h->X, h->M, N, h->I, v, (float*)h->XI.p, (uint32_t*)h->PI.p, h->stream), "RStS gather");
+  {
+    PScope ps(h, P_GATHER);
+    TRY(ensure(h, X_(h)->gbase, sizeof(int64_t) * (size_t)(v.numel / v.dim[0])));
+    CK(launch_gather(h->X, h->M, N, h->I, v, (float*)h->XI.p, (uint32_t*)h->PI.p, (int64_t*)X_(h)->gbase.p,
+                     h->stream), "RStS gather");
+  }
   v.X = (const float*)h->XI.p;
   v.M = (const uint32_t*)h->PI.p;
   h->view = v;
@@ -1428,7 +1534,8 @@ trd_status trd_create(trd_t** out, int N, const int64_t* I, const int32_t* R, in
   if (!out) return TRD_EINVAL;
   *out = nullptr;
   if (N < 3 || N > kMaxN || !I || !R) return TRD_EINVAL;
-  if (precision != TRD_FP64 && precision != TRD_FP32 && precision != TRD_BF16) return TRD_EINVAL;
+  if (precision != TRD_FP64 && precision != TRD_FP32 && precision != TRD_BF16 && precision != TRD_TF32X3)
+    return TRD_EINVAL;
   double logtot = 0;
   for (int m = 0; m < N; ++m) {
     if (I[m] < 1 || I[m] > (int64_t(1) << 31) - 1) return TRD_EINVAL;
@@ -1499,7 +1606,7 @@ void trd_destroy(trd_t* h) {
   DevBuf* xb[] = {&x->Ework, &x->meta,    &x->stat_sum2, &x->Gloc,    &x->recA, &x->recC,
                   &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr, &x->bc_ctr, &x->stop_part, &x->stop_ctr, &x->probe_lin, &x->Qb[0], &x->Qb[1], &x->probe_cand, &x->rows_dev,
                   &x->bShi,  &x->bSlo,    &x->bSh,       &x->bThi,    &x->bTlo,    &x->bTT,
-                  &x->Mst[0], &x->Mst[1]};
+                  &x->Mst[0], &x->Mst[1], &x->bShlo, &x->Xpad, &x->bTThi, &x->bTTlo, &x->gbase};
   for (DevBuf* b : xb) free_buf(*b);
   for (int k = 0; k < kMaxN; ++k) { free_buf(x->Eloc[k]); free_buf(x->tmpZ[k]); free_buf(x->smpZ[k]); }
   DevBuf* sb[] = {&x->smpA, &x->smpC, &x->smpGA, &x->smpGC, &x->smpGAd, &x->smpGCd, &x->smpPre, &x->smpPost,
@@ -1508,6 +1615,9 @@ void trd_destroy(trd_t* h) {
   for (auto& p : x->pending) { x->ev_pool.push_back(p.a); x->ev_pool.push_back(p.b); }
   if (x->ev_open) x->ev_pool.push_back(x->ev_open);
   for (cudaEvent_t e : x->ev_pool) cudaEventDestroy(e);
+  for (int q = 0; q < Extra::kIdxSlots; ++q)
+    if (x->idx_ev[q]) cudaEventDestroy(x->idx_ev[q]);
+  if (x->idx_ring) cudaFreeHost(x->idx_ring);
   if (h->scal) cudaFree(h->scal);
   if (h->dstatus) cudaFree(h->dstatus);
   if (h->report_dev) cudaFree(h->report_dev);
@@ -1719,6 +1829,33 @@ trd_status trd_core_update(trd_t* h, int k, double lambda, double eta, int gram,
      "eta");
   TRY(sync_and_status(h));
   *eta_out = h->host_pinned[0];
+  return TRD_OK;
+}
+
+trd_status trd_set_gradient(trd_t* h, int k, const double* d_host) {
+  TRY(check_handle(h));
+  touch(h);
+  TRY(check_k(h, k));
+  if (!d_host) return set_err(h, TRD_EINVAL, "d must not be NULL");
+  if (h->pass1_k != k) return set_err(h, TRD_EINVAL, "trd_residual_weights must run for this core first");
+  const size_t bytes = sizeof(double) * h->I[k] * h->K[k];
+  TRY(ensure(h, h->d, bytes));
+  CK(cudaMemcpyAsync(h->d.p, d_host, bytes, cudaMemcpyHostToDevice, h->stream), "gradient upload");
+  TRY(sync_and_status(h));
+  h->grad_k = k;
+  return TRD_OK;
+}
+
+trd_status trd_line_search_terms(trd_t* h, int k, double lambda, int gram, double* num_out, double* den_out) {
+  TRY(check_handle(h));
+  touch(h);
+  TRY(check_k(h, k));
+  if (gram < TRD_GRAM_GLOBAL || gram > TRD_GRAM_NONE) return set_err(h, TRD_EINVAL, "bad gram kind");
+  if (!num_out || !den_out) return set_err(h, TRD_EINVAL, "num_out and den_out must not be NULL");
+  double terms[2] = {0.0, 0.0};
+  TRY(run_update(h, k, lambda, -1.0, gram, nullptr, terms));
+  *num_out = terms[0];
+  *den_out = terms[1];
   return TRD_OK;
 }
 

@@ -573,23 +573,50 @@ struct GatherArgs {
   float* XI;
   uint32_t* PI;
   int64_t words;
+  const int64_t* obase;   // offset in X of fibre o of the sketch (all modes but the first)
+  int64_t nouter;         // fibres: numel / sdim[0]
 };
 
+// Offset in X of every fibre of the sketch along its first mode: o = overline{i_2 ... i_N}
+// (first digit fastest) -> sum_{m >= 1} idx_m(i_m) stride_m.  One thread per fibre.
+__global__ void k_gather_base(GatherArgs g, int64_t* __restrict__ obase) {
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < g.nouter; o += step) {
+    int64_t rem = o, full = 0;
+    for (int m = 1; m < g.N; ++m) {
+      int64_t i;
+      rem = qdivmod(rem, g.sdim[m], i);
+      full += (g.idx[m] ? (int64_t)g.idx[m][i] : i) * g.fstride[m];
+    }
+    obase[o] = full;
+  }
+}
+
+// RStS gather: X_I[l] and the observation bit of sketch entry l (a warp per 32 consecutive
+// entries, whose bits one ballot packs).  Entry l is position i_1 = l mod s_1 of fibre
+// o = l div s_1; the warp divides once and steps its lanes across at most a few fibres, so
+// consecutive lanes read consecutive positions of X along mode 1 (or its sampled indices).
 __global__ void k_gather(GatherArgs g) {
   const int lane = threadIdx.x & 31;
   const int64_t wpb = blockDim.x >> 5;
+  const int64_t s1 = g.sdim[0];
+  const int32_t* idx1 = g.idx[0];
   for (int64_t wd = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); wd < g.words;
        wd += (int64_t)gridDim.x * wpb) {
     const int64_t l = wd * 32 + lane;
+    int64_t r0;
+    const int64_t o0 = qdivmod(wd * 32, s1, r0);     // warp-uniform
+    int64_t i1 = r0 + lane, o = o0;
+    if (s1 >= 32) {
+      if (i1 >= s1) { i1 -= s1; ++o; }
+    } else {
+      int64_t r;
+      o += qdivmod(i1, s1, r);
+      i1 = r;
+    }
     bool obs = false;
     if (l < g.numel) {
-      int64_t rem = l, full = 0;
-      for (int m = 0; m < g.N; ++m) {
-        int64_t i;
-        rem = qdivmod(rem, g.sdim[m], i);
-        const int64_t fi = g.idx[m] ? (int64_t)g.idx[m][i] : i;
-        full += fi * g.fstride[m];
-      }
+      const int64_t full = g.obase[o] + (idx1 ? (int64_t)idx1[i1] : i1);
       g.XI[l] = g.X[full];
       obs = g.M ? ((g.M[full >> 5] >> (full & 31)) & 1u) : true;
     }
@@ -599,7 +626,7 @@ __global__ void k_gather(GatherArgs g) {
 }
 
 cudaError_t launch_gather(const float* X, const uint32_t* M, int N, const int64_t* full_dim,
-                          const View& v, float* XI, uint32_t* PI, cudaStream_t st) {
+                          const View& v, float* XI, uint32_t* PI, int64_t* obase, cudaStream_t st) {
   GatherArgs g;
   g.X = X; g.M = M; g.N = N; g.numel = v.numel; g.XI = XI; g.PI = PI;
   int64_t stride = 1;
@@ -609,6 +636,8 @@ cudaError_t launch_gather(const float* X, const uint32_t* M, int N, const int64_
     stride *= full_dim[m];
     g.idx[m] = v.idx[m];
   }
+  g.nouter = v.numel / v.dim[0];
+  g.obase = obase;
   g.words = (v.numel + 31) / 32;
   const int64_t words_padded = (g.words + 3) / 4 * 4;
   // zero the padding words
@@ -616,6 +645,8 @@ cudaError_t launch_gather(const float* X, const uint32_t* M, int N, const int64_
     cudaError_t e = cudaMemsetAsync(PI + g.words, 0, (words_padded - g.words) * 4, st);
     if (e != cudaSuccess) return e;
   }
+  k_gather_base<<<(unsigned)imin((g.nouter + 255) / 256, 152 * 8), 256, 0, st>>>(g, obase);
+  note_launch();
   const unsigned blocks = (unsigned)imin((g.words + 7) / 8, 152 * 32);
   k_gather<<<blocks, 256, 0, st>>>(g);
   note_launch();

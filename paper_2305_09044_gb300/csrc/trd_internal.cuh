@@ -226,7 +226,7 @@ cudaError_t launch_reconstruct_mats(const void* A, const void* C, bool fp64, int
                                     int Kp, const float* Xref, float* out, double* err_part,
                                     int parts, cudaStream_t st);
 cudaError_t launch_gather(const float* X, const uint32_t* M, int N, const int64_t* full_dim,
-                          const View& v, float* XI, uint32_t* PI, cudaStream_t st);
+                          const View& v, float* XI, uint32_t* PI, int64_t* obase, cudaStream_t st);
 cudaError_t launch_set_scalar(double* p, double v, cudaStream_t st);
 cudaError_t launch_to_bf16_split(const void* src, bool src_double, int64_t rows, int Kp,
                                  int64_t ld_src, __nv_bfloat16* hi, __nv_bfloat16* lo,
@@ -239,21 +239,36 @@ cudaError_t launch_pass_simt(const PassArgs& a, bool is_double, bool rows_case, 
                              int splits, int* ctas_out, int* splits_out, cudaStream_t st);
 
 // pass_tc.cu (tcgen05 BF16 data passes)
-int tc_kpad(int Kp);   // padded contraction of the tensor-core passes (0: unsupported)
+// Operands of the tensor-core data passes: device arrays [rows][kpad] of BF16, or of FP32
+// holding TF32-rounded values (the TF32 kind).
+struct PassOperands {
+  const void* S_hi = nullptr;   // stationary operand, hi and lo splits
+  const void* S_lo = nullptr;
+  const void* S_h = nullptr;    // pass 2: step operand (TF32: its hi split)
+  const void* S_h_lo = nullptr; // pass 2, TF32 only: lo split of the step operand
+  const void* T_hi = nullptr;   // streaming operand, hi and lo splits
+  const void* T_lo = nullptr;
+  const void* T_hiT = nullptr;  // TF32 pass 1: the streaming splits transposed, [kpad][ldT]
+  const void* T_loT = nullptr;
+  int64_t ldT = 0;
+};
+// padded contraction of the tensor-core passes: BF16 64, 128 or 256, TF32 64; 0 = unsupported
+int tc_kpad(int Kp, bool tf32);
 int tc_bm();
-int tc_bn();
+int tc_bn(int kpad, bool tf32);   // streaming columns per tile of that configuration
 cudaError_t launch_wait_selftest(bool arrive, uint32_t limit, int* err, cudaStream_t st);
 cudaError_t launch_tc_prep(const float* src, int64_t rows, int Kp, __nv_bfloat16* hi, __nv_bfloat16* lo,
                            cudaStream_t st);
+cudaError_t launch_tc_prep_tf32(const float* src, int64_t rows, int Kp, float* hi, float* lo, cudaStream_t st,
+                                float* hiT = nullptr, float* loT = nullptr, int64_t ldT = 0);
 cudaError_t launch_mask_rows(const uint32_t* M, int64_t P_in, int64_t P_out, int64_t W, uint32_t* out,
                              cudaStream_t st);
 cudaError_t launch_mask_transpose(const uint32_t* M, int64_t P_in, int64_t P_out, int64_t WT, uint32_t* out,
                                   cudaStream_t st);
 cudaError_t launch_reduce_slots(const float* part, int64_t RB, int64_t NT, int G, int64_t P_stat, int Kp,
                                 double* out, cudaStream_t st);
-cudaError_t launch_pass_tc(bool rows_case, bool pass2, const __nv_bfloat16* S_hi, const __nv_bfloat16* S_lo,
-                           const __nv_bfloat16* S_h, const __nv_bfloat16* T_hi, const __nv_bfloat16* T_lo,
-                           const float* X, int64_t P_in, int64_t ldx, int64_t P_out, const uint32_t* Mst, int64_t W,
+cudaError_t launch_pass_tc(bool tf32, bool rows_case, bool pass2, const PassOperands& o, const float* X,
+                           int64_t P_in, int64_t ldx, int64_t P_out, const uint32_t* Mst, int64_t W,
                            int64_t P_stat, int64_t P_strm, int Kp, const double* sigma, float* Tpart,
                            double* stat_part, int* err, int G, bool full_stats, cudaStream_t st);
 cudaError_t launch_pad_rows(const float* X, int64_t P_in, int64_t P_out, int64_t ld, float* out, cudaStream_t st);

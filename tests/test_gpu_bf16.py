@@ -27,6 +27,9 @@ SHAPES = [
     ((32, 28, 20, 12), (8, 8, 16, 8)),      # K' = 128, K = 64 / 128
     ((23, 17, 9, 13), (2, 3, 4, 3)),        # odd inner block 391: data rows re-laid with stride 392
     ((30, 26, 22), (3, 2, 3)),              # inner block 30 (order 3)
+    ((40, 36, 32), (16, 16, 16)),           # K' = 256: 32-column tiles, step operand in TMEM
+    ((20, 18, 16, 14), (16, 8, 16, 8)),     # K' = 256 with K = 128, order 4
+    ((40, 48, 44), (12, 16, 12)),           # K' = 144 padded to 256, K = 192 / 192 / 144
 ]
 
 
