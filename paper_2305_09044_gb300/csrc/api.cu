@@ -128,6 +128,7 @@ struct Extra {
   uint64_t q_ver[kMaxN] = {};
   // sampled correntropy loss: cores in FP64, merged halves, their gradients, partials
   DevBuf smpZ[kMaxN], smpA, smpC, smpGA, smpGC, smpGAd, smpGCd, smpPre, smpPost, smpDpart, smpD, smpLoss;
+  DevBuf smpKa, smpKb, smpPa, smpPb, smpCa, smpCb, smpUa, smpUb, smpG;   // entry grouping
   // BF16 tensor-core operands and the padded mask rows of the current view
   DevBuf bShi, bSlo, bSh, bThi, bTlo, bTT;
   // observation bits re-laid per stationary index: [0] inner index along the outer one
@@ -1610,7 +1611,8 @@ void trd_destroy(trd_t* h) {
   for (DevBuf* b : xb) free_buf(*b);
   for (int k = 0; k < kMaxN; ++k) { free_buf(x->Eloc[k]); free_buf(x->tmpZ[k]); free_buf(x->smpZ[k]); }
   DevBuf* sb[] = {&x->smpA, &x->smpC, &x->smpGA, &x->smpGC, &x->smpGAd, &x->smpGCd, &x->smpPre, &x->smpPost,
-                  &x->smpDpart, &x->smpD, &x->smpLoss};
+                  &x->smpDpart, &x->smpD, &x->smpLoss, &x->smpKa, &x->smpKb, &x->smpPa, &x->smpPb,
+                  &x->smpCa, &x->smpCb, &x->smpUa, &x->smpUb, &x->smpG};
   for (DevBuf* b : sb) free_buf(*b);
   for (auto& p : x->pending) { x->ev_pool.push_back(p.a); x->ev_pool.push_back(p.b); }
   if (x->ev_open) x->ev_pool.push_back(x->ev_open);
@@ -2300,6 +2302,35 @@ static trd_status sampled_setup(trd_t* h, const void* const* cores_dev, int fp64
   return TRD_OK;
 }
 
+// The sampled entries grouped by their inner-block index a and outer-block index b.
+static trd_status sampled_order(trd_t* h, const int32_t* idx_dev, int64_t M, const Split& sp, const Split2& s2,
+                                bool fp64, SampledWork& wk) {
+  Extra* x = X_(h);
+  if (M > INT32_MAX || sp.P_in > INT32_MAX || sp.P_out > INT32_MAX)
+    return set_err(h, TRD_ENOTIMPL, "sampled loss supports fewer than 2^31 entries and block sizes below 2^31");
+  if (sp.Kp > 512) return set_err(h, TRD_ENOTIMPL, "sampled loss supports r_1 r_c <= 512");
+  TRY(ensure(h, x->smpKa, sizeof(int32_t) * (size_t)M));
+  TRY(ensure(h, x->smpKb, sizeof(int32_t) * (size_t)M));
+  TRY(ensure(h, x->smpPa, sizeof(int32_t) * (size_t)M));
+  TRY(ensure(h, x->smpPb, sizeof(int32_t) * (size_t)M));
+  TRY(ensure(h, x->smpG, (fp64 ? sizeof(double) : sizeof(float)) * (size_t)M));
+  TRY(ensure(h, x->smpCa, sizeof(uint32_t) * (size_t)sp.P_in));
+  TRY(ensure(h, x->smpCb, sizeof(uint32_t) * (size_t)sp.P_out));
+  TRY(ensure(h, x->smpUa, sizeof(uint32_t) * (size_t)sp.P_in));
+  TRY(ensure(h, x->smpUb, sizeof(uint32_t) * (size_t)sp.P_out));
+  wk.ka = (int32_t*)x->smpKa.p;
+  wk.kb = (int32_t*)x->smpKb.p;
+  wk.perm_a = (int32_t*)x->smpPa.p;
+  wk.perm_b = (int32_t*)x->smpPb.p;
+  wk.cnt_a = (uint32_t*)x->smpCa.p;
+  wk.cnt_b = (uint32_t*)x->smpCb.p;
+  wk.cur_a = (uint32_t*)x->smpUa.p;
+  wk.cur_b = (uint32_t*)x->smpUb.p;
+  wk.g = x->smpG.p;
+  CK(launch_sampled_order(idx_dev, &s2, M, sp.P_in, sp.P_out, wk, h->stream), "sampled entry grouping");
+  return TRD_OK;
+}
+
 trd_status trd_sampled_fwd(trd_t* h, const void* const* cores_dev, const int32_t* idx_dev, const void* x_dev,
                            int64_t M, double sigma, int fp64, void* resid_dev, double* loss_out) {
   TRY(check_handle(h));
@@ -2311,10 +2342,12 @@ trd_status trd_sampled_fwd(trd_t* h, const void* const* cores_dev, const int32_t
   Split sp;
   Split2 s2;
   TRY(sampled_setup(h, cores_dev, fp64, Zc, sp, s2));
-  const int parts = 4 * h->num_sms;
+  const int parts = 8 * h->num_sms;
   TRY(ensure(h, x->smpLoss, sizeof(double) * parts));
-  CK(launch_sampled_kernel(x->smpA.p, x->smpC.p, fp64 != 0, sp.Kp, idx_dev, &s2, x_dev, M, sigma, resid_dev,
-                           (double*)x->smpLoss.p, parts, false, 0.0, nullptr, nullptr, h->stream),
+  SampledWork wk;
+  TRY(sampled_order(h, idx_dev, M, sp, s2, fp64 != 0, wk));
+  CK(launch_sampled_rows(x->smpA.p, x->smpC.p, fp64 != 0, sp.Kp, x_dev, M, sp.P_in, sigma, resid_dev,
+                         (double*)x->smpLoss.p, parts, false, 0.0, nullptr, nullptr, wk, h->stream),
      "sampled forward");
   std::vector<double> lp((size_t)parts);
   CK(cudaMemcpyAsync(lp.data(), x->smpLoss.p, sizeof(double) * parts, cudaMemcpyDeviceToHost, h->stream),
@@ -2345,10 +2378,12 @@ trd_status trd_sampled_bwd(trd_t* h, const void* const* cores_dev, const int32_t
   TRY(ensure(h, x->smpGC, e * sp.P_out * sp.Kp));
   CK(cudaMemsetAsync(x->smpGA.p, 0, e * sp.P_in * sp.Kp, h->stream), "clear gA");
   CK(cudaMemsetAsync(x->smpGC.p, 0, e * sp.P_out * sp.Kp, h->stream), "clear gC");
-  const int parts = 4 * h->num_sms;
-  CK(launch_sampled_kernel(x->smpA.p, x->smpC.p, dbl, sp.Kp, idx_dev, &s2, x_dev, M, sigma, nullptr, nullptr, parts,
-                           true, g_scale, x->smpGA.p, x->smpGC.p, h->stream),
-     "sampled adjoint scatter");
+  const int parts = 8 * h->num_sms;
+  SampledWork wk;
+  TRY(sampled_order(h, idx_dev, M, sp, s2, dbl, wk));
+  CK(launch_sampled_rows(x->smpA.p, x->smpC.p, dbl, sp.Kp, x_dev, M, sp.P_in, sigma, nullptr, nullptr, parts, true,
+                         g_scale, x->smpGA.p, x->smpGC.p, wk, h->stream),
+     "sampled adjoint");
   // the back-contraction reads FP64 halves
   const double* gAd = (const double*)x->smpGA.p;
   const double* gCd = (const double*)x->smpGC.p;

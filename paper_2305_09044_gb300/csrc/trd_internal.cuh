@@ -350,10 +350,18 @@ struct Split2 {
   int64_t dim[kMaxN];
   int* err;                          // device status word (DEV_BOUNDS on a bad index)
 };
-cudaError_t launch_sampled_kernel(const void* A, const void* C, bool fp64, int Kp, const int32_t* idx,
-                                  const Split2* sp, const void* x, int64_t M, double sigma, void* resid,
-                                  double* loss_part, int parts, bool backward, double g_scale, void* gA, void* gC,
-                                  cudaStream_t st);
+// Work arrays of the sampled loss: per entry its block indices (ka, kb), the entry numbers
+// grouped by a and by b, per-block counts and cursors, and the per-entry adjoint factor g.
+struct SampledWork {
+  int32_t *ka = nullptr, *kb = nullptr, *perm_a = nullptr, *perm_b = nullptr;
+  uint32_t *cnt_a = nullptr, *cnt_b = nullptr, *cur_a = nullptr, *cur_b = nullptr;
+  void* g = nullptr;
+};
+cudaError_t launch_sampled_order(const int32_t* idx, const Split2* sp, int64_t M, int64_t P_in, int64_t P_out,
+                                 const SampledWork& wk, cudaStream_t st);
+cudaError_t launch_sampled_rows(const void* A, const void* C, bool fp64, int Kp, const void* x, int64_t M,
+                                int64_t P_in, double sigma, void* resid, double* loss_part, int parts, bool backward,
+                                double g_scale, void* gA, void* gC, const SampledWork& wk, cudaStream_t st);
 cudaError_t launch_to_double(const float* src, int64_t n, double* dst, cudaStream_t st);
 cudaError_t launch_from_double(const double* src, int64_t n, void* dst, bool fp64, cudaStream_t st);
 
