@@ -57,6 +57,10 @@ def parse():
                     help="skip the other north-star configurations (30^3, 64^5, 1024x1024x256, sampled 128^4)")
     ap.add_argument("--configs-only", action="store_true",
                     help="run only the other configurations and print them as one JSON line")
+    ap.add_argument("--only-config", default=None, choices=[None, "tiny3", "cfg64", "video", "grad128"],
+                    help="with --configs-only: run one configuration (short runs for profiling)")
+    ap.add_argument("--conv-iters", type=int, default=None,
+                    help="override the iteration limit of the configurations' time-to-1e-3 runs")
     ap.add_argument("--cpu-budget", type=float, default=3.0,
                     help="seconds of oracle work per configuration and thread setting (0: skip)")
     ap.add_argument("--oracle-probe", default=None, help=argparse.SUPPRESS)
@@ -203,8 +207,9 @@ def recorded_traffic(prec):
     when the kernel source changed since those counters were taken."""
     import hashlib
     import re
-    name, src = (("k_pass_tc_100x4_rank8.md", "pass_tc.cu") if prec == "bf16"
-                 else ("k_pass_simt_100x4_rank8.md", "pass_simt.cu"))
+    name, src = {"bf16": ("k_pass_tc_100x4_rank8.md", "pass_tc.cuh"),
+                 "tf32x3": ("k_pass_tc_tf32_100x4_rank8.md", "pass_tc.cuh")}.get(
+        prec, ("k_pass_simt_100x4_rank8.md", "pass_simt.cu"))
     try:
         txt = open(os.path.join(ROOT, "profiles", name)).read()
         m = re.search(r"traffic_bytes_per_launch: (\d+) .*source sha1 ([0-9a-f]+)", txt)
@@ -340,7 +345,7 @@ def run_ours(args, rank, world, local):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[prec],
+           "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp64": "f64", "tf32x3": "tf32x3"}[prec],
            "data": "synthetic", "config": workload_config(w, prec), "iters_per_s": 1e3 / ms_step,
            "roofline": roofline(prec, prof, w, measured), "e2e": e2e, "gpu_launches": launches, "clocks": ck}
     if measured:
@@ -387,10 +392,22 @@ def other_configs(args, torch, measured):
     128^4 forward + backward."""
     pk, _ = peaks()
     budget = 0.0 if args.no_cpu_baseline else args.cpu_budget
-    res = {"tiny3": run_tiny(torch, pk, budget)}
-    res["cfg64"] = run_sketched(torch, pk, "cfg64", ["bf16"], 10, budget, conv_iters=60, conv_budget=6.0)
-    res["video"] = run_sketched(torch, pk, "video", ["bf16", "fp32"], 10, budget, conv_iters=60, conv_budget=6.0)
-    res["grad128"] = run_sampled(torch, pk, 5, budget)
+    want = [args.only_config] if args.only_config else ["tiny3", "cfg64", "video", "grad128"]
+    ci = args.conv_iters
+    res = {}
+    if "tiny3" in want:
+        res["tiny3"] = run_tiny(torch, pk, budget)
+    if "cfg64" in want:
+        # from the random initialisation the 64^5 rank-10 problem sits near relative error 1 for
+        # tens of iterations before it converges (the oracle shows the same plateau on small
+        # analogues), so its time to 1e-3 gets a longer iteration limit
+        res["cfg64"] = run_sketched(torch, pk, "cfg64", ["bf16"], 10, budget,
+                                    conv_iters=400 if ci is None else ci, conv_budget=4.0)
+    if "video" in want:
+        res["video"] = run_sketched(torch, pk, "video", ["bf16", "fp32"], 10, budget,
+                                    conv_iters=60 if ci is None else ci, conv_budget=6.0)
+    if "grad128" in want:
+        res["grad128"] = run_sampled(torch, pk, 5, budget)
     return res
 
 

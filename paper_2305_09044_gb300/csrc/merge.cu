@@ -593,35 +593,53 @@ __global__ void k_gather_base(GatherArgs g, int64_t* __restrict__ obase) {
 }
 
 // RStS gather: X_I[l] and the observation bit of sketch entry l (a warp per 32 consecutive
-// entries, whose bits one ballot packs).  Entry l is position i_1 = l mod s_1 of fibre
-// o = l div s_1; the warp divides once and steps its lanes across at most a few fibres, so
-// consecutive lanes read consecutive positions of X along mode 1 (or its sampled indices).
+// entries, whose bits one ballot packs; each warp takes GW such words at once so that every
+// lane has GW independent loads in flight).  Entry l is position i_1 = l mod s_1 of fibre
+// o = l div s_1; the warp divides once per word and steps its lanes across at most a few
+// fibres, so consecutive lanes read consecutive positions of X along mode 1 (or its sampled
+// indices).
+constexpr int GW = 4;
 __global__ void k_gather(GatherArgs g) {
   const int lane = threadIdx.x & 31;
   const int64_t wpb = blockDim.x >> 5;
   const int64_t s1 = g.sdim[0];
   const int32_t* idx1 = g.idx[0];
-  for (int64_t wd = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); wd < g.words;
-       wd += (int64_t)gridDim.x * wpb) {
-    const int64_t l = wd * 32 + lane;
-    int64_t r0;
-    const int64_t o0 = qdivmod(wd * 32, s1, r0);     // warp-uniform
-    int64_t i1 = r0 + lane, o = o0;
-    if (s1 >= 32) {
-      if (i1 >= s1) { i1 -= s1; ++o; }
-    } else {
-      int64_t r;
-      o += qdivmod(i1, s1, r);
-      i1 = r;
+  for (int64_t wd0 = ((int64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * GW; wd0 < g.words;
+       wd0 += (int64_t)gridDim.x * wpb * GW) {
+    int64_t full[GW];
+    bool live[GW];
+#pragma unroll
+    for (int q = 0; q < GW; ++q) {
+      const int64_t wd = wd0 + q;
+      const int64_t l = wd * 32 + lane;
+      int64_t r0;
+      const int64_t o0 = qdivmod(wd * 32, s1, r0);     // warp-uniform
+      int64_t i1 = r0 + lane, o = o0;
+      if (s1 >= 32) {
+        if (i1 >= s1) { i1 -= s1; ++o; }
+      } else {
+        int64_t r;
+        o += qdivmod(i1, s1, r);
+        i1 = r;
+      }
+      live[q] = wd < g.words && l < g.numel;
+      full[q] = live[q] ? g.obase[o] + (idx1 ? (int64_t)idx1[i1] : i1) : 0;
     }
-    bool obs = false;
-    if (l < g.numel) {
-      const int64_t full = g.obase[o] + (idx1 ? (int64_t)idx1[i1] : i1);
-      g.XI[l] = g.X[full];
-      obs = g.M ? ((g.M[full >> 5] >> (full & 31)) & 1u) : true;
+    float xv[GW];
+    uint32_t mw[GW];
+#pragma unroll
+    for (int q = 0; q < GW; ++q) {
+      xv[q] = live[q] ? __ldg(g.X + full[q]) : 0.f;
+      mw[q] = (live[q] && g.M) ? __ldg(g.M + (full[q] >> 5)) : 0xffffffffu;
     }
-    const unsigned bits = __ballot_sync(0xffffffffu, obs);
-    if (lane == 0) g.PI[wd] = bits;
+#pragma unroll
+    for (int q = 0; q < GW; ++q) {
+      const int64_t wd = wd0 + q;
+      if (live[q]) g.XI[wd * 32 + lane] = xv[q];
+      const bool obs = live[q] && ((mw[q] >> (full[q] & 31)) & 1u);
+      const unsigned bits = __ballot_sync(0xffffffffu, obs);
+      if (lane == 0 && wd < g.words) g.PI[wd] = bits;
+    }
   }
 }
 
@@ -647,7 +665,7 @@ cudaError_t launch_gather(const float* X, const uint32_t* M, int N, const int64_
   }
   k_gather_base<<<(unsigned)imin((g.nouter + 255) / 256, 152 * 8), 256, 0, st>>>(g, obase);
   note_launch();
-  const unsigned blocks = (unsigned)imin((g.words + 7) / 8, 152 * 32);
+  const unsigned blocks = (unsigned)imin((g.words + 8 * GW - 1) / (8 * GW), 152 * 16);
   k_gather<<<blocks, 256, 0, st>>>(g);
   note_launch();
   return cudaGetLastError();

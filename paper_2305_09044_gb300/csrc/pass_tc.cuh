@@ -713,6 +713,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const float sk = isinf(sg) ? 0.0f : (float)sqrt(1.4426950408889634 / (2.0 * sg * sg));
     constexpr uint32_t CMASK = CPW == 32 ? 0xffffffffu : ((1u << CPW) - 1u);
     float sw = 0.f, se2 = 0.f, swe2 = 0.f, sden = 0.f;
+    // the lean epilogue works on slot pairs with packed FP32x2 arithmetic and keeps its running
+    // sum (w e^2 in pass 1, w D2^2 in pass 2) in two packed accumulators: four independent
+    // chains instead of one FMA chain through every slot
+    float2 acc2a = make_float2(0.f, 0.f), acc2b = make_float2(0.f, 0.f);
+    const float2 sk2 = make_float2(sk, sk), nsk2 = make_float2(-sk, -sk), neg1 = make_float2(-1.f, -1.f);
     uint32_t nobs = 0, nnf = 0, nslot = 0;
     constexpr int KPW = KP / NGRP;                  // contraction columns of T per warp
     constexpr bool CHUNKED = TF32 && !PASS2;        // T summed over chunks in registers
@@ -838,20 +843,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           // lean: only what the update needs (y, or den) and the objective sum w e^2; a
           // non-finite residual on an observed slot propagates as NaN and rejects the step.
           // Pass 1 masks the residual first (e' = 0 off the mask, so w(e') = 1 and y = w e' = 0
-          // without further selects); pass 2 masks the weight.
+          // without further selects); pass 2 masks the weight.  w = exp2(-(e s)^2).
 #pragma unroll
-          for (int j = 0; j < CPW; ++j) {
-            const bool bit = (seen >> j) & 1u;
+          for (int j = 0; j < CPW; j += 2) {
+            const bool b0 = (seen >> j) & 1u, b1 = (seen >> (j + 1)) & 1u;
+            float2 e2 = __ffma2_rn(make_float2(xh[j], xh[j + 1]), neg1, make_float2(xv[j], xv[j + 1]));
+            if (!PASS2) {
+              e2.x = b0 ? e2.x : 0.f;
+              e2.y = b1 ? e2.y : 0.f;
+            }
+            const float2 m2 = __fmul2_rn(__fmul2_rn(e2, sk2), __fmul2_rn(e2, nsk2));   // -(e s)^2
             if (PASS2) {
-              const float t = (xv[j] - xh[j]) * sk;
-              const float w = bit ? fast_ex2(-(t * t)) : 0.f;
-              sden = fmaf(w * dh[j], dh[j], sden);
+              const float2 w2 = make_float2(b0 ? fast_ex2(m2.x) : 0.f, b1 ? fast_ex2(m2.y) : 0.f);
+              const float2 d2 = make_float2(dh[j], dh[j + 1]);
+              if ((j >> 1) & 1) acc2b = __ffma2_rn(__fmul2_rn(w2, d2), d2, acc2b);
+              else acc2a = __ffma2_rn(__fmul2_rn(w2, d2), d2, acc2a);
             } else {
-              const float e = bit ? xv[j] - xh[j] : 0.f;
-              const float t = e * sk;
-              const float y = fast_ex2(-(t * t)) * e;
-              swe2 = fmaf(y, e, swe2);
-              xv[j] = y;
+              const float2 y2 = __fmul2_rn(make_float2(fast_ex2(m2.x), fast_ex2(m2.y)), e2);
+              if ((j >> 1) & 1) acc2b = __ffma2_rn(y2, e2, acc2b);
+              else acc2a = __ffma2_rn(y2, e2, acc2a);
+              xv[j] = y2.x;
+              xv[j + 1] = y2.y;
             }
           }
         }
@@ -915,7 +927,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
     }
-    if (!FULL) nnf = (isfinite(swe2) && isfinite(sden)) ? 0u : 1u;
+    if (!FULL) {
+      const float lean = (acc2a.x + acc2b.x) + (acc2a.y + acc2b.y);
+      if (PASS2) sden += lean;
+      else swe2 += lean;
+      nnf = (isfinite(swe2) && isfinite(sden)) ? 0u : 1u;
+    }
     // statistics: warp shuffle, then one row per CTA (fixed order)
     const double fv[7] = {(double)sw, (double)se2, (double)swe2, (double)nobs, (double)nnf, (double)nslot,
                           (double)sden};

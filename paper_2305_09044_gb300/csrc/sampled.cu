@@ -125,17 +125,33 @@ __global__ void k_smp_rows_a(const T* __restrict__ A, const T* __restrict__ C, i
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const T nk = (T)(-1.0 / (2.0 * sigma * sigma));
+  const T gs = (T)(-g_scale);     // g = g_scale d loss / d x_hat = -g_scale w e
   const int nv = (Kp + 31) >> 5;
+  // e, w and g are the same on every lane after the shuffle reduction and are formed in T: the
+  // FP64 unit (which also converts between FP32 and FP64) issues at a small fraction of the
+  // FP32 rate here, so the FP32 path widens only the per-item loss sum
   double loss = 0.0;
   for (int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w0 * kSmpChunk < n; w0 += warps) {
     const int64_t p0 = w0 * kSmpChunk, p1 = imin(n, p0 + kSmpChunk);
     int32_t cur = -1;
+    T lsum = T(0);                // sum of (1 - w) over this work item
     T av[kSmpMaxV], acc[kSmpMaxV];
 #pragma unroll
     for (int v = 0; v < kSmpMaxV; ++v) av[v] = acc[v] = T(0);
+    // the next entry's number, block indices and value are loaded one step ahead, off the
+    // dependent chain perm -> (a, b) -> rows of the current entry
+    int32_t mn = perm_a[p0];
+    int32_t an = ka[mn], bn = kb[mn];
+    T xn = x[mn];
     for (int64_t p = p0; p < p1; ++p) {
-      const int32_t m = perm_a[p];
-      const int32_t a = ka[m], b = kb[m];
+      const int32_t m = mn, a = an, b = bn;
+      const T xm = xn;
+      if (p + 1 < p1) {
+        mn = perm_a[p + 1];
+        an = ka[mn];
+        bn = kb[mn];
+        xn = x[mn];
+      }
       if (a != cur) {
         if (backward && cur >= 0) {
 #pragma unroll
@@ -161,14 +177,12 @@ __global__ void k_smp_rows_a(const T* __restrict__ A, const T* __restrict__ C, i
         part = fma(av[v], cv[v], part);
       }
       for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      const T e = x[m] - part;
+      const T e = xm - part;
       const T w = texp(e * e * nk);
-      if (lane == 0) {
-        loss += sigma * sigma * (1.0 - (double)w);
-        if (resid) resid[m] = e;
-      }
+      lsum += T(1) - w;
+      if (lane == 0 && resid) resid[m] = e;
       if (backward) {
-        const T g = (T)(g_scale * -((double)w * (double)e));
+        const T g = gs * (w * e);
         if (lane == 0) garr[m] = g;
 #pragma unroll
         for (int v = 0; v < kSmpMaxV; ++v) acc[v] = fma(g, cv[v], acc[v]);
@@ -181,7 +195,9 @@ __global__ void k_smp_rows_a(const T* __restrict__ A, const T* __restrict__ C, i
         if (v < nv && k < Kp) atomicAdd(gA + (int64_t)cur * Kp + k, acc[v]);
       }
     }
+    loss += (double)lsum;
   }
+  loss *= sigma * sigma;
   if (!loss_part) return;
   if (lane == 0) sred[threadIdx.x >> 5] = loss;
   __syncthreads();
@@ -208,9 +224,18 @@ __global__ void k_smp_rows_b(const T* __restrict__ A, int Kp, const int32_t* __r
     T acc[kSmpMaxV];
 #pragma unroll
     for (int v = 0; v < kSmpMaxV; ++v) acc[v] = T(0);
+    int32_t mn = perm_b[p0];
+    int32_t an = ka[mn], bn = kb[mn];
+    T gn = garr[mn];
     for (int64_t p = p0; p < p1; ++p) {
-      const int32_t m = perm_b[p];
-      const int32_t b = kb[m], a = ka[m];
+      const int32_t b = bn, a = an;
+      const T g = gn;
+      if (p + 1 < p1) {
+        mn = perm_b[p + 1];
+        an = ka[mn];
+        bn = kb[mn];
+        gn = garr[mn];
+      }
       if (b != cur) {
         if (cur >= 0) {
 #pragma unroll
@@ -222,7 +247,6 @@ __global__ void k_smp_rows_b(const T* __restrict__ A, int Kp, const int32_t* __r
         }
         cur = b;
       }
-      const T g = garr[m];
 #pragma unroll
       for (int v = 0; v < kSmpMaxV; ++v) {
         const int k = lane + 32 * v;
