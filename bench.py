@@ -391,6 +391,8 @@ def other_configs(args, torch, measured):
     baseline): 30^3 FP64 trajectory, 64^5 and 1024 x 1024 x 256 RStS iterations, sampled
     128^4 forward + backward."""
     pk, _ = peaks()
+    if measured:
+        _MEASURED.update(measured)
     budget = 0.0 if args.no_cpu_baseline else args.cpu_budget
     want = [args.only_config] if args.only_config else ["tiny3", "cfg64", "video", "grad128"]
     ci = args.conv_iters
@@ -757,6 +759,36 @@ def pass_roofline(ph, slots_per_pass, pk, label, steps=2, Kp=None, tf32_peak=Non
     return r
 
 
+_MEASURED = {}
+
+
+def measured_fp64(pk):
+    return _MEASURED.get("fp64_tflops") or 1.25
+
+
+def fp64_roofline(w, ph, fp64_peak, steps=2):
+    """FP64 factorisation and solves of the scaled step (Eq. sg / Eq. hI) per iteration, from
+    the traced phases: K^3 / 3 flops per Cholesky (K = r_k r_{k+1}), 2 I_k K^2 per pair of
+    substitutions, against the FP64 GEMM peak measured in this run.  Latency-bound at these
+    sizes (K <= 400); reported so the fraction is on record."""
+    N = len(w.dims)
+    Ks = [w.ranks[k] * w.ranks[(k + 1) % N] for k in range(N)]
+    chol = sum(K ** 3 / 3.0 for K in Ks)
+    solve = sum(2.0 * w.dims[k] * Ks[k] ** 2 for k in range(N))
+    c_ms = ph.get("cholesky_ms", 0.0) / steps
+    s_ms = ph.get("solve_ms", 0.0) / steps
+    r = {"K": Ks, "peak_fp64_tflops": fp64_peak, "peak_source": "measured in this run (cuBLAS FP64 GEMM)"}
+    if c_ms > 0:
+        r["cholesky_ms_per_iter"] = c_ms
+        r["cholesky_tflops"] = chol / (c_ms / 1e3) / 1e12
+        r["cholesky_frac"] = r["cholesky_tflops"] / fp64_peak
+    if s_ms > 0:
+        r["solve_ms_per_iter"] = s_ms
+        r["solve_tflops"] = solve / (s_ms / 1e3) / 1e12
+        r["solve_frac"] = r["solve_tflops"] / fp64_peak
+    return r
+
+
 def run_tiny(torch, pk, budget):
     """North-star configuration 1: 30^3 rank 3, 30 % missing, 10 % outliers, adaptive width,
     100 iterations on the FP64 path (launch-latency bound)."""
@@ -829,6 +861,7 @@ def run_sketched(torch, pk, name, precs, steps, budget, conv_iters, conv_budget)
                                       "unit": "GB/s", "frac": gbytes / (gather_ms / 1e3) / 1e9 / pk["hbm_gbs"],
                                       "ms_per_launch": gather_ms,
                                       "algorithmic_bytes_per_launch": gbytes}
+        leg["fp64_kernels"] = fp64_roofline(w, ph, measured_fp64(pk))
         t.init_cores(w.init_seed)
         leg["time_to_rel_err_1e-3"] = converge_steps(t, Xt, kw, conv_iters, conv_budget, torch)
         out[prec] = leg
