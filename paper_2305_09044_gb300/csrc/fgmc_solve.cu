@@ -513,44 +513,55 @@ __device__ __forceinline__ double rsqrt_pivot(double p) {
   return fma(0.5 * y, e, y);
 }
 
-// one warp: lane i holds row j0 + i of the diagonal block (columns j0 .. j0 + 31)
-__global__ void __launch_bounds__(32) k_bchol_diag(double* __restrict__ W, double* __restrict__ rdiag, int K,
-                                                   int j0, int* __restrict__ dstatus) {
+// Cholesky of the 32 x 32 diagonal block at (j0, j0), in shared memory, 128 threads.  The FP64
+// unit issues about one warp instruction per 70 clocks per scheduler on this GPU, so the
+// trailing update of every pivot is spread over four warps (all four schedulers): thread t
+// owns row i = t / 4 of the block and updates its columns j < m <= i with stride 4.  Rows and
+// columns beyond the matrix (a ragged last block) are identity.  rdiag receives 1 / L_jj.
+constexpr int BCH_DT = 128;
+__global__ void __launch_bounds__(BCH_DT) k_bchol_diag(double* __restrict__ W, double* __restrict__ rdiag, int K,
+                                                       int j0, int* __restrict__ dstatus) {
   if (*(volatile int*)dstatus & DEV_SINGULAR) return;
-  const int lane = threadIdx.x;
+  __shared__ double a[BCH_NB][BCH_NB + 1];
+  __shared__ double rr[BCH_NB];
+  __shared__ int s_bad;
+  const int t = threadIdx.x;
   const int nb = imin(BCH_NB, K - j0);
-  const bool live = lane < nb;
-  const double* row = W + (int64_t)(j0 + lane) * K + j0;
-  double a[BCH_NB];
-#pragma unroll
-  for (int m = 0; m < BCH_NB; ++m) a[m] = live ? (m <= lane ? row[m] : 0.0) : (m == lane ? 1.0 : 0.0);
-  bool bad = false;
-  double myr = 1.0;
-#pragma unroll
-  for (int j = 0; j < BCH_NB; ++j) {
-    const double piv = __shfl_sync(0xffffffffu, a[j], j);
-    bad |= !(piv > 0.0) || !isfinite(piv);
-    const double rj = bad ? 1.0 : rsqrt_pivot(piv);
-    const double dj = bad ? 1.0 : piv * rj;
-    if (lane > j) a[j] *= rj;
-    if (lane == j) { a[j] = dj; myr = rj; }
-#pragma unroll
-    for (int m = j + 1; m < BCH_NB; ++m) {
-      const double lmj = __shfl_sync(0xffffffffu, a[j], m);
-      if (lane >= m) a[m] = fma(-a[j], lmj, a[m]);
-    }
+  for (int e = t; e < BCH_NB * BCH_NB; e += BCH_DT) {
+    const int i = e / BCH_NB, m = e % BCH_NB;
+    a[i][m] = (i < nb && m < nb) ? (m <= i ? W[(int64_t)(j0 + i) * K + j0 + m] : 0.0) : (i == m ? 1.0 : 0.0);
   }
-  if (bad) {
-    if (lane == 0) atomicOr(dstatus, (int)DEV_SINGULAR);
+  if (t == 0) s_bad = 0;
+  __syncthreads();
+  const int i = t >> 2, sub = t & 3;    // this thread's row and column phase
+  for (int j = 0; j < BCH_NB; ++j) {
+    if (t == 0) {
+      const double piv = a[j][j];
+      const bool bad = !(piv > 0.0) || !isfinite(piv);
+      if (bad) s_bad = 1;
+      const double rj = bad ? 1.0 : rsqrt_pivot(piv);
+      rr[j] = rj;
+      a[j][j] = bad ? 1.0 : piv * rj;
+    }
+    __syncthreads();
+    // column j below the pivot: L_ij = a_ij / L_jj (row i's four threads read it after the barrier)
+    if (sub == 0 && i > j) a[i][j] *= rr[j];
+    __syncthreads();
+    if (i > j) {
+      const double lij = a[i][j];
+      for (int m = j + 1 + sub; m <= i; m += 4) a[i][m] = fma(-lij, a[m][j], a[i][m]);
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (t == 0) atomicOr(dstatus, (int)DEV_SINGULAR);
     return;
   }
-  if (live) {
-    double* wr = W + (int64_t)(j0 + lane) * K + j0;
-#pragma unroll
-    for (int m = 0; m < BCH_NB; ++m)
-      if (m <= lane) wr[m] = a[m];
-    rdiag[j0 + lane] = myr;
+  for (int e = t; e < BCH_NB * BCH_NB; e += BCH_DT) {
+    const int r = e / BCH_NB, m = e % BCH_NB;
+    if (r < nb && m <= r) W[(int64_t)(j0 + r) * K + j0 + m] = a[r][m];
   }
+  if (t < nb) rdiag[j0 + t] = rr[t];
 }
 
 // rows i >= j0 + 32: row i of the panel, x, solves x L11^T = a (forward substitution in the
@@ -637,7 +648,7 @@ cudaError_t launch_cholesky(const double* G, int K, double lambda, double* L, do
   k_bchol_init<<<(unsigned)imin((n + 255) / 256, 1024), 256, 0, st>>>(G, K, lambda, L, scal);
   note_launch();
   for (int j0 = 0; j0 < K; j0 += BCH_NB) {
-    k_bchol_diag<<<1, 32, 0, st>>>(L, rdiag, K, j0, dstatus);
+    k_bchol_diag<<<1, BCH_DT, 0, st>>>(L, rdiag, K, j0, dstatus);
     note_launch();
     const int rest = K - j0 - BCH_NB;
     if (rest <= 0) break;
@@ -688,14 +699,113 @@ __global__ void k_solve_rows(const double* __restrict__ L, const double* __restr
   }
 }
 
+// The same substitutions with the row held in registers: lane l keeps entries l + 32 v (v < NV,
+// K <= 32 NV), the solved entry of step j is broadcast by a shuffle from lane j mod 32, and the
+// factor's next column (forward) or row (backward) is loaded one step ahead so that its L2
+// latency overlaps the current step.  The FP64 pipe (one warp-DFMA per scheduler every few tens
+// of cycles on this part) is then the bound instead of shared-memory round trips and barriers.
+// Per entry the arithmetic and its order are those of k_solve_rows (fma(-L, y, b), j ascending
+// then descending), so both kernels give identical results.
+template <int NV>
+__global__ void __launch_bounds__(32) k_solve_rows_reg(const double* __restrict__ L, const double* __restrict__ d,
+                                                       double* __restrict__ h, int K, int64_t rows) {
+  const int lane = threadIdx.x & 31;
+  const double* rdiag = L + (int64_t)K * K;
+  const double* Lc = rdiag + K;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    double b[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int m = lane + 32 * v;
+      b[v] = m < K ? d[row * K + m] : 0.0;
+    }
+    // forward: y_j = b_j / L_jj, then b_m -= L_mj y_j for m > j; step j = 32 vb + jj
+#pragma unroll
+    for (int vb = 0; vb < NV; ++vb) {
+      const int jend = min(32, K - 32 * vb);
+      if (jend <= 0) continue;
+      double c[NV], cn[NV];
+#pragma unroll
+      for (int v = vb; v < NV; ++v) {
+        const int m = lane + 32 * v;
+        c[v] = m < K ? Lc[(int64_t)(32 * vb) * K + m] : 0.0;
+      }
+      double rd = rdiag[32 * vb];
+      for (int jj = 0; jj < jend; ++jj) {
+        const int j = 32 * vb + jj;
+        const bool more = jj + 1 < jend;
+#pragma unroll
+        for (int v = vb; v < NV; ++v) {
+          const int m = lane + 32 * v;
+          cn[v] = (more && m < K) ? Lc[(int64_t)(j + 1) * K + m] : 0.0;
+        }
+        const double rdn = more ? rdiag[j + 1] : 0.0;
+        const double y = __shfl_sync(0xffffffffu, b[vb], jj) * rd;
+        const double t = fma(-c[vb], y, b[vb]);
+        b[vb] = lane == jj ? y : (lane > jj ? t : b[vb]);
+#pragma unroll
+        for (int v = vb + 1; v < NV; ++v) b[v] = fma(-c[v], y, b[v]);
+#pragma unroll
+        for (int v = vb; v < NV; ++v) c[v] = cn[v];
+        rd = rdn;
+      }
+    }
+    // backward: h_j = b_j / L_jj, then b_m -= L_jm h_j for m < j; j descending
+#pragma unroll
+    for (int vb = NV - 1; vb >= 0; --vb) {
+      const int jend = min(32, K - 32 * vb);
+      if (jend <= 0) continue;
+      double c[NV], cn[NV];
+      const int jt = 32 * vb + jend - 1;
+#pragma unroll
+      for (int v = 0; v <= vb; ++v) {
+        const int m = lane + 32 * v;
+        c[v] = m < jt ? L[(int64_t)jt * K + m] : 0.0;
+      }
+      double rd = rdiag[jt];
+      for (int jj = jend - 1; jj >= 0; --jj) {
+        const int j = 32 * vb + jj;
+        const bool more = jj > 0;
+#pragma unroll
+        for (int v = 0; v <= vb; ++v) {
+          const int m = lane + 32 * v;
+          cn[v] = (more && m < j - 1) ? L[(int64_t)(j - 1) * K + m] : 0.0;
+        }
+        const double rdn = more ? rdiag[j - 1] : 0.0;
+        const double y = __shfl_sync(0xffffffffu, b[vb], jj) * rd;
+        const double t = fma(-c[vb], y, b[vb]);
+        b[vb] = lane == jj ? y : (lane < jj ? t : b[vb]);
+#pragma unroll
+        for (int v = 0; v < vb; ++v) b[v] = fma(-c[v], y, b[v]);
+#pragma unroll
+        for (int v = 0; v <= vb; ++v) c[v] = cn[v];
+        rd = rdn;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int m = lane + 32 * v;
+      if (m < K) h[row * K + m] = b[v];
+    }
+  }
+}
+
 cudaError_t launch_solve_rows(const double* L, const double* d, double* h, int K, int64_t rows,
                               cudaStream_t st) {
   const int warps = 1;
   const size_t smem = (size_t)warps * K * sizeof(double);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_solve_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const unsigned blocks = (unsigned)imin((rows + warps - 1) / warps, 8192);
-  k_solve_rows<<<blocks, warps * 32, smem, st>>>(L, d, h, K, rows);
+  if (K <= 256) {
+    k_solve_rows_reg<8><<<blocks, 32, 0, st>>>(L, d, h, K, rows);
+  } else if (K <= 416) {
+    k_solve_rows_reg<13><<<blocks, 32, 0, st>>>(L, d, h, K, rows);
+  } else if (K <= 512) {
+    k_solve_rows_reg<16><<<blocks, 32, 0, st>>>(L, d, h, K, rows);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_solve_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_solve_rows<<<blocks, warps * 32, smem, st>>>(L, d, h, K, rows);
+  }
   note_launch();
   return cudaGetLastError();
 }
