@@ -228,9 +228,26 @@ def roofline(prec, prof, w, measured=None):
     launches_pass = prof["pass1_n"] + prof["pass2_n"]
     pass_ms = (prof["pass1_ms"] + prof["pass2_ms"]) / max(launches_pass, 1)
     hbm_bytes = n_slots * (4 + 1 / 8)                   # x (FP32) + mask bit per slot
+    line_search = None
+    if prec == "bf16":
+        # pass 1 (k_pass_tc) reads x and the mask bit and writes the slot's weight byte; the
+        # line search (k_pass_wls) reads that byte back: one byte per slot
+        launches_pass = prof["pass1_n"]
+        pass_ms = prof["pass1_ms"] / max(launches_pass, 1)
+        hbm_bytes = n_slots * (4 + 1 / 8 + 1)
+        ls_ms = prof["pass2_ms"] / max(prof["pass2_n"], 1)
+        ls_bytes = n_slots * 1.0
+        line_search = {"kernel": "k_pass_wls (line search from the cached weights)", "bound": "hbm",
+                       "ms_per_launch": ls_ms, "launches": prof["pass2_n"],
+                       "algorithmic_bytes_per_launch": ls_bytes,
+                       "achieved": ls_bytes / (ls_ms / 1e3) / 1e9 if ls_ms > 0 else None,
+                       "peak": pk["hbm_gbs"], "unit": "GB/s"}
+        if line_search["achieved"]:
+            line_search["frac"] = line_search["achieved"] / pk["hbm_gbs"]
     if prec in ("bf16", "tf32x3"):
         achieved = hbm_bytes / (pass_ms / 1e3) / 1e9
-        kname = ("k_pass_tc (fused tcgen05 data pass, passes 1+2)" if prec == "bf16" else
+        kname = ("k_pass_tc (fused tcgen05 data pass 1: residual, weight, gradient contraction; "
+                 "weights cached as bytes)" if prec == "bf16" else
                  "k_pass_tc TF32 (fused tcgen05 data pass, 3-term TF32 products, passes 1+2)")
         roof = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -270,6 +287,8 @@ def roofline(prec, prof, w, measured=None):
                                          if k.endswith("_ms") and v > 0}
     roof["algorithmic_bytes_per_launch"] = hbm_bytes
     roof["hbm_gbs_achieved"] = hbm_bytes / (pass_ms / 1e3) / 1e9
+    if line_search:
+        roof["line_search_pass"] = line_search
     return roof
 
 
@@ -740,18 +759,30 @@ def phase_summary(ph, steps=2):
     return {k[:-3]: round(v / steps, 4) for k, v in ph.items() if k.endswith("_ms") and v > 0}
 
 
-def pass_roofline(ph, slots_per_pass, pk, label, steps=2, Kp=None, tf32_peak=None):
+def pass_roofline(ph, slots_per_pass, pk, label, steps=2, Kp=None, tf32_peak=None, cached_weights=False):
     """Fused data passes of the traced steps: algorithmic bytes (x and the mask bit per slot)
     over the average pass time, against the measured HBM copy bandwidth; for the TF32 passes
-    also the executed tensor flops (3 product terms) against the measured TF32 peak."""
+    also the executed tensor flops (3 product terms) against the measured TF32 peak.  With
+    cached_weights (BF16), pass 1 also writes a weight byte per slot and the line-search pass,
+    reported on its own, reads it back."""
     n = ph.get("pass1_n", 0) + ph.get("pass2_n", 0)
     if n == 0:
         return None
     ms = (ph["pass1_ms"] + ph["pass2_ms"]) / n
     byt = slots_per_pass * (4 + 1 / 8)
+    if cached_weights and ph.get("pass1_n", 0):
+        n = ph["pass1_n"]
+        ms = ph["pass1_ms"] / n
+        byt = slots_per_pass * (4 + 1 / 8 + 1)
     gbs = byt / (ms / 1e3) / 1e9
     r = {"kernel": label, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
          "frac": gbs / pk["hbm_gbs"], "ms_per_launch": ms, "launches": n, "algorithmic_bytes_per_launch": byt}
+    if cached_weights and ph.get("pass2_n", 0):
+        ls = ph["pass2_ms"] / ph["pass2_n"]
+        lb = slots_per_pass * 1.0
+        r["line_search_pass"] = {"kernel": "k_pass_wls", "ms_per_launch": ls, "launches": ph["pass2_n"],
+                                 "algorithmic_bytes_per_launch": lb, "achieved": lb / (ls / 1e3) / 1e9,
+                                 "frac": lb / (ls / 1e3) / 1e9 / pk["hbm_gbs"], "unit": "GB/s"}
     if Kp and tf32_peak:
         fl = slots_per_pass * 3 * 4 * Kp
         r["tensor_tflops_executed"] = fl / (ms / 1e3) / 1e12
@@ -854,7 +885,8 @@ def run_sketched(torch, pk, name, precs, steps, budget, conv_iters, conv_budget)
         leg = {"ms_per_iter": ms, "iters_per_s": 1e3 / ms, "sampled_entries_per_s": sum(slots) / (ms / 1e3),
                "kernel_launches_per_iter": launches, "phase_ms_per_step_untimed": phase_summary(ph)}
         leg["roofline_pass"] = pass_roofline(ph, np.mean(slots), pk,
-                                             f"fused data pass ({prec})", Kp=None)
+                                             f"fused data pass ({prec})", Kp=None,
+                                             cached_weights=(prec == "bf16"))
         if gather_ms > 0:
             leg["roofline_gather"] = {"kernel": "k_gather (RStS sketch X_I, P_I)", "bound": "hbm",
                                       "achieved": gbytes / (gather_ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],

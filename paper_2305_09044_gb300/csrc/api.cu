@@ -165,6 +165,14 @@ struct Extra {
   int64_t ldx = 0;
   int mst_o = 0;
   int tcG = 0;
+  // BF16: the weights of the last tensor-core pass 1 (one byte per slot, unit-major), read by
+  // the line-search pass of the same core update instead of the data and the mask
+  DevBuf wq;
+  int wq_k = -1;                // core whose pass 1 wrote them (-1: none)
+  uint64_t wq_gen = 0;
+  int64_t wq_Pst = -1, wq_Pstr = -1;
+  int wq_Kp = -1;
+  bool wq_rows = false;
   // tracing: event pairs around data-pass launches (kind 0 = pass 1, 1 = pass 2)
   int prof = 0;            // 0 off, 1 data passes, 2 every phase
   // CUDA graph of a full (unsketched) trd_step: captured on the second consecutive step with
@@ -838,10 +846,24 @@ trd_status run_pass1_tc(trd_handle* h, int k, bool full_stats) {
     ops.T_loT = x->bTTlo.p;
     ops.ldT = x->ldTT;
   }
+  unsigned char* wq = nullptr;
+  if (!is_tf32(h)) {
+    TRY(ensure(h, x->wq, (size_t)tc_wq_bytes(sp.Kp, sp.P_stat, sp.P_strm)));
+    wq = (unsigned char*)x->wq.p;
+  }
+  x->wq_k = -1;
   CK(launch_pass_tc(is_tf32(h), sp.rows, false, ops, x->Xtc, sp.P_in, x->ldx, sp.P_out, (const uint32_t*)x->Mst[o].p, W, sp.P_stat, sp.P_strm, sp.Kp,
                     h->scal + S_SIGMA, (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, G, full_stats,
-                    h->stream),
+                    h->stream, wq),
      "tensor-core data pass 1");
+  if (wq) {
+    x->wq_k = k;
+    x->wq_gen = x->view_gen;
+    x->wq_Pst = sp.P_stat;
+    x->wq_Pstr = sp.P_strm;
+    x->wq_Kp = sp.Kp;
+    x->wq_rows = sp.rows;
+  }
   prof_end(h, 0);
   PScope ps(h, P_REDUCE);
   // the back-contraction sums the partial slots itself; the row-sampling gradient is the
@@ -902,11 +924,19 @@ trd_status run_pass2_tc(trd_handle* h, int k, double** den) {
   ops.S_h_lo = tf ? x->bShlo.p : nullptr;
   ops.T_hi = x->bThi.p;
   ops.T_lo = x->bTlo.p;
+  // BF16 after this core's pass 1 on the same view: the line search reads pass 1's weights
+  const bool cached = !tf && h->pass1_k == k && x->wq_k == k && x->wq_gen == x->view_gen &&
+                      x->wq_Pst == sp.P_stat && x->wq_Pstr == sp.P_strm && x->wq_Kp == sp.Kp && x->wq_rows == sp.rows;
   prof_begin(h);
-  CK(launch_pass_tc(tf, sp.rows, true, ops, x->Xtc, sp.P_in, x->ldx, sp.P_out,
-                    (const uint32_t*)x->Mst[x->mst_o].p, x->W, sp.P_stat, sp.P_strm, sp.Kp, h->scal + S_SIGMA,
-                    (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, x->tcG, false, h->stream),
-     "tensor-core data pass 2");
+  if (cached)
+    CK(launch_pass_wls(x->bSh.p, x->bThi.p, (const unsigned char*)x->wq.p, sp.Kp, sp.P_stat, sp.P_strm,
+                       (double*)h->stat_part.p, h->dstatus, x->tcG, (const double*)h->stat_sum.p + 4, h->stream),
+       "line-search pass from cached weights");
+  else
+    CK(launch_pass_tc(tf, sp.rows, true, ops, x->Xtc, sp.P_in, x->ldx, sp.P_out,
+                      (const uint32_t*)x->Mst[x->mst_o].p, x->W, sp.P_stat, sp.P_strm, sp.Kp, h->scal + S_SIGMA,
+                      (float*)h->Tpart.p, (double*)h->stat_part.p, h->dstatus, x->tcG, false, h->stream),
+       "tensor-core data pass 2");
   prof_end(h, 1);
   // the line-search denominator is summed from the per-CTA partials by the update kernel
   *den = nullptr;
@@ -1607,7 +1637,7 @@ void trd_destroy(trd_t* h) {
   DevBuf* xb[] = {&x->Ework, &x->meta,    &x->stat_sum2, &x->Gloc,    &x->recA, &x->recC,
                   &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr, &x->bc_ctr, &x->stop_part, &x->stop_ctr, &x->probe_lin, &x->Qb[0], &x->Qb[1], &x->probe_cand, &x->rows_dev,
                   &x->bShi,  &x->bSlo,    &x->bSh,       &x->bThi,    &x->bTlo,    &x->bTT,
-                  &x->Mst[0], &x->Mst[1], &x->bShlo, &x->Xpad, &x->bTThi, &x->bTTlo, &x->gbase};
+                  &x->Mst[0], &x->Mst[1], &x->bShlo, &x->Xpad, &x->bTThi, &x->bTTlo, &x->gbase, &x->wq};
   for (DevBuf* b : xb) free_buf(*b);
   for (int k = 0; k < kMaxN; ++k) { free_buf(x->Eloc[k]); free_buf(x->tmpZ[k]); free_buf(x->smpZ[k]); }
   DevBuf* sb[] = {&x->smpA, &x->smpC, &x->smpGA, &x->smpGC, &x->smpGAd, &x->smpGCd, &x->smpPre, &x->smpPost,

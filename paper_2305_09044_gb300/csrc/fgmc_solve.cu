@@ -854,7 +854,9 @@ __global__ void k_step_update(double* __restrict__ Z, float* __restrict__ Zf, Ha
       dn = *den_in;
     }
     if (lane == 0) {
-      double eta = fixed_eta > 0 ? fixed_eta : (dn > 0 ? *num / dn : 0.0);
+      // a NaN denominator (non-finite weights or direction) rejects the step as non-finite;
+      // a zero one (no observed slot) gives no step
+      double eta = fixed_eta > 0 ? fixed_eta : (isnan(dn) ? dn : (dn > 0 ? *num / dn : 0.0));
       const bool finite = isfinite(eta);
       if (!finite) eta = 0.0;
       if (*dstatus & (DEV_SINGULAR | DEV_NONFINITE)) eta = 0.0;

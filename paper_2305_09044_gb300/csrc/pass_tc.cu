@@ -288,9 +288,12 @@ cudaError_t launch_tc_prep_tf32(const float* src, int64_t rows, int Kp, float* h
 cudaError_t launch_pass_tc(bool tf32, bool rows_case, bool pass2, const PassOperands& o, const float* X,
                            int64_t P_in, int64_t ldx, int64_t P_out, const uint32_t* Mst, int64_t W,
                            int64_t P_stat, int64_t P_strm, int Kp, const double* sigma, float* Tpart,
-                           double* stat_part, int* err, int G, bool full_stats, cudaStream_t st) {
+                           double* stat_part, int* err, int G, bool full_stats, cudaStream_t st,
+                           unsigned char* wq) {
   using namespace tc;
   const int KPAD = tc_kpad(Kp, tf32);
+  // BF16 pass 1 always leaves its weights in the cache (the line-search pass reads them)
+  if (!tf32 && !pass2 && (!wq || ((uintptr_t)wq & 15))) return cudaErrorInvalidValue;
   // TMA row strides must be multiples of 16 bytes: callers pass X re-laid with ldx % 4 == 0
   if (!KPAD || (ldx % 4) != 0 || ldx < P_in || ((uintptr_t)X & 15)) return cudaErrorInvalidValue;
   Params p{};
@@ -304,12 +307,31 @@ cudaError_t launch_pass_tc(bool tf32, bool rows_case, bool pass2, const PassOper
   p.Tpart = Tpart;
   p.stat_part = stat_part;
   p.err = err;
+  p.wq = wq;
   if (tf32) return launch_pass_tc_tf32(KPAD, rows_case, pass2, full_stats, o, X, P_in, ldx, P_out, p, G, st);
   if (KPAD == 64)
     return launch_pass_tc_kp<64, false>(rows_case, pass2, full_stats, o, X, P_in, ldx, P_out, p, G, st);
   if (KPAD == 128)
     return launch_pass_tc_kp<128, false>(rows_case, pass2, full_stats, o, X, P_in, ldx, P_out, p, G, st);
   return launch_pass_tc_kp<256, false>(rows_case, pass2, full_stats, o, X, P_in, ldx, P_out, p, G, st);
+}
+
+int64_t tc_wq_bytes(int Kp, int64_t P_stat, int64_t P_strm) {
+  const int kpad = tc_kpad(Kp, false);
+  if (!kpad) return 0;
+  const int64_t BN = tc_bn(kpad, false);
+  return ((P_stat + tc::BM - 1) / tc::BM) * ((P_strm + BN - 1) / BN) * tc::BM * BN;
+}
+
+cudaError_t launch_pass_wls(const void* S_h, const void* T_hi, const unsigned char* wq, int Kp, int64_t P_stat,
+                            int64_t P_strm, double* stat_part, int* err, int G, const double* nf_in,
+                            cudaStream_t st) {
+  using namespace tc;
+  const int kpad = tc_kpad(Kp, false);
+  if (!kpad || !wq || ((uintptr_t)wq & 15)) return cudaErrorInvalidValue;
+  if (kpad == 64) return launch_pass_wls_kp<64>(S_h, T_hi, wq, P_stat, P_strm, stat_part, err, G, nf_in, st);
+  if (kpad == 128) return launch_pass_wls_kp<128>(S_h, T_hi, wq, P_stat, P_strm, stat_part, err, G, nf_in, st);
+  return launch_pass_wls_kp<256>(S_h, T_hi, wq, P_stat, P_strm, stat_part, err, G, nf_in, st);
 }
 
 }  // namespace trd

@@ -128,7 +128,25 @@ struct Params {
   const uint32_t* shw[2];
   int sh_off[2];
   int sh_ld;
+  // BF16 pass 1: the weight of every slot as 8-bit fixed point (q = round(255 w), 0 off the
+  // mask), unit-major: unit u's BM x BN bytes at wq + u BM BN, row r's BN bytes at r BN with
+  // its 16-byte chunks permuted by wq_chunk (so that the line-search pass reads them from
+  // shared memory without bank conflicts)
+  unsigned char* wq;
+  // line-search pass from the cache: pass 1's reduced count of non-finite observed residuals
+  // (such residuals get weight 0 in the cache; a non-zero count makes den NaN, as a pass that
+  // recomputes the weights would)
+  const double* nf_in;
 };
+
+// Byte offset of 16-byte chunk ch of row r inside one unit's weight block (BN bytes per row):
+// the chunk index is XORed with the row's position among the rows that share a 128-byte line,
+// so that 16-byte reads of one chunk by 32 consecutive rows fall on distinct banks.
+template <int BN>
+__host__ __device__ constexpr int wq_chunk(int r, int ch) {
+  constexpr int CHR = BN / 16, RPL = 128 / BN;   // chunks per row, rows per 128-byte line
+  return r * BN + ((ch ^ ((r / RPL) & (CHR - 1))) << 4);
+}
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -167,6 +185,9 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 __device__ __forceinline__ bool mbar_wait_n(uint64_t* b, uint32_t parity, volatile int* abort_flag, uint32_t limit) {
+  // a phase that has already completed is seen by the non-blocking probe (cheaper than a
+  // try_wait, measured)
+  if (mbar_test(b, parity)) return true;
   for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_try(b, parity)) return true;
     if (*abort_flag) return false;
@@ -360,6 +381,24 @@ __device__ __forceinline__ float fast_ex2(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+
+// Weights of two slots -> two bytes round(255 w) in the low half of a word: w * 255 + 1.5 2^23
+// (exact for w in [0, 1]; the FMA rounds to the nearest integer) keeps the integer in the low
+// mantissa bits.
+__device__ __forceinline__ uint32_t quant_pair(float w0, float w1) {
+  const float2 q = __ffma2_rn(make_float2(w0, w1), make_float2(255.f, 255.f), make_float2(12582912.f, 12582912.f));
+  return __byte_perm(__float_as_uint(q.x), __float_as_uint(q.y), 0x0040);
+}
+
+// Contiguous global -> shared copy of `bytes` (a multiple of 16, both addresses 16-byte
+// aligned) completing on an mbarrier, with an L2 policy.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(bar)), "l"(policy)
+      : "memory");
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -816,10 +855,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t seen = mword & vmask;
         nslot += __popc(vmask);
         nobs += __popc(seen);
+        // BF16 pass 1: this thread's CPW weights as bytes, four per word (zero off the mask)
+        constexpr bool WQ = !PASS2 && !TF32;
+        uint32_t qw[WQ ? CPW / 4 : 1];
         // branch-free slot update (predicated selects keep the slots independent)
         if (FULL) {
           // exact statistics: sum w, sum e^2, sum w e^2 and a count of non-finite residuals
           uint32_t fin = 0;
+          float wprev = 0.f;   // weight of the even slot of the current pair (WQ)
 #pragma unroll
           for (int j = 0; j < CPW; ++j) {
             const float e = xv[j] - xh[j];
@@ -828,6 +871,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // selects, not products with 0, so that a NaN stored at an unobserved slot stays out
             const float eu = use ? e : 0.f;
             const float uw = use ? fast_ex2(e * e * nk) : 0.f;
+            if constexpr (WQ) {
+              if (j & 1) {
+                const uint32_t t = quant_pair(wprev, uw);
+                qw[j >> 2] = (j & 2) ? __byte_perm(qw[j >> 2], t, 0x5410) : t;
+              } else {
+                wprev = uw;
+              }
+            }
             if (PASS2) {
               sden = fmaf(uw * dh[j], dh[j], sden);
             } else {
@@ -859,12 +910,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               if ((j >> 1) & 1) acc2b = __ffma2_rn(__fmul2_rn(w2, d2), d2, acc2b);
               else acc2a = __ffma2_rn(__fmul2_rn(w2, d2), d2, acc2a);
             } else {
-              const float2 y2 = __fmul2_rn(make_float2(fast_ex2(m2.x), fast_ex2(m2.y)), e2);
+              const float2 w2 = make_float2(fast_ex2(m2.x), fast_ex2(m2.y));
+              const float2 y2 = __fmul2_rn(w2, e2);
               if ((j >> 1) & 1) acc2b = __ffma2_rn(y2, e2, acc2b);
               else acc2a = __ffma2_rn(y2, e2, acc2a);
               xv[j] = y2.x;
               xv[j + 1] = y2.y;
+              if constexpr (WQ) {
+                const uint32_t t = quant_pair(b0 ? w2.x : 0.f, b1 ? w2.y : 0.f);
+                qw[j >> 2] = (j & 2) ? __byte_perm(qw[j >> 2], t, 0x5410) : t;
+              }
             }
+          }
+        }
+        if constexpr (WQ) {
+          // the unit's weight block: this thread's CPW bytes of row `row`, CPW / 16 chunks
+          unsigned char* wb = p.wq + u * (int64_t)(BM * BN);
+          if constexpr (CPW == 32) {
+            // both chunks lie in one 32-byte sector (the chunk permutation only swaps them when
+            // the row's XOR term is odd): one full-sector store; streaming (evict-first), so
+            // that the cache written during the pass does not push the pass's own reusable
+            // lines (operands, mask rows, tile edges) out of L2
+            const int p0 = wq_chunk<BN>(row, c0 >> 4);
+            const bool swap = (p0 >> 4) & 1;
+            const uint32_t* a = swap ? qw + 4 : qw;
+            const uint32_t* b2 = swap ? qw : qw + 4;
+            asm volatile("st.global.cs.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(wb + (p0 & ~31)), "r"(a[0]),
+                         "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b2[0]), "r"(b2[1]), "r"(b2[2]), "r"(b2[3])
+                         : "memory");
+          } else {
+#pragma unroll
+            for (int h = 0; h < CPW / 16; ++h)
+              __stcs(reinterpret_cast<uint4*>(wb + wq_chunk<BN>(row, (c0 >> 4) + h)),
+                     make_uint4(qw[4 * h], qw[4 * h + 1], qw[4 * h + 2], qw[4 * h + 3]));
           }
         }
         if (!PASS2) {
@@ -961,6 +1039,259 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+// ------------------------------------------------------------------ line search from cached weights
+// Pass 2 of the BF16 path after a BF16 pass 1 of the same core update: the exact line search's
+// denominator den = sum w D2^2 (Sec. 3.2) with D2 = S_h S_str^T (one BF16 term, FP32 in TMEM)
+// and w the weight pass 1 left in its unit-major cache (8-bit fixed point, w = q / 255; zero
+// off the mask and outside the tensor).  Pass 1 computed these weights from the same residuals
+// (the cores do not change between the passes), so this pass reads one byte per slot instead
+// of the data tile and the mask, and runs neither the reconstruction GEMM nor the exponential.
+// Units and their partition over the CTAs are those of pass 1 (any partition works: the cache
+// is indexed by unit).  Roles: warp 0 operand producer (S_h per segment, S_str tiles), warp 1
+// TMEM allocator + MMA issuer, warps 2..9 epilogue (TMEM lane quarter = warp % 4, two column
+// groups), warp 10 weight producer (one bulk copy per unit).  Every wait is bounded.
+template <int KP>
+struct WCfg {
+  static constexpr int BN = Cfg<KP, false, false>::BN;   // the streaming columns of pass 1's units
+  static constexpr int NSUB = KP / 64;                    // 128-byte K sub-tiles per operand row
+  static constexpr int KSTEPS = KP / 16;                  // MMAs of K = 16
+  static constexpr int NGRP = 2;                          // column groups
+  static constexpr int CPW = BN / NGRP;                   // columns per epilogue warp (32 or 16)
+  static constexpr int EPIW = 4 * NGRP;                   // epilogue warps (4 TMEM lane quarters each)
+  static constexpr int WT = BM * BN;                      // bytes of one unit's weights
+  static constexpr int S_TILE = BM * KP * 2, T_TILE = BN * KP * 2;
+  static constexpr int SUB_S = BM * 128, SUB_T = BN * 128;
+  static constexpr int ND = 4;
+  static constexpr int TS = KP == 256 ? 4 : (KP == 128 ? 6 : 8);
+  static constexpr int WS = (KP == 64 || BN == 32) ? 16 : 8;
+  static constexpr int T0 = S_TILE, W0 = T0 + TS * T_TILE, BARS = W0 + WS * WT, TOTAL = BARS + 1024;
+  static constexpr int WPW = 2 + EPIW;                    // warp index of the weight producer
+  static constexpr int NTH = 32 * (3 + EPIW);
+};
+
+template <int KP>
+__global__ void __launch_bounds__(WCfg<KP>::NTH, 1)
+    k_pass_wls(const __grid_constant__ CUtensorMap mS_h, const __grid_constant__ CUtensorMap mT_hi, const Params p) {
+  using C = WCfg<KP>;
+  constexpr int BN = C::BN, CPW = C::CPW, NSUB = C::NSUB, KSTEPS = C::KSTEPS, WT = C::WT;
+  constexpr int ND = C::ND, TS = C::TS, WS = C::WS, EPIW = C::EPIW;
+  static_assert(C::TOTAL + 1024 <= SMEM_LIMIT, "shared memory");
+  static_assert(CPW == 16 || CPW == 32, "one or two 16-byte weight chunks per epilogue thread");
+  static_assert(ND * BN <= 256, "TMEM columns");
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::BARS);
+  uint64_t* w_full = bars;                // [WS] weight block landed
+  uint64_t* w_empty = w_full + WS;        // [WS] weight block read by every epilogue thread
+  uint64_t* t_full = w_empty + WS;        // [TS] streaming operand landed
+  uint64_t* t_empty = t_full + TS;        // [TS] streaming operand consumed (MMA commit)
+  uint64_t* d_full = t_empty + TS;        // [ND] D2 done
+  uint64_t* d_empty = d_full + ND;        // [ND] D2 read by the epilogue
+  uint64_t* s_full = d_empty + ND;        //      step operand landed
+  uint64_t* s_empty = s_full + 1;         //      segment's MMAs done with it
+  uint64_t* mma_done = s_empty + 1;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(mma_done + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 2);
+  double* red = reinterpret_cast<double*>(mma_done + 4);   // [EPIW epilogue warps]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = blockIdx.x;
+  const int64_t u_begin = c * p.U / p.G, u_end = (c + 1) * p.U / p.G;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < WS; ++s) {
+      mbar_init(&w_full[s], 1);
+      mbar_init(&w_empty[s], 32 * EPIW);
+    }
+    for (int s = 0; s < TS; ++s) {
+      mbar_init(&t_full[s], 1);
+      mbar_init(&t_empty[s], 1);
+    }
+    for (int b = 0; b < ND; ++b) {
+      mbar_init(&d_full[b], 1);
+      mbar_init(&d_empty[b], 32 * EPIW);
+    }
+    mbar_init(s_full, 1);
+    mbar_init(s_empty, 1);
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)), "r"(256)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- operand producer
+    if (lane == 0) {
+      const uint64_t keep = policy_evict_last();
+      int64_t it = 0;
+      int g = 0;
+      bool ok = true;
+      int last_phase[TS];
+      for (int s = 0; s < TS; ++s) last_phase[s] = -1;
+      int s_phase = -1;
+      for (int64_t u = u_begin; u < u_end && ok; ++g) {
+        const int64_t rb = u / p.NT;
+        const int64_t seg_end = imin(u_end, (rb + 1) * p.NT);
+        if (g > 0) ok = mbar_wait(s_empty, (uint32_t)((g - 1) & 1), abort_flag);
+        if (!ok) break;
+        mbar_expect_tx(s_full, C::S_TILE);
+        s_phase = g & 1;
+#pragma unroll
+        for (int sb = 0; sb < NSUB; ++sb)
+          tma_2d_hint(sm + sb * C::SUB_S, &mS_h, s_full, sb * 64, (int)(rb * BM), keep);
+        for (int64_t tc = u - rb * p.NT; u < seg_end; ++u, ++it, ++tc) {
+          const int s = (int)(it % TS);
+          if (!mbar_wait(&t_empty[s], (uint32_t)(((it / TS) & 1) ^ 1), abort_flag)) { ok = false; break; }
+          unsigned char* tb = sm + C::T0 + s * C::T_TILE;
+          mbar_expect_tx(&t_full[s], C::T_TILE);
+          last_phase[s] = (int)((it / TS) & 1);
+#pragma unroll
+          for (int sb = 0; sb < NSUB; ++sb)
+            tma_2d_hint(tb + sb * C::SUB_T, &mT_hi, &t_full[s], sb * 64, (int)(tc * BN), keep);
+        }
+      }
+      if (!ok) {
+        for (int s = 0; s < TS; ++s)
+          if (last_phase[s] >= 0)
+            for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+              if (mbar_try(&t_full[s], (uint32_t)last_phase[s])) break;
+        if (s_phase >= 0)
+          for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+            if (mbar_try(s_full, (uint32_t)s_phase)) break;
+      }
+    }
+  } else if (warp == C::WPW) {
+    // ---------------------------------------------------------------- weight producer
+    if (lane == 0) {
+      const uint64_t once = policy_evict_first();
+      bool ok = true;
+      int last_phase[WS];
+      for (int s = 0; s < WS; ++s) last_phase[s] = -1;
+      int64_t it = 0;
+      for (int64_t u = u_begin; u < u_end; ++u, ++it) {
+        const int s = (int)(it % WS);
+        if (!mbar_wait(&w_empty[s], (uint32_t)(((it / WS) & 1) ^ 1), abort_flag)) { ok = false; break; }
+        mbar_expect_tx(&w_full[s], WT);
+        last_phase[s] = (int)((it / WS) & 1);
+        bulk_g2s(sm + C::W0 + s * WT, p.wq + u * (int64_t)WT, WT, &w_full[s], once);
+      }
+      if (!ok)
+        for (int s = 0; s < WS; ++s)
+          if (last_phase[s] >= 0)
+            for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+              if (mbar_try(&w_full[s], (uint32_t)last_phase[s])) break;
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t ID = idesc_mma(BM, BN, false);
+      const uint64_t dA = sdesc(su32(sm));
+      int64_t it = 0;
+      int g = 0;
+      bool ok = true;
+      for (int64_t u = u_begin; u < u_end && ok; ++g) {
+        const int64_t rb = u / p.NT;
+        const int64_t seg_end = imin(u_end, (rb + 1) * p.NT);
+        if (!mbar_wait(s_full, (uint32_t)(g & 1), abort_flag)) { ok = false; break; }
+        for (; u < seg_end; ++u, ++it) {
+          const int s = (int)(it % TS), b = (int)(it & (ND - 1));
+          if (!mbar_wait(&t_full[s], (uint32_t)((it / TS) & 1), abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&d_empty[b], (uint32_t)(((it / ND) & 1) ^ 1), abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint64_t dB = sdesc(su32(sm + C::T0 + s * C::T_TILE));
+#pragma unroll
+          for (int kk = 0; kk < KSTEPS; ++kk) {
+            const uint64_t ka = (uint64_t)(((kk >> 2) * C::SUB_S + (kk & 3) * 32) >> 4);
+            const uint64_t kb = (uint64_t)(((kk >> 2) * C::SUB_T + (kk & 3) * 32) >> 4);
+            tc_mma<false>(tmem + (uint32_t)(b * BN), dA + ka, dB + kb, ID, kk > 0);
+          }
+          tc_commit(&d_full[b]);
+          tc_commit(&t_empty[s]);
+        }
+        if (!ok) break;
+        tc_commit(s_empty);
+      }
+      tc_commit(mma_done);
+      for (uint32_t i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try(mma_done, 0)) break;
+    }
+  } else if (warp >= 2 && warp < C::WPW) {
+    // ---------------------------------------------------------------- epilogue
+    const int q = warp & 3, grp = (warp - 2) >> 2;
+    const int row = q * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const int c0 = grp * CPW;
+    float2 acc2a = make_float2(0.f, 0.f), acc2b = make_float2(0.f, 0.f);
+    const float2 off = make_float2(-8388608.f, -8388608.f);
+    int64_t it = 0;
+    for (int64_t u = u_begin; u < u_end; ++u, ++it) {
+      const int b = (int)(it & (ND - 1)), ws = (int)(it % WS);
+      // the warp leaves together when a wait gives up (the TMEM loads are warp-wide)
+      if (!__all_sync(0xffffffffu, mbar_wait(&d_full[b], (uint32_t)((it / ND) & 1), abort_flag))) break;
+      tc_fence_after();
+      uint32_t rd[CPW];
+      tmem_issue<CPW>(tmem + lane_base + (uint32_t)(b * BN + c0), rd);
+      if (!__all_sync(0xffffffffu, mbar_wait(&w_full[ws], (uint32_t)((it / WS) & 1), abort_flag))) {
+        tmem_wait<CPW>(rd);
+        break;
+      }
+      const unsigned char* wt = sm + C::W0 + ws * WT;
+      uint32_t wv[CPW / 4];
+#pragma unroll
+      for (int h = 0; h < CPW / 16; ++h) {
+        const uint4 v = *reinterpret_cast<const uint4*>(wt + wq_chunk<BN>(row, (c0 >> 4) + h));
+        wv[4 * h] = v.x;
+        wv[4 * h + 1] = v.y;
+        wv[4 * h + 2] = v.z;
+        wv[4 * h + 3] = v.w;
+      }
+      mbar_arrive(&w_empty[ws]);
+      tmem_wait<CPW>(rd);
+      tc_fence_before();
+      mbar_arrive(&d_empty[b]);
+      // den += q D2^2 (the factor 1 / 255 is applied once at the end); byte k of a word -> the
+      // float 2^23 + q (exponent byte 0x4B above it), minus 2^23, exactly
+#pragma unroll
+      for (int j = 0; j < CPW; j += 2) {
+        const uint32_t wd = wv[j >> 2];
+        const uint32_t sel = (uint32_t)(j & 3);
+        const float2 w2 = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(wd, 0x4B000000u, 0x7540u | sel)),
+                                                 __uint_as_float(__byte_perm(wd, 0x4B000000u, 0x7540u | (sel + 1)))),
+                                     off);
+        const float2 d2 = make_float2(__uint_as_float(rd[j]), __uint_as_float(rd[j + 1]));
+        if ((j >> 1) & 1) acc2b = __ffma2_rn(__fmul2_rn(w2, d2), d2, acc2b);
+        else acc2a = __ffma2_rn(__fmul2_rn(w2, d2), d2, acc2a);
+      }
+    }
+    double den = (double)((acc2a.x + acc2b.x) + (acc2a.y + acc2b.y)) * (1.0 / 255.0);
+    for (int o = 16; o > 0; o >>= 1) den += __shfl_down_sync(0xffffffffu, den, o);
+    if (lane == 0) red[warp - 2] = den;
+  }
+  // ------------------------------------------------------------------ teardown
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double den = 0.0;
+    for (int w = 0; w < EPIW; ++w) den += red[w];
+    if (p.nf_in && !(*p.nf_in == 0.0)) den = __longlong_as_double(0x7ff8000000000000ll);
+    for (int f = 0; f < 8; ++f) p.stat_part[c * 8 + f] = 0.0;
+    p.stat_part[c * 8 + 4] = isfinite(den) ? 0.0 : 1.0;   // non-finite count (0 or 1)
+    p.stat_part[c * 8 + 6] = den;
+    if (*abort_flag) atomicOr(p.err, (int)DEV_TIMEOUT);
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+  }
+}
+
 // ------------------------------------------------------------------ host side
 // Tiled 2-D tensor map (cuTensorMapEncodeTiled through the runtime's driver entry point).
 bool make_map(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t outer,
@@ -1041,6 +1372,37 @@ cudaError_t launch_pass_tc_kp(bool rows_case, bool pass2, bool full_stats, const
   if (full_stats)
     return rows_case ? go(k_pass_tc<true, false, true, KP, TF32>, SM1) : go(k_pass_tc<false, false, true, KP, TF32>, SM1);
   return rows_case ? go(k_pass_tc<true, false, false, KP, TF32>, SM1) : go(k_pass_tc<false, false, false, KP, TF32>, SM1);
+}
+
+// Launch the line-search pass from cached weights (BF16 operands [rows][KP]: S_h over the
+// stationary rows, the hi split of the streaming operand).
+template <int KP>
+cudaError_t launch_pass_wls_kp(const void* S_h, const void* T_hi, const unsigned char* wq, int64_t P_stat,
+                               int64_t P_strm, double* stat_part, int* err, int G, const double* nf_in,
+                               cudaStream_t st) {
+  using C = WCfg<KP>;
+  CUtensorMap mS_h, mT_hi;
+  const CUtensorMapSwizzle SW = CU_TENSOR_MAP_SWIZZLE_128B;
+  if (!make_map(&mS_h, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, S_h, KP, P_stat, (uint64_t)KP * 2, 64, BM, SW) ||
+      !make_map(&mT_hi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, T_hi, KP, P_strm, (uint64_t)KP * 2, 64, C::BN, SW))
+    return cudaErrorInvalidValue;
+  Params p{};
+  p.P_stat = P_stat;
+  p.P_strm = P_strm;
+  p.RB = (P_stat + BM - 1) / BM;
+  p.NT = (P_strm + C::BN - 1) / C::BN;
+  p.U = p.RB * p.NT;
+  p.G = (int)imin(G, p.U);
+  p.stat_part = stat_part;
+  p.err = err;
+  p.wq = const_cast<unsigned char*>(wq);
+  p.nf_in = nf_in;
+  const size_t smem = (size_t)C::TOTAL + 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_pass_wls<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_pass_wls<KP><<<p.G, C::NTH, smem, st>>>(mS_h, mT_hi, p);
+  note_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace tc

@@ -270,7 +270,17 @@ cudaError_t launch_reduce_slots(const float* part, int64_t RB, int64_t NT, int G
 cudaError_t launch_pass_tc(bool tf32, bool rows_case, bool pass2, const PassOperands& o, const float* X,
                            int64_t P_in, int64_t ldx, int64_t P_out, const uint32_t* Mst, int64_t W,
                            int64_t P_stat, int64_t P_strm, int Kp, const double* sigma, float* Tpart,
-                           double* stat_part, int* err, int G, bool full_stats, cudaStream_t st);
+                           double* stat_part, int* err, int G, bool full_stats, cudaStream_t st,
+                           unsigned char* wq = nullptr);
+// Bytes of the BF16 pass-1 weight cache for a P_stat x P_strm pass of width Kp (one byte per
+// slot of every unit, units padded to whole tiles).
+int64_t tc_wq_bytes(int Kp, int64_t P_stat, int64_t P_strm);
+// Line-search pass of the BF16 path from the weights cached by pass 1 (same Kp, P_stat,
+// P_strm): per-CTA partials of den = sum w (S_h S_str^T)^2 in stat_part[8 c + 6]; nf_in
+// (device, nullable): pass 1's count of non-finite observed residuals (non-zero -> den NaN).
+cudaError_t launch_pass_wls(const void* S_h, const void* T_hi, const unsigned char* wq, int Kp, int64_t P_stat,
+                            int64_t P_strm, double* stat_part, int* err, int G, const double* nf_in,
+                            cudaStream_t st);
 cudaError_t launch_pad_rows(const float* X, int64_t P_in, int64_t P_out, int64_t ld, float* out, cudaStream_t st);
 
 // fgmc_solve.cu

@@ -107,6 +107,28 @@ def test_nonfinite_observed_entry_is_reported(torch_cuda, prec):
     assert ei.value.status == binding.TRD_ENONFINITE
 
 
+def test_nonfinite_residual_rejects_the_bf16_step(torch_cuda):
+    """A NaN at an observed entry: the residual pass reports it, and the scaled step that
+    follows is rejected (its line-search denominator is not finite) and leaves the core as it
+    was.  On the BF16 path the line search reads the weights pass 1 cached, which carry 0 for
+    that entry; pass 1's non-finite count makes the denominator NaN all the same."""
+    from paper_2305_09044_gb300 import TrdError, binding
+    X, P, words, truth, Xt = problem(DIMS, RANKS, 0.3, 0.1, 44)
+    obs = np.flatnonzero(flat(P) > 0)
+    Xbad = flat(X).copy()
+    Xbad[obs[len(obs) // 3]] = np.nan
+    t, keep = _handle(torch_cuda, "bf16", Xbad.reshape(X.shape, order="F"), words)
+    cores = O.init_cores(DIMS, RANKS, seed=9)
+    t.set_cores(cores)
+    s = t.residual_weights(2, 1.5, raise_nonfinite=False)
+    assert s["n_nonfinite"] == 1
+    t.core_gradient(2)
+    with pytest.raises(TrdError) as ei:
+        t.core_update(2, -1e-10)
+    assert ei.value.status == binding.TRD_ENONFINITE
+    assert np.array_equal(t.get_core(2), cores[2].astype(t.get_core(2).dtype))
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 def test_nan_at_unobserved_entries_is_ignored(torch_cuda, prec):
     """Unobserved entries take no part in the method (P masks them, Eq. 6): storing NaN
