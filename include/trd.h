@@ -60,8 +60,9 @@ typedef enum {
   TRD_FP32 = 1,   /* CUDA-core FP32 data passes, FP32 accumulation; K' <= 256 */
   TRD_BF16 = 2,   /* tcgen05 tensor cores, mixed BF16: the reconstruction in 3-term split BF16
                      (hi*hi + hi*lo + lo*hi), the gradient and line-search products in one
-                     BF16 term, FP32 accumulation; residual and weight in FP32; K' <= 256,
-                     else TRD_ENOTIMPL */
+                     BF16 term, FP32 accumulation; residual and weight in FP32, the weight
+                     carried from the residual pass to the line search as 8-bit fixed point
+                     (w = q / 255, absolute error <= 1/510); K' <= 256, else TRD_ENOTIMPL */
   TRD_TF32X3 = 3  /* tcgen05 tensor cores, TF32 with the 3-term split of both operands in every
                      product (about 22 significant bits per operand: FP32-level accuracy),
                      FP32 accumulation; K' <= 64 on the tensor cores, wider contractions run
@@ -213,7 +214,9 @@ trd_status trd_fgmc_gram(trd_t* handle, int k, double* G_host);
 
 /* Step 'update Z_k' (Eq. hI, Eq. ftrbcn and the exact line search): h = d (G + lambda I)^-1
  * in FP64 (LDL^T factorisation and substitutions for K_k <= 128, Cholesky above); eta = <d,h> / ||sqrt(W) o P o (h B^T)||^2 on the sketch when eta <= 0
- * (second data pass, W recomputed from the same residuals), else the given eta;
+ * (second data pass with the W of the last trd_residual_weights for k: recomputed from the
+ * same residuals, or, with TRD_BF16, read back from the one byte per slot that pass stored),
+ * else the given eta; a non-finite denominator rejects the step (TRD_ENONFINITE);
  * Z_k <- Z_k + eta fold(h) (update-sign reading); core k's FGMC factor is refreshed
  * before the next Gram that uses it.
  * lambda >= 0 absolute, < 0 means |lambda| tr(G)/K.  `gram` is a trd_gram_kind.
@@ -237,7 +240,7 @@ trd_status trd_core_update(trd_t* handle, int k, double lambda, double eta, int 
  * above).  Needs trd_residual_weights for k on this handle (the view of the line search).
  * trd_line_search_terms: h = d (G + lambda I)^-1 (as trd_core_update, `gram` a
  * trd_gram_kind), then *num_out = <d, h> and *den_out = sum w (h B^T)^2 over this handle's
- * view (the second data pass, W recomputed); the core is not changed.  Needs a gradient for
+ * view (the second data pass, W as in trd_core_update); the core is not changed.  Needs a gradient for
  * k.  Both synchronise.  Errors: TRD_EINVAL (order of calls, NULL), TRD_ESINGULAR. */
 trd_status trd_set_gradient(trd_t* handle, int k, const double* d_host);
 trd_status trd_line_search_terms(trd_t* handle, int k, double lambda, int gram, double* num_out,
