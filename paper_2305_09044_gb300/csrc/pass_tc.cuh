@@ -748,15 +748,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const double sg = *p.sigma;
     // exp(-e^2 / (2 sigma^2)) = exp2(-e^2 * k), k = log2(e) / (2 sigma^2); sigma = inf -> k = 0
     const float nk = isinf(sg) ? 0.0f : (float)(-1.4426950408889634 / (2.0 * sg * sg));
-    // exp(-e^2 / (2 sigma^2)) = exp2(-(e s)^2) with s = sqrt(log2(e) / (2 sigma^2))
-    const float sk = isinf(sg) ? 0.0f : (float)sqrt(1.4426950408889634 / (2.0 * sg * sg));
     constexpr uint32_t CMASK = CPW == 32 ? 0xffffffffu : ((1u << CPW) - 1u);
     float sw = 0.f, se2 = 0.f, swe2 = 0.f, sden = 0.f;
     // the lean epilogue works on slot pairs with packed FP32x2 arithmetic and keeps its running
     // sum (w e^2 in pass 1, w D2^2 in pass 2) in two packed accumulators: four independent
     // chains instead of one FMA chain through every slot
     float2 acc2a = make_float2(0.f, 0.f), acc2b = make_float2(0.f, 0.f);
-    const float2 sk2 = make_float2(sk, sk), nsk2 = make_float2(-sk, -sk), neg1 = make_float2(-1.f, -1.f);
+    const float2 nk2 = make_float2(nk, nk), neg1 = make_float2(-1.f, -1.f);
     uint32_t nobs = 0, nnf = 0, nslot = 0;
     constexpr int KPW = KP / NGRP;                  // contraction columns of T per warp
     constexpr bool CHUNKED = TF32 && !PASS2;        // T summed over chunks in registers
@@ -767,6 +765,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int64_t it = 0, ch = 0;
     int g = 0;
     bool ok = true;
+    // phases of the next tile's accumulator and data tile already seen complete by an early
+    // probe (a probe of a completed phase takes about 110 cycles: issued before the arithmetic,
+    // its latency hides behind it; a phase still open is waited for as usual)
+    bool pre_d = false, pre_x = false;
     for (int64_t u = u_begin; u < u_end && ok; ++g) {
       const int64_t rb = u / p.NT;
       const int64_t seg_end = imin(u_end, (rb + 1) * p.NT);
@@ -815,12 +817,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int64_t nc = p.P_strm - t0 - c0;  // valid columns for this warp
         const uint32_t vmask = (!row_ok || nc <= 0) ? 0u : (nc >= CPW ? CMASK : ((1u << nc) - 1u));
         // accumulators first: the TMEM loads are in flight while X is read from shared memory
-        if (!mbar_wait(&d_full[b], (uint32_t)((it / ND) & 1), abort_flag)) { ok = false; break; }
+        if (!pre_d && !mbar_wait(&d_full[b], (uint32_t)((it / ND) & 1), abort_flag)) { ok = false; break; }
         tc_fence_after();
         uint32_t rx[CPW], rd[CPW];
         tmem_issue<CPW>(tmem + lane_base + (uint32_t)(b * BN + c0), rx);
         if (PASS2) tmem_issue<CPW>(tmem + lane_base + (uint32_t)((ND + b) * BN + c0), rd);
-        if (!mbar_wait(&x_full[xs], (uint32_t)((it / XS) & 1), abort_flag)) {
+        if (!pre_x && !mbar_wait(&x_full[xs], (uint32_t)((it / XS) & 1), abort_flag)) {
           if (PASS2) tmem_wait_x2<CPW>(rx, rd);
           else tmem_wait<CPW>(rx);
           ok = false;
@@ -843,6 +845,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
         mbar_arrive(&x_empty[xs]);
+        // early probes: this tile's Y buffer, the next tile's accumulator and data tile
+        const bool pre_y = !PASS2 && mbar_test(&y_empty[yb], (uint32_t)(((it / NY) & 1) ^ 1));
+        pre_d = u + 1 < u_end && mbar_test(&d_full[(it + 1) & (ND - 1)], (uint32_t)(((it + 1) / ND) & 1));
+        pre_x = u + 1 < u_end && mbar_test(&x_full[(it + 1) % XS], (uint32_t)(((it + 1) / XS) & 1));
         if (PASS2) tmem_wait_x2<CPW>(rx, rd);
         else tmem_wait<CPW>(rx);
 #pragma unroll
@@ -894,7 +900,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           // lean: only what the update needs (y, or den) and the objective sum w e^2; a
           // non-finite residual on an observed slot propagates as NaN and rejects the step.
           // Pass 1 masks the residual first (e' = 0 off the mask, so w(e') = 1 and y = w e' = 0
-          // without further selects); pass 2 masks the weight.  w = exp2(-(e s)^2).
+          // without further selects); pass 2 masks the weight.  w = exp2(e^2 k), as in the
+          // full-statistics form.
 #pragma unroll
           for (int j = 0; j < CPW; j += 2) {
             const bool b0 = (seen >> j) & 1u, b1 = (seen >> (j + 1)) & 1u;
@@ -903,7 +910,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               e2.x = b0 ? e2.x : 0.f;
               e2.y = b1 ? e2.y : 0.f;
             }
-            const float2 m2 = __fmul2_rn(__fmul2_rn(e2, sk2), __fmul2_rn(e2, nsk2));   // -(e s)^2
+            const float2 m2 = __fmul2_rn(__fmul2_rn(e2, e2), nk2);   // -e^2 log2(e) / (2 sigma^2)
             if (PASS2) {
               const float2 w2 = make_float2(b0 ? fast_ex2(m2.x) : 0.f, b1 ? fast_ex2(m2.y) : 0.f);
               const float2 d2 = make_float2(dh[j], dh[j + 1]);
@@ -954,7 +961,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               yh[j] = tf32_rna(xv[j]);
               yl[j] = tf32_rna(xv[j] - __uint_as_float(yh[j]));
             }
-            if (!mbar_wait(&y_empty[yb], (uint32_t)(((it / NY) & 1) ^ 1), abort_flag)) { ok = false; break; }
+            if (!pre_y && !mbar_wait(&y_empty[yb], (uint32_t)(((it / NY) & 1) ^ 1), abort_flag)) { ok = false; break; }
             const uint32_t ycol = tmem + lane_base + col_y + (uint32_t)(yb * C::Y_COLS + c0);
             tmem_st<CPW>(ycol, yh);
             tmem_st<CPW>(ycol + (uint32_t)BN, yl);
@@ -962,7 +969,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             uint32_t ypk[CPW / 2];
 #pragma unroll
             for (int j = 0; j < CPW; j += 2) ypk[j >> 1] = pack_bf16(xv[j], xv[j + 1]);
-            if (!mbar_wait(&y_empty[yb], (uint32_t)(((it / NY) & 1) ^ 1), abort_flag)) { ok = false; break; }
+            if (!pre_y && !mbar_wait(&y_empty[yb], (uint32_t)(((it / NY) & 1) ^ 1), abort_flag)) { ok = false; break; }
             // this warp's CPW residuals of row `row` -> CPW / 2 columns of Y buffer yb in TMEM
             tmem_st<CPW / 2>(tmem + lane_base + col_y + (uint32_t)(yb * C::Y_COLS + (c0 >> 1)), ypk);
           }
