@@ -1054,45 +1054,58 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // (the cores do not change between the passes), so this pass reads one byte per slot instead
 // of the data tile and the mask, and runs neither the reconstruction GEMM nor the exponential.
 // Units and their partition over the CTAs are those of pass 1 (any partition works: the cache
-// is indexed by unit).  Roles: warp 0 operand producer (S_h per segment, S_str tiles), warp 1
-// TMEM allocator + MMA issuer, warps 2..9 epilogue (TMEM lane quarter = warp % 4, two column
-// groups), warp 10 weight producer (one bulk copy per unit).  Every wait is bounded.
+// is indexed by unit).  Units are handed between the roles in groups of two (one MMA, one
+// commit, one weight copy and one accumulator buffer per group): every barrier wait costs about
+// a hundred cycles even when its phase has completed, and per unit those waits bounded the pass.
+// Roles: warp 0 operand producer (S_h per segment, S_str tiles), warp 1 TMEM allocator + MMA
+// issuer, warps 2..9 epilogue (TMEM lane quarter = warp % 4, two column groups), warp 10 weight
+// producer (one bulk copy per group).  Every wait is bounded.
 template <int KP>
 struct WCfg {
   static constexpr int BN = Cfg<KP, false, false>::BN;   // the streaming columns of pass 1's units
+  static constexpr int GRP = KP == 64 ? 4 : 2;            // units per handoff (one MMA, one commit)
+  static constexpr int GBN = GRP * BN;                    // columns of one group's accumulator
   static constexpr int NSUB = KP / 64;                    // 128-byte K sub-tiles per operand row
   static constexpr int KSTEPS = KP / 16;                  // MMAs of K = 16
-  static constexpr int NGRP = 2;                          // column groups
-  static constexpr int CPW = BN / NGRP;                   // columns per epilogue warp (32 or 16)
+  static constexpr int NGRP = 2;                          // column groups of the epilogue
+  static constexpr int CPW = BN / NGRP;                   // columns of a unit per epilogue warp (32 or 16)
   static constexpr int EPIW = 4 * NGRP;                   // epilogue warps (4 TMEM lane quarters each)
   static constexpr int WT = BM * BN;                      // bytes of one unit's weights
   static constexpr int S_TILE = BM * KP * 2, T_TILE = BN * KP * 2;
   static constexpr int SUB_S = BM * 128, SUB_T = BN * 128;
-  static constexpr int ND = 4;
-  static constexpr int TS = KP == 256 ? 4 : (KP == 128 ? 6 : 8);
-  static constexpr int WS = (KP == 64 || BN == 32) ? 16 : 8;
-  static constexpr int T0 = S_TILE, W0 = T0 + TS * T_TILE, BARS = W0 + WS * WT, TOTAL = BARS + 1024;
+  static constexpr int TSTAGE = GRP * T_TILE, WSTAGE = GRP * WT;
+  static constexpr int ND = 512 / GBN < 4 ? 512 / GBN : 4;   // accumulator buffers (ND GBN <= 512 columns)
+  static constexpr int TS = 3;
+  static constexpr int WS = KP == 64 ? 3 : (KP == 128 ? 5 : 6);
+  static constexpr int T0 = S_TILE, W0 = T0 + TS * TSTAGE, BARS = W0 + WS * WSTAGE, TOTAL = BARS + 1024;
   static constexpr int WPW = 2 + EPIW;                    // warp index of the weight producer
   static constexpr int NTH = 32 * (3 + EPIW);
 };
 
+// Units of a CTA's range are taken in groups of GRP consecutive units of one stationary block
+// (the last group of a block may be shorter); every role walks the same group sequence.  The
+// epilogue reads a group's accumulators two units at a time (register budget).
+// Streaming-operand stage layout: K sub-tile sb of unit h at sb * GRP * SUB_T + h * SUB_T, so
+// that the group's GBN rows of each sub-tile are contiguous (one MMA of N = g BN).
 template <int KP>
 __global__ void __launch_bounds__(WCfg<KP>::NTH, 1)
     k_pass_wls(const __grid_constant__ CUtensorMap mS_h, const __grid_constant__ CUtensorMap mT_hi, const Params p) {
   using C = WCfg<KP>;
-  constexpr int BN = C::BN, CPW = C::CPW, NSUB = C::NSUB, KSTEPS = C::KSTEPS, WT = C::WT;
-  constexpr int ND = C::ND, TS = C::TS, WS = C::WS, EPIW = C::EPIW;
+  constexpr int BN = C::BN, GRP = C::GRP, GBN = C::GBN, CPW = C::CPW, NSUB = C::NSUB, KSTEPS = C::KSTEPS;
+  constexpr int WT = C::WT, ND = C::ND, TS = C::TS, WS = C::WS, EPIW = C::EPIW;
   static_assert(C::TOTAL + 1024 <= SMEM_LIMIT, "shared memory");
   static_assert(CPW == 16 || CPW == 32, "one or two 16-byte weight chunks per epilogue thread");
-  static_assert(ND * BN <= 256, "TMEM columns");
+  static_assert(ND * GBN <= 512, "TMEM columns");
+  static_assert(GBN <= 256 && GBN % 16 == 0, "UMMA N");
+  static_assert(GRP % 2 == 0, "the epilogue takes units in pairs");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::BARS);
-  uint64_t* w_full = bars;                // [WS] weight block landed
-  uint64_t* w_empty = w_full + WS;        // [WS] weight block read by every epilogue thread
-  uint64_t* t_full = w_empty + WS;        // [TS] streaming operand landed
-  uint64_t* t_empty = t_full + TS;        // [TS] streaming operand consumed (MMA commit)
-  uint64_t* d_full = t_empty + TS;        // [ND] D2 done
+  uint64_t* w_full = bars;                // [WS] a group's weight blocks landed
+  uint64_t* w_empty = w_full + WS;        // [WS] weight blocks read by every epilogue thread
+  uint64_t* t_full = w_empty + WS;        // [TS] a group's streaming operands landed
+  uint64_t* t_empty = t_full + TS;        // [TS] streaming operands consumed (MMA commit)
+  uint64_t* d_full = t_empty + TS;        // [ND] a group's D2 done
   uint64_t* d_empty = d_full + ND;        // [ND] D2 read by the epilogue
   uint64_t* s_full = d_empty + ND;        //      step operand landed
   uint64_t* s_empty = s_full + 1;         //      segment's MMAs done with it
@@ -1124,7 +1137,7 @@ __global__ void __launch_bounds__(WCfg<KP>::NTH, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)), "r"(256)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)), "r"(512)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -1138,30 +1151,35 @@ __global__ void __launch_bounds__(WCfg<KP>::NTH, 1)
     if (lane == 0) {
       const uint64_t keep = policy_evict_last();
       int64_t it = 0;
-      int g = 0;
+      int sg = 0;
       bool ok = true;
       int last_phase[TS];
       for (int s = 0; s < TS; ++s) last_phase[s] = -1;
       int s_phase = -1;
-      for (int64_t u = u_begin; u < u_end && ok; ++g) {
+      for (int64_t u = u_begin; u < u_end && ok; ++sg) {
         const int64_t rb = u / p.NT;
         const int64_t seg_end = imin(u_end, (rb + 1) * p.NT);
-        if (g > 0) ok = mbar_wait(s_empty, (uint32_t)((g - 1) & 1), abort_flag);
+        if (sg > 0) ok = mbar_wait(s_empty, (uint32_t)((sg - 1) & 1), abort_flag);
         if (!ok) break;
         mbar_expect_tx(s_full, C::S_TILE);
-        s_phase = g & 1;
+        s_phase = sg & 1;
 #pragma unroll
         for (int sb = 0; sb < NSUB; ++sb)
           tma_2d_hint(sm + sb * C::SUB_S, &mS_h, s_full, sb * 64, (int)(rb * BM), keep);
-        for (int64_t tc = u - rb * p.NT; u < seg_end; ++u, ++it, ++tc) {
+        for (; u < seg_end; ++it) {
+          const int g = (int)imin(GRP, seg_end - u);
+          const int64_t tc = u - rb * p.NT;
           const int s = (int)(it % TS);
           if (!mbar_wait(&t_empty[s], (uint32_t)(((it / TS) & 1) ^ 1), abort_flag)) { ok = false; break; }
-          unsigned char* tb = sm + C::T0 + s * C::T_TILE;
-          mbar_expect_tx(&t_full[s], C::T_TILE);
+          unsigned char* tb = sm + C::T0 + s * C::TSTAGE;
+          mbar_expect_tx(&t_full[s], (uint32_t)(g * C::T_TILE));
           last_phase[s] = (int)((it / TS) & 1);
+          for (int h = 0; h < g; ++h)
 #pragma unroll
-          for (int sb = 0; sb < NSUB; ++sb)
-            tma_2d_hint(tb + sb * C::SUB_T, &mT_hi, &t_full[s], sb * 64, (int)(tc * BN), keep);
+            for (int sb = 0; sb < NSUB; ++sb)
+              tma_2d_hint(tb + sb * GRP * C::SUB_T + h * C::SUB_T, &mT_hi, &t_full[s], sb * 64, (int)((tc + h) * BN),
+                          keep);
+          u += g;
         }
       }
       if (!ok) {
@@ -1182,12 +1200,18 @@ __global__ void __launch_bounds__(WCfg<KP>::NTH, 1)
       int last_phase[WS];
       for (int s = 0; s < WS; ++s) last_phase[s] = -1;
       int64_t it = 0;
-      for (int64_t u = u_begin; u < u_end; ++u, ++it) {
-        const int s = (int)(it % WS);
-        if (!mbar_wait(&w_empty[s], (uint32_t)(((it / WS) & 1) ^ 1), abort_flag)) { ok = false; break; }
-        mbar_expect_tx(&w_full[s], WT);
-        last_phase[s] = (int)((it / WS) & 1);
-        bulk_g2s(sm + C::W0 + s * WT, p.wq + u * (int64_t)WT, WT, &w_full[s], once);
+      for (int64_t u = u_begin; u < u_end && ok;) {
+        const int64_t seg_end = imin(u_end, (u / p.NT + 1) * p.NT);
+        for (; u < seg_end; ++it) {
+          const int g = (int)imin(GRP, seg_end - u);
+          const int s = (int)(it % WS);
+          if (!mbar_wait(&w_empty[s], (uint32_t)(((it / WS) & 1) ^ 1), abort_flag)) { ok = false; break; }
+          mbar_expect_tx(&w_full[s], (uint32_t)(g * WT));
+          last_phase[s] = (int)((it / WS) & 1);
+          // the group's units are consecutive, so are their weight blocks
+          bulk_g2s(sm + C::W0 + s * C::WSTAGE, p.wq + u * (int64_t)WT, (uint32_t)(g * WT), &w_full[s], once);
+          u += g;
+        }
       }
       if (!ok)
         for (int s = 0; s < WS; ++s)
@@ -1198,29 +1222,30 @@ __global__ void __launch_bounds__(WCfg<KP>::NTH, 1)
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      constexpr uint32_t ID = idesc_mma(BM, BN, false);
       const uint64_t dA = sdesc(su32(sm));
       int64_t it = 0;
-      int g = 0;
+      int sg = 0;
       bool ok = true;
-      for (int64_t u = u_begin; u < u_end && ok; ++g) {
-        const int64_t rb = u / p.NT;
-        const int64_t seg_end = imin(u_end, (rb + 1) * p.NT);
-        if (!mbar_wait(s_full, (uint32_t)(g & 1), abort_flag)) { ok = false; break; }
-        for (; u < seg_end; ++u, ++it) {
+      for (int64_t u = u_begin; u < u_end && ok; ++sg) {
+        const int64_t seg_end = imin(u_end, (u / p.NT + 1) * p.NT);
+        if (!mbar_wait(s_full, (uint32_t)(sg & 1), abort_flag)) { ok = false; break; }
+        for (; u < seg_end; ++it) {
+          const int g = (int)imin(GRP, seg_end - u);
           const int s = (int)(it % TS), b = (int)(it & (ND - 1));
           if (!mbar_wait(&t_full[s], (uint32_t)((it / TS) & 1), abort_flag)) { ok = false; break; }
           if (!mbar_wait(&d_empty[b], (uint32_t)(((it / ND) & 1) ^ 1), abort_flag)) { ok = false; break; }
           tc_fence_after();
-          const uint64_t dB = sdesc(su32(sm + C::T0 + s * C::T_TILE));
+          const uint64_t dB = sdesc(su32(sm + C::T0 + s * C::TSTAGE));
+          const uint32_t id = idesc_mma(BM, g * BN, false);   // N = g BN
 #pragma unroll
           for (int kk = 0; kk < KSTEPS; ++kk) {
             const uint64_t ka = (uint64_t)(((kk >> 2) * C::SUB_S + (kk & 3) * 32) >> 4);
-            const uint64_t kb = (uint64_t)(((kk >> 2) * C::SUB_T + (kk & 3) * 32) >> 4);
-            tc_mma<false>(tmem + (uint32_t)(b * BN), dA + ka, dB + kb, ID, kk > 0);
+            const uint64_t kb = (uint64_t)(((kk >> 2) * GRP * C::SUB_T + (kk & 3) * 32) >> 4);
+            tc_mma<false>(tmem + (uint32_t)(b * GBN), dA + ka, dB + kb, id, kk > 0);
           }
           tc_commit(&d_full[b]);
           tc_commit(&t_empty[s]);
+          u += g;
         }
         if (!ok) break;
         tc_commit(s_empty);
@@ -1238,43 +1263,79 @@ __global__ void __launch_bounds__(WCfg<KP>::NTH, 1)
     float2 acc2a = make_float2(0.f, 0.f), acc2b = make_float2(0.f, 0.f);
     const float2 off = make_float2(-8388608.f, -8388608.f);
     int64_t it = 0;
-    for (int64_t u = u_begin; u < u_end; ++u, ++it) {
-      const int b = (int)(it & (ND - 1)), ws = (int)(it % WS);
-      // the warp leaves together when a wait gives up (the TMEM loads are warp-wide)
-      if (!__all_sync(0xffffffffu, mbar_wait(&d_full[b], (uint32_t)((it / ND) & 1), abort_flag))) break;
-      tc_fence_after();
-      uint32_t rd[CPW];
-      tmem_issue<CPW>(tmem + lane_base + (uint32_t)(b * BN + c0), rd);
-      if (!__all_sync(0xffffffffu, mbar_wait(&w_full[ws], (uint32_t)((it / WS) & 1), abort_flag))) {
-        tmem_wait<CPW>(rd);
-        break;
-      }
-      const unsigned char* wt = sm + C::W0 + ws * WT;
-      uint32_t wv[CPW / 4];
+    bool ok = true;
+    for (int64_t u = u_begin; u < u_end && ok;) {
+      const int64_t seg_end = imin(u_end, (u / p.NT + 1) * p.NT);
+      for (; u < seg_end; ++it) {
+        const int g = (int)imin(GRP, seg_end - u);
+        const int b = (int)(it & (ND - 1)), ws = (int)(it % WS);
+        // the warp leaves together when a wait gives up (the TMEM loads are warp-wide)
+        if (!__all_sync(0xffffffffu, mbar_wait(&d_full[b], (uint32_t)((it / ND) & 1), abort_flag))) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        uint32_t rd[2][CPW];
+        tmem_issue<CPW>(tmem + lane_base + (uint32_t)(b * GBN + c0), rd[0]);
+        if (g > 1) tmem_issue<CPW>(tmem + lane_base + (uint32_t)(b * GBN + BN + c0), rd[1]);
+        if (!__all_sync(0xffffffffu, mbar_wait(&w_full[ws], (uint32_t)((it / WS) & 1), abort_flag))) {
+          tmem_wait<CPW>(rd[0]);
+          if (g > 1) tmem_wait<CPW>(rd[1]);
+          ok = false;
+          break;
+        }
+        const unsigned char* wt = sm + C::W0 + ws * C::WSTAGE;
+        uint32_t wv[GRP][CPW / 4];
 #pragma unroll
-      for (int h = 0; h < CPW / 16; ++h) {
-        const uint4 v = *reinterpret_cast<const uint4*>(wt + wq_chunk<BN>(row, (c0 >> 4) + h));
-        wv[4 * h] = v.x;
-        wv[4 * h + 1] = v.y;
-        wv[4 * h + 2] = v.z;
-        wv[4 * h + 3] = v.w;
-      }
-      mbar_arrive(&w_empty[ws]);
-      tmem_wait<CPW>(rd);
-      tc_fence_before();
-      mbar_arrive(&d_empty[b]);
-      // den += q D2^2 (the factor 1 / 255 is applied once at the end); byte k of a word -> the
-      // float 2^23 + q (exponent byte 0x4B above it), minus 2^23, exactly
+        for (int h = 0; h < GRP; ++h) {
+          if (h < g) {
 #pragma unroll
-      for (int j = 0; j < CPW; j += 2) {
-        const uint32_t wd = wv[j >> 2];
-        const uint32_t sel = (uint32_t)(j & 3);
-        const float2 w2 = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(wd, 0x4B000000u, 0x7540u | sel)),
-                                                 __uint_as_float(__byte_perm(wd, 0x4B000000u, 0x7540u | (sel + 1)))),
-                                     off);
-        const float2 d2 = make_float2(__uint_as_float(rd[j]), __uint_as_float(rd[j + 1]));
-        if ((j >> 1) & 1) acc2b = __ffma2_rn(__fmul2_rn(w2, d2), d2, acc2b);
-        else acc2a = __ffma2_rn(__fmul2_rn(w2, d2), d2, acc2a);
+            for (int m = 0; m < CPW / 16; ++m) {
+              const uint4 v = *reinterpret_cast<const uint4*>(wt + h * WT + wq_chunk<BN>(row, (c0 >> 4) + m));
+              wv[h][4 * m] = v.x;
+              wv[h][4 * m + 1] = v.y;
+              wv[h][4 * m + 2] = v.z;
+              wv[h][4 * m + 3] = v.w;
+            }
+          }
+        }
+        mbar_arrive(&w_empty[ws]);
+#pragma unroll
+        for (int h0 = 0; h0 < GRP; h0 += 2) {
+          if (h0 >= g) break;
+          if (h0 > 0) {
+            // the next pair of this group's accumulators
+            tmem_issue<CPW>(tmem + lane_base + (uint32_t)(b * GBN + h0 * BN + c0), rd[0]);
+            if (h0 + 1 < g) tmem_issue<CPW>(tmem + lane_base + (uint32_t)(b * GBN + (h0 + 1) * BN + c0), rd[1]);
+          }
+          tmem_wait<CPW>(rd[0]);
+          if (h0 + 1 < g) tmem_wait<CPW>(rd[1]);
+          if (h0 + 2 >= g) {
+            // every accumulator of the group is in registers: release the buffer to the MMA
+            tc_fence_before();
+            mbar_arrive(&d_empty[b]);
+          }
+          // den += q D2^2 (the factor 1 / 255 is applied once at the end); byte k of a word ->
+          // the float 2^23 + q (exponent byte 0x4B above it), minus 2^23, exactly
+#pragma unroll
+          for (int h1 = 0; h1 < 2; ++h1) {
+            if (h0 + h1 < g) {
+#pragma unroll
+              for (int j = 0; j < CPW; j += 2) {
+                const uint32_t wd = wv[h0 + h1][j >> 2];
+                const uint32_t sel = (uint32_t)(j & 3);
+                const float2 w2 =
+                    __fadd2_rn(make_float2(__uint_as_float(__byte_perm(wd, 0x4B000000u, 0x7540u | sel)),
+                                           __uint_as_float(__byte_perm(wd, 0x4B000000u, 0x7540u | (sel + 1)))),
+                               off);
+                const float2 d2 = make_float2(__uint_as_float(rd[h1][j]), __uint_as_float(rd[h1][j + 1]));
+                if ((j >> 1) & 1) acc2b = __ffma2_rn(__fmul2_rn(w2, d2), d2, acc2b);
+                else acc2a = __ffma2_rn(__fmul2_rn(w2, d2), d2, acc2a);
+              }
+            }
+          }
+        }
+        u += g;
       }
     }
     double den = (double)((acc2a.x + acc2b.x) + (acc2a.y + acc2b.y)) * (1.0 / 255.0);
@@ -1295,7 +1356,7 @@ __global__ void __launch_bounds__(WCfg<KP>::NTH, 1)
   }
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
 }
 
