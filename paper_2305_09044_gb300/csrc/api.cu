@@ -94,6 +94,11 @@ struct Extra {
   DevBuf tmpZ[kMaxN];   // cores given to trd_reconstruct_from
   DevBuf probe_a, probe_b, probe_x;   // adaptive-width probe: inner / outer index, data
   DevBuf dotpart, solve_ctr;          // per-row parts of <d, h>, completion counter
+  // TF32 x 3 / FP32 with K <= 128: (G + lambda I)^{-1} formed on the side stream, so that the
+  // update's h = d (G + lambda I)^{-1} is one row-times-matrix product
+  DevBuf Minv, Ident, inv_dot, inv_ctr, inv_num;
+  int ident_K = 0;
+  int minv_k = -1;            // core whose inverse Minv holds (-1: none)
   DevBuf bc_ctr;                      // per-row completion counters of the back-contraction
   DevBuf stop_part, stop_ctr;         // stopping quantity: per-block sums, completion counter
   DevBuf probe_cand;                  // selection candidates of the adaptive width
@@ -214,6 +219,13 @@ struct Extra {
 Extra* X_(trd_handle* h);
 
 bool is_fp64(const trd_handle* h) { return h->prec == TRD_FP64; }
+// Whether the scaled step takes h from an explicit inverse formed on the side stream (K <= 128):
+// only where the data pass is long enough to hide it.  The side stream has the two SMs the pass
+// leaves free; the inverse (K one-warp substitution rows) fits under the TF32 x 3 and FP32
+// passes (0.24 and 1 ms at 100^4, measured 2.48 -> 2.43 ms per TF32 x 3 step) but not under
+// the BF16 pass 1 (0.12 ms: the step time did not change), and FP64 keeps its substitutions
+// for the 1e-10 contract.
+bool inverse_path(const trd_handle* h) { return h->prec == TRD_TF32X3 || h->prec == TRD_FP32; }
 bool is_tf32(const trd_handle* h) { return h->prec == TRD_TF32X3; }
 // the data passes of this contraction width run on the tensor cores (BF16 up to K' = 256,
 // TF32 up to K' = 64); FP64, FP32 and wider TF32 contractions run the CUDA-core passes
@@ -1098,12 +1110,37 @@ bool prefactor(trd_handle* h, int k, double lambda) {
     PScope ps(h, P_GRAM);
     st = ensure_gram(h, k);
   }
+  x->minv_k = -1;
   if (st == TRD_OK) {
     PScope ps(h, P_CHOL);
     double* Lcm = (double*)h->L.p;
     if (launch_ldl_factor((const double*)h->G.p, K, lambda, Lcm, Lcm + (size_t)K * K, h->scal, h->dstatus,
                           x->side) != cudaSuccess)
       st = TRD_ECUDA;
+    if (st == TRD_OK && inverse_path(h)) {
+      // the explicit inverse from the factor (the 1e-5 contract leaves room for the inverse's
+      // rounding; the FP64 path keeps the substitutions)
+      if (ensure(h, x->Minv, sizeof(double) * (size_t)K * K) != TRD_OK ||
+          ensure(h, x->Ident, sizeof(double) * (size_t)K * K) != TRD_OK ||
+          ensure(h, x->inv_dot, sizeof(double) * (size_t)K) != TRD_OK || ensure(h, x->inv_num, 64) != TRD_OK) {
+        st = TRD_ENOMEM;
+      } else {
+        if (!x->inv_ctr.p) {
+          if (ensure(h, x->inv_ctr, 256) != TRD_OK || cudaMemsetAsync(x->inv_ctr.p, 0, 256, x->side) != cudaSuccess)
+            st = TRD_ECUDA;
+        }
+        if (st == TRD_OK && x->ident_K != K) {
+          if (launch_identity((double*)x->Ident.p, K, x->side) != cudaSuccess) st = TRD_ECUDA;
+          x->ident_K = K;
+        }
+        if (st == TRD_OK &&
+            launch_ldl_solve(Lcm, Lcm + (size_t)K * K, (const double*)x->Ident.p, (double*)x->Minv.p, K, K,
+                             (double*)x->inv_dot.p, (unsigned int*)x->inv_ctr.p, (double*)x->inv_num.p,
+                             x->side) != cudaSuccess)
+          st = TRD_ECUDA;
+        if (st == TRD_OK) x->minv_k = k;
+      }
+    }
   }
   const bool ok = st == TRD_OK && cudaEventRecord(x->ev_join, x->side) == cudaSuccess;
   // the next core's chain prefix does not involve E_k: form it behind the join, so that it
@@ -1154,9 +1191,15 @@ trd_status run_update(trd_handle* h, int k, double lambda, double eta_fixed, int
     double* Dinv = Lcm + (size_t)K * K;
     PScope ps(h, P_SOLVE);
     TRY(ensure(h, xs->dotpart, sizeof(double) * (size_t)h->I[k]));
-    CK(launch_ldl_solve(Lcm, Dinv, d, hh, K, h->I[k], (double*)xs->dotpart.p, (unsigned int*)xs->solve_ctr.p,
-                        h->scal + S_NUM, h->stream),
-       "triangular solves");
+    if (xs->minv_k == k && inverse_path(h))
+      CK(launch_inv_rows((const double*)xs->Minv.p, d, hh, K, h->I[k], (double*)xs->dotpart.p,
+                         (unsigned int*)xs->solve_ctr.p, h->scal + S_NUM, h->stream),
+         "h from the inverse");
+    else
+      CK(launch_ldl_solve(Lcm, Dinv, d, hh, K, h->I[k], (double*)xs->dotpart.p, (unsigned int*)xs->solve_ctr.p,
+                          h->scal + S_NUM, h->stream),
+         "triangular solves");
+    xs->minv_k = -1;
     dot_done = true;
   } else {
     const double* G;
@@ -1637,7 +1680,8 @@ void trd_destroy(trd_t* h) {
   DevBuf* xb[] = {&x->Ework, &x->meta,    &x->stat_sum2, &x->Gloc,    &x->recA, &x->recC,
                   &x->errp,  &x->probe_a, &x->probe_b,   &x->probe_x, &x->dotpart, &x->solve_ctr, &x->bc_ctr, &x->stop_part, &x->stop_ctr, &x->probe_lin, &x->Qb[0], &x->Qb[1], &x->probe_cand, &x->rows_dev,
                   &x->bShi,  &x->bSlo,    &x->bSh,       &x->bThi,    &x->bTlo,    &x->bTT,
-                  &x->Mst[0], &x->Mst[1], &x->bShlo, &x->Xpad, &x->bTThi, &x->bTTlo, &x->gbase, &x->wq};
+                  &x->Mst[0], &x->Mst[1], &x->bShlo, &x->Xpad, &x->bTThi, &x->bTTlo, &x->gbase, &x->wq,
+                  &x->Minv, &x->Ident, &x->inv_dot, &x->inv_ctr, &x->inv_num};
   for (DevBuf* b : xb) free_buf(*b);
   for (int k = 0; k < kMaxN; ++k) { free_buf(x->Eloc[k]); free_buf(x->tmpZ[k]); free_buf(x->smpZ[k]); }
   DevBuf* sb[] = {&x->smpA, &x->smpC, &x->smpGA, &x->smpGC, &x->smpGAd, &x->smpGCd, &x->smpPre, &x->smpPost,

@@ -459,6 +459,94 @@ cudaError_t launch_ldl_solve(const double* Lcm, const double* Dinv, const double
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ explicit inverse, K <= 128
+// Minv = (L D L^T)^{-1} from the factor: the row substitutions above applied to the identity
+// (Minv is symmetric, so its rows are its columns).  The paths whose per-step contract is 1e-5
+// or looser form it on the side stream while the data pass runs; their h = d Minv then costs
+// one parallel row-times-matrix product instead of 2 K dependent substitution steps per row.
+__global__ void k_identity(double* __restrict__ I, int K) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * K; e += gridDim.x * blockDim.x)
+    I[e] = (e / K == e % K) ? 1.0 : 0.0;
+}
+
+cudaError_t launch_identity(double* I, int K, cudaStream_t st) {
+  k_identity<<<(unsigned)((K * K + 255) / 256), 256, 0, st>>>(I, K);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// h = d Minv for rows of d (I_k x K, row-major), one block per row: thread (j, q) sums the
+// terms i of part q (contiguous, ascending) of h_j, the parts are added in q order; <d, h> as
+// in k_ldl_solve (per-row parts, the last block adds them in row order and resets the counter).
+constexpr int INV_NT = 256;
+__global__ void __launch_bounds__(INV_NT) k_inv_rows(const double* __restrict__ Minv, const double* __restrict__ d,
+                                                     double* __restrict__ h, int K, int Kpad, int64_t rows,
+                                                     double* __restrict__ dot_part, unsigned int* __restrict__ ctr,
+                                                     double* __restrict__ num) {
+  __shared__ double sd[kLdlKmax];
+  __shared__ double part[INV_NT];
+  __shared__ double sdot[INV_NT / 32];
+  __shared__ int s_last;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int Q = INV_NT / Kpad, j = t % Kpad, q = t / Kpad;
+  const int i0 = q * K / Q, i1 = (q + 1) * K / Q;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const double* dr = d + row * K;
+    for (int i = t; i < K; i += INV_NT) sd[i] = dr[i];
+    __syncthreads();
+    double a0 = 0.0, a1 = 0.0;
+    if (j < K) {
+      int i = i0;
+      for (; i + 1 < i1; i += 2) {
+        a0 = fma(sd[i], Minv[(int64_t)i * K + j], a0);
+        a1 = fma(sd[i + 1], Minv[(int64_t)(i + 1) * K + j], a1);
+      }
+      if (i < i1) a0 = fma(sd[i], Minv[(int64_t)i * K + j], a0);
+    }
+    part[t] = a0 + a1;
+    __syncthreads();
+    double dh = 0.0;
+    if (t < K) {
+      double hj = 0.0;
+      for (int qq = 0; qq < Q; ++qq) hj += part[qq * Kpad + t];
+      h[row * K + t] = hj;
+      dh = sd[t] * hj;
+    }
+    for (int o = 16; o > 0; o >>= 1) dh += __shfl_down_sync(0xffffffffu, dh, o);
+    if (lane == 0) sdot[w] = dh;
+    __syncthreads();
+    if (t == 0) {
+      double sdh = 0.0;
+      for (int ww = 0; ww < INV_NT / 32; ++ww) sdh += sdot[ww];
+      dot_part[row] = sdh;
+    }
+    __syncthreads();
+  }
+  __threadfence();
+  if (t == 0) s_last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last || w != 0) return;
+  __threadfence();
+  double acc = 0.0;
+  for (int64_t r = lane; r < rows; r += 32) acc += __ldcg(dot_part + r);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    *num = acc;
+    *ctr = 0u;
+  }
+}
+
+cudaError_t launch_inv_rows(const double* Minv, const double* d, double* h, int K, int64_t rows, double* dot_part,
+                            unsigned int* ctr, double* num, cudaStream_t st) {
+  if (K < 1 || K > kLdlKmax || rows < 1) return rows == 0 ? cudaSuccess : cudaErrorInvalidValue;
+  int Kpad = 1;
+  while (Kpad < K) Kpad <<= 1;
+  const unsigned blocks = (unsigned)imin(rows, 65535);
+  k_inv_rows<<<blocks, INV_NT, 0, st>>>(Minv, d, h, K, Kpad, rows, dot_part, ctr, num);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ Cholesky of G + lambda I (K > 128)
 // Blocked right-looking Cholesky (G + lambda I = L L^T, FP64) for the Gram sizes beyond the
 // register-resident LDL^T (K > 128), spread over the GPU: per panel of 32 columns, one warp

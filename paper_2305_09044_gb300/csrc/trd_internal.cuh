@@ -301,6 +301,10 @@ cudaError_t launch_ldl_solve(const double* Lcm, const double* Dinv, const double
 // factor, its reciprocal diagonal, its column-major copy (read by launch_solve_rows)
 cudaError_t launch_cholesky(const double* G, int K, double lambda, double* L, double* scal,
                             int* dstatus, cudaStream_t st);
+// Identity K x K (FP64); h = d Minv for rows of d with <d, h> fused (as launch_ldl_solve).
+cudaError_t launch_identity(double* I, int K, cudaStream_t st);
+cudaError_t launch_inv_rows(const double* Minv, const double* d, double* h, int K, int64_t rows, double* dot_part,
+                            unsigned int* ctr, double* num, cudaStream_t st);
 cudaError_t launch_solve_rows(const double* L, const double* d, double* h, int K, int64_t rows,
                               cudaStream_t st);
 cudaError_t launch_dot(const double* a, const double* b, int64_t n, double* out,
