@@ -932,6 +932,8 @@ __global__ void k_step_update(double* __restrict__ Z, float* __restrict__ Zf, Ha
                               const double* __restrict__ den_in, double fixed_eta, int* dstatus,
                               double* __restrict__ eta_out, double* __restrict__ eta_slot) {
   __shared__ double s_eta;
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     double dn = 0.0;
@@ -986,8 +988,8 @@ cudaError_t launch_step_update(double* Z, float* Zf, const double* h, int64_t n,
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t work = adv.S ? imax(n, adv.n) : n;
-  k_step_update<<<(unsigned)imax(1, imin((work + 255) / 256, 2 * (int64_t)sms)), 256, 0, st>>>(
-      Z, Zf, adv, h, n, num, part, ctas, den, fixed_eta, dstatus, eta, eta_slot);
+  pdl_launch(k_step_update, dim3((unsigned)imax(1, imin((work + 255) / 256, 2 * (int64_t)sms))), dim3(256), 0, st, Z,
+             Zf, adv, h, n, num, part, ctas, den, fixed_eta, dstatus, eta, eta_slot);
   note_launch();
   return cudaGetLastError();
 }

@@ -36,6 +36,8 @@ __global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_
   constexpr int JMAX = NC > 0 ? NC : kMaxN;
   const int n = NC > 0 ? NC : ch.n;
   extern __shared__ __align__(16) unsigned char smem_chain[];
+  pdl_wait();
+  pdl_trigger();
   const int warps = blockDim.x >> 5;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Tc* Mb = reinterpret_cast<Tc*>(smem_chain) + (size_t)w * 3 * cap;
@@ -135,7 +137,8 @@ cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool trans
   auto go = [&](auto kern, size_t esz, auto* o) {
     const size_t smem = (size_t)warps * 3 * cap * esz + tab;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<(unsigned)blocks, warps * 32, smem, st>>>(ch, o, transposed, ld, cap, hi, lo, kpad);
+    pdl_launch(kern, dim3((unsigned)blocks), dim3(warps * 32), smem, st, ch, o, (int)transposed, ld, cap, hi, lo,
+               kpad);
   };
   if (out_double) {
     double* o = (double*)out;
@@ -187,6 +190,8 @@ __global__ void k_backcontract(const double* __restrict__ Tm, SlotSrc sl, int Kp
   // rate on this GPU is close to the FP64 rate.
   extern __shared__ __align__(16) unsigned char smem_bc[];
   __shared__ int s_last;
+  pdl_wait();
+  pdl_trigger();
   const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int szM = mr * mc, szPre = mc * rk, szPost = rk1 * mr, szV = mr * rk;
   const int K = rk * rk1;
@@ -390,9 +395,8 @@ cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int 
   auto go = [&](auto kern, auto tag) -> cudaError_t {
     using E = decltype(tag);
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<grid, threads, smem, st>>>((const double*)Tsum_d, sl, Kp, rows_case ? 1 : 0, mr, mc, (const E*)pre, n_pre,
-                                      (const E*)post, n_post, preC, postC, Ik, rk, rk1, per, dpart, d, ctr, wb,
-                                      tab_rb);
+    pdl_launch(kern, grid, dim3(threads), smem, st, (const double*)Tsum_d, sl, Kp, rows_case ? 1 : 0, mr, mc,
+               (const E*)pre, n_pre, (const E*)post, n_post, preC, postC, Ik, rk, rk1, per, dpart, d, ctr, wb, tab_rb);
     return cudaSuccess;
   };
   if (fp64) {
@@ -434,6 +438,8 @@ cudaError_t launch_reduce_T(const void* Tpart, bool is_double, int splits, int64
 // (field 2) is also written to `obj` when given (the step report's slot).
 __global__ void k_reduce_stats(const double* __restrict__ part, int ctas, double* __restrict__ out,
                                double* __restrict__ obj) {
+  pdl_wait();
+  pdl_trigger();
   const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double s = 0.0;
   for (int c = lane; c < ctas; c += 32) s += part[(int64_t)c * 8 + f];
@@ -446,7 +452,7 @@ __global__ void k_reduce_stats(const double* __restrict__ part, int ctas, double
 
 cudaError_t launch_reduce_stats(const double* stat_part, int ctas, double* stat_sum,
                                 int* /*dstatus*/, cudaStream_t st, double* obj) {
-  k_reduce_stats<<<1, 256, 0, st>>>(stat_part, ctas, stat_sum, obj);
+  pdl_launch(k_reduce_stats, dim3(1), dim3(256), 0, st, stat_part, ctas, stat_sum, obj);
   note_launch();
   return cudaGetLastError();
 }

@@ -26,6 +26,8 @@ __global__ void k_wait_selftest(int arrive, uint32_t limit, int* err) {
 // BF16 hi/lo split of a merged matrix [rows][Kp] (float) into [rows][kpad] (zero padded).
 __global__ void k_split_rows(const float* __restrict__ src, int64_t rows, int Kp, int kpad,
                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t n = rows * kpad;
   const int step = gridDim.x * blockDim.x, e0 = blockIdx.x * blockDim.x + threadIdx.x;
   RowCol rc(e0, step, kpad);
@@ -234,7 +236,8 @@ cudaError_t launch_tc_prep(const float* src, int64_t rows, int Kp, __nv_bfloat16
   const int kpad = tc_kpad(Kp, false);
   if (!kpad) return cudaErrorInvalidValue;
   const int64_t n = rows * kpad;
-  tc::k_split_rows<<<(unsigned)imin((n + 255) / 256, 8192), 256, 0, st>>>(src, rows, Kp, kpad, hi, lo);
+  pdl_launch(tc::k_split_rows, dim3((unsigned)imin((n + 255) / 256, 8192)), dim3(256), 0, st, src, rows, Kp, kpad, hi,
+             lo);
   note_launch();
   return cudaGetLastError();
 }

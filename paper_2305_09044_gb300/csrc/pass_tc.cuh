@@ -496,6 +496,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // the set-up above touches no global memory: it overlaps the previous kernel's tail
+  pdl_wait();
+  pdl_trigger();
   // TMEM columns: D1[b] at b BN (b < ND); pass 1: the T accumulator at ND BN (KP columns)
   // followed by the NY weighted-residual buffers Y (the A operand of GEMM 2: BF16 pairs, or
   // TF32 hi then lo); pass 2: D2[b] at (ND + b) BN, then the step operand S_h (SH_TMEM)
@@ -1145,6 +1148,8 @@ __global__ void __launch_bounds__(WCfg<KP>::NTH, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  pdl_wait();
+  pdl_trigger();
 
   if (warp == 0) {
     // ---------------------------------------------------------------- operand producer
@@ -1430,7 +1435,8 @@ cudaError_t launch_pass_tc_kp(bool rows_case, bool pass2, bool full_stats, const
     const size_t smem = (size_t)smem_bytes + 1024;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<p.G, NTHREADS, smem, st>>>(mS_hi, mS_lo, mS_h, mT_hi, mT_lo, mX, mTT_hi, mTT_lo, p);
+    e = pdl_launch(kern, dim3(p.G), dim3(NTHREADS), smem, st, mS_hi, mS_lo, mS_h, mT_hi, mT_lo, mX, mTT_hi, mTT_lo, p);
+    if (e != cudaSuccess) return e;
     note_launch();
     return cudaGetLastError();
   };
@@ -1468,7 +1474,8 @@ cudaError_t launch_pass_wls_kp(const void* S_h, const void* T_hi, const unsigned
   const size_t smem = (size_t)C::TOTAL + 1024;
   cudaError_t e = cudaFuncSetAttribute(k_pass_wls<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_pass_wls<KP><<<p.G, C::NTH, smem, st>>>(mS_h, mT_hi, p);
+  e = pdl_launch(k_pass_wls<KP>, dim3(p.G), dim3(C::NTH), smem, st, mS_h, mT_hi, p);
+  if (e != cudaSuccess) return e;
   note_launch();
   return cudaGetLastError();
 }

@@ -270,6 +270,8 @@ __global__ void k_to_double(const float* __restrict__ src, int64_t n, double* __
 
 template <typename T>
 __global__ void k_from_double(const double* __restrict__ src, int64_t n, T* __restrict__ dst) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = (T)src[i];
 }
@@ -331,9 +333,11 @@ cudaError_t launch_to_double(const float* src, int64_t n, double* dst, cudaStrea
 
 cudaError_t launch_from_double(const double* src, int64_t n, void* dst, bool fp64, cudaStream_t st) {
   if (fp64)
-    k_from_double<double><<<(unsigned)imin((n + 255) / 256, 4096), 256, 0, st>>>(src, n, (double*)dst);
+    pdl_launch(k_from_double<double>, dim3((unsigned)imin((n + 255) / 256, 4096)), dim3(256), 0, st, src, n,
+               (double*)dst);
   else
-    k_from_double<float><<<(unsigned)imin((n + 255) / 256, 4096), 256, 0, st>>>(src, n, (float*)dst);
+    pdl_launch(k_from_double<float>, dim3((unsigned)imin((n + 255) / 256, 4096)), dim3(256), 0, st, src, n,
+               (float*)dst);
   note_launch();
   return cudaGetLastError();
 }

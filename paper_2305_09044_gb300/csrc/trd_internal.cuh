@@ -12,6 +12,31 @@
 
 namespace trd {
 
+// Programmatic dependent launch along the main stream's chain of small kernels: a kernel so
+// launched may become resident while its predecessor in the stream finishes (its launch and
+// prologue overlap the predecessor's tail); it calls pdl_wait() before touching anything an
+// earlier kernel wrote (the wait returns once the predecessor has completed and its memory is
+// visible; it is a no-op for a kernel launched without the attribute), then pdl_trigger() so
+// that its own successor may launch.  Only kernels that begin this way are launched with
+// pdl_launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+
 constexpr int kMaxN = TRD_MAX_ORDER;
 constexpr int kMaxR = TRD_MAX_RANK;
 constexpr int64_t kProbeMax = int64_t(1) << 20;   // adaptive-width probe size
