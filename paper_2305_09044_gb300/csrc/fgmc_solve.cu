@@ -11,6 +11,8 @@ namespace trd {
 // staged through shared memory in chunks of 32; each thread owns output entries.
 __global__ void k_fgmc_E(const double* __restrict__ Z, const int32_t* __restrict__ idx, int64_t n_all,
                          int r, int r1, int CH, double* __restrict__ E) {
+  pdl_wait();
+  pdl_trigger();
   // slice range of this block row (gridDim.y parts, contiguous)
   const int64_t per = (n_all + gridDim.y - 1) / gridDim.y;
   const int64_t qb = (int64_t)blockIdx.y * per;
@@ -46,6 +48,8 @@ __global__ void k_fgmc_E(const double* __restrict__ Z, const int32_t* __restrict
 }
 
 __global__ void k_sum_parts(const double* __restrict__ part, int parts, int64_t n, double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int q = 0; q < parts; ++q) s += part[(int64_t)q * n + i];
@@ -62,6 +66,8 @@ __global__ void k_sum_parts(const double* __restrict__ part, int parts, int64_t 
 // part order: the result does not depend on scheduling).  256 threads, 2 x 2 outputs each.
 __global__ void __launch_bounds__(256) k_fgmc_E_gram(const double* __restrict__ Z, int64_t n_all, int r, int r1,
                                                      double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int T = 32, CH = 32;
   __shared__ double sa[CH][T + 1], sb[CH][T + 1];
   const int K = r * r1;
@@ -117,10 +123,10 @@ cudaError_t launch_fgmc_E(const double* Z, const int32_t* idx, int64_t n, int rk
   if (!idx && work && rk * rk1 > kLdlKmax) {
     const int nt = (rk * rk1 + 31) / 32, pairs = nt * (nt + 1) / 2;
     const int parts = (int)imax(1, imin(imin(16, (n + 63) / 64), (2 * 152 + pairs - 1) / pairs));
-    k_fgmc_E_gram<<<dim3((unsigned)pairs, (unsigned)parts), 256, 0, st>>>(Z, n, rk, rk1, parts > 1 ? work : E);
+    pdl_launch(k_fgmc_E_gram, dim3(dim3((unsigned)pairs, (unsigned)parts)), dim3(256), 0, st, Z, n, rk, rk1, parts > 1 ? work : E);
     note_launch();
     if (parts == 1) return cudaGetLastError();
-    k_sum_parts<<<(unsigned)imin((tot + 255) / 256, 4096), 256, 0, st>>>(work, parts, tot, E);
+    pdl_launch(k_sum_parts, dim3((unsigned)imin((tot + 255) / 256, 4096)), dim3(256), 0, st, work, parts, tot, E);
     note_launch();
     return cudaGetLastError();
   }
@@ -134,10 +140,10 @@ cudaError_t launch_fgmc_E(const double* Z, const int32_t* idx, int64_t n, int rk
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_fgmc_E, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid(blocks, (unsigned)parts);
-  k_fgmc_E<<<grid, 128, smem, st>>>(Z, idx, n, rk, rk1, CH, parts > 1 ? work : E);
+  pdl_launch(k_fgmc_E, dim3(grid), dim3(128), smem, st, Z, idx, n, rk, rk1, CH, parts > 1 ? work : E);
   note_launch();
   if (parts == 1) return cudaGetLastError();
-  k_sum_parts<<<(unsigned)imin((tot + 255) / 256, 4096), 256, 0, st>>>(work, parts, tot, E);
+  pdl_launch(k_sum_parts, dim3((unsigned)imin((tot + 255) / 256, 4096)), dim3(256), 0, st, work, parts, tot, E);
   note_launch();
   return cudaGetLastError();
 }
@@ -149,6 +155,8 @@ cudaError_t launch_fgmc_E(const double* Z, const int32_t* idx, int64_t n, int rk
 // FP64 issue rate per SM is low).
 __global__ void k_dgemm(const double* __restrict__ A, const double* __restrict__ B,
                         double* __restrict__ C, int M, int N, int K, int transB) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sA[8][9], sB[8][9];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int row = blockIdx.y * 8 + ty, col = blockIdx.x * 8 + tx;
@@ -171,7 +179,7 @@ __global__ void k_dgemm(const double* __restrict__ A, const double* __restrict__
 cudaError_t launch_dgemm(const double* A, const double* B, double* C, int M, int N, int K,
                          bool transB, cudaStream_t st) {
   dim3 grid((N + 7) / 8, (M + 7) / 8), block(8, 8);
-  k_dgemm<<<grid, block, 0, st>>>(A, B, C, M, N, K, transB ? 1 : 0);
+  pdl_launch(k_dgemm, dim3(grid), dim3(block), 0, st, A, B, C, M, N, K, transB ? 1 : 0);
   note_launch();
   return cudaGetLastError();
 }
@@ -180,6 +188,8 @@ cudaError_t launch_dgemm(const double* A, const double* B, double* C, int M, int
 // G[a + b q, a' + b' q] = T[b p + b', a q + a'] for the subchain with p x q slices
 // (p = r_{k+1}, q = r_k); T is p^2 x q^2 row-major.
 __global__ void k_phi(const double* __restrict__ T, int p, int q, double* __restrict__ G) {
+  pdl_wait();
+  pdl_trigger();
   const int K = p * q;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * K; e += gridDim.x * blockDim.x) {
     const int r = e / K, c = e % K;
@@ -190,7 +200,7 @@ __global__ void k_phi(const double* __restrict__ T, int p, int q, double* __rest
 
 cudaError_t launch_phi(const double* T, int p, int q, double* G, cudaStream_t st) {
   const int K = p * q;
-  k_phi<<<(K * K + 255) / 256, 256, 0, st>>>(T, p, q, G);
+  pdl_launch(k_phi, dim3((K * K + 255) / 256), dim3(256), 0, st, T, p, q, G);
   note_launch();
   return cudaGetLastError();
 }
@@ -246,6 +256,8 @@ template <int S>
 __global__ void __launch_bounds__(LDL_NT, 1)
     k_ldl_factor(const double* __restrict__ G, int K, double lam_in, double* __restrict__ Lcm,
                  double* __restrict__ Dinv, double* __restrict__ scal, int* __restrict__ dstatus) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double s_c[2][kLdlKmax];
   __shared__ double s_l[2][kLdlKmax];
   __shared__ double s_red[LDL_NT / 32];
@@ -431,11 +443,11 @@ cudaError_t launch_ldl_factor(const double* G, int K, double lambda, double* Lcm
   if (K < 1 || K > kLdlKmax) return cudaErrorInvalidValue;
   const int nel = K * (K + 1) / 2;
   if (nel <= 9 * LDL_NT)
-    k_ldl_factor<9><<<1, LDL_NT, 0, st>>>(G, K, lambda, Lcm, Dinv, scal, dstatus);
+    pdl_launch(k_ldl_factor<9>, dim3(1), dim3(LDL_NT), 0, st, G, K, lambda, Lcm, Dinv, scal, dstatus);
   else if (nel <= 20 * LDL_NT)
-    k_ldl_factor<20><<<1, LDL_NT, 0, st>>>(G, K, lambda, Lcm, Dinv, scal, dstatus);
+    pdl_launch(k_ldl_factor<20>, dim3(1), dim3(LDL_NT), 0, st, G, K, lambda, Lcm, Dinv, scal, dstatus);
   else
-    k_ldl_factor<33><<<1, LDL_NT, 0, st>>>(G, K, lambda, Lcm, Dinv, scal, dstatus);
+    pdl_launch(k_ldl_factor<33>, dim3(1), dim3(LDL_NT), 0, st, G, K, lambda, Lcm, Dinv, scal, dstatus);
   note_launch();
   return cudaGetLastError();
 }
@@ -465,12 +477,14 @@ cudaError_t launch_ldl_solve(const double* Lcm, const double* Dinv, const double
 // or looser form it on the side stream while the data pass runs; their h = d Minv then costs
 // one parallel row-times-matrix product instead of 2 K dependent substitution steps per row.
 __global__ void k_identity(double* __restrict__ I, int K) {
+  pdl_wait();
+  pdl_trigger();
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * K; e += gridDim.x * blockDim.x)
     I[e] = (e / K == e % K) ? 1.0 : 0.0;
 }
 
 cudaError_t launch_identity(double* I, int K, cudaStream_t st) {
-  k_identity<<<(unsigned)((K * K + 255) / 256), 256, 0, st>>>(I, K);
+  pdl_launch(k_identity, dim3((unsigned)((K * K + 255) / 256)), dim3(256), 0, st, I, K);
   note_launch();
   return cudaGetLastError();
 }
@@ -561,6 +575,8 @@ constexpr int BCH_NB = 32;
 
 __global__ void k_bchol_init(const double* __restrict__ G, int K, double lam_in, double* __restrict__ W,
                              double* __restrict__ scal) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double s_red[8];
   __shared__ double s_lam;
   const int tid = threadIdx.x;
@@ -609,6 +625,8 @@ __device__ __forceinline__ double rsqrt_pivot(double p) {
 constexpr int BCH_DT = 128;
 __global__ void __launch_bounds__(BCH_DT) k_bchol_diag(double* __restrict__ W, double* __restrict__ rdiag, int K,
                                                        int j0, int* __restrict__ dstatus) {
+  pdl_wait();
+  pdl_trigger();
   if (*(volatile int*)dstatus & DEV_SINGULAR) return;
   __shared__ double a[BCH_NB][BCH_NB + 1];
   __shared__ double rr[BCH_NB];
@@ -656,6 +674,8 @@ __global__ void __launch_bounds__(BCH_DT) k_bchol_diag(double* __restrict__ W, d
 // column-oriented form: x_t is final at step t and is subtracted from the later entries)
 __global__ void __launch_bounds__(256) k_bchol_panel(double* __restrict__ W, const double* __restrict__ rdiag,
                                                      int K, int j0, const int* __restrict__ dstatus) {
+  pdl_wait();
+  pdl_trigger();
   if (*(volatile const int*)dstatus & DEV_SINGULAR) return;
   __shared__ double sL[BCH_NB][BCH_NB + 1];
   __shared__ double sr[BCH_NB];
@@ -683,6 +703,8 @@ __global__ void __launch_bounds__(256) k_bchol_panel(double* __restrict__ W, con
 // the packed lower triangle of tiles -> (bi, bj), bj <= bi
 __global__ void __launch_bounds__(256) k_bchol_update(double* __restrict__ W, int K, int j0,
                                                       const int* __restrict__ dstatus) {
+  pdl_wait();
+  pdl_trigger();
   if (*(volatile const int*)dstatus & DEV_SINGULAR) return;
   __shared__ double sa[BCH_NB][BCH_NB + 1];
   __shared__ double sb[BCH_NB][BCH_NB + 1];
@@ -713,6 +735,8 @@ __global__ void __launch_bounds__(256) k_bchol_update(double* __restrict__ W, in
 // column-major copy of the lower triangle: Lc[j K + i] = L[i][j], i >= j (32 x 32 tiles)
 __global__ void __launch_bounds__(256) k_bchol_colcopy(const double* __restrict__ W, double* __restrict__ Lc,
                                                        int K, const int* __restrict__ dstatus) {
+  pdl_wait();
+  pdl_trigger();
   if (*(volatile const int*)dstatus & DEV_SINGULAR) return;
   __shared__ double t[BCH_NB][BCH_NB + 1];
   const int i0 = blockIdx.y * BCH_NB, j0 = blockIdx.x * BCH_NB;
@@ -733,21 +757,21 @@ cudaError_t launch_cholesky(const double* G, int K, double lambda, double* L, do
   double* rdiag = L + (int64_t)K * K;
   double* Lc = rdiag + K;
   const int64_t n = (int64_t)K * K;
-  k_bchol_init<<<(unsigned)imin((n + 255) / 256, 1024), 256, 0, st>>>(G, K, lambda, L, scal);
+  pdl_launch(k_bchol_init, dim3((unsigned)imin((n + 255) / 256, 1024)), dim3(256), 0, st, G, K, lambda, L, scal);
   note_launch();
   for (int j0 = 0; j0 < K; j0 += BCH_NB) {
-    k_bchol_diag<<<1, BCH_DT, 0, st>>>(L, rdiag, K, j0, dstatus);
+    pdl_launch(k_bchol_diag, dim3(1), dim3(BCH_DT), 0, st, L, rdiag, K, j0, dstatus);
     note_launch();
     const int rest = K - j0 - BCH_NB;
     if (rest <= 0) break;
-    k_bchol_panel<<<(unsigned)imin((rest + 7) / 8, 1024), 256, 0, st>>>(L, rdiag, K, j0, dstatus);
+    pdl_launch(k_bchol_panel, dim3((unsigned)imin((rest + 7) / 8, 1024)), dim3(256), 0, st, L, rdiag, K, j0, dstatus);
     note_launch();
     const int nt = (rest + BCH_NB - 1) / BCH_NB;
-    k_bchol_update<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(L, K, j0, dstatus);
+    pdl_launch(k_bchol_update, dim3((unsigned)(nt * (nt + 1) / 2)), dim3(256), 0, st, L, K, j0, dstatus);
     note_launch();
   }
   const unsigned tb = (unsigned)((K + BCH_NB - 1) / BCH_NB);
-  k_bchol_colcopy<<<dim3(tb, tb), 256, 0, st>>>(L, Lc, K, dstatus);
+  pdl_launch(k_bchol_colcopy, dim3(dim3(tb, tb)), dim3(256), 0, st, L, Lc, K, dstatus);
   note_launch();
   return cudaGetLastError();
 }
@@ -1001,6 +1025,8 @@ cudaError_t launch_step_update(double* Z, float* Zf, const double* h, int64_t n,
 __global__ void __launch_bounds__(256) k_stop_error(const double* __restrict__ D, double* __restrict__ Dprev,
                                                     int64_t n, double* __restrict__ part,
                                                     unsigned int* __restrict__ ctr, double* __restrict__ e_out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double s1[8], s2[8];
   __shared__ int s_last;
   double a = 0.0, b = 0.0;
@@ -1046,7 +1072,7 @@ __global__ void __launch_bounds__(256) k_stop_error(const double* __restrict__ D
 cudaError_t launch_stop_error(const double* D, double* Dprev, int64_t n, double* part, unsigned int* ctr,
                               double* e_out, cudaStream_t st) {
   const unsigned blocks = (unsigned)imax(1, imin((n + 255) / 256, kStopBlocks));
-  k_stop_error<<<blocks, 256, 0, st>>>(D, Dprev, n, part, ctr, e_out);
+  pdl_launch(k_stop_error, dim3(blocks), dim3(256), 0, st, D, Dprev, n, part, ctr, e_out);
   note_launch();
   return cudaGetLastError();
 }

@@ -586,6 +586,8 @@ struct GatherArgs {
 // Offset in X of every fibre of the sketch along its first mode: o = overline{i_2 ... i_N}
 // (first digit fastest) -> sum_{m >= 1} idx_m(i_m) stride_m.  One thread per fibre.
 __global__ void k_gather_base(GatherArgs g, int64_t* __restrict__ obase) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < g.nouter; o += step) {
     int64_t rem = o, full = 0;
@@ -606,6 +608,8 @@ __global__ void k_gather_base(GatherArgs g, int64_t* __restrict__ obase) {
 // indices).
 constexpr int GW = 4;
 __global__ void k_gather(GatherArgs g) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int64_t wpb = blockDim.x >> 5;
   const int64_t s1 = g.sdim[0];
@@ -669,10 +673,10 @@ cudaError_t launch_gather(const float* X, const uint32_t* M, int N, const int64_
     cudaError_t e = cudaMemsetAsync(PI + g.words, 0, (words_padded - g.words) * 4, st);
     if (e != cudaSuccess) return e;
   }
-  k_gather_base<<<(unsigned)imin((g.nouter + 255) / 256, 152 * 8), 256, 0, st>>>(g, obase);
+  pdl_launch(k_gather_base, dim3((unsigned)imin((g.nouter + 255) / 256, 152 * 8)), dim3(256), 0, st, g, obase);
   note_launch();
   const unsigned blocks = (unsigned)imin((g.words + 8 * GW - 1) / (8 * GW), 152 * 16);
-  k_gather<<<blocks, 256, 0, st>>>(g);
+  pdl_launch(k_gather, dim3(blocks), dim3(256), 0, st, g);
   note_launch();
   return cudaGetLastError();
 }

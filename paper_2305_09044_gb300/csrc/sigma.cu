@@ -288,6 +288,8 @@ constexpr int kSelBatch = 8;
 
 __global__ void __launch_bounds__(kSelThreads) k_sel_digit(const uint64_t* __restrict__ keys, int64_t n,
                                                            double* __restrict__ work, int digit) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ unsigned int h[4][256];
   for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&h[0][0])[i] = 0;
   const uint64_t* u = reinterpret_cast<const uint64_t*>(work);
@@ -344,6 +346,8 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_digit(const uint64_t* __res
 // are appended to cand[] (warp-aggregated atomic count in u[24]; their order is irrelevant).
 __global__ void __launch_bounds__(kSelThreads) k_sel_compact(const uint64_t* __restrict__ keys, int64_t n,
                                                              double* __restrict__ work, uint64_t* __restrict__ cand) {
+  pdl_wait();
+  pdl_trigger();
   uint64_t* u = reinterpret_cast<uint64_t*>(work);
   uint64_t pre[4];
 #pragma unroll
@@ -382,6 +386,8 @@ __global__ void __launch_bounds__(kFinThreads) k_sel_finish(const uint64_t* __re
                                                             double rms_override, double sigma_prev,
                                                             const double* __restrict__ sigma_prev_dev,
                                                             double* __restrict__ sigma_out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ unsigned int h[4][256];
   __shared__ uint64_t s_pre[4], s_rank[4];
   uint64_t* u = reinterpret_cast<uint64_t*>(work);
@@ -486,6 +492,8 @@ __global__ void __launch_bounds__(kSelThreads)
     k_sel_probe(const T* __restrict__ A, const T* __restrict__ C, int Kp, const int32_t* __restrict__ pa,
                 const int32_t* __restrict__ pb, const float* __restrict__ px, int64_t n,
                 uint64_t* __restrict__ keys, double* __restrict__ work) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ unsigned int h0[256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) h0[i] = 0;
   __syncthreads();
@@ -543,6 +551,8 @@ __global__ void __launch_bounds__(kSelThreads)
     k_sel_probe16(const T* __restrict__ A, const T* __restrict__ C, int Kp, const int32_t* __restrict__ pa,
                   const int32_t* __restrict__ pb, const float* __restrict__ px, int64_t n,
                   uint64_t* __restrict__ keys, double* __restrict__ work) {
+  pdl_wait();
+  pdl_trigger();
   using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
   constexpr int VW = 16 / sizeof(T);
   __shared__ unsigned int h0[256];
@@ -659,13 +669,13 @@ __global__ void k_probe_setup(const float* __restrict__ X, const uint32_t* __res
 cudaError_t run_digits(const uint64_t* keys, int64_t n, double* work, uint64_t* cand, double rms_override,
                        double sigma_prev, const double* sigma_prev_dev, double* sigma_out, cudaStream_t st) {
   const int nb = (int)imax(1, imin(kSelBlocks, (n + 32 * kSelBatch * 8 - 1) / (32 * kSelBatch * 8)));
-  k_sel_digit<<<nb, kSelThreads, 0, st>>>(keys, n, work, 1);
+  pdl_launch(k_sel_digit, dim3(nb), dim3(kSelThreads), 0, st, keys, n, work, 1);
   note_launch();
-  k_sel_digit<<<nb, kSelThreads, 0, st>>>(keys, n, work, 2);
+  pdl_launch(k_sel_digit, dim3(nb), dim3(kSelThreads), 0, st, keys, n, work, 2);
   note_launch();
-  k_sel_compact<<<nb, kSelThreads, 0, st>>>(keys, n, work, cand);
+  pdl_launch(k_sel_compact, dim3(nb), dim3(kSelThreads), 0, st, keys, n, work, cand);
   note_launch();
-  k_sel_finish<<<1, kFinThreads, 0, st>>>(cand, work, rms_override, sigma_prev, sigma_prev_dev, sigma_out);
+  pdl_launch(k_sel_finish, dim3(1), dim3(kFinThreads), 0, st, cand, work, rms_override, sigma_prev, sigma_prev_dev, sigma_out);
   note_launch();
   return cudaGetLastError();
 }
@@ -703,16 +713,16 @@ cudaError_t launch_probe_sigma_merged(const void* A, const void* C, bool fp64, i
   // one lane per probe, a few probes per lane
   const int nb = (int)imax(1, imin(kSelBlocks, (n + 2 * kSelThreads - 1) / (2 * kSelThreads)));
   if (fp64 && Kp % 2 == 0)
-    k_sel_probe16<double><<<nb, kSelThreads, 0, st>>>((const double*)A, (const double*)C, Kp, pa, pb, px, n, keys,
+    pdl_launch(k_sel_probe16<double>, dim3(nb), dim3(kSelThreads), 0, st, (const double*)A, (const double*)C, Kp, pa, pb, px, n, keys,
                                                       work);
   else if (fp64)
-    k_sel_probe<double><<<nb, kSelThreads, 0, st>>>((const double*)A, (const double*)C, Kp, pa, pb, px, n,
+    pdl_launch(k_sel_probe<double>, dim3(nb), dim3(kSelThreads), 0, st, (const double*)A, (const double*)C, Kp, pa, pb, px, n,
                                                            keys, work);
   else if (Kp % 4 == 0)
-    k_sel_probe16<float><<<nb, kSelThreads, 0, st>>>((const float*)A, (const float*)C, Kp, pa, pb, px, n, keys,
+    pdl_launch(k_sel_probe16<float>, dim3(nb), dim3(kSelThreads), 0, st, (const float*)A, (const float*)C, Kp, pa, pb, px, n, keys,
                                                      work);
   else
-    k_sel_probe<float><<<nb, kSelThreads, 0, st>>>((const float*)A, (const float*)C, Kp, pa, pb, px, n,
+    pdl_launch(k_sel_probe<float>, dim3(nb), dim3(kSelThreads), 0, st, (const float*)A, (const float*)C, Kp, pa, pb, px, n,
                                                           keys, work);
   note_launch();
   e = cudaGetLastError();
