@@ -962,6 +962,9 @@ __global__ void k_step_update(double* __restrict__ Z, float* __restrict__ Zf, Ha
     const int lane = threadIdx.x;
     double dn = 0.0;
     if (part) {
+      // the loads are independent: unrolled so that several are in flight (the sum keeps its
+      // order)
+#pragma unroll 8
       for (int c = lane; c < ctas; c += 32) dn += part[(int64_t)c * 8 + 6];
       for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(0xffffffffu, dn, o);
     } else if (den_in) {
@@ -985,6 +988,7 @@ __global__ void k_step_update(double* __restrict__ Z, float* __restrict__ Zf, Ha
   __syncthreads();
   const double e = s_eta;
   if (e == 0.0) return;   // a rejected step leaves the core untouched (h may be non-finite)
+#pragma unroll 4
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double z = fma(e, h[i], Z[i]);
     Z[i] = z;
@@ -994,7 +998,30 @@ __global__ void k_step_update(double* __restrict__ Z, float* __restrict__ Zf, Ha
   const float ef = (float)e;
   const int step = gridDim.x * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
   RowCol rc(i0, step, adv.Kp);
-  for (int64_t i = i0; i < adv.n; i += step, rc.next()) {
+  // four elements per round, all loads first (S and S_h never overlap, but the compiler cannot
+  // know it through the struct, so it would not move a load above the previous store)
+  int64_t i = i0;
+  for (; i + 3 * (int64_t)step < adv.n; i += 4 * (int64_t)step) {
+    float sv[4], hv[4];
+    int64_t q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t ii = i + u * (int64_t)step;
+      sv[u] = adv.S[ii];
+      hv[u] = adv.Sh[ii];
+      q[u] = (int64_t)rc.r * adv.kpad + rc.c;
+      rc.next();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float v = fmaf(ef, hv[u], sv[u]);
+      adv.S[i + u * (int64_t)step] = v;
+      const __nv_bfloat16 vh = bf16_rn(v);
+      adv.hi[q[u]] = vh;
+      adv.lo[q[u]] = bf16_rn(v - __bfloat162float(vh));
+    }
+  }
+  for (; i < adv.n; i += step, rc.next()) {
     const float v = fmaf(ef, adv.Sh[i], adv.S[i]);
     adv.S[i] = v;
     const __nv_bfloat16 vh = bf16_rn(v);
