@@ -123,7 +123,8 @@ cudaError_t launch_fgmc_E(const double* Z, const int32_t* idx, int64_t n, int rk
   if (!idx && work && rk * rk1 > kLdlKmax) {
     const int nt = (rk * rk1 + 31) / 32, pairs = nt * (nt + 1) / 2;
     const int parts = (int)imax(1, imin(imin(16, (n + 63) / 64), (2 * 152 + pairs - 1) / pairs));
-    pdl_launch(k_fgmc_E_gram, dim3(dim3((unsigned)pairs, (unsigned)parts)), dim3(256), 0, st, Z, n, rk, rk1, parts > 1 ? work : E);
+    pdl_launch(k_fgmc_E_gram, dim3((unsigned)pairs, (unsigned)parts), dim3(256), 0, st, Z, n, rk, rk1,
+               parts > 1 ? work : E);
     note_launch();
     if (parts == 1) return cudaGetLastError();
     pdl_launch(k_sum_parts, dim3((unsigned)imin((tot + 255) / 256, 4096)), dim3(256), 0, st, work, parts, tot, E);

@@ -396,7 +396,8 @@ cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int 
     using E = decltype(tag);
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     pdl_launch(kern, grid, dim3(threads), smem, st, (const double*)Tsum_d, sl, Kp, rows_case ? 1 : 0, mr, mc,
-               (const E*)pre, n_pre, (const E*)post, n_post, preC, postC, Ik, rk, rk1, per, dpart, d, ctr, wb, tab_rb);
+               (const E*)pre, n_pre, (const E*)post, n_post, preC, postC, Ik, rk, rk1, per, dpart, d, ctr, wb,
+               tab_rb);
     return cudaSuccess;
   };
   if (fp64) {

@@ -675,7 +675,8 @@ cudaError_t run_digits(const uint64_t* keys, int64_t n, double* work, uint64_t* 
   note_launch();
   pdl_launch(k_sel_compact, dim3(nb), dim3(kSelThreads), 0, st, keys, n, work, cand);
   note_launch();
-  pdl_launch(k_sel_finish, dim3(1), dim3(kFinThreads), 0, st, cand, work, rms_override, sigma_prev, sigma_prev_dev, sigma_out);
+  pdl_launch(k_sel_finish, dim3(1), dim3(kFinThreads), 0, st, cand, work, rms_override, sigma_prev, sigma_prev_dev,
+             sigma_out);
   note_launch();
   return cudaGetLastError();
 }
@@ -713,17 +714,17 @@ cudaError_t launch_probe_sigma_merged(const void* A, const void* C, bool fp64, i
   // one lane per probe, a few probes per lane
   const int nb = (int)imax(1, imin(kSelBlocks, (n + 2 * kSelThreads - 1) / (2 * kSelThreads)));
   if (fp64 && Kp % 2 == 0)
-    pdl_launch(k_sel_probe16<double>, dim3(nb), dim3(kSelThreads), 0, st, (const double*)A, (const double*)C, Kp, pa, pb, px, n, keys,
-                                                      work);
+    pdl_launch(k_sel_probe16<double>, dim3(nb), dim3(kSelThreads), 0, st, (const double*)A, (const double*)C, Kp, pa,
+               pb, px, n, keys, work);
   else if (fp64)
-    pdl_launch(k_sel_probe<double>, dim3(nb), dim3(kSelThreads), 0, st, (const double*)A, (const double*)C, Kp, pa, pb, px, n,
-                                                           keys, work);
+    pdl_launch(k_sel_probe<double>, dim3(nb), dim3(kSelThreads), 0, st, (const double*)A, (const double*)C, Kp, pa,
+               pb, px, n, keys, work);
   else if (Kp % 4 == 0)
-    pdl_launch(k_sel_probe16<float>, dim3(nb), dim3(kSelThreads), 0, st, (const float*)A, (const float*)C, Kp, pa, pb, px, n, keys,
-                                                     work);
+    pdl_launch(k_sel_probe16<float>, dim3(nb), dim3(kSelThreads), 0, st, (const float*)A, (const float*)C, Kp, pa, pb,
+               px, n, keys, work);
   else
-    pdl_launch(k_sel_probe<float>, dim3(nb), dim3(kSelThreads), 0, st, (const float*)A, (const float*)C, Kp, pa, pb, px, n,
-                                                          keys, work);
+    pdl_launch(k_sel_probe<float>, dim3(nb), dim3(kSelThreads), 0, st, (const float*)A, (const float*)C, Kp, pa, pb,
+               px, n, keys, work);
   note_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
