@@ -772,7 +772,7 @@ cudaError_t launch_cholesky(const double* G, int K, double lambda, double* L, do
     note_launch();
   }
   const unsigned tb = (unsigned)((K + BCH_NB - 1) / BCH_NB);
-  pdl_launch(k_bchol_colcopy, dim3(dim3(tb, tb)), dim3(256), 0, st, L, Lc, K, dstatus);
+  pdl_launch(k_bchol_colcopy, dim3(tb, tb), dim3(256), 0, st, L, Lc, K, dstatus);
   note_launch();
   return cudaGetLastError();
 }
