@@ -541,11 +541,14 @@ __global__ void __launch_bounds__(kSelThreads)
   sel_first_finish(work, h0, c, se, sx, s2);
 }
 
-// Sixteen lanes per probe: a half warp reads the two merged rows of one probe with 16-byte
-// loads (a 64-entry FP32 row is one load per lane), four probes' loads in flight at a time,
-// and a shuffle tree inside the half warp sums the lane partials.  The warp takes its 32
-// probes m0 + j in two columns (half h owns probes 16 h + s, s = 0..15), so that lane j ends
-// up holding the reconstruction of its own probe.  Needs Kp a multiple of 16 / sizeof(T).
+// Eight lanes per probe: four probes per step of a warp, each probe's two merged rows read by
+// its eight lanes with 16-byte loads (one 128-byte line per probe and load instruction, so the
+// loads stay coalesced), a three-level shuffle tree per probe, and one shuffle that hands the
+// sum to the lane owning the probe (the warp takes its 32 probes m0 + j in eight steps; lane j
+// ends up holding the reconstruction of probe j).  A sixteen-lane form with four probes in
+// flight per lane executed 28 warp instructions per probe (measured), most of them index
+// shuffles and shuffle trees; this one about a third of that.  Needs Kp a multiple of
+// 16 / sizeof(T).
 template <typename T>
 __global__ void __launch_bounds__(kSelThreads)
     k_sel_probe16(const T* __restrict__ A, const T* __restrict__ C, int Kp, const int32_t* __restrict__ pa,
@@ -558,7 +561,7 @@ __global__ void __launch_bounds__(kSelThreads)
   __shared__ unsigned int h0[256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) h0[i] = 0;
   __syncthreads();
-  const int lane = threadIdx.x & 31, sub = lane & 15, half = lane & 16;
+  const int lane = threadIdx.x & 31, g = lane >> 3, sub = lane & 7;
   const int nv = Kp / VW;
   double c = 0, se = 0, sx = 0, s2 = 0;
   uint32_t cf = 0;
@@ -573,48 +576,33 @@ __global__ void __launch_bounds__(kSelThreads)
     const float xf = obs ? px[m] : 0.f;
     T mine = T(0);
 #pragma unroll
-    for (int s0 = 0; s0 < 16; s0 += 4) {
-      int32_t as[4], bs[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        as[q] = __shfl_sync(0xffffffffu, a, half + s0 + q);
-        bs[q] = __shfl_sync(0xffffffffu, bi, half + s0 + q);
-      }
-      T acc[4] = {T(0), T(0), T(0), T(0)};
-      for (int v = sub; v < nv; v += 16) {
-        V xa[4], xc[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (as[q] >= 0) {
-            xa[q] = reinterpret_cast<const V*>(A + (int64_t)as[q] * Kp)[v];
-            xc[q] = reinterpret_cast<const V*>(C + (int64_t)bs[q] * Kp)[v];
-          } else {
-            xa[q] = V{};
-            xc[q] = V{};
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
+    for (int st = 0; st < 8; ++st) {
+      // probe st * 4 + g of the warp's 32
+      const int32_t ap = __shfl_sync(0xffffffffu, a, st * 4 + g);
+      const int32_t bp = __shfl_sync(0xffffffffu, bi, st * 4 + g);
+      T acc = T(0);
+      if (ap >= 0) {
+        const V* ra = reinterpret_cast<const V*>(A + (int64_t)ap * Kp);
+        const V* rc = reinterpret_cast<const V*>(C + (int64_t)bp * Kp);
+        for (int v = sub; v < nv; v += 8) {
+          const V xa = ra[v], xc = rc[v];
           if constexpr (VW == 4) {
-            acc[q] = fma(xa[q].x, xc[q].x, acc[q]);
-            acc[q] = fma(xa[q].y, xc[q].y, acc[q]);
-            acc[q] = fma(xa[q].z, xc[q].z, acc[q]);
-            acc[q] = fma(xa[q].w, xc[q].w, acc[q]);
+            acc = fma(xa.x, xc.x, acc);
+            acc = fma(xa.y, xc.y, acc);
+            acc = fma(xa.z, xc.z, acc);
+            acc = fma(xa.w, xc.w, acc);
           } else {
-            acc[q] = fma(xa[q].x, xc[q].x, acc[q]);
-            acc[q] = fma(xa[q].y, xc[q].y, acc[q]);
+            acc = fma(xa.x, xc.x, acc);
+            acc = fma(xa.y, xc.y, acc);
           }
         }
       }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        T t = acc[q];
-        t += __shfl_xor_sync(0xffffffffu, t, 8);
-        t += __shfl_xor_sync(0xffffffffu, t, 4);
-        t += __shfl_xor_sync(0xffffffffu, t, 2);
-        t += __shfl_xor_sync(0xffffffffu, t, 1);
-        if (sub == s0 + q) mine = t;
-      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      // lane j's probe is computed at step j / 4 by the eight lanes of group j % 4
+      const T t = __shfl_sync(0xffffffffu, acc, (lane & 3) * 8);
+      if (st == (lane >> 2)) mine = t;
     }
     if constexpr (VW == 4) {
       float e = 0.f, x2 = 0.f;
