@@ -1105,6 +1105,7 @@ bool prefactor(trd_handle* h, int k, double lambda) {
   }
   cudaStream_t main_stream = h->stream;
   h->stream = x->side;       // the phase scopes below trace the side stream
+  pdl_on = false;            // plain launches on the side stream (restored below)
   trd_status st;
   {
     PScope ps(h, P_GRAM);
@@ -1154,6 +1155,7 @@ bool prefactor(trd_handle* h, int k, double lambda) {
     x->side_tail = true;
   }
   h->stream = main_stream;
+  pdl_on = true;
   if (!ok) {
     // join whatever was forked, then let run_update compute everything on the main stream
     cudaGetLastError();
