@@ -38,7 +38,8 @@ extern "C" {
 #endif
 
 #define TRD_MAX_ORDER 8   /* tensor order N is 3..TRD_MAX_ORDER */
-#define TRD_MAX_RANK 32   /* every r_k is 1..TRD_MAX_RANK */
+#define TRD_MAX_RANK 128  /* every r_k is 1..TRD_MAX_RANK */
+#define TRD_MAX_CORE_K 8192  /* every core's r_k r_{k+1} is at most TRD_MAX_CORE_K */
 
 typedef enum {
   TRD_OK = 0,
@@ -113,7 +114,9 @@ typedef struct {
 /* ---------------------------------------------------------------- handle */
 
 /* Create a handle for an order-N tensor (3 <= N <= TRD_MAX_ORDER) with mode sizes I[0..N-1]
- * (each >= 1, product < 2^40) and ring ranks R[0..N-1] (Def. 1, 1 <= r_k <= TRD_MAX_RANK).
+ * (each >= 1, product < 2^40) and ring ranks R[0..N-1] (Def. 1, 1 <= r_k <= TRD_MAX_RANK,
+ * r_k r_{k+1} <= TRD_MAX_CORE_K).  The data passes further need a cut of the ring whose width
+ * r_1 r_c is at most 256 (112 for TRD_FP64); a call that finds none returns TRD_ENOTIMPL.
  * `precision` is a trd_precision.  `cuda_stream` is a cudaStream_t on which every call is
  * ordered; it must outlive the handle.  NULL (the legacy default stream) gives the handle
  * its own blocking stream, which keeps the legacy stream's implicit ordering with the

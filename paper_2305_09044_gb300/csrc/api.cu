@@ -318,15 +318,22 @@ size_t elt(const trd_handle* h) { return is_fp64(h) ? sizeof(double) : sizeof(fl
 // Balanced split of the view's modes into [0, c) and [c, N).
 Split choose_split(const trd_handle* h, const View& v, int k) {
   Split sp;
-  double best = 1e300;
-  int bestc = 1;
+  // the most balanced cut among those whose contraction width r_1 r_{c+1} the data passes take
+  // (FP64 112, the other precisions 256); when none does, the most balanced cut (the pass then
+  // reports it).  A ring with two large neighbouring ranks (the paper's video rank [80, 80, 3,
+  // 20]) is cut through its small edges instead of through the balanced but 6400-wide one.
+  const int kmax = h->prec == TRD_FP64 ? 112 : 256;
+  double best = 1e300, best_fit = 1e300;
+  int bestc = 1, fitc = -1;
   for (int c = 1; c < h->N; ++c) {
     double a = 0, b = 0;
     for (int m = 0; m < c; ++m) a += log((double)v.dim[m]);
     for (int m = c; m < h->N; ++m) b += log((double)v.dim[m]);
     const double cost = fabs(a - b);
     if (cost < best - 1e-12) { best = cost; bestc = c; }
+    if (h->R[0] * h->R[c] <= kmax && cost < best_fit - 1e-12) { best_fit = cost; fitc = c; }
   }
+  if (fitc > 0) bestc = fitc;
   sp.c = bestc;
   sp.P_in = 1;
   sp.P_out = 1;
@@ -1618,6 +1625,8 @@ trd_status trd_create(trd_t** out, int N, const int64_t* I, const int32_t* R, in
     if (R[m] < 1 || R[m] > kMaxR) return TRD_EINVAL;
     logtot += log2((double)I[m]);
   }
+  for (int m = 0; m < N; ++m)
+    if (R[m] * R[(m + 1) % N] > TRD_MAX_CORE_K) return TRD_EINVAL;
   if (logtot >= 40.0) return TRD_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {

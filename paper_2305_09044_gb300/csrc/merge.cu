@@ -128,12 +128,17 @@ cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool trans
     cap = max(cap, ch.rows[0] * ch.cols[j]);
     cap = max(cap, ch.rows[j] * ch.cols[j]);
   }
-  // a few multi-indices per warp, so that the per-warp set-up is shared
-  const int warps = 4;
+  // a few multi-indices per warp, so that the per-warp set-up is shared; fewer warps per block
+  // when the slice products are large (three buffers of cap entries per warp: rank-80 slices
+  // need 77 KB per warp in FP32)
+  const size_t tab = sizeof(int) * (size_t)2 * cap;
+  const size_t esz_max = out_double ? sizeof(double) : sizeof(float);
+  const size_t per_warp = (size_t)3 * cap * esz_max;
+  const int warps = (int)imax(1, imin(4, (int64_t)((kSmemOptIn - tab) / per_warp)));
+  if ((size_t)warps * per_warp + tab > kSmemOptIn) return cudaErrorInvalidValue;
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t blocks = imax(1, imin((ch.count + warps - 1) / warps, (int64_t)sms * 8));
-  const size_t tab = sizeof(int) * (size_t)2 * cap;
   auto go = [&](auto kern, size_t esz, auto* o) {
     const size_t smem = (size_t)warps * 3 * cap * esz + tab;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -366,6 +371,158 @@ __global__ void k_backcontract(const double* __restrict__ Tm, SlotSrc sl, int Kp
   if (threadIdx.x == 0) ctr[ik] = 0u;
 }
 
+// The same back-contraction for K = r_k r_{k+1} > 1024 (two large neighbouring ranks, such as
+// the paper's video rank [80, 80, 3, 20]: K = 6400 and 1600): one block of 256 threads per
+// (row, split); the K outputs are spread over the block's threads (entry e = t + 256 u, u <
+// UW), and the block takes its pairs one after another, staging M(s), Pre and Post in shared
+// memory, forming V = M Pre together and then every thread adding its entries of Post V.  The
+// index maps (tabulated once per block) and the fixed-order split sum are those of
+// k_backcontract.
+template <typename T, int UW>
+__global__ void __launch_bounds__(256, UW > 8 ? 1 : 4) k_backcontract_wide(
+    const double* __restrict__ Tm, SlotSrc sl, int Kp, int rows_case, int mr, int mc, const T* __restrict__ pre,
+    int64_t n_pre, const T* __restrict__ post, int64_t n_post, BcCore preC, BcCore postC, int64_t Ik, int rk,
+    int rk1, int64_t pairs_per_split, double* __restrict__ part_out, double* __restrict__ d,
+    unsigned* __restrict__ ctr) {
+  extern __shared__ __align__(16) unsigned char smem_bw[];
+  __shared__ int s_last;
+  pdl_wait();
+  pdl_trigger();
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int szM = mr * mc, szPre = mc * rk, szPost = rk1 * mr, szV = mr * rk;
+  const int K = rk * rk1;
+  T* sM = reinterpret_cast<T*>(smem_bw);
+  T* sPre = sM + szM;
+  T* sPost = sPre + szPre;
+  T* sV = sPost + szPost;
+  int* tM = reinterpret_cast<int*>(sV + szV);
+  int* tPre = tM + szM;
+  int* tPost = tPre + szPre;
+  int* tV = tPost + szPost;
+  int* tU = tV + szV;
+  for (int e = t; e < szM; e += nt) {
+    const int i = e / mc, j = e % mc;
+    tM[e] = rows_case ? j * mr + i : i * mc + j;
+  }
+  for (int e = t; e < szPre; e += nt) tPre[e] = (e % rk) * mc + e / rk;
+  for (int e = t; e < szPost; e += nt) tPost[e] = (e % mr) * rk1 + e / mr;
+  for (int e = t; e < szV; e += nt) tV[e] = (e / rk) * mc | (e % rk) << 16;
+  for (int e = t; e < K; e += nt) tU[e] = (e / rk) * mr | (e % rk) << 16;
+  const int64_t U = sl.RB * sl.NT, G = sl.G;
+  auto cta_range = [&](int64_t rb, int& c0o, int& nco) {
+    const int64_t ulo = rb * sl.NT, uhi = ulo + sl.NT;
+    int64_t c0 = (ulo * G) / U;
+    while (c0 > 0 && c0 * U >= (ulo + 1) * G) --c0;
+    while ((c0 + 1) * U < (ulo + 1) * G) ++c0;
+    int64_t c1 = c0 + 1;
+    while (c1 < G && c1 * U < uhi * G) ++c1;
+    c0o = (int)c0;
+    nco = (int)(c1 - c0);
+  };
+  const int64_t ik = blockIdx.x;
+  const int64_t npairs = n_pre * n_post;
+  const int64_t q0 = (int64_t)blockIdx.y * pairs_per_split;
+  const int64_t q1 = min(npairs, q0 + pairs_per_split);
+  const bool has_pre = pre || preC.core, has_post = post || postC.core;
+  const int64_t cs = sl.bm * Kp;
+  T acc[UW];
+#pragma unroll
+  for (int u = 0; u < UW; ++u) acc[u] = T(0);
+  __syncthreads();
+  for (int64_t q = q0; q < q1; ++q) {
+    int64_t ip;
+    const int64_t iq = qdivmod(q, n_pre, ip);
+    const int64_t s = ip + n_pre * (ik + Ik * iq);
+    if (sl.part) {
+      int64_t r;
+      const int64_t rb = qdivmod(s, sl.bm, r);
+      int c0, nc;
+      cta_range(rb, c0, nc);
+      const float* src = sl.part + ((c0 + rb) * sl.bm + r) * Kp;
+      for (int e = t; e < szM; e += nt) {
+        const float* a = src + tM[e];
+        float v = a[0];
+        for (int tt = 1; tt < nc; ++tt) v += a[tt * cs];
+        sM[e] = (T)v;
+      }
+    } else {
+      const double* Ts = Tm + s * (int64_t)Kp;
+      for (int e = t; e < szM; e += nt) sM[e] = (T)Ts[tM[e]];
+    }
+    if (pre) {
+      for (int e = t; e < szPre; e += nt) sPre[e] = pre[ip * (int64_t)szPre + e];
+    } else if (preC.core) {
+      const int64_t off = (preC.idx ? (int64_t)preC.idx[ip] : ip) * (int64_t)szPre;
+      if (sizeof(T) == 4 && preC.coref) {
+        for (int e = t; e < szPre; e += nt) sPre[e] = (T)preC.coref[off + tPre[e]];
+      } else {
+        for (int e = t; e < szPre; e += nt) sPre[e] = (T)preC.core[off + tPre[e]];
+      }
+    }
+    if (post) {
+      for (int e = t; e < szPost; e += nt) sPost[e] = post[iq * (int64_t)szPost + e];
+    } else if (postC.core) {
+      const int64_t off = (postC.idx ? (int64_t)postC.idx[iq] : iq) * (int64_t)szPost;
+      if (sizeof(T) == 4 && postC.coref) {
+        for (int e = t; e < szPost; e += nt) sPost[e] = (T)postC.coref[off + tPost[e]];
+      } else {
+        for (int e = t; e < szPost; e += nt) sPost[e] = (T)postC.core[off + tPost[e]];
+      }
+    }
+    __syncthreads();
+    // V = M * Pre  (mr x rk)
+    for (int e = t; e < szV; e += nt) {
+      const int tv = tV[e], imc = tv & 0xffff, a = tv >> 16;
+      T v;
+      if (has_pre) {
+        v = T(0);
+        for (int j = 0; j < mc; ++j) v = fma(sM[imc + j], sPre[j * rk + a], v);
+      } else {
+        v = sM[imc + a];
+      }
+      sV[e] = v;
+    }
+    __syncthreads();
+    // U = Post * V  (rk1 x rk); thread t owns entries e = t + 256 u (e = beta * rk + alpha)
+#pragma unroll
+    for (int u = 0; u < UW; ++u) {
+      const int e = t + 256 * u;
+      if (e < K) {
+        const int tu = tU[e], bmr = tu & 0xffff, a = tu >> 16;
+        T v;
+        if (has_post) {
+          v = T(0);
+          for (int i = 0; i < mr; ++i) v = fma(sPost[bmr + i], sV[i * rk + a], v);
+        } else {
+          v = sV[e];
+        }
+        acc[u] += v;
+      }
+    }
+    __syncthreads();
+  }
+  const bool split = gridDim.y > 1;
+  double* o = split ? part_out + ((int64_t)blockIdx.y * Ik + ik) * K : d + ik * K;
+#pragma unroll
+  for (int u = 0; u < UW; ++u) {
+    const int e = t + 256 * u;
+    if (e < K) o[e] = (double)acc[u];
+  }
+  if (!split) return;
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(ctr + ik, 1u) == gridDim.y - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int e = t; e < K; e += nt) {
+    double sum = 0.0;
+    for (unsigned y = 0; y < gridDim.y; ++y) sum += __ldcg(part_out + ((int64_t)y * Ik + ik) * K + e);
+    d[ik * K + e] = sum;
+  }
+  if (t == 0) ctr[ik] = 0u;
+}
+
 cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int mr, int mc,
                                 const void* pre, int64_t n_pre, const void* post,
                                 int64_t n_post, int64_t Ik, int rk, int rk1, double* dpart,
@@ -385,7 +542,27 @@ cudaError_t launch_backcontract(const void* Tsum_d, int Kp, bool rows_case, int 
   const int per_warp = mr * mc + mc * rk + rk1 * mr + mr * rk;
   const size_t esz = fp64 ? sizeof(double) : sizeof(float);
   const int K = rk * rk1;
-  if (K > 1024) return cudaErrorInvalidValue;
+  if (K > 1024) {
+    // wide form: the K outputs over a block's threads, the staged matrices in shared memory
+    if (K > 256 * 32) return cudaErrorInvalidValue;
+    const size_t esz_w = fp64 ? sizeof(double) : sizeof(float);
+    const int szs = mr * mc + mc * rk + rk1 * mr + mr * rk;
+    const size_t smem_w = (size_t)szs * esz_w + sizeof(int) * (size_t)(szs + K) + 16;
+    // the packed index maps hold row offsets below 2^16 (M and Post) and columns below 2^15
+    if (smem_w > kSmemOptIn || mr * mc > 65535 || rk1 * mr > 65535 || rk > 32767) return cudaErrorInvalidValue;
+    auto gow = [&](auto kern, auto tag) -> cudaError_t {
+      using E = decltype(tag);
+      if (smem_w > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w);
+      return pdl_launch(kern, grid, dim3(256), smem_w, st, (const double*)Tsum_d, sl, Kp, rows_case ? 1 : 0, mr, mc,
+                        (const E*)pre, n_pre, (const E*)post, n_post, preC, postC, Ik, rk, rk1, per, dpart, d, ctr);
+    };
+    cudaError_t e;
+    if (fp64) e = K <= 256 * 8 ? gow(k_backcontract_wide<double, 8>, 0.0) : gow(k_backcontract_wide<double, 32>, 0.0);
+    else e = K <= 256 * 8 ? gow(k_backcontract_wide<float, 8>, 0.0f) : gow(k_backcontract_wide<float, 32>, 0.0f);
+    note_launch();
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
   const size_t work = std::max((size_t)(threads / 32) * per_warp * esz,
                                (size_t)(threads / 32) * std::min(K, 1024) * sizeof(double));
   const int tab_rb = (sl.part && sl.RB <= 4096) ? (int)sl.RB : 0;

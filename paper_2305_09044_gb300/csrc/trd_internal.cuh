@@ -11,6 +11,8 @@
 #include "../../include/trd.h"
 
 namespace trd {
+// opt-in dynamic shared memory per block on this GPU (227 KB)
+constexpr size_t kSmemOptIn = 232448;
 
 // Programmatic dependent launch along the main stream's chain of small kernels: a kernel so
 // launched may become resident while its predecessor in the stream finishes (its launch and

@@ -22,6 +22,10 @@ the orders 3-5, TR ranks 3-20, 20-80 % missing and 10-20 % outliers of its exper
           entry from the two-component mixture 0.8 N(0, 1e-3) + 0.2 N(0, 0.5) on the [0, 1]
           scale (here scaled by the clean tensor's range), PSNR against the clean tensor
   imagec  the same image tensor and noise with 70 % of the entries missing (completion)
+  videop  1920 x 1080 x 3 x 50 (a 50-frame colour video) at the paper's video TR rank
+          (80, 80, 3, 20), 70 % missing, the image workloads' mixture noise on every entry,
+          RStS sketch 200 per non-updated mode (J = 200 x 3 x 50 = 3e4 sampled fibres when a
+          frame mode is updated)
 """
 from __future__ import annotations
 
@@ -68,6 +72,8 @@ WORKLOADS = {
                       data_seed=1006, init_seed=2006, sample_seed=3006),
     "imagec": Workload("imagec", (3, 1352, 2000), (3, 20, 20), 0.7, 0.2, outlier_kind="gmm",
                        data_seed=1006, init_seed=2006, sample_seed=3006),
+    "videop": Workload("videop", (1920, 1080, 3, 50), (80, 80, 3, 20), 0.7, 0.2, outlier_kind="gmm",
+                       sketch=200, data_seed=1007, init_seed=2007, sample_seed=3007),
 }
 
 # variances of the two mixture components of the 'gmm' noise, on data rescaled to [0, 1]

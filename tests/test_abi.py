@@ -50,8 +50,10 @@ def test_create_rejects_bad_shapes(lib):
     R = (C.c_int32 * 2)(2, 2)
     assert lib.trd_create(C.byref(h), 2, I, R, 1, None) == 1      # N < 3
     I3 = (C.c_int64 * 3)(4, 4, 4)
-    R3 = (C.c_int32 * 3)(2, 99, 2)
+    R3 = (C.c_int32 * 3)(2, 129, 2)
     assert lib.trd_create(C.byref(h), 3, I3, R3, 1, None) == 1    # rank too large
+    R3 = (C.c_int32 * 3)(2, 100, 100)
+    assert lib.trd_create(C.byref(h), 3, I3, R3, 1, None) == 1    # r_k r_{k+1} too large
     assert lib.trd_create(C.byref(h), 3, I3, (C.c_int32 * 3)(2, 2, 2), 9, None) == 1  # precision
 
 

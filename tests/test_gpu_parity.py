@@ -243,14 +243,22 @@ def test_trajectory_sketched_fp32(torch_cuda):
                                              ("fp32", (10, 9, 8, 7), (8, 16, 8, 16)),
                                              ("fp32", (9, 8, 7, 6, 5), (11, 11, 11, 11, 11)),
                                              ("fp64", (8, 20, 120), (3, 20, 20)),
-                                             ("fp64", (5, 24, 22, 6), (4, 12, 17, 4))])
+                                             ("fp64", (5, 24, 22, 6), (4, 12, 17, 4)),
+                                             ("fp64", (40, 36, 3, 8), (20, 20, 3, 4)),
+                                             ("fp64", (6, 30, 5, 24), (36, 36, 3, 3)),
+                                             ("fp64", (4, 48, 6, 30), (46, 46, 2, 2))])
 def test_scaled_step_large_gram(torch_cuda, prec, dims, ranks):
     """K = r_k r_{k+1} of 100, 128 and 121: the FP64 LDL^T factorisation and the
     row-parallel solves of the scaled step (Eq. sg, Eq. hI) at the Gram sizes of the 64^5 rank-10
     workload and beyond, against the oracle's Cholesky, from identical state.  K = 400 (the
     image ranks (3, 20, 20)) and 204 take the blocked multi-CTA Cholesky, both with a ragged
     last panel, and the FGMC factor of their r_k r_{k+1} > 128 cores comes from the tiled
-    slice-Gram kernel (compared here through G^{!=k}, 1e-12)."""
+    slice-Gram kernel (compared here through G^{!=k}, 1e-12).  Ranks (20, 20, 3, 4): the most
+    balanced cut of the ring (through the two rank-20 edges, r_1 r_c = 400) is wider than the
+    FP64 data pass takes, so the pass cuts through the rank-3 edge (r_1 r_c = 60).  K = 1296
+    and 2116 (two large neighbouring ranks, as in the paper's video rank [80, 80, 3, 20]) take
+    the wide back-contraction (8 and 32 outputs per thread) and the row solves with the factor
+    read from L2."""
     t, X, P, Xt, keep = _make(torch_cuda, dims, ranks, prec)
     cores = O.init_cores(dims, ranks, seed=13)
     sigma = 2.0
@@ -265,6 +273,35 @@ def test_scaled_step_large_gram(torch_cuda, prec, dims, ranks):
         assert abs(eta - st.eta) <= TOL[prec] * abs(st.eta), (k, eta, st.eta)
         assert rel(t.get_core(k) - cores[k], st.cores[k] - cores[k]) <= TOL[prec]
         cores = st.cores
+
+
+def test_video_rank_fp32(torch_cuda):
+    """The paper's video rank [80, 80, 3, 20] on a small video-shaped tensor in FP32, against
+    the oracle from identical state: the data pass cuts the ring through the rank-3 edge
+    (r_1 r_c = 240), d (Eq. sd) of the K = 6400 and 1600 cores comes from the wide
+    back-contraction, the FGMC Gram (Eq. FGMC) at K = 6400 and 1600 equals the explicit B^T B,
+    and the updates (blocked Cholesky and row solves at K = 6400) give the oracle's step size.
+    G is singular for the K = 6400 and 1600 cores here (1440 and 576 rows), so the test
+    regularises with lambda = 1e-6 tr(G) / K and compares the step size of the better-posed
+    K = 240 and 60 cores only."""
+    dims, ranks = (8, 24, 3, 20), (80, 80, 3, 20)
+    t, X, P, Xt, keep = _make(torch_cuda, dims, ranks, "fp32")
+    cores = O.init_cores(dims, ranks, seed=11)
+    sigma = 1.3
+    for k in range(len(dims)):
+        t.set_cores(cores)
+        st = O.core_update(X, P, cores, k, sigma, gram="none")
+        t.residual_weights(k, sigma)
+        d = t.core_gradient(k)
+        assert rel(d, st.d) <= TOL["fp32"], (k, rel(d, st.d))
+        if k in (0, 3):
+            assert rel(t.fgmc_gram(k), O.explicit_gram(cores, k)) <= 1e-12, k
+        eta = t.core_update(k, -1e-6)
+        assert math.isfinite(eta) and eta > 0, (k, eta)
+        if k in (1, 2):
+            ref = O.core_update(X, P, cores, k, sigma, lam=-1e-6)
+            assert abs(eta - ref.eta) <= 1e-4 * abs(ref.eta), (k, eta, ref.eta)
+        cores = t.get_cores()
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16"])
