@@ -778,31 +778,32 @@ cudaError_t launch_cholesky(const double* G, int K, double lambda, double* L, do
 }
 
 // ------------------------------------------------------------------ h = d (G + lambda I)^{-1}
-// b[m] -= v[m] y for m in [m_lo, m_hi), lane-strided, with the factor's entries v[] (from L2 or
-// HBM: the factor does not fit in shared memory) loaded SOLVE_U per lane at a time and the next
-// group's loads issued before the current group's FMAs, so that about 2 SOLVE_U loads per lane
-// are in flight while the FP64 pipe works (one load in flight at a time left each step bound by
-// the load latency: 0.16 TFLOP/s at K = 6400).  Per entry the arithmetic is b - v y, as before.
+// b[m] -= v[m] y for m in [m_lo, m_hi), strided over the block's threads, with the factor's
+// entries v[] (from L2 or HBM: the factor does not fit in shared memory) loaded SOLVE_U per
+// thread at a time and the next group's loads issued before the current group's FMAs (one
+// load in flight at a time left each step bound by the load latency: 0.16 TFLOP/s at
+// K = 6400).  Per entry the arithmetic is b - v y, as before.
 constexpr int SOLVE_U = 16;
+constexpr int SOLVE_NT = 128;
 __device__ __forceinline__ void axpy_strided(double* __restrict__ b, const double* __restrict__ v, double y,
-                                             int m_lo, int m_hi, int lane) {
-  int m0 = m_lo + lane;
+                                             int m_lo, int m_hi, int tid) {
+  int m0 = m_lo + tid;
   double c[SOLVE_U];
 #pragma unroll
   for (int u = 0; u < SOLVE_U; ++u) {
-    const int m = m0 + 32 * u;
+    const int m = m0 + SOLVE_NT * u;
     c[u] = m < m_hi ? v[m] : 0.0;
   }
-  for (; m0 < m_hi; m0 += 32 * SOLVE_U) {
+  for (; m0 < m_hi; m0 += SOLVE_NT * SOLVE_U) {
     double n[SOLVE_U];
 #pragma unroll
     for (int u = 0; u < SOLVE_U; ++u) {
-      const int m = m0 + 32 * (SOLVE_U + u);
+      const int m = m0 + SOLVE_NT * (SOLVE_U + u);
       n[u] = m < m_hi ? v[m] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < SOLVE_U; ++u) {
-      const int m = m0 + 32 * u;
+      const int m = m0 + SOLVE_NT * u;
       if (m < m_hi) b[m] -= c[u] * y;
     }
 #pragma unroll
@@ -810,35 +811,36 @@ __device__ __forceinline__ void axpy_strided(double* __restrict__ b, const doubl
   }
 }
 
-// One warp per row of d: forward substitution with L (column j of L read from the column-major
-// copy), then back substitution with L^T (row j of L), both with unit stride across the lanes.
-// The factor comes from L2 (K > 512: too large for shared memory).
-__global__ void k_solve_rows(const double* __restrict__ L, const double* __restrict__ d,
-                             double* __restrict__ h, int K, int64_t rows) {
-  extern __shared__ double sb[];
-  const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// One block of SOLVE_NT threads per row of d (the row in shared memory, K doubles: at
+// K = 6400 four rows fit an SM, so four warps per row keep four warps on each scheduler to
+// hide the factor's load latency): forward substitution with L (column j of L read from the
+// column-major copy), then back substitution with L^T (row j of L), both with unit stride
+// across the threads and a block barrier per step.  For K > 512.
+__global__ void __launch_bounds__(SOLVE_NT) k_solve_rows(const double* __restrict__ L, const double* __restrict__ d,
+                                                         double* __restrict__ h, int K, int64_t rows) {
+  extern __shared__ double b[];
+  const int tid = threadIdx.x;
   const double* rdiag = L + (int64_t)K * K;
   const double* Lc = rdiag + K;
-  double* b = sb + (size_t)w * K;
-  for (int64_t row = (int64_t)blockIdx.x * warps + w; row < rows; row += (int64_t)gridDim.x * warps) {
-    for (int m = lane; m < K; m += 32) b[m] = d[row * K + m];
-    __syncwarp();
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    for (int m = tid; m < K; m += SOLVE_NT) b[m] = d[row * K + m];
+    __syncthreads();
     for (int j = 0; j < K; ++j) {
       const double yj = b[j] * rdiag[j];
-      __syncwarp();
-      if (lane == 0) b[j] = yj;
-      axpy_strided(b, Lc + (int64_t)j * K, yj, j + 1, K, lane);
-      __syncwarp();
+      __syncthreads();
+      if (tid == 0) b[j] = yj;
+      axpy_strided(b, Lc + (int64_t)j * K, yj, j + 1, K, tid);
+      __syncthreads();
     }
     for (int j = K - 1; j >= 0; --j) {
       const double hj = b[j] * rdiag[j];
-      __syncwarp();
-      if (lane == 0) b[j] = hj;
-      axpy_strided(b, L + (int64_t)j * K, hj, 0, j, lane);
-      __syncwarp();
+      __syncthreads();
+      if (tid == 0) b[j] = hj;
+      axpy_strided(b, L + (int64_t)j * K, hj, 0, j, tid);
+      __syncthreads();
     }
-    for (int m = lane; m < K; m += 32) h[row * K + m] = b[m];
-    __syncwarp();
+    for (int m = tid; m < K; m += SOLVE_NT) h[row * K + m] = b[m];
+    __syncthreads();
   }
 }
 
@@ -935,9 +937,7 @@ __global__ void __launch_bounds__(32) k_solve_rows_reg(const double* __restrict_
 
 cudaError_t launch_solve_rows(const double* L, const double* d, double* h, int K, int64_t rows,
                               cudaStream_t st) {
-  const int warps = 1;
-  const size_t smem = (size_t)warps * K * sizeof(double);
-  const unsigned blocks = (unsigned)imin((rows + warps - 1) / warps, 8192);
+  const unsigned blocks = (unsigned)imin(rows, 8192);     // one warp (registers) or block per row
   if (K <= 256) {
     k_solve_rows_reg<8><<<blocks, 32, 0, st>>>(L, d, h, K, rows);
   } else if (K <= 416) {
@@ -945,9 +945,11 @@ cudaError_t launch_solve_rows(const double* L, const double* d, double* h, int K
   } else if (K <= 512) {
     k_solve_rows_reg<16><<<blocks, 32, 0, st>>>(L, d, h, K, rows);
   } else {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_solve_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_solve_rows<<<blocks, warps * 32, smem, st>>>(L, d, h, K, rows);
+    const size_t smem_row = (size_t)K * sizeof(double);
+    if (smem_row > kSmemOptIn) return cudaErrorInvalidValue;
+    if (smem_row > 48 * 1024)
+      cudaFuncSetAttribute(k_solve_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+    k_solve_rows<<<blocks, SOLVE_NT, smem_row, st>>>(L, d, h, K, rows);
   }
   note_launch();
   return cudaGetLastError();
