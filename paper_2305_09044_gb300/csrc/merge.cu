@@ -30,9 +30,12 @@ __device__ __forceinline__ void chain_slice(const Chain& ch, int j, int64_t sl, 
 
 // NC: the chain length as a compile-time constant (1..4; 0 = read from ch.n), so that the
 // digit arithmetic stays in registers and the per-core parameters are static operands.
+// Per warp: buffer A (capA entries: the first slice, then every other product), buffer B (capP:
+// the products of the later slices) and the slice buffer Zs (capZ: the later slices), where
+// capP = max_{j>=1} R0 C_j, capZ = max_{j>=1} R_j C_j and capA = max(R0 C_0, capP).
 template <typename Tc, typename Tout, int NC>
-__global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_t ld, int cap,
-                        __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int kpad) {
+__global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_t ld, int capA, int capP,
+                        int capZ, __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int kpad) {
   constexpr int JMAX = NC > 0 ? NC : kMaxN;
   const int n = NC > 0 ? NC : ch.n;
   extern __shared__ __align__(16) unsigned char smem_chain[];
@@ -40,17 +43,18 @@ __global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_
   pdl_trigger();
   const int warps = blockDim.x >> 5;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Tc* Mb = reinterpret_cast<Tc*>(smem_chain) + (size_t)w * 3 * cap;
-  Tc* Mn = Mb + cap;
-  Tc* Zs = Mn + cap;
+  const int per_warp = capA + capP + capZ;
+  Tc* const bufA = reinterpret_cast<Tc*>(smem_chain) + (size_t)w * per_warp;
+  Tc* const bufB = bufA + capA;
+  Tc* Zs = bufB + capP;
   // maps shared by every p: output position pos <- column-major entry of the product, and
   // column-major entry e -> (row e mod R0, column e / R0) packed as a | b << 16
-  int* tOut = reinterpret_cast<int*>(reinterpret_cast<Tc*>(smem_chain) + (size_t)warps * 3 * cap);
-  int* tAB = tOut + cap;
   const int R0 = ch.rows[0], CN = ch.cols[n - 1];
+  int* tOut = reinterpret_cast<int*>(reinterpret_cast<Tc*>(smem_chain) + (size_t)warps * per_warp);
+  int* tAB = tOut + R0 * CN;
   for (int pos = threadIdx.x; pos < R0 * CN; pos += blockDim.x)
     tOut[pos] = transposed ? pos : (pos % CN) * R0 + pos / CN;
-  for (int e = threadIdx.x; e < cap; e += blockDim.x) tAB[e] = (e % R0) | (e / R0) << 16;
+  for (int e = threadIdx.x; e < capP; e += blockDim.x) tAB[e] = (e % R0) | (e / R0) << 16;
   __syncthreads();
   // digits of this warp's first p and of the stride between its p's (mixed radix, digit 0
   // fastest), advanced by digit-wise addition with carries
@@ -66,6 +70,8 @@ __global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_
     }
   }
   for (int64_t p = (int64_t)blockIdx.x * warps + w; p < ch.count; p += stride) {
+    Tc* Mb = bufA;
+    Tc* Mn = bufB;
     int C = ch.cols[0];
     // M(a, c) at Mb[c R0 + a]; slice j element (c, b) at Zs[b R_j + c] (the core layout)
     chain_slice(ch, 0, ch.idx[0] ? (int64_t)ch.idx[0][dig[0]] : dig[0], R0 * C, Mb, lane);
@@ -123,27 +129,28 @@ __global__ void k_chain(Chain ch, Tout* __restrict__ out, int transposed, int64_
 cudaError_t launch_chain(const Chain& ch, void* out, bool out_double, bool transposed,
                          int64_t ld, cudaStream_t st, __nv_bfloat16* hi, __nv_bfloat16* lo, int kpad) {
   if (ch.n <= 0 || ch.count <= 0) return cudaSuccess;
-  int cap = 1;
-  for (int j = 0; j < ch.n; ++j) {
-    cap = max(cap, ch.rows[0] * ch.cols[j]);
-    cap = max(cap, ch.rows[j] * ch.cols[j]);
+  int capP = 1, capZ = 1;
+  for (int j = 1; j < ch.n; ++j) {
+    capP = max(capP, ch.rows[0] * ch.cols[j]);
+    capZ = max(capZ, ch.rows[j] * ch.cols[j]);
   }
+  const int capA = max(capP, ch.rows[0] * ch.cols[0]);
   // a few multi-indices per warp, so that the per-warp set-up is shared; fewer warps per block
-  // when the slice products are large (three buffers of cap entries per warp: rank-80 slices
-  // need 77 KB per warp in FP32)
-  const size_t tab = sizeof(int) * (size_t)2 * cap;
+  // when the slice products are large (a rank-80 x 80 first slice takes 25.6 KB per warp in
+  // FP32)
+  const size_t tab = sizeof(int) * ((size_t)ch.rows[0] * ch.cols[ch.n - 1] + capP);
   const size_t esz_max = out_double ? sizeof(double) : sizeof(float);
-  const size_t per_warp = (size_t)3 * cap * esz_max;
+  const size_t per_warp = (size_t)(capA + capP + capZ) * esz_max;
   const int warps = (int)imax(1, imin(4, (int64_t)((kSmemOptIn - tab) / per_warp)));
   if ((size_t)warps * per_warp + tab > kSmemOptIn) return cudaErrorInvalidValue;
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t blocks = imax(1, imin((ch.count + warps - 1) / warps, (int64_t)sms * 8));
   auto go = [&](auto kern, size_t esz, auto* o) {
-    const size_t smem = (size_t)warps * 3 * cap * esz + tab;
+    const size_t smem = (size_t)warps * (capA + capP + capZ) * esz + tab;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    pdl_launch(kern, dim3((unsigned)blocks), dim3(warps * 32), smem, st, ch, o, (int)transposed, ld, cap, hi, lo,
-               kpad);
+    pdl_launch(kern, dim3((unsigned)blocks), dim3(warps * 32), smem, st, ch, o, (int)transposed, ld, capA, capP,
+               capZ, hi, lo, kpad);
   };
   if (out_double) {
     double* o = (double*)out;
