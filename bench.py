@@ -11,7 +11,11 @@ steps.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32|fp64]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 
-Prints one JSON line on rank 0.
+Prints one JSON line on rank 0.  Besides the headline step it carries (rank 0, N = 1) the
+FP32 / TF32 x 3 comparison legs, the image-shaped PSNR runs, the 1920 x 1080 x 3 x 50
+completion at the paper's video rank [80, 80, 3, 20] (`video_rank80`), the other north-star
+configurations and the CPU oracle baseline; `--no-image`, `--no-video-rank80`, `--no-configs`
+and `--no-cpu-baseline` skip them.
 """
 from __future__ import annotations
 
@@ -63,6 +67,8 @@ def parse():
                     help="override the iteration limit of the configurations' time-to-1e-3 runs")
     ap.add_argument("--video-rank80", action="store_true",
                     help="run only the 1920x1080x3x50 rank [80,80,3,20] completion and print it as one JSON line")
+    ap.add_argument("--no-video-rank80", action="store_true",
+                    help="skip the 1920x1080x3x50 rank [80,80,3,20] completion in the full run")
     ap.add_argument("--cpu-budget", type=float, default=3.0,
                     help="seconds of oracle work per configuration and thread setting (0: skip)")
     ap.add_argument("--oracle-probe", default=None, help=argparse.SUPPRESS)
@@ -377,6 +383,11 @@ def run_ours(args, rank, world, local):
         out["row_sampling"] = row_sampling(t, w, torch)
     if rank == 0 and not args.no_image:
         out["image"] = [image_quality(name, prec, torch) for name in ("image", "imagec")]
+        if not args.no_video_rank80:
+            try:
+                out["video_rank80"] = video_rank80(torch, prec)
+            except Exception as exc:          # reported, so that the other legs still print
+                out["video_rank80"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     # comparison path on the same device data (FP32 CUDA-core passes)
     for other in precs[1:]:
