@@ -13,7 +13,7 @@ steps.
 
 Prints one JSON line on rank 0.  Besides the headline step it carries (rank 0, N = 1) the
 FP32 / TF32 x 3 comparison legs, the image-shaped PSNR runs, the 1920 x 1080 x 3 x 50
-completion at the paper's video rank [80, 80, 3, 20] (`video_rank80`), the other north-star
+completion at the paper's video rank [80, 80, 3, 20] (`video_rank80`), the other benchmark
 configurations and the CPU oracle baseline; `--no-image`, `--no-video-rank80`, `--no-configs`
 and `--no-cpu-baseline` skip them.
 """
@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-rows", action="store_true", help="skip the row-sampling variant's measurement")
     ap.add_argument("--converge-iters", type=int, default=60)
     ap.add_argument("--no-configs", action="store_true",
-                    help="skip the other north-star configurations (30^3, 64^5, 1024x1024x256, sampled 128^4)")
+                    help="skip the other benchmark configurations (30^3, 64^5, 1024x1024x256, sampled 128^4)")
     ap.add_argument("--configs-only", action="store_true",
                     help="run only the other configurations and print them as one JSON line")
     ap.add_argument("--only-config", default=None, choices=[None, "tiny3", "cfg64", "video", "grad128"],
@@ -419,7 +419,7 @@ def run_ours(args, rank, world, local):
 
 
 def other_configs(args, torch, measured):
-    """The other spec configurations on this GPU (each with its own roofline and CPU
+    """The other benchmark configurations on this GPU (each with its own roofline and CPU
     baseline): 30^3 FP64 trajectory, 64^5 and 1024 x 1024 x 256 RStS iterations, sampled
     128^4 forward + backward."""
     pk, _ = peaks()
@@ -891,7 +891,7 @@ def fp64_roofline(w, ph, fp64_peak, steps=2):
 
 
 def run_tiny(torch, pk, budget):
-    """North-star configuration 1: 30^3 rank 3, 30 % missing, 10 % outliers, adaptive width,
+    """Benchmark configuration 1: 30^3 rank 3, 30 % missing, 10 % outliers, adaptive width,
     100 iterations on the FP64 path (launch-latency bound)."""
     from paper_2305_09044_gb300 import TRD, synth
     w = synth.WORKLOADS["tiny3"]
@@ -924,7 +924,7 @@ def run_tiny(torch, pk, budget):
 
 
 def run_sketched(torch, pk, name, precs, steps, budget, conv_iters, conv_budget):
-    """North-star configurations 3 (64^5 rank 10, sketch 24 per non-updated mode) and 4
+    """Benchmark configurations 3 (64^5 rank 10, sketch 24 per non-updated mode) and 4
     (1024 x 1024 x 256 rank 16, sketch 128 x 128 x full): SAWRTRD iterations with the RStS
     gather inside every core update; iterations/s, sampled entries/s, per-phase times, the
     gather's and the data passes' rooflines, and time to recovery error 1e-3 per precision."""
@@ -976,7 +976,7 @@ def run_sketched(torch, pk, name, precs, steps, budget, conv_iters, conv_budget)
 
 
 def run_sampled(torch, pk, steps, budget):
-    """North-star configuration 5: sampled correntropy loss of a 128^4 rank-20 TR model at
+    """Benchmark configuration 5: sampled correntropy loss of a 128^4 rank-20 TR model at
     2^24 observed entries (10 % outliers), forward + hand-written adjoint through the C ABI,
     FP32; forward+backward evaluations per second and sampled entries per second."""
     from paper_2305_09044_gb300 import TRD, synth

@@ -44,7 +44,7 @@ def _instance(dims, ranks, M, seed, scale=0.5):
 
 
 def test_adjoint_fp64_oracle_and_finite_differences(torch_cuda):
-    """8^4, rank 4 (the benchmark spec's FD instance): loss and gradient equal the oracle's, and
+    """8^4, rank 4 (the finite-difference check's instance): loss and gradient equal the oracle's, and
     the gradient matches FP64 central differences of the GPU loss at step 1e-6."""
     torch = torch_cuda
     from paper_2305_09044_gb300 import TRD

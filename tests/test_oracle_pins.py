@@ -440,7 +440,7 @@ def test_stop_matrix_is_gram_of_unfolding():
     assert O.stop_error(D, D) == 0.0
 
 
-# ---------------------------------------------------------------- convergence (north star c, d)
+# ---------------------------------------------------------------- convergence
 
 def _tiny_problem(seed_data, dims=(30, 30, 30), ranks=(3, 3, 3), observed=1.0):
     rng = np.random.default_rng(seed_data)
@@ -476,7 +476,7 @@ def test_monotone_decrease_exact_tr(observed):
 
 
 def test_planted_outliers_get_small_weights():
-    """North star (d): after AWRTRD with the adaptive kernel width, planted outliers whose
+    """After AWRTRD with the adaptive kernel width, planted outliers whose
     corruption exceeds 3.72 sigma (exp(-3.72^2/2) < 1e-3) get weights below 1e-3.
     Seeds: data 43, init 2002 (a sweep of 10 data/init seed pairs 42+i / 2001+i recovers
     6 exactly within 100 iterations; the other 4 stall near 0.32 relative error)."""
