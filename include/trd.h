@@ -135,6 +135,21 @@ const char* trd_last_error(const trd_t* handle);
 /* Static name of a status code. */
 const char* trd_status_string(trd_status status);
 
+/* The cut of the ring that the data passes use for a tensor (or a sketch of it) of mode sizes
+ * I[0..N-1] and ring ranks R[0..N-1] (Thm. 1's two-block form of the reconstruction): modes
+ * [0, c) form one block and [c, N) the other, and the contraction between them is
+ * R[0] R[c] = r_1 r_{c+1} wide.  The data passes take widths up to 256 (112 for TRD_FP64);
+ * among the cuts that fit, the one whose two blocks are closest in size (by the logarithm
+ * of their entry counts; the lowest c on a tie) is used.  Host only: needs no device and no
+ * handle, so a caller can check its ranks before allocating anything.
+ *   c_out      receives c (1 <= c < N)
+ *   width_out  receives R[0] R[c]
+ * Errors: TRD_EINVAL (a shape trd_create rejects, or a NULL output), TRD_ENOTIMPL (no cut
+ * fits: c_out and width_out then describe the most balanced cut, which the data passes
+ * reject). */
+trd_status trd_ring_cut(int N, const int64_t* I, const int32_t* R, int precision, int32_t* c_out,
+                        int32_t* width_out);
+
 /* ---------------------------------------------------------------- data and cores */
 
 /* Attach the data tensor X (Eq. TRWOPT) and its observation mask P (Eq. TRWOPT; bit-packed,

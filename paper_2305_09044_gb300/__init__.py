@@ -5,6 +5,6 @@ The compute lives in libtrd.so (CUDA kernels for sm_103a behind the C ABI of
 include/trd.h); `binding` marshals arguments to it, `synth` draws seeded workloads.
 The library is loaded lazily so that the workload generator imports without a GPU.
 """
-from .binding import TRD, TrdError, draw_indices, load  # noqa: F401
+from .binding import TRD, TrdError, draw_indices, load, ring_cut  # noqa: F401
 
-__all__ = ["TRD", "TrdError", "draw_indices", "load"]
+__all__ = ["TRD", "TrdError", "draw_indices", "load", "ring_cut"]

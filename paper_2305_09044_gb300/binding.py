@@ -37,7 +37,7 @@ EXPORTS = [
     "trd_recovery_error", "trd_sampled_fwd", "trd_sampled_bwd", "trd_set_profiling",
     "trd_get_profile", "trd_kernel_launches", "trd_sigma_from_residuals_noalloc",
     "trd_wait_selftest", "trd_set_graphs", "trd_sample_rows", "trd_psnr", "trd_set_gradient",
-    "trd_line_search_terms",
+    "trd_line_search_terms", "trd_ring_cut",
 ]
 
 
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
         "trd_psnr": [vp, vp, dbl, P(dbl)],
         "trd_set_gradient": [vp, C.c_int, P(dbl)],
         "trd_line_search_terms": [vp, C.c_int, dbl, C.c_int, P(dbl), P(dbl)],
+        "trd_ring_cut": [C.c_int, P(i64), P(i32), C.c_int, P(i32), P(i32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -156,6 +157,20 @@ def draw_indices(seed: int, t: int, k: int, j: int, N: int, I: int, s: int) -> n
     if st != TRD_OK:
         raise TrdError(st, "trd_draw_indices")
     return out
+
+
+def ring_cut(dims: Sequence[int], ranks: Sequence[int], precision: str = "fp32"):
+    """(c, r_1 r_{c+1}, fits) of trd_ring_cut: where the data passes cut the ring for these
+    mode sizes and ranks, and whether that width is one they take (host only)."""
+    lib = load()
+    N = len(dims)
+    I = (C.c_int64 * N)(*[int(d) for d in dims])
+    R = (C.c_int32 * N)(*[int(r) for r in ranks])
+    c, w = C.c_int32(), C.c_int32()
+    st = lib.trd_ring_cut(N, I, R, PRECISIONS[precision], C.byref(c), C.byref(w))
+    if st not in (TRD_OK, TRD_ENOTIMPL):
+        raise TrdError(st, "trd_ring_cut")
+    return int(c.value), int(w.value), st == TRD_OK
 
 
 class TRD:

@@ -315,25 +315,32 @@ void touch(trd_handle* h) {
 
 size_t elt(const trd_handle* h) { return is_fp64(h) ? sizeof(double) : sizeof(float); }
 
-// Balanced split of the view's modes into [0, c) and [c, N).
-Split choose_split(const trd_handle* h, const View& v, int k) {
-  Split sp;
-  // the most balanced cut among those whose contraction width r_1 r_{c+1} the data passes take
-  // (FP64 112, the other precisions 256); when none does, the most balanced cut (the pass then
-  // reports it).  A ring with two large neighbouring ranks (the paper's video rank [80, 80, 3,
-  // 20]) is cut through its small edges instead of through the balanced but 6400-wide one.
-  const int kmax = h->prec == TRD_FP64 ? 112 : 256;
+// The cut c of the ring (modes [0, c) and [c, N)) for mode sizes dim: the most balanced cut
+// (by the logarithm of the two blocks' entry counts) among those whose contraction width
+// R[0] R[c] the data passes take (FP64 112, the other precisions 256); when none does, the
+// most balanced cut (*fits = false; the pass then reports it).  A ring with two large
+// neighbouring ranks (the paper's video rank [80, 80, 3, 20]) is cut through its small edges
+// instead of through the balanced but 6400-wide one.
+int ring_cut(int N, const int64_t* dim, const int* R, int prec, bool* fits) {
+  const int kmax = prec == TRD_FP64 ? 112 : 256;
   double best = 1e300, best_fit = 1e300;
   int bestc = 1, fitc = -1;
-  for (int c = 1; c < h->N; ++c) {
+  for (int c = 1; c < N; ++c) {
     double a = 0, b = 0;
-    for (int m = 0; m < c; ++m) a += log((double)v.dim[m]);
-    for (int m = c; m < h->N; ++m) b += log((double)v.dim[m]);
+    for (int m = 0; m < c; ++m) a += log((double)dim[m]);
+    for (int m = c; m < N; ++m) b += log((double)dim[m]);
     const double cost = fabs(a - b);
     if (cost < best - 1e-12) { best = cost; bestc = c; }
-    if (h->R[0] * h->R[c] <= kmax && cost < best_fit - 1e-12) { best_fit = cost; fitc = c; }
+    if (R[0] * R[c] <= kmax && cost < best_fit - 1e-12) { best_fit = cost; fitc = c; }
   }
-  if (fitc > 0) bestc = fitc;
+  if (fits) *fits = fitc > 0;
+  return fitc > 0 ? fitc : bestc;
+}
+
+// Split of the view's modes into [0, c) and [c, N) at the cut above.
+Split choose_split(const trd_handle* h, const View& v, int k) {
+  Split sp;
+  const int bestc = ring_cut(h->N, v.dim, h->R, h->prec, nullptr);
   sp.c = bestc;
   sp.P_in = 1;
   sp.P_out = 1;
@@ -1612,22 +1619,39 @@ const char* trd_status_string(trd_status s) {
 
 const char* trd_last_error(const trd_t* h) { return h ? h->err.c_str() : "null handle"; }
 
+// The shape rules of trd_create (order, mode sizes, ranks, r_k r_{k+1}, entry count, precision).
+static bool valid_shape(int N, const int64_t* I, const int32_t* R, int precision) {
+  if (N < 3 || N > kMaxN || !I || !R) return false;
+  if (precision != TRD_FP64 && precision != TRD_FP32 && precision != TRD_BF16 && precision != TRD_TF32X3)
+    return false;
+  double logtot = 0;
+  for (int m = 0; m < N; ++m) {
+    if (I[m] < 1 || I[m] > (int64_t(1) << 31) - 1) return false;
+    if (R[m] < 1 || R[m] > kMaxR) return false;
+    logtot += log2((double)I[m]);
+  }
+  for (int m = 0; m < N; ++m)
+    if (R[m] * R[(m + 1) % N] > TRD_MAX_CORE_K) return false;
+  return logtot < 40.0;
+}
+
+trd_status trd_ring_cut(int N, const int64_t* I, const int32_t* R, int precision, int32_t* c_out,
+                        int32_t* width_out) {
+  if (!c_out || !width_out || !valid_shape(N, I, R, precision)) return TRD_EINVAL;
+  int Ri[kMaxN];
+  for (int m = 0; m < N; ++m) Ri[m] = R[m];
+  bool fits = false;
+  const int c = ring_cut(N, I, Ri, precision, &fits);
+  *c_out = c;
+  *width_out = Ri[0] * Ri[c];
+  return fits ? TRD_OK : TRD_ENOTIMPL;
+}
+
 trd_status trd_create(trd_t** out, int N, const int64_t* I, const int32_t* R, int precision,
                       void* cuda_stream) {
   if (!out) return TRD_EINVAL;
   *out = nullptr;
-  if (N < 3 || N > kMaxN || !I || !R) return TRD_EINVAL;
-  if (precision != TRD_FP64 && precision != TRD_FP32 && precision != TRD_BF16 && precision != TRD_TF32X3)
-    return TRD_EINVAL;
-  double logtot = 0;
-  for (int m = 0; m < N; ++m) {
-    if (I[m] < 1 || I[m] > (int64_t(1) << 31) - 1) return TRD_EINVAL;
-    if (R[m] < 1 || R[m] > kMaxR) return TRD_EINVAL;
-    logtot += log2((double)I[m]);
-  }
-  for (int m = 0; m < N; ++m)
-    if (R[m] * R[(m + 1) % N] > TRD_MAX_CORE_K) return TRD_EINVAL;
-  if (logtot >= 40.0) return TRD_EINVAL;
+  if (!valid_shape(N, I, R, precision)) return TRD_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();
